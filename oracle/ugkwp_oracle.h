@@ -1,0 +1,141 @@
+/*
+ * ugkwp_oracle.h -- CPU FP64 oracle of the UGKWP particle phase, the wave flux
+ * and the source iteration (Yang, Zhu, Liu, Xu, "Unified gas-kinetic
+ * wave-particle method for frequency-dependent radiation transport equation").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may include,
+ * link or call this code; only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark use it.  It shares no source with the
+ * CUDA path: it is a plain, slow, step-by-step restatement of the method.
+ *
+ * Conventions (same meaning as the C ABI of the product, declared separately):
+ *   cells are indexed c = iy*nx + ix; (cell, group) arrays are [c*G + g];
+ *   x-faces f = iy*(nx+1) + fx (face fx sits at x = fx*dx);
+ *   y-faces f = fy*nx + ix (face fy sits at y = fy*dy);
+ *   sides: 0 = x-, 1 = x+, 2 = y-, 3 = y+.
+ */
+#ifndef UGKWP_ORACLE_H
+#define UGKWP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_BC_REFLECT = 0, OR_BC_VACUUM = 1, OR_BC_BLACKBODY = 2 };
+enum { OR_SURVIVED = 0, OR_ABSORBED = 1, OR_ESCAPED = 2, OR_REMOVED = 3 };
+enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_CAPACITY = -3, OR_ERR_NOCONV = -4,
+       OR_ERR_NONFINITE = -5 };
+
+typedef struct {
+  int32_t dim, nx, ny, G;
+  int32_t grey;          /* 1: one grey group, b = 1, particles carry no frequency */
+  int32_t wave_order;    /* 1: cell-average upwind values, 2: van Leer linear reconstruction */
+  int32_t si_max_iters;
+  int32_t bc[4];
+  int32_t _pad0;
+  double dx, dy;
+  double sig_p, sig_q, sig_cap;   /* sigma = sigma0 * nu^p * T^q, capped (cap <= 0: none) */
+  double a, c, eps, dt;
+  double omega_ref;               /* reference particle energy (rho*V units) */
+  double si_tol;
+  double src_on;                  /* multiplies the patch source */
+  double bcT[4];
+  uint64_t seed;
+  uint32_t instance;
+  uint32_t _pad1;
+  const double* nu_edges;         /* [G+1] */
+  const double* sigma0;           /* [ncell] */
+  const double* cv;               /* [ncell] */
+  const double* src_T;            /* [ncell] or NULL */
+} or_problem;
+
+/* Structure-of-arrays particle set.  In 1D, ox holds mu and y, oy are 0. */
+typedef struct {
+  double *x, *y, *ox, *oy, *nu, *w;
+  uint64_t* id;
+  int32_t *cell, *grp;
+} or_particles;
+
+/* One record per particle processed in a step (survivors in, then newborns). */
+typedef struct {
+  uint64_t id;
+  int32_t fate, cell0, cell1, grp, nseg, _pad;
+  double x, y, ox, oy, nu, w, t_end;
+} or_record;
+
+typedef struct {
+  /* arrays owned by the caller */
+  double* W;       /* [ncell*G] particle net energy w^{fr,p} (in minus out) */
+  double* E_surv;  /* [ncell*G] energy of collisionless survivors by end cell */
+  double* E_abs;   /* [ncell*G] energy of collided particles by collision cell */
+  double* esc;     /* [4*G] particle energy leaving through each side */
+  double* inflow;  /* [4*G] particle energy entering from each side's ghost */
+  double* Fwave;   /* [nface*G] wave flux (x-faces then y-faces) */
+  double* Feq;     /* [nface*G] equilibrium flux of the last source iteration */
+  int32_t* N;      /* [nbins] birth counts, nbins = (ncell+4)*G */
+  double* omega;   /* [nbins] */
+  double* e_eff;   /* [nbins] */
+  /* scalars written by the oracle */
+  int64_t n_in, n_born, n_survived, n_absorbed, n_escaped, n_removed, n_segments;
+  int32_t si_iters, status;
+  double E_rad0, E_mat0, E_rad1, E_mat1;   /* sum V (rho/c) and sum V Cv T, before/after */
+  double bnd_in_macro, bnd_out_macro;      /* through boundary faces, energy units */
+  double bnd_in_part, bnd_out_part;        /* particles, energy units */
+  double src_in;
+} or_tallies;
+
+/* --- building blocks (each is pinned separately by the tests) --- */
+void   or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_uniform(uint32_t wa, uint32_t wb);
+double or_draw(const or_problem* P, uint64_t id, int64_t step, int64_t j);
+double or_sigma(const or_problem* P, int c, double nu, double T);
+double or_sigma_group(const or_problem* P, int c, int g, double T);
+double or_planck_integral(double x1, double x2);      /* (15/pi^4) int_x1^x2 t^3/(e^t-1) dt */
+double or_planck_dintegral(double x1, double x2);     /* (15/pi^4) int_x1^x2 t^4 e^t/(e^t-1)^2 dt */
+double or_phi(const or_problem* P, int g, double T);  /* angle-integrated group equilibrium */
+double or_dphi(const or_problem* P, int g, double T); /* its T-derivative */
+void   or_coefs(double x, double* f2, double* f4, double* f5, double* c4);
+double or_nu_cdf(double nlo, double nhi, double T, double nu);
+double or_sample_nu(double nlo, double nhi, double T, double eta);
+
+/* Stream one particle (Algorithm 1, steps 3-5).  If draws != NULL the
+ * uniforms are taken from it in order (n_draws of them) instead of Philox.
+ * Returns the fate.  trace_x/trace_t (nullable, cap trace_cap) receive the
+ * position and elapsed time at the end of every flight segment. */
+int or_stream_particle(const or_problem* P, const double* T, int64_t step,
+                       double* x, double* y, double* ox, double* oy, double nu,
+                       double w, uint64_t id, int32_t* cell, int32_t g,
+                       int newborn, int64_t first_draw,
+                       const double* draws, int64_t n_draws,
+                       or_tallies* tal, int32_t* nseg, double* t_end,
+                       double* trace_x, double* trace_t, int trace_cap, int* n_trace);
+
+int or_birth_counts(const or_problem* P, const double* T, const double* rho_h,
+                    or_tallies* tal, int64_t* n_new);
+
+int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
+                 const double* e_eff, double* Fwave);
+
+int or_source_iteration(const or_problem* P, const double* T_n, const double* rho_n,
+                        const double* R, double* T_out, double* rho_out,
+                        double* Feq_out, int* iters);
+
+/* One full time step (Algorithm 1).  Inputs T, rho, rho_h ([ncell], [ncell*G]) and
+ * n_in particles; outputs the new macroscopic state, the surviving particles
+ * (capacity cap_out) and, if rec != NULL, one record per processed particle. */
+int or_step(const or_problem* P, int64_t step,
+            const double* T, const double* rho, const double* rho_h,
+            int64_t n_in, const or_particles* pin,
+            double* T_out, double* rho_out, double* rho_h_out, double* rho_p_out,
+            or_particles* pout, int64_t cap_out, int64_t* n_out,
+            or_record* rec, int64_t rec_cap,
+            or_tallies* tal);
+
+/* Initial equilibrium rho_g = Phi_g(T0) per cell. */
+void or_init_rho(const or_problem* P, const double* T0, double* rho);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

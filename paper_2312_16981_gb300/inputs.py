@@ -1,0 +1,179 @@
+"""Problem descriptions and seeded synthetic workloads.
+
+This module holds no arithmetic of the method: it only lays out the inputs a
+user supplies -- the grid, the group edges, per-cell opacity scale and heat
+capacity, the initial temperature, boundary conditions, the reference particle
+weight and the seed.  Both the CUDA path and the CPU oracle consume the same
+``Problem``; nothing here evaluates opacities, Planck integrals or fluxes.
+
+Workloads are synthetic stand-ins shaped like the paper's Marshak-wave
+(Sec. 3.1, Eq. sigmaMarsharkMF) and Olson-type (Sec. 3.5-3.6) set-ups, in
+normalised units a = c = h = k = 1, eps = 1.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+BC_REFLECT, BC_VACUUM, BC_BLACKBODY = 0, 1, 2
+FP64, MIXED = 0, 1
+
+
+@dataclass
+class Problem:
+    """One UGKWP problem: a 1D slab or a 2D rectangle of uniform cells."""
+
+    dim: int
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    G: int
+    nu_edges: np.ndarray          # [G+1], increasing, > 0 (unused when grey)
+    sigma0: np.ndarray            # [ncell] opacity scale
+    cv: np.ndarray                # [ncell] heat capacity
+    T0: np.ndarray                # [ncell] initial material temperature
+    dt: float
+    sig_p: float = -3.0           # sigma = sigma0 * nu^p * T^q, capped
+    sig_q: float = -0.5
+    sig_cap: float = 1e6
+    grey: int = 0
+    a: float = 1.0
+    c: float = 1.0
+    eps: float = 1.0
+    bc: List[int] = field(default_factory=lambda: [BC_REFLECT] * 4)
+    bcT: List[float] = field(default_factory=lambda: [0.0] * 4)
+    src_T: Optional[np.ndarray] = None   # [ncell] source temperature, 0 = none
+    src_on: float = 0.0
+    omega_ref: float = 1e-6
+    seed: int = 0
+    instance: int = 0
+    si_tol: float = 1e-12
+    si_max_iters: int = 500
+    wave_order: int = 2
+    precision: int = FP64
+    particle_capacity: int = 1 << 20
+    n_steps: int = 1
+    name: str = "problem"
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * (self.ny if self.dim == 2 else 1)
+
+    @property
+    def nface(self) -> int:
+        ny = self.ny if self.dim == 2 else 1
+        n = (self.nx + 1) * ny
+        if self.dim == 2:
+            n += self.nx * (self.ny + 1)
+        return n
+
+    @property
+    def nbins(self) -> int:
+        return (self.ncell + 4) * self.G
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+def log_groups(G: int, nu_min: float, nu_max: float) -> np.ndarray:
+    """Logarithmically spaced group edges (Sec. 3, numerical set-up)."""
+    return np.geomspace(nu_min, nu_max, G + 1)
+
+
+# ----------------------------------------------------------------------------
+# The five workloads.  Unstated fields take the readings listed in the design
+# document (slab length 1, reflecting far side, Cv = 1, CFL-1 time steps for
+# the 2D cases, nu in [1e-3, 10] with cap 1e6).
+
+def grey_slab(nx: int = 100, steps: int = 100, omega_ref: float = 2.5e-7,
+              seed: int = 0) -> Problem:
+    """Grey 1D slab: sigma = 10, T0 = 0.01, black body T = 1 at x = 0,
+    reflecting at x = 1, Cv = 1, dt = 1e-3 (about 1e5 particles per step)."""
+    n = nx
+    return Problem(
+        dim=1, nx=n, ny=1, dx=1.0 / n, dy=1.0, G=1, grey=1,
+        nu_edges=np.array([0.0, 1.0]), sigma0=np.full(n, 10.0), cv=np.ones(n),
+        T0=np.full(n, 0.01), dt=1e-3, sig_p=0.0, sig_q=0.0, sig_cap=0.0,
+        bc=[BC_BLACKBODY, BC_REFLECT, BC_REFLECT, BC_REFLECT], bcT=[1.0, 0.0, 0.0, 0.0],
+        omega_ref=omega_ref, seed=seed, n_steps=steps, name="grey_slab_100x1",
+        particle_capacity=1 << 19)
+
+
+def multigroup_slab(nx: int = 200, G: int = 30, steps: int = 500,
+                    omega_ref: float = 1e-8, sigma0: float = 1e2,
+                    seed: int = 0, dt: float = 1e-4) -> Problem:
+    """Frequency-dependent 1D slab (Marshak-wave shape): sigma =
+    sigma0 nu^-3 T^-1/2 capped at 1e6, G log groups on [1e-3, 10], T = 1 black
+    body at x = 0 into T = 1e-3, reflecting at x = 1, dt = 1e-4."""
+    return Problem(
+        dim=1, nx=nx, ny=1, dx=1.0 / nx, dy=1.0, G=G, grey=0,
+        nu_edges=log_groups(G, 1e-3, 10.0), sigma0=np.full(nx, sigma0), cv=np.ones(nx),
+        T0=np.full(nx, 1e-3), dt=dt,
+        bc=[BC_BLACKBODY, BC_REFLECT, BC_REFLECT, BC_REFLECT], bcT=[1.0, 0.0, 0.0, 0.0],
+        omega_ref=omega_ref, seed=seed, n_steps=steps,
+        name="multigroup_slab_%dx%d" % (nx, G), particle_capacity=1 << 22)
+
+
+def checkerboard_2d(n: int = 256, G: int = 30, block: int = 16, patch: int = 32,
+                    steps: int = 100, omega_ref: float = 1e-9, seed: int = 0,
+                    precision: int = FP64) -> Problem:
+    """2D [0,1]^2 checkerboard of block x block cells alternating sigma0 = 1e3
+    and 1, same nu^-3 T^-1/2 law, G groups, isotropic T_s = 1 source in a
+    central patch x patch square, T0 = 1e-3, reflecting walls, dt = dx/c."""
+    ix, iy = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    thick = ((ix // block) + (iy // block)) % 2 == 0
+    sig0 = np.where(thick, 1e3, 1.0).reshape(-1).astype(np.float64)
+    lo, hi = n // 2 - patch // 2, n // 2 + patch // 2
+    src = np.zeros((n, n))
+    src[lo:hi, lo:hi] = 1.0
+    dx = 1.0 / n
+    return Problem(
+        dim=2, nx=n, ny=n, dx=dx, dy=dx, G=G, grey=0,
+        nu_edges=log_groups(G, 1e-3, 10.0), sigma0=sig0, cv=np.ones(n * n),
+        T0=np.full(n * n, 1e-3), dt=dx, src_T=src.reshape(-1), src_on=1.0,
+        bc=[BC_REFLECT] * 4, bcT=[0.0] * 4, omega_ref=omega_ref, seed=seed,
+        n_steps=steps, precision=precision, name="checkerboard_%dx%dx%d" % (n, n, G),
+        particle_capacity=1 << 25)
+
+
+def ensemble_slabs(n_instances: int = 256, seed: int = 0, steps: int = 100) -> List[Problem]:
+    """Ensemble of independent 1D slabs with uneven sizes: cells U{64..1024},
+    G in {8,16,32,64}, sigma0 log-U[1, 1e4], black-body T U[0.5, 2], target
+    particle counts log-U[1e4, 1e6].  Drawn from a seeded numpy generator."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for k in range(n_instances):
+        nx = int(rng.integers(64, 1025))
+        G = int(rng.choice([8, 16, 32, 64]))
+        s0 = float(10.0 ** rng.uniform(0.0, 4.0))
+        Tb = float(rng.uniform(0.5, 2.0))
+        target = float(10.0 ** rng.uniform(4.0, 6.0))
+        p = multigroup_slab(nx=nx, G=G, steps=steps, sigma0=s0, seed=seed)
+        p.bcT = [Tb, 0.0, 0.0, 0.0]
+        p.instance = k
+        # reference weight scaled with the energy a black body at Tb feeds in
+        p.omega_ref = 0.25 * Tb ** 4 * p.dt * steps / target
+        p.name = "ensemble_%d" % k
+        out.append(p)
+    return out
+
+
+def small_multigroup(nx: int = 24, G: int = 6, omega_ref: float = 2e-6, dt: float = 2e-3,
+                     seed: int = 0) -> Problem:
+    """A small multigroup slab that the oracle finishes in seconds but that
+    still spans several tiles of particles and a ragged tail."""
+    p = multigroup_slab(nx=nx, G=G, steps=10, omega_ref=omega_ref, seed=seed, dt=dt)
+    p.name = "small_multigroup_%dx%d" % (nx, G)
+    p.particle_capacity = 1 << 18
+    return p
+
+
+def small_checkerboard(n: int = 16, G: int = 4, omega_ref: float = 2e-6, seed: int = 0) -> Problem:
+    p = checkerboard_2d(n=n, G=G, block=4, patch=4, steps=5, omega_ref=omega_ref, seed=seed)
+    p.name = "small_checkerboard_%dx%dx%d" % (n, n, G)
+    p.particle_capacity = 1 << 18
+    return p
