@@ -1,0 +1,296 @@
+#!/usr/bin/env python
+"""Benchmark of the UGKWP time step on GB300.
+
+Workload: the 1D frequency-dependent slab (200 cells, 30 log groups on
+nu in [1e-3, 10], sigma = 1e2 nu^-3 T^-1/2 capped at 1e6, black body T = 1
+into T = 1e-3, dt = 1e-4, FP64), started from a seeded synthetic mid-run
+Marshak-front state holding 1e6 particles (the regime the 500-step run
+reaches).  A step is one pass of the whole hot path: birth counts and scan,
+wave flux, the particle kernel (sampling, streaming with t_f reset, tallies,
+compaction) and the source iteration.
+
+Metric: particle segments per second over the timed steps (device time from
+CUDA events on the launching stream, L2 flushed between timed steps), plus
+steps/s.  `--impl reference` times the CPU oracle on the same workload.
+Launch: `python bench.py --gpus N --steps K --warmup W`; for N > 1 under
+torch.distributed.run each rank runs an independent replica (the method has
+no cross-problem exchange) and the job value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2312_16981_gb300 import inputs as I  # noqa: E402
+
+N_PARTICLES = 1_000_000
+WORKLOAD = "multigroup_slab_200x30_fp64"
+METRIC = "particle segments/s"
+KERNELS_PER_STEP = 8   # birth, scan x3, wave, particles, source iteration, end of step
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def workload(rank: int = 0):
+    p = I.multigroup_slab()
+    p.instance = rank
+    s = I.synthetic_state(p, N_PARTICLES, seed=1)
+    return p, s
+
+
+def config_dict(p, n_particles, extra=None):
+    d = {"workload": WORKLOAD, "cells": p.ncell, "groups": p.G, "dt": p.dt,
+         "particles_at_start": n_particles, "state": "seeded synthetic Marshak front",
+         "precision": "fp64", "l2": "flushed between timed steps (512 MiB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_segments_per_s(p, s, n_sample, steps):
+    """The CPU oracle as it stands, on `steps` steps of a bounded sample."""
+    import oracle as O
+    op = O.OracleProblem(p)
+    parts = {k: v[:n_sample] for k, v in s["particles"].items()} if n_sample else s["particles"]
+    st = O.State(p, s["T"].copy(), s["rho"].copy(), s["rho_h"].copy(),
+                 O.ParticleSet.from_arrays(parts, cap=max(len(parts["id"]) * 2, 1 << 16)), s["step"])
+    segs, t = 0, 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st2, tal, _, status = O.step(op, st, cap_out=max(st.particles.n * 2, 1 << 16))
+        t += time.perf_counter() - t0
+        segs += tal.c.n_segments
+        st = st2
+    return segs, t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p, s = workload()
+    n_sample = 100_000
+    _ = oracle_segments_per_s(p, s, n_sample, max(args.warmup, 0) and 1)
+    segs, t = oracle_segments_per_s(p, s, n_sample, args.steps)
+    v = segs / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "segments/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(p, N_PARTICLES, {"sample": "first %d of %d particles per step" % (n_sample, N_PARTICLES)}),
+            "cpu_baseline": {"value": v, "unit": "segments/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d steps of the workload with %d of its %d particles (full 200x30 source iteration)" % (args.steps, n_sample, N_PARTICLES)},
+            "e2e": {"value": v, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def algorithmic_bytes(p, phase, n_in, n_out, si_iters):
+    """Algorithmic HBM bytes of one launch of a phase (see the design notes)."""
+    ncg = p.ncell * p.G
+    if phase == "particles":
+        per = 4 * 8 + 8 + 4   # x, mu, nu, w (FP64), id, bin key
+        return per * n_in + per * n_out + 3 * 8 * ncg
+    if phase == "source_iteration":
+        return si_iters * 10 * 8 * ncg
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2312_16981_gb300 import binding as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p, s = workload(rank)
+    sim = B.Simulation(p, device="cuda:%d" % local)
+    sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
+    for _ in range(max(args.warmup, 3)):
+        sim.step(1)
+    t = sim.tallies()
+    assert t["status_bits"] == 0, t["status_bits"]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda:%d" % local)
+
+    # ---- timed region (device time per step from CUDA events)
+    phases = np.zeros(6)
+    segs = 0
+    n_in_sum = n_out_sum = 0
+    si_sum = 0
+    ms_steps = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ms = sim.step_timed()
+            t = sim.tallies()
+            phases += np.array(ms)
+            ms_steps.append(ms[0])
+            segs += t["n_segments"]
+            n_in_sum += t["n_in"] + t["n_born"]
+            n_out_sum += t["n_survived"]
+            si_sum += t["si_iters"]
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.summary()
+    assert t["status_bits"] == 0, t["status_bits"]
+    total_ms = float(phases[0])
+    if world > 1:
+        tt = torch.tensor([total_ms, float(segs)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        total_ms_max, segs_all = float(mx[0]), float(tt[1])
+    else:
+        total_ms_max, segs_all = total_ms, float(segs)
+    value = segs_all / (total_ms_max / 1e3)
+
+    # ---- roofline of the dominant kernel
+    names = ["total", "birth_scan", "wave", "particles", "source_iteration", "end"]
+    dom = int(np.argmax(phases[1:])) + 1
+    pk, src = peaks()
+    K = args.steps
+    per_launch_ms = phases[dom] / K
+    abytes = algorithmic_bytes(p, names[dom], n_in_sum / K, n_out_sum / K, si_sum / K)
+    if abytes > 0:
+        ach = abytes / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                "peak_source": src, "algorithmic_bytes_per_launch": abytes}
+    else:
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": 0.0, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": 0.0, "traffic": None, "peak_source": src}
+
+    # ---- end to end through the C ABI with host buffers
+    Tdev = sim.device_array("T")
+    Rdev = sim.device_array("rho")
+    Th = torch.empty(Tdev.shape, dtype=torch.float64, pin_memory=True)
+    Rh = torch.empty(Rdev.shape, dtype=torch.float64, pin_memory=True)
+    Th.copy_(Tdev)
+    Rh.copy_(Rdev)
+    torch.cuda.synchronize()
+    e2e_segs = 0
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Tdev.copy_(Th, non_blocking=True)
+        Rdev.copy_(Rh, non_blocking=True)
+        sim.step(1)
+        Th.copy_(Tdev, non_blocking=True)
+        Rh.copy_(Rdev, non_blocking=True)
+        tt = sim.tallies()           # synchronises: the step's result is on the host
+        e2e_segs += tt["n_segments"]
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e = {"value": e2e_segs / e2e_s, "unit": "segments/s",
+           "h2d_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
+           "d2h_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
+           "what": "per step: H2D of T, rho from pinned host memory, ugkwp_step, D2H of T, rho and the tally report"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_sample = 100_000
+        osegs, ot = oracle_segments_per_s(p, s, n_sample, 3)
+        cpu = {"value": osegs / ot, "unit": "segments/s", "cores": 1, "kind": "oracle",
+               "sample": "3 oracle steps of the same workload with the first %d of %d particles "
+                         "(full 200x30 source iteration each step)" % (n_sample, N_PARTICLES)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
+                "steps": K, "warmup": args.warmup, "ms_per_step": total_ms_max / K,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config_dict(p, N_PARTICLES, {"parallelism": "replicas"}),
+                "steps_per_s": K / (total_ms_max / 1e3),
+                "phase_ms_per_step": {n: float(phases[i] / K) for i, n in enumerate(names)},
+                "particles_per_step": n_in_sum / K, "si_iters_per_step": si_sum / K,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": KERNELS_PER_STEP * K}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

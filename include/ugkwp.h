@@ -1,0 +1,206 @@
+/*
+ * ugkwp.h -- C ABI of the GB300 (sm_103a) implementation of the per-time-step
+ * particle phase of the unified gas-kinetic wave-particle (UGKWP) method for
+ * the frequency-dependent radiation transport equation, with the wave-part
+ * flux and the matrix-free source iteration around it.
+ *
+ * Method: Yang, Zhu, Liu, Xu, "Unified gas-kinetic wave-particle method for
+ * frequency-dependent radiation transport equation" -- Algorithm 1 (the time
+ * step), Eqs. particle-tf-formula, IhpFormula, wfrpFormula, macroSysFinal,
+ * the interface-reset remark, Eqs. Blinear/kg with App. A (frequency of a
+ * particle), App. B with Algorithm 2 (source iteration).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns UGKWP_OK (0) or a negative UGKWP_ERR_* code.  Nothing
+ *    throws across the ABI.  ugkwp_last_error() gives a message.
+ *  - The library never allocates device memory: the caller passes one device
+ *    workspace (size from ugkwp_workspace_size) and keeps ownership of it; the
+ *    handle itself is a small host allocation freed by ugkwp_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously; only ugkwp_tallies, ugkwp_get_state and
+ *    ugkwp_set_state synchronise the stream.
+ *  - Layout: cells c = iy*nx + ix; per (cell, group) arrays [c*G + g];
+ *    x-faces f = iy*(nx+1) + fx (at x = fx*dx), then y-faces nxface + fy*nx + ix;
+ *    sides 0 = x-, 1 = x+, 2 = y-, 3 = y+.  Normalised units h = k = 1.
+ *  - Errors found on the device during a step (particle capacity exceeded,
+ *    source iteration not converged, non-finite state, a bounded wait that
+ *    timed out) are latched in a status word and returned by ugkwp_tallies.
+ */
+#ifndef UGKWP_H
+#define UGKWP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UGKWP_OK 0
+#define UGKWP_ERR_ARG (-1)          /* invalid argument or inconsistent problem */
+#define UGKWP_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define UGKWP_ERR_CAPACITY (-3)     /* more surviving particles than capacity, or a bin overflowed */
+#define UGKWP_ERR_NOCONV (-4)       /* source iteration hit si_max_iters */
+#define UGKWP_ERR_NONFINITE (-5)    /* NaN/Inf in the macroscopic state */
+#define UGKWP_ERR_TIMEOUT (-6)      /* a bounded device-side wait gave up */
+#define UGKWP_ERR_WORKSPACE (-7)    /* workspace too small or misaligned */
+#define UGKWP_ERR_UNSUPPORTED (-8)  /* a combination this build does not implement */
+
+/* device status bits (ugkwp_tallies.status_bits) */
+#define UGKWP_ST_CAPACITY 1u
+#define UGKWP_ST_NOCONV 2u
+#define UGKWP_ST_NONFINITE 4u
+#define UGKWP_ST_TIMEOUT 8u
+
+enum { UGKWP_BC_REFLECT = 0, UGKWP_BC_VACUUM = 1, UGKWP_BC_BLACKBODY = 2 };
+enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
+
+/* Problem statement (Sec. 3 numerical set-up; all pointers are HOST pointers,
+ * read during ugkwp_init only; the caller keeps ownership).
+ *   sigma(nu, T) = sigma0[c] * nu^sig_p * T^sig_q, capped at sig_cap (> 0)
+ *   (Eq. sigmaMarsharkMF: sig_p = -3, sig_q = -1/2); group opacity by Simpson's
+ *   rule on the edges and midpoint of each group.  grey = 1: one group, no
+ *   frequency dependence, Phi = a c T^4.
+ *   Boundary sides: REFLECT (mirror), VACUUM (no inflow), BLACKBODY at bcT
+ *   (1D only in this build).  src_T: a cell with src_T > 0 receives
+ *   src_on * c * dt * Phi_g(src_T) in rho_g each step. */
+typedef struct ugkwp_problem {
+  int32_t dim;            /* 1 or 2 */
+  int32_t nx, ny;         /* cells; ny ignored (1) in 1D */
+  int32_t G;              /* groups, 1..64 */
+  int32_t grey;           /* 1: grey (G == 1) */
+  int32_t wave_order;     /* 1: cell averages, 2: van Leer reconstruction of rho_h */
+  int32_t si_max_iters;   /* source-iteration cap */
+  int32_t precision;      /* UGKWP_FP64 or UGKWP_MIXED (particle state in FP32) */
+  int32_t bc[4];
+  int32_t _pad0;
+  double dx, dy;
+  double sig_p, sig_q, sig_cap;
+  double a, c, eps, dt;
+  double omega_ref;       /* reference particle energy (rho*V units), <= 0: no particles */
+  double si_tol;          /* source-iteration tolerance (relative, max norm) */
+  double src_on;
+  double bcT[4];
+  uint64_t seed;          /* Philox key = (seed_lo, seed_hi ^ instance) */
+  uint32_t instance;
+  uint32_t _pad1;
+  int64_t particle_capacity;   /* maximum surviving particles held between steps */
+  const double* nu_edges;      /* [G+1] increasing, > 0 (ignored when grey) */
+  const double* sigma0;        /* [ncell] */
+  const double* cv;            /* [ncell] */
+  const double* T0;            /* [ncell] initial material temperature */
+  const double* rho0;          /* [ncell*G] initial rho_g, or NULL: Phi_g(T0) */
+  const double* src_T;         /* [ncell] or NULL */
+} ugkwp_problem;
+
+typedef struct ugkwp_handle ugkwp_handle;
+
+/* Device pointers into the workspace (valid until the next step) and host
+ * copies of the per-step counters and energy ledger. */
+typedef struct ugkwp_tally_report {
+  const double* T;        /* [ncell]   material temperature T^{n+1} */
+  const double* rho;      /* [ncell*G] rho^{n+1} */
+  const double* rho_h;    /* [ncell*G] wave part rho^{n+1} - rho^p */
+  const double* rho_p;    /* [ncell*G] particle part (collisionless survivors / V) */
+  const double* W;        /* [ncell*G] w^{fr,p}, particle energy in minus out (Eq. wfrpFormula) */
+  const double* Fwave;    /* [nface*G] wave-part flux F^{fr,wave} */
+  const double* Feq;      /* [nface*G] equilibrium flux of the last source iterate */
+  const double* esc;      /* [4*G] particle energy escaped per side */
+  const double* inflow;   /* [4*G] particle energy entering per side */
+  int64_t step;           /* steps completed */
+  int64_t n_particles;    /* particles alive after the last step */
+  int64_t n_in, n_born, n_survived, n_absorbed, n_escaped, n_removed, n_segments;
+  int32_t si_iters;
+  uint32_t status_bits;   /* UGKWP_ST_* latched since init */
+  double E_rad0, E_mat0, E_rad1, E_mat1;      /* sum V rho/c, sum V Cv T before/after */
+  double bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
+} ugkwp_tally_report;
+
+/* Host-side structure-of-arrays particle buffers for ugkwp_get_state /
+ * ugkwp_set_state (parity checks, checkpoints).  1D: ox holds mu; y, oy are 0. */
+typedef struct ugkwp_particles_host {
+  double *x, *y, *ox, *oy, *nu, *w;
+  uint64_t* id;
+  int32_t *cell, *grp;
+} ugkwp_particles_host;
+
+/* Per-particle end record written when a record buffer is attached
+ * (ugkwp_set_records): one per particle processed in a step, at its position
+ * in the step's processing order (survivors first, then newborns). */
+typedef struct ugkwp_record {
+  uint64_t id;
+  int32_t fate;           /* 0 survived, 1 absorbed (collided), 2 escaped, 3 removed */
+  int32_t cell0, cell1, grp, nseg, _pad;
+  double x, y, ox, oy, nu, w, t_end;
+} ugkwp_record;
+
+/* Workspace bytes for problem p (256-byte aligned pieces). */
+int ugkwp_workspace_size(const ugkwp_problem* p, size_t* bytes);
+
+/* Copy the problem into the device workspace, set the initial state
+ * (T0, rho0 or Phi_g(T0), no particles) and return a handle.  The workspace
+ * must stay allocated until ugkwp_destroy. */
+int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* stream,
+               ugkwp_handle** out);
+
+/* Advance nsteps time steps (Algorithm 1), asynchronously on `stream`:
+ * birth counts and scan (Eq. IhpFormula), streaming of survivors and
+ * newborns with t_f reset and tallies (Eqs. particle-tf-formula, wfrpFormula),
+ * wave flux (Sec. 2.2), source iteration (App. B), compaction. */
+int ugkwp_step(ugkwp_handle* h, int nsteps, void* stream);
+
+/* One step like ugkwp_step, bracketed by CUDA events on `stream`, then
+ * synchronise: phase_ms[0] the whole step, [1] birth counts and their scan,
+ * [2] wave flux, [3] particle kernel, [4] source iteration, [5] end of step
+ * (device milliseconds).  For measurement; the events are created and
+ * destroyed per call. */
+int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms);
+
+/* Synchronise `stream` and fill *out (device pointers + host counters). */
+int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream);
+
+/* Copy the state to host arrays: T [ncell], rho, rho_h, rho_p [ncell*G] (any
+ * may be NULL) and up to `cap` particles; *n receives the particle count.
+ * Synchronises `stream`. */
+int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, double* rho_p,
+                    ugkwp_particles_host* parts, int64_t cap, int64_t* n, void* stream);
+
+/* Replace the state from host arrays (T, rho, rho_h required; parts may be
+ * NULL when n == 0) and set the step counter.  Synchronises `stream`. */
+int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const double* rho_h,
+                    const ugkwp_particles_host* parts, int64_t n, int64_t step, void* stream);
+
+/* Attach (or detach with NULL) a DEVICE buffer of `cap` ugkwp_record entries
+ * that the next steps fill; records beyond cap are dropped. */
+int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap);
+
+const char* ugkwp_last_error(const ugkwp_handle* h);
+void ugkwp_destroy(ugkwp_handle* h);
+
+/* ---- kernel-level entry points (device pointers; parity tests of single
+ * building blocks).  Each is asynchronous on `stream`. ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters [n*4] under key (k0, k1). */
+int ugkwp_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, int64_t n,
+                 void* stream);
+
+/* Group Planck fractions b_g(T) = (15/pi^4) int_{nu_g/T}^{nu_{g+1}/T} t^3/(e^t-1) dt and
+ * the derivative fractions d_g(T) with dPhi_g/dT = a c T^3 d_g(T), for n temperatures:
+ * d_b, d_d are [n*G] (d_d may be NULL).  d_nu_edges is a DEVICE array [G+1]. */
+int ugkwp_planck(const double* d_T, int64_t n, const double* d_nu_edges, int G, double* d_b,
+                 double* d_d, void* stream);
+
+/* Time-integrated coefficients at x = dt/tau for n values: d_out [n*4] =
+ * (C2/tau, C4 - e, (C5 + dt e/2)/tau, C4) (Eq. C2Formula and the UGKS free-flux
+ * coefficients). */
+int ugkwp_coefs(const double* d_x, int64_t n, double* d_out, void* stream);
+
+/* Frequency of a particle from uniforms d_eta [n] for group [nlo, nhi] at
+ * temperature T (App. A, linear-frequency sampling) into d_nu [n]. */
+int ugkwp_sample_nu(const double* d_eta, int64_t n, double nlo, double nhi, double T, double* d_nu,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,347 @@
+"""ctypes binding of ``libugkwp.so`` (C ABI in ``include/ugkwp.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of the library.  PyTorch supplies the device workspace and the stream.  There
+is no CPU fallback: if the library or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+from .inputs import Problem
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libugkwp.so")
+_lib = None
+
+OK = 0
+ERRORS = {-1: "ARG", -2: "CUDA", -3: "CAPACITY", -4: "NOCONV", -5: "NONFINITE", -6: "TIMEOUT",
+          -7: "WORKSPACE", -8: "UNSUPPORTED"}
+ST_CAPACITY, ST_NOCONV, ST_NONFINITE, ST_TIMEOUT = 1, 2, 4, 8
+
+_dp = C.POINTER(C.c_double)
+
+
+class UGKWPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("ugkwp error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class CProblem(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("G", C.c_int32),
+        ("grey", C.c_int32), ("wave_order", C.c_int32), ("si_max_iters", C.c_int32),
+        ("precision", C.c_int32), ("bc", C.c_int32 * 4), ("_pad0", C.c_int32),
+        ("dx", C.c_double), ("dy", C.c_double),
+        ("sig_p", C.c_double), ("sig_q", C.c_double), ("sig_cap", C.c_double),
+        ("a", C.c_double), ("c", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
+        ("omega_ref", C.c_double), ("si_tol", C.c_double), ("src_on", C.c_double),
+        ("bcT", C.c_double * 4), ("seed", C.c_uint64), ("instance", C.c_uint32),
+        ("_pad1", C.c_uint32), ("particle_capacity", C.c_int64),
+        ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("T0", _dp), ("rho0", _dp),
+        ("src_T", _dp),
+    ]
+
+
+class CTallyReport(C.Structure):
+    _fields_ = [
+        ("T", C.c_void_p), ("rho", C.c_void_p), ("rho_h", C.c_void_p), ("rho_p", C.c_void_p),
+        ("W", C.c_void_p), ("Fwave", C.c_void_p), ("Feq", C.c_void_p), ("esc", C.c_void_p),
+        ("inflow", C.c_void_p),
+        ("step", C.c_int64), ("n_particles", C.c_int64), ("n_in", C.c_int64), ("n_born", C.c_int64),
+        ("n_survived", C.c_int64), ("n_absorbed", C.c_int64), ("n_escaped", C.c_int64),
+        ("n_removed", C.c_int64), ("n_segments", C.c_int64), ("si_iters", C.c_int32),
+        ("status_bits", C.c_uint32),
+        ("E_rad0", C.c_double), ("E_mat0", C.c_double), ("E_rad1", C.c_double), ("E_mat1", C.c_double),
+        ("bnd_in_macro", C.c_double), ("bnd_in_part", C.c_double), ("bnd_out_part", C.c_double),
+        ("src_in", C.c_double),
+    ]
+
+
+class CParticlesHost(C.Structure):
+    _fields_ = [("x", _dp), ("y", _dp), ("ox", _dp), ("oy", _dp), ("nu", _dp), ("w", _dp),
+                ("id", C.POINTER(C.c_uint64)), ("cell", C.POINTER(C.c_int32)),
+                ("grp", C.POINTER(C.c_int32))]
+
+
+RECORD = np.dtype([
+    ("id", np.uint64), ("fate", np.int32), ("cell0", np.int32), ("cell1", np.int32),
+    ("grp", np.int32), ("nseg", np.int32), ("_pad", np.int32),
+    ("x", np.float64), ("y", np.float64), ("ox", np.float64), ("oy", np.float64),
+    ("nu", np.float64), ("w", np.float64), ("t_end", np.float64)])
+
+FUNCTIONS = {
+    "ugkwp_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "ugkwp_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ugkwp_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "ugkwp_step_timed": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float)]),
+    "ugkwp_tallies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ugkwp_get_state": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp, C.c_void_p, C.c_int64,
+                                  C.POINTER(C.c_int64), C.c_void_p]),
+    "ugkwp_set_state": (C.c_int, [C.c_void_p, _dp, _dp, _dp, C.c_void_p, C.c_int64, C.c_int64,
+                                  C.c_void_p]),
+    "ugkwp_set_records": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "ugkwp_last_error": (C.c_char_p, [C.c_void_p]),
+    "ugkwp_destroy": (None, [C.c_void_p]),
+    "ugkwp_philox": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64, C.c_void_p]),
+    "ugkwp_planck": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_void_p]),
+    "ugkwp_coefs": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ugkwp_sample_nu": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                  C.c_void_p, C.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (built by ``paper_2312_16981_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libugkwp.so is not built (%s); run __graft_entry__.build()" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in FUNCTIONS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, handle=None):
+    if code != OK:
+        msg = load().ugkwp_last_error(handle)
+        raise UGKWPError(code, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class _HostProblem:
+    """C problem struct plus the host arrays it points to."""
+
+    def __init__(self, p: Problem, rho0: Optional[np.ndarray] = None):
+        keep = {}
+
+        def arr(a, n):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.size < n:
+                raise ValueError("array of %d values where the problem needs %d" % (a.size, n))
+            keep[id(a)] = a
+            return a.ctypes.data_as(_dp)
+
+        s = CProblem()
+        s.dim, s.nx, s.ny, s.G = p.dim, p.nx, (p.ny if p.dim == 2 else 1), p.G
+        s.grey, s.wave_order, s.si_max_iters, s.precision = p.grey, p.wave_order, p.si_max_iters, p.precision
+        for i in range(4):
+            s.bc[i] = int(p.bc[i])
+            s.bcT[i] = float(p.bcT[i])
+        s.dx, s.dy = p.dx, p.dy
+        s.sig_p, s.sig_q, s.sig_cap = p.sig_p, p.sig_q, p.sig_cap
+        s.a, s.c, s.eps, s.dt = p.a, p.c, p.eps, p.dt
+        s.omega_ref, s.si_tol, s.src_on = p.omega_ref, p.si_tol, p.src_on
+        s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
+        s.particle_capacity = int(p.particle_capacity)
+        s.nu_edges = arr(p.nu_edges, p.G + 1)
+        s.sigma0 = arr(p.sigma0, p.ncell)
+        s.cv = arr(p.cv, p.ncell)
+        s.T0 = arr(p.T0, p.ncell)
+        s.rho0 = arr(rho0, p.ncell * p.G)
+        s.src_T = arr(p.src_T, p.ncell)
+        self.s = s
+        self._keep = keep
+
+
+def workspace_bytes(p: Problem) -> int:
+    hp = _HostProblem(p)
+    n = C.c_size_t()
+    _check(load().ugkwp_workspace_size(C.byref(hp.s), C.byref(n)))
+    return n.value
+
+
+class Simulation:
+    """One UGKWP problem resident on a GPU."""
+
+    def __init__(self, p: Problem, device: str = "cuda:0", rho0: Optional[np.ndarray] = None,
+                 stream=None):
+        import torch
+        L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the UGKWP library has no CPU path")
+        self.p = p
+        self.device = torch.device(device)
+        self.stream = stream
+        hp = _HostProblem(p, rho0)
+        n = C.c_size_t()
+        _check(L.ugkwp_workspace_size(C.byref(hp.s), C.byref(n)))
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.ugkwp_init(C.byref(hp.s), C.c_void_p(_ptr(self.workspace)), n.value,
+                                C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self.h = h
+        self._records = None
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().ugkwp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check(load().ugkwp_step(self.h, int(n), C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def step_timed(self):
+        """One step; returns device milliseconds: total, birth+scan, wave flux,
+        particles, source iteration, end of step."""
+        ms = (C.c_float * 6)()
+        _check(load().ugkwp_step_timed(self.h, C.c_void_p(_stream_ptr(self.stream)), ms), self.h)
+        return list(ms)
+
+    def tallies(self) -> Dict:
+        r = CTallyReport()
+        _check(load().ugkwp_tallies(self.h, C.byref(r), C.c_void_p(_stream_ptr(self.stream))), self.h)
+        out = {k: getattr(r, k) for k, _ in CTallyReport._fields_[9:]}
+        out["ptr"] = {k: getattr(r, k) for k, _ in CTallyReport._fields_[:9]}
+        return out
+
+    def device_array(self, name: str):
+        """A torch view (float64, on the device) of a tally array."""
+        import torch
+        r = self.tallies()
+        p = self.p
+        n = {"T": p.ncell, "rho": p.ncell * p.G, "rho_h": p.ncell * p.G, "rho_p": p.ncell * p.G,
+             "W": p.ncell * p.G, "Fwave": p.nface * p.G, "Feq": p.nface * p.G, "esc": 4 * p.G,
+             "inflow": 4 * p.G}[name]
+        off = r["ptr"][name] - _ptr(self.workspace)
+        return self.workspace[off: off + 8 * n].view(torch.float64)
+
+    def get_state(self, cap: Optional[int] = None) -> Dict[str, np.ndarray]:
+        p = self.p
+        T = np.zeros(p.ncell)
+        rho = np.zeros(p.ncell * p.G)
+        rho_h = np.zeros_like(rho)
+        rho_p = np.zeros_like(rho)
+        n = C.c_int64()
+        L = load()
+        sp = C.c_void_p(_stream_ptr(self.stream))
+        _check(L.ugkwp_get_state(self.h, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
+                                 rho_h.ctypes.data_as(_dp), rho_p.ctypes.data_as(_dp), None, 0,
+                                 C.byref(n), sp), self.h)
+        m = n.value if cap is None else min(cap, n.value)
+        parts = {f: np.zeros(max(m, 1)) for f in ("x", "y", "ox", "oy", "nu", "w")}
+        parts["id"] = np.zeros(max(m, 1), dtype=np.uint64)
+        parts["cell"] = np.zeros(max(m, 1), dtype=np.int32)
+        parts["grp"] = np.zeros(max(m, 1), dtype=np.int32)
+        cs = CParticlesHost(*[parts[f].ctypes.data_as(_dp) for f in ("x", "y", "ox", "oy", "nu", "w")],
+                            parts["id"].ctypes.data_as(C.POINTER(C.c_uint64)),
+                            parts["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
+                            parts["grp"].ctypes.data_as(C.POINTER(C.c_int32)))
+        if m > 0:
+            _check(L.ugkwp_get_state(self.h, None, None, None, None, C.byref(cs), m, C.byref(n), sp), self.h)
+        parts = {k: v[:m] for k, v in parts.items()}
+        return dict(T=T, rho=rho, rho_h=rho_h, rho_p=rho_p, particles=parts, n=n.value)
+
+    def set_state(self, T, rho, rho_h, particles: Optional[Dict[str, np.ndarray]] = None,
+                  step: int = 0):
+        L = load()
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        rho_h = np.ascontiguousarray(rho_h, dtype=np.float64)
+        n = 0 if particles is None else len(particles["id"])
+        keep = []
+        cs = None
+        if n:
+            arrs = {}
+            for f in ("x", "y", "ox", "oy", "nu", "w"):
+                arrs[f] = np.ascontiguousarray(particles[f], dtype=np.float64)
+            arrs["id"] = np.ascontiguousarray(particles["id"], dtype=np.uint64)
+            arrs["cell"] = np.ascontiguousarray(particles["cell"], dtype=np.int32)
+            arrs["grp"] = np.ascontiguousarray(particles["grp"], dtype=np.int32)
+            keep.append(arrs)
+            cs = CParticlesHost(*[arrs[f].ctypes.data_as(_dp) for f in ("x", "y", "ox", "oy", "nu", "w")],
+                                arrs["id"].ctypes.data_as(C.POINTER(C.c_uint64)),
+                                arrs["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
+                                arrs["grp"].ctypes.data_as(C.POINTER(C.c_int32)))
+        _check(L.ugkwp_set_state(self.h, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
+                                 rho_h.ctypes.data_as(_dp), None if cs is None else C.byref(cs), n,
+                                 int(step), C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def attach_records(self, cap: int):
+        import torch
+        self._records = torch.zeros(cap * RECORD.itemsize, dtype=torch.uint8, device=self.device)
+        self._rec_cap = cap
+        _check(load().ugkwp_set_records(self.h, C.c_void_p(_ptr(self._records)), cap), self.h)
+
+    def detach_records(self):
+        _check(load().ugkwp_set_records(self.h, None, 0), self.h)
+        self._records = None
+
+    def records(self, n: int) -> np.ndarray:
+        import torch
+        torch.cuda.synchronize(self.device)
+        n = min(n, self._rec_cap)
+        raw = self._records[: n * RECORD.itemsize].cpu().numpy()
+        return raw.view(RECORD).copy()
+
+
+# ---------------------------------------------------------------------------
+# kernel-level entry points (torch tensors on the device)
+
+def philox(ctr, k0: int, k1: int):
+    """ctr: int32/uint32-valued tensor [n, 4] on the device -> [n, 4] words (int64 view)."""
+    import torch
+    ctr = ctr.contiguous().to(torch.int32)
+    out = torch.empty_like(ctr)
+    _check(load().ugkwp_philox(C.c_void_p(_ptr(ctr)), k0 & 0xFFFFFFFF, k1 & 0xFFFFFFFF,
+                               C.c_void_p(_ptr(out)), ctr.shape[0], C.c_void_p(_stream_ptr())))
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def planck(T, nu_edges):
+    """b_g(T) and d_g(T) for temperatures T [n] and edges [G+1] (device float64)."""
+    import torch
+    T = T.contiguous().to(torch.float64)
+    nu = nu_edges.contiguous().to(torch.float64)
+    G = nu.numel() - 1
+    b = torch.empty(T.numel(), G, dtype=torch.float64, device=T.device)
+    d = torch.empty_like(b)
+    _check(load().ugkwp_planck(C.c_void_p(_ptr(T)), T.numel(), C.c_void_p(_ptr(nu)), G,
+                               C.c_void_p(_ptr(b)), C.c_void_p(_ptr(d)), C.c_void_p(_stream_ptr())))
+    return b, d
+
+
+def coefs(x):
+    import torch
+    x = x.contiguous().to(torch.float64)
+    out = torch.empty(x.numel(), 4, dtype=torch.float64, device=x.device)
+    _check(load().ugkwp_coefs(C.c_void_p(_ptr(x)), x.numel(), C.c_void_p(_ptr(out)),
+                              C.c_void_p(_stream_ptr())))
+    return out
+
+
+def sample_nu(eta, nlo: float, nhi: float, T: float):
+    import torch
+    eta = eta.contiguous().to(torch.float64)
+    nu = torch.empty_like(eta)
+    _check(load().ugkwp_sample_nu(C.c_void_p(_ptr(eta)), eta.numel(), nlo, nhi, T,
+                                  C.c_void_p(_ptr(nu)), C.c_void_p(_stream_ptr())))
+    return nu

@@ -1,0 +1,435 @@
+// ugkwp_api.cu -- host runtime behind the C ABI declared in include/ugkwp.h:
+// workspace layout, problem upload, the per-step launch sequence of
+// Algorithm 1, state and tally transfer, and the kernel-level entry points.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ugkwp.h"
+#include "ugkwp_device.cuh"
+#include "ugkwp_launch.h"
+
+using ugkwp::Ctrl;
+using ugkwp::Dev;
+
+struct ugkwp_handle {
+  Dev d;
+  ugkwp_problem p;     // scalars; host pointers cleared after init
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  char err[512];
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(ugkwp_handle* h, int code, const char* msg) {
+  char* dst = h ? h->err : g_err;
+  snprintf(dst, 512, "%s", msg);
+  return code;
+}
+
+int cuda_fail(ugkwp_handle* h, cudaError_t e, const char* where) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+  return fail(h, UGKWP_ERR_CUDA, buf);
+}
+
+#define CK(call, h)                                  \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+long long ncell_of(const ugkwp_problem* p) { return (long long)p->nx * (p->dim == 2 ? p->ny : 1); }
+long long nxface_of(const ugkwp_problem* p) { return (long long)(p->nx + 1) * (p->dim == 2 ? p->ny : 1); }
+long long nface_of(const ugkwp_problem* p) {
+  return nxface_of(p) + (p->dim == 2 ? (long long)p->nx * (p->ny + 1) : 0);
+}
+
+int validate(const ugkwp_problem* p, ugkwp_handle* h) {
+  if (!p) return fail(h, UGKWP_ERR_ARG, "problem is NULL");
+  if (p->dim != 1 && p->dim != 2) return fail(h, UGKWP_ERR_ARG, "dim must be 1 or 2");
+  if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) return fail(h, UGKWP_ERR_ARG, "nx, ny must be >= 1");
+  if (p->G < 1 || p->G > ugkwp::kMaxG) return fail(h, UGKWP_ERR_ARG, "G must be in 1..64");
+  if (p->grey && p->G != 1) return fail(h, UGKWP_ERR_ARG, "grey requires G == 1");
+  if (!(p->dx > 0) || (p->dim == 2 && !(p->dy > 0))) return fail(h, UGKWP_ERR_ARG, "dx, dy must be > 0");
+  if (!(p->dt > 0) || !(p->c > 0) || !(p->eps > 0) || !(p->a > 0))
+    return fail(h, UGKWP_ERR_ARG, "dt, c, eps, a must be > 0");
+  if (!p->sigma0 || !p->cv || !p->T0) return fail(h, UGKWP_ERR_ARG, "sigma0, cv, T0 are required");
+  if (!p->grey && !p->nu_edges) return fail(h, UGKWP_ERR_ARG, "nu_edges required unless grey");
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] < 0 || p->bc[s] > 2) return fail(h, UGKWP_ERR_ARG, "bad boundary condition");
+    if (p->dim == 1 && s < 2 && p->bc[s] == UGKWP_BC_BLACKBODY && !(p->bcT[s] > 0))
+      return fail(h, UGKWP_ERR_ARG, "black-body side needs bcT > 0");
+    if (p->dim == 2 && p->bc[s] == UGKWP_BC_BLACKBODY)
+      return fail(h, UGKWP_ERR_UNSUPPORTED, "black-body sides are 1D only in this build");
+  }
+  if (p->wave_order != 1 && p->wave_order != 2) return fail(h, UGKWP_ERR_ARG, "wave_order must be 1 or 2");
+  if (p->si_max_iters < 1) return fail(h, UGKWP_ERR_ARG, "si_max_iters must be >= 1");
+  if (p->precision != UGKWP_FP64) return fail(h, UGKWP_ERR_UNSUPPORTED, "only FP64 particles in this build");
+  if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
+  const long long nbins = (ncell_of(p) + 4) * p->G;
+  if (nbins >= (1ll << 24)) return fail(h, UGKWP_ERR_ARG, "(ncell+4)*G must be < 2^24 (particle id layout)");
+  return UGKWP_OK;
+}
+
+// Bump allocator over the workspace; with base == nullptr it only sizes.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(long long n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (size_t)(n > 0 ? n : 0);
+    return p;
+  }
+};
+
+void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
+  const long long nc = ncell_of(p), G = p->G, ncg = nc * G, nb = (nc + 4) * G;
+  const long long nf = nface_of(p), P = p->particle_capacity;
+  d.nu_edges = cv.take<double>(G + 1);
+  d.sigma0 = cv.take<double>(nc);
+  d.cv = cv.take<double>(nc);
+  d.src = p->src_T ? cv.take<double>(ncg) : nullptr;
+  d.ghost_phi = cv.take<double>(4 * G);
+  d.ghost_sig = cv.take<double>(4 * G);
+  d.T = cv.take<double>(nc);
+  d.rho = cv.take<double>(ncg);
+  d.rho_h = cv.take<double>(ncg);
+  d.rho_p = cv.take<double>(ncg);
+  d.sigT = cv.take<double>(ncg);
+  d.sT = cv.take<double>(nc);
+  d.N = cv.take<uint32_t>(nb);
+  d.off = cv.take<uint32_t>(nb + 1);
+  d.part = cv.take<uint32_t>(ugkwp::scan_parts((int)nb) + 1);
+  d.omega = cv.take<double>(nb);
+  d.e_eff = cv.take<double>(nb);
+  d.khat = cv.take<double>(nb);
+  d.W = cv.take<double>(ncg);
+  d.E_surv = cv.take<double>(ncg);
+  d.esc = cv.take<double>(4 * G);
+  d.inflow = cv.take<double>(4 * G);
+  d.Fwave = cv.take<double>(nf * G);
+  d.Feq = cv.take<double>(nf * G);
+  d.R = cv.take<double>(ncg);
+  d.Tk[0] = cv.take<double>(nc);
+  d.Tk[1] = cv.take<double>(nc);
+  d.sigk[0] = cv.take<double>(ncg);
+  d.sigk[1] = cv.take<double>(ncg);
+  d.phik[0] = cv.take<double>(ncg);
+  d.phik[1] = cv.take<double>(ncg);
+  d.dphik = cv.take<double>(ncg);
+  d.ctrl = cv.take<Ctrl>(1);
+  *src_T_tmp = d.R;   // scratch during init only
+  for (int b = 0; b < 2; ++b) {
+    d.px[b] = cv.take<double>(P);
+    d.pox[b] = cv.take<double>(P);
+    d.py[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
+    d.poy[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
+    d.pnu[b] = cv.take<double>(P);
+    d.pw[b] = cv.take<double>(P);
+    d.pid[b] = cv.take<unsigned long long>(P);
+    d.pkey[b] = cv.take<uint32_t>(P);
+  }
+}
+
+void fill_scalars(const ugkwp_problem* p, Dev& d) {
+  d.dim = p->dim;
+  d.nx = p->nx;
+  d.ny = p->dim == 2 ? p->ny : 1;
+  d.G = p->G;
+  d.ncell = (int)ncell_of(p);
+  d.nbins = (d.ncell + 4) * p->G;
+  d.nface = (int)nface_of(p);
+  d.nxface = (int)nxface_of(p);
+  d.grey = p->grey;
+  d.wave_order = p->wave_order;
+  d.si_max_iters = p->si_max_iters;
+  d.precision = p->precision;
+  for (int s = 0; s < 4; ++s) { d.bc[s] = p->bc[s]; d.bcT[s] = p->bcT[s]; }
+  d.dx = p->dx;
+  d.dy = p->dim == 2 ? p->dy : 1.0;
+  d.vol = p->dim == 2 ? p->dx * p->dy : p->dx;
+  d.sig_p = p->grey ? 0.0 : p->sig_p;
+  d.sig_q = p->sig_q;
+  d.sig_cap = p->sig_cap;
+  d.a = p->a;
+  d.c = p->c;
+  d.eps = p->eps;
+  d.dt = p->dt;
+  d.v = p->c / p->eps;
+  d.rate_f = p->c / (p->eps * p->eps);
+  d.omega_ref = p->omega_ref;
+  d.si_tol = p->si_tol;
+  d.src_on = p->src_on;
+  d.key0 = (uint32_t)p->seed;
+  d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
+  d.capacity = p->particle_capacity;
+  d.rec = nullptr;
+  d.rec_cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ugkwp_workspace_size(const ugkwp_problem* p, size_t* bytes) {
+  int st = validate(p, nullptr);
+  if (st) return st;
+  if (!bytes) return fail(nullptr, UGKWP_ERR_ARG, "bytes is NULL");
+  Carver cv{nullptr};
+  Dev d{};
+  double* tmp;
+  carve(p, cv, d, &tmp);
+  *bytes = cv.off + 256;
+  return UGKWP_OK;
+}
+
+int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* stream,
+               ugkwp_handle** out) {
+  if (!out) return fail(nullptr, UGKWP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int st = validate(p, nullptr);
+  if (st) return st;
+  size_t need = 0;
+  ugkwp_workspace_size(p, &need);
+  if (!d_workspace || bytes < need)
+    return fail(nullptr, UGKWP_ERR_WORKSPACE, "workspace missing or smaller than ugkwp_workspace_size");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256)
+    return fail(nullptr, UGKWP_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  ugkwp_handle* h = new (std::nothrow) ugkwp_handle;
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "out of host memory");
+  h->err[0] = 0;
+  h->p = *p;
+  h->ws = d_workspace;
+  h->ws_bytes = bytes;
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver cv{static_cast<char*>(d_workspace)};
+  Dev& d = h->d;
+  d = Dev{};
+  double* src_T_tmp = nullptr;
+  carve(p, cv, d, &src_T_tmp);
+  fill_scalars(p, d);
+  const long long nc = d.ncell, G = d.G, ncg = nc * G;
+  // zero everything but the particle buffers
+  const size_t head = (size_t)((char*)d.px[0] - (char*)d_workspace);
+  auto bad = [&](cudaError_t e, const char* w) { int r = cuda_fail(h, e, w); snprintf(g_err, 512, "%s", h->err); delete h; return r; };
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(d_workspace, 0, head, s)) != cudaSuccess) return bad(e, "memset");
+  std::vector<double> edges(G + 1);
+  if (p->grey) { edges[0] = 0.0; edges[1] = 1.0; }
+  else for (int g = 0; g <= G; ++g) edges[g] = p->nu_edges[g];
+  if ((e = cudaMemcpyAsync((void*)d.nu_edges, edges.data(), sizeof(double) * (G + 1), cudaMemcpyHostToDevice, s))) return bad(e, "nu_edges");
+  if ((e = cudaMemcpyAsync((void*)d.sigma0, p->sigma0, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "sigma0");
+  if ((e = cudaMemcpyAsync((void*)d.cv, p->cv, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "cv");
+  if ((e = cudaMemcpyAsync(d.T, p->T0, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "T0");
+  if (p->rho0) {
+    if ((e = cudaMemcpyAsync(d.rho, p->rho0, sizeof(double) * ncg, cudaMemcpyHostToDevice, s))) return bad(e, "rho0");
+    if ((e = cudaMemcpyAsync(d.rho_h, p->rho0, sizeof(double) * ncg, cudaMemcpyHostToDevice, s))) return bad(e, "rho0");
+  }
+  if (p->src_T)
+    if ((e = cudaMemcpyAsync(src_T_tmp, p->src_T, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "src_T");
+  if ((e = ugkwp::launch_init_tables(d, p->src_T ? src_T_tmp : nullptr, p->rho0 ? 0 : 1, s))) return bad(e, "init kernel");
+  if ((e = cudaStreamSynchronize(s))) return bad(e, "init sync");
+  h->p.nu_edges = h->p.sigma0 = h->p.cv = h->p.T0 = h->p.rho0 = h->p.src_T = nullptr;
+  *out = h;
+  return UGKWP_OK;
+}
+
+int ugkwp_step(ugkwp_handle* h, int nsteps, void* stream) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  if (nsteps < 0) return fail(h, UGKWP_ERR_ARG, "nsteps < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int n = 0; n < nsteps; ++n) {
+    CK(ugkwp::launch_birth_and_scan(h->d, s), h);
+    CK(ugkwp::launch_wave(h->d, s), h);
+    CK(ugkwp::launch_stream(h->d, s), h);
+    CK(ugkwp::launch_si(h->d, s), h);
+    CK(ugkwp::launch_end_step(h->d, s), h);
+  }
+  return UGKWP_OK;
+}
+
+int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms) {
+  if (!h || !phase_ms) return fail(h, UGKWP_ERR_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&ev[i]), h);
+  int rc = UGKWP_OK;
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  if (!e) e = ugkwp::launch_birth_and_scan(h->d, s);
+  if (!e) e = cudaEventRecord(ev[1], s);
+  if (!e) e = ugkwp::launch_wave(h->d, s);
+  if (!e) e = cudaEventRecord(ev[2], s);
+  if (!e) e = ugkwp::launch_stream(h->d, s);
+  if (!e) e = cudaEventRecord(ev[3], s);
+  if (!e) e = ugkwp::launch_si(h->d, s);
+  if (!e) e = cudaEventRecord(ev[4], s);
+  if (!e) e = ugkwp::launch_end_step(h->d, s);
+  if (!e) e = cudaEventRecord(ev[5], s);
+  if (!e) e = cudaEventSynchronize(ev[5]);
+  if (!e) {
+    cudaEventElapsedTime(&phase_ms[0], ev[0], ev[5]);
+    for (int i = 1; i < 6; ++i) cudaEventElapsedTime(&phase_ms[i], ev[i - 1], ev[i]);
+  } else {
+    rc = cuda_fail(h, e, "timed step");
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
+int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream) {
+  if (!h || !out) return fail(h, UGKWP_ERR_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  Ctrl c;
+  CK(cudaMemcpyAsync(&c, h->d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
+  CK(cudaStreamSynchronize(s), h);
+  const Dev& d = h->d;
+  out->T = d.T; out->rho = d.rho; out->rho_h = d.rho_h; out->rho_p = d.rho_p; out->W = d.W;
+  out->Fwave = d.Fwave; out->Feq = d.Feq; out->esc = d.esc; out->inflow = d.inflow;
+  out->step = (int64_t)c.step;
+  out->n_particles = (int64_t)c.n_part[c.cur];
+  out->n_in = (int64_t)c.n_in; out->n_born = (int64_t)c.n_born; out->n_survived = (int64_t)c.n_survived;
+  out->n_absorbed = (int64_t)c.n_absorbed; out->n_escaped = (int64_t)c.n_escaped;
+  out->n_removed = (int64_t)c.n_removed; out->n_segments = (int64_t)c.n_segments;
+  out->si_iters = (int32_t)c.si_iters;
+  out->status_bits = c.status;
+  out->E_rad0 = c.E_rad0; out->E_mat0 = c.E_mat0; out->E_rad1 = c.E_rad1; out->E_mat1 = c.E_mat1;
+  out->bnd_in_macro = c.bnd_in_macro; out->bnd_in_part = c.bnd_in_part;
+  out->bnd_out_part = c.bnd_out_part; out->src_in = c.src_in;
+  return UGKWP_OK;
+}
+
+int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, double* rho_p,
+                    ugkwp_particles_host* parts, int64_t cap, int64_t* n, void* stream) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dev& d = h->d;
+  const size_t ncg = (size_t)d.ncell * d.G;
+  Ctrl c;
+  CK(cudaMemcpyAsync(&c, d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
+  CK(cudaStreamSynchronize(s), h);
+  if (T) CK(cudaMemcpyAsync(T, d.T, sizeof(double) * d.ncell, cudaMemcpyDeviceToHost, s), h);
+  if (rho) CK(cudaMemcpyAsync(rho, d.rho, sizeof(double) * ncg, cudaMemcpyDeviceToHost, s), h);
+  if (rho_h) CK(cudaMemcpyAsync(rho_h, d.rho_h, sizeof(double) * ncg, cudaMemcpyDeviceToHost, s), h);
+  if (rho_p) CK(cudaMemcpyAsync(rho_p, d.rho_p, sizeof(double) * ncg, cudaMemcpyDeviceToHost, s), h);
+  const long long np = (long long)c.n_part[c.cur];
+  if (n) *n = np;
+  if (parts && cap > 0) {
+    const long long m = np < cap ? np : cap;
+    const unsigned b = c.cur;
+    std::vector<uint32_t> key(m > 0 ? m : 1);
+    if (m > 0) {
+      CK(cudaMemcpyAsync(parts->x, d.px[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(parts->ox, d.pox[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(parts->nu, d.pnu[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(parts->w, d.pw[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(parts->id, d.pid[b], sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(key.data(), d.pkey[b], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s), h);
+      if (d.dim == 2) {
+        CK(cudaMemcpyAsync(parts->y, d.py[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+        CK(cudaMemcpyAsync(parts->oy, d.poy[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+      }
+    }
+    CK(cudaStreamSynchronize(s), h);
+    for (long long i = 0; i < m; ++i) {
+      parts->cell[i] = (int32_t)(key[i] / (uint32_t)d.G);
+      parts->grp[i] = (int32_t)(key[i] % (uint32_t)d.G);
+      if (d.dim == 1) { parts->y[i] = 0.0; parts->oy[i] = 0.0; }
+    }
+  }
+  CK(cudaStreamSynchronize(s), h);
+  return UGKWP_OK;
+}
+
+int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const double* rho_h,
+                    const ugkwp_particles_host* parts, int64_t n, int64_t step, void* stream) {
+  if (!h || !T || !rho || !rho_h) return fail(h, UGKWP_ERR_ARG, "NULL argument");
+  if (n < 0 || n > h->d.capacity) return fail(h, UGKWP_ERR_CAPACITY, "n exceeds particle capacity");
+  if (n > 0 && !parts) return fail(h, UGKWP_ERR_ARG, "particles missing");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dev& d = h->d;
+  const size_t ncg = (size_t)d.ncell * d.G;
+  CK(cudaMemcpyAsync(d.T, T, sizeof(double) * d.ncell, cudaMemcpyHostToDevice, s), h);
+  CK(cudaMemcpyAsync(d.rho, rho, sizeof(double) * ncg, cudaMemcpyHostToDevice, s), h);
+  CK(cudaMemcpyAsync(d.rho_h, rho_h, sizeof(double) * ncg, cudaMemcpyHostToDevice, s), h);
+  std::vector<uint32_t> key(n > 0 ? n : 1);
+  for (long long i = 0; i < n; ++i) {
+    if (parts->cell[i] < 0 || parts->cell[i] >= d.ncell || parts->grp[i] < 0 || parts->grp[i] >= d.G)
+      return fail(h, UGKWP_ERR_ARG, "particle cell or group out of range");
+    key[i] = (uint32_t)(parts->cell[i] * d.G + parts->grp[i]);
+  }
+  if (n > 0) {
+    CK(cudaMemcpyAsync(d.px[0], parts->x, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.pox[0], parts->ox, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.pnu[0], parts->nu, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.pw[0], parts->w, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.pid[0], parts->id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.pkey[0], key.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s), h);
+    if (d.dim == 2) {
+      CK(cudaMemcpyAsync(d.py[0], parts->y, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+      CK(cudaMemcpyAsync(d.poy[0], parts->oy, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+    }
+  }
+  Ctrl c;
+  CK(cudaMemcpyAsync(&c, d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
+  CK(cudaStreamSynchronize(s), h);
+  c.cur = 0;
+  c.n_part[0] = (unsigned long long)n;
+  c.n_part[1] = 0;
+  c.step = (unsigned long long)step;
+  CK(cudaMemcpyAsync(d.ctrl, &c, sizeof c, cudaMemcpyHostToDevice, s), h);
+  CK(cudaStreamSynchronize(s), h);
+  return UGKWP_OK;
+}
+
+int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  static_assert(sizeof(ugkwp_record) == sizeof(ugkwp::RecordOut), "record layout");
+  h->d.rec = reinterpret_cast<ugkwp::RecordOut*>(d_records);
+  h->d.rec_cap = d_records ? cap : 0;
+  return UGKWP_OK;
+}
+
+const char* ugkwp_last_error(const ugkwp_handle* h) { return h ? h->err : g_err; }
+
+void ugkwp_destroy(ugkwp_handle* h) { delete h; }
+
+int ugkwp_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, int64_t n,
+                 void* stream) {
+  if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return fail(nullptr, UGKWP_ERR_ARG, "bad arguments");
+  if (n == 0) return UGKWP_OK;
+  CK(ugkwp::launch_unit_philox(d_ctr, k0, k1, d_out, n, (cudaStream_t)stream), nullptr);
+  return UGKWP_OK;
+}
+
+int ugkwp_planck(const double* d_T, int64_t n, const double* d_nu_edges, int G, double* d_b,
+                 double* d_d, void* stream) {
+  if (n < 0 || G < 1 || (n > 0 && (!d_T || !d_nu_edges || !d_b)))
+    return fail(nullptr, UGKWP_ERR_ARG, "bad arguments");
+  if (n == 0) return UGKWP_OK;
+  CK(ugkwp::launch_unit_planck(d_T, n, d_nu_edges, G, d_b, d_d, (cudaStream_t)stream), nullptr);
+  return UGKWP_OK;
+}
+
+int ugkwp_coefs(const double* d_x, int64_t n, double* d_out, void* stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_out))) return fail(nullptr, UGKWP_ERR_ARG, "bad arguments");
+  if (n == 0) return UGKWP_OK;
+  CK(ugkwp::launch_unit_coefs(d_x, n, d_out, (cudaStream_t)stream), nullptr);
+  return UGKWP_OK;
+}
+
+int ugkwp_sample_nu(const double* d_eta, int64_t n, double nlo, double nhi, double T, double* d_nu,
+                    void* stream) {
+  if (n < 0 || !(nhi > nlo) || (n > 0 && (!d_eta || !d_nu))) return fail(nullptr, UGKWP_ERR_ARG, "bad arguments");
+  if (n == 0) return UGKWP_OK;
+  CK(ugkwp::launch_unit_sample(d_eta, n, nlo, nhi, T, d_nu, (cudaStream_t)stream), nullptr);
+  return UGKWP_OK;
+}
+
+}  // extern "C"

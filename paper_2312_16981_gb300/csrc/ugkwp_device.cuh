@@ -1,0 +1,363 @@
+// ugkwp_device.cuh -- device building blocks of the UGKWP particle phase on
+// sm_103a: counter-based random numbers, opacities, Planck group fractions,
+// time-integrated flux coefficients and the linear-frequency sampler.
+//
+// Method: Yang, Zhu, Liu, Xu, "Unified gas-kinetic wave-particle method for
+// frequency-dependent radiation transport equation".
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ugkwp {
+
+constexpr int kMaxG = 64;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kPi4over15 = kPi * kPi * kPi * kPi / 15.0;   // int_0^inf t^3/(e^t-1) dt
+constexpr double k15overPi4 = 15.0 / (kPi * kPi * kPi * kPi);
+
+enum { BC_REFLECT = 0, BC_VACUUM = 1, BC_BLACKBODY = 2 };
+enum { FATE_SURVIVED = 0, FATE_ABSORBED = 1, FATE_ESCAPED = 2, FATE_REMOVED = 3 };
+enum : uint32_t { ST_CAPACITY = 1u, ST_NOCONV = 2u, ST_NONFINITE = 4u, ST_TIMEOUT = 8u };
+
+// Bits of a newborn's 64-bit identity: (birth step << 44) | (bin << 20) | k.
+constexpr int kIdBinShift = 20;
+constexpr int kIdStepShift = 44;
+constexpr uint32_t kMaxPerBin = (1u << 20) - 1u;
+
+// --------------------------------------------------------------------------
+// Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform in (0,1): the 52 top bits m of (a, b), then m 2^-52 + 2^-53 (exact).
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
+  const unsigned long long m = ((unsigned long long)a << 20) | (unsigned long long)(b >> 12);
+  return __ll2double_rn((long long)m) * 0x1p-52 + 0x1p-53;
+}
+
+// The draw sequence of one particle in one step: draw j comes from Philox
+// block j/2 of counter (id_lo, id_hi, step, j/2), words (0,1) for even j and
+// (2,3) for odd j; one Philox evaluation serves two draws.
+struct Draws {
+  uint32_t id_lo, id_hi, step, j, held;   // held = 1 + index of the Philox block in blk
+  uint4 blk;
+  __device__ __forceinline__ void init(unsigned long long id, uint32_t s, uint32_t first) {
+    id_lo = (uint32_t)id;
+    id_hi = (uint32_t)(id >> 32);
+    step = s;
+    j = first;
+    held = 0;
+  }
+  __device__ __forceinline__ double next(uint32_t k0, uint32_t k1) {
+    const uint32_t b = j >> 1;
+    if (held != b + 1u) {
+      blk = philox4x32_10(make_uint4(id_lo, id_hi, step, b), k0, k1);
+      held = b + 1u;
+    }
+    const double u = (j & 1u) ? u01(blk.z, blk.w) : u01(blk.x, blk.y);
+    ++j;
+    return u;
+  }
+};
+
+// --------------------------------------------------------------------------
+// Problem constants and device pointers, passed to every kernel by value.
+struct Dev {
+  // geometry / model
+  int dim, nx, ny, G, ncell, nbins, nface, nxface;
+  int grey, wave_order, si_max_iters, precision;
+  int bc[4];
+  double dx, dy, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
+  double v;          // c/eps, particle speed
+  double rate_f;     // c/eps^2: 1/tau = rate_f * sigma
+  double omega_ref, si_tol, src_on;
+  double bcT[4];
+  uint32_t key0, key1;
+  long long capacity;
+  // constant inputs
+  const double* nu_edges;   // [G+1]
+  const double* sigma0;     // [ncell]
+  const double* cv;         // [ncell]
+  const double* src;        // [ncell*G] per-step source increment of rho (or null)
+  const double* ghost_phi;  // [4*G] Phi_g(T_b) per side
+  const double* ghost_sig;  // [4*G] sigma_g(T_b) per side (sigma0 of the adjacent cell)
+  // state
+  double* T;        // [ncell]   T^n, then T^{n+1}
+  double* rho;      // [ncell*G] rho^n, then rho^{n+1}
+  double* rho_h;    // [ncell*G]
+  double* rho_p;    // [ncell*G]
+  // per-step work arrays
+  double* sigT;     // [ncell*G] sigma_g(T^n)
+  double* sT;       // [ncell]   sigma0 T^q
+  uint32_t* N;      // [nbins]
+  uint32_t* off;    // [nbins+1] exclusive scan of N
+  uint32_t* part;   // [scan partials]
+  double* omega;    // [nbins]
+  double* e_eff;    // [nbins]
+  double* khat;     // [nbins] sampler slope in units of B(nu_mid)
+  double* W;        // [ncell*G]
+  double* E_surv;   // [ncell*G]
+  double* esc;      // [4*G]
+  double* inflow;   // [4*G]
+  double* Fwave;    // [nface*G]
+  double* Feq;      // [nface*G]
+  double* R;        // [ncell*G] constant part of the rho equation
+  double* Tk[2];    // [ncell] iterates
+  double* sigk[2];  // [ncell*G]
+  double* phik[2];  // [ncell*G]
+  double* dphik;    // [ncell*G]
+  // particles: two structure-of-arrays buffers, selected by ctrl->cur
+  double* px[2];
+  double* py[2];
+  double* pox[2];
+  double* poy[2];
+  double* pnu[2];
+  double* pw[2];
+  unsigned long long* pid[2];
+  uint32_t* pkey[2];    // bin c*G + g
+  // control block and optional records
+  struct Ctrl* ctrl;
+  struct RecordOut* rec;
+  long long rec_cap;
+};
+
+// Record layout identical to ugkwp_record in the public header.
+struct RecordOut {
+  unsigned long long id;
+  int fate, cell0, cell1, grp, nseg, pad;
+  double x, y, ox, oy, nu, w, t_end;
+};
+
+// Device control block: counters, status, barrier and reduction slots.
+struct Ctrl {
+  unsigned long long step;
+  unsigned long long n_part[2];   // particles held in buffer 0/1
+  unsigned int cur;               // buffer holding this step's input
+  unsigned int status;            // ST_* bits, latched
+  unsigned long long n_new, n_out;
+  unsigned long long n_in, n_born, n_survived, n_absorbed, n_escaped, n_removed, n_segments;
+  unsigned int si_iters;
+  unsigned int bar_count;         // grid barrier arrivals (monotone)
+  unsigned int bar_timeout_spins; // bounded-wait limit (0: default)
+  unsigned int pad0;
+  unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)
+  double E_rad0, E_mat0, E_rad1, E_mat1, bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
+};
+
+// --------------------------------------------------------------------------
+// Opacity sigma(nu, T) = sigma0 nu^p T^q, capped (Eq. sigmaMarsharkMF form).
+__device__ __forceinline__ double pow_fast(double b, double e) {
+  if (e == 0.0) return 1.0;
+  if (e == -3.0) return 1.0 / (b * b * b);
+  if (e == -0.5) return 1.0 / sqrt(b);
+  if (e == 1.0) return b;
+  return pow(b, e);
+}
+
+__device__ __forceinline__ double cap_sigma(const Dev& d, double s) {
+  return (d.sig_cap > 0.0 && !(s <= d.sig_cap)) ? d.sig_cap : s;
+}
+
+// sigma0*T^q for cell c at temperature T
+__device__ __forceinline__ double sigma_T(const Dev& d, int c, double T) {
+  return d.sigma0[c] * pow_fast(T, d.sig_q);
+}
+
+// Simpson group opacity (Sec. 3: edges and midpoint, weights 1-4-1).
+__device__ __forceinline__ double sigma_group(const Dev& d, double sT, int g) {
+  if (d.grey) return cap_sigma(d, sT);
+  const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b);
+  const double sa = cap_sigma(d, sT * pow_fast(a, d.sig_p));
+  const double sm = cap_sigma(d, sT * pow_fast(m, d.sig_p));
+  const double sb = cap_sigma(d, sT * pow_fast(b, d.sig_p));
+  return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
+}
+
+// --------------------------------------------------------------------------
+// Planck integrals by series (in place of quadrature):
+//   lower part L(x) = int_0^x t^3/(e^t-1) dt = x^3/3 - x^4/8 + sum_m B_2m x^{2m+3}/((2m+3)(2m)!),
+//     used for x <= 2 (radius of convergence 2 pi; 16 terms reach 1e-17);
+//   upper part U(x) = int_x^inf = sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4),
+//     used for x > 2 (ceil(39/x) terms).
+__host__ __device__ constexpr double fact_d(int n) { return n <= 1 ? 1.0 : n * fact_d(n - 1); }
+__host__ __device__ constexpr double bern_coef(long long num, long long den, int m) {
+  return ((double)num / (double)den) / ((2.0 * m + 3.0) * fact_d(2 * m));
+}
+// B_2 .. B_32 as exact rationals
+__device__ constexpr double kBern[16] = {
+    bern_coef(1, 6, 1),         bern_coef(-1, 30, 2),          bern_coef(1, 42, 3),
+    bern_coef(-1, 30, 4),       bern_coef(5, 66, 5),           bern_coef(-691, 2730, 6),
+    bern_coef(7, 6, 7),         bern_coef(-3617, 510, 8),      bern_coef(43867, 798, 9),
+    bern_coef(-174611, 330, 10), bern_coef(854513, 138, 11),   bern_coef(-236364091, 2730, 12),
+    bern_coef(8553103, 6, 13),  bern_coef(-23749461029LL, 870, 14),
+    bern_coef(8615841276005LL, 14322, 15), bern_coef(-7709321041217LL, 510, 16)};
+
+__device__ __forceinline__ double planck_lower(double x) {
+  const double y = x * x;
+  double s = kBern[15];
+#pragma unroll
+  for (int m = 14; m >= 0; --m) s = fma(s, y, kBern[m]);
+  // x^3 (1/3 - x/8 + y s)
+  return x * x * x * fma(y, s, fma(-0.125, x, 1.0 / 3.0));
+}
+
+__device__ __forceinline__ double planck_upper(double x, double e1) {
+  // e1 = exp(-x); terms n = 1..nt with e^{-nx}
+  const int nt = x >= 39.0 ? 1 : (int)(39.0 / x) + 1;
+  const double x2 = x * x, x3 = x2 * x;
+  double en = e1, s = 0.0;
+#pragma unroll
+  for (int n = 1; n <= 20; ++n) {
+    if (n > nt) break;
+    const double r = 1.0 / (double)n;   // folded at compile time (unrolled)
+    const double poly = r * fma(r, fma(r, fma(6.0, r, 6.0 * x), 3.0 * x2), x3);
+    s = fma(en, poly, s);
+    en *= e1;
+  }
+  return s;
+}
+
+// Per edge: value V (L(x) if x <= 2 else U(x)), flag lower, and x^4/(e^x - 1).
+struct EdgeVal {
+  double V, g4;
+  bool lower;
+};
+
+__device__ __forceinline__ EdgeVal planck_edge(double x) {
+  EdgeVal r;
+  if (!(x > 0.0)) { r.V = 0.0; r.g4 = 0.0; r.lower = true; return r; }
+  if (x <= 2.0) {
+    r.lower = true;
+    r.V = planck_lower(x);
+    const double x2 = x * x;
+    r.g4 = x2 * x2 / expm1(x);
+  } else {
+    r.lower = false;
+    if (x > 740.0) { r.V = 0.0; r.g4 = 0.0; return r; }
+    const double e1 = exp(-x);
+    r.V = planck_upper(x, e1);
+    const double x2 = x * x;
+    r.g4 = x2 * x2 * e1 / (1.0 - e1);
+  }
+  return r;
+}
+
+// b = (15/pi^4) int_{x_lo}^{x_hi} t^3/(e^t-1) dt from the two edge values.
+__device__ __forceinline__ double planck_fraction(const EdgeVal& lo, const EdgeVal& hi) {
+  double I;
+  if (hi.lower) I = hi.V - lo.V;
+  else if (!lo.lower) I = lo.V - hi.V;
+  else I = (kPi4over15 - lo.V) - hi.V;
+  return k15overPi4 * I;
+}
+
+// dPhi_g/dT = a c T^3 [4 b + (15/pi^4)(g4(x_lo) - g4(x_hi))]: returns the bracket.
+__device__ __forceinline__ double planck_dfraction(double b, const EdgeVal& lo, const EdgeVal& hi) {
+  return 4.0 * b + k15overPi4 * (lo.g4 - hi.g4);
+}
+
+// --------------------------------------------------------------------------
+// Time-integrated coefficients at x = dt/tau (Eq. C2Formula; C4, C5 of the
+// UGKS free flux).  Below x = 1 the Taylor series (22 terms), else closed
+// forms with expm1.
+//   f2 = C2/tau          = sum_{k>=2} (-1)^k (1-k) x^k/(k+1)!
+//   f4 = C4 - e          = sum_{k>=1} (-1)^{k+1} k x^k/(k+1)!
+//   f5 = (C5 + dt e/2)/tau = sum_{k>=2} (-1)^k k(1-k) x^k/(2 (k+1)!)
+//   c4 = C4              = sum_{k>=0} (-1)^k x^k/(k+1)!
+constexpr int kSer = 22;
+__host__ __device__ constexpr double sgn(int k) { return (k & 1) ? -1.0 : 1.0; }
+__host__ __device__ constexpr double a2(int k) { return sgn(k) * (1.0 - k) / fact_d(k + 1); }
+__host__ __device__ constexpr double a4(int k) { return -sgn(k) * k / fact_d(k + 1); }
+__host__ __device__ constexpr double a5(int k) { return sgn(k) * k * (1.0 - k) / (2.0 * fact_d(k + 1)); }
+__host__ __device__ constexpr double ac4(int k) { return sgn(k) / fact_d(k + 1); }
+
+__device__ __forceinline__ double coef_f2(double x) {
+  if (x < 1.0) {
+    double s = a2(kSer);
+#pragma unroll
+    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, a2(k));
+    return s * x * x;
+  }
+  const double e = exp(-x), E1 = -expm1(-x);
+  return 2.0 * E1 / x - 1.0 - e;
+}
+
+__device__ __forceinline__ double coef_f4(double x) {
+  if (x < 1.0) {
+    double s = a4(kSer);
+#pragma unroll
+    for (int k = kSer - 1; k >= 1; --k) s = fma(s, x, a4(k));
+    return s * x;
+  }
+  return -expm1(-x) / x - exp(-x);
+}
+
+__device__ __forceinline__ double coef_f5(double x) {
+  if (x < 1.0) {
+    double s = a5(kSer);
+#pragma unroll
+    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, a5(k));
+    return s * x * x;
+  }
+  const double e = exp(-x);
+  return e * (1.0 + 0.5 * x) + expm1(-x) / x;
+}
+
+__device__ __forceinline__ double coef_c4(double x) {
+  if (x < 1.0) {
+    double s = ac4(kSer);
+#pragma unroll
+    for (int k = kSer - 1; k >= 0; --k) s = fma(s, x, ac4(k));
+    return s;
+  }
+  return -expm1(-x) / x;
+}
+
+// --------------------------------------------------------------------------
+// Linear-frequency sampling (Eqs. Blinear, kg; App. A).  With B in units of
+// B(nu_mid) and slope khat clamped to |khat| <= 2/dnu (non-negative density),
+// G(nu_lo + u) = eta is the quadratic (khat/2) u^2 + A u - eta dnu = 0 with
+// A = 1 - khat dnu/2 >= 0; its root in [0, dnu] is taken in the form
+// u = 2 eta dnu / (A + sqrt(A^2 + 2 khat eta dnu)), free of cancellation.
+__device__ __forceinline__ double planck_ratio(double nu, double nmid, double T) {
+  // B(nu)/B(nmid) = (nu/nmid)^3 e^{(nmid-nu)/T} (1 - e^{-nmid/T}) / (1 - e^{-nu/T})
+  const double r = nu / nmid;
+  double ex = (nmid - nu) / T;
+  if (ex > 700.0) ex = 700.0;
+  return r * r * r * exp(ex) * (expm1(-nmid / T) / expm1(-nu / T));
+}
+
+__device__ __forceinline__ double sampler_khat(double nlo, double nhi, double T) {
+  if (!(T > 0.0)) return 0.0;
+  const double dnu = nhi - nlo, nmid = 0.5 * (nlo + nhi);
+  double k = (planck_ratio(nhi, nmid, T) - planck_ratio(nlo, nmid, T)) / dnu;
+  const double kmax = 2.0 / dnu;
+  k = fmin(fmax(k, -kmax), kmax);
+  return k == k ? k : 0.0;
+}
+
+__device__ __forceinline__ double sample_nu(double nlo, double nhi, double khat, double eta) {
+  const double dnu = nhi - nlo;
+  const double A = fma(-0.5 * khat, dnu, 1.0);
+  const double q = eta * dnu;
+  const double u = 2.0 * q / (A + sqrt(fma(A, A, 2.0 * khat * q)));
+  return fmin(nlo + u, nhi);
+}
+
+// --------------------------------------------------------------------------
+// atomics on non-negative doubles ordered as their bit patterns
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {
+  if (v != v) v = __longlong_as_double(0x7FF0000000000000LL);  // NaN -> +inf
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace ugkwp

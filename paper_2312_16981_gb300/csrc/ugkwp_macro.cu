@@ -1,0 +1,790 @@
+// ugkwp_macro.cu -- cell/face kernels of the UGKWP step on sm_103a:
+// birth counts and their scan (Eq. IhpFormula), the wave-part flux (Sec. 2.2),
+// the matrix-free source iteration (App. B, Algorithm 2) as one cooperative
+// persistent kernel, the end-of-step bookkeeping, initialisation, and the
+// kernel-level entry points used by the parity tests.
+#include "ugkwp_device.cuh"
+#include "ugkwp_launch.h"
+
+namespace ugkwp {
+
+// --------------------------------------------------------------------------
+// Initialisation: Phi_g(T0) where rho0 is not given, ghost tables, source.
+__device__ void phi_dphi_cell(const Dev& d, double T, int g, double* phi, double* dphi) {
+  // Phi_g(T) = a c T^4 b_g(T), dPhi_g/dT = a c T^3 (4 b_g + ...); grey: b = 1
+  if (!(T > 0.0)) { *phi = 0.0; if (dphi) *dphi = 0.0; return; }
+  const double ac = d.a * d.c, T3 = T * T * T;
+  if (d.grey) { *phi = ac * T3 * T; if (dphi) *dphi = 4.0 * ac * T3; return; }
+  const EdgeVal lo = planck_edge(d.nu_edges[g] / T), hi = planck_edge(d.nu_edges[g + 1] / T);
+  const double b = planck_fraction(lo, hi);
+  *phi = ac * T3 * T * b;
+  if (dphi) *dphi = ac * T3 * planck_dfraction(b, lo, hi);
+}
+
+__global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int n = d.ncell * d.G;
+  for (int i = tid; i < n; i += stride) {
+    const int c = i / d.G, g = i - c * d.G;
+    if (init_rho) {
+      double p;
+      phi_dphi_cell(d, d.T[c], g, &p, nullptr);
+      d.rho[i] = p;
+      d.rho_h[i] = p;
+      d.rho_p[i] = 0.0;
+    }
+    if (d.src) {
+      double p = 0.0;
+      if (src_T && src_T[c] > 0.0) phi_dphi_cell(d, src_T[c], g, &p, nullptr);
+      const_cast<double*>(d.src)[i] = d.src_on * d.c * d.dt * p;
+    }
+  }
+  for (int i = tid; i < 4 * d.G; i += stride) {
+    const int side = i / d.G, g = i - side * d.G;
+    double p = 0.0, s = 0.0;
+    if (d.bc[side] == BC_BLACKBODY) {
+      const int cin = side == 0 ? 0 : (side == 1 ? d.nx - 1 : 0);
+      phi_dphi_cell(d, d.bcT[side], g, &p, nullptr);
+      s = sigma_group(d, sigma_T(d, cin, d.bcT[side]), g);
+    }
+    const_cast<double*>(d.ghost_phi)[i] = p;
+    const_cast<double*>(d.ghost_sig)[i] = s;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Birth counts (Eq. IhpFormula, weight formula of Sec. 2.2): per bin the
+// collisionless part E = e^{-dt/tau} max(rho_h, 0) V, tau from the Simpson
+// group opacity at T^n, N = floor(E/omega_ref + 1/2), omega = E/N, e_eff = e
+// if N > 0 else 0.  Black-body ghost bins (1D) carry the entering part of the
+// ghost's collisionless particles, E = e (c/eps)/4 Phi_g(T_b) dt.  Also
+// stores sigma_g(T^n), sigma0 T^q per cell, the sampler slope per bin, zeroes
+// this step's tallies and resets the per-step counters.
+__global__ void k_birth(Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  if (tid == 0) {
+    ctrl->n_new = 0;
+    ctrl->n_out = 0;
+    ctrl->n_in = ctrl->n_part[ctrl->cur];
+    ctrl->n_born = ctrl->n_survived = ctrl->n_absorbed = ctrl->n_escaped = 0;
+    ctrl->n_removed = ctrl->n_segments = 0;
+    ctrl->bar_count = 0;
+    for (int s = 0; s < 3; ++s) ctrl->err_slot[s][0] = ctrl->err_slot[s][1] = 0ull;
+    ctrl->E_rad0 = ctrl->E_mat0 = ctrl->E_rad1 = ctrl->E_mat1 = 0.0;
+    ctrl->bnd_in_macro = ctrl->bnd_in_part = ctrl->bnd_out_part = ctrl->src_in = 0.0;
+  }
+  const int G = d.G;
+  for (int b = tid; b < d.nbins; b += stride) {
+    const int cell = b / G, g = b - cell * G;
+    double E, sig, Tb;
+    if (cell < d.ncell) {
+      Tb = d.T[cell];
+      const double sT = sigma_T(d, cell, Tb);
+      if (g == 0) d.sT[cell] = sT;
+      sig = sigma_group(d, sT, g);
+      d.sigT[b] = sig;
+      d.W[b] = 0.0;
+      d.E_surv[b] = 0.0;
+      const double rh = d.rho_h[b];
+      E = (rh > 0.0 ? rh : 0.0) * d.vol;
+    } else {
+      const int side = cell - d.ncell;
+      d.esc[side * G + g] = 0.0;
+      d.inflow[side * G + g] = 0.0;
+      if (d.dim != 1 || side > 1 || d.bc[side] != BC_BLACKBODY) {
+        d.N[b] = 0; d.omega[b] = 0.0; d.e_eff[b] = 0.0; d.khat[b] = 0.0;
+        continue;
+      }
+      sig = d.ghost_sig[side * G + g];
+      Tb = d.bcT[side];
+      E = 0.25 * d.v * d.ghost_phi[side * G + g] * d.dt;
+    }
+    const double e = exp(-d.dt * d.rate_f * sig);
+    E *= e;
+    uint32_t N = 0;
+    double w = 0.0, ee = 0.0;
+    if (d.omega_ref > 0.0 && E > 0.0) {
+      double q = floor(E / d.omega_ref + 0.5);
+      if (q > (double)kMaxPerBin) { q = (double)kMaxPerBin; atomicOr(&ctrl->status, ST_CAPACITY); }
+      N = (uint32_t)q;
+      if (N) { w = E / (double)N; ee = e; }
+    }
+    d.N[b] = N;
+    d.omega[b] = w;
+    d.e_eff[b] = ee;
+    d.khat[b] = (N && !d.grey) ? sampler_khat(d.nu_edges[g], d.nu_edges[g + 1], Tb) : 0.0;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Exclusive scan of the birth counts: per-block sums, a one-block scan of
+// the sums, then per-block scans with their offsets.  Tile = 4096 bins.
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_tot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_warp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t x = lane < nw ? s_warp[lane] : 0u, xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    if (lane < nw) s_warp[lane] = xi - x;
+    if (lane == nw - 1) s_tot = xi;   // block total
+  }
+  __syncthreads();
+  const uint32_t res = s_warp[wid] + inc - v;
+  if (total) *total = s_tot;
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Dev d) {
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k)
+    if (base + k < d.nbins) s += d.N[base + k];
+  uint32_t tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) d.part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(Dev d, int nparts) {
+  // one block: exclusive scan of nparts (<= kScanTile) block sums in place
+  const int base = threadIdx.x * kScanPer;
+  uint32_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < nparts ? d.part[base + k] : 0u; s += v[k]; }
+  uint32_t tot;
+  uint32_t ex = block_exclusive_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < nparts) d.part[base + k] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) {
+    d.ctrl->n_new = tot;
+    d.ctrl->n_born = tot;
+    d.off[d.nbins] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Dev d) {
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+  uint32_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < d.nbins ? d.N[base + k] : 0u; s += v[k]; }
+  uint32_t ex = block_exclusive_scan(s, nullptr) + d.part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < d.nbins) d.off[base + k] = ex;
+    ex += v[k];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Face walk helpers: face f -> axis, the line of cells through it and its
+// position along the line.
+struct FaceRef {
+  int axis, line, k, nk;   // face between line cells k-1 and k, 0..nk
+  double h;
+};
+
+__device__ __forceinline__ FaceRef face_ref(const Dev& d, int f) {
+  FaceRef r;
+  if (f < d.nxface) {
+    r.axis = 0; r.line = f / (d.nx + 1); r.k = f - r.line * (d.nx + 1); r.nk = d.nx; r.h = d.dx;
+  } else {
+    const int q = f - d.nxface;
+    r.axis = 1; r.k = q / d.nx; r.line = q - r.k * d.nx; r.nk = d.ny; r.h = d.dy;
+  }
+  return r;
+}
+
+__device__ __forceinline__ int line_cell(const Dev& d, const FaceRef& r, int k) {
+  return r.axis == 0 ? r.line * d.nx + k : k * d.nx + r.line;
+}
+
+// rho_h at line position k including ghosts (mirror / black body / vacuum)
+__device__ __forceinline__ double rho_h_at(const Dev& d, const FaceRef& r, int k, int g) {
+  if (k >= 0 && k < r.nk) return d.rho_h[line_cell(d, r, k) * d.G + g];
+  const int side = r.axis * 2 + (k < 0 ? 0 : 1);
+  if (d.bc[side] == BC_REFLECT) return d.rho_h[line_cell(d, r, k < 0 ? 0 : r.nk - 1) * d.G + g];
+  if (d.bc[side] == BC_BLACKBODY) return d.ghost_phi[side * d.G + g];
+  return 0.0;
+}
+
+__device__ __forceinline__ double van_leer(double a, double b) {
+  return a * b > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+// A = C4_f - e_h, B = C5_f + dt e_h/2 of one half (face coefficients, upwind e).
+__device__ __forceinline__ void half_coefs(double xf, double tauf, double xh, double e_eff,
+                                           double dt, double* A, double* B) {
+  const double f4 = coef_f4(xf);
+  if (e_eff > 0.0) {
+    const double dd = xh - xf;
+    const double efh = fabs(dd) < 0.5 ? exp(-xh) * expm1(dd) : exp(-xf) - exp(-xh);
+    *A = f4 + efh;
+    *B = tauf * coef_f5(xf) - 0.5 * dt * efh;
+  } else {
+    *A = coef_c4(xf);
+    *B = -tauf * f4;
+  }
+}
+
+// Wave-part flux F^{fr,wave} on every (face, group) (Sec. 2.2): upwind
+// half-range integrals with C4, C5 from the harmonic-mean face opacity and the
+// sampled fraction e of the upwind cell; wave_order 2 reconstructs rho_h with
+// van Leer slopes.  Reflecting walls carry none.
+__global__ void k_wave(Dev d) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int G = d.G;
+  const double v = d.v;
+  for (int i = tid; i < d.nface * G; i += stride) {
+    const int f = i / G, g = i - f * G;
+    const FaceRef r = face_ref(d, f);
+    const int sideL = r.axis * 2, sideR = sideL + 1;
+    const bool lin = r.k - 1 >= 0, rin = r.k < r.nk;
+    if ((!lin && d.bc[sideL] == BC_REFLECT) || (!rin && d.bc[sideR] == BC_REFLECT)) {
+      d.Fwave[i] = 0.0;
+      continue;
+    }
+    const double rl = rho_h_at(d, r, r.k - 1, g), rr = rho_h_at(d, r, r.k, g);
+    double sl, sr, fl, fr;
+    if (d.wave_order >= 2) {
+      const double rll = rho_h_at(d, r, r.k - 2, g), rrr = rho_h_at(d, r, r.k + 1, g);
+      sl = lin ? van_leer((rl - rll) / r.h, (rr - rl) / r.h) : 0.0;
+      sr = rin ? van_leer((rr - rl) / r.h, (rrr - rr) / r.h) : 0.0;
+      fl = rl + 0.5 * r.h * sl;
+      fr = rr - 0.5 * r.h * sr;
+    } else {
+      sl = sr = (rr - rl) / r.h;
+      fl = rl;
+      fr = rr;
+    }
+    double sgl = -1.0, sgr = -1.0, el = 0.0, er = 0.0;
+    if (lin) {
+      const int cl = line_cell(d, r, r.k - 1);
+      sgl = d.sigT[cl * G + g];
+      el = d.e_eff[cl * G + g];
+    } else if (d.bc[sideL] == BC_BLACKBODY) {
+      sgl = d.ghost_sig[sideL * G + g];
+      el = d.e_eff[(d.ncell + sideL) * G + g];
+    }
+    if (rin) {
+      const int cr = line_cell(d, r, r.k);
+      sgr = d.sigT[cr * G + g];
+      er = d.e_eff[cr * G + g];
+    } else if (d.bc[sideR] == BC_BLACKBODY) {
+      sgr = d.ghost_sig[sideR * G + g];
+      er = d.e_eff[(d.ncell + sideR) * G + g];
+    }
+    if (sgl < 0.0) sgl = sgr;
+    if (sgr < 0.0) sgr = sgl;
+    const double sf = 2.0 * sgl * sgr / (sgl + sgr);
+    const double tauf = 1.0 / (d.rate_f * sf);
+    const double xf = d.dt / tauf;
+    double AL, BL, AR, BR;
+    half_coefs(xf, tauf, d.dt * d.rate_f * sgl, el, d.dt, &AL, &BL);
+    half_coefs(xf, tauf, d.dt * d.rate_f * sgr, er, d.dt, &AR, &BR);
+    d.Fwave[i] = AL * (v * 0.25) * fl - AR * (v * 0.25) * fr + (BL * sl + BR * sr) * (v * v / 6.0);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Grid-wide barrier for the cooperative source-iteration kernel: a
+// monotonically increasing arrival counter, bounded spin.  On timeout the
+// status bit is set and the caller returns.
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int target) {
+  __shared__ int s_timeout;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&ctrl->bar_count, 1u);
+    const unsigned int limit = ctrl->bar_timeout_spins ? ctrl->bar_timeout_spins : (1u << 25);
+    unsigned int spins = 0;
+    int to = 0;
+    while (true) {
+      const unsigned int c = atomicAdd(&ctrl->bar_count, 0u);
+      if (c >= target) break;
+      if (++spins > limit) { to = 1; break; }
+      __nanosleep(64);
+    }
+    if (to) atomicOr(&ctrl->status, ST_TIMEOUT);
+    __threadfence();
+    s_timeout = to;
+  }
+  __syncthreads();
+  return s_timeout == 0;
+}
+
+// Equilibrium flux on a face between lower-index side (l) and upper side (u):
+// F = C2 (c/eps)^2/3 (Phi_u - Phi_l)/h, C2 = tau f2(dt/tau), tau from the
+// harmonic-mean opacity (App. B).  Both adjacent cells evaluate the same
+// expression with the same operand order, so the two copies agree bitwise.
+__device__ __forceinline__ double feq_face(const Dev& d, double sl, double su, double pl, double pu,
+                                           double h) {
+  const double sf = 2.0 * sl * su / (sl + su);
+  const double tau = 1.0 / (d.rate_f * sf);
+  return tau * coef_f2(d.dt / tau) * (d.v * d.v / 3.0) * (pu - pl) / h;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Planck and opacity of one cell at temperature T for the lane's groups:
+// sigma_g, Phi_g and dPhi_g/dT, g = lane + 32 j.  Edge values are shared
+// between neighbouring lanes by shuffles.
+template <int NC>
+__device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
+                                            double* dphi) {
+  const int lane = threadIdx.x & 31, G = d.G;
+  const double sT = sigma_T(d, c, T);
+  const double ac = d.a * d.c, T3 = T * T * T;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (d.grey) {
+      sig[j] = cap_sigma(d, sT);
+      phi[j] = T > 0.0 ? ac * T3 * T : 0.0;
+      dphi[j] = T > 0.0 ? 4.0 * ac * T3 : 0.0;
+      continue;
+    }
+    EdgeVal lo;
+    if (g <= G && T > 0.0) lo = planck_edge(d.nu_edges[g] / T);
+    else { lo.V = 0.0; lo.g4 = 0.0; lo.lower = true; }
+    EdgeVal hi;
+    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
+    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
+    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
+    if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] / T);
+    if (g < G) {
+      sig[j] = sigma_group(d, sT, g);
+      if (T > 0.0) {
+        const double b = planck_fraction(lo, hi);
+        phi[j] = ac * T3 * T * b;
+        dphi[j] = ac * T3 * planck_dfraction(b, lo, hi);
+      } else {
+        phi[j] = 0.0;
+        dphi[j] = 0.0;
+      }
+    } else {
+      sig[j] = 1.0; phi[j] = 0.0; dphi[j] = 0.0;
+    }
+  }
+}
+
+// Neighbour values across one face of cell c: opacity and Phi at iterate k,
+// or the ghost's.  Returns false for a reflecting wall (no flux).
+__device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir, int g, int cur,
+                                          double sig_c, double* sn, double* pn, int* nc) {
+  const int ix = c % d.nx, iy = c / d.nx;
+  const int jx = ix + (axis == 0 ? dir : 0), jy = iy + (axis == 1 ? dir : 0);
+  const int nyy = d.dim == 2 ? d.ny : 1;
+  if (jx < 0 || jx >= d.nx || jy < 0 || jy >= nyy) {
+    const int side = axis * 2 + (dir > 0 ? 1 : 0);
+    *nc = -1 - side;
+    if (d.bc[side] == BC_REFLECT) return false;
+    if (d.bc[side] == BC_BLACKBODY) {
+      *sn = d.ghost_sig[side * d.G + g];
+      *pn = d.ghost_phi[side * d.G + g];
+    } else {
+      *sn = sig_c;
+      *pn = 0.0;
+    }
+    return true;
+  }
+  const int n = jy * d.nx + jx;
+  *nc = n;
+  *sn = __ldcg(d.sigk[cur] + n * d.G + g);
+  *pn = __ldcg(d.phik[cur] + n * d.G + g);
+  return true;
+}
+
+__device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {
+  const int ix = c % d.nx, iy = c / d.nx;
+  if (axis == 0) return iy * (d.nx + 1) + ix + (dir > 0 ? 1 : 0);
+  return d.nxface + (iy + (dir > 0 ? 1 : 0)) * d.nx + ix;
+}
+
+// Source iteration (App. B, Algorithm 2) in 1D and 2D, one warp per cell and
+// one lane per group.  Iterate k: equilibrium fluxes from sigma^k, Phi^k of
+// the cell and its neighbours (Jacobi), then the linearised closed-form update
+//   T^{k+1} = [Cv T^n + sum_g (a_g/c)(Q_g - Phi_g + Phi'_g T^k)/(1 + a_g)]
+//           / [Cv + sum_g (a_g/c) Phi'_g/(1 + a_g)],
+//   rho^{k+1}_g = (Q_g + a_g (Phi_g + Phi'_g (T^{k+1} - T^k)))/(1 + a_g),
+// a_g = c dt sigma_g/eps^2, Q_g = R_g + (dt/h)(F^eq_in - F^eq_out), and
+// sigma^{k+1}, Phi^{k+1}, Phi'^{k+1} at T^{k+1} for the next iterate; one
+// grid barrier per iterate.  Stopping rule: max over cells of |dT|/T and of
+// max_g |d rho_g| / sum_g |rho_g| both <= si_tol.  The prologue assembles
+// R = rho^n + wave-flux divergence + w^{fr,p}/V + source; the epilogue writes
+// T^{n+1}, rho^{n+1}, rho^p = E_surv/V, rho^h = rho^{n+1} - rho^p and the
+// energy ledger.
+template <int NC>
+__global__ void __launch_bounds__(256) k_si(Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int gw = blockIdx.x * nwb + wib, nw = gridDim.x * nwb;
+  const int G = d.G;
+  const double dt = d.dt, V = d.vol;
+  __shared__ double s_red[8][4];
+  unsigned int bar = 0;
+  double e_rad0 = 0.0, e_mat0 = 0.0, e_src = 0.0;
+
+  // ---- prologue
+  for (int c = gw; c < d.ncell; c += nw) {
+    const int ix = c % d.nx, iy = c / d.nx;
+    const int fxl = iy * (d.nx + 1) + ix, fxr = fxl + 1;
+    const int fyl = d.nxface + iy * d.nx + ix, fyr = fyl + d.nx;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int g = lane + 32 * j;
+      if (g < G) {
+        const int i = c * G + g;
+        const double r0 = d.rho[i];
+        double r = r0 + (dt / d.dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
+        if (d.dim == 2) r += (dt / d.dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
+        r += d.W[i] / V;
+        if (d.src) { r += d.src[i]; e_src += V * d.src[i] / d.c; }
+        d.R[i] = r;
+        e_rad0 += V * r0 / d.c;
+      }
+    }
+    const double T = d.T[c];
+    if (lane == 0) e_mat0 += V * d.cv[c] * T;
+    double sg[NC], ph[NC], dp[NC];
+    cell_planck<NC>(d, c, T, sg, ph, dp);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int g = lane + 32 * j;
+      if (g < G) {
+        __stcg(d.sigk[0] + c * G + g, sg[j]);
+        __stcg(d.phik[0] + c * G + g, ph[j]);
+        __stcg(d.dphik + c * G + g, dp[j]);
+      }
+    }
+    if (lane == 0) __stcg(d.Tk[0] + c, T);
+  }
+  e_rad0 = warp_sum(e_rad0);
+  e_src = warp_sum(e_src);
+  if (lane == 0) {
+    atomicAdd(&ctrl->E_rad0, e_rad0);
+    atomicAdd(&ctrl->E_mat0, e_mat0);
+    if (e_src != 0.0) atomicAdd(&ctrl->src_in, e_src);
+  }
+  if (!grid_barrier(ctrl, (++bar) * gridDim.x)) return;
+
+  // ---- iterations
+  int it = 0, converged = 0;
+  for (; it < d.si_max_iters; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    double werrT = 0.0, werrR = 0.0;
+    for (int c = gw; c < d.ncell; c += nw) {
+      const double Tc = __ldcg(d.Tk[cur] + c), Tn = d.T[c], cv = d.cv[c];
+      double Q[NC], a[NC], phc[NC], dpc[NC];
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int g = lane + 32 * j;
+        Q[j] = 0.0; a[j] = 0.0; phc[j] = 0.0; dpc[j] = 0.0;
+        if (g >= G) continue;
+        const int i = c * G + g;
+        const double sc = __ldcg(d.sigk[cur] + i);
+        phc[j] = __ldcg(d.phik[cur] + i);
+        dpc[j] = __ldcg(d.dphik + i);
+        double q = d.R[i];
+        for (int axis = 0; axis < d.dim; ++axis) {
+          const double h = axis == 0 ? d.dx : d.dy;
+          double Fin = 0.0, Fout = 0.0;
+          for (int dir = -1; dir <= 1; dir += 2) {
+            double sn, pn;
+            int nc;
+            double F = 0.0;
+            if (neighbour(d, c, axis, dir, g, cur, sc, &sn, &pn, &nc)) {
+              F = dir < 0 ? feq_face(d, sn, sc, pn, phc[j], h) : feq_face(d, sc, sn, phc[j], pn, h);
+            }
+            const bool owner = dir > 0 ? true : (nc < 0);   // upper face, or a boundary face
+            if (owner) d.Feq[face_index(d, c, axis, dir) * G + g] = F;
+            if (dir < 0) Fin = F; else Fout = F;
+          }
+          q += (dt / h) * (Fin - Fout);
+        }
+        Q[j] = q;
+        a[j] = dt * d.rate_f * sc;
+        const double ap = a[j] / d.c / (1.0 + a[j]);
+        num += ap * (q - phc[j] + dpc[j] * Tc);
+        den += ap * dpc[j];
+      }
+      num = warp_sum(num);
+      den = warp_sum(den);
+      double Tnew = (cv * Tn + num) / (cv + den);
+      if (!(Tnew > 1e-30)) Tnew = (Tnew == Tnew) ? 1e-30 : Tnew;
+      double dmax = 0.0, rsum = 0.0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int g = lane + 32 * j;
+        if (g >= G) continue;
+        const int i = c * G + g;
+        const double r = (Q[j] + a[j] * (phc[j] + dpc[j] * (Tnew - Tc))) / (1.0 + a[j]);
+        dmax = fmax(dmax, fabs(r - __ldcg(d.rho + i)));
+        rsum += fabs(r);
+        __stcg(d.rho + i, r);
+      }
+      dmax = warp_max(dmax);
+      rsum = warp_sum(rsum);
+      const double eR = rsum > 0.0 ? dmax / rsum : 0.0;
+      const double eT = fabs(Tnew - Tc) / Tnew;
+      werrT = fmax(werrT, (eT == eT) ? eT : 1e300);
+      werrR = fmax(werrR, (eR == eR) ? eR : 1e300);
+      if (lane == 0) __stcg(d.Tk[nxt] + c, Tnew);
+      double sg[NC], ph[NC], dp[NC];
+      cell_planck<NC>(d, c, Tnew, sg, ph, dp);
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int g = lane + 32 * j;
+        if (g < G) {
+          __stcg(d.sigk[nxt] + c * G + g, sg[j]);
+          __stcg(d.phik[nxt] + c * G + g, ph[j]);
+          __stcg(d.dphik + c * G + g, dp[j]);
+        }
+      }
+    }
+    if (lane == 0) { s_red[wib][0] = werrT; s_red[wib][1] = werrR; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double mT = 0.0, mR = 0.0;
+      for (int w = 0; w < nwb; ++w) { mT = fmax(mT, s_red[w][0]); mR = fmax(mR, s_red[w][1]); }
+      atomic_max_nonneg(&ctrl->err_slot[it % 3][0], mT);
+      atomic_max_nonneg(&ctrl->err_slot[it % 3][1], mR);
+      if (blockIdx.x == 0) {
+        ctrl->err_slot[(it + 1) % 3][0] = 0ull;
+        ctrl->err_slot[(it + 1) % 3][1] = 0ull;
+      }
+    }
+    if (!grid_barrier(ctrl, (++bar) * gridDim.x)) return;
+    const double eT = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][0], 0ull));
+    const double eR = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][1], 0ull));
+    if (eT <= d.si_tol && eR <= d.si_tol) { converged = 1; ++it; break; }
+  }
+  // iterate `it - 1` wrote Tk[it & 1]
+  const int fin = it > 0 ? (it & 1) : 0;
+
+  // ---- epilogue
+  double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
+  int bad = 0;
+  for (int c = gw; c < d.ncell; c += nw) {
+    const double T = __ldcg(d.Tk[fin] + c);
+    if (!(T == T) || T > 1e300) bad = 1;
+    if (lane == 0) {
+      d.T[c] = T;
+      e_mat1 += V * d.cv[c] * T;
+    }
+    const int ix = c % d.nx, iy = c / d.nx;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int g = lane + 32 * j;
+      if (g >= G) continue;
+      const int i = c * G + g;
+      const double r = __ldcg(d.rho + i);
+      const double rp = d.E_surv[i] / V;
+      d.rho_p[i] = rp;
+      d.rho_h[i] = r - rp;
+      e_rad1 += V * r / d.c;
+      // boundary faces: energy entering the domain
+      for (int axis = 0; axis < d.dim; ++axis) {
+        const double S = d.dim == 2 ? (axis == 0 ? d.dy : d.dx) : 1.0;
+        const int k = axis == 0 ? ix : iy, nk = axis == 0 ? d.nx : d.ny;
+        if (k == 0) {
+          const int f = face_index(d, c, axis, -1);
+          b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+        }
+        if (k == nk - 1) {
+          const int f = face_index(d, c, axis, +1);
+          b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+        }
+      }
+    }
+  }
+  e_rad1 = warp_sum(e_rad1);
+  b_in = warp_sum(b_in);
+  if (lane == 0) {
+    atomicAdd(&ctrl->E_rad1, e_rad1);
+    atomicAdd(&ctrl->E_mat1, e_mat1);
+    if (b_in != 0.0) atomicAdd(&ctrl->bnd_in_macro, b_in);
+    if (bad) atomicOr(&ctrl->status, ST_NONFINITE);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->si_iters = (unsigned int)it;
+    if (!converged) atomicOr(&ctrl->status, ST_NOCONV);
+  }
+}
+
+// End of step: swap particle buffers, advance the step counter, particle
+// ledger from the side tallies.
+__global__ void k_end_step(Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  if (threadIdx.x == 0) {
+    const unsigned long long n = ctrl->n_out;
+    const unsigned long long cap = (unsigned long long)d.capacity;
+    ctrl->n_part[ctrl->cur ^ 1u] = n < cap ? n : cap;
+    ctrl->n_part[ctrl->cur] = 0;
+    ctrl->cur ^= 1u;
+    ctrl->step += 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double pin = 0.0, pout = 0.0;
+    for (int i = threadIdx.x; i < 4 * d.G; i += 32) { pin += d.inflow[i]; pout += d.esc[i]; }
+    pin = warp_sum(pin);
+    pout = warp_sum(pout);
+    if (threadIdx.x == 0) {
+      ctrl->bnd_in_part = pin / d.c;
+      ctrl->bnd_out_part = pout / d.c;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// kernel-level entry points
+__global__ void k_unit_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 o = philox4x32_10(c, k0, k1);
+    out[4 * i] = o.x; out[4 * i + 1] = o.y; out[4 * i + 2] = o.z; out[4 * i + 3] = o.w;
+  }
+}
+
+__global__ void k_unit_planck(const double* T, long long n, const double* nu, int G, double* b,
+                              double* dd) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * G;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long t = i / G;
+    const int g = (int)(i - t * G);
+    const double TT = T[t];
+    const EdgeVal lo = planck_edge(nu[g] / TT), hi = planck_edge(nu[g + 1] / TT);
+    const double bb = planck_fraction(lo, hi);
+    b[i] = bb;
+    if (dd) dd[i] = planck_dfraction(bb, lo, hi);
+  }
+}
+
+__global__ void k_unit_coefs(const double* x, long long n, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double xx = x[i];
+    out[4 * i] = coef_f2(xx);
+    out[4 * i + 1] = coef_f4(xx);
+    out[4 * i + 2] = coef_f5(xx);
+    out[4 * i + 3] = coef_c4(xx);
+  }
+}
+
+__global__ void k_unit_sample(const double* eta, long long n, double nlo, double nhi, double T,
+                              double* nu) {
+  const double kh = sampler_khat(nlo, nhi, T);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    nu[i] = sample_nu(nlo, nhi, kh, eta[i]);
+}
+
+// --------------------------------------------------------------------------
+// host launchers
+static int grid_for(long long n, int threads, int cap = 152 * 16) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+cudaError_t launch_init_tables(const Dev& d, const double* src_T, int init_rho, cudaStream_t s) {
+  k_init_tables<<<grid_for((long long)d.ncell * d.G, 256), 256, 0, s>>>(d, src_T, init_rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_birth_and_scan(const Dev& d, cudaStream_t s) {
+  k_birth<<<grid_for(d.nbins, 256), 256, 0, s>>>(d);
+  const int nparts = (d.nbins + kScanTile - 1) / kScanTile;
+  k_scan_reduce<<<nparts, kScanThreads, 0, s>>>(d);
+  k_scan_partials<<<1, kScanThreads, 0, s>>>(d, nparts);
+  k_scan_apply<<<nparts, kScanThreads, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+int scan_parts(int nbins) { return (nbins + kScanTile - 1) / kScanTile; }
+
+cudaError_t launch_wave(const Dev& d, cudaStream_t s) {
+  k_wave<<<grid_for((long long)d.nface * d.G, 256), 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+static int g_si_blocks[2] = {0, 0};
+
+cudaError_t launch_si(const Dev& d, cudaStream_t s) {
+  const int nc = d.G > 32 ? 1 : 0;
+  void* fn = nc ? (void*)k_si<2> : (void*)k_si<1>;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!g_si_blocks[nc]) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0);
+    g_si_blocks[nc] = per > 0 ? per : 1;
+  }
+  long long want = ((long long)d.ncell + 7) / 8;   // 8 warps (cells) per block
+  long long maxb = (long long)sms * g_si_blocks[nc];
+  int blocks = (int)(want < maxb ? want : maxb);
+  if (blocks < 1) blocks = 1;
+  Dev dd = d;
+  void* args[] = {&dd};
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_end_step(const Dev& d, cudaStream_t s) {
+  k_end_step<<<1, 32, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, long long n,
+                               cudaStream_t s) {
+  k_unit_philox<<<grid_for(n, 256), 256, 0, s>>>(ctr, k0, k1, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_unit_planck(const double* T, long long n, const double* nu, int G, double* b,
+                               double* dd, cudaStream_t s) {
+  k_unit_planck<<<grid_for(n * G, 256), 256, 0, s>>>(T, n, nu, G, b, dd);
+  return cudaGetLastError();
+}
+cudaError_t launch_unit_coefs(const double* x, long long n, double* out, cudaStream_t s) {
+  k_unit_coefs<<<grid_for(n, 256), 256, 0, s>>>(x, n, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_unit_sample(const double* eta, long long n, double nlo, double nhi, double T,
+                               double* nu, cudaStream_t s) {
+  k_unit_sample<<<grid_for(n, 256), 256, 0, s>>>(eta, n, nlo, nhi, T, nu);
+  return cudaGetLastError();
+}
+
+}  // namespace ugkwp

@@ -1,0 +1,344 @@
+// ugkwp_stream.cu -- the particle kernel of the UGKWP step on sm_103a.
+//
+// One persistent launch processes a virtual index space [0, n_surv + n_new):
+// first the particles that survived the previous step (Algorithm 1: a free
+// time t_f = min(-tau ln eta, dt), Eq. particle-tf-formula), then the
+// particles sampled this step from the wave part's collisionless fraction
+// (Eq. IhpFormula; born in registers with t_f = dt, never stored unless they
+// survive).  Each particle streams cell by cell with the free time reset on
+// entering a new cell (interface remark: t_f2 = min(-tau_i ln eta, dt - t_tra)),
+// reflects at mirror walls, escapes through open sides.  Tallies: the net
+// particle energy per (cell, group) w^{fr,p} (Eq. wfrpFormula, accumulated as
+// end minus start, which telescopes the face crossings), the energy of the
+// collisionless survivors per end cell, escapes and inflow per side.
+// Collided particles are dropped (Algorithm 1, last step); survivors are
+// compacted block by block into the other particle buffer.
+#include "ugkwp_device.cuh"
+#include "ugkwp_launch.h"
+
+namespace ugkwp {
+
+constexpr int kStreamThreads = 256;
+
+// largest b with off[b] <= j, for off[0] = 0 <= j < off[nbins]
+__device__ __forceinline__ int find_bin(const uint32_t* __restrict__ off, int nbins, uint32_t j) {
+  int lo = 0, hi = nbins;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Sum v over runs of equal keys among consecutive lanes and add each run's
+// total once (keys < 0 contribute nothing).  Particles are held nearly sorted
+// by (cell, group), so a warp usually issues one atomic per run.
+__device__ __forceinline__ void warp_run_add(double* base, int key, double v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(full, head);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(full, v, o);
+    if (lane - o >= start) v += t;
+  }
+  const int nxt = __shfl_down_sync(full, key, 1);
+  const bool tail = lane == 31 || nxt != key;
+  if (tail && key >= 0) atomicAdd(base + key, v);
+}
+
+// exclusive rank of `flag` within the block and the block's count
+__device__ __forceinline__ unsigned block_rank(bool flag, unsigned* total) {
+  __shared__ unsigned s_cnt[32];
+  __shared__ unsigned s_tot;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned b = __ballot_sync(full, flag);
+  const unsigned r = __popc(b & ((1u << lane) - 1u));
+  if (lane == 0) s_cnt[wid] = __popc(b);
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned x = lane < nw ? s_cnt[lane] : 0u;
+    unsigned inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(full, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane < nw) s_cnt[lane] = inc - x;
+    if (lane == nw - 1) s_tot = inc;
+  }
+  __syncthreads();
+  const unsigned res = s_cnt[wid] + r;
+  *total = s_tot;
+  __syncthreads();
+  return res;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
+  const long long n_surv = (long long)ctrl->n_part[cur];
+  const long long n_tot = n_surv + (long long)ctrl->n_new;
+  const uint32_t step = (uint32_t)ctrl->step;
+  const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
+  const double v = d.v, dt = d.dt, inv_rate = d.eps * d.eps / d.c;
+  const double* __restrict__ in_x = d.px[cur];
+  const double* __restrict__ in_y = d.py[cur];
+  const double* __restrict__ in_ox = d.pox[cur];
+  const double* __restrict__ in_oy = d.poy[cur];
+  const double* __restrict__ in_nu = d.pnu[cur];
+  const double* __restrict__ in_w = d.pw[cur];
+  const unsigned long long* __restrict__ in_id = d.pid[cur];
+  const uint32_t* __restrict__ in_key = d.pkey[cur];
+  __shared__ unsigned long long s_base;
+
+  unsigned long long c_seg = 0, c_abs = 0, c_esc = 0, c_surv = 0, c_rem = 0;
+  const long long ntiles = (n_tot + kStreamThreads - 1) / kStreamThreads;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long i = t * kStreamThreads + threadIdx.x;
+    const bool valid = i < n_tot;
+    double x = 0.0, y = 0.0, ox = 0.0, oy = 0.0, nu = 0.0, w = 0.0;
+    unsigned long long id = 0ull;
+    int cell = 0, g = 0, gside = -1;
+    bool newborn = false;
+    Draws rng;
+    rng.init(0ull, step, 0u);
+    if (valid) {
+      if (i < n_surv) {
+        x = in_x[i];
+        ox = in_ox[i];
+        if (DIM == 2) { y = in_y[i]; oy = in_oy[i]; }
+        nu = in_nu[i];
+        w = in_w[i];
+        id = in_id[i];
+        const uint32_t key = in_key[i];
+        cell = (int)(key / (uint32_t)G);
+        g = (int)(key - (uint32_t)cell * (uint32_t)G);
+        rng.init(id, step, 0u);
+      } else {
+        newborn = true;
+        const uint32_t j = (uint32_t)(i - n_surv);
+        const int bin = find_bin(d.off, d.nbins, j);
+        const uint32_t k = j - __ldg(d.off + bin);
+        id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
+             (unsigned long long)k;
+        rng.init(id, step, 0u);
+        const int cb = bin / G;
+        g = bin - cb * G;
+        double Tb;
+        if (cb < d.ncell) {
+          const int cx = cb % nx, cy = cb / nx;
+          x = cx * d.dx + rng.next(d.key0, d.key1) * d.dx;
+          if (DIM == 2) y = cy * d.dy + rng.next(d.key0, d.key1) * d.dy;
+          if (DIM == 1) {
+            ox = 2.0 * rng.next(d.key0, d.key1) - 1.0;
+          } else {
+            const double muz = 2.0 * rng.next(d.key0, d.key1) - 1.0;
+            const double ph = rng.next(d.key0, d.key1);
+            double sp, cp;
+            sincospi(2.0 * ph, &sp, &cp);
+            const double s = sqrt(fmax(0.0, 1.0 - muz * muz));
+            ox = s * cp;
+            oy = s * sp;
+          }
+          cell = cb;
+          Tb = d.T[cb];
+        } else {
+          // black-body ghost (1D): the entering set, mu ~ 2 mu dmu, distance
+          // uniform within reach v mu dt
+          const int side = cb - d.ncell;
+          const double u = rng.next(d.key0, d.key1);
+          const double m = sqrt(rng.next(d.key0, d.key1));
+          const double dd = u * v * m * dt;
+          x = side == 0 ? -dd : nx * d.dx + dd;
+          ox = side == 0 ? m : -m;
+          cell = side == 0 ? -1 : nx;
+          gside = side;
+          Tb = d.bcT[side];
+        }
+        (void)Tb;
+        if (!d.grey)
+          nu = sample_nu(d.nu_edges[g], d.nu_edges[g + 1], __ldg(d.khat + bin), rng.next(d.key0, d.key1));
+        w = __ldg(d.omega + bin);
+      }
+    }
+
+    // ---- streaming
+    int fate = FATE_REMOVED, nseg = 0, eside = -1;
+    const int cell0 = cell;
+    double t_tra = 0.0;
+    if (valid) {
+      const double nup = d.grey ? 1.0 : pow_fast(nu, d.sig_p);
+      double t_rem;
+      bool collided;
+      if (newborn) {
+        t_rem = dt;
+        collided = false;
+      } else {
+        const double u = rng.next(d.key0, d.key1);
+        const double sig = cap_sigma(d, d.sT[cell] * nup);
+        const double tc = -log(u) * inv_rate / sig;
+        collided = tc < dt;
+        t_rem = collided ? tc : dt;
+      }
+      bool ghost = gside >= 0;
+      int cx = DIM == 2 ? cell % nx : cell;
+      int cy = DIM == 2 ? cell / nx : 0;
+      for (int guard = 0;; ++guard) {
+        if (guard >= 4096) {            // defensive bound (NaN state)
+          atomicOr(&ctrl->status, ST_NONFINITE);
+          fate = FATE_REMOVED;
+          break;
+        }
+        const double xL = cx * d.dx, xR = (cx + 1) * d.dx;
+        double tx = INFINITY, ty = INFINITY;
+        if (ox > 0.0) tx = fmax(xR - x, 0.0) / (v * ox);
+        else if (ox < 0.0) tx = fmax(x - xL, 0.0) / (v * -ox);
+        double yB = 0.0, yT = 0.0;
+        if (DIM == 2) {
+          yB = cy * d.dy;
+          yT = (cy + 1) * d.dy;
+          if (oy > 0.0) ty = fmax(yT - y, 0.0) / (v * oy);
+          else if (oy < 0.0) ty = fmax(y - yB, 0.0) / (v * -oy);
+        }
+        const int axis = (tx <= ty) ? 0 : 1;
+        const double tf = axis == 0 ? tx : ty;
+        if (tf < t_rem) {
+          ++nseg;
+          t_tra += tf;
+          t_rem -= tf;
+          int dir;
+          if (axis == 0) {
+            dir = ox > 0.0 ? 1 : -1;
+            x = dir > 0 ? xR : xL;
+            if (DIM == 2) y += v * oy * tf;
+          } else {
+            dir = oy > 0.0 ? 1 : -1;
+            y = dir > 0 ? yT : yB;
+            x += v * ox * tf;
+          }
+          const int nxc = cx + (axis == 0 ? dir : 0), nyc = cy + (axis == 1 ? dir : 0);
+          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny) {
+            const int side = axis * 2 + (dir > 0 ? 1 : 0);
+            if (d.bc[side] == BC_REFLECT) {
+              if (axis == 0) ox = -ox; else oy = -oy;
+              continue;
+            }
+            fate = FATE_ESCAPED;
+            eside = side;
+            break;
+          }
+          ghost = false;
+          cx = nxc;
+          cy = nyc;
+          cell = cy * nx + cx;
+          const double u = rng.next(d.key0, d.key1);
+          const double sig = cap_sigma(d, d.sT[cell] * nup);
+          const double tc = -log(u) * inv_rate / sig;
+          const double avail = dt - t_tra;
+          collided = tc < avail;
+          t_rem = collided ? tc : avail;
+          continue;
+        }
+        ++nseg;
+        x += v * ox * t_rem;
+        if (DIM == 2) y += v * oy * t_rem;
+        t_tra += t_rem;
+        t_rem = 0.0;
+        fate = ghost ? FATE_REMOVED : (collided ? FATE_ABSORBED : FATE_SURVIVED);
+        break;
+      }
+    }
+
+    // ---- tallies
+    const int lane = threadIdx.x & 31;
+    warp_run_add(d.E_surv, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, w);
+    if (valid && fate != FATE_REMOVED) {
+      const bool start_in = gside < 0;
+      const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
+      if (!(start_in && end_in && cell0 == cell)) {
+        if (start_in) atomicAdd(d.W + cell0 * G + g, -w);
+        if (end_in) atomicAdd(d.W + cell * G + g, w);
+      }
+      if (!start_in) atomicAdd(d.inflow + gside * G + g, w);
+      if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, w);
+    }
+    if (valid) {
+      c_seg += (unsigned long long)nseg;
+      c_abs += fate == FATE_ABSORBED;
+      c_esc += fate == FATE_ESCAPED;
+      c_surv += fate == FATE_SURVIVED;
+      c_rem += fate == FATE_REMOVED;
+      if (d.rec && i < d.rec_cap) {
+        RecordOut& r = d.rec[i];
+        r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = cell; r.grp = g; r.nseg = nseg; r.pad = 0;
+        r.x = x; r.y = y; r.ox = ox; r.oy = oy; r.nu = nu; r.w = w; r.t_end = t_tra;
+      }
+    }
+
+    // ---- compaction of the collisionless survivors
+    const bool keep = valid && fate == FATE_SURVIVED;
+    unsigned cnt;
+    const unsigned rank = block_rank(keep, &cnt);
+    if (threadIdx.x == 0) s_base = cnt ? atomicAdd(&ctrl->n_out, (unsigned long long)cnt) : 0ull;
+    __syncthreads();
+    if (keep) {
+      const unsigned long long o = s_base + rank;
+      if (o < (unsigned long long)d.capacity) {
+        d.px[nxb][o] = x;
+        d.pox[nxb][o] = ox;
+        if (DIM == 2) { d.py[nxb][o] = y; d.poy[nxb][o] = oy; }
+        d.pnu[nxb][o] = nu;
+        d.pw[nxb][o] = w;
+        d.pid[nxb][o] = id;
+        d.pkey[nxb][o] = (uint32_t)(cell * G + g);
+      } else {
+        atomicOr(&ctrl->status, ST_CAPACITY);
+      }
+    }
+    __syncthreads();
+  }
+  c_seg = warp_sum_u64(c_seg);
+  c_abs = warp_sum_u64(c_abs);
+  c_esc = warp_sum_u64(c_esc);
+  c_surv = warp_sum_u64(c_surv);
+  c_rem = warp_sum_u64(c_rem);
+  if ((threadIdx.x & 31) == 0) {
+    if (c_seg) atomicAdd(&ctrl->n_segments, c_seg);
+    if (c_abs) atomicAdd(&ctrl->n_absorbed, c_abs);
+    if (c_esc) atomicAdd(&ctrl->n_escaped, c_esc);
+    if (c_surv) atomicAdd(&ctrl->n_survived, c_surv);
+    if (c_rem) atomicAdd(&ctrl->n_removed, c_rem);
+  }
+}
+
+static int g_stream_blocks[3] = {0, 0, 0};
+
+cudaError_t launch_stream(const Dev& d, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fn = d.dim == 2 ? (const void*)k_stream64<2> : (const void*)k_stream64<1>;
+  int& per = g_stream_blocks[d.dim];
+  if (!per) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kStreamThreads, 0);
+    if (per < 1) per = 1;
+  }
+  const int blocks = sms * per;
+  if (d.dim == 2) k_stream64<2><<<blocks, kStreamThreads, 0, s>>>(d);
+  else k_stream64<1><<<blocks, kStreamThreads, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace ugkwp

@@ -177,3 +177,51 @@ def small_checkerboard(n: int = 16, G: int = 4, omega_ref: float = 2e-6, seed: i
     p.name = "small_checkerboard_%dx%dx%d" % (n, n, G)
     p.particle_capacity = 1 << 18
     return p
+
+
+def synthetic_state(p: Problem, n_particles: int, seed: int = 1, front: float = 0.2,
+                    step: int = 0) -> dict:
+    """A seeded mid-run state shaped like a Marshak front, for full-size runs
+    that both the CUDA path and the oracle start from.
+
+    Pure input generation: a temperature profile falling from 1 to T0 over
+    `front` of the slab, a radiation field T^4 spread over the groups by a
+    log-normal bump near nu ~ 3T, and n_particles particles placed in
+    (cell, group) bins in proportion to that field, uniform in the cell,
+    isotropic, with frequency uniform in the group and weight
+    omega_ref * U(0.5, 1.5).  1D slabs only.
+    """
+    assert p.dim == 1
+    rng = np.random.Generator(np.random.Philox(seed))
+    xc = (np.arange(p.nx) + 0.5) * p.dx
+    T0 = float(np.min(p.T0))
+    L = p.nx * p.dx
+    T = T0 + (1.0 - T0) * np.sqrt(np.clip(1.0 - xc / (front * L), 0.0, None))
+    if p.grey:
+        shape = np.ones((p.nx, 1))
+    else:
+        lnu = np.log(np.sqrt(p.nu_edges[:-1] * p.nu_edges[1:]))
+        shape = np.exp(-0.5 * ((lnu[None, :] - np.log(3.0 * T[:, None])) / 0.7) ** 2)
+        shape /= shape.sum(1, keepdims=True)
+    rho = (T[:, None] ** 4) * shape
+    prob = rho.reshape(-1) / rho.sum()
+    bins = rng.choice(p.nx * p.G, size=n_particles, p=prob)
+    bins.sort()
+    cell = (bins // p.G).astype(np.int32)
+    grp = (bins % p.G).astype(np.int32)
+    x = (cell + rng.random(n_particles)) * p.dx
+    mu = 2.0 * rng.random(n_particles) - 1.0
+    if p.grey:
+        nu = np.zeros(n_particles)
+    else:
+        lo, hi = p.nu_edges[grp], p.nu_edges[grp + 1]
+        nu = lo + (hi - lo) * rng.random(n_particles)
+    w = p.omega_ref * (0.5 + rng.random(n_particles))
+    # unique identities (birth step 0): bin and rank within the bin
+    first = np.searchsorted(bins, bins, side="left")
+    k = np.arange(n_particles) - first
+    pid = (np.uint64(step) << np.uint64(44)) | (bins.astype(np.uint64) << np.uint64(20)) | k.astype(np.uint64)
+    parts = dict(x=x, y=np.zeros(n_particles), ox=mu, oy=np.zeros(n_particles), nu=nu, w=w,
+                 id=pid, cell=cell, grp=grp)
+    rho = rho.reshape(-1)
+    return dict(T=T, rho=rho, rho_h=0.5 * rho, particles=parts, step=step + 1)

@@ -1,0 +1,188 @@
+"""Whole-step parity of the CUDA path against the oracle, through the C ABI.
+
+Each case loads the oracle's state after some steps into the GPU (same
+particles, same order), runs one step on both with per-particle records, and
+compares: birth counts exactly, every particle's end state (position,
+direction, cell, fate, free time) element by element with event flips
+counted, the surviving particle set, the tallies, and T and rho after the
+source iteration.  Plus multi-step runs from the initial state, the energy
+ledger, edge cases (no particles, ragged tails, capacity overflow) and the
+full-size 200x30 slab in the launch configuration the benchmark times."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_16981_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FLIP_FRACTION = 1e-4     # end states allowed to differ by an event flip
+POS_RTOL = 1e-9          # end positions / times of unflipped particles
+T_RTOL = 1e-9            # cell temperature after the source iteration
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2312_16981_gb300 import binding
+    binding.load()
+    return binding
+
+
+def oracle_run(p, nsteps):
+    op = O.OracleProblem(p)
+    st = O.initial_state(op)
+    for _ in range(nsteps):
+        st, _, _, status = O.step(op, st)
+        assert status == 0
+    return op, st
+
+
+def compare_records(p, rg, ro):
+    assert len(rg) == len(ro)
+    np.testing.assert_array_equal(rg["id"], ro["id"])
+    np.testing.assert_array_equal(rg["grp"], ro["grp"])
+    np.testing.assert_array_equal(rg["cell0"], ro["cell0"])
+    same = (rg["fate"] == ro["fate"]) & (rg["cell1"] == ro["cell1"]) & (rg["nseg"] == ro["nseg"])
+    flips = int((~same).sum())
+    assert flips <= max(1, FLIP_FRACTION * len(rg)), flips
+    L = max(p.nx * p.dx, (p.ny * p.dy) if p.dim == 2 else 0.0)
+    for f in ("x", "y", "ox", "oy", "nu", "w", "t_end"):
+        a, b = rg[f][same], ro[f][same]
+        scale = {"x": L, "y": L, "t_end": p.dt, "ox": 1.0, "oy": 1.0}.get(f, None)
+        tol = POS_RTOL * (scale if scale is not None else np.abs(b))
+        bad = np.abs(a - b) > tol + 1e-300
+        assert not bad.any(), (f, a[bad][:5], b[bad][:5])
+    return flips
+
+
+def one_step(B, p, before):
+    op, st = oracle_run(p, before)
+    sim = B.Simulation(p)
+    sim.set_state(st.T, st.rho, st.rho_h, st.particles.view(), step=st.step)
+    _, n_new, _ = O.birth_counts(op, st.T, st.rho_h)
+    sim.attach_records(st.particles.n + n_new + 8)
+    sim.step(1)
+    t = sim.tallies()
+    g = sim.get_state()
+    rg = sim.records(t["n_in"] + t["n_born"])
+    st2, tal, ro, status = O.step(op, st, records=True)
+    assert status == 0 and t["status_bits"] == 0
+    return sim, t, g, rg, st2, tal, ro
+
+
+def check_step(B, p, before):
+    sim, t, g, rg, st2, tal, ro = one_step(B, p, before)
+    assert t["n_born"] == tal.c.n_born and t["n_in"] == tal.c.n_in
+    flips = compare_records(p, rg, ro)
+    assert abs(t["n_survived"] - tal.c.n_survived) <= flips
+    # surviving particles as sets keyed by id
+    pg, po = g["particles"], st2.particles.view()
+    if flips == 0:
+        ig, io = np.argsort(pg["id"]), np.argsort(po["id"])
+        np.testing.assert_array_equal(pg["id"][ig], po["id"][io])
+        np.testing.assert_array_equal(pg["cell"][ig], po["cell"][io])
+        np.testing.assert_allclose(pg["x"][ig], po["x"][io], rtol=0, atol=POS_RTOL)
+    # tallies and macroscopic state
+    W = sim.device_array("W").cpu().numpy()
+    scale = np.abs(tal.W).max() + np.abs(tal.E_surv).max() + 1e-300
+    assert np.abs(W - tal.W).max() <= 1e-12 * scale + flips * tal.omega.max()
+    np.testing.assert_allclose(g["T"], st2.T, rtol=T_RTOL, atol=0)
+    rs = np.abs(st2.rho.reshape(p.ncell, p.G)).sum(1, keepdims=True)
+    assert (np.abs(g["rho"] - st2.rho).reshape(p.ncell, p.G) <= 1e-9 * rs + 1e-300).all()
+    assert abs(t["si_iters"] - tal.c.si_iters) <= 1
+    return t, tal
+
+
+@pytest.mark.parametrize("before", [0, 3])
+def test_step_parity_multigroup_slab(B, before):
+    p = I.small_multigroup(nx=24, G=6, omega_ref=1e-6)
+    t, tal = check_step(B, p, before)
+    assert t["n_born"] > 300
+
+
+def test_step_parity_grey_slab(B):
+    p = I.grey_slab(nx=50, omega_ref=2e-6)
+    p.particle_capacity = 1 << 18
+    check_step(B, p, 5)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_step_parity_checkerboard_2d(B, order):
+    p = I.small_checkerboard(n=16, G=4, omega_ref=2e-7)
+    p.wave_order = order
+    t, tal = check_step(B, p, 2)
+    assert t["n_born"] > 1000
+
+
+def test_multi_step_trajectory(B):
+    p = I.small_multigroup(nx=20, G=5, omega_ref=2e-6)
+    op, st = oracle_run(p, 0)
+    sim = B.Simulation(p)
+    for n in range(8):
+        sim.step(1)
+        st, tal, _, _ = O.step(op, st)
+        g = sim.get_state()
+        np.testing.assert_allclose(g["T"], st.T, rtol=T_RTOL, atol=0)
+        assert g["n"] == st.particles.n
+
+
+def test_energy_ledger_on_gpu(B):
+    p = I.small_multigroup(nx=16, G=4, omega_ref=1e-6)
+    p.bc = [I.BC_REFLECT] * 4
+    p.T0 = np.linspace(0.3, 1.0, p.nx)
+    sim = B.Simulation(p)
+    for _ in range(5):
+        sim.step(1)
+        t = sim.tallies()
+        E0, E1 = t["E_rad0"] + t["E_mat0"], t["E_rad1"] + t["E_mat1"]
+        assert abs(E1 - E0) <= 1e-13 * E0
+    assert t["n_in"] > 0
+
+
+def test_pure_wave_no_particles(B):
+    p = I.small_checkerboard(n=12, G=3, omega_ref=0.0)
+    op, st = oracle_run(p, 0)
+    sim = B.Simulation(p)
+    for _ in range(3):
+        sim.step(1)
+        st, _, _, _ = O.step(op, st)
+    g = sim.get_state()
+    t = sim.tallies()
+    assert t["n_born"] == 0 and g["n"] == 0
+    np.testing.assert_allclose(g["T"], st.T, rtol=T_RTOL)
+
+
+def test_capacity_overflow_is_reported(B):
+    p = I.small_multigroup(nx=16, G=4, omega_ref=1e-7)
+    p.particle_capacity = 100
+    sim = B.Simulation(p)
+    sim.step(2)
+    t = sim.tallies()
+    assert t["status_bits"] & B.ST_CAPACITY
+    assert t["n_particles"] <= 100
+
+
+def test_full_size_multigroup_slab_one_step(B):
+    # the 200-cell, 30-group slab at 1e6 particles, in the benchmark's launch
+    # configuration: both sides start from the same seeded synthetic
+    # mid-run state and take one full step
+    p = I.multigroup_slab()
+    s = I.synthetic_state(p, 1_000_000, seed=3)
+    sim = B.Simulation(p)
+    sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
+    op = O.OracleProblem(p)
+    st = O.State(p, s["T"], s["rho"], s["rho_h"], O.ParticleSet.from_arrays(s["particles"]), s["step"])
+    _, n_new, _ = O.birth_counts(op, st.T, st.rho_h)
+    sim.attach_records(1_000_000 + n_new + 8)
+    sim.step(1)
+    t = sim.tallies()
+    rg = sim.records(t["n_in"] + t["n_born"])
+    gg = sim.get_state()
+    st2, tal, ro, status = O.step(op, st, records=True)
+    assert status == 0 and t["status_bits"] == 0
+    assert t["n_in"] == 1_000_000 and t["n_born"] == tal.c.n_born
+    compare_records(p, rg, ro)
+    np.testing.assert_allclose(gg["T"], st2.T, rtol=T_RTOL, atol=0)
+    rs = np.abs(st2.rho.reshape(p.ncell, p.G)).sum(1, keepdims=True)
+    assert (np.abs(gg["rho"] - st2.rho).reshape(p.ncell, p.G) <= 1e-9 * rs).all()
