@@ -130,14 +130,14 @@ static double gl_panel(integrand_fn f, double a, double b) {
 }
 
 /* Composite rule on n equal panels, n doubled until two successive values
- * agree to 1e-13; the finer one is then correct to rounding, since the
+ * agree to 1e-14; the finer one is then correct to rounding, since the
  * 20-point rule's error falls like h^40 on these analytic integrands.      */
 static double gl_composite(integrand_fn f, double a, double b) {
   double prev = gl_panel(f, a, b);
   for (int n = 2; n <= 4096; n *= 2) {
     double h = (b - a) / n, s = 0.0;
     for (int i = 0; i < n; ++i) s += gl_panel(f, a + i * h, i == n - 1 ? b : a + (i + 1) * h);
-    if (fabs(s - prev) <= 1e-13 * fabs(s)) return s;
+    if (fabs(s - prev) <= 1e-14 * fabs(s)) return s;
     prev = s;
   }
   return prev;
@@ -154,11 +154,19 @@ static double integrate(integrand_fn f, double x1, double x2) {
     total += gl_composite(f, a, b);
     a = b;
   }
-  /* beyond t = 800 both integrands are below 1e-330: zero in binary64 */
+  /* beyond t = 800 both integrands are below 1e-340: zero in binary64 */
   return total;
 }
 
-static double planck_t3(double t) { return t * t * t / expm1(t); }
+/* t^3/(e^t - 1), written with e^{-t} above t = 1 so that it does not overflow
+ * to zero at t ~ 709.8 (which would truncate the tail of deep-Wien groups). */
+static double planck_t3(double t) {
+  if (t > 1.0) {
+    double em = exp(-t);
+    return t * t * t * em / (1.0 - em);
+  }
+  return t * t * t / expm1(t);
+}
 
 static double planck_t4(double t) {
   if (t > 1.0) {

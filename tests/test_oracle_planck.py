@@ -31,7 +31,7 @@ def test_large_x_closed_form():
     # for x >= 40 only the n = 1 term of the Bose series survives:
     # int_x^inf t^3 e^-t dt = e^-x (x^3 + 3x^2 + 6x + 6)
     P = lambda x: math.exp(-x) * (x ** 3 + 3 * x ** 2 + 6 * x + 6)
-    for a, b in [(40.0, 45.0), (50.0, 80.0), (100.0, 101.0)]:
+    for a, b in [(40.0, 45.0), (50.0, 80.0), (100.0, 101.0), (600.0, 800.0), (683.3, 928.8)]:
         exact = 15 / math.pi ** 4 * (P(a) - P(b))
         assert abs(O.planck_integral(a, b) - exact) <= 1e-13 * exact
 
