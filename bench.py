@@ -48,10 +48,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def workload(rank: int = 0):
+def workload(rank: int = 0, n_particles: int = N_PARTICLES):
     p = I.multigroup_slab()
     p.instance = rank
-    s = I.synthetic_state(p, N_PARTICLES, seed=1)
+    p.particle_capacity = max(p.particle_capacity, int(n_particles * 1.5))
+    s = I.synthetic_state(p, n_particles, seed=1)
     return p, s
 
 
@@ -79,7 +80,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -102,7 +103,7 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm = [float(r[1]) for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v})
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
                 "reasons": reasons, "samples": len(rows)}
 
@@ -145,24 +146,50 @@ def run_reference(args):
     return 0
 
 
-def algorithmic_bytes(p, phase, n_in, n_out, si_iters):
+def algorithmic_bytes(p, phase, n_in, n_out, si_iters, mixed=False):
     """Algorithmic HBM bytes of one launch of a phase (see the design notes)."""
     ncg = p.ncell * p.G
     if phase == "particles":
-        per = 4 * 8 + 8 + 4   # x, mu, nu, w (FP64), id, bin key
+        per = (4 * 4 if mixed else 4 * 8) + 8 + 4   # x, mu, nu, w; id; bin key
         return per * n_in + per * n_out + 3 * 8 * ncg
     if phase == "source_iteration":
         return si_iters * 10 * 8 * ncg
     return 0
 
 
+def timed_steps(sim, steps, flush, sampler=None):
+    """Device time per step (CUDA events) with L2 flushed between steps."""
+    import torch
+    phases = np.zeros(6)
+    segs = n_in = n_out = si = 0
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.fill_(1)
+        ms = sim.step_timed()
+        t = sim.tallies()
+        phases += np.array(ms)
+        segs += t["n_segments"]
+        n_in += t["n_in"] + t["n_born"]
+        n_out += t["n_survived"]
+        si += t["si_iters"]
+    torch.cuda.synchronize()
+    assert t["status_bits"] == 0, t["status_bits"]
+    return phases, segs, n_in, n_out, si
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--particles", type=int, default=N_PARTICLES,
+                    help="particles in the starting state (profiling runs use other sizes)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps of one precision only (no e2e, mixed or CPU legs): for profiler runs")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="particle precision of the headline (quick) run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -175,6 +202,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
     if world > 1:
         dist.init_process_group("nccl")
 
@@ -182,41 +210,36 @@ def main():
         if world > 1:
             dist.barrier()
 
-    p, s = workload(rank)
-    sim = B.Simulation(p, device="cuda:%d" % local)
-    sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
-    for _ in range(max(args.warmup, 3)):
-        sim.step(1)
-    t = sim.tallies()
-    assert t["status_bits"] == 0, t["status_bits"]
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda:%d" % local)
+    K = args.steps
+    names = ["total", "birth_scan", "wave", "particles", "source_iteration", "end"]
+    pk, src = peaks()
+    p, s = workload(rank, args.particles)
+    if args.quick and args.precision == "mixed":
+        p = p.replace(precision=I.MIXED)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
-    # ---- timed region (device time per step from CUDA events)
-    phases = np.zeros(6)
-    segs = 0
-    n_in_sum = n_out_sum = 0
-    si_sum = 0
-    ms_steps = []
+    def prepare(prob):
+        sim = B.Simulation(prob, device=dev)
+        sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
+        for _ in range(max(args.warmup, 3)):
+            sim.step(1)
+        assert sim.tallies()["status_bits"] == 0
+        return sim
+
+    sim = prepare(p)
+    simm = None if args.quick else prepare(p.replace(precision=I.MIXED))
+
+    # ---- timed regions: FP64, then mixed precision (device time, CUDA events)
     barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)
-            ms = sim.step_timed()
-            t = sim.tallies()
-            phases += np.array(ms)
-            ms_steps.append(ms[0])
-            segs += t["n_segments"]
-            n_in_sum += t["n_in"] + t["n_born"]
-            n_out_sum += t["n_survived"]
-            si_sum += t["si_iters"]
-    torch.cuda.synchronize()
+        phases, segs, n_in, n_out, si = timed_steps(sim, K, flush)
+        if simm is not None:
+            mph, msegs, min_, mout, msi = timed_steps(simm, K, flush)
     barrier()
     clocks = clk.summary()
-    assert t["status_bits"] == 0, t["status_bits"]
     total_ms = float(phases[0])
     if world > 1:
-        tt = torch.tensor([total_ms, float(segs)], dtype=torch.float64, device="cuda")
+        tt = torch.tensor([total_ms, float(segs)], dtype=torch.float64, device=dev)
         mx = tt.clone()
         dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
@@ -225,66 +248,77 @@ def main():
         total_ms_max, segs_all = total_ms, float(segs)
     value = segs_all / (total_ms_max / 1e3)
 
-    # ---- roofline of the dominant kernel
-    names = ["total", "birth_scan", "wave", "particles", "source_iteration", "end"]
+    # ---- roofline of the dominant kernel (FP64 build)
     dom = int(np.argmax(phases[1:])) + 1
-    pk, src = peaks()
-    K = args.steps
     per_launch_ms = phases[dom] / K
-    abytes = algorithmic_bytes(p, names[dom], n_in_sum / K, n_out_sum / K, si_sum / K)
-    if abytes > 0:
-        ach = abytes / (per_launch_ms * 1e-3) / 1e9
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
-                "peak_source": src, "algorithmic_bytes_per_launch": abytes}
+    abytes = algorithmic_bytes(p, names[dom], n_in / K, n_out / K, si / K, mixed=p.precision == I.MIXED)
+    ach = abytes / (per_launch_ms * 1e-3) / 1e9 if abytes else 0.0
+    roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+            "peak_source": src, "algorithmic_bytes_per_launch": abytes}
+
+    line = {"metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": total_ms_max / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": config_dict(p, args.particles, {"parallelism": "replicas" if world > 1 else "single"}),
+            "steps_per_s": K / (total_ms_max / 1e3),
+            "phase_ms_per_step": {n: float(phases[i] / K) for i, n in enumerate(names)},
+            "particles_per_step": n_in / K, "si_iters_per_step": si / K,
+            "roofline": roof, "clocks": clocks}
+
+    if simm is not None:
+        mb = algorithmic_bytes(p, "particles", min_ / K, mout / K, 0, mixed=True)
+        mach = mb / (mph[3] / K * 1e-3) / 1e9
+        line["mixed"] = {
+            "value": msegs / (mph[0] / 1e3), "unit": "segments/s",
+            "dtype": "f32 particle state, f64 tallies and source iteration",
+            "ms_per_step": float(mph[0] / K),
+            "speedup_vs_fp64": (msegs / mph[0]) / (segs / phases[0]),
+            "phase_ms_per_step": {n: float(mph[i] / K) for i, n in enumerate(names)},
+            "particle_kernel_roofline": {"bound": "hbm", "achieved": mach, "peak": pk["hbm_gbs"],
+                                         "unit": "GB/s", "frac": mach / pk["hbm_gbs"],
+                                         "algorithmic_bytes_per_launch": mb}}
+        simm.close()
+
+        # ---- end to end through the C ABI with host buffers
+        Tdev = sim.device_array("T")
+        Rdev = sim.device_array("rho")
+        Th = torch.empty(Tdev.shape, dtype=torch.float64, pin_memory=True)
+        Rh = torch.empty(Rdev.shape, dtype=torch.float64, pin_memory=True)
+        Th.copy_(Tdev)
+        Rh.copy_(Rdev)
+        torch.cuda.synchronize()
+        e2e_segs = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            Tdev.copy_(Th, non_blocking=True)
+            Rdev.copy_(Rh, non_blocking=True)
+            sim.step(1)
+            Th.copy_(Tdev, non_blocking=True)
+            Rh.copy_(Rdev, non_blocking=True)
+            tt = sim.tallies()           # synchronises: the step's result is on the host
+            e2e_segs += tt["n_segments"]
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        line["e2e"] = {"value": e2e_segs / e2e_s, "unit": "segments/s",
+                       "h2d_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
+                       "d2h_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
+                       "what": "per step: H2D of T and rho from pinned host memory, ugkwp_step "
+                               "(CUDA graph), D2H of T, rho and the tally report"}
+        line["gpu_launches"] = KERNELS_PER_STEP * K * 3
     else:
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": 0.0, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": 0.0, "traffic": None, "peak_source": src}
+        line["gpu_launches"] = KERNELS_PER_STEP * K
 
-    # ---- end to end through the C ABI with host buffers
-    Tdev = sim.device_array("T")
-    Rdev = sim.device_array("rho")
-    Th = torch.empty(Tdev.shape, dtype=torch.float64, pin_memory=True)
-    Rh = torch.empty(Rdev.shape, dtype=torch.float64, pin_memory=True)
-    Th.copy_(Tdev)
-    Rh.copy_(Rdev)
-    torch.cuda.synchronize()
-    e2e_segs = 0
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Tdev.copy_(Th, non_blocking=True)
-        Rdev.copy_(Rh, non_blocking=True)
-        sim.step(1)
-        Th.copy_(Tdev, non_blocking=True)
-        Rh.copy_(Rdev, non_blocking=True)
-        tt = sim.tallies()           # synchronises: the step's result is on the host
-        e2e_segs += tt["n_segments"]
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    e2e = {"value": e2e_segs / e2e_s, "unit": "segments/s",
-           "h2d_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
-           "d2h_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
-           "what": "per step: H2D of T, rho from pinned host memory, ugkwp_step, D2H of T, rho and the tally report"}
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not args.quick:
         n_sample = 100_000
         osegs, ot = oracle_segments_per_s(p, s, n_sample, 3)
-        cpu = {"value": osegs / ot, "unit": "segments/s", "cores": 1, "kind": "oracle",
-               "sample": "3 oracle steps of the same workload with the first %d of %d particles "
-                         "(full 200x30 source iteration each step)" % (n_sample, N_PARTICLES)}
-
+        line["cpu_baseline"] = {
+            "value": osegs / ot, "unit": "segments/s", "cores": 1, "kind": "oracle",
+            "sample": "3 oracle steps of the same workload with the first %d of %d particles "
+                      "(full 200x30 source iteration each step)" % (n_sample, args.particles)}
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
-                "steps": K, "warmup": args.warmup, "ms_per_step": total_ms_max / K,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": config_dict(p, N_PARTICLES, {"parallelism": "replicas"}),
-                "steps_per_s": K / (total_ms_max / 1e3),
-                "phase_ms_per_step": {n: float(phases[i] / K) for i, n in enumerate(names)},
-                "particles_per_step": n_in_sum / K, "si_iters_per_step": si_sum / K,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": KERNELS_PER_STEP * K}
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:

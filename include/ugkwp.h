@@ -195,6 +195,15 @@ int ugkwp_planck(const double* d_T, int64_t n, const double* d_nu_edges, int G, 
  * coefficients). */
 int ugkwp_coefs(const double* d_x, int64_t n, double* d_out, void* stream);
 
+/* Exclusive prefix sum of per-bin birth counts (the birth ordinals of
+ * Eq. IhpFormula's sampled particles): d_offsets[i] = sum_{j<i} d_counts[j]
+ * for i = 0..n (n + 1 values, d_offsets[n] = the total).  n <= 2^24 and the
+ * total must fit in 32 bits.  d_scratch: a DEVICE buffer of at least
+ * UGKWP_SCAN_SCRATCH_BYTES(n) bytes for the per-block partial sums. */
+#define UGKWP_SCAN_SCRATCH_BYTES(n) (4 * (((n) + 4095) / 4096) + 4)
+int ugkwp_exclusive_scan(const uint32_t* d_counts, int64_t n, uint32_t* d_offsets, void* d_scratch,
+                         size_t scratch_bytes, void* stream);
+
 /* Frequency of a particle from uniforms d_eta [n] for group [nlo, nhi] at
  * temperature T (App. A, linear-frequency sampling) into d_nu [n]. */
 int ugkwp_sample_nu(const double* d_eta, int64_t n, double nlo, double nhi, double T, double* d_nu,

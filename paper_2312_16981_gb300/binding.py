@@ -94,7 +94,13 @@ FUNCTIONS = {
     "ugkwp_coefs": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ugkwp_sample_nu": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double,
                                   C.c_void_p, C.c_void_p]),
+    "ugkwp_exclusive_scan": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
+                                       C.c_void_p]),
 }
+
+
+def scan_scratch_bytes(n: int) -> int:
+    return 4 * ((n + 4095) // 4096) + 4
 
 
 def load(path: str = LIB_PATH):
@@ -345,3 +351,17 @@ def sample_nu(eta, nlo: float, nhi: float, T: float):
     _check(load().ugkwp_sample_nu(C.c_void_p(_ptr(eta)), eta.numel(), nlo, nhi, T,
                                   C.c_void_p(_ptr(nu)), C.c_void_p(_stream_ptr())))
     return nu
+
+
+def exclusive_scan(counts):
+    """Exclusive prefix sum of uint32 counts (int32 tensor on the device) ->
+    [n + 1] offsets (int64 view of the uint32 results)."""
+    import torch
+    counts = counts.contiguous().to(torch.int32)
+    n = counts.numel()
+    out = torch.empty(n + 1, dtype=torch.int32, device=counts.device)
+    scratch = torch.empty(scan_scratch_bytes(n), dtype=torch.uint8, device=counts.device)
+    _check(load().ugkwp_exclusive_scan(C.c_void_p(_ptr(counts) if n else 0), n, C.c_void_p(_ptr(out)),
+                                       C.c_void_p(_ptr(scratch)), scratch.numel(),
+                                       C.c_void_p(_stream_ptr())))
+    return out.to(torch.int64) & 0xFFFFFFFF

@@ -19,6 +19,9 @@ struct ugkwp_handle {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   char err[512];
+  // one step captured as a CUDA graph, replayed by ugkwp_step
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -69,7 +72,8 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
   }
   if (p->wave_order != 1 && p->wave_order != 2) return fail(h, UGKWP_ERR_ARG, "wave_order must be 1 or 2");
   if (p->si_max_iters < 1) return fail(h, UGKWP_ERR_ARG, "si_max_iters must be >= 1");
-  if (p->precision != UGKWP_FP64) return fail(h, UGKWP_ERR_UNSUPPORTED, "only FP64 particles in this build");
+  if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED)
+    return fail(h, UGKWP_ERR_ARG, "precision must be UGKWP_FP64 or UGKWP_MIXED");
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
   const long long nbins = (ncell_of(p) + 4) * p->G;
   if (nbins >= (1ll << 24)) return fail(h, UGKWP_ERR_ARG, "(ncell+4)*G must be < 2^24 (particle id layout)");
@@ -106,7 +110,7 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.sT = cv.take<double>(nc);
   d.N = cv.take<uint32_t>(nb);
   d.off = cv.take<uint32_t>(nb + 1);
-  d.part = cv.take<uint32_t>(ugkwp::scan_parts((int)nb) + 1);
+  d.part = cv.take<uint32_t>(ugkwp::scan_parts(nb) + 1);
   d.omega = cv.take<double>(nb);
   d.e_eff = cv.take<double>(nb);
   d.khat = cv.take<double>(nb);
@@ -126,13 +130,31 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.dphik = cv.take<double>(ncg);
   d.ctrl = cv.take<Ctrl>(1);
   *src_T_tmp = d.R;   // scratch during init only
+  const bool mixed = p->precision == UGKWP_MIXED;
+  d.sT_f = mixed ? cv.take<float>(nc) : nullptr;
+  d.omega_f = mixed ? cv.take<float>(nb) : nullptr;
+  d.khat_f = mixed ? cv.take<float>(nb) : nullptr;
+  d.particles_begin = nullptr;
   for (int b = 0; b < 2; ++b) {
-    d.px[b] = cv.take<double>(P);
-    d.pox[b] = cv.take<double>(P);
-    d.py[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
-    d.poy[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
-    d.pnu[b] = cv.take<double>(P);
-    d.pw[b] = cv.take<double>(P);
+    if (mixed) {
+      d.fx[b] = cv.take<float>(P);
+      if (!b) d.particles_begin = d.fx[0];
+      d.fox[b] = cv.take<float>(P);
+      d.fy[b] = p->dim == 2 ? cv.take<float>(P) : nullptr;
+      d.foy[b] = p->dim == 2 ? cv.take<float>(P) : nullptr;
+      d.fnu[b] = cv.take<float>(P);
+      d.fw[b] = cv.take<float>(P);
+      d.px[b] = d.pox[b] = d.py[b] = d.poy[b] = d.pnu[b] = d.pw[b] = nullptr;
+    } else {
+      d.px[b] = cv.take<double>(P);
+      if (!b) d.particles_begin = d.px[0];
+      d.pox[b] = cv.take<double>(P);
+      d.py[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
+      d.poy[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
+      d.pnu[b] = cv.take<double>(P);
+      d.pw[b] = cv.take<double>(P);
+      d.fx[b] = d.fox[b] = d.fy[b] = d.foy[b] = d.fnu[b] = d.fw[b] = nullptr;
+    }
     d.pid[b] = cv.take<unsigned long long>(P);
     d.pkey[b] = cv.take<uint32_t>(P);
   }
@@ -217,7 +239,7 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
   fill_scalars(p, d);
   const long long nc = d.ncell, G = d.G, ncg = nc * G;
   // zero everything but the particle buffers
-  const size_t head = (size_t)((char*)d.px[0] - (char*)d_workspace);
+  const size_t head = (size_t)((char*)d.particles_begin - (char*)d_workspace);
   auto bad = [&](cudaError_t e, const char* w) { int r = cuda_fail(h, e, w); snprintf(g_err, 512, "%s", h->err); delete h; return r; };
   cudaError_t e;
   if ((e = cudaMemsetAsync(d_workspace, 0, head, s)) != cudaSuccess) return bad(e, "memset");
@@ -241,17 +263,53 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
   return UGKWP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+cudaError_t enqueue_step(const Dev& d, cudaStream_t s) {
+  cudaError_t e = ugkwp::launch_birth_and_scan(d, s);
+  if (!e) e = ugkwp::launch_wave(d, s);
+  if (!e) e = ugkwp::launch_stream(d, s);
+  if (!e) e = ugkwp::launch_si(d, s);
+  if (!e) e = ugkwp::launch_end_step(d, s);
+  return e;
+}
+
+void drop_graph(ugkwp_handle* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  h->exec = nullptr;
+}
+
+// Capture one step (every kernel reads the step's counts from the device
+// control block, so the same graph serves every step).
+int capture_step(ugkwp_handle* h) {
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), h);
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
+  cudaError_t e = enqueue_step(h->d, h->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capturing the step"); }
+  if (e2) return cuda_fail(h, e2, "end of capture");
+  e = cudaGraphInstantiate(&h->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e) { h->exec = nullptr; return cuda_fail(h, e, "instantiating the step graph"); }
+  return UGKWP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ugkwp_step(ugkwp_handle* h, int nsteps, void* stream) {
   if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
   if (nsteps < 0) return fail(h, UGKWP_ERR_ARG, "nsteps < 0");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int n = 0; n < nsteps; ++n) {
-    CK(ugkwp::launch_birth_and_scan(h->d, s), h);
-    CK(ugkwp::launch_wave(h->d, s), h);
-    CK(ugkwp::launch_stream(h->d, s), h);
-    CK(ugkwp::launch_si(h->d, s), h);
-    CK(ugkwp::launch_end_step(h->d, s), h);
+  if (!h->exec) {
+    int st = capture_step(h);
+    if (st) return st;
   }
+  for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->exec, s), h);
   return UGKWP_OK;
 }
 
@@ -324,23 +382,50 @@ int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, doub
     const long long m = np < cap ? np : cap;
     const unsigned b = c.cur;
     std::vector<uint32_t> key(m > 0 ? m : 1);
-    if (m > 0) {
+    const bool mixed = d.precision == UGKWP_MIXED;
+    std::vector<float> fb(mixed && m > 0 ? (size_t)m * 6 : 1);
+    if (m > 0 && !mixed) {
       CK(cudaMemcpyAsync(parts->x, d.px[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(parts->ox, d.pox[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(parts->nu, d.pnu[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(parts->w, d.pw[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
-      CK(cudaMemcpyAsync(parts->id, d.pid[b], sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, s), h);
-      CK(cudaMemcpyAsync(key.data(), d.pkey[b], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s), h);
       if (d.dim == 2) {
         CK(cudaMemcpyAsync(parts->y, d.py[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
         CK(cudaMemcpyAsync(parts->oy, d.poy[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       }
+    } else if (m > 0) {
+      float* f = fb.data();
+      CK(cudaMemcpyAsync(f, d.fx[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(f + m, d.fox[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(f + 2 * m, d.fnu[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(f + 3 * m, d.fw[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+      if (d.dim == 2) {
+        CK(cudaMemcpyAsync(f + 4 * m, d.fy[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+        CK(cudaMemcpyAsync(f + 5 * m, d.foy[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+      }
+    }
+    if (m > 0) {
+      CK(cudaMemcpyAsync(parts->id, d.pid[b], sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, s), h);
+      CK(cudaMemcpyAsync(key.data(), d.pkey[b], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s), h);
     }
     CK(cudaStreamSynchronize(s), h);
     for (long long i = 0; i < m; ++i) {
-      parts->cell[i] = (int32_t)(key[i] / (uint32_t)d.G);
+      const int cell = (int)(key[i] / (uint32_t)d.G);
+      parts->cell[i] = (int32_t)cell;
       parts->grp[i] = (int32_t)(key[i] % (uint32_t)d.G);
-      if (d.dim == 1) { parts->y[i] = 0.0; parts->oy[i] = 0.0; }
+      if (mixed) {
+        const float* f = fb.data();
+        const int ix = cell % d.nx, iy = cell / d.nx;
+        parts->x[i] = ix * d.dx + (double)f[i];
+        parts->ox[i] = f[m + i];
+        parts->nu[i] = f[2 * m + i];
+        parts->w[i] = f[3 * m + i];
+        parts->y[i] = d.dim == 2 ? iy * d.dy + (double)f[4 * m + i] : 0.0;
+        parts->oy[i] = d.dim == 2 ? (double)f[5 * m + i] : 0.0;
+      } else if (d.dim == 1) {
+        parts->y[i] = 0.0;
+        parts->oy[i] = 0.0;
+      }
     }
   }
   CK(cudaStreamSynchronize(s), h);
@@ -364,17 +449,40 @@ int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const d
       return fail(h, UGKWP_ERR_ARG, "particle cell or group out of range");
     key[i] = (uint32_t)(parts->cell[i] * d.G + parts->grp[i]);
   }
-  if (n > 0) {
+  std::vector<float> fb(d.precision == UGKWP_MIXED && n > 0 ? (size_t)n * 6 : 1);
+  if (n > 0 && d.precision != UGKWP_MIXED) {
     CK(cudaMemcpyAsync(d.px[0], parts->x, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.pox[0], parts->ox, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.pnu[0], parts->nu, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.pw[0], parts->w, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
-    CK(cudaMemcpyAsync(d.pid[0], parts->id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s), h);
-    CK(cudaMemcpyAsync(d.pkey[0], key.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s), h);
     if (d.dim == 2) {
       CK(cudaMemcpyAsync(d.py[0], parts->y, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
       CK(cudaMemcpyAsync(d.poy[0], parts->oy, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     }
+  } else if (n > 0) {
+    // positions relative to the particle's cell, in FP32
+    float* f = fb.data();
+    for (long long i = 0; i < n; ++i) {
+      const int ix = parts->cell[i] % d.nx, iy = parts->cell[i] / d.nx;
+      f[i] = (float)(parts->x[i] - ix * d.dx);
+      f[n + i] = (float)parts->ox[i];
+      f[2 * n + i] = (float)parts->nu[i];
+      f[3 * n + i] = (float)parts->w[i];
+      f[4 * n + i] = d.dim == 2 ? (float)(parts->y[i] - iy * d.dy) : 0.0f;
+      f[5 * n + i] = d.dim == 2 ? (float)parts->oy[i] : 0.0f;
+    }
+    CK(cudaMemcpyAsync(d.fx[0], f, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.fox[0], f + n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.fnu[0], f + 2 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.fw[0], f + 3 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+    if (d.dim == 2) {
+      CK(cudaMemcpyAsync(d.fy[0], f + 4 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+      CK(cudaMemcpyAsync(d.foy[0], f + 5 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+    }
+  }
+  if (n > 0) {
+    CK(cudaMemcpyAsync(d.pid[0], parts->id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(d.pkey[0], key.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s), h);
   }
   Ctrl c;
   CK(cudaMemcpyAsync(&c, d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
@@ -393,12 +501,18 @@ int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap) {
   static_assert(sizeof(ugkwp_record) == sizeof(ugkwp::RecordOut), "record layout");
   h->d.rec = reinterpret_cast<ugkwp::RecordOut*>(d_records);
   h->d.rec_cap = d_records ? cap : 0;
+  drop_graph(h);   // the captured step holds the old record pointer
   return UGKWP_OK;
 }
 
 const char* ugkwp_last_error(const ugkwp_handle* h) { return h ? h->err : g_err; }
 
-void ugkwp_destroy(ugkwp_handle* h) { delete h; }
+void ugkwp_destroy(ugkwp_handle* h) {
+  if (!h) return;
+  drop_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
 
 int ugkwp_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, int64_t n,
                  void* stream) {
@@ -421,6 +535,17 @@ int ugkwp_coefs(const double* d_x, int64_t n, double* d_out, void* stream) {
   if (n < 0 || (n > 0 && (!d_x || !d_out))) return fail(nullptr, UGKWP_ERR_ARG, "bad arguments");
   if (n == 0) return UGKWP_OK;
   CK(ugkwp::launch_unit_coefs(d_x, n, d_out, (cudaStream_t)stream), nullptr);
+  return UGKWP_OK;
+}
+
+int ugkwp_exclusive_scan(const uint32_t* d_counts, int64_t n, uint32_t* d_offsets, void* d_scratch,
+                         size_t scratch_bytes, void* stream) {
+  if (n < 0 || n > (1ll << 24) || !d_offsets || (n > 0 && !d_counts))
+    return fail(nullptr, UGKWP_ERR_ARG, "bad arguments (0 <= n <= 2^24, counts and offsets required)");
+  if (!d_scratch || scratch_bytes < (size_t)UGKWP_SCAN_SCRATCH_BYTES(n))
+    return fail(nullptr, UGKWP_ERR_WORKSPACE, "scratch smaller than UGKWP_SCAN_SCRATCH_BYTES(n)");
+  CK(ugkwp::launch_scan(d_counts, n, static_cast<uint32_t*>(d_scratch), d_offsets, nullptr, nullptr,
+                        (cudaStream_t)stream), nullptr);
   return UGKWP_OK;
 }
 

@@ -69,6 +69,48 @@ struct Draws {
   }
 };
 
+// FP32 uniforms from the same two words as the FP64 draw
+// u = (m + 1/2) 2^-52, m = (a << 20) | (b >> 12): u and 1 - u are each formed
+// with 2^-24 relative precision (so -ln u stays accurate both for small u and
+// for u near 1), both in (0, 1).  -ln u uses log1p(-(1-u)) above u = 1/2.
+struct UPair {
+  float u, v;   // u and 1 - u
+};
+
+__device__ __forceinline__ UPair u01f(uint32_t a, uint32_t b) {
+  UPair r;
+  r.u = __uint2float_rz(a) * 0x1p-32f + (__uint2float_rz(b >> 12) + 0.5f) * 0x1p-52f;
+  r.v = __uint2float_rz(~a) * 0x1p-32f + (__uint2float_rz((~b) >> 12) + 0.5f) * 0x1p-52f;
+  return r;
+}
+
+__device__ __forceinline__ float neg_log_u(const UPair& p) {
+  return p.v < 0.5f ? -log1pf(-p.v) : -logf(p.u);
+}
+
+struct DrawsF {
+  uint32_t id_lo, id_hi, step, j, held;
+  uint4 blk;
+  __device__ __forceinline__ void init(unsigned long long id, uint32_t s, uint32_t first) {
+    id_lo = (uint32_t)id;
+    id_hi = (uint32_t)(id >> 32);
+    step = s;
+    j = first;
+    held = 0;
+  }
+  __device__ __forceinline__ UPair next2(uint32_t k0, uint32_t k1) {
+    const uint32_t b = j >> 1;
+    if (held != b + 1u) {
+      blk = philox4x32_10(make_uint4(id_lo, id_hi, step, b), k0, k1);
+      held = b + 1u;
+    }
+    const UPair u = (j & 1u) ? u01f(blk.z, blk.w) : u01f(blk.x, blk.y);
+    ++j;
+    return u;
+  }
+  __device__ __forceinline__ float next(uint32_t k0, uint32_t k1) { return next2(k0, k1).u; }
+};
+
 // --------------------------------------------------------------------------
 // Problem constants and device pointers, passed to every kernel by value.
 struct Dev {
@@ -124,6 +166,17 @@ struct Dev {
   double* pw[2];
   unsigned long long* pid[2];
   uint32_t* pkey[2];    // bin c*G + g
+  // mixed precision: FP32 state, positions local to the cell (0 <= xi <= dx)
+  float* fx[2];
+  float* fy[2];
+  float* fox[2];
+  float* foy[2];
+  float* fnu[2];
+  float* fw[2];
+  float* sT_f;      // [ncell] sigma0 T^q
+  float* omega_f;   // [nbins]
+  float* khat_f;    // [nbins]
+  void* particles_begin;   // first particle buffer (start of the part left uninitialised)
   // control block and optional records
   struct Ctrl* ctrl;
   struct RecordOut* rec;
@@ -279,12 +332,21 @@ __host__ __device__ constexpr double a2(int k) { return sgn(k) * (1.0 - k) / fac
 __host__ __device__ constexpr double a4(int k) { return -sgn(k) * k / fact_d(k + 1); }
 __host__ __device__ constexpr double a5(int k) { return sgn(k) * k * (1.0 - k) / (2.0 * fact_d(k + 1)); }
 __host__ __device__ constexpr double ac4(int k) { return sgn(k) / fact_d(k + 1); }
+// compile-time tables (k = 0..22)
+#define UGKWP_SER_TABLE(f)                                                                   \
+  {f(0),  f(1),  f(2),  f(3),  f(4),  f(5),  f(6),  f(7),  f(8),  f(9),  f(10), f(11),      \
+   f(12), f(13), f(14), f(15), f(16), f(17), f(18), f(19), f(20), f(21), f(22)}
+__device__ constexpr double kA2[kSer + 1] = UGKWP_SER_TABLE(a2);
+__device__ constexpr double kA4[kSer + 1] = UGKWP_SER_TABLE(a4);
+__device__ constexpr double kA5[kSer + 1] = UGKWP_SER_TABLE(a5);
+__device__ constexpr double kAC4[kSer + 1] = UGKWP_SER_TABLE(ac4);
+#undef UGKWP_SER_TABLE
 
 __device__ __forceinline__ double coef_f2(double x) {
   if (x < 1.0) {
-    double s = a2(kSer);
+    double s = kA2[kSer];
 #pragma unroll
-    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, a2(k));
+    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, kA2[k]);
     return s * x * x;
   }
   const double e = exp(-x), E1 = -expm1(-x);
@@ -293,9 +355,9 @@ __device__ __forceinline__ double coef_f2(double x) {
 
 __device__ __forceinline__ double coef_f4(double x) {
   if (x < 1.0) {
-    double s = a4(kSer);
+    double s = kA4[kSer];
 #pragma unroll
-    for (int k = kSer - 1; k >= 1; --k) s = fma(s, x, a4(k));
+    for (int k = kSer - 1; k >= 1; --k) s = fma(s, x, kA4[k]);
     return s * x;
   }
   return -expm1(-x) / x - exp(-x);
@@ -303,9 +365,9 @@ __device__ __forceinline__ double coef_f4(double x) {
 
 __device__ __forceinline__ double coef_f5(double x) {
   if (x < 1.0) {
-    double s = a5(kSer);
+    double s = kA5[kSer];
 #pragma unroll
-    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, a5(k));
+    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, kA5[k]);
     return s * x * x;
   }
   const double e = exp(-x);
@@ -314,9 +376,9 @@ __device__ __forceinline__ double coef_f5(double x) {
 
 __device__ __forceinline__ double coef_c4(double x) {
   if (x < 1.0) {
-    double s = ac4(kSer);
+    double s = kAC4[kSer];
 #pragma unroll
-    for (int k = kSer - 1; k >= 0; --k) s = fma(s, x, ac4(k));
+    for (int k = kSer - 1; k >= 0; --k) s = fma(s, x, kAC4[k]);
     return s;
   }
   return -expm1(-x) / x;
@@ -351,6 +413,22 @@ __device__ __forceinline__ double sample_nu(double nlo, double nhi, double khat,
   const double q = eta * dnu;
   const double u = 2.0 * q / (A + sqrt(fma(A, A, 2.0 * khat * q)));
   return fmin(nlo + u, nhi);
+}
+
+__device__ __forceinline__ float sample_nu_f(float nlo, float nhi, float khat, float eta) {
+  const float dnu = nhi - nlo;
+  const float A = fmaf(-0.5f * khat, dnu, 1.0f);
+  const float q = eta * dnu;
+  const float u = 2.0f * q / (A + sqrtf(fmaf(A, A, 2.0f * khat * q)));
+  return fminf(nlo + u, nhi);
+}
+
+__device__ __forceinline__ float pow_fast_f(float b, float e) {
+  if (e == 0.0f) return 1.0f;
+  if (e == -3.0f) return __frcp_rn(b * b * b);
+  if (e == -0.5f) return rsqrtf(b);
+  if (e == 1.0f) return b;
+  return __powf(b, e);
 }
 
 // --------------------------------------------------------------------------

@@ -81,7 +81,10 @@ __global__ void k_birth(Dev d) {
     if (cell < d.ncell) {
       Tb = d.T[cell];
       const double sT = sigma_T(d, cell, Tb);
-      if (g == 0) d.sT[cell] = sT;
+      if (g == 0) {
+        d.sT[cell] = sT;
+        if (d.sT_f) d.sT_f[cell] = (float)sT;
+      }
       sig = sigma_group(d, sT, g);
       d.sigT[b] = sig;
       d.W[b] = 0.0;
@@ -94,6 +97,7 @@ __global__ void k_birth(Dev d) {
       d.inflow[side * G + g] = 0.0;
       if (d.dim != 1 || side > 1 || d.bc[side] != BC_BLACKBODY) {
         d.N[b] = 0; d.omega[b] = 0.0; d.e_eff[b] = 0.0; d.khat[b] = 0.0;
+        if (d.omega_f) { d.omega_f[b] = 0.0f; d.khat_f[b] = 0.0f; }
         continue;
       }
       sig = d.ghost_sig[side * G + g];
@@ -113,7 +117,12 @@ __global__ void k_birth(Dev d) {
     d.N[b] = N;
     d.omega[b] = w;
     d.e_eff[b] = ee;
-    d.khat[b] = (N && !d.grey) ? sampler_khat(d.nu_edges[g], d.nu_edges[g + 1], Tb) : 0.0;
+    const double kh = (N && !d.grey) ? sampler_khat(d.nu_edges[g], d.nu_edges[g + 1], Tb) : 0.0;
+    d.khat[b] = kh;
+    if (d.omega_f) {
+      d.omega_f[b] = (float)w;
+      d.khat_f[b] = (float)kh;
+    }
   }
 }
 
@@ -152,46 +161,53 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
   return res;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Dev d) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ N, long long n,
+                                                             uint32_t* __restrict__ part) {
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k)
-    if (base + k < d.nbins) s += d.N[base + k];
+    if (base + k < n) s += N[base + k];
   uint32_t tot;
   block_exclusive_scan(s, &tot);
-  if (threadIdx.x == 0) d.part[blockIdx.x] = tot;
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(Dev d, int nparts) {
-  // one block: exclusive scan of nparts (<= kScanTile) block sums in place
+// one block: exclusive scan of nparts (<= kScanTile) block sums in place; the
+// grand total goes to off[n] and, when given, to two 64-bit counters
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* __restrict__ part, int nparts,
+                                                               uint32_t* __restrict__ off_total,
+                                                               unsigned long long* total_a,
+                                                               unsigned long long* total_b) {
   const int base = threadIdx.x * kScanPer;
   uint32_t v[kScanPer], s = 0;
 #pragma unroll
-  for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < nparts ? d.part[base + k] : 0u; s += v[k]; }
+  for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < nparts ? part[base + k] : 0u; s += v[k]; }
   uint32_t tot;
   uint32_t ex = block_exclusive_scan(s, &tot);
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
-    if (base + k < nparts) d.part[base + k] = ex;
+    if (base + k < nparts) part[base + k] = ex;
     ex += v[k];
   }
   if (threadIdx.x == 0) {
-    d.ctrl->n_new = tot;
-    d.ctrl->n_born = tot;
-    d.off[d.nbins] = tot;
+    *off_total = tot;
+    if (total_a) *total_a = tot;
+    if (total_b) *total_b = tot;
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Dev d) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ N, long long n,
+                                                            const uint32_t* __restrict__ part,
+                                                            uint32_t* __restrict__ off) {
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
   uint32_t v[kScanPer], s = 0;
 #pragma unroll
-  for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < d.nbins ? d.N[base + k] : 0u; s += v[k]; }
-  uint32_t ex = block_exclusive_scan(s, nullptr) + d.part[blockIdx.x];
+  for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < n ? N[base + k] : 0u; s += v[k]; }
+  uint32_t ex = block_exclusive_scan(s, nullptr) + part[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
-    if (base + k < d.nbins) d.off[base + k] = ex;
+    if (base + k < n) off[base + k] = ex;
     ex += v[k];
   }
 }
@@ -725,16 +741,21 @@ cudaError_t launch_init_tables(const Dev& d, const double* src_T, int init_rho, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_birth_and_scan(const Dev& d, cudaStream_t s) {
-  k_birth<<<grid_for(d.nbins, 256), 256, 0, s>>>(d);
-  const int nparts = (d.nbins + kScanTile - 1) / kScanTile;
-  k_scan_reduce<<<nparts, kScanThreads, 0, s>>>(d);
-  k_scan_partials<<<1, kScanThreads, 0, s>>>(d, nparts);
-  k_scan_apply<<<nparts, kScanThreads, 0, s>>>(d);
+int scan_parts(long long n) { return (int)((n + kScanTile - 1) / kScanTile); }
+
+cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t* off,
+                        unsigned long long* total_a, unsigned long long* total_b, cudaStream_t s) {
+  const int nparts = scan_parts(n);
+  if (nparts > 0) k_scan_reduce<<<nparts, kScanThreads, 0, s>>>(N, n, part);
+  k_scan_partials<<<1, kScanThreads, 0, s>>>(part, nparts, off + n, total_a, total_b);
+  if (nparts > 0) k_scan_apply<<<nparts, kScanThreads, 0, s>>>(N, n, part, off);
   return cudaGetLastError();
 }
 
-int scan_parts(int nbins) { return (nbins + kScanTile - 1) / kScanTile; }
+cudaError_t launch_birth_and_scan(const Dev& d, cudaStream_t s) {
+  k_birth<<<grid_for(d.nbins, 256), 256, 0, s>>>(d);
+  return launch_scan(d.N, d.nbins, d.part, d.off, &d.ctrl->n_new, &d.ctrl->n_born, s);
+}
 
 cudaError_t launch_wave(const Dev& d, cudaStream_t s) {
   k_wave<<<grid_for((long long)d.nface * d.G, 256), 256, 0, s>>>(d);
@@ -757,9 +778,18 @@ cudaError_t launch_si(const Dev& d, cudaStream_t s) {
   long long maxb = (long long)sms * g_si_blocks[nc];
   int blocks = (int)(want < maxb ? want : maxb);
   if (blocks < 1) blocks = 1;
-  Dev dd = d;
-  void* args[] = {&dd};
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, 0, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (nc) return cudaLaunchKernelEx(&cfg, k_si<2>, d);
+  return cudaLaunchKernelEx(&cfg, k_si<1>, d);
 }
 
 cudaError_t launch_end_step(const Dev& d, cudaStream_t s) {

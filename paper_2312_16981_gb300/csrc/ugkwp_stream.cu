@@ -323,21 +323,271 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
   }
 }
 
-static int g_stream_blocks[3] = {0, 0, 0};
+// Mixed precision (FP32 particle state and arithmetic, FP64 tallies): the
+// same algorithm as k_stream64 with positions held relative to the cell
+// (0 <= xi <= dx) and FP32 uniforms from the same Philox words.  A survivor costs 28 B read and 28 B written in 1D.
+template <int DIM>
+__global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
+  const long long n_surv = (long long)ctrl->n_part[cur];
+  const long long n_tot = n_surv + (long long)ctrl->n_new;
+  const uint32_t step = (uint32_t)ctrl->step;
+  const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
+  const float dxf = (float)d.dx, dyf = (float)d.dy, vf = (float)d.v, dtf = (float)d.dt;
+  const float inv_rate = (float)(d.eps * d.eps / d.c);
+  const float capf = d.sig_cap > 0.0 ? (float)d.sig_cap : INFINITY;
+  const float spf = (float)d.sig_p;
+  const float* __restrict__ in_x = d.fx[cur];
+  const float* __restrict__ in_y = d.fy[cur];
+  const float* __restrict__ in_ox = d.fox[cur];
+  const float* __restrict__ in_oy = d.foy[cur];
+  const float* __restrict__ in_nu = d.fnu[cur];
+  const float* __restrict__ in_w = d.fw[cur];
+  const unsigned long long* __restrict__ in_id = d.pid[cur];
+  const uint32_t* __restrict__ in_key = d.pkey[cur];
+  __shared__ unsigned long long s_base;
+
+  unsigned long long c_seg = 0, c_abs = 0, c_esc = 0, c_surv = 0, c_rem = 0;
+  const long long ntiles = (n_tot + kStreamThreads - 1) / kStreamThreads;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long i = t * kStreamThreads + threadIdx.x;
+    const bool valid = i < n_tot;
+    float xi = 0.f, eta = 0.f, ox = 0.f, oy = 0.f, nu = 0.f, w = 0.f;
+    unsigned long long id = 0ull;
+    int cx = 0, cy = 0, g = 0, gside = -1;
+    bool newborn = false;
+    DrawsF rng;
+    rng.init(0ull, step, 0u);
+    if (valid) {
+      if (i < n_surv) {
+        xi = in_x[i];
+        ox = in_ox[i];
+        if (DIM == 2) { eta = in_y[i]; oy = in_oy[i]; }
+        nu = in_nu[i];
+        w = in_w[i];
+        id = in_id[i];
+        const uint32_t key = in_key[i];
+        const int cell = (int)(key / (uint32_t)G);
+        g = (int)(key - (uint32_t)cell * (uint32_t)G);
+        cx = cell % nx;
+        cy = cell / nx;
+        rng.init(id, step, 0u);
+      } else {
+        newborn = true;
+        const uint32_t j = (uint32_t)(i - n_surv);
+        const int bin = find_bin(d.off, d.nbins, j);
+        const uint32_t k = j - __ldg(d.off + bin);
+        id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
+             (unsigned long long)k;
+        rng.init(id, step, 0u);
+        const int cb = bin / G;
+        g = bin - cb * G;
+        if (cb < d.ncell) {
+          cx = cb % nx;
+          cy = cb / nx;
+          xi = rng.next(d.key0, d.key1) * dxf;
+          if (DIM == 2) eta = rng.next(d.key0, d.key1) * dyf;
+          if (DIM == 1) {
+            ox = 2.0f * rng.next(d.key0, d.key1) - 1.0f;
+          } else {
+            const float muz = 2.0f * rng.next(d.key0, d.key1) - 1.0f;
+            const float ph = rng.next(d.key0, d.key1);
+            float sp, cp;
+            sincospif(2.0f * ph, &sp, &cp);
+            const float s = sqrtf(fmaxf(0.0f, 1.0f - muz * muz));
+            ox = s * cp;
+            oy = s * sp;
+          }
+        } else {
+          const int side = cb - d.ncell;
+          const float u = rng.next(d.key0, d.key1);
+          const float m = sqrtf(rng.next(d.key0, d.key1));
+          const float dd = u * vf * m * dtf;
+          cx = side == 0 ? -1 : nx;
+          xi = side == 0 ? dxf - dd : dd;
+          ox = side == 0 ? m : -m;
+          gside = side;
+        }
+        if (!d.grey)
+          nu = sample_nu_f((float)d.nu_edges[g], (float)d.nu_edges[g + 1], __ldg(d.khat_f + bin),
+                           rng.next(d.key0, d.key1));
+        w = __ldg(d.omega_f + bin);
+      }
+    }
+    const int cell0 = gside >= 0 ? cx : cy * nx + cx;
+
+    // ---- streaming
+    int fate = FATE_REMOVED, nseg = 0, eside = -1;
+    float t_tra = 0.0f;
+    if (valid) {
+      const float nup = d.grey ? 1.0f : pow_fast_f(nu, spf);
+      float t_rem;
+      bool collided;
+      if (newborn) {
+        t_rem = dtf;
+        collided = false;
+      } else {
+        const UPair u = rng.next2(d.key0, d.key1);
+        const float sig = fminf(__ldg(d.sT_f + cy * nx + cx) * nup, capf);
+        const float tc = neg_log_u(u) * inv_rate / sig;
+        collided = tc < dtf;
+        t_rem = collided ? tc : dtf;
+      }
+      bool ghost = gside >= 0;
+      const float ivx = ox != 0.0f ? __frcp_rn(vf * fabsf(ox)) : 0.0f;
+      const float ivy = (DIM == 2 && oy != 0.0f) ? __frcp_rn(vf * fabsf(oy)) : 0.0f;
+      for (int guard = 0;; ++guard) {
+        if (guard >= 4096) {
+          atomicOr(&ctrl->status, ST_NONFINITE);
+          fate = FATE_REMOVED;
+          break;
+        }
+        float tx = INFINITY, ty = INFINITY;
+        if (ox > 0.0f) tx = fmaxf(dxf - xi, 0.0f) * ivx;
+        else if (ox < 0.0f) tx = fmaxf(xi, 0.0f) * ivx;
+        if (DIM == 2) {
+          if (oy > 0.0f) ty = fmaxf(dyf - eta, 0.0f) * ivy;
+          else if (oy < 0.0f) ty = fmaxf(eta, 0.0f) * ivy;
+        }
+        const int axis = (tx <= ty) ? 0 : 1;
+        const float tf = axis == 0 ? tx : ty;
+        if (tf < t_rem) {
+          ++nseg;
+          t_tra += tf;
+          t_rem -= tf;
+          int dir;
+          if (axis == 0) {
+            dir = ox > 0.0f ? 1 : -1;
+            xi = dir > 0 ? dxf : 0.0f;
+            if (DIM == 2) eta = fminf(fmaxf(fmaf(vf * oy, tf, eta), 0.0f), dyf);
+          } else {
+            dir = oy > 0.0f ? 1 : -1;
+            eta = dir > 0 ? dyf : 0.0f;
+            xi = fminf(fmaxf(fmaf(vf * ox, tf, xi), 0.0f), dxf);
+          }
+          const int nxc = cx + (axis == 0 ? dir : 0), nyc = cy + (axis == 1 ? dir : 0);
+          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny) {
+            const int side = axis * 2 + (dir > 0 ? 1 : 0);
+            if (d.bc[side] == BC_REFLECT) {
+              if (axis == 0) ox = -ox; else oy = -oy;
+              continue;
+            }
+            fate = FATE_ESCAPED;
+            eside = side;
+            break;
+          }
+          ghost = false;
+          if (axis == 0) xi = dir > 0 ? 0.0f : dxf;
+          else eta = dir > 0 ? 0.0f : dyf;
+          cx = nxc;
+          cy = nyc;
+          const UPair u = rng.next2(d.key0, d.key1);
+          const float sig = fminf(__ldg(d.sT_f + cy * nx + cx) * nup, capf);
+          const float tc = neg_log_u(u) * inv_rate / sig;
+          const float avail = dtf - t_tra;
+          collided = tc < avail;
+          t_rem = collided ? tc : avail;
+          continue;
+        }
+        ++nseg;
+        xi = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
+        if (DIM == 2) eta = fminf(fmaxf(fmaf(vf * oy, t_rem, eta), 0.0f), dyf);
+        t_tra += t_rem;
+        fate = ghost ? FATE_REMOVED : (collided ? FATE_ABSORBED : FATE_SURVIVED);
+        break;
+      }
+    }
+    const int cell = cy * nx + cx;
+
+    // ---- tallies (FP64)
+    const int lane = threadIdx.x & 31;
+    const double wd = (double)w;
+    warp_run_add(d.E_surv, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wd);
+    if (valid && fate != FATE_REMOVED) {
+      const bool start_in = gside < 0;
+      const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
+      if (!(start_in && end_in && cell0 == cell)) {
+        if (start_in) atomicAdd(d.W + cell0 * G + g, -wd);
+        if (end_in) atomicAdd(d.W + cell * G + g, wd);
+      }
+      if (!start_in) atomicAdd(d.inflow + gside * G + g, wd);
+      if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, wd);
+    }
+    if (valid) {
+      c_seg += (unsigned long long)nseg;
+      c_abs += fate == FATE_ABSORBED;
+      c_esc += fate == FATE_ESCAPED;
+      c_surv += fate == FATE_SURVIVED;
+      c_rem += fate == FATE_REMOVED;
+      if (d.rec && i < d.rec_cap) {
+        RecordOut& r = d.rec[i];
+        r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = (fate == FATE_REMOVED && gside >= 0) ? cx : cell;
+        r.grp = g; r.nseg = nseg; r.pad = 0;
+        r.x = cx * d.dx + (double)xi;
+        r.y = DIM == 2 ? cy * d.dy + (double)eta : 0.0;
+        r.ox = ox; r.oy = oy; r.nu = nu; r.w = wd; r.t_end = t_tra;
+      }
+    }
+
+    // ---- compaction
+    const bool keep = valid && fate == FATE_SURVIVED;
+    unsigned cnt;
+    const unsigned rank = block_rank(keep, &cnt);
+    if (threadIdx.x == 0) s_base = cnt ? atomicAdd(&ctrl->n_out, (unsigned long long)cnt) : 0ull;
+    __syncthreads();
+    if (keep) {
+      const unsigned long long o = s_base + rank;
+      if (o < (unsigned long long)d.capacity) {
+        d.fx[nxb][o] = xi;
+        d.fox[nxb][o] = ox;
+        if (DIM == 2) { d.fy[nxb][o] = eta; d.foy[nxb][o] = oy; }
+        d.fnu[nxb][o] = nu;
+        d.fw[nxb][o] = w;
+        d.pid[nxb][o] = id;
+        d.pkey[nxb][o] = (uint32_t)(cell * G + g);
+      } else {
+        atomicOr(&ctrl->status, ST_CAPACITY);
+      }
+    }
+    __syncthreads();
+  }
+  c_seg = warp_sum_u64(c_seg);
+  c_abs = warp_sum_u64(c_abs);
+  c_esc = warp_sum_u64(c_esc);
+  c_surv = warp_sum_u64(c_surv);
+  c_rem = warp_sum_u64(c_rem);
+  if ((threadIdx.x & 31) == 0) {
+    if (c_seg) atomicAdd(&ctrl->n_segments, c_seg);
+    if (c_abs) atomicAdd(&ctrl->n_absorbed, c_abs);
+    if (c_esc) atomicAdd(&ctrl->n_escaped, c_esc);
+    if (c_surv) atomicAdd(&ctrl->n_survived, c_surv);
+    if (c_rem) atomicAdd(&ctrl->n_removed, c_rem);
+  }
+}
+
+static int g_stream_blocks[2][3] = {{0, 0, 0}, {0, 0, 0}};
 
 cudaError_t launch_stream(const Dev& d, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = d.dim == 2 ? (const void*)k_stream64<2> : (const void*)k_stream64<1>;
-  int& per = g_stream_blocks[d.dim];
+  const int mixed = d.precision == 1;
+  const void* fn = mixed ? (d.dim == 2 ? (const void*)k_stream32<2> : (const void*)k_stream32<1>)
+                         : (d.dim == 2 ? (const void*)k_stream64<2> : (const void*)k_stream64<1>);
+  int& per = g_stream_blocks[mixed][d.dim];
   if (!per) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kStreamThreads, 0);
     if (per < 1) per = 1;
   }
   const int blocks = sms * per;
-  if (d.dim == 2) k_stream64<2><<<blocks, kStreamThreads, 0, s>>>(d);
-  else k_stream64<1><<<blocks, kStreamThreads, 0, s>>>(d);
+  if (mixed) {
+    if (d.dim == 2) k_stream32<2><<<blocks, kStreamThreads, 0, s>>>(d);
+    else k_stream32<1><<<blocks, kStreamThreads, 0, s>>>(d);
+  } else {
+    if (d.dim == 2) k_stream64<2><<<blocks, kStreamThreads, 0, s>>>(d);
+    else k_stream64<1><<<blocks, kStreamThreads, 0, s>>>(d);
+  }
   return cudaGetLastError();
 }
 

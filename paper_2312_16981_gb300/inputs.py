@@ -180,16 +180,18 @@ def small_checkerboard(n: int = 16, G: int = 4, omega_ref: float = 2e-6, seed: i
 
 
 def synthetic_state(p: Problem, n_particles: int, seed: int = 1, front: float = 0.2,
-                    step: int = 0) -> dict:
+                    step: int = 0, wave_fraction: float = 0.02) -> dict:
     """A seeded mid-run state shaped like a Marshak front, for full-size runs
     that both the CUDA path and the oracle start from.
 
     Pure input generation: a temperature profile falling from 1 to T0 over
-    `front` of the slab, a radiation field T^4 spread over the groups by a
-    log-normal bump near nu ~ 3T, and n_particles particles placed in
-    (cell, group) bins in proportion to that field, uniform in the cell,
-    isotropic, with frequency uniform in the group and weight
-    omega_ref * U(0.5, 1.5).  1D slabs only.
+    `front` of the slab; a spectral shape T^4 x (log-normal bump near
+    nu ~ 3T); n_particles particles placed in (cell, group) bins in
+    proportion to that shape, uniform in the cell, isotropic, with frequency
+    uniform in the group and weight omega_ref * U(0.5, 1.5); the wave part
+    rho_h = wave_fraction x the shape, and rho = rho_h + the particles' energy
+    per volume (so most of the radiation is carried by particles, as in a
+    running slab).  1D slabs only.
     """
     assert p.dim == 1
     rng = np.random.Generator(np.random.Philox(seed))
@@ -203,8 +205,8 @@ def synthetic_state(p: Problem, n_particles: int, seed: int = 1, front: float = 
         lnu = np.log(np.sqrt(p.nu_edges[:-1] * p.nu_edges[1:]))
         shape = np.exp(-0.5 * ((lnu[None, :] - np.log(3.0 * T[:, None])) / 0.7) ** 2)
         shape /= shape.sum(1, keepdims=True)
-    rho = (T[:, None] ** 4) * shape
-    prob = rho.reshape(-1) / rho.sum()
+    field = ((T[:, None] ** 4) * shape).reshape(-1)
+    prob = field / field.sum()
     bins = rng.choice(p.nx * p.G, size=n_particles, p=prob)
     bins.sort()
     cell = (bins // p.G).astype(np.int32)
@@ -223,5 +225,6 @@ def synthetic_state(p: Problem, n_particles: int, seed: int = 1, front: float = 
     pid = (np.uint64(step) << np.uint64(44)) | (bins.astype(np.uint64) << np.uint64(20)) | k.astype(np.uint64)
     parts = dict(x=x, y=np.zeros(n_particles), ox=mu, oy=np.zeros(n_particles), nu=nu, w=w,
                  id=pid, cell=cell, grp=grp)
-    rho = rho.reshape(-1)
-    return dict(T=T, rho=rho, rho_h=0.5 * rho, particles=parts, step=step + 1)
+    rho_p = np.bincount(bins, weights=w, minlength=p.nx * p.G) / p.dx
+    rho_h = wave_fraction * field
+    return dict(T=T, rho=rho_h + rho_p, rho_h=rho_h, particles=parts, step=step + 1)

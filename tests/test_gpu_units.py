@@ -71,3 +71,24 @@ def test_sampler_matches_bisection(B, nlo, nhi, T):
         want = O.sample_nu(nlo, nhi, T, e)
         # the inverse is ill-conditioned only where the clamped density vanishes
         assert abs(v - want) <= 1e-12 * nhi + 2e-8 * (nhi - nlo) * (e < 1e-6 or e > 1 - 1e-6)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 4095, 4096, 4097, 100_003, 1 << 24])
+def test_exclusive_scan_bit_exact(B, n):
+    rng = np.random.Generator(np.random.Philox(n + 1))
+    hi = max(1, min(1 << 12, (1 << 32) // max(n, 1) - 1))
+    counts = rng.integers(0, hi, size=n, dtype=np.int64)
+    counts[rng.random(n) < 0.3] = 0          # empty bins, as in thick cells
+    got = B.exclusive_scan(torch.from_numpy(counts).to(torch.int32).cuda()).cpu().numpy()
+    want = np.concatenate([[0], np.cumsum(counts)])
+    np.testing.assert_array_equal(got, want)
+
+
+def test_exclusive_scan_rejects_small_scratch(B):
+    import ctypes
+    c = torch.zeros(10000, dtype=torch.int32, device="cuda")
+    out = torch.zeros(10001, dtype=torch.int32, device="cuda")
+    scratch = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    code = B.load().ugkwp_exclusive_scan(ctypes.c_void_p(c.data_ptr()), 10000, ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(scratch.data_ptr()), 4, None)
+    assert code == -7
