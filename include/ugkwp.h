@@ -204,6 +204,27 @@ int ugkwp_coefs(const double* d_x, int64_t n, double* d_out, void* stream);
 int ugkwp_exclusive_scan(const uint32_t* d_counts, int64_t n, uint32_t* d_offsets, void* d_scratch,
                          size_t scratch_bytes, void* stream);
 
+/* The same exclusive scan, allocating nothing: for callers that cannot get
+ * device memory -- a program whose GPU memory is all held by its own pool
+ * allocator, a plug-in whose host framework forbids cudaMalloc/cudaFree
+ * inside its time step (they can synchronise the whole device), or code
+ * that only holds pointers to buffers allocated by someone else.  It has no
+ * counterpart in the paper.  The scratch (per-block partial sums) is a
+ * fixed 16 KiB device array compiled into the library, resident on every GPU
+ * that loads the library until the process exits; n is limited to
+ * UGKWP_NOALLOC_SCAN_MAX_N and larger n is rejected with UGKWP_ERR_ARG
+ * (message from ugkwp_last_error(NULL)).  The caller still passes the
+ * counts and the n + 1 offsets (DEVICE pointers).  The first call on a
+ * device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array, so calls that overlap on the GPU (on
+ * different streams, or from different host threads) race and must not be
+ * issued; each call overwrites the partials it reads, so nothing is left to
+ * clear between calls.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+#define UGKWP_NOALLOC_SCAN_MAX_N (1ll << 24)
+int ugkwp_exclusive_scan_noalloc(const uint32_t* d_counts, int64_t n, uint32_t* d_offsets, void* stream);
+
 /* Frequency of a particle from uniforms d_eta [n] for group [nlo, nhi] at
  * temperature T (App. A, linear-frequency sampling) into d_nu [n]. */
 int ugkwp_sample_nu(const double* d_eta, int64_t n, double nlo, double nhi, double T, double* d_nu,

@@ -96,6 +96,7 @@ FUNCTIONS = {
                                   C.c_void_p, C.c_void_p]),
     "ugkwp_exclusive_scan": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
+    "ugkwp_exclusive_scan_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
 

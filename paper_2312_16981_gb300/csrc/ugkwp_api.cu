@@ -198,6 +198,8 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
 
 }  // namespace
 
+void ugkwp::set_global_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 extern "C" {
 
 int ugkwp_workspace_size(const ugkwp_problem* p, size_t* bytes) {

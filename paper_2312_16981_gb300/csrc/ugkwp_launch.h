@@ -15,6 +15,9 @@ cudaError_t launch_stream(const Dev& d, cudaStream_t s);
 cudaError_t launch_si(const Dev& d, cudaStream_t s);
 cudaError_t launch_end_step(const Dev& d, cudaStream_t s);
 
+// message returned by ugkwp_last_error(NULL)
+void set_global_error(const char* msg);
+
 cudaError_t launch_unit_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                                long long n, cudaStream_t s);
 cudaError_t launch_unit_planck(const double* T, long long n, const double* nu, int G, double* b,
