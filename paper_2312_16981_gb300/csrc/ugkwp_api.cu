@@ -97,6 +97,8 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   const long long nc = ncell_of(p), G = p->G, ncg = nc * G, nb = (nc + 4) * G;
   const long long nf = nface_of(p), P = p->particle_capacity;
   d.nu_edges = cv.take<double>(G + 1);
+  d.nu_edges_f = cv.take<float>(G + 1);
+  d.nu_pow = cv.take<double>(3 * G);
   d.sigma0 = cv.take<double>(nc);
   d.cv = cv.take<double>(nc);
   d.src = p->src_T ? cv.take<double>(ncg) : nullptr;

@@ -176,6 +176,8 @@ struct Dev {
   float* sT_f;      // [ncell] sigma0 T^q
   float* omega_f;   // [nbins]
   float* khat_f;    // [nbins]
+  float* nu_edges_f;       // [G+1] group edges in FP32
+  const double* nu_pow;    // [3*G] nu^p at the lower edge, midpoint and upper edge of each group
   void* particles_begin;   // first particle buffer (start of the part left uninitialised)
   // control block and optional records
   struct Ctrl* ctrl;
@@ -225,13 +227,13 @@ __device__ __forceinline__ double sigma_T(const Dev& d, int c, double T) {
   return d.sigma0[c] * pow_fast(T, d.sig_q);
 }
 
-// Simpson group opacity (Sec. 3: edges and midpoint, weights 1-4-1).
+// Simpson group opacity (Sec. 3: edges and midpoint, weights 1-4-1), with
+// nu^p at the three points taken from a table built once.
 __device__ __forceinline__ double sigma_group(const Dev& d, double sT, int g) {
   if (d.grey) return cap_sigma(d, sT);
-  const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b);
-  const double sa = cap_sigma(d, sT * pow_fast(a, d.sig_p));
-  const double sm = cap_sigma(d, sT * pow_fast(m, d.sig_p));
-  const double sb = cap_sigma(d, sT * pow_fast(b, d.sig_p));
+  const double sa = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g));
+  const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1));
+  const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2));
   return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
 }
 

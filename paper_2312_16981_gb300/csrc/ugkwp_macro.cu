@@ -21,6 +21,20 @@ __device__ void phi_dphi_cell(const Dev& d, double T, int g, double* phi, double
   if (dphi) *dphi = ac * T3 * planck_dfraction(b, lo, hi);
 }
 
+__global__ void k_init_pow(Dev d) {
+  // nu^p at the Simpson points and FP32 edges; before anything uses sigma_group
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int g = tid; g < d.G; g += stride) {
+    const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b);
+    double* np = const_cast<double*>(d.nu_pow);
+    np[3 * g] = d.grey ? 1.0 : pow_fast(a, d.sig_p);
+    np[3 * g + 1] = d.grey ? 1.0 : pow_fast(m, d.sig_p);
+    np[3 * g + 2] = d.grey ? 1.0 : pow_fast(b, d.sig_p);
+  }
+  for (int g = tid; g <= d.G; g += stride)
+    if (d.nu_edges_f) d.nu_edges_f[g] = (float)d.nu_edges[g];
+}
+
 __global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const int n = d.ncell * d.G;
@@ -737,6 +751,7 @@ static int grid_for(long long n, int threads, int cap = 152 * 16) {
 }
 
 cudaError_t launch_init_tables(const Dev& d, const double* src_T, int init_rho, cudaStream_t s) {
+  k_init_pow<<<1, 64, 0, s>>>(d);
   k_init_tables<<<grid_for((long long)d.ncell * d.G, 256), 256, 0, s>>>(d, src_T, init_rho);
   return cudaGetLastError();
 }
@@ -753,34 +768,40 @@ cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t
 }
 
 cudaError_t launch_birth_and_scan(const Dev& d, cudaStream_t s) {
-  k_birth<<<grid_for(d.nbins, 256), 256, 0, s>>>(d);
+  k_birth<<<grid_for(d.nbins, 64), 64, 0, s>>>(d);
   return launch_scan(d.N, d.nbins, d.part, d.off, &d.ctrl->n_new, &d.ctrl->n_born, s);
 }
 
 cudaError_t launch_wave(const Dev& d, cudaStream_t s) {
-  k_wave<<<grid_for((long long)d.nface * d.G, 256), 256, 0, s>>>(d);
+  k_wave<<<grid_for((long long)d.nface * d.G, 64), 64, 0, s>>>(d);
   return cudaGetLastError();
 }
 
-static int g_si_blocks[2] = {0, 0};
+static int g_si_blocks[2][2] = {{0, 0}, {0, 0}};
 
+// One warp per cell.  On GB300 the FP64 pipe of an SM is the limit of this
+// kernel, so a small grid is spread one warp per block over all SMs; a large
+// grid uses 8-warp blocks (fewer arrivals at the grid barrier).
 cudaError_t launch_si(const Dev& d, cudaStream_t s) {
   const int nc = d.G > 32 ? 1 : 0;
   void* fn = nc ? (void*)k_si<2> : (void*)k_si<1>;
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (!g_si_blocks[nc]) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0);
-    g_si_blocks[nc] = per > 0 ? per : 1;
+  const int small = d.ncell <= 8 * sms;
+  const int threads = small ? 32 : 256;
+  int& per = g_si_blocks[nc][small];
+  if (!per) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+    if (per < 1) per = 1;
   }
-  long long want = ((long long)d.ncell + 7) / 8;   // 8 warps (cells) per block
-  long long maxb = (long long)sms * g_si_blocks[nc];
+  const long long want = ((long long)d.ncell * 32 + threads - 1) / threads;
+  const long long maxb = (long long)sms * per;
   int blocks = (int)(want < maxb ? want : maxb);
   if (blocks < 1) blocks = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

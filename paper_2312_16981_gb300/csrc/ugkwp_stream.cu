@@ -50,32 +50,69 @@ __device__ __forceinline__ void warp_run_add(double* base, int key, double v) {
   if (tail && key >= 0) atomicAdd(base + key, v);
 }
 
-// exclusive rank of `flag` within the block and the block's count
-__device__ __forceinline__ unsigned block_rank(bool flag, unsigned* total) {
-  __shared__ unsigned s_cnt[32];
-  __shared__ unsigned s_tot;
+// The same run aggregation for FP32 weights without FP64 arithmetic in the
+// warp: an error-free two-sum (Knuth) keeps each run's sum as hi + lo in
+// FP32 (about 48 bits), and only the tail lane converts it for the FP64
+// atomic.  On GB300 an FP64 warp instruction costs tens of cycles of an SM
+// sub-partition, so the double-precision version limited the mixed kernel.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void warp_run_add_f(double* base, int key, float v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(full, head);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  float hi = v, lo = 0.0f;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float th = __shfl_up_sync(full, hi, o);
+    const float tl = __shfl_up_sync(full, lo, o);
+    if (lane - o >= start) {
+      float s, e;
+      two_sum(hi, th, s, e);
+      hi = s;
+      lo = lo + tl + e;
+    }
+  }
+  const int nxt = __shfl_down_sync(full, key, 1);
+  const bool tail = lane == 31 || nxt != key;
+  if (tail && key >= 0) atomicAdd(base + key, (double)hi + (double)lo);
+}
+
+// Block compaction: exclusive rank of `flag` within the block plus the start
+// of the block's slots in the output buffer, reserved with one atomic by warp
+// 0.  Two barriers per tile; the shared slots are double-buffered by tile
+// parity, so a warp still reading this tile's values never sees the next
+// tile's writes (those happen after the next tile's first barrier).
+__device__ __forceinline__ unsigned long long block_slots(bool flag, int parity, unsigned long long* counter,
+                                                          unsigned* rank) {
+  __shared__ unsigned s_cnt[2][32];
+  __shared__ unsigned long long s_base[2];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned b = __ballot_sync(full, flag);
-  const unsigned r = __popc(b & ((1u << lane) - 1u));
-  if (lane == 0) s_cnt[wid] = __popc(b);
+  if (lane == 0) s_cnt[parity][wid] = __popc(b);
   __syncthreads();
   if (wid == 0) {
-    const unsigned x = lane < nw ? s_cnt[lane] : 0u;
+    const unsigned x = lane < nw ? s_cnt[parity][lane] : 0u;
     unsigned inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned t = __shfl_up_sync(full, inc, o);
       if (lane >= o) inc += t;
     }
-    if (lane < nw) s_cnt[lane] = inc - x;
-    if (lane == nw - 1) s_tot = inc;
+    if (lane < nw) s_cnt[parity][lane] = inc - x;
+    if (lane == nw - 1) s_base[parity] = inc ? atomicAdd(counter, (unsigned long long)inc) : 0ull;
   }
   __syncthreads();
-  const unsigned res = s_cnt[wid] + r;
-  *total = s_tot;
-  __syncthreads();
-  return res;
+  *rank = s_cnt[parity][wid] + __popc(b & ((1u << lane) - 1u));
+  return s_base[parity];
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -101,11 +138,11 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
   const double* __restrict__ in_w = d.pw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-  __shared__ unsigned long long s_base;
 
   unsigned long long c_seg = 0, c_abs = 0, c_esc = 0, c_surv = 0, c_rem = 0;
   const long long ntiles = (n_tot + kStreamThreads - 1) / kStreamThreads;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
     const long long i = t * kStreamThreads + threadIdx.x;
     const bool valid = i < n_tot;
     double x = 0.0, y = 0.0, ox = 0.0, oy = 0.0, nu = 0.0, w = 0.0;
@@ -289,12 +326,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
 
     // ---- compaction of the collisionless survivors
     const bool keep = valid && fate == FATE_SURVIVED;
-    unsigned cnt;
-    const unsigned rank = block_rank(keep, &cnt);
-    if (threadIdx.x == 0) s_base = cnt ? atomicAdd(&ctrl->n_out, (unsigned long long)cnt) : 0ull;
-    __syncthreads();
+    unsigned rank;
+    const unsigned long long base = block_slots(keep, tile_iter & 1, &ctrl->n_out, &rank);
     if (keep) {
-      const unsigned long long o = s_base + rank;
+      const unsigned long long o = base + rank;
       if (o < (unsigned long long)d.capacity) {
         d.px[nxb][o] = x;
         d.pox[nxb][o] = ox;
@@ -307,7 +342,6 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
         atomicOr(&ctrl->status, ST_CAPACITY);
       }
     }
-    __syncthreads();
   }
   c_seg = warp_sum_u64(c_seg);
   c_abs = warp_sum_u64(c_abs);
@@ -346,11 +380,11 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
   const float* __restrict__ in_w = d.fw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-  __shared__ unsigned long long s_base;
 
   unsigned long long c_seg = 0, c_abs = 0, c_esc = 0, c_surv = 0, c_rem = 0;
   const long long ntiles = (n_tot + kStreamThreads - 1) / kStreamThreads;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
     const long long i = t * kStreamThreads + threadIdx.x;
     const bool valid = i < n_tot;
     float xi = 0.f, eta = 0.f, ox = 0.f, oy = 0.f, nu = 0.f, w = 0.f;
@@ -410,7 +444,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
           gside = side;
         }
         if (!d.grey)
-          nu = sample_nu_f((float)d.nu_edges[g], (float)d.nu_edges[g + 1], __ldg(d.khat_f + bin),
+          nu = sample_nu_f(__ldg(d.nu_edges_f + g), __ldg(d.nu_edges_f + g + 1), __ldg(d.khat_f + bin),
                            rng.next(d.key0, d.key1));
         w = __ldg(d.omega_f + bin);
       }
@@ -502,15 +536,13 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
 
     // ---- tallies (FP64)
     const int lane = threadIdx.x & 31;
-    const double wd = (double)w;
-    warp_run_add(d.E_surv, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wd);
-    if (valid && fate != FATE_REMOVED) {
+    warp_run_add_f(d.E_surv, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, w);
+    if (valid && fate != FATE_REMOVED && (gside >= 0 || fate == FATE_ESCAPED || cell0 != cell)) {
+      const double wd = (double)w;
       const bool start_in = gside < 0;
       const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
-      if (!(start_in && end_in && cell0 == cell)) {
-        if (start_in) atomicAdd(d.W + cell0 * G + g, -wd);
-        if (end_in) atomicAdd(d.W + cell * G + g, wd);
-      }
+      if (start_in) atomicAdd(d.W + cell0 * G + g, -wd);
+      if (end_in) atomicAdd(d.W + cell * G + g, wd);
       if (!start_in) atomicAdd(d.inflow + gside * G + g, wd);
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, wd);
     }
@@ -526,18 +558,16 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
         r.grp = g; r.nseg = nseg; r.pad = 0;
         r.x = cx * d.dx + (double)xi;
         r.y = DIM == 2 ? cy * d.dy + (double)eta : 0.0;
-        r.ox = ox; r.oy = oy; r.nu = nu; r.w = wd; r.t_end = t_tra;
+        r.ox = ox; r.oy = oy; r.nu = nu; r.w = (double)w; r.t_end = t_tra;
       }
     }
 
     // ---- compaction
     const bool keep = valid && fate == FATE_SURVIVED;
-    unsigned cnt;
-    const unsigned rank = block_rank(keep, &cnt);
-    if (threadIdx.x == 0) s_base = cnt ? atomicAdd(&ctrl->n_out, (unsigned long long)cnt) : 0ull;
-    __syncthreads();
+    unsigned rank;
+    const unsigned long long base = block_slots(keep, tile_iter & 1, &ctrl->n_out, &rank);
     if (keep) {
-      const unsigned long long o = s_base + rank;
+      const unsigned long long o = base + rank;
       if (o < (unsigned long long)d.capacity) {
         d.fx[nxb][o] = xi;
         d.fox[nxb][o] = ox;
@@ -550,7 +580,6 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
         atomicOr(&ctrl->status, ST_CAPACITY);
       }
     }
-    __syncthreads();
   }
   c_seg = warp_sum_u64(c_seg);
   c_abs = warp_sum_u64(c_abs);
