@@ -174,6 +174,30 @@ int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const d
  * that the next steps fill; records beyond cap are dropped. */
 int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap);
 
+/* ---- ensembles: independent problems advanced together ----
+ * Members share dim, precision and si_max_iters but may differ in every
+ * other field (cells, groups, opacities, boundaries, weights, seeds,
+ * instance numbers).  One ugkwp_step advances all of them with the same
+ * kernels as a single problem: one launch per phase over every member's
+ * bins, faces and cells, one persistent particle launch whose tiles run over
+ * all members' particles (so uneven members share the GPU), and one
+ * cooperative source iteration in which each member stops at its own
+ * convergence.  A member's results equal those of the same problem run
+ * alone (same identities and random streams, up to the summation order of
+ * FP64 atomics).  At most 4096 members; records are not available. */
+int ugkwp_workspace_size_ensemble(const ugkwp_problem* probs, int n, size_t* bytes);
+int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, size_t bytes, void* stream,
+                        ugkwp_handle** out);
+/* Per-member forms of ugkwp_tallies / ugkwp_get_state / ugkwp_set_state
+ * (the plain calls address member 0). */
+int ugkwp_tallies_member(ugkwp_handle* h, int member, ugkwp_tally_report* out, void* stream);
+int ugkwp_get_state_member(ugkwp_handle* h, int member, double* T, double* rho, double* rho_h,
+                           double* rho_p, ugkwp_particles_host* parts, int64_t cap, int64_t* n,
+                           void* stream);
+int ugkwp_set_state_member(ugkwp_handle* h, int member, const double* T, const double* rho,
+                           const double* rho_h, const ugkwp_particles_host* parts, int64_t n,
+                           int64_t step, void* stream);
+
 const char* ugkwp_last_error(const ugkwp_handle* h);
 void ugkwp_destroy(ugkwp_handle* h);
 

@@ -86,6 +86,14 @@ FUNCTIONS = {
     "ugkwp_set_state": (C.c_int, [C.c_void_p, _dp, _dp, _dp, C.c_void_p, C.c_int64, C.c_int64,
                                   C.c_void_p]),
     "ugkwp_set_records": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "ugkwp_workspace_size_ensemble": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
+    "ugkwp_init_ensemble": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                      C.POINTER(C.c_void_p)]),
+    "ugkwp_tallies_member": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "ugkwp_get_state_member": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, C.c_void_p, C.c_int64,
+                                         C.POINTER(C.c_int64), C.c_void_p]),
+    "ugkwp_set_state_member": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_void_p, C.c_int64,
+                                         C.c_int64, C.c_void_p]),
     "ugkwp_last_error": (C.c_char_p, [C.c_void_p]),
     "ugkwp_destroy": (None, [C.c_void_p]),
     "ugkwp_philox": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64, C.c_void_p]),
@@ -180,25 +188,28 @@ def workspace_bytes(p: Problem) -> int:
 
 
 class Simulation:
-    """One UGKWP problem resident on a GPU."""
+    """One UGKWP problem (or an ensemble of independent ones) resident on a GPU."""
 
-    def __init__(self, p: Problem, device: str = "cuda:0", rho0: Optional[np.ndarray] = None,
+    def __init__(self, p, device: str = "cuda:0", rho0: Optional[np.ndarray] = None,
                  stream=None):
         import torch
         L = load()
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the UGKWP library has no CPU path")
-        self.p = p
+        probs = list(p) if isinstance(p, (list, tuple)) else [p]
+        self.members = probs
+        self.p = probs[0]
         self.device = torch.device(device)
         self.stream = stream
-        hp = _HostProblem(p, rho0)
+        hps = [_HostProblem(q, rho0 if k == 0 else None) for k, q in enumerate(probs)]
+        arr = (CProblem * len(probs))(*[hp.s for hp in hps])
         n = C.c_size_t()
-        _check(L.ugkwp_workspace_size(C.byref(hp.s), C.byref(n)))
+        _check(L.ugkwp_workspace_size_ensemble(arr, len(probs), C.byref(n)))
         self.workspace = torch.empty(n.value, dtype=torch.uint8, device=self.device)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
-            _check(L.ugkwp_init(C.byref(hp.s), C.c_void_p(_ptr(self.workspace)), n.value,
-                                C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+            _check(L.ugkwp_init_ensemble(arr, len(probs), C.c_void_p(_ptr(self.workspace)), n.value,
+                                         C.c_void_p(_stream_ptr(stream)), C.byref(h)))
         self.h = h
         self._records = None
 
@@ -223,9 +234,10 @@ class Simulation:
         _check(load().ugkwp_step_timed(self.h, C.c_void_p(_stream_ptr(self.stream)), ms), self.h)
         return list(ms)
 
-    def tallies(self) -> Dict:
+    def tallies(self, member: int = 0) -> Dict:
         r = CTallyReport()
-        _check(load().ugkwp_tallies(self.h, C.byref(r), C.c_void_p(_stream_ptr(self.stream))), self.h)
+        _check(load().ugkwp_tallies_member(self.h, member, C.byref(r),
+                                           C.c_void_p(_stream_ptr(self.stream))), self.h)
         out = {k: getattr(r, k) for k, _ in CTallyReport._fields_[9:]}
         out["ptr"] = {k: getattr(r, k) for k, _ in CTallyReport._fields_[:9]}
         return out
@@ -241,8 +253,8 @@ class Simulation:
         off = r["ptr"][name] - _ptr(self.workspace)
         return self.workspace[off: off + 8 * n].view(torch.float64)
 
-    def get_state(self, cap: Optional[int] = None) -> Dict[str, np.ndarray]:
-        p = self.p
+    def get_state(self, cap: Optional[int] = None, member: int = 0) -> Dict[str, np.ndarray]:
+        p = self.members[member]
         T = np.zeros(p.ncell)
         rho = np.zeros(p.ncell * p.G)
         rho_h = np.zeros_like(rho)
@@ -250,9 +262,9 @@ class Simulation:
         n = C.c_int64()
         L = load()
         sp = C.c_void_p(_stream_ptr(self.stream))
-        _check(L.ugkwp_get_state(self.h, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
-                                 rho_h.ctypes.data_as(_dp), rho_p.ctypes.data_as(_dp), None, 0,
-                                 C.byref(n), sp), self.h)
+        _check(L.ugkwp_get_state_member(self.h, member, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
+                                        rho_h.ctypes.data_as(_dp), rho_p.ctypes.data_as(_dp), None, 0,
+                                        C.byref(n), sp), self.h)
         m = n.value if cap is None else min(cap, n.value)
         parts = {f: np.zeros(max(m, 1)) for f in ("x", "y", "ox", "oy", "nu", "w")}
         parts["id"] = np.zeros(max(m, 1), dtype=np.uint64)
@@ -263,12 +275,13 @@ class Simulation:
                             parts["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
                             parts["grp"].ctypes.data_as(C.POINTER(C.c_int32)))
         if m > 0:
-            _check(L.ugkwp_get_state(self.h, None, None, None, None, C.byref(cs), m, C.byref(n), sp), self.h)
+            _check(L.ugkwp_get_state_member(self.h, member, None, None, None, None, C.byref(cs), m,
+                                            C.byref(n), sp), self.h)
         parts = {k: v[:m] for k, v in parts.items()}
         return dict(T=T, rho=rho, rho_h=rho_h, rho_p=rho_p, particles=parts, n=n.value)
 
     def set_state(self, T, rho, rho_h, particles: Optional[Dict[str, np.ndarray]] = None,
-                  step: int = 0):
+                  step: int = 0, member: int = 0):
         L = load()
         T = np.ascontiguousarray(T, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -288,9 +301,9 @@ class Simulation:
                                 arrs["id"].ctypes.data_as(C.POINTER(C.c_uint64)),
                                 arrs["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
                                 arrs["grp"].ctypes.data_as(C.POINTER(C.c_int32)))
-        _check(L.ugkwp_set_state(self.h, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
-                                 rho_h.ctypes.data_as(_dp), None if cs is None else C.byref(cs), n,
-                                 int(step), C.c_void_p(_stream_ptr(self.stream))), self.h)
+        _check(L.ugkwp_set_state_member(self.h, member, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
+                                        rho_h.ctypes.data_as(_dp), None if cs is None else C.byref(cs), n,
+                                        int(step), C.c_void_p(_stream_ptr(self.stream))), self.h)
 
     def attach_records(self, cap: int):
         import torch

@@ -14,8 +14,11 @@ using ugkwp::Ctrl;
 using ugkwp::Dev;
 
 struct ugkwp_handle {
-  Dev d;
-  ugkwp_problem p;     // scalars; host pointers cleared after init
+  Dev d;                        // member 0 (what the single-problem calls address)
+  std::vector<Dev> members;     // every member's descriptor (host copy of the device table)
+  ugkwp::Ens ens{};             // device view of the ensemble (used when M > 1)
+  int M = 1;
+  ugkwp_problem p;     // scalars of member 0; host pointers cleared after init
   void* ws = nullptr;
   size_t ws_bytes = 0;
   char err[512];
@@ -204,80 +207,185 @@ void ugkwp::set_global_error(const char* msg) { snprintf(g_err, sizeof g_err, "%
 
 extern "C" {
 
-int ugkwp_workspace_size(const ugkwp_problem* p, size_t* bytes) {
-  int st = validate(p, nullptr);
-  if (st) return st;
-  if (!bytes) return fail(nullptr, UGKWP_ERR_ARG, "bytes is NULL");
+}  // extern "C"
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t member_bytes(const ugkwp_problem* p) {
   Carver cv{nullptr};
   Dev d{};
   double* tmp;
   carve(p, cv, d, &tmp);
-  *bytes = cv.off + 256;
+  return align256(cv.off);
+}
+
+size_t table_bytes(int M) {
+  return align256(sizeof(Dev) * (size_t)M) + 4 * align256(sizeof(int) * (size_t)(M + 1)) + 256;
+}
+
+int validate_members(const ugkwp_problem* probs, int M) {
+  if (!probs || M < 1) return fail(nullptr, UGKWP_ERR_ARG, "need at least one problem");
+  if (M > ugkwp::kMaxEnsemble) return fail(nullptr, UGKWP_ERR_ARG, "too many ensemble members (max 4096)");
+  for (int m = 0; m < M; ++m) {
+    int st = validate(&probs[m], nullptr);
+    if (st) return st;
+    if (probs[m].dim != probs[0].dim || probs[m].precision != probs[0].precision)
+      return fail(nullptr, UGKWP_ERR_ARG, "ensemble members must share dim and precision");
+    if (probs[m].si_max_iters != probs[0].si_max_iters)
+      return fail(nullptr, UGKWP_ERR_ARG, "ensemble members must share si_max_iters");
+  }
   return UGKWP_OK;
 }
 
-int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* stream,
-               ugkwp_handle** out) {
-  if (!out) return fail(nullptr, UGKWP_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  int st = validate(p, nullptr);
-  if (st) return st;
-  size_t need = 0;
-  ugkwp_workspace_size(p, &need);
-  if (!d_workspace || bytes < need)
-    return fail(nullptr, UGKWP_ERR_WORKSPACE, "workspace missing or smaller than ugkwp_workspace_size");
-  if (reinterpret_cast<uintptr_t>(d_workspace) % 256)
-    return fail(nullptr, UGKWP_ERR_WORKSPACE, "workspace must be 256-byte aligned");
-  ugkwp_handle* h = new (std::nothrow) ugkwp_handle;
-  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "out of host memory");
-  h->err[0] = 0;
-  h->p = *p;
-  h->ws = d_workspace;
-  h->ws_bytes = bytes;
-  cudaStream_t s = (cudaStream_t)stream;
-  Carver cv{static_cast<char*>(d_workspace)};
-  Dev& d = h->d;
+// Copy member m's problem into its workspace region and set its initial state.
+cudaError_t init_member(const ugkwp_problem* p, char* base, Dev& d, cudaStream_t s, const char** where) {
+  Carver cv{base};
   d = Dev{};
   double* src_T_tmp = nullptr;
   carve(p, cv, d, &src_T_tmp);
   fill_scalars(p, d);
   const long long nc = d.ncell, G = d.G, ncg = nc * G;
   // zero everything but the particle buffers
-  const size_t head = (size_t)((char*)d.particles_begin - (char*)d_workspace);
-  auto bad = [&](cudaError_t e, const char* w) { int r = cuda_fail(h, e, w); snprintf(g_err, 512, "%s", h->err); delete h; return r; };
+  const size_t head = (size_t)((char*)d.particles_begin - base);
   cudaError_t e;
-  if ((e = cudaMemsetAsync(d_workspace, 0, head, s)) != cudaSuccess) return bad(e, "memset");
+  *where = "memset";
+  if ((e = cudaMemsetAsync(base, 0, head, s))) return e;
   std::vector<double> edges(G + 1);
   if (p->grey) { edges[0] = 0.0; edges[1] = 1.0; }
   else for (int g = 0; g <= G; ++g) edges[g] = p->nu_edges[g];
-  if ((e = cudaMemcpyAsync((void*)d.nu_edges, edges.data(), sizeof(double) * (G + 1), cudaMemcpyHostToDevice, s))) return bad(e, "nu_edges");
-  if ((e = cudaMemcpyAsync((void*)d.sigma0, p->sigma0, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "sigma0");
-  if ((e = cudaMemcpyAsync((void*)d.cv, p->cv, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "cv");
-  if ((e = cudaMemcpyAsync(d.T, p->T0, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "T0");
+  *where = "problem upload";
+  if ((e = cudaMemcpyAsync((void*)d.nu_edges, edges.data(), sizeof(double) * (G + 1), cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync((void*)d.sigma0, p->sigma0, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync((void*)d.cv, p->cv, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(d.T, p->T0, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return e;
   if (p->rho0) {
-    if ((e = cudaMemcpyAsync(d.rho, p->rho0, sizeof(double) * ncg, cudaMemcpyHostToDevice, s))) return bad(e, "rho0");
-    if ((e = cudaMemcpyAsync(d.rho_h, p->rho0, sizeof(double) * ncg, cudaMemcpyHostToDevice, s))) return bad(e, "rho0");
+    if ((e = cudaMemcpyAsync(d.rho, p->rho0, sizeof(double) * ncg, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(d.rho_h, p->rho0, sizeof(double) * ncg, cudaMemcpyHostToDevice, s))) return e;
   }
   if (p->src_T)
-    if ((e = cudaMemcpyAsync(src_T_tmp, p->src_T, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return bad(e, "src_T");
-  if ((e = ugkwp::launch_init_tables(d, p->src_T ? src_T_tmp : nullptr, p->rho0 ? 0 : 1, s))) return bad(e, "init kernel");
+    if ((e = cudaMemcpyAsync(src_T_tmp, p->src_T, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return e;
+  *where = "init kernel";
+  if ((e = ugkwp::launch_init_tables(d, p->src_T ? src_T_tmp : nullptr, p->rho0 ? 0 : 1, s))) return e;
+  // the source temperatures sat in R; wait before the next member's upload reuses host data
+  *where = "init sync";
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ugkwp_workspace_size_ensemble(const ugkwp_problem* probs, int n, size_t* bytes) {
+  int st = validate_members(probs, n);
+  if (st) return st;
+  if (!bytes) return fail(nullptr, UGKWP_ERR_ARG, "bytes is NULL");
+  size_t tot = 0;
+  for (int m = 0; m < n; ++m) tot += member_bytes(&probs[m]);
+  *bytes = tot + table_bytes(n) + 256;
+  return UGKWP_OK;
+}
+
+int ugkwp_workspace_size(const ugkwp_problem* p, size_t* bytes) {
+  return ugkwp_workspace_size_ensemble(p, 1, bytes);
+}
+
+int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, size_t bytes, void* stream,
+                        ugkwp_handle** out) {
+  if (!out) return fail(nullptr, UGKWP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  int st = ugkwp_workspace_size_ensemble(probs, n, &need);
+  if (st) return st;
+  if (!d_workspace || bytes < need)
+    return fail(nullptr, UGKWP_ERR_WORKSPACE, "workspace missing or smaller than the required size");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256)
+    return fail(nullptr, UGKWP_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  ugkwp_handle* h = new (std::nothrow) ugkwp_handle;
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "out of host memory");
+  h->err[0] = 0;
+  h->p = probs[0];
+  h->M = n;
+  h->ws = d_workspace;
+  h->ws_bytes = bytes;
+  h->members.resize(n);
+  cudaStream_t s = (cudaStream_t)stream;
+  auto bad = [&](cudaError_t e, const char* w) {
+    int r = cuda_fail(h, e, w);
+    snprintf(g_err, 512, "%s", h->err);
+    delete h;
+    return r;
+  };
+  char* base = static_cast<char*>(d_workspace);
+  std::vector<int> cell0(n + 1, 0), bin0(n + 1, 0), fg0(n + 1, 0);
+  long long max_bins = 0;
+  int max_G = 0;
+  for (int m = 0; m < n; ++m) {
+    const char* where = "";
+    cudaError_t e = init_member(&probs[m], base, h->members[m], s, &where);
+    if (e) return bad(e, where);
+    base += member_bytes(&probs[m]);
+    const Dev& d = h->members[m];
+    cell0[m + 1] = cell0[m] + d.ncell;
+    bin0[m + 1] = bin0[m] + d.nbins;
+    fg0[m + 1] = fg0[m] + d.nface * d.G;
+    if (d.nbins > max_bins) max_bins = d.nbins;
+    if (d.G > max_G) max_G = d.G;
+  }
+  // device tables
+  Carver cv{base};
+  Dev* d_devs = cv.take<Dev>(n);
+  int* d_cell0 = cv.take<int>(n + 1);
+  int* d_bin0 = cv.take<int>(n + 1);
+  int* d_fg0 = cv.take<int>(n + 1);
+  int* d_tile0 = cv.take<int>(n + 1);
+  unsigned int* d_bar = cv.take<unsigned int>(1);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_devs, h->members.data(), sizeof(Dev) * n, cudaMemcpyHostToDevice, s))) return bad(e, "member table");
+  if ((e = cudaMemcpyAsync(d_cell0, cell0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
+  if ((e = cudaMemcpyAsync(d_bin0, bin0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
+  if ((e = cudaMemcpyAsync(d_fg0, fg0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
+  if ((e = cudaMemsetAsync(d_tile0, 0, sizeof(int) * (n + 1), s))) return bad(e, "tables");
+  if ((e = cudaMemsetAsync(d_bar, 0, sizeof(unsigned int), s))) return bad(e, "tables");
   if ((e = cudaStreamSynchronize(s))) return bad(e, "init sync");
+  ugkwp::Ens& E = h->ens;
+  E.M = n;
+  E.devs = d_devs;
+  E.cell0 = d_cell0;
+  E.bin0 = d_bin0;
+  E.fg0 = d_fg0;
+  E.tile0 = d_tile0;
+  E.bar = d_bar;
+  E.total_bins = bin0[n];
+  E.total_fg = fg0[n];
+  E.total_cells = cell0[n];
+  E.max_parts = ugkwp::scan_parts(max_bins);
+  E.max_G = max_G;
+  h->d = h->members[0];
   h->p.nu_edges = h->p.sigma0 = h->p.cv = h->p.T0 = h->p.rho0 = h->p.src_T = nullptr;
   *out = h;
   return UGKWP_OK;
+}
+
+int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* stream,
+               ugkwp_handle** out) {
+  return ugkwp_init_ensemble(p, 1, d_workspace, bytes, stream, out);
 }
 
 }  // extern "C"
 
 namespace {
 
-cudaError_t enqueue_step(const Dev& d, cudaStream_t s) {
-  cudaError_t e = ugkwp::launch_birth_and_scan(d, s);
-  if (!e) e = ugkwp::launch_wave(d, s);
-  if (!e) e = ugkwp::launch_stream(d, s);
-  if (!e) e = ugkwp::launch_si(d, s);
-  if (!e) e = ugkwp::launch_end_step(d, s);
-  return e;
+cudaError_t enqueue_step(const ugkwp_handle* h, cudaStream_t s) {
+  const Dev& d = h->d;
+  const ugkwp::Ens* e = h->M > 1 ? &h->ens : nullptr;
+  cudaError_t r = ugkwp::launch_birth_and_scan(d, e, s);
+  if (!r) r = ugkwp::launch_wave(d, e, s);
+  if (!r) r = ugkwp::launch_stream(d, e, s);
+  if (!r) r = ugkwp::launch_si(d, e, s);
+  if (!r) r = ugkwp::launch_end_step(d, e, s);
+  return r;
 }
 
 void drop_graph(ugkwp_handle* h) {
@@ -291,7 +399,7 @@ int capture_step(ugkwp_handle* h) {
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), h);
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
-  cudaError_t e = enqueue_step(h->d, h->cap_stream);
+  cudaError_t e = enqueue_step(h, h->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
   if (e) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capturing the step"); }
   if (e2) return cuda_fail(h, e2, "end of capture");
@@ -323,16 +431,17 @@ int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms) {
   cudaEvent_t ev[6];
   for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&ev[i]), h);
   int rc = UGKWP_OK;
+  const ugkwp::Ens* en = h->M > 1 ? &h->ens : nullptr;
   cudaError_t e = cudaEventRecord(ev[0], s);
-  if (!e) e = ugkwp::launch_birth_and_scan(h->d, s);
+  if (!e) e = ugkwp::launch_birth_and_scan(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[1], s);
-  if (!e) e = ugkwp::launch_wave(h->d, s);
+  if (!e) e = ugkwp::launch_wave(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[2], s);
-  if (!e) e = ugkwp::launch_stream(h->d, s);
+  if (!e) e = ugkwp::launch_stream(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[3], s);
-  if (!e) e = ugkwp::launch_si(h->d, s);
+  if (!e) e = ugkwp::launch_si(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[4], s);
-  if (!e) e = ugkwp::launch_end_step(h->d, s);
+  if (!e) e = ugkwp::launch_end_step(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[5], s);
   if (!e) e = cudaEventSynchronize(ev[5]);
   if (!e) {
@@ -345,13 +454,14 @@ int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms) {
   return rc;
 }
 
-int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream) {
+int ugkwp_tallies_member(ugkwp_handle* h, int m, ugkwp_tally_report* out, void* stream) {
   if (!h || !out) return fail(h, UGKWP_ERR_ARG, "NULL argument");
+  if (m < 0 || m >= h->M) return fail(h, UGKWP_ERR_ARG, "member index out of range");
   cudaStream_t s = (cudaStream_t)stream;
+  const Dev& d = h->members[m];
   Ctrl c;
-  CK(cudaMemcpyAsync(&c, h->d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
+  CK(cudaMemcpyAsync(&c, d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
   CK(cudaStreamSynchronize(s), h);
-  const Dev& d = h->d;
   out->T = d.T; out->rho = d.rho; out->rho_h = d.rho_h; out->rho_p = d.rho_p; out->W = d.W;
   out->Fwave = d.Fwave; out->Feq = d.Feq; out->esc = d.esc; out->inflow = d.inflow;
   out->step = (int64_t)c.step;
@@ -367,11 +477,17 @@ int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream) {
   return UGKWP_OK;
 }
 
-int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, double* rho_p,
-                    ugkwp_particles_host* parts, int64_t cap, int64_t* n, void* stream) {
+int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream) {
+  return ugkwp_tallies_member(h, 0, out, stream);
+}
+
+int ugkwp_get_state_member(ugkwp_handle* h, int member, double* T, double* rho, double* rho_h,
+                           double* rho_p, ugkwp_particles_host* parts, int64_t cap, int64_t* n,
+                           void* stream) {
   if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  if (member < 0 || member >= h->M) return fail(h, UGKWP_ERR_ARG, "member index out of range");
   cudaStream_t s = (cudaStream_t)stream;
-  const Dev& d = h->d;
+  const Dev& d = h->members[member];
   const size_t ncg = (size_t)d.ncell * d.G;
   Ctrl c;
   CK(cudaMemcpyAsync(&c, d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
@@ -436,13 +552,20 @@ int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, doub
   return UGKWP_OK;
 }
 
-int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const double* rho_h,
-                    const ugkwp_particles_host* parts, int64_t n, int64_t step, void* stream) {
+int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, double* rho_p,
+                    ugkwp_particles_host* parts, int64_t cap, int64_t* n, void* stream) {
+  return ugkwp_get_state_member(h, 0, T, rho, rho_h, rho_p, parts, cap, n, stream);
+}
+
+int ugkwp_set_state_member(ugkwp_handle* h, int member, const double* T, const double* rho,
+                           const double* rho_h, const ugkwp_particles_host* parts, int64_t n,
+                           int64_t step, void* stream) {
   if (!h || !T || !rho || !rho_h) return fail(h, UGKWP_ERR_ARG, "NULL argument");
-  if (n < 0 || n > h->d.capacity) return fail(h, UGKWP_ERR_CAPACITY, "n exceeds particle capacity");
+  if (member < 0 || member >= h->M) return fail(h, UGKWP_ERR_ARG, "member index out of range");
+  if (n < 0 || n > h->members[member].capacity) return fail(h, UGKWP_ERR_CAPACITY, "n exceeds particle capacity");
   if (n > 0 && !parts) return fail(h, UGKWP_ERR_ARG, "particles missing");
   cudaStream_t s = (cudaStream_t)stream;
-  const Dev& d = h->d;
+  const Dev& d = h->members[member];
   const size_t ncg = (size_t)d.ncell * d.G;
   CK(cudaMemcpyAsync(d.T, T, sizeof(double) * d.ncell, cudaMemcpyHostToDevice, s), h);
   CK(cudaMemcpyAsync(d.rho, rho, sizeof(double) * ncg, cudaMemcpyHostToDevice, s), h);
@@ -500,11 +623,18 @@ int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const d
   return UGKWP_OK;
 }
 
+int ugkwp_set_state(ugkwp_handle* h, const double* T, const double* rho, const double* rho_h,
+                    const ugkwp_particles_host* parts, int64_t n, int64_t step, void* stream) {
+  return ugkwp_set_state_member(h, 0, T, rho, rho_h, parts, n, step, stream);
+}
+
 int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap) {
   if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  if (h->M > 1) return fail(h, UGKWP_ERR_UNSUPPORTED, "records are for single-problem handles");
   static_assert(sizeof(ugkwp_record) == sizeof(ugkwp::RecordOut), "record layout");
   h->d.rec = reinterpret_cast<ugkwp::RecordOut*>(d_records);
   h->d.rec_cap = d_records ? cap : 0;
+  h->members[0] = h->d;
   drop_graph(h);   // the captured step holds the old record pointer
   return UGKWP_OK;
 }

@@ -11,6 +11,7 @@
 namespace ugkwp {
 
 constexpr int kMaxG = 64;
+constexpr int kMaxEnsemble = 4096;   // members advanced together in one step
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kPi4over15 = kPi * kPi * kPi * kPi / 15.0;   // int_0^inf t^3/(e^t-1) dt
 constexpr double k15overPi4 = 15.0 / (kPi * kPi * kPi * kPi);
@@ -184,6 +185,33 @@ struct Dev {
   struct RecordOut* rec;
   long long rec_cap;
 };
+
+// Ensemble view (independent problems advanced together): per-member
+// descriptors and prefix tables over the members' index spaces.  Member m
+// owns global indices [tab[m], tab[m+1]).  A single problem uses M = 1 and the
+// kernels' non-ensemble instantiation, which never reads these tables.
+struct Ens {
+  int M;
+  const Dev* devs;        // [M] member descriptors (device copy)
+  const int* cell0;       // [M+1] prefix of ncell
+  const int* bin0;        // [M+1] prefix of nbins
+  const int* fg0;         // [M+1] prefix of nface*G
+  int* tile0;             // [M+1] prefix of this step's particle tiles (written on the device)
+  unsigned int* bar;      // grid-barrier arrivals of the ensemble source iteration
+  // totals known on the host (launch shapes)
+  long long total_bins, total_fg, total_cells;
+  int max_parts, max_G;
+};
+
+// Member owning global index i: largest m with tab[m] <= i.
+__device__ __forceinline__ int find_member(const int* __restrict__ tab, int M, long long i) {
+  int lo = 0, hi = M;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)__ldg(tab + mid) <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 // Record layout identical to ugkwp_record in the public header.
 struct RecordOut {

@@ -6,14 +6,14 @@
 namespace ugkwp {
 
 cudaError_t launch_init_tables(const Dev& d, const double* src_T, int init_rho, cudaStream_t s);
-cudaError_t launch_birth_and_scan(const Dev& d, cudaStream_t s);
+cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s);
 int scan_parts(long long n);
 cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t* off,
                         unsigned long long* total_a, unsigned long long* total_b, cudaStream_t s);
-cudaError_t launch_wave(const Dev& d, cudaStream_t s);
-cudaError_t launch_stream(const Dev& d, cudaStream_t s);
-cudaError_t launch_si(const Dev& d, cudaStream_t s);
-cudaError_t launch_end_step(const Dev& d, cudaStream_t s);
+cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s);
+cudaError_t launch_stream(const Dev& d, const Ens* e, cudaStream_t s);
+cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s);
+cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s);
 
 // message returned by ugkwp_last_error(NULL)
 void set_global_error(const char* msg);

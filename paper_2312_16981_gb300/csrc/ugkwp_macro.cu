@@ -74,10 +74,17 @@ __global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
 // ghost's collisionless particles, E = e (c/eps)/4 Phi_g(T_b) dt.  Also
 // stores sigma_g(T^n), sigma0 T^q per cell, the sampler slope per bin, zeroes
 // this step's tallies and resets the per-step counters.
-__global__ void k_birth(Dev d) {
+template <bool ENS>
+__global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long total = ENS ? e.total_bins : (long long)d0.nbins;
+  for (long long gb = tid; gb < total; gb += stride) {
+  const int m = ENS ? find_member(e.bin0, e.M, gb) : 0;
+  const Dev& d = ENS ? e.devs[m] : d0;
+  const int b = (int)(ENS ? gb - e.bin0[m] : gb);
   Ctrl* ctrl = d.ctrl;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  if (tid == 0) {
+  if (b == 0) {
     ctrl->n_new = 0;
     ctrl->n_out = 0;
     ctrl->n_in = ctrl->n_part[ctrl->cur];
@@ -89,7 +96,7 @@ __global__ void k_birth(Dev d) {
     ctrl->bnd_in_macro = ctrl->bnd_in_part = ctrl->bnd_out_part = ctrl->src_in = 0.0;
   }
   const int G = d.G;
-  for (int b = tid; b < d.nbins; b += stride) {
+  {
     const int cell = b / G, g = b - cell * G;
     double E, sig, Tb;
     if (cell < d.ncell) {
@@ -138,6 +145,7 @@ __global__ void k_birth(Dev d) {
       d.khat_f[b] = (float)kh;
     }
   }
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -175,24 +183,23 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
   return res;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ N, long long n,
-                                                             uint32_t* __restrict__ part) {
-  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+__device__ __forceinline__ void scan_reduce_body(const uint32_t* __restrict__ N, long long n,
+                                                 uint32_t* __restrict__ part, int blk) {
+  const long long base = (long long)blk * kScanTile + (long long)threadIdx.x * kScanPer;
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k)
     if (base + k < n) s += N[base + k];
   uint32_t tot;
   block_exclusive_scan(s, &tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+  if (threadIdx.x == 0) part[blk] = tot;
 }
 
 // one block: exclusive scan of nparts (<= kScanTile) block sums in place; the
 // grand total goes to off[n] and, when given, to two 64-bit counters
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* __restrict__ part, int nparts,
-                                                               uint32_t* __restrict__ off_total,
-                                                               unsigned long long* total_a,
-                                                               unsigned long long* total_b) {
+__device__ __forceinline__ void scan_partials_body(uint32_t* __restrict__ part, int nparts,
+                                                   uint32_t* __restrict__ off_total,
+                                                   unsigned long long* total_a, unsigned long long* total_b) {
   const int base = threadIdx.x * kScanPer;
   uint32_t v[kScanPer], s = 0;
 #pragma unroll
@@ -211,19 +218,81 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* __rest
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ N, long long n,
-                                                            const uint32_t* __restrict__ part,
-                                                            uint32_t* __restrict__ off) {
-  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+__device__ __forceinline__ void scan_apply_body(const uint32_t* __restrict__ N, long long n,
+                                                const uint32_t* __restrict__ part, uint32_t* __restrict__ off,
+                                                int blk) {
+  const long long base = (long long)blk * kScanTile + (long long)threadIdx.x * kScanPer;
   uint32_t v[kScanPer], s = 0;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < n ? N[base + k] : 0u; s += v[k]; }
-  uint32_t ex = block_exclusive_scan(s, nullptr) + part[blockIdx.x];
+  uint32_t ex = block_exclusive_scan(s, nullptr) + part[blk];
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
     if (base + k < n) off[base + k] = ex;
     ex += v[k];
   }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ N, long long n,
+                                                             uint32_t* __restrict__ part) {
+  scan_reduce_body(N, n, part, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* __restrict__ part, int nparts,
+                                                               uint32_t* __restrict__ off_total,
+                                                               unsigned long long* total_a,
+                                                               unsigned long long* total_b) {
+  scan_partials_body(part, nparts, off_total, total_a, total_b);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ N, long long n,
+                                                            const uint32_t* __restrict__ part,
+                                                            uint32_t* __restrict__ off) {
+  scan_apply_body(N, n, part, off, blockIdx.x);
+}
+
+// Ensemble: one scan per member, member = blockIdx.y.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_ens(const Ens e) {
+  const Dev& d = e.devs[blockIdx.y];
+  if ((long long)blockIdx.x * kScanTile >= d.nbins) return;
+  scan_reduce_body(d.N, d.nbins, d.part, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials_ens(const Ens e) {
+  const Dev& d = e.devs[blockIdx.y];
+  scan_partials_body(d.part, (d.nbins + kScanTile - 1) / kScanTile, d.off + d.nbins, &d.ctrl->n_new,
+                     &d.ctrl->n_born);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply_ens(const Ens e) {
+  const Dev& d = e.devs[blockIdx.y];
+  if ((long long)blockIdx.x * kScanTile >= d.nbins) return;
+  scan_apply_body(d.N, d.nbins, d.part, d.off, blockIdx.x);
+}
+
+// Ensemble: prefix over members of this step's particle tiles (survivors +
+// newborns, tiles of kParticleTile), one block; also resets the barrier.
+constexpr int kParticleTile = 256;
+__global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
+  __shared__ int s_carry;
+  if (threadIdx.x == 0) { s_carry = 0; *e.bar = 0u; }
+  __syncthreads();
+  for (int base = 0; base < e.M; base += blockDim.x) {
+    const int m = base + threadIdx.x;
+    uint32_t t = 0;
+    if (m < e.M) {
+      const Ctrl* c = e.devs[m].ctrl;
+      const unsigned long long n = c->n_part[c->cur] + c->n_new;
+      t = (uint32_t)((n + kParticleTile - 1) / kParticleTile);
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(t, &tot);
+    if (m < e.M) e.tile0[m] = s_carry + (int)ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += (int)tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) e.tile0[e.M] = s_carry;
 }
 
 // --------------------------------------------------------------------------
@@ -281,11 +350,17 @@ __device__ __forceinline__ void half_coefs(double xf, double tauf, double xh, do
 // half-range integrals with C4, C5 from the harmonic-mean face opacity and the
 // sampled fraction e of the upwind cell; wave_order 2 reconstructs rho_h with
 // van Leer slopes.  Reflecting walls carry none.
-__global__ void k_wave(Dev d) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const int G = d.G;
-  const double v = d.v;
-  for (int i = tid; i < d.nface * G; i += stride) {
+template <bool ENS>
+__global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long total = ENS ? e.total_fg : (long long)d0.nface * d0.G;
+  for (long long gi = tid; gi < total; gi += stride) {
+    const int m = ENS ? find_member(e.fg0, e.M, gi) : 0;
+    const Dev& d = ENS ? e.devs[m] : d0;
+    const int i = (int)(ENS ? gi - e.fg0[m] : gi);
+    const int G = d.G;
+    const double v = d.v;
     const int f = i / G, g = i - f * G;
     const FaceRef r = face_ref(d, f);
     const int sideL = r.axis * 2, sideR = sideL + 1;
@@ -340,22 +415,23 @@ __global__ void k_wave(Dev d) {
 // Grid-wide barrier for the cooperative source-iteration kernel: a
 // monotonically increasing arrival counter, bounded spin.  On timeout the
 // status bit is set and the caller returns.
-__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned int target) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_ctrl, unsigned int limit_in,
+                                             unsigned int target) {
   __shared__ int s_timeout;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(&ctrl->bar_count, 1u);
-    const unsigned int limit = ctrl->bar_timeout_spins ? ctrl->bar_timeout_spins : (1u << 25);
+    atomicAdd(count, 1u);
+    const unsigned int limit = limit_in ? limit_in : (1u << 25);
     unsigned int spins = 0;
     int to = 0;
     while (true) {
-      const unsigned int c = atomicAdd(&ctrl->bar_count, 0u);
+      const unsigned int c = atomicAdd(count, 0u);
       if (c >= target) break;
       if (++spins > limit) { to = 1; break; }
       __nanosleep(64);
     }
-    if (to) atomicOr(&ctrl->status, ST_TIMEOUT);
+    if (to) atomicOr(&status_ctrl->status, ST_TIMEOUT);
     __threadfence();
     s_timeout = to;
   }
@@ -473,66 +549,103 @@ __device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir
 // R = rho^n + wave-flux divergence + w^{fr,p}/V + source; the epilogue writes
 // T^{n+1}, rho^{n+1}, rho^p = E_surv/V, rho^h = rho^{n+1} - rho^p and the
 // energy ledger.
-template <int NC>
-__global__ void __launch_bounds__(256) k_si(Dev d) {
-  Ctrl* ctrl = d.ctrl;
+// Members of an ensemble converge separately: a member whose errors met the
+// rule stops updating while the others go on (every block keeps the same
+// per-member record, so all blocks leave the loop together).
+
+template <int NC, bool ENS>
+__global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, const Ens e) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-  const int gw = blockIdx.x * nwb + wib, nw = gridDim.x * nwb;
-  const int G = d.G;
-  const double dt = d.dt, V = d.vol;
+  const long long gw = blockIdx.x * (long long)nwb + wib, nw = (long long)gridDim.x * nwb;
+  const long long total = ENS ? e.total_cells : (long long)d0.ncell;
+  const int M = ENS ? e.M : 1;
+  unsigned int* bar_count = ENS ? e.bar : &d0.ctrl->bar_count;
+  Ctrl* st_ctrl = ENS ? e.devs[0].ctrl : d0.ctrl;
+  const unsigned int spin_limit = st_ctrl->bar_timeout_spins;
   __shared__ double s_red[8][4];
+  __shared__ int s_conv[ENS ? kMaxEnsemble : 1];   // iterate count at convergence, 0 = still running
+  __shared__ int s_any;
   unsigned int bar = 0;
-  double e_rad0 = 0.0, e_mat0 = 0.0, e_src = 0.0;
 
   // ---- prologue
-  for (int c = gw; c < d.ncell; c += nw) {
-    const int ix = c % d.nx, iy = c / d.nx;
-    const int fxl = iy * (d.nx + 1) + ix, fxr = fxl + 1;
-    const int fyl = d.nxface + iy * d.nx + ix, fyr = fyl + d.nx;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      const int g = lane + 32 * j;
-      if (g < G) {
-        const int i = c * G + g;
-        const double r0 = d.rho[i];
-        double r = r0 + (dt / d.dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
-        if (d.dim == 2) r += (dt / d.dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
-        r += d.W[i] / V;
-        if (d.src) { r += d.src[i]; e_src += V * d.src[i] / d.c; }
-        d.R[i] = r;
-        e_rad0 += V * r0 / d.c;
+  {
+    double e_rad0 = 0.0, e_mat0 = 0.0, e_src = 0.0;
+    int acc_m = -1;
+    for (long long gc = gw; gc < total; gc += nw) {
+      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+      if (ENS && m != acc_m && acc_m >= 0) {
+        e_rad0 = warp_sum(e_rad0);
+        e_src = warp_sum(e_src);
+        if (lane == 0) {
+          Ctrl* cc = e.devs[acc_m].ctrl;
+          atomicAdd(&cc->E_rad0, e_rad0);
+          atomicAdd(&cc->E_mat0, e_mat0);
+          if (e_src != 0.0) atomicAdd(&cc->src_in, e_src);
+        }
+        e_rad0 = e_mat0 = e_src = 0.0;
       }
-    }
-    const double T = d.T[c];
-    if (lane == 0) e_mat0 += V * d.cv[c] * T;
-    double sg[NC], ph[NC], dp[NC];
-    cell_planck<NC>(d, c, T, sg, ph, dp);
+      acc_m = m;
+      const Dev& d = ENS ? e.devs[m] : d0;
+      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
+      const int G = d.G;
+      const double dt = d.dt, V = d.vol;
+      const int ix = c % d.nx, iy = c / d.nx;
+      const int fxl = iy * (d.nx + 1) + ix, fxr = fxl + 1;
+      const int fyl = d.nxface + iy * d.nx + ix, fyr = fyl + d.nx;
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      const int g = lane + 32 * j;
-      if (g < G) {
-        __stcg(d.sigk[0] + c * G + g, sg[j]);
-        __stcg(d.phik[0] + c * G + g, ph[j]);
-        __stcg(d.dphik + c * G + g, dp[j]);
+      for (int j = 0; j < NC; ++j) {
+        const int g = lane + 32 * j;
+        if (g < G) {
+          const int i = c * G + g;
+          const double r0 = d.rho[i];
+          double r = r0 + (dt / d.dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
+          if (d.dim == 2) r += (dt / d.dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
+          r += d.W[i] / V;
+          if (d.src) { r += d.src[i]; e_src += V * d.src[i] / d.c; }
+          d.R[i] = r;
+          e_rad0 += V * r0 / d.c;
+        }
       }
+      const double T = d.T[c];
+      if (lane == 0) e_mat0 += V * d.cv[c] * T;
+      double sg[NC], ph[NC], dp[NC];
+      cell_planck<NC>(d, c, T, sg, ph, dp);
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int g = lane + 32 * j;
+        if (g < G) {
+          __stcg(d.sigk[0] + c * G + g, sg[j]);
+          __stcg(d.phik[0] + c * G + g, ph[j]);
+          __stcg(d.dphik + c * G + g, dp[j]);
+        }
+      }
+      if (lane == 0) __stcg(d.Tk[0] + c, T);
     }
-    if (lane == 0) __stcg(d.Tk[0] + c, T);
+    e_rad0 = warp_sum(e_rad0);
+    e_src = warp_sum(e_src);
+    if (lane == 0 && acc_m >= 0) {
+      Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
+      atomicAdd(&cc->E_rad0, e_rad0);
+      atomicAdd(&cc->E_mat0, e_mat0);
+      if (e_src != 0.0) atomicAdd(&cc->src_in, e_src);
+    }
   }
-  e_rad0 = warp_sum(e_rad0);
-  e_src = warp_sum(e_src);
-  if (lane == 0) {
-    atomicAdd(&ctrl->E_rad0, e_rad0);
-    atomicAdd(&ctrl->E_mat0, e_mat0);
-    if (e_src != 0.0) atomicAdd(&ctrl->src_in, e_src);
-  }
-  if (!grid_barrier(ctrl, (++bar) * gridDim.x)) return;
+  for (int k = threadIdx.x; k < (ENS ? M : 1); k += blockDim.x) s_conv[k] = 0;
+  if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
 
   // ---- iterations
-  int it = 0, converged = 0;
-  for (; it < d.si_max_iters; ++it) {
+  const int max_it = ENS ? e.devs[0].si_max_iters : d0.si_max_iters;
+  int it = 0, all_done = 0;
+  for (; it < max_it; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
     double werrT = 0.0, werrR = 0.0;
-    for (int c = gw; c < d.ncell; c += nw) {
+    for (long long gc = gw; gc < total; gc += nw) {
+      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+      if (ENS && s_conv[m]) continue;
+      const Dev& d = ENS ? e.devs[m] : d0;
+      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
+      const int G = d.G;
+      const double dt = d.dt;
       const double Tc = __ldcg(d.Tk[cur] + c), Tn = d.T[c], cv = d.cv[c];
       double Q[NC], a[NC], phc[NC], dpc[NC];
       double num = 0.0, den = 0.0;
@@ -587,8 +700,16 @@ __global__ void __launch_bounds__(256) k_si(Dev d) {
       rsum = warp_sum(rsum);
       const double eR = rsum > 0.0 ? dmax / rsum : 0.0;
       const double eT = fabs(Tnew - Tc) / Tnew;
-      werrT = fmax(werrT, (eT == eT) ? eT : 1e300);
-      werrR = fmax(werrR, (eR == eR) ? eR : 1e300);
+      if (ENS) {
+        // members differ between warps: each warp reports to its own member
+        if (lane == 0) {
+          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][0], (eT == eT) ? eT : 1e300);
+          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][1], (eR == eR) ? eR : 1e300);
+        }
+      } else {
+        werrT = fmax(werrT, (eT == eT) ? eT : 1e300);
+        werrR = fmax(werrR, (eR == eR) ? eR : 1e300);
+      }
       if (lane == 0) __stcg(d.Tk[nxt] + c, Tnew);
       double sg[NC], ph[NC], dp[NC];
       cell_planck<NC>(d, c, Tnew, sg, ph, dp);
@@ -602,79 +723,135 @@ __global__ void __launch_bounds__(256) k_si(Dev d) {
         }
       }
     }
-    if (lane == 0) { s_red[wib][0] = werrT; s_red[wib][1] = werrR; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double mT = 0.0, mR = 0.0;
-      for (int w = 0; w < nwb; ++w) { mT = fmax(mT, s_red[w][0]); mR = fmax(mR, s_red[w][1]); }
-      atomic_max_nonneg(&ctrl->err_slot[it % 3][0], mT);
-      atomic_max_nonneg(&ctrl->err_slot[it % 3][1], mR);
-      if (blockIdx.x == 0) {
-        ctrl->err_slot[(it + 1) % 3][0] = 0ull;
-        ctrl->err_slot[(it + 1) % 3][1] = 0ull;
+    if (!ENS) {
+      Ctrl* ctrl = d0.ctrl;
+      if (lane == 0) { s_red[wib][0] = werrT; s_red[wib][1] = werrR; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double mT = 0.0, mR = 0.0;
+        for (int w = 0; w < nwb; ++w) { mT = fmax(mT, s_red[w][0]); mR = fmax(mR, s_red[w][1]); }
+        atomic_max_nonneg(&ctrl->err_slot[it % 3][0], mT);
+        atomic_max_nonneg(&ctrl->err_slot[it % 3][1], mR);
+        if (blockIdx.x == 0) {
+          ctrl->err_slot[(it + 1) % 3][0] = 0ull;
+          ctrl->err_slot[(it + 1) % 3][1] = 0ull;
+        }
+      }
+    } else if (blockIdx.x == 0) {
+      for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        Ctrl* cc = e.devs[k].ctrl;
+        cc->err_slot[(it + 1) % 3][0] = 0ull;
+        cc->err_slot[(it + 1) % 3][1] = 0ull;
       }
     }
-    if (!grid_barrier(ctrl, (++bar) * gridDim.x)) return;
-    const double eT = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][0], 0ull));
-    const double eR = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][1], 0ull));
-    if (eT <= d.si_tol && eR <= d.si_tol) { converged = 1; ++it; break; }
+    if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+    if (!ENS) {
+      Ctrl* ctrl = d0.ctrl;
+      const double eT = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][0], 0ull));
+      const double eR = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][1], 0ull));
+      if (eT <= d0.si_tol && eR <= d0.si_tol) { s_conv[0] = it + 1; all_done = 1; ++it; break; }
+    } else {
+      if (threadIdx.x == 0) s_any = 0;
+      __syncthreads();
+      int running = 0;
+      for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        if (s_conv[k]) continue;
+        Ctrl* cc = e.devs[k].ctrl;
+        const double eT = __longlong_as_double((long long)atomicAdd(&cc->err_slot[it % 3][0], 0ull));
+        const double eR = __longlong_as_double((long long)atomicAdd(&cc->err_slot[it % 3][1], 0ull));
+        const double tol = e.devs[k].si_tol;
+        if (eT <= tol && eR <= tol) s_conv[k] = it + 1; else running = 1;
+      }
+      if (running) s_any = 1;
+      __syncthreads();
+      if (!s_any) { all_done = 1; ++it; break; }
+    }
   }
-  // iterate `it - 1` wrote Tk[it & 1]
-  const int fin = it > 0 ? (it & 1) : 0;
 
-  // ---- epilogue
-  double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
-  int bad = 0;
-  for (int c = gw; c < d.ncell; c += nw) {
-    const double T = __ldcg(d.Tk[fin] + c);
-    if (!(T == T) || T > 1e300) bad = 1;
-    if (lane == 0) {
-      d.T[c] = T;
-      e_mat1 += V * d.cv[c] * T;
-    }
-    const int ix = c % d.nx, iy = c / d.nx;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      const int g = lane + 32 * j;
-      if (g >= G) continue;
-      const int i = c * G + g;
-      const double r = __ldcg(d.rho + i);
-      const double rp = d.E_surv[i] / V;
-      d.rho_p[i] = rp;
-      d.rho_h[i] = r - rp;
-      e_rad1 += V * r / d.c;
-      // boundary faces: energy entering the domain
-      for (int axis = 0; axis < d.dim; ++axis) {
-        const double S = d.dim == 2 ? (axis == 0 ? d.dy : d.dx) : 1.0;
-        const int k = axis == 0 ? ix : iy, nk = axis == 0 ? d.nx : d.ny;
-        if (k == 0) {
-          const int f = face_index(d, c, axis, -1);
-          b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+  // ---- epilogue: member m's last iterate wrote Tk[s_conv[m] & 1] (or Tk[it & 1])
+  {
+    double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
+    int bad = 0, acc_m = -1;
+    for (long long gc = gw; gc < total; gc += nw) {
+      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+      if (ENS && m != acc_m && acc_m >= 0) {
+        e_rad1 = warp_sum(e_rad1);
+        b_in = warp_sum(b_in);
+        if (lane == 0) {
+          Ctrl* cc = e.devs[acc_m].ctrl;
+          atomicAdd(&cc->E_rad1, e_rad1);
+          atomicAdd(&cc->E_mat1, e_mat1);
+          if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
+          if (bad) atomicOr(&cc->status, ST_NONFINITE);
         }
-        if (k == nk - 1) {
-          const int f = face_index(d, c, axis, +1);
-          b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+        e_rad1 = e_mat1 = b_in = 0.0;
+        bad = 0;
+      }
+      acc_m = m;
+      const Dev& d = ENS ? e.devs[m] : d0;
+      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
+      const int G = d.G;
+      const double dt = d.dt, V = d.vol;
+      const int ran = s_conv[ENS ? m : 0] ? s_conv[ENS ? m : 0] : it;
+      const int fin = ran > 0 ? (ran & 1) : 0;
+      const double T = __ldcg(d.Tk[fin] + c);
+      if (!(T == T) || T > 1e300) bad = 1;
+      if (lane == 0) {
+        d.T[c] = T;
+        e_mat1 += V * d.cv[c] * T;
+      }
+      const int ix = c % d.nx, iy = c / d.nx;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int g = lane + 32 * j;
+        if (g >= G) continue;
+        const int i = c * G + g;
+        const double r = __ldcg(d.rho + i);
+        const double rp = d.E_surv[i] / V;
+        d.rho_p[i] = rp;
+        d.rho_h[i] = r - rp;
+        e_rad1 += V * r / d.c;
+        // boundary faces: energy entering the domain
+        for (int axis = 0; axis < d.dim; ++axis) {
+          const double S = d.dim == 2 ? (axis == 0 ? d.dy : d.dx) : 1.0;
+          const int k = axis == 0 ? ix : iy, nk = axis == 0 ? d.nx : d.ny;
+          if (k == 0) {
+            const int f = face_index(d, c, axis, -1);
+            b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+          }
+          if (k == nk - 1) {
+            const int f = face_index(d, c, axis, +1);
+            b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+          }
         }
       }
     }
+    e_rad1 = warp_sum(e_rad1);
+    b_in = warp_sum(b_in);
+    if (lane == 0 && acc_m >= 0) {
+      Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
+      atomicAdd(&cc->E_rad1, e_rad1);
+      atomicAdd(&cc->E_mat1, e_mat1);
+      if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
+      if (bad) atomicOr(&cc->status, ST_NONFINITE);
+    }
   }
-  e_rad1 = warp_sum(e_rad1);
-  b_in = warp_sum(b_in);
-  if (lane == 0) {
-    atomicAdd(&ctrl->E_rad1, e_rad1);
-    atomicAdd(&ctrl->E_mat1, e_mat1);
-    if (b_in != 0.0) atomicAdd(&ctrl->bnd_in_macro, b_in);
-    if (bad) atomicOr(&ctrl->status, ST_NONFINITE);
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      Ctrl* cc = ENS ? e.devs[k].ctrl : d0.ctrl;
+      const int ran = s_conv[ENS ? k : 0];
+      cc->si_iters = (unsigned int)(ran ? ran : it);
+      if (!ran) atomicOr(&cc->status, ST_NOCONV);
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctrl->si_iters = (unsigned int)it;
-    if (!converged) atomicOr(&ctrl->status, ST_NOCONV);
-  }
+  (void)all_done;
 }
 
 // End of step: swap particle buffers, advance the step counter, particle
 // ledger from the side tallies.
-__global__ void k_end_step(Dev d) {
+template <bool ENS>
+__global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
+  const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
   Ctrl* ctrl = d.ctrl;
   if (threadIdx.x == 0) {
     const unsigned long long n = ctrl->n_out;
@@ -767,35 +944,49 @@ cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_birth_and_scan(const Dev& d, cudaStream_t s) {
-  k_birth<<<grid_for(d.nbins, 64), 64, 0, s>>>(d);
+cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s) {
+  if (e && e->M > 1) {
+    k_birth<true><<<grid_for(e->total_bins, 64, 152 * 64), 64, 0, s>>>(d, *e);
+    const dim3 g(e->max_parts, e->M);
+    k_scan_reduce_ens<<<g, kScanThreads, 0, s>>>(*e);
+    k_scan_partials_ens<<<dim3(1, e->M), kScanThreads, 0, s>>>(*e);
+    k_scan_apply_ens<<<g, kScanThreads, 0, s>>>(*e);
+    k_tiles<<<1, 1024, 0, s>>>(*e);
+    return cudaGetLastError();
+  }
+  const Ens none{};
+  k_birth<false><<<grid_for(d.nbins, 64), 64, 0, s>>>(d, none);
   return launch_scan(d.N, d.nbins, d.part, d.off, &d.ctrl->n_new, &d.ctrl->n_born, s);
 }
 
-cudaError_t launch_wave(const Dev& d, cudaStream_t s) {
-  k_wave<<<grid_for((long long)d.nface * d.G, 64), 64, 0, s>>>(d);
+cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s) {
+  if (e && e->M > 1) {
+    k_wave<true><<<grid_for(e->total_fg, 64, 152 * 64), 64, 0, s>>>(d, *e);
+  } else {
+    const Ens none{};
+    k_wave<false><<<grid_for((long long)d.nface * d.G, 64), 64, 0, s>>>(d, none);
+  }
   return cudaGetLastError();
 }
 
-static int g_si_blocks[2][2] = {{0, 0}, {0, 0}};
+static int g_si_blocks[2][2][2] = {};
 
 // One warp per cell.  On GB300 the FP64 pipe of an SM is the limit of this
 // kernel, so a small grid is spread one warp per block over all SMs; a large
 // grid uses 8-warp blocks (fewer arrivals at the grid barrier).
-cudaError_t launch_si(const Dev& d, cudaStream_t s) {
-  const int nc = d.G > 32 ? 1 : 0;
-  void* fn = nc ? (void*)k_si<2> : (void*)k_si<1>;
+template <int NC, bool ENS>
+static cudaError_t launch_si_t(const Dev& d, const Ens& e, long long ncell, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int small = d.ncell <= 8 * sms;
+  const int small = ncell <= 8 * sms;
   const int threads = small ? 32 : 256;
-  int& per = g_si_blocks[nc][small];
+  int& per = g_si_blocks[NC - 1][ENS][small];
   if (!per) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_si<NC, ENS>, threads, 0);
     if (per < 1) per = 1;
   }
-  const long long want = ((long long)d.ncell * 32 + threads - 1) / threads;
+  const long long want = (ncell * 32 + threads - 1) / threads;
   const long long maxb = (long long)sms * per;
   int blocks = (int)(want < maxb ? want : maxb);
   if (blocks < 1) blocks = 1;
@@ -809,12 +1000,27 @@ cudaError_t launch_si(const Dev& d, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (nc) return cudaLaunchKernelEx(&cfg, k_si<2>, d);
-  return cudaLaunchKernelEx(&cfg, k_si<1>, d);
+  return cudaLaunchKernelEx(&cfg, k_si<NC, ENS>, d, e);
 }
 
-cudaError_t launch_end_step(const Dev& d, cudaStream_t s) {
-  k_end_step<<<1, 32, 0, s>>>(d);
+cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s) {
+  if (e && e->M > 1) {
+    if (e->M > kMaxEnsemble) return cudaErrorInvalidValue;
+    if (e->max_G > 32) return launch_si_t<2, true>(d, *e, e->total_cells, s);
+    return launch_si_t<1, true>(d, *e, e->total_cells, s);
+  }
+  const Ens none{};
+  if (d.G > 32) return launch_si_t<2, false>(d, none, d.ncell, s);
+  return launch_si_t<1, false>(d, none, d.ncell, s);
+}
+
+cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
+  if (e && e->M > 1) {
+    k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e);
+  } else {
+    const Ens none{};
+    k_end_step<false><<<1, 32, 0, s>>>(d, none);
+  }
   return cudaGetLastError();
 }
 

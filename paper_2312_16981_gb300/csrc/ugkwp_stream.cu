@@ -121,8 +121,43 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
+struct Counters {
+  unsigned long long seg = 0, abs = 0, esc = 0, surv = 0, rem = 0;
+};
+
+__device__ __forceinline__ void flush_counters(Ctrl* ctrl, Counters& c) {
+  c.seg = warp_sum_u64(c.seg);
+  c.abs = warp_sum_u64(c.abs);
+  c.esc = warp_sum_u64(c.esc);
+  c.surv = warp_sum_u64(c.surv);
+  c.rem = warp_sum_u64(c.rem);
+  if ((threadIdx.x & 31) == 0) {
+    if (c.seg) atomicAdd(&ctrl->n_segments, c.seg);
+    if (c.abs) atomicAdd(&ctrl->n_absorbed, c.abs);
+    if (c.esc) atomicAdd(&ctrl->n_escaped, c.esc);
+    if (c.surv) atomicAdd(&ctrl->n_survived, c.surv);
+    if (c.rem) atomicAdd(&ctrl->n_removed, c.rem);
+  }
+  c = Counters();
+}
+
+__device__ __forceinline__ long long tiles_of(const Dev& d) {
+  const Ctrl* ctrl = d.ctrl;
+  const long long n = (long long)ctrl->n_part[ctrl->cur] + (long long)ctrl->n_new;
+  return (n + kStreamThreads - 1) / kStreamThreads;
+}
+
+template <int DIM, bool ENS>
+__global__ void __launch_bounds__(kStreamThreads) k_stream64(const __grid_constant__ Dev d0, const Ens e) {
+  Counters cnt;
+  int acc_m = 0;
+  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0);
+  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
+  const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
+  if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
+  const Dev& d = ENS ? e.devs[m] : d0;
+  const long long lt = ENS ? t - (long long)e.tile0[m] : t;
   Ctrl* ctrl = d.ctrl;
   const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
   const long long n_surv = (long long)ctrl->n_part[cur];
@@ -138,12 +173,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
   const double* __restrict__ in_w = d.pw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-
-  unsigned long long c_seg = 0, c_abs = 0, c_esc = 0, c_surv = 0, c_rem = 0;
-  const long long ntiles = (n_tot + kStreamThreads - 1) / kStreamThreads;
-  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
-    const long long i = t * kStreamThreads + threadIdx.x;
+  {
+    const long long i = lt * kStreamThreads + threadIdx.x;
     const bool valid = i < n_tot;
     double x = 0.0, y = 0.0, ox = 0.0, oy = 0.0, nu = 0.0, w = 0.0;
     unsigned long long id = 0ull;
@@ -312,11 +343,11 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, w);
     }
     if (valid) {
-      c_seg += (unsigned long long)nseg;
-      c_abs += fate == FATE_ABSORBED;
-      c_esc += fate == FATE_ESCAPED;
-      c_surv += fate == FATE_SURVIVED;
-      c_rem += fate == FATE_REMOVED;
+      cnt.seg += (unsigned long long)nseg;
+      cnt.abs += fate == FATE_ABSORBED;
+      cnt.esc += fate == FATE_ESCAPED;
+      cnt.surv += fate == FATE_SURVIVED;
+      cnt.rem += fate == FATE_REMOVED;
       if (d.rec && i < d.rec_cap) {
         RecordOut& r = d.rec[i];
         r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = cell; r.grp = g; r.nseg = nseg; r.pad = 0;
@@ -343,25 +374,24 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(Dev d) {
       }
     }
   }
-  c_seg = warp_sum_u64(c_seg);
-  c_abs = warp_sum_u64(c_abs);
-  c_esc = warp_sum_u64(c_esc);
-  c_surv = warp_sum_u64(c_surv);
-  c_rem = warp_sum_u64(c_rem);
-  if ((threadIdx.x & 31) == 0) {
-    if (c_seg) atomicAdd(&ctrl->n_segments, c_seg);
-    if (c_abs) atomicAdd(&ctrl->n_absorbed, c_abs);
-    if (c_esc) atomicAdd(&ctrl->n_escaped, c_esc);
-    if (c_surv) atomicAdd(&ctrl->n_survived, c_surv);
-    if (c_rem) atomicAdd(&ctrl->n_removed, c_rem);
   }
+  flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
 // Mixed precision (FP32 particle state and arithmetic, FP64 tallies): the
 // same algorithm as k_stream64 with positions held relative to the cell
 // (0 <= xi <= dx) and FP32 uniforms from the same Philox words.  A survivor costs 28 B read and 28 B written in 1D.
-template <int DIM>
-__global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
+template <int DIM, bool ENS>
+__global__ void __launch_bounds__(kStreamThreads) k_stream32(const __grid_constant__ Dev d0, const Ens e) {
+  Counters cnt;
+  int acc_m = 0;
+  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0);
+  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
+  const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
+  if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
+  const Dev& d = ENS ? e.devs[m] : d0;
+  const long long lt = ENS ? t - (long long)e.tile0[m] : t;
   Ctrl* ctrl = d.ctrl;
   const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
   const long long n_surv = (long long)ctrl->n_part[cur];
@@ -380,12 +410,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
   const float* __restrict__ in_w = d.fw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-
-  unsigned long long c_seg = 0, c_abs = 0, c_esc = 0, c_surv = 0, c_rem = 0;
-  const long long ntiles = (n_tot + kStreamThreads - 1) / kStreamThreads;
-  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
-    const long long i = t * kStreamThreads + threadIdx.x;
+  {
+    const long long i = lt * kStreamThreads + threadIdx.x;
     const bool valid = i < n_tot;
     float xi = 0.f, eta = 0.f, ox = 0.f, oy = 0.f, nu = 0.f, w = 0.f;
     unsigned long long id = 0ull;
@@ -547,11 +573,11 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, wd);
     }
     if (valid) {
-      c_seg += (unsigned long long)nseg;
-      c_abs += fate == FATE_ABSORBED;
-      c_esc += fate == FATE_ESCAPED;
-      c_surv += fate == FATE_SURVIVED;
-      c_rem += fate == FATE_REMOVED;
+      cnt.seg += (unsigned long long)nseg;
+      cnt.abs += fate == FATE_ABSORBED;
+      cnt.esc += fate == FATE_ESCAPED;
+      cnt.surv += fate == FATE_SURVIVED;
+      cnt.rem += fate == FATE_REMOVED;
       if (d.rec && i < d.rec_cap) {
         RecordOut& r = d.rec[i];
         r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = (fate == FATE_REMOVED && gside >= 0) ? cx : cell;
@@ -581,43 +607,38 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(Dev d) {
       }
     }
   }
-  c_seg = warp_sum_u64(c_seg);
-  c_abs = warp_sum_u64(c_abs);
-  c_esc = warp_sum_u64(c_esc);
-  c_surv = warp_sum_u64(c_surv);
-  c_rem = warp_sum_u64(c_rem);
-  if ((threadIdx.x & 31) == 0) {
-    if (c_seg) atomicAdd(&ctrl->n_segments, c_seg);
-    if (c_abs) atomicAdd(&ctrl->n_absorbed, c_abs);
-    if (c_esc) atomicAdd(&ctrl->n_escaped, c_esc);
-    if (c_surv) atomicAdd(&ctrl->n_survived, c_surv);
-    if (c_rem) atomicAdd(&ctrl->n_removed, c_rem);
   }
+  flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
-static int g_stream_blocks[2][3] = {{0, 0, 0}, {0, 0, 0}};
+static int g_stream_blocks[2][3][2] = {};
 
-cudaError_t launch_stream(const Dev& d, cudaStream_t s) {
+template <int DIM, bool ENS>
+static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int mixed = d.precision == 1;
-  const void* fn = mixed ? (d.dim == 2 ? (const void*)k_stream32<2> : (const void*)k_stream32<1>)
-                         : (d.dim == 2 ? (const void*)k_stream64<2> : (const void*)k_stream64<1>);
-  int& per = g_stream_blocks[mixed][d.dim];
+  const void* fn = mixed ? (const void*)k_stream32<DIM, ENS> : (const void*)k_stream64<DIM, ENS>;
+  int& per = g_stream_blocks[mixed][DIM][ENS];
   if (!per) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kStreamThreads, 0);
     if (per < 1) per = 1;
   }
   const int blocks = sms * per;
-  if (mixed) {
-    if (d.dim == 2) k_stream32<2><<<blocks, kStreamThreads, 0, s>>>(d);
-    else k_stream32<1><<<blocks, kStreamThreads, 0, s>>>(d);
-  } else {
-    if (d.dim == 2) k_stream64<2><<<blocks, kStreamThreads, 0, s>>>(d);
-    else k_stream64<1><<<blocks, kStreamThreads, 0, s>>>(d);
-  }
+  if (mixed) k_stream32<DIM, ENS><<<blocks, kStreamThreads, 0, s>>>(d, e);
+  else k_stream64<DIM, ENS><<<blocks, kStreamThreads, 0, s>>>(d, e);
   return cudaGetLastError();
+}
+
+cudaError_t launch_stream(const Dev& d, const Ens* e, cudaStream_t s) {
+  const int mixed = d.precision == 1;
+  if (e && e->M > 1) {
+    if (d.dim == 2) return launch_stream_t<2, true>(d, *e, mixed, s);
+    return launch_stream_t<1, true>(d, *e, mixed, s);
+  }
+  const Ens none{};
+  if (d.dim == 2) return launch_stream_t<2, false>(d, none, mixed, s);
+  return launch_stream_t<1, false>(d, none, mixed, s);
 }
 
 }  // namespace ugkwp
