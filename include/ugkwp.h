@@ -198,6 +198,29 @@ int ugkwp_set_state_member(ugkwp_handle* h, int member, const double* T, const d
                            const double* rho_h, const ugkwp_particles_host* parts, int64_t n,
                            int64_t step, void* stream);
 
+/* ---- checkpoint / restore ----
+ * The state of every member (T, rho, rho_h, rho_p, the live particles and
+ * the control block with the step counter) copied device-to-device into a
+ * caller-owned DEVICE buffer of ugkwp_checkpoint_size bytes (256-byte
+ * aligned), asynchronously on `stream`.  Identities and counter-based random
+ * streams make a restored run repeat the same steps, up to the summation
+ * order of FP64 atomics. */
+int ugkwp_checkpoint_size(const ugkwp_handle* h, size_t* bytes);
+int ugkwp_checkpoint(ugkwp_handle* h, void* d_buf, size_t bytes, void* stream);
+int ugkwp_restore(ugkwp_handle* h, const void* d_buf, size_t bytes, void* stream);
+
+/* ---- launch shape of the particle kernel ----
+ * block: 128, 256 or 512 threads; particles_per_thread: 1 or 2 (sub-tiles
+ * per tile); blocks_per_sm: 0 for as many as fit. */
+int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int blocks_per_sm);
+/* Time every launch shape on `steps` identical steps (the state is saved in
+ * d_ckpt, a buffer of ugkwp_checkpoint_size bytes, and restored before each
+ * candidate and at the end), keep the fastest particle phase, and report it
+ * in best[3] = {block, particles_per_thread, blocks_per_sm} and *best_ms.
+ * Synchronises `stream`. */
+int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void* stream, int* best,
+                   float* best_ms);
+
 const char* ugkwp_last_error(const ugkwp_handle* h);
 void ugkwp_destroy(ugkwp_handle* h);
 

@@ -95,6 +95,12 @@ FUNCTIONS = {
     "ugkwp_set_state_member": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_void_p, C.c_int64,
                                          C.c_int64, C.c_void_p]),
     "ugkwp_last_error": (C.c_char_p, [C.c_void_p]),
+    "ugkwp_checkpoint_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "ugkwp_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ugkwp_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ugkwp_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "ugkwp_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p,
+                                 C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ugkwp_destroy": (None, [C.c_void_p]),
     "ugkwp_philox": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64, C.c_void_p]),
     "ugkwp_planck": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
@@ -304,6 +310,67 @@ class Simulation:
         _check(L.ugkwp_set_state_member(self.h, member, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
                                         rho_h.ctypes.data_as(_dp), None if cs is None else C.byref(cs), n,
                                         int(step), C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def checkpoint_buffer(self):
+        """A device buffer (torch uint8) large enough for one checkpoint."""
+        import torch
+        n = C.c_size_t()
+        _check(load().ugkwp_checkpoint_size(self.h, C.byref(n)), self.h)
+        return torch.empty(n.value, dtype=torch.uint8, device=self.device)
+
+    def checkpoint(self, buf):
+        _check(load().ugkwp_checkpoint(self.h, C.c_void_p(_ptr(buf)), buf.numel(),
+                                       C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def restore(self, buf):
+        _check(load().ugkwp_restore(self.h, C.c_void_p(_ptr(buf)), buf.numel(),
+                                    C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def set_launch(self, block: int, particles_per_thread: int = 1, blocks_per_sm: int = 0):
+        _check(load().ugkwp_set_launch(self.h, block, particles_per_thread, blocks_per_sm), self.h)
+
+    def autotune(self, steps: int = 2, cache: Optional[str] = None):
+        """Pick the particle kernel's launch shape by timing each candidate on
+        identical steps (state saved and restored).  With `cache` (a JSON
+        file), a shape found before for the same GPU and workload signature
+        is reused without timing."""
+        import json
+        import torch
+        key = None
+        if cache:
+            props = torch.cuda.get_device_properties(self.device)
+            total = sum(self.get_state(cap=0, member=m)["n"] for m in range(len(self.members)))
+            key = "%s|sm%d|dim%d|prec%d|members%d|particles2^%d" % (
+                props.name, props.multi_processor_count, self.p.dim, self.p.precision,
+                len(self.members), max(0, int(total).bit_length()))
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except (OSError, ValueError):
+                known = {}
+            if key in known:
+                b, ppt, per, ms = known[key]
+                self.set_launch(b, ppt, per)
+                return {"block": b, "particles_per_thread": ppt, "blocks_per_sm": per, "ms": ms, "cached": True}
+        buf = self.checkpoint_buffer()
+        best = (C.c_int * 3)()
+        ms = C.c_float()
+        _check(load().ugkwp_autotune(self.h, C.c_void_p(_ptr(buf)), buf.numel(), steps,
+                                     C.c_void_p(_stream_ptr(self.stream)), best, C.byref(ms)), self.h)
+        out = {"block": best[0], "particles_per_thread": best[1], "blocks_per_sm": best[2],
+               "ms": ms.value, "cached": False}
+        if cache:
+            import os
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except (OSError, ValueError):
+                known = {}
+            known[key] = [best[0], best[1], best[2], ms.value]
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(known, f, indent=1)
+        return out
 
     def attach_records(self, cap: int):
         import torch

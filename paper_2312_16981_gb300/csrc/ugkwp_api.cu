@@ -18,6 +18,7 @@ struct ugkwp_handle {
   std::vector<Dev> members;     // every member's descriptor (host copy of the device table)
   ugkwp::Ens ens{};             // device view of the ensemble (used when M > 1)
   int M = 1;
+  ugkwp::StreamShape shape;     // launch shape of the particle kernel
   ugkwp_problem p;     // scalars of member 0; host pointers cleared after init
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -362,6 +363,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   E.total_cells = cell0[n];
   E.max_parts = ugkwp::scan_parts(max_bins);
   E.max_G = max_G;
+  E.tile = h->shape.block * h->shape.ppt;
   h->d = h->members[0];
   h->p.nu_edges = h->p.sigma0 = h->p.cv = h->p.T0 = h->p.rho0 = h->p.src_T = nullptr;
   *out = h;
@@ -382,7 +384,7 @@ cudaError_t enqueue_step(const ugkwp_handle* h, cudaStream_t s) {
   const ugkwp::Ens* e = h->M > 1 ? &h->ens : nullptr;
   cudaError_t r = ugkwp::launch_birth_and_scan(d, e, s);
   if (!r) r = ugkwp::launch_wave(d, e, s);
-  if (!r) r = ugkwp::launch_stream(d, e, s);
+  if (!r) r = ugkwp::launch_stream(d, e, h->shape, s);
   if (!r) r = ugkwp::launch_si(d, e, s);
   if (!r) r = ugkwp::launch_end_step(d, e, s);
   return r;
@@ -437,7 +439,7 @@ int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms) {
   if (!e) e = cudaEventRecord(ev[1], s);
   if (!e) e = ugkwp::launch_wave(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[2], s);
-  if (!e) e = ugkwp::launch_stream(h->d, en, s);
+  if (!e) e = ugkwp::launch_stream(h->d, en, h->shape, s);
   if (!e) e = cudaEventRecord(ev[3], s);
   if (!e) e = ugkwp::launch_si(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[4], s);
@@ -636,6 +638,105 @@ int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap) {
   h->d.rec_cap = d_records ? cap : 0;
   h->members[0] = h->d;
   drop_graph(h);   // the captured step holds the old record pointer
+  return UGKWP_OK;
+}
+
+int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int blocks_per_sm) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  if ((block != 128 && block != 256 && block != 512) || (particles_per_thread != 1 && particles_per_thread != 2) ||
+      blocks_per_sm < 0)
+    return fail(h, UGKWP_ERR_ARG, "block must be 128, 256 or 512; particles per thread 1 or 2");
+  h->shape.block = block;
+  h->shape.ppt = particles_per_thread;
+  h->shape.blocks_per_sm = blocks_per_sm;
+  h->ens.tile = block * particles_per_thread;
+  drop_graph(h);
+  return UGKWP_OK;
+}
+
+int ugkwp_checkpoint_size(const ugkwp_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(nullptr, UGKWP_ERR_ARG, "NULL argument");
+  size_t tot = align256(sizeof(size_t) * (size_t)h->M);
+  for (int m = 0; m < h->M; ++m) tot += ugkwp::ckpt_bytes(h->members[m]);
+  *bytes = tot;
+  return UGKWP_OK;
+}
+
+namespace {
+int checkpoint_io(ugkwp_handle* h, void* d_buf, size_t bytes, void* stream, int save) {
+  size_t need = 0;
+  ugkwp_checkpoint_size(h, &need);
+  if (!d_buf || bytes < need) return fail(h, UGKWP_ERR_WORKSPACE, "checkpoint buffer smaller than ugkwp_checkpoint_size");
+  if (reinterpret_cast<uintptr_t>(d_buf) % 256) return fail(h, UGKWP_ERR_WORKSPACE, "checkpoint buffer must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<size_t> offs(h->M);
+  size_t o = align256(sizeof(size_t) * (size_t)h->M);
+  for (int m = 0; m < h->M; ++m) { offs[m] = o; o += ugkwp::ckpt_bytes(h->members[m]); }
+  // the member offsets live in the buffer's head (copied from pageable memory: staged before return)
+  CK(cudaMemcpyAsync(d_buf, offs.data(), sizeof(size_t) * h->M, cudaMemcpyHostToDevice, s), h);
+  CK(ugkwp::launch_checkpoint(h->d, h->M > 1 ? &h->ens : nullptr, static_cast<char*>(d_buf),
+                              static_cast<const size_t*>(d_buf), save, s), h);
+  return UGKWP_OK;
+}
+}  // namespace
+
+int ugkwp_checkpoint(ugkwp_handle* h, void* d_buf, size_t bytes, void* stream) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  return checkpoint_io(h, d_buf, bytes, stream, 1);
+}
+
+int ugkwp_restore(ugkwp_handle* h, const void* d_buf, size_t bytes, void* stream) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  return checkpoint_io(h, const_cast<void*>(d_buf), bytes, stream, 0);
+}
+
+int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void* stream, int* best,
+                   float* best_ms) {
+  if (!h || !best) return fail(h, UGKWP_ERR_ARG, "NULL argument");
+  if (steps < 1) return fail(h, UGKWP_ERR_ARG, "steps must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ugkwp_checkpoint(h, d_ckpt, bytes, stream);
+  if (st) return st;
+  const ugkwp::StreamShape keep = h->shape;
+  const int blocks[3] = {128, 256, 512}, ppts[2] = {1, 2}, pers[2] = {0, -1};
+  float best_t = 1e30f;
+  ugkwp::StreamShape best_s = keep;
+  for (int bi = 0; bi < 3; ++bi)
+    for (int pi = 0; pi < 2; ++pi)
+      for (int qi = 0; qi < 2; ++qi) {
+        ugkwp::StreamShape sh;
+        sh.block = blocks[bi];
+        sh.ppt = ppts[pi];
+        // -1: half of what fits (longer persistent loops, fewer resident warps)
+        int occ = 0;
+        if (pers[qi] < 0) {
+          int dev = 0;
+          cudaGetDevice(&dev);
+          occ = 2048 / sh.block / 2;
+          if (occ < 1) occ = 1;
+        }
+        sh.blocks_per_sm = pers[qi] < 0 ? occ : 0;
+        h->shape = sh;
+        h->ens.tile = sh.block * sh.ppt;
+        if ((st = ugkwp_restore(h, d_ckpt, bytes, stream))) return st;
+        float total = 0.f;
+        for (int k = 0; k < steps; ++k) {
+          float ms[6];
+          if ((st = ugkwp_step_timed(h, stream, ms))) return st;
+          total += ms[3];
+        }
+        if (total < best_t) { best_t = total; best_s = sh; }
+      }
+  h->shape = best_s;
+  h->ens.tile = best_s.block * best_s.ppt;
+  drop_graph(h);
+  if ((st = ugkwp_restore(h, d_ckpt, bytes, stream))) return st;
+  CK(cudaStreamSynchronize(s), h);
+  best[0] = best_s.block;
+  best[1] = best_s.ppt;
+  best[2] = best_s.blocks_per_sm;
+  if (best_ms) *best_ms = best_t / steps;
+  (void)keep;
   return UGKWP_OK;
 }
 

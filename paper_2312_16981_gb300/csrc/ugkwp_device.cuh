@@ -201,6 +201,14 @@ struct Ens {
   // totals known on the host (launch shapes)
   long long total_bins, total_fg, total_cells;
   int max_parts, max_G;
+  int tile;               // particles per tile of the particle kernel (block x particles per thread)
+};
+
+// Launch shape of the particle kernel (picked by the autotuner).
+struct StreamShape {
+  int block = 256;        // threads per block: 128, 256 or 512
+  int ppt = 1;            // particles per thread per tile: 1 or 2
+  int blocks_per_sm = 0;  // 0: as many as fit
 };
 
 // Member owning global index i: largest m with tab[m] <= i.

@@ -11,9 +11,13 @@ int scan_parts(long long n);
 cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t* off,
                         unsigned long long* total_a, unsigned long long* total_b, cudaStream_t s);
 cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s);
-cudaError_t launch_stream(const Dev& d, const Ens* e, cudaStream_t s);
+cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s);
 cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s);
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s);
+
+size_t ckpt_bytes(const Dev& d);
+cudaError_t launch_checkpoint(const Dev& d, const Ens* e, char* buf, const size_t* d_offs, int save,
+                              cudaStream_t s);
 
 // message returned by ugkwp_last_error(NULL)
 void set_global_error(const char* msg);

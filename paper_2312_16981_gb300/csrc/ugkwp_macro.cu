@@ -271,9 +271,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply_ens(const Ens e) {
 }
 
 // Ensemble: prefix over members of this step's particle tiles (survivors +
-// newborns, tiles of kParticleTile), one block; also resets the barrier.
-constexpr int kParticleTile = 256;
+// newborns, tiles of e.tile particles), one block; also resets the barrier.
 __global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
+  const unsigned long long kParticleTile = (unsigned long long)e.tile;
   __shared__ int s_carry;
   if (threadIdx.x == 0) { s_carry = 0; *e.bar = 0u; }
   __syncthreads();
@@ -872,6 +872,104 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
       ctrl->bnd_out_part = pout / d.c;
     }
   }
+}
+
+// --------------------------------------------------------------------------
+// Checkpoint / restore of a member's state in a caller buffer laid out as
+// [Ctrl][T][rho][rho_h][rho_p][particle arrays, capacity entries each].
+// Only the particles alive in the current buffer are copied; their count is
+// read on the device (from the live control block when saving, from the
+// saved one when restoring), so neither direction synchronises the host.
+struct CkptLayout {
+  size_t ctrl, T, rho, rho_h, rho_p, part[8], total;
+};
+
+__host__ __device__ inline size_t ckpt_align(size_t x) { return (x + 255) & ~size_t(255); }
+
+__host__ __device__ inline CkptLayout ckpt_layout(const Dev& d) {
+  CkptLayout L;
+  const size_t nc = (size_t)d.ncell, ncg = (size_t)d.ncell * d.G, P = (size_t)d.capacity;
+  const size_t fs = d.precision == 1 ? 4 : 8;
+  size_t o = 0;
+  L.ctrl = o; o = ckpt_align(o + sizeof(Ctrl));
+  L.T = o; o = ckpt_align(o + 8 * nc);
+  L.rho = o; o = ckpt_align(o + 8 * ncg);
+  L.rho_h = o; o = ckpt_align(o + 8 * ncg);
+  L.rho_p = o; o = ckpt_align(o + 8 * ncg);
+  for (int k = 0; k < 6; ++k) { L.part[k] = o; o = ckpt_align(o + fs * P); }   // x y ox oy nu w
+  L.part[6] = o; o = ckpt_align(o + 8 * P);                                   // id
+  L.part[7] = o; o = ckpt_align(o + 4 * P);                                   // key
+  L.total = o;
+  return L;
+}
+
+size_t ckpt_bytes(const Dev& d) { return ckpt_layout(d).total; }
+
+template <typename TT>
+__device__ __forceinline__ void copy_n(TT* dst, const TT* src, long long n) {
+  if (!dst || !src) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// save = 1: state -> buf; save = 0: buf -> state.  Member = blockIdx.y.
+__global__ void k_checkpoint(const Ens e, const __grid_constant__ Dev d0, char* buf, const size_t* offs, int save) {
+  const Dev& d = e.M > 1 ? e.devs[blockIdx.y] : d0;
+  char* b = buf + offs[blockIdx.y];
+  const CkptLayout L = ckpt_layout(d);
+  Ctrl* saved = reinterpret_cast<Ctrl*>(b + L.ctrl);
+  const Ctrl* src_ctrl = save ? d.ctrl : saved;
+  const unsigned cur = src_ctrl->cur;
+  const long long n = (long long)src_ctrl->n_part[cur];
+  const long long nc = d.ncell, ncg = (long long)d.ncell * d.G;
+  double* T = reinterpret_cast<double*>(b + L.T);
+  double* rho = reinterpret_cast<double*>(b + L.rho);
+  double* rho_h = reinterpret_cast<double*>(b + L.rho_h);
+  double* rho_p = reinterpret_cast<double*>(b + L.rho_p);
+  if (save) {
+    copy_n(T, (const double*)d.T, nc);
+    copy_n(rho, (const double*)d.rho, ncg);
+    copy_n(rho_h, (const double*)d.rho_h, ncg);
+    copy_n(rho_p, (const double*)d.rho_p, ncg);
+  } else {
+    copy_n(d.T, (const double*)T, nc);
+    copy_n(d.rho, (const double*)rho, ncg);
+    copy_n(d.rho_h, (const double*)rho_h, ncg);
+    copy_n(d.rho_p, (const double*)rho_p, ncg);
+  }
+  if (d.precision == 1) {
+    float* live[6] = {d.fx[cur], d.fy[cur], d.fox[cur], d.foy[cur], d.fnu[cur], d.fw[cur]};
+    for (int k = 0; k < 6; ++k) {
+      float* c = reinterpret_cast<float*>(b + L.part[k]);
+      if (save) copy_n(c, (const float*)live[k], n); else copy_n(live[k], (const float*)c, n);
+    }
+  } else {
+    double* live[6] = {d.px[cur], d.py[cur], d.pox[cur], d.poy[cur], d.pnu[cur], d.pw[cur]};
+    for (int k = 0; k < 6; ++k) {
+      double* c = reinterpret_cast<double*>(b + L.part[k]);
+      if (save) copy_n(c, (const double*)live[k], n); else copy_n(live[k], (const double*)c, n);
+    }
+  }
+  unsigned long long* cid = reinterpret_cast<unsigned long long*>(b + L.part[6]);
+  uint32_t* ckey = reinterpret_cast<uint32_t*>(b + L.part[7]);
+  if (save) {
+    copy_n(cid, (const unsigned long long*)d.pid[cur], n);
+    copy_n(ckey, (const uint32_t*)d.pkey[cur], n);
+  } else {
+    copy_n(d.pid[cur], (const unsigned long long*)cid, n);
+    copy_n(d.pkey[cur], (const uint32_t*)ckey, n);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (save) *saved = *d.ctrl; else *d.ctrl = *saved;
+  }
+}
+
+cudaError_t launch_checkpoint(const Dev& d, const Ens* e, char* buf, const size_t* d_offs, int save,
+                              cudaStream_t s) {
+  const Ens none{};
+  const int M = e && e->M > 1 ? e->M : 1;
+  k_checkpoint<<<dim3(152 * 4, M), 256, 0, s>>>(e && e->M > 1 ? *e : none, d, buf, d_offs, save);
+  return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------

@@ -18,7 +18,6 @@
 
 namespace ugkwp {
 
-constexpr int kStreamThreads = 256;
 
 // largest b with off[b] <= j, for off[0] = 0 <= j < off[nbins]
 __device__ __forceinline__ int find_bin(const uint32_t* __restrict__ off, int nbins, uint32_t j) {
@@ -141,19 +140,20 @@ __device__ __forceinline__ void flush_counters(Ctrl* ctrl, Counters& c) {
   c = Counters();
 }
 
-__device__ __forceinline__ long long tiles_of(const Dev& d) {
+__device__ __forceinline__ long long tiles_of(const Dev& d, long long tile) {
   const Ctrl* ctrl = d.ctrl;
   const long long n = (long long)ctrl->n_part[ctrl->cur] + (long long)ctrl->n_new;
-  return (n + kStreamThreads - 1) / kStreamThreads;
+  return (n + tile - 1) / tile;
 }
 
-template <int DIM, bool ENS>
-__global__ void __launch_bounds__(kStreamThreads) k_stream64(const __grid_constant__ Dev d0, const Ens e) {
+template <int DIM, bool ENS, int PPT>
+__global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev d0, const Ens e) {
   Counters cnt;
   int acc_m = 0;
-  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0);
-  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
+  const long long tile = (long long)blockDim.x * PPT;   // PPT sub-tiles of one particle per thread
+  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
+  int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
   const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
   if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
   const Dev& d = ENS ? e.devs[m] : d0;
@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(const __grid_consta
   const double* __restrict__ in_w = d.pw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-  {
-    const long long i = lt * kStreamThreads + threadIdx.x;
+  for (int sub = 0; sub < PPT; ++sub, ++tile_iter) {
+    const long long i = lt * tile + (long long)sub * blockDim.x + threadIdx.x;
     const bool valid = i < n_tot;
     double x = 0.0, y = 0.0, ox = 0.0, oy = 0.0, nu = 0.0, w = 0.0;
     unsigned long long id = 0ull;
@@ -381,13 +381,14 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream64(const __grid_consta
 // Mixed precision (FP32 particle state and arithmetic, FP64 tallies): the
 // same algorithm as k_stream64 with positions held relative to the cell
 // (0 <= xi <= dx) and FP32 uniforms from the same Philox words.  A survivor costs 28 B read and 28 B written in 1D.
-template <int DIM, bool ENS>
-__global__ void __launch_bounds__(kStreamThreads) k_stream32(const __grid_constant__ Dev d0, const Ens e) {
+template <int DIM, bool ENS, int PPT>
+__global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_constant__ Dev d0, const Ens e) {
   Counters cnt;
   int acc_m = 0;
-  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0);
-  int tile_iter = 0;   // per-block count of tiles: parity of the shared slots
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tile_iter) {
+  const long long tile = (long long)blockDim.x * PPT;   // PPT sub-tiles of one particle per thread
+  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
+  int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
   const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
   if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
   const Dev& d = ENS ? e.devs[m] : d0;
@@ -410,8 +411,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(const __grid_consta
   const float* __restrict__ in_w = d.fw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-  {
-    const long long i = lt * kStreamThreads + threadIdx.x;
+  for (int sub = 0; sub < PPT; ++sub, ++tile_iter) {
+    const long long i = lt * tile + (long long)sub * blockDim.x + threadIdx.x;
     const bool valid = i < n_tot;
     float xi = 0.f, eta = 0.f, ox = 0.f, oy = 0.f, nu = 0.f, w = 0.f;
     unsigned long long id = 0ull;
@@ -611,34 +612,43 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream32(const __grid_consta
   flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
-static int g_stream_blocks[2][3][2] = {};
+static int g_stream_occ[2][3][2][3][3] = {};   // [mixed][dim][ens][ppt][block index]
 
-template <int DIM, bool ENS>
-static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, cudaStream_t s) {
+template <int DIM, bool ENS, int PPT>
+static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, const StreamShape& sh,
+                                   cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = mixed ? (const void*)k_stream32<DIM, ENS> : (const void*)k_stream64<DIM, ENS>;
-  int& per = g_stream_blocks[mixed][DIM][ENS];
-  if (!per) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kStreamThreads, 0);
-    if (per < 1) per = 1;
+  const void* fn = mixed ? (const void*)k_stream32<DIM, ENS, PPT> : (const void*)k_stream64<DIM, ENS, PPT>;
+  const int bi = sh.block == 128 ? 0 : (sh.block == 512 ? 2 : 1);
+  int& occ = g_stream_occ[mixed][DIM][ENS][PPT][bi];
+  if (!occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.block, 0);
+    if (occ < 1) occ = 1;
   }
+  int per = sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ;
   const int blocks = sms * per;
-  if (mixed) k_stream32<DIM, ENS><<<blocks, kStreamThreads, 0, s>>>(d, e);
-  else k_stream64<DIM, ENS><<<blocks, kStreamThreads, 0, s>>>(d, e);
+  if (mixed) k_stream32<DIM, ENS, PPT><<<blocks, sh.block, 0, s>>>(d, e);
+  else k_stream64<DIM, ENS, PPT><<<blocks, sh.block, 0, s>>>(d, e);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream(const Dev& d, const Ens* e, cudaStream_t s) {
-  const int mixed = d.precision == 1;
-  if (e && e->M > 1) {
-    if (d.dim == 2) return launch_stream_t<2, true>(d, *e, mixed, s);
-    return launch_stream_t<1, true>(d, *e, mixed, s);
+template <bool ENS>
+static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s) {
+  if (d.dim == 2) {
+    if (sh.ppt == 2) return launch_stream_t<2, ENS, 2>(d, e, mixed, sh, s);
+    return launch_stream_t<2, ENS, 1>(d, e, mixed, sh, s);
   }
+  if (sh.ppt == 2) return launch_stream_t<1, ENS, 2>(d, e, mixed, sh, s);
+  return launch_stream_t<1, ENS, 1>(d, e, mixed, sh, s);
+}
+
+cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s) {
+  const int mixed = d.precision == 1;
+  if (e && e->M > 1) return launch_stream_dim<true>(d, *e, mixed, sh, s);
   const Ens none{};
-  if (d.dim == 2) return launch_stream_t<2, false>(d, none, mixed, s);
-  return launch_stream_t<1, false>(d, none, mixed, s);
+  return launch_stream_dim<false>(d, none, mixed, sh, s);
 }
 
 }  // namespace ugkwp
