@@ -107,6 +107,17 @@ def lib():
             _dp, _dp, _dp, _dp, C.POINTER(CParticles), C.c_int64, C.POINTER(C.c_int64),
             C.c_void_p, C.c_int64, C.POINTER(CTallies)]
         L.or_init_rho.argtypes = [C.POINTER(CProblem), _dp, _dp]
+        L.or_dsigma_group.argtypes = [C.POINTER(CProblem), C.c_int, C.c_int, C.c_double,
+                                      C.c_double, C.c_double]
+        L.or_dsigma_group.restype = C.c_double
+        L.or_dcoefs.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
+        L.or_wave_flux_tangent.argtypes = [C.POINTER(CProblem), _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_source_iteration_tangent.argtypes = [C.POINTER(CProblem), _dp, _dp, _dp, _dp, _dp,
+                                                  _dp, _dp, C.POINTER(C.c_int)]
+        L.or_step_tangent.argtypes = [
+            C.POINTER(CProblem), C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int64,
+            C.POINTER(CParticles), _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+            C.POINTER(CParticles), _dp, C.c_int64, C.POINTER(C.c_int64), C.POINTER(CTallies)]
         _lib = L
     return _lib
 
@@ -375,3 +386,110 @@ def step(prob: OracleProblem, st: State, records: bool = False, cap_out: Optiona
     if rec is not None:
         rec = rec[:rec_cap]
     return new, tal, rec, status
+
+
+# ---------------------------------------------------------------------------
+# pathwise derivative (tangent) with respect to the per-cell log-opacity scales
+
+def dsigma_group(prob: OracleProblem, c: int, g: int, T: float, ds: float, dT: float) -> float:
+    return lib().or_dsigma_group(prob.ref, c, g, T, ds, dT)
+
+
+def dcoefs(x: float):
+    """x-derivatives (f2', f4', f5', c4') of the flux coefficients."""
+    o = [C.c_double() for _ in range(4)]
+    lib().or_dcoefs(x, *[C.byref(v) for v in o])
+    return tuple(v.value for v in o)
+
+
+def wave_flux_tangent(prob: OracleProblem, T, dT, ds, rho_h, drho_h, e_eff) -> np.ndarray:
+    p = prob.p
+    out = np.zeros(p.nface * p.G)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (T, dT, ds, rho_h, drho_h, e_eff)]
+    lib().or_wave_flux_tangent(prob.ref, *[_d(v) for v in a], _d(out))
+    return out
+
+
+def source_iteration_tangent(prob: OracleProblem, dT_n, ds, dR, T, rho):
+    p = prob.p
+    dT = np.zeros(p.ncell)
+    drho = np.zeros(p.ncell * p.G)
+    it = C.c_int()
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (dT_n, ds, dR, T, rho)]
+    st = lib().or_source_iteration_tangent(prob.ref, *[_d(v) for v in a], _d(dT), _d(drho), C.byref(it))
+    return st, dT, drho, it.value
+
+
+class Tangent:
+    """Tangent of a state: dT, drho, drho_h and one weight tangent per particle."""
+
+    def __init__(self, p, dT, drho, drho_h, dw):
+        self.dT, self.drho, self.drho_h, self.dw = dT, drho, drho_h, dw
+
+    @staticmethod
+    def zero(st: State) -> "Tangent":
+        p = st.p
+        return Tangent(p, np.zeros(p.ncell), np.zeros(p.ncell * p.G), np.zeros(p.ncell * p.G),
+                       np.zeros(max(st.particles.cap, 1)))
+
+
+def step_tangent(prob: OracleProblem, st: State, tg: Tangent, ds, cap_out: Optional[int] = None):
+    """One step and its tangent along ds (log-opacity scales) and tg.
+    Returns (new_state, new_tangent, tallies, status)."""
+    p = prob.p
+    pin = st.particles
+    cap = cap_out if cap_out is not None else max(p.particle_capacity, 16)
+    pout = ParticleSet(cap)
+    ncg = p.ncell * p.G
+    T_out, dT_out = np.zeros(p.ncell), np.zeros(p.ncell)
+    rho_out, drho_out = np.zeros(ncg), np.zeros(ncg)
+    rho_h_out, drho_h_out, rho_p_out = np.zeros(ncg), np.zeros(ncg), np.zeros(ncg)
+    dw_out = np.zeros(cap)
+    dw_in = np.ascontiguousarray(tg.dw, dtype=np.float64)
+    if len(dw_in) < max(pin.n, 1):
+        raise ValueError("weight tangents shorter than the particle set")
+    tal = Tallies(p)
+    n_out = C.c_int64(0)
+    cin, cout = pin.cstruct(), pout.cstruct()
+    ds = np.ascontiguousarray(ds, dtype=np.float64)
+    status = lib().or_step_tangent(
+        prob.ref, st.step, _d(ds), _d(st.T), _d(tg.dT), _d(st.rho), _d(tg.drho), _d(st.rho_h),
+        _d(tg.drho_h), pin.n, C.byref(cin), _d(dw_in), _d(T_out), _d(dT_out), _d(rho_out),
+        _d(drho_out), _d(rho_h_out), _d(drho_h_out), _d(rho_p_out), C.byref(cout), _d(dw_out), cap,
+        C.byref(n_out), C.byref(tal.c))
+    pout.n = min(n_out.value, cap)
+    new = State(p, T_out, rho_out, rho_h_out, pout, st.step + 1)
+    new.rho_p = rho_p_out
+    return new, Tangent(p, dT_out, drho_out, drho_h_out, dw_out), tal, status
+
+
+def with_log_opacity(p, s):
+    """The problem with sigma0_c scaled by exp(s_c)."""
+    return p.replace(sigma0=np.asarray(p.sigma0, dtype=np.float64) * np.exp(np.asarray(s, dtype=np.float64)))
+
+
+def misfit(p, steps: int, T_target, cap: Optional[int] = None, records: bool = False):
+    """L = sum_c (T_c - T_target_c)^2 after `steps` oracle steps from the
+    initial state; also the per-step records (decisions) when asked."""
+    prob = OracleProblem(p)
+    st = initial_state(prob)
+    recs = []
+    for _ in range(steps):
+        st, _, rec, status = step(prob, st, records=records, cap_out=cap)
+        if status != 0:
+            raise RuntimeError("oracle step failed with status %d" % status)
+        recs.append(rec)
+    return float(np.sum((st.T - T_target) ** 2)), st, recs
+
+
+def misfit_tangent(p, steps: int, T_target, ds, cap: Optional[int] = None):
+    """(L, dL) with dL the pathwise directional derivative of L along ds."""
+    prob = OracleProblem(p)
+    st = initial_state(prob)
+    tg = Tangent.zero(st)
+    for _ in range(steps):
+        st, tg, _, status = step_tangent(prob, st, tg, ds, cap_out=cap)
+        if status != 0:
+            raise RuntimeError("oracle tangent step failed with status %d" % status)
+    r = st.T - T_target
+    return float(np.sum(r * r)), float(np.sum(2.0 * r * tg.dT)), st

@@ -1,6 +1,7 @@
 """Build step for the CPU oracle (test infrastructure only).
 
-Compiles ``ugkwp_oracle.c`` with gcc into ``liboracle.so`` beside it.
+Compiles ``ugkwp_oracle.c`` (the step) and ``ugkwp_oracle_tangent.c`` (its
+pathwise derivative) with gcc into ``liboracle.so`` beside them.
 ``-ffp-contract=off`` keeps the arithmetic identical on x86-64 and AArch64
 (no fused multiply-adds are formed on either).
 """
@@ -8,18 +9,18 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "ugkwp_oracle.c")
+SRCS = [os.path.join(HERE, f) for f in ("ugkwp_oracle.c", "ugkwp_oracle_tangent.c")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "ugkwp_oracle.h"))
+        [os.path.getmtime(s) for s in SRCS] + [os.path.getmtime(os.path.join(HERE, "ugkwp_oracle.h"))]
     ):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-Wall", "-Wno-unused-function", SRC, "-o", tmp, "-lm"]
+           "-Wall", "-Wno-unused-function", *SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

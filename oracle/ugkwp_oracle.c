@@ -706,6 +706,30 @@ int or_step(const or_problem* P, int64_t step,
             or_particles* pout, int64_t cap_out, int64_t* n_out,
             or_record* rec, int64_t rec_cap,
             or_tallies* tal) {
+  return or_step_core(P, step, T, rho, rho_h, n_in, pin, T_out, rho_out, rho_h_out, rho_p_out,
+                      pout, cap_out, n_out, rec, rec_cap, tal, NULL, NULL, NULL, NULL);
+}
+
+/* A particle streamed a second time from the same start (same identity,
+ * step and draws, hence the same path) carrying another weight into another
+ * set of tallies. */
+static void restream(const or_problem* P, const double* T, int64_t step, double x, double y,
+                     double ox, double oy, double nu, double w, uint64_t id, int32_t cell,
+                     int32_t g, int newborn, int64_t first_draw, or_tallies* tal) {
+  int32_t nseg;
+  double tend;
+  or_stream_particle(P, T, step, &x, &y, &ox, &oy, nu, w, id, &cell, g, newborn, first_draw,
+                     NULL, 0, tal, &nseg, &tend, NULL, NULL, 0, NULL);
+}
+
+int or_step_core(const or_problem* P, int64_t step,
+                 const double* T, const double* rho, const double* rho_h,
+                 int64_t n_in, const or_particles* pin,
+                 double* T_out, double* rho_out, double* rho_h_out, double* rho_p_out,
+                 or_particles* pout, int64_t cap_out, int64_t* n_out,
+                 or_record* rec, int64_t rec_cap,
+                 or_tallies* tal,
+                 const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2) {
   const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1, G = P->G, ncell = nx * ny;
   const int nface = nface_of(P), nxf = nxface_of(P);
   const double V = vol_of(P), dt = P->dt;
@@ -744,6 +768,8 @@ int or_step(const or_problem* P, int64_t step,
     double x = pin->x[i], y = pin->y[i], ox = pin->ox[i], oy = pin->oy[i];
     int32_t cell = pin->cell[i], cell0 = cell, nseg;
     double tend;
+    if (tal2)
+      restream(P, T, step, x, y, ox, oy, pin->nu[i], w2_in[i], pin->id[i], cell, pin->grp[i], 0, 0, tal2);
     int fate = or_stream_particle(P, T, step, &x, &y, &ox, &oy, pin->nu[i], pin->w[i], pin->id[i],
                                   &cell, pin->grp[i], 0, 0, NULL, 0, tal, &nseg, &tend,
                                   NULL, NULL, 0, NULL);
@@ -754,6 +780,7 @@ int or_step(const or_problem* P, int64_t step,
         pout->x[nout] = x; pout->y[nout] = y; pout->ox[nout] = ox; pout->oy[nout] = oy;
         pout->nu[nout] = pin->nu[i]; pout->w[nout] = pin->w[i]; pout->id[nout] = pin->id[i];
         pout->cell[nout] = cell; pout->grp[nout] = pin->grp[i];
+        if (w2_out) w2_out[nout] = w2_in[i];
       } else status = OR_ERR_CAPACITY;
       ++nout;
     } else if (fate == OR_ABSORBED) ++tal->n_absorbed;
@@ -807,6 +834,7 @@ int or_step(const or_problem* P, int64_t step,
       if (!P->grey) nu = or_sample_nu(P->nu_edges[g], P->nu_edges[g + 1], Tb, or_draw(P, id, step, j++));
       int32_t cell0 = cell, nseg;
       double tend, w = tal->omega[b];
+      if (tal2) restream(P, T, step, x, y, ox, oy, nu, w2_bins[b], id, cell, g, 1, j, tal2);
       int fate = or_stream_particle(P, T, step, &x, &y, &ox, &oy, nu, w, id, &cell, g, 1, j,
                                     NULL, 0, tal, &nseg, &tend, NULL, NULL, 0, NULL);
       tal->n_segments += nseg;
@@ -816,6 +844,7 @@ int or_step(const or_problem* P, int64_t step,
           pout->x[nout] = x; pout->y[nout] = y; pout->ox[nout] = ox; pout->oy[nout] = oy;
           pout->nu[nout] = nu; pout->w[nout] = w; pout->id[nout] = id;
           pout->cell[nout] = cell; pout->grp[nout] = g;
+          if (w2_out) w2_out[nout] = w2_bins[b];
         } else status = OR_ERR_CAPACITY;
         ++nout;
       } else if (fate == OR_ABSORBED) ++tal->n_absorbed;

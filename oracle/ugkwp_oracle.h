@@ -132,6 +132,44 @@ int or_step(const or_problem* P, int64_t step,
             or_record* rec, int64_t rec_cap,
             or_tallies* tal);
 
+/* or_step with an optional second weight per particle: when tal2 != NULL
+ * every particle is streamed once more along the same path carrying w2_in[i]
+ * (survivors in) or w2_bins[b] (newborns of bin b) into tal2 (W, E_surv,
+ * E_abs, esc, inflow; zeroed by the caller), and survivors carry their
+ * second weight to w2_out in output order.  The tangent step uses it: the
+ * particle tallies are linear in the weights along a fixed path. */
+int or_step_core(const or_problem* P, int64_t step,
+                 const double* T, const double* rho, const double* rho_h,
+                 int64_t n_in, const or_particles* pin,
+                 double* T_out, double* rho_out, double* rho_h_out, double* rho_p_out,
+                 or_particles* pout, int64_t cap_out, int64_t* n_out,
+                 or_record* rec, int64_t rec_cap,
+                 or_tallies* tal,
+                 const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2);
+
+/* --- tangent (forward-mode pathwise derivative), ugkwp_oracle_tangent.c ---
+ * Directions: ds[c] changes the log of sigma0_c; dT, drho, drho_h and the
+ * particles' weight tangents change the incoming state.  Every discrete
+ * decision of the step is held fixed (common random numbers). */
+double or_dsigma_group(const or_problem* P, int c, int g, double T, double ds, double dT);
+void   or_dcoefs(double x, double* df2, double* df4, double* df5, double* dc4);
+int    or_wave_flux_tangent(const or_problem* P, const double* T, const double* dT,
+                            const double* ds, const double* rho_h, const double* drho_h,
+                            const double* e_eff, double* dFwave);
+/* T, rho: the converged solution of the source iteration; dR: tangent of its
+ * constant part R. */
+int    or_source_iteration_tangent(const or_problem* P, const double* dT_n, const double* ds,
+                                   const double* dR, const double* T, const double* rho,
+                                   double* dT_out, double* drho_out, int* iters);
+int    or_step_tangent(const or_problem* P, int64_t step, const double* ds,
+                       const double* T, const double* dT, const double* rho, const double* drho,
+                       const double* rho_h, const double* drho_h,
+                       int64_t n_in, const or_particles* pin, const double* dw_in,
+                       double* T_out, double* dT_out, double* rho_out, double* drho_out,
+                       double* rho_h_out, double* drho_h_out, double* rho_p_out,
+                       or_particles* pout, double* dw_out, int64_t cap_out, int64_t* n_out,
+                       or_tallies* tal);
+
 /* Initial equilibrium rho_g = Phi_g(T0) per cell. */
 void or_init_rho(const or_problem* P, const double* T0, double* rho);
 
