@@ -707,7 +707,7 @@ int or_step(const or_problem* P, int64_t step,
             or_record* rec, int64_t rec_cap,
             or_tallies* tal) {
   return or_step_core(P, step, T, rho, rho_h, n_in, pin, T_out, rho_out, rho_h_out, rho_p_out,
-                      pout, cap_out, n_out, rec, rec_cap, tal, NULL, NULL, NULL, NULL);
+                      pout, cap_out, n_out, rec, rec_cap, tal, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* A particle streamed a second time from the same start (same identity,
@@ -729,7 +729,8 @@ int or_step_core(const or_problem* P, int64_t step,
                  or_particles* pout, int64_t cap_out, int64_t* n_out,
                  or_record* rec, int64_t rec_cap,
                  or_tallies* tal,
-                 const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2) {
+                 const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2,
+                 double* w2_scale) {
   const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1, G = P->G, ncell = nx * ny;
   const int nface = nface_of(P), nxf = nxface_of(P);
   const double V = vol_of(P), dt = P->dt;
@@ -892,17 +893,43 @@ int or_step_core(const or_problem* P, int64_t step,
   tal->si_iters = iters;
   free(R);
 
-  /* wave / particle split and energy ledger */
+  /* wave / particle split and energy ledger.  Reading (the paper is silent
+   * on it): the collisionless survivors of a (cell, group) never hold more
+   * energy than rho^{n+1} leaves there.  Where E_surv/V > rho^{n+1} their
+   * weights are scaled by f = max(rho^{n+1}, 0) V / E_surv, so that
+   * rho^p = max(rho^{n+1}, 0) and rho^h = rho^{n+1} - rho^p >= min(rho^{n+1}, 0);
+   * rho^{n+1} and the energy are unchanged.  Without it a cold cell crossed by
+   * many survivors accumulates a negative wave part that the source
+   * iteration takes out of the material, until T^{n+1} has no positive
+   * solution. */
+  double* fscale = malloc(sizeof(double) * (size_t)ncell * G);
+  int any_scaled = 0;
   tal->E_rad1 = tal->E_mat1 = 0.0;
   for (int c = 0; c < ncell; ++c) {
     for (int g = 0; g < G; ++g) {
-      double rp = tal->E_surv[c * G + g] / V;
-      rho_p_out[c * G + g] = rp;
-      rho_h_out[c * G + g] = rho_out[c * G + g] - rp;
-      tal->E_rad1 += V * rho_out[c * G + g] / P->c;
+      const int i = c * G + g;
+      double rp = tal->E_surv[i] / V, r = rho_out[i];
+      fscale[i] = 1.0;
+      if (rp > 0.0 && r < rp) {
+        fscale[i] = r > 0.0 ? r / rp : 0.0;
+        rp = r > 0.0 ? r : 0.0;
+        any_scaled = 1;
+      }
+      rho_p_out[i] = rp;
+      rho_h_out[i] = r - rp;
+      tal->E_rad1 += V * r / P->c;
     }
     tal->E_mat1 += V * P->cv[c] * T_out[c];
   }
+  if (any_scaled) {
+    const int64_t m = nout < cap_out ? nout : cap_out;
+    for (int64_t k = 0; k < m; ++k) {
+      const double f = fscale[pout->cell[k] * G + pout->grp[k]];
+      if (f != 1.0) pout->w[k] *= f;
+    }
+  }
+  if (w2_scale) memcpy(w2_scale, fscale, sizeof(double) * (size_t)ncell * G);
+  free(fscale);
   double bin = 0.0;
   for (int axis = 0; axis < P->dim; ++axis) {
     const int nk = axis == 0 ? nx : ny, nlines = axis == 0 ? ny : nx;

@@ -136,8 +136,10 @@ int or_step(const or_problem* P, int64_t step,
  * every particle is streamed once more along the same path carrying w2_in[i]
  * (survivors in) or w2_bins[b] (newborns of bin b) into tal2 (W, E_surv,
  * E_abs, esc, inflow; zeroed by the caller), and survivors carry their
- * second weight to w2_out in output order.  The tangent step uses it: the
- * particle tallies are linear in the weights along a fixed path. */
+ * second weight to w2_out in output order (before the end-of-step weight
+ * scaling, whose factors per (cell, group) go to w2_scale when it is not
+ * NULL).  The tangent step uses it: the particle tallies are linear in the
+ * weights along a fixed path. */
 int or_step_core(const or_problem* P, int64_t step,
                  const double* T, const double* rho, const double* rho_h,
                  int64_t n_in, const or_particles* pin,
@@ -145,7 +147,8 @@ int or_step_core(const or_problem* P, int64_t step,
                  or_particles* pout, int64_t cap_out, int64_t* n_out,
                  or_record* rec, int64_t rec_cap,
                  or_tallies* tal,
-                 const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2);
+                 const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2,
+                 double* w2_scale);
 
 /* --- tangent (forward-mode pathwise derivative), ugkwp_oracle_tangent.c ---
  * Directions: ds[c] changes the log of sigma0_c; dT, drho, drho_h and the

@@ -395,8 +395,9 @@ int or_step_tangent(const or_problem* P, int64_t step, const double* ds,
   dtal.E_abs = calloc(ncg, sizeof(double));
   dtal.esc = calloc(4 * G, sizeof(double));
   dtal.inflow = calloc(4 * G, sizeof(double));
+  double* fscale = malloc(sizeof(double) * ncg);
   int status = or_step_core(P, step, T, rho, rho_h, n_in, pin, T_out, rho_out, rho_h_out, rho_p_out,
-                            pout, cap_out, n_out, NULL, 0, tal, dw_in, dw_bins, dw_out, &dtal);
+                            pout, cap_out, n_out, NULL, 0, tal, dw_in, dw_bins, dw_out, &dtal, fscale);
 
   /* wave flux and the constant part of the rho equation */
   double* dFw = calloc((size_t)nface * G, sizeof(double));
@@ -418,8 +419,33 @@ int or_step_tangent(const or_problem* P, int64_t step, const double* ds,
   int iters = 0;
   int st = or_source_iteration_tangent(P, dT, ds, dR, T_out, rho_out, dT_out, drho_out, &iters);
   if (st && !status) status = st;
-  for (size_t i = 0; i < ncg; ++i) drho_h_out[i] = drho_out[i] - dtal.E_surv[i] / V;
+  /* wave / particle split with the survivors' scaling: where f != 1 the
+   * particle part is max(rho^{n+1}, 0), each survivor's weight w f with
+   * f = rho^{n+1} V / E_surv (or 0), so df = drho^{n+1} V/E_surv
+   * - rho^{n+1} V dE_surv/E_surv^2. */
+  double* df = calloc(ncg, sizeof(double));
+  for (size_t i = 0; i < ncg; ++i) {
+    if (fscale[i] == 1.0) {
+      drho_h_out[i] = drho_out[i] - dtal.E_surv[i] / V;
+    } else if (fscale[i] > 0.0) {
+      drho_h_out[i] = 0.0;
+      double Es = tal->E_surv[i];
+      df[i] = drho_out[i] * V / Es - rho_out[i] * V * dtal.E_surv[i] / (Es * Es);
+    } else {
+      drho_h_out[i] = drho_out[i];
+    }
+  }
+  {
+    const int64_t m = *n_out < cap_out ? *n_out : cap_out;
+    for (int64_t k = 0; k < m; ++k) {
+      const size_t i = (size_t)pout->cell[k] * G + pout->grp[k];
+      const double f = fscale[i];
+      if (f == 1.0) continue;
+      dw_out[k] = f > 0.0 ? dw_out[k] * f + (pout->w[k] / f) * df[i] : 0.0;
+    }
+  }
 
+  free(df); free(fscale);
   free(dw_bins); free(dFw); free(dR);
   free(dtal.W); free(dtal.E_surv); free(dtal.E_abs); free(dtal.esc); free(dtal.inflow);
   return status;

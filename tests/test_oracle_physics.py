@@ -283,3 +283,24 @@ def test_birth_count_rounding():
             if N:
                 assert abs(tal.omega[b] * N - E) <= 1e-15 * E
     assert n_new == tal.N.sum()
+
+
+def test_particle_part_never_exceeds_the_total():
+    """Reading on the wave/particle split: survivors are scaled so that
+    rho_p <= max(rho^{n+1}, 0) in every (cell, group); the survivors' weights
+    then add up to rho_p V, and rho^{n+1} (so the energy) is untouched."""
+    for p in (I.small_checkerboard(n=8, G=3, omega_ref=2e-6), I.small_multigroup(nx=12, G=4, omega_ref=2e-6)):
+        prob = O.OracleProblem(p)
+        st = O.initial_state(prob)
+        V = p.dx * (p.dy if p.dim == 2 else 1.0)
+        scaled = 0
+        for _ in range(4):
+            st, tal, _, status = O.step(prob, st)
+            assert status == 0
+            assert np.all(st.rho_p <= np.maximum(st.rho, 0.0) * (1 + 1e-14) + 1e-300)
+            np.testing.assert_allclose(st.rho_h + st.rho_p, st.rho, rtol=1e-14, atol=1e-300)
+            parts = st.particles.view()
+            sums = np.bincount(parts["cell"] * p.G + parts["grp"], weights=parts["w"], minlength=p.ncell * p.G)
+            np.testing.assert_allclose(sums / V, st.rho_p, rtol=1e-12, atol=1e-300)
+            scaled += int(np.sum(st.rho_p != tal.E_surv / V))
+        assert scaled > 0   # the case exercises the scaling
