@@ -37,7 +37,7 @@ from paper_2312_16981_gb300 import inputs as I  # noqa: E402
 N_PARTICLES = 1_000_000
 WORKLOAD = "multigroup_slab_200x30_fp64"
 METRIC = "particle segments/s"
-KERNELS_PER_STEP = 8   # birth, scan x3, wave, particles, source iteration, end of step
+KERNELS_PER_STEP = 9   # birth, scan x3, wave, particles, source iteration, end of step, survivor scaling
 
 
 def peaks():
@@ -177,6 +177,155 @@ def timed_steps(sim, steps, flush, sampler=None):
     return phases, segs, n_in, n_out, si
 
 
+def device_ms(fn, flush=None):
+    """Device milliseconds of fn() on the current stream (CUDA events)."""
+    import torch
+    if flush is not None:
+        flush.fill_(1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def ensemble_leg(B, dev, flush, steps, warmup, members=256, evolve=100, autotune_cache=None):
+    """256 independent slabs with uneven cells, groups, opacity and boundary
+    temperature, each run from its cold initial state for `evolve` steps
+    (its reference weight is set so that about 1e4-1e6 particles are alive
+    by then): one batched (mixed precision, autotuned) step against the same
+    members stepped one after another, in FP64 and in mixed precision.  All
+    three are timed the same way: CUDA events around one step of every
+    member (CUDA graph replay), L2 flushed before each step."""
+    probs = I.ensemble_slabs(members, steps=evolve)
+    for p in probs:
+        target = 0.25 * p.bcT[0] ** 4 * p.dt * evolve / p.omega_ref
+        p.particle_capacity = int(2.0 * target) + 65536
+
+    def segments(sims_members):
+        tot = alive = 0
+        for sim, mm in sims_members:
+            t = sim.tallies(member=mm)
+            assert t["status_bits"] == 0, (mm, t["status_bits"])
+            tot += t["n_segments"]
+            alive += t["n_particles"]
+        return tot, alive
+
+    out = {"members": members, "evolved_steps": evolve,
+           "cells_x_groups": int(sum(p.ncell * p.G for p in probs))}
+    # batched, mixed precision, autotuned launch shape
+    ens = B.Simulation([p.replace(precision=I.MIXED) for p in probs], device=dev)
+    ens.step(evolve)
+    out["particles_alive"] = segments([(ens, m) for m in range(members)])[1]
+    tune = ens.autotune(steps=2, cache=autotune_cache)
+    for _ in range(max(warmup, 3)):
+        ens.step(1)
+    ms = segs = 0.0
+    for _ in range(steps):
+        ms += device_ms(lambda: ens.step(1), flush)
+        segs += segments([(ens, m) for m in range(members)])[0]
+    out["batched_mixed"] = {"value": segs / (ms / 1e3), "unit": "segments/s",
+                            "ms_per_step": ms / steps, "launch_shape": tune}
+    ens.close()
+    del ens
+    # the same members one after another, one graph each
+    for name, prec in (("sequential_fp64", I.FP64), ("sequential_mixed", I.MIXED)):
+        sims = [B.Simulation(p.replace(precision=prec), device=dev) for p in probs]
+        for sm in sims:
+            sm.step(evolve + max(warmup, 3))
+
+        def all_one():
+            for sm in sims:
+                sm.step(1)
+        ms = segs = 0.0
+        for _ in range(steps):
+            ms += device_ms(all_one, flush)
+            segs += segments([(sm, 0) for sm in sims])[0]
+        out[name] = {"value": segs / (ms / 1e3), "unit": "segments/s", "ms_per_step": ms / steps}
+        for sm in sims:
+            sm.close()
+        del sims
+    b = out["batched_mixed"]["value"]
+    out["speedup_batched_mixed_vs_sequential_fp64"] = b / out["sequential_fp64"]["value"]
+    out["speedup_batched_mixed_vs_sequential_mixed"] = b / out["sequential_mixed"]["value"]
+    return out
+
+
+def matched_error_leg(B, dev, steps=200, seeds=8, refine=16):
+    """Tally error of the mixed build against the FP64 build on the physical
+    200x30 slab run from its initial state: the reference is the mean of
+    `seeds` FP64 runs with `refine` times more particles (omega_ref/refine);
+    each build then runs `seeds` seeds at the workload's omega_ref, and the
+    error is the relative RMS temperature difference from the reference.
+    Same-seed runs of the two builds are also compared directly."""
+    base = I.multigroup_slab()
+
+    def run(prec, omega, seed, cap):
+        p = base.replace(precision=prec, omega_ref=omega, seed=seed, particle_capacity=cap)
+        sim = B.Simulation(p, device=dev)
+        segs, ms = 0, 0.0
+        for _ in range(steps):
+            ms += device_ms(lambda: sim.step(1))
+            t = sim.tallies()
+            segs += t["n_segments"]
+        assert t["status_bits"] == 0, t["status_bits"]
+        st = sim.get_state(cap=0)
+        sim.close()
+        return st["T"], segs, ms, st["n"]
+
+    refs = [run(I.FP64, base.omega_ref / refine, 1000 + r, 1 << 25)[0] for r in range(seeds)]
+    Tref = np.mean(refs, axis=0)
+    # cells the front has reached (elsewhere T stays at T0 in every run)
+    hot = Tref > 2.0 * float(np.min(base.T0))
+
+    def rel_rms(T):
+        return float(np.sqrt(np.mean(((T[hot] - Tref[hot]) / Tref[hot]) ** 2)))
+    res = {}
+    runs = {}
+    for name, prec in (("fp64", I.FP64), ("mixed", I.MIXED)):
+        rs = [run(prec, base.omega_ref, 1 + r, 1 << 23) for r in range(seeds)]
+        runs[name] = rs
+        errs = [rel_rms(r[0]) for r in rs]
+        res[name] = {"rel_rms_T_error": float(np.mean(errs)), "per_seed": errs,
+                     "segments_per_s": sum(r[1] for r in rs) / (sum(r[2] for r in rs) / 1e3),
+                     "particles_at_end": int(np.mean([r[3] for r in rs]))}
+    same = [float(np.max(np.abs(a[0] - b[0]) / a[0])) for a, b in zip(runs["fp64"], runs["mixed"])]
+    ratio = res["mixed"]["rel_rms_T_error"] / res["fp64"]["rel_rms_T_error"]
+    return {"what": "%d steps of the 200x30 slab from its initial state; reference = mean of %d FP64 runs "
+                    "at omega_ref/%d; error = relative RMS of T over the %d cells the front reached, mean "
+                    "over %d seeds" % (steps, seeds, refine, int(hot.sum()), seeds),
+            "fp64": res["fp64"], "mixed": res["mixed"], "error_ratio_mixed_over_fp64": ratio,
+            "matched": bool(ratio <= 1.05),
+            "same_seed_max_rel_T_diff_mixed_vs_fp64": max(same),
+            "reference_self_noise_estimate": float(np.std(refs, axis=0)[hot].mean() / Tref[hot].mean()
+                                                   / np.sqrt(seeds))}
+
+
+def checkerboard_leg(B, dev, flush, steps, warmup, n_particles):
+    """The 2D 256x256 checkerboard (30 groups, thick/thin 16x16 blocks,
+    central T_s = 1 source) from a seeded synthetic state with n_particles
+    particles: FP64 and mixed precision builds, phase times from CUDA events."""
+    p = I.checkerboard_2d()
+    p.particle_capacity = max(p.particle_capacity, int(1.6 * n_particles))
+    s = I.synthetic_state(p, n_particles, seed=3, front=0.35)
+    out = {"workload": "checkerboard_2d_256x256x30", "particles_at_start": n_particles}
+    names = ["total", "birth_scan", "wave", "particles", "source_iteration", "end"]
+    for name, prec in (("fp64", I.FP64), ("mixed", I.MIXED)):
+        sim = B.Simulation(p.replace(precision=prec), device=dev)
+        sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
+        for _ in range(max(warmup, 3)):
+            sim.step(1)
+        ph, segs, n_in, n_out, si = timed_steps(sim, steps, flush)
+        out[name] = {"value": segs / (ph[0] / 1e3), "unit": "segments/s", "ms_per_step": float(ph[0] / steps),
+                     "phase_ms_per_step": {n: float(ph[i] / steps) for i, n in enumerate(names)},
+                     "particles_per_step": n_in / steps, "si_iters_per_step": si / steps}
+        sim.close()
+        del sim
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +339,11 @@ def main():
                     help="timed steps of one precision only (no e2e, mixed or CPU legs): for profiler runs")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="particle precision of the headline (quick) run")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--no-matched-error", action="store_true", help="skip the matched-error leg")
+    ap.add_argument("--ensemble-steps", type=int, default=10)
+    ap.add_argument("--no-checkerboard", action="store_true", help="skip the 2D checkerboard leg")
+    ap.add_argument("--checkerboard-particles", type=int, default=20_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -310,6 +464,15 @@ def main():
         line["gpu_launches"] = KERNELS_PER_STEP * K * 3
     else:
         line["gpu_launches"] = KERNELS_PER_STEP * K
+
+    extra_legs = rank == 0 and world == 1 and not args.quick
+    if extra_legs and not args.no_matched_error:
+        line["matched_error"] = matched_error_leg(B, dev)
+    if extra_legs and not args.no_checkerboard:
+        line["checkerboard_2d"] = checkerboard_leg(B, dev, flush, min(K, 10), args.warmup,
+                                                   args.checkerboard_particles)
+    if extra_legs and not args.no_ensemble:
+        line["batched_ensemble"] = ensemble_leg(B, dev, flush, args.ensemble_steps, args.warmup)
 
     if rank == 0 and not args.no_cpu_baseline and not args.quick:
         n_sample = 100_000

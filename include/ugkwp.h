@@ -221,6 +221,63 @@ int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int b
 int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void* stream, int* best,
                    float* best_ms);
 
+/* ---- adjoint: gradient of a function of the final state with respect to
+ * the per-cell log-opacity scales s_c (sigma0_c -> sigma0_c e^{s_c}) ----
+ * The paper has no adjoint; this is the reverse mode of the step of
+ * Algorithm 1 as implemented here.  The derivative is pathwise: every Monte
+ * Carlo decision of a step (birth counts N, face crossings, collision,
+ * survival, escape) is held as the forward step took it, with the same
+ * Philox draws (common random numbers).  Along that path the particle
+ * tallies are linear in the weights, a newborn's weight is E/N at fixed N
+ * (Eq. IhpFormula), a survivor keeps its weight; the Simpson group opacity,
+ * the wave flux (Sec. 2.2) and the converged source iteration (App. B,
+ * differentiated through its fixed point) carry the rest.  Single-problem
+ * FP64 handles only (UGKWP_ERR_UNSUPPORTED otherwise).
+ *
+ * Usage: checkpoint the forward run every k steps (ugkwp_checkpoint); for
+ * the backward pass, restore a checkpoint and re-run its k steps with
+ * ugkwp_step_taped (one tape per step), then call ugkwp_adjoint_step on the
+ * tapes in reverse order, after ugkwp_adjoint_seed for the last step.
+ * Restored steps repeat the forward ones up to the summation order of FP64
+ * atomics.  All buffers are caller-owned DEVICE memory, 256-byte aligned. */
+
+/* Bytes of one step's tape holding up to rec_cap processed particles (the
+ * step's survivors in plus its newborns; a step with more sets
+ * UGKWP_ST_CAPACITY in the forward status and in the adjoint's). */
+int ugkwp_tape_size(ugkwp_handle* h, int64_t rec_cap, size_t* bytes);
+/* One step (like ugkwp_step with nsteps = 1, without the captured graph)
+ * that also writes its tape: T^n, rho_h^n, T^{n+1}, rho^{n+1}, the birth
+ * counts, the step's counts, and per processed particle its start cell, end
+ * cell, output slot and group.  Asynchronous on `stream`. */
+int ugkwp_step_taped(ugkwp_handle* h, void* d_tape, size_t bytes, int64_t rec_cap, void* stream);
+/* Bytes of the adjoint workspace (adjoint state, dL/ds, per-step work). */
+int ugkwp_adjoint_workspace_size(ugkwp_handle* h, size_t* bytes);
+/* Start the reverse pass: zero the workspace and set the adjoint of the
+ * final temperature to d_dL_dT [ncell] (device; NULL leaves it 0). */
+int ugkwp_adjoint_seed(ugkwp_handle* h, void* d_adj, size_t bytes, const double* d_dL_dT, void* stream);
+/* Reverse one step from its tape: maps the adjoints of the step's outputs to
+ * those of its inputs and adds the step's explicit part to dL/ds.  The
+ * adjoint source iteration stops at max |d mu| <= si_tol max |mu| (cap
+ * si_max_iters, else UGKWP_ST_NOCONV).  Asynchronous on `stream`. */
+int ugkwp_adjoint_step(ugkwp_handle* h, const void* d_tape, size_t tape_bytes, int64_t rec_cap, void* d_adj,
+                       size_t adj_bytes, void* stream);
+/* Before reversing a recomputed segment whose end is the start of the
+ * segment reversed last: survivors are compacted in a thread-order-dependent
+ * order, so re-index the particles' weight adjoints from the order held in
+ * d_ckpt (that later segment's checkpoint) to the handle's current particle
+ * order (the recomputed segment's end), matching particle identities.  A
+ * particle present on one side only gets 0 and is counted in the result's
+ * `unmatched`.  Asynchronous on `stream`. */
+int ugkwp_adjoint_remap(ugkwp_handle* h, void* d_adj, size_t adj_bytes, const void* d_ckpt, size_t ckpt_bytes,
+                        void* stream);
+/* Copy dL/ds [ncell] and dL/dT of the first reversed step's input [ncell]
+ * (either pointer may be NULL; device destinations), and report the adjoint's
+ * latched UGKWP_ST_* bits, the last step's adjoint source iterations and the
+ * particles left unmatched by ugkwp_adjoint_remap (any pointer may be NULL).
+ * Synchronises `stream`. */
+int ugkwp_adjoint_result(ugkwp_handle* h, const void* d_adj, size_t bytes, double* d_dL_ds, double* d_dL_dT0,
+                         uint32_t* status_bits, int32_t* si_iters, uint64_t* unmatched, void* stream);
+
 const char* ugkwp_last_error(const ugkwp_handle* h);
 void ugkwp_destroy(ugkwp_handle* h);
 

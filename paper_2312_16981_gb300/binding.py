@@ -101,6 +101,17 @@ FUNCTIONS = {
     "ugkwp_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "ugkwp_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p,
                                  C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "ugkwp_tape_size": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_size_t)]),
+    "ugkwp_step_taped": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64, C.c_void_p]),
+    "ugkwp_adjoint_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "ugkwp_adjoint_seed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "ugkwp_adjoint_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64, C.c_void_p,
+                                     C.c_size_t, C.c_void_p]),
+    "ugkwp_adjoint_remap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                                      C.c_void_p]),
+    "ugkwp_adjoint_result": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_uint64), C.c_void_p]),
     "ugkwp_destroy": (None, [C.c_void_p]),
     "ugkwp_philox": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64, C.c_void_p]),
     "ugkwp_planck": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
@@ -325,6 +336,58 @@ class Simulation:
     def restore(self, buf):
         _check(load().ugkwp_restore(self.h, C.c_void_p(_ptr(buf)), buf.numel(),
                                     C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    # ---- adjoint (pathwise gradient with respect to log sigma0 per cell)
+    def tape_buffer(self, rec_cap: int):
+        """A device buffer for one step's tape holding up to rec_cap particles."""
+        import torch
+        n = C.c_size_t()
+        _check(load().ugkwp_tape_size(self.h, int(rec_cap), C.byref(n)), self.h)
+        return torch.empty(n.value, dtype=torch.uint8, device=self.device)
+
+    def step_taped(self, tape, rec_cap: int):
+        _check(load().ugkwp_step_taped(self.h, C.c_void_p(_ptr(tape)), tape.numel(), int(rec_cap),
+                                       C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def adjoint_buffer(self):
+        import torch
+        n = C.c_size_t()
+        _check(load().ugkwp_adjoint_workspace_size(self.h, C.byref(n)), self.h)
+        return torch.empty(n.value, dtype=torch.uint8, device=self.device)
+
+    def adjoint_seed(self, adj, dL_dT=None):
+        """dL_dT: torch float64 tensor [ncell] on this device (None: zero)."""
+        if dL_dT is not None:
+            assert dL_dT.dtype.is_floating_point and dL_dT.numel() == self.p.ncell
+        ptr = None if dL_dT is None else C.c_void_p(_ptr(dL_dT.contiguous()))
+        _check(load().ugkwp_adjoint_seed(self.h, C.c_void_p(_ptr(adj)), adj.numel(), ptr,
+                                         C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def adjoint_step(self, tape, rec_cap: int, adj):
+        _check(load().ugkwp_adjoint_step(self.h, C.c_void_p(_ptr(tape)), tape.numel(), int(rec_cap),
+                                         C.c_void_p(_ptr(adj)), adj.numel(),
+                                         C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def adjoint_remap(self, adj, ckpt):
+        """Re-index the particles' weight adjoints from checkpoint `ckpt`'s
+        particle order to the current one (by particle identity)."""
+        _check(load().ugkwp_adjoint_remap(self.h, C.c_void_p(_ptr(adj)), adj.numel(), C.c_void_p(_ptr(ckpt)),
+                                          ckpt.numel(), C.c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def adjoint_result(self, adj):
+        """(dL/ds, dL/dT of the first reversed step's input, status bits, last
+        adjoint source iterations, particles unmatched across checkpoints);
+        the arrays are torch float64 on the device."""
+        import torch
+        ds = torch.empty(self.p.ncell, dtype=torch.float64, device=self.device)
+        dT = torch.empty(self.p.ncell, dtype=torch.float64, device=self.device)
+        st = C.c_uint32()
+        it = C.c_int32()
+        um = C.c_uint64()
+        _check(load().ugkwp_adjoint_result(self.h, C.c_void_p(_ptr(adj)), adj.numel(), C.c_void_p(_ptr(ds)),
+                                           C.c_void_p(_ptr(dT)), C.byref(st), C.byref(it), C.byref(um),
+                                           C.c_void_p(_stream_ptr(self.stream))), self.h)
+        return ds, dT, st.value, it.value, um.value
 
     def set_launch(self, block: int, particles_per_thread: int = 1, blocks_per_sm: int = 0):
         _check(load().ugkwp_set_launch(self.h, block, particles_per_thread, blocks_per_sm), self.h)

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libugkwp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["ugkwp_api.cu", "ugkwp_macro.cu", "ugkwp_stream.cu", "ugkwp_noalloc.cu"]
+SOURCES = ["ugkwp_api.cu", "ugkwp_macro.cu", "ugkwp_stream.cu", "ugkwp_noalloc.cu", "ugkwp_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

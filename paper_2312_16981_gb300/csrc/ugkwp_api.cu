@@ -127,6 +127,7 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.Fwave = cv.take<double>(nf * G);
   d.Feq = cv.take<double>(nf * G);
   d.R = cv.take<double>(ncg);
+  d.wscale = cv.take<double>(ncg);
   d.Tk[0] = cv.take<double>(nc);
   d.Tk[1] = cv.take<double>(nc);
   d.sigk[0] = cv.take<double>(ncg);
@@ -200,6 +201,8 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.capacity = p->particle_capacity;
   d.rec = nullptr;
   d.rec_cap = 0;
+  d.tape = nullptr;
+  d.tape_cap = 0;
 }
 
 }  // namespace
@@ -379,15 +382,18 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
 
 namespace {
 
-cudaError_t enqueue_step(const ugkwp_handle* h, cudaStream_t s) {
-  const Dev& d = h->d;
-  const ugkwp::Ens* e = h->M > 1 ? &h->ens : nullptr;
+cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::StreamShape& sh,
+                             cudaStream_t s) {
   cudaError_t r = ugkwp::launch_birth_and_scan(d, e, s);
   if (!r) r = ugkwp::launch_wave(d, e, s);
-  if (!r) r = ugkwp::launch_stream(d, e, h->shape, s);
+  if (!r) r = ugkwp::launch_stream(d, e, sh, s);
   if (!r) r = ugkwp::launch_si(d, e, s);
   if (!r) r = ugkwp::launch_end_step(d, e, s);
   return r;
+}
+
+cudaError_t enqueue_step(const ugkwp_handle* h, cudaStream_t s) {
+  return enqueue_step_dev(h->d, h->M > 1 ? &h->ens : nullptr, h->shape, s);
 }
 
 void drop_graph(ugkwp_handle* h) {
@@ -737,6 +743,126 @@ int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void*
   best[2] = best_s.blocks_per_sm;
   if (best_ms) *best_ms = best_t / steps;
   (void)keep;
+  return UGKWP_OK;
+}
+
+// ---- adjoint: tape of a forward step, reverse steps, result
+namespace {
+int adjoint_check(ugkwp_handle* h) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  if (h->M > 1) return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint is for single-problem handles");
+  if (h->d.precision != UGKWP_FP64)
+    return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint tape is written by the FP64 particle kernel");
+  return UGKWP_OK;
+}
+}  // namespace
+
+int ugkwp_tape_size(ugkwp_handle* h, int64_t rec_cap, size_t* bytes) {
+  int st = adjoint_check(h);
+  if (st) return st;
+  if (!bytes || rec_cap < 0) return fail(h, UGKWP_ERR_ARG, "bad arguments");
+  *bytes = ugkwp::tape_layout(h->d, rec_cap).total;
+  return UGKWP_OK;
+}
+
+int ugkwp_step_taped(ugkwp_handle* h, void* d_tape, size_t bytes, int64_t rec_cap, void* stream) {
+  int st = adjoint_check(h);
+  if (st) return st;
+  if (!d_tape || rec_cap < 0) return fail(h, UGKWP_ERR_ARG, "bad arguments");
+  const ugkwp::TapeLayout L = ugkwp::tape_layout(h->d, rec_cap);
+  if (bytes < L.total) return fail(h, UGKWP_ERR_WORKSPACE, "tape smaller than ugkwp_tape_size");
+  if (reinterpret_cast<uintptr_t>(d_tape) % 256) return fail(h, UGKWP_ERR_WORKSPACE, "tape must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dev& d = h->d;
+  char* b = static_cast<char*>(d_tape);
+  const size_t ncg = (size_t)d.ncell * d.G;
+  CK(cudaMemcpyAsync(b + L.T0, d.T, sizeof(double) * d.ncell, cudaMemcpyDeviceToDevice, s), h);
+  CK(cudaMemcpyAsync(b + L.rho_h0, d.rho_h, sizeof(double) * ncg, cudaMemcpyDeviceToDevice, s), h);
+  Dev dt = d;
+  dt.tape = reinterpret_cast<ugkwp::TapeRec*>(b + L.rec);
+  dt.tape_cap = rec_cap;
+  CK(enqueue_step_dev(dt, nullptr, h->shape, s), h);
+  CK(cudaMemcpyAsync(b + L.T1, d.T, sizeof(double) * d.ncell, cudaMemcpyDeviceToDevice, s), h);
+  CK(cudaMemcpyAsync(b + L.rho1, d.rho, sizeof(double) * ncg, cudaMemcpyDeviceToDevice, s), h);
+  CK(cudaMemcpyAsync(b + L.wscale, d.wscale, sizeof(double) * ncg, cudaMemcpyDeviceToDevice, s), h);
+  CK(cudaMemcpyAsync(b + L.Esurv, d.E_surv, sizeof(double) * ncg, cudaMemcpyDeviceToDevice, s), h);
+  CK(cudaMemcpyAsync(b + L.N, d.N, sizeof(uint32_t) * d.nbins, cudaMemcpyDeviceToDevice, s), h);
+  CK(cudaMemcpyAsync(b + L.hdr, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToDevice, s), h);
+  return UGKWP_OK;
+}
+
+int ugkwp_adjoint_workspace_size(ugkwp_handle* h, size_t* bytes) {
+  int st = adjoint_check(h);
+  if (st) return st;
+  if (!bytes) return fail(h, UGKWP_ERR_ARG, "NULL argument");
+  *bytes = ugkwp::adjoint_bytes(h->d);
+  return UGKWP_OK;
+}
+
+namespace {
+int adjoint_ws_check(ugkwp_handle* h, const void* d_adj, size_t bytes) {
+  if (!d_adj || bytes < ugkwp::adjoint_bytes(h->d))
+    return fail(h, UGKWP_ERR_WORKSPACE, "adjoint workspace smaller than ugkwp_adjoint_workspace_size");
+  if (reinterpret_cast<uintptr_t>(d_adj) % 256)
+    return fail(h, UGKWP_ERR_WORKSPACE, "adjoint workspace must be 256-byte aligned");
+  return UGKWP_OK;
+}
+}  // namespace
+
+int ugkwp_adjoint_seed(ugkwp_handle* h, void* d_adj, size_t bytes, const double* d_dL_dT, void* stream) {
+  int st = adjoint_check(h);
+  if (st || (st = adjoint_ws_check(h, d_adj, bytes))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(d_adj, 0, ugkwp::adjoint_bytes(h->d), s), h);
+  const ugkwp::AdjView a = ugkwp::adjoint_view(h->d, d_adj);
+  CK(cudaMemcpyAsync(&a.ctrl->bar_limit, &h->d.ctrl->bar_timeout_spins, sizeof(unsigned int),
+                     cudaMemcpyDeviceToDevice, s), h);
+  if (d_dL_dT)
+    CK(cudaMemcpyAsync(a.lamT, d_dL_dT, sizeof(double) * h->d.ncell, cudaMemcpyDeviceToDevice, s), h);
+  return UGKWP_OK;
+}
+
+int ugkwp_adjoint_step(ugkwp_handle* h, const void* d_tape, size_t tape_bytes, int64_t rec_cap, void* d_adj,
+                       size_t adj_bytes, void* stream) {
+  int st = adjoint_check(h);
+  if (st || (st = adjoint_ws_check(h, d_adj, adj_bytes))) return st;
+  if (!d_tape || rec_cap < 0) return fail(h, UGKWP_ERR_ARG, "bad arguments");
+  if (tape_bytes < ugkwp::tape_layout(h->d, rec_cap).total)
+    return fail(h, UGKWP_ERR_WORKSPACE, "tape smaller than ugkwp_tape_size");
+  const ugkwp::TapeView t = ugkwp::tape_view(h->d, d_tape, rec_cap);
+  const ugkwp::AdjView a = ugkwp::adjoint_view(h->d, d_adj);
+  CK(ugkwp::launch_adjoint_step(h->d, t, a, (cudaStream_t)stream), h);
+  return UGKWP_OK;
+}
+
+int ugkwp_adjoint_remap(ugkwp_handle* h, void* d_adj, size_t adj_bytes, const void* d_ckpt, size_t ckpt_bytes,
+                        void* stream) {
+  int st = adjoint_check(h);
+  if (st || (st = adjoint_ws_check(h, d_adj, adj_bytes))) return st;
+  size_t need = 0;
+  ugkwp_checkpoint_size(h, &need);
+  if (!d_ckpt || ckpt_bytes < need) return fail(h, UGKWP_ERR_WORKSPACE, "checkpoint buffer smaller than ugkwp_checkpoint_size");
+  const ugkwp::AdjView a = ugkwp::adjoint_view(h->d, d_adj);
+  // single-problem checkpoint: member 0 starts after the 256-byte offset table
+  const char* member = static_cast<const char*>(d_ckpt) + align256(sizeof(size_t));
+  CK(ugkwp::launch_adjoint_remap(h->d, a, member, (cudaStream_t)stream), h);
+  return UGKWP_OK;
+}
+
+int ugkwp_adjoint_result(ugkwp_handle* h, const void* d_adj, size_t bytes, double* d_dL_ds, double* d_dL_dT0,
+                         uint32_t* status_bits, int32_t* si_iters, uint64_t* unmatched, void* stream) {
+  int st = adjoint_check(h);
+  if (st || (st = adjoint_ws_check(h, d_adj, bytes))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const ugkwp::AdjView a = ugkwp::adjoint_view(h->d, const_cast<void*>(d_adj));
+  if (d_dL_ds) CK(cudaMemcpyAsync(d_dL_ds, a.lamS, sizeof(double) * h->d.ncell, cudaMemcpyDeviceToDevice, s), h);
+  if (d_dL_dT0) CK(cudaMemcpyAsync(d_dL_dT0, a.lamT, sizeof(double) * h->d.ncell, cudaMemcpyDeviceToDevice, s), h);
+  ugkwp::AdjCtrl c;
+  CK(cudaMemcpyAsync(&c, a.ctrl, sizeof c, cudaMemcpyDeviceToHost, s), h);
+  CK(cudaStreamSynchronize(s), h);
+  if (status_bits) *status_bits = c.status;
+  if (si_iters) *si_iters = (int32_t)c.iters;
+  if (unmatched) *unmatched = (uint64_t)c.unmatched;
   return UGKWP_OK;
 }
 

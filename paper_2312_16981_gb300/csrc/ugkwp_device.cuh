@@ -154,6 +154,7 @@ struct Dev {
   double* Fwave;    // [nface*G]
   double* Feq;      // [nface*G]
   double* R;        // [ncell*G] constant part of the rho equation
+  double* wscale;   // [ncell*G] end-of-step scaling of the survivors' weights (1: none)
   double* Tk[2];    // [ncell] iterates
   double* sigk[2];  // [ncell*G]
   double* phik[2];  // [ncell*G]
@@ -184,6 +185,9 @@ struct Dev {
   struct Ctrl* ctrl;
   struct RecordOut* rec;
   long long rec_cap;
+  // optional adjoint tape: one entry per processed particle (taped steps only)
+  struct TapeRec* tape;
+  long long tape_cap;
 };
 
 // Ensemble view (independent problems advanced together): per-member
@@ -228,6 +232,17 @@ struct RecordOut {
   double x, y, ox, oy, nu, w, t_end;
 };
 
+// Adjoint tape entry of one processed particle: where its weight was counted
+// in this step.  c0 = start cell, or -1 - side for a black-body ghost birth;
+// c1 = end cell of a survivor or the collision cell of an absorbed particle,
+// else -1 (escaped, removed); slot = its index in the next step's input if it
+// survived, else -1; g = group; w = its weight in this step (before the
+// end-of-step scaling of survivors).
+struct TapeRec {
+  int c0, c1, slot, g;
+  double w;
+};
+
 // Device control block: counters, status, barrier and reduction slots.
 struct Ctrl {
   unsigned long long step;
@@ -239,7 +254,7 @@ struct Ctrl {
   unsigned int si_iters;
   unsigned int bar_count;         // grid barrier arrivals (monotone)
   unsigned int bar_timeout_spins; // bounded-wait limit (0: default)
-  unsigned int pad0;
+  unsigned int scaled;            // some survivors' weights need scaling this step
   unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)
   double E_rad0, E_mat0, E_rad1, E_mat1, bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
 };
@@ -270,6 +285,18 @@ __device__ __forceinline__ double sigma_group(const Dev& d, double sT, int g) {
   const double sa = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g));
   const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1));
   const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2));
+  return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
+}
+
+// d sigma_g / d s for sigma0 -> sigma0 e^s: the Simpson sum of the point
+// values below the cap (a capped point does not depend on s).  The
+// T-derivative is q/T times the same sum.
+__device__ __forceinline__ double sigma_group_ds(const Dev& d, double sT, int g) {
+  auto pt = [&](double s) { return (d.sig_cap > 0.0 && !(s <= d.sig_cap)) ? 0.0 : s; };
+  if (d.grey) return pt(sT);
+  const double sa = pt(sT * __ldg(d.nu_pow + 3 * g));
+  const double sm = pt(sT * __ldg(d.nu_pow + 3 * g + 1));
+  const double sb = pt(sT * __ldg(d.nu_pow + 3 * g + 2));
   return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
 }
 
@@ -420,6 +447,52 @@ __device__ __forceinline__ double coef_c4(double x) {
     return s;
   }
   return -expm1(-x) / x;
+}
+
+// x-derivatives of the same coefficients: the differentiated series below
+// x = 1, and from the closed forms above it with e = exp(-x):
+//   c4' = (e - c4)/x,  f4' = c4' + e,  f2' = 2 c4' + e,  f5' = -e (1 + x)/2 - c4'.
+__host__ __device__ constexpr double da2(int k) { return k * a2(k); }
+__host__ __device__ constexpr double da4(int k) { return k * a4(k); }
+__host__ __device__ constexpr double da5(int k) { return k * a5(k); }
+__host__ __device__ constexpr double dac4(int k) { return k * ac4(k); }
+#define UGKWP_SER_TABLE(f)                                                                   \
+  {f(0),  f(1),  f(2),  f(3),  f(4),  f(5),  f(6),  f(7),  f(8),  f(9),  f(10), f(11),      \
+   f(12), f(13), f(14), f(15), f(16), f(17), f(18), f(19), f(20), f(21), f(22)}
+__device__ constexpr double kD2[kSer + 1] = UGKWP_SER_TABLE(da2);
+__device__ constexpr double kD4[kSer + 1] = UGKWP_SER_TABLE(da4);
+__device__ constexpr double kD5[kSer + 1] = UGKWP_SER_TABLE(da5);
+__device__ constexpr double kDC4[kSer + 1] = UGKWP_SER_TABLE(dac4);
+#undef UGKWP_SER_TABLE
+
+struct CoefDeriv {
+  double f2, f4, f5, c4;
+};
+
+// sum_{k>=1} t[k] x^(k-1) by Horner
+__device__ __forceinline__ double dser(const double* t, double x) {
+  double s = t[kSer];
+#pragma unroll
+  for (int k = kSer - 1; k >= 1; --k) s = fma(s, x, t[k]);
+  return s;
+}
+
+__device__ __forceinline__ CoefDeriv coef_derivs(double x) {
+  CoefDeriv r;
+  if (x < 1.0) {
+    r.f2 = dser(kD2, x);
+    r.f4 = dser(kD4, x);
+    r.f5 = dser(kD5, x);
+    r.c4 = dser(kDC4, x);
+    return r;
+  }
+  const double e = exp(-x), c4 = -expm1(-x) / x;
+  const double d4 = (e - c4) / x;
+  r.c4 = d4;
+  r.f4 = d4 + e;
+  r.f2 = 2.0 * d4 + e;
+  r.f5 = -0.5 * e * (1.0 + x) - d4;
+  return r;
 }
 
 // --------------------------------------------------------------------------

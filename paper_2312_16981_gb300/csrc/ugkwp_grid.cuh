@@ -1,0 +1,105 @@
+// ugkwp_grid.cuh -- cell and face helpers shared by the step kernels and
+// their adjoint: face indexing along grid lines, the van Leer limiter, warp
+// reductions and the per-cell opacity/Planck evaluation of the source
+// iteration (one warp per cell, one lane per group).
+#pragma once
+#include "ugkwp_device.cuh"
+
+namespace ugkwp {
+
+// --------------------------------------------------------------------------
+// Face walk helpers: face f -> axis, the line of cells through it and its
+// position along the line.
+struct FaceRef {
+  int axis, line, k, nk;   // face between line cells k-1 and k, 0..nk
+  double h;
+};
+
+__device__ __forceinline__ FaceRef face_ref(const Dev& d, int f) {
+  FaceRef r;
+  if (f < d.nxface) {
+    r.axis = 0; r.line = f / (d.nx + 1); r.k = f - r.line * (d.nx + 1); r.nk = d.nx; r.h = d.dx;
+  } else {
+    const int q = f - d.nxface;
+    r.axis = 1; r.k = q / d.nx; r.line = q - r.k * d.nx; r.nk = d.ny; r.h = d.dy;
+  }
+  return r;
+}
+
+__device__ __forceinline__ int line_cell(const Dev& d, const FaceRef& r, int k) {
+  return r.axis == 0 ? r.line * d.nx + k : k * d.nx + r.line;
+}
+
+// rho_h at line position k including ghosts (mirror / black body / vacuum)
+__device__ __forceinline__ double rho_h_at(const Dev& d, const FaceRef& r, int k, int g) {
+  if (k >= 0 && k < r.nk) return d.rho_h[line_cell(d, r, k) * d.G + g];
+  const int side = r.axis * 2 + (k < 0 ? 0 : 1);
+  if (d.bc[side] == BC_REFLECT) return d.rho_h[line_cell(d, r, k < 0 ? 0 : r.nk - 1) * d.G + g];
+  if (d.bc[side] == BC_BLACKBODY) return d.ghost_phi[side * d.G + g];
+  return 0.0;
+}
+
+__device__ __forceinline__ double van_leer(double a, double b) {
+  return a * b > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Planck and opacity of one cell at temperature T for the lane's groups:
+// sigma_g, Phi_g and dPhi_g/dT, g = lane + 32 j.  Edge values are shared
+// between neighbouring lanes by shuffles.
+template <int NC>
+__device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
+                                            double* dphi) {
+  const int lane = threadIdx.x & 31, G = d.G;
+  const double sT = sigma_T(d, c, T);
+  const double ac = d.a * d.c, T3 = T * T * T;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (d.grey) {
+      sig[j] = cap_sigma(d, sT);
+      phi[j] = T > 0.0 ? ac * T3 * T : 0.0;
+      dphi[j] = T > 0.0 ? 4.0 * ac * T3 : 0.0;
+      continue;
+    }
+    EdgeVal lo;
+    if (g <= G && T > 0.0) lo = planck_edge(d.nu_edges[g] / T);
+    else { lo.V = 0.0; lo.g4 = 0.0; lo.lower = true; }
+    EdgeVal hi;
+    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
+    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
+    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
+    if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] / T);
+    if (g < G) {
+      sig[j] = sigma_group(d, sT, g);
+      if (T > 0.0) {
+        const double b = planck_fraction(lo, hi);
+        phi[j] = ac * T3 * T * b;
+        dphi[j] = ac * T3 * planck_dfraction(b, lo, hi);
+      } else {
+        phi[j] = 0.0;
+        dphi[j] = 0.0;
+      }
+    } else {
+      sig[j] = 1.0; phi[j] = 0.0; dphi[j] = 0.0;
+    }
+  }
+}
+
+__device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {
+  const int ix = c % d.nx, iy = c / d.nx;
+  if (axis == 0) return iy * (d.nx + 1) + ix + (dir > 0 ? 1 : 0);
+  return d.nxface + (iy + (dir > 0 ? 1 : 0)) * d.nx + ix;
+}
+
+}  // namespace ugkwp

@@ -19,6 +19,58 @@ size_t ckpt_bytes(const Dev& d);
 cudaError_t launch_checkpoint(const Dev& d, const Ens* e, char* buf, const size_t* d_offs, int save,
                               cudaStream_t s);
 
+// ---- adjoint (ugkwp_adjoint.cu)
+// Tape of one forward step, in a caller buffer: the control block after the
+// step (counts), T^n, T^{n+1}, rho^{n+1}, rho_h^n, the survivors' scaling
+// factors and E_surv per (cell, group), the birth counts N and one TapeRec
+// per processed particle.
+struct TapeLayout {
+  size_t hdr, T0, T1, rho1, rho_h0, wscale, Esurv, N, rec, total;
+};
+struct TapeView {
+  const Ctrl* hdr;
+  const double *T0, *T1, *rho1, *rho_h0, *wscale, *Esurv;
+  const uint32_t* N;
+  const TapeRec* rec;
+  long long rec_cap;
+};
+// Control block of the adjoint workspace.
+struct AdjCtrl {
+  unsigned int bar_count;       // grid barrier arrivals (reset before each adjoint step)
+  unsigned int status;          // ST_* bits, latched since the seed
+  unsigned int cur;             // which lamW buffer holds the next step's weight adjoints
+  unsigned int iters;           // adjoint source iterations of the last step
+  unsigned int bar_limit;       // bounded-wait limit (0: default)
+  unsigned int pad;
+  unsigned long long err_slot[3][2];
+  unsigned long long unmatched; // particles without a partner across a checkpoint boundary
+};
+// Adjoint workspace: the adjoint state (of T^n, rho^n, rho_h^n and the
+// incoming particles' weights), the accumulated dL/ds and per-step work.
+struct AdjView {
+  AdjCtrl* ctrl;
+  double *lamT, *lamS, *lamT0, *ls, *lamRho, *lamRhoH;
+  double* lamW[2];
+  double *lamR, *lamRhoH0, *lamSig0, *lamE, *Sb;
+  double *mu[2], *gT, *D, *Jl;
+  double *sig1, *sig1s, *phi1, *dphi1, *sig0, *sig0s, *dFdT;
+  unsigned long long* hkeys;    // id -> weight-adjoint hash (remap across checkpoints)
+  double* hvals;
+  long long hsize;              // power of two >= 2 x capacity
+  long long cap;
+};
+TapeLayout tape_layout(const Dev& d, long long rec_cap);
+TapeView tape_view(const Dev& d, const void* base, long long rec_cap);
+size_t adjoint_bytes(const Dev& d);
+AdjView adjoint_view(const Dev& d, void* base);
+cudaError_t launch_adjoint_step(const Dev& d, const TapeView& t, const AdjView& a, cudaStream_t s);
+// Re-index the weight adjoints from a checkpoint's particle order (ids and
+// count read from the checkpoint buffer of member 0) to the handle's current
+// particle order, matching by particle identity.
+cudaError_t launch_adjoint_remap(const Dev& d, const AdjView& a, const char* ckpt_member, cudaStream_t s);
+size_t ckpt_ids_offset(const Dev& d);
+size_t ckpt_ctrl_offset(const Dev& d);
+
 // message returned by ugkwp_last_error(NULL)
 void set_global_error(const char* msg);
 

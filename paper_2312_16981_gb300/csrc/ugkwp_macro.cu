@@ -4,6 +4,7 @@
 // persistent kernel, the end-of-step bookkeeping, initialisation, and the
 // kernel-level entry points used by the parity tests.
 #include "ugkwp_device.cuh"
+#include "ugkwp_grid.cuh"
 #include "ugkwp_launch.h"
 
 namespace ugkwp {
@@ -91,6 +92,7 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     ctrl->n_born = ctrl->n_survived = ctrl->n_absorbed = ctrl->n_escaped = 0;
     ctrl->n_removed = ctrl->n_segments = 0;
     ctrl->bar_count = 0;
+    ctrl->scaled = 0;
     for (int s = 0; s < 3; ++s) ctrl->err_slot[s][0] = ctrl->err_slot[s][1] = 0ull;
     ctrl->E_rad0 = ctrl->E_mat0 = ctrl->E_rad1 = ctrl->E_mat1 = 0.0;
     ctrl->bnd_in_macro = ctrl->bnd_in_part = ctrl->bnd_out_part = ctrl->src_in = 0.0;
@@ -295,42 +297,6 @@ __global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
   if (threadIdx.x == 0) e.tile0[e.M] = s_carry;
 }
 
-// --------------------------------------------------------------------------
-// Face walk helpers: face f -> axis, the line of cells through it and its
-// position along the line.
-struct FaceRef {
-  int axis, line, k, nk;   // face between line cells k-1 and k, 0..nk
-  double h;
-};
-
-__device__ __forceinline__ FaceRef face_ref(const Dev& d, int f) {
-  FaceRef r;
-  if (f < d.nxface) {
-    r.axis = 0; r.line = f / (d.nx + 1); r.k = f - r.line * (d.nx + 1); r.nk = d.nx; r.h = d.dx;
-  } else {
-    const int q = f - d.nxface;
-    r.axis = 1; r.k = q / d.nx; r.line = q - r.k * d.nx; r.nk = d.ny; r.h = d.dy;
-  }
-  return r;
-}
-
-__device__ __forceinline__ int line_cell(const Dev& d, const FaceRef& r, int k) {
-  return r.axis == 0 ? r.line * d.nx + k : k * d.nx + r.line;
-}
-
-// rho_h at line position k including ghosts (mirror / black body / vacuum)
-__device__ __forceinline__ double rho_h_at(const Dev& d, const FaceRef& r, int k, int g) {
-  if (k >= 0 && k < r.nk) return d.rho_h[line_cell(d, r, k) * d.G + g];
-  const int side = r.axis * 2 + (k < 0 ? 0 : 1);
-  if (d.bc[side] == BC_REFLECT) return d.rho_h[line_cell(d, r, k < 0 ? 0 : r.nk - 1) * d.G + g];
-  if (d.bc[side] == BC_BLACKBODY) return d.ghost_phi[side * d.G + g];
-  return 0.0;
-}
-
-__device__ __forceinline__ double van_leer(double a, double b) {
-  return a * b > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
-}
-
 // A = C4_f - e_h, B = C5_f + dt e_h/2 of one half (face coefficients, upwind e).
 __device__ __forceinline__ void half_coefs(double xf, double tauf, double xh, double e_eff,
                                            double dt, double* A, double* B) {
@@ -450,59 +416,6 @@ __device__ __forceinline__ double feq_face(const Dev& d, double sl, double su, d
   return tau * coef_f2(d.dt / tau) * (d.v * d.v / 3.0) * (pu - pl) / h;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Planck and opacity of one cell at temperature T for the lane's groups:
-// sigma_g, Phi_g and dPhi_g/dT, g = lane + 32 j.  Edge values are shared
-// between neighbouring lanes by shuffles.
-template <int NC>
-__device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
-                                            double* dphi) {
-  const int lane = threadIdx.x & 31, G = d.G;
-  const double sT = sigma_T(d, c, T);
-  const double ac = d.a * d.c, T3 = T * T * T;
-#pragma unroll
-  for (int j = 0; j < NC; ++j) {
-    const int g = lane + 32 * j;
-    if (d.grey) {
-      sig[j] = cap_sigma(d, sT);
-      phi[j] = T > 0.0 ? ac * T3 * T : 0.0;
-      dphi[j] = T > 0.0 ? 4.0 * ac * T3 : 0.0;
-      continue;
-    }
-    EdgeVal lo;
-    if (g <= G && T > 0.0) lo = planck_edge(d.nu_edges[g] / T);
-    else { lo.V = 0.0; lo.g4 = 0.0; lo.lower = true; }
-    EdgeVal hi;
-    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
-    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
-    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
-    if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] / T);
-    if (g < G) {
-      sig[j] = sigma_group(d, sT, g);
-      if (T > 0.0) {
-        const double b = planck_fraction(lo, hi);
-        phi[j] = ac * T3 * T * b;
-        dphi[j] = ac * T3 * planck_dfraction(b, lo, hi);
-      } else {
-        phi[j] = 0.0;
-        dphi[j] = 0.0;
-      }
-    } else {
-      sig[j] = 1.0; phi[j] = 0.0; dphi[j] = 0.0;
-    }
-  }
-}
-
 // Neighbour values across one face of cell c: opacity and Phi at iterate k,
 // or the ghost's.  Returns false for a reflecting wall (no flux).
 __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir, int g, int cur,
@@ -528,12 +441,6 @@ __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir
   *sn = __ldcg(d.sigk[cur] + n * d.G + g);
   *pn = __ldcg(d.phik[cur] + n * d.G + g);
   return true;
-}
-
-__device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {
-  const int ix = c % d.nx, iy = c / d.nx;
-  if (axis == 0) return iy * (d.nx + 1) + ix + (dir > 0 ? 1 : 0);
-  return d.nxface + (iy + (dir > 0 ? 1 : 0)) * d.nx + ix;
 }
 
 // Source iteration (App. B, Algorithm 2) in 1D and 2D, one warp per cell and
@@ -771,21 +678,24 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   // ---- epilogue: member m's last iterate wrote Tk[s_conv[m] & 1] (or Tk[it & 1])
   {
     double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
-    int bad = 0, acc_m = -1;
+    int bad = 0, scaled = 0, acc_m = -1;
     for (long long gc = gw; gc < total; gc += nw) {
       const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
       if (ENS && m != acc_m && acc_m >= 0) {
         e_rad1 = warp_sum(e_rad1);
         b_in = warp_sum(b_in);
+        const bool sc_any = __any_sync(0xffffffffu, scaled);
         if (lane == 0) {
           Ctrl* cc = e.devs[acc_m].ctrl;
           atomicAdd(&cc->E_rad1, e_rad1);
           atomicAdd(&cc->E_mat1, e_mat1);
           if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
           if (bad) atomicOr(&cc->status, ST_NONFINITE);
+          if (sc_any) atomicOr(&cc->scaled, 1u);
         }
         e_rad1 = e_mat1 = b_in = 0.0;
         bad = 0;
+        scaled = 0;
       }
       acc_m = m;
       const Dev& d = ENS ? e.devs[m] : d0;
@@ -807,7 +717,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (g >= G) continue;
         const int i = c * G + g;
         const double r = __ldcg(d.rho + i);
-        const double rp = d.E_surv[i] / V;
+        // survivors never hold more than rho^{n+1} leaves in their (cell,
+        // group): their weights are scaled to it (rho and the energy unchanged)
+        double rp = d.E_surv[i] / V, f = 1.0;
+        if (rp > 0.0 && r < rp) {
+          f = r > 0.0 ? r / rp : 0.0;
+          rp = r > 0.0 ? r : 0.0;
+          scaled = 1;
+        }
+        d.wscale[i] = f;
         d.rho_p[i] = rp;
         d.rho_h[i] = r - rp;
         e_rad1 += V * r / d.c;
@@ -834,6 +752,10 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       atomicAdd(&cc->E_mat1, e_mat1);
       if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
       if (bad) atomicOr(&cc->status, ST_NONFINITE);
+    }
+    if (__any_sync(0xffffffffu, scaled) && lane == 0 && acc_m >= 0) {
+      Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
+      atomicOr(&cc->scaled, 1u);
     }
   }
   if (blockIdx.x == 0) {
@@ -874,6 +796,28 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
   }
 }
 
+// Survivors' weights scaled by the factor the source-iteration epilogue set
+// for their (cell, group) (a reading where the paper is silent: the particle
+// part never exceeds rho^{n+1}).  Runs after the buffer swap; a member with
+// nothing to scale returns at once.
+template <bool ENS>
+__global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__ Dev d0, const Ens e) {
+  const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
+  const Ctrl* ctrl = d.ctrl;
+  if (!ctrl->scaled) return;
+  const unsigned cur = ctrl->cur;
+  const long long n = (long long)ctrl->n_part[cur];
+  const uint32_t* __restrict__ key = d.pkey[cur];
+  const bool mixed = d.precision == 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double f = __ldg(d.wscale + key[i]);
+    if (f == 1.0) continue;
+    if (mixed) d.fw[cur][i] = (float)((double)d.fw[cur][i] * f);
+    else d.pw[cur][i] *= f;
+  }
+}
+
 // --------------------------------------------------------------------------
 // Checkpoint / restore of a member's state in a caller buffer laid out as
 // [Ctrl][T][rho][rho_h][rho_p][particle arrays, capacity entries each].
@@ -904,6 +848,8 @@ __host__ __device__ inline CkptLayout ckpt_layout(const Dev& d) {
 }
 
 size_t ckpt_bytes(const Dev& d) { return ckpt_layout(d).total; }
+size_t ckpt_ids_offset(const Dev& d) { return ckpt_layout(d).part[6]; }
+size_t ckpt_ctrl_offset(const Dev& d) { return ckpt_layout(d).ctrl; }
 
 template <typename TT>
 __device__ __forceinline__ void copy_n(TT* dst, const TT* src, long long n) {
@@ -1115,9 +1061,11 @@ cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s) {
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
     k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e);
+    k_scale_survivors<true><<<dim3(8, e->M), 256, 0, s>>>(d, *e);
   } else {
     const Ens none{};
     k_end_step<false><<<1, 32, 0, s>>>(d, none);
+    k_scale_survivors<false><<<152 * 4, 256, 0, s>>>(d, none);
   }
   return cudaGetLastError();
 }

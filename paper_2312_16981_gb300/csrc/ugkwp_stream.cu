@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
     const bool keep = valid && fate == FATE_SURVIVED;
     unsigned rank;
     const unsigned long long base = block_slots(keep, tile_iter & 1, &ctrl->n_out, &rank);
+    int slot = -1;
     if (keep) {
       const unsigned long long o = base + rank;
       if (o < (unsigned long long)d.capacity) {
@@ -369,6 +370,21 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         d.pw[nxb][o] = w;
         d.pid[nxb][o] = id;
         d.pkey[nxb][o] = (uint32_t)(cell * G + g);
+        slot = (int)o;
+      } else {
+        atomicOr(&ctrl->status, ST_CAPACITY);
+      }
+    }
+    // adjoint tape: where this particle's weight was counted
+    if (!ENS && d.tape && valid) {
+      if (i < d.tape_cap) {
+        TapeRec tr;
+        tr.c0 = gside >= 0 ? -1 - gside : cell0;
+        tr.c1 = (fate == FATE_SURVIVED || fate == FATE_ABSORBED) ? cell : -1;
+        tr.slot = slot;
+        tr.g = g;
+        tr.w = w;
+        d.tape[i] = tr;
       } else {
         atomicOr(&ctrl->status, ST_CAPACITY);
       }

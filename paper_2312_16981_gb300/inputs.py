@@ -140,6 +140,25 @@ def checkerboard_2d(n: int = 256, G: int = 30, block: int = 16, patch: int = 32,
         particle_capacity=1 << 25)
 
 
+def adjoint_grid(n: int = 128, G: int = 16, patch: int = 16, steps: int = 200,
+                 omega_ref: float = 2.4e-8, seed: int = 0) -> Problem:
+    """2D [0,1]^2 grid for the opacity-gradient workload: n x n cells, G log
+    groups on [1e-3, 10], base sigma0 = 1e2 (sigma = sigma0 e^{s_c} nu^-3
+    T^-1/2, capped at 1e6; the per-cell scales s_c are the parameters),
+    isotropic T_s = 1 source in a central patch x patch square, T0 = 1e-3,
+    reflecting walls, dt = dx/c."""
+    lo, hi = n // 2 - patch // 2, n // 2 + patch // 2
+    src = np.zeros((n, n))
+    src[lo:hi, lo:hi] = 1.0
+    dx = 1.0 / n
+    return Problem(
+        dim=2, nx=n, ny=n, dx=dx, dy=dx, G=G, grey=0,
+        nu_edges=log_groups(G, 1e-3, 10.0), sigma0=np.full(n * n, 1e2), cv=np.ones(n * n),
+        T0=np.full(n * n, 1e-3), dt=dx, src_T=src.reshape(-1), src_on=1.0,
+        bc=[BC_REFLECT] * 4, bcT=[0.0] * 4, omega_ref=omega_ref, seed=seed,
+        n_steps=steps, name="adjoint_grid_%dx%dx%d" % (n, n, G), particle_capacity=1 << 23)
+
+
 def ensemble_slabs(n_instances: int = 256, seed: int = 0, steps: int = 100) -> List[Problem]:
     """Ensemble of independent 1D slabs with uneven sizes: cells U{64..1024},
     G in {8,16,32,64}, sigma0 log-U[1, 1e4], black-body T U[0.5, 2], target
@@ -185,34 +204,53 @@ def synthetic_state(p: Problem, n_particles: int, seed: int = 1, front: float = 
     that both the CUDA path and the oracle start from.
 
     Pure input generation: a temperature profile falling from 1 to T0 over
-    `front` of the slab; a spectral shape T^4 x (log-normal bump near
+    `front` of the slab (1D) or of the distance from the domain centre (2D,
+    the source patch sits there); a spectral shape T^4 x (log-normal bump near
     nu ~ 3T); n_particles particles placed in (cell, group) bins in
-    proportion to that shape, uniform in the cell, isotropic, with frequency
-    uniform in the group and weight omega_ref * U(0.5, 1.5); the wave part
-    rho_h = wave_fraction x the shape, and rho = rho_h + the particles' energy
-    per volume (so most of the radiation is carried by particles, as in a
-    running slab).  1D slabs only.
+    proportion to that shape, uniform in the cell, isotropic (3D directions
+    projected on the plane in 2D), with frequency uniform in the group and
+    weight omega_ref * U(0.5, 1.5); the wave part rho_h = wave_fraction x the
+    shape, and rho = rho_h + the particles' energy per volume (so most of the
+    radiation is carried by particles, as in a running problem).
     """
-    assert p.dim == 1
     rng = np.random.Generator(np.random.Philox(seed))
-    xc = (np.arange(p.nx) + 0.5) * p.dx
     T0 = float(np.min(p.T0))
-    L = p.nx * p.dx
-    T = T0 + (1.0 - T0) * np.sqrt(np.clip(1.0 - xc / (front * L), 0.0, None))
+    if p.dim == 1:
+        L = p.nx * p.dx
+        dist = (np.arange(p.nx) + 0.5) * p.dx
+        V = p.dx
+    else:
+        L = 0.5 * min(p.nx * p.dx, p.ny * p.dy)
+        xc = (np.arange(p.nx) + 0.5) * p.dx - 0.5 * p.nx * p.dx
+        yc = (np.arange(p.ny) + 0.5) * p.dy - 0.5 * p.ny * p.dy
+        dist = np.hypot(xc[None, :], yc[:, None]).reshape(-1)
+        V = p.dx * p.dy
+    ncell = p.ncell
+    T = T0 + (1.0 - T0) * np.sqrt(np.clip(1.0 - dist / (front * L), 0.0, None))
     if p.grey:
-        shape = np.ones((p.nx, 1))
+        shape = np.ones((ncell, 1))
     else:
         lnu = np.log(np.sqrt(p.nu_edges[:-1] * p.nu_edges[1:]))
         shape = np.exp(-0.5 * ((lnu[None, :] - np.log(3.0 * T[:, None])) / 0.7) ** 2)
         shape /= shape.sum(1, keepdims=True)
     field = ((T[:, None] ** 4) * shape).reshape(-1)
     prob = field / field.sum()
-    bins = rng.choice(p.nx * p.G, size=n_particles, p=prob)
+    bins = rng.choice(ncell * p.G, size=n_particles, p=prob)
     bins.sort()
     cell = (bins // p.G).astype(np.int32)
     grp = (bins % p.G).astype(np.int32)
-    x = (cell + rng.random(n_particles)) * p.dx
-    mu = 2.0 * rng.random(n_particles) - 1.0
+    if p.dim == 1:
+        x = (cell + rng.random(n_particles)) * p.dx
+        y = np.zeros(n_particles)
+        ox = 2.0 * rng.random(n_particles) - 1.0
+        oy = np.zeros(n_particles)
+    else:
+        x = (cell % p.nx + rng.random(n_particles)) * p.dx
+        y = (cell // p.nx + rng.random(n_particles)) * p.dy
+        muz = 2.0 * rng.random(n_particles) - 1.0
+        phi = 2.0 * np.pi * rng.random(n_particles)
+        sxy = np.sqrt(np.maximum(0.0, 1.0 - muz * muz))
+        ox, oy = sxy * np.cos(phi), sxy * np.sin(phi)
     if p.grey:
         nu = np.zeros(n_particles)
     else:
@@ -223,8 +261,7 @@ def synthetic_state(p: Problem, n_particles: int, seed: int = 1, front: float = 
     first = np.searchsorted(bins, bins, side="left")
     k = np.arange(n_particles) - first
     pid = (np.uint64(step) << np.uint64(44)) | (bins.astype(np.uint64) << np.uint64(20)) | k.astype(np.uint64)
-    parts = dict(x=x, y=np.zeros(n_particles), ox=mu, oy=np.zeros(n_particles), nu=nu, w=w,
-                 id=pid, cell=cell, grp=grp)
-    rho_p = np.bincount(bins, weights=w, minlength=p.nx * p.G) / p.dx
+    parts = dict(x=x, y=y, ox=ox, oy=oy, nu=nu, w=w, id=pid, cell=cell, grp=grp)
+    rho_p = np.bincount(bins, weights=w, minlength=ncell * p.G) / V
     rho_h = wave_fraction * field
     return dict(T=T, rho=rho_h + rho_p, rho_h=rho_h, particles=parts, step=step + 1)
