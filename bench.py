@@ -252,7 +252,7 @@ def ensemble_leg(B, dev, flush, steps, warmup, members=256, evolve=100, autotune
     return out
 
 
-def matched_error_leg(B, dev, steps=200, seeds=8, refine=16):
+def matched_error_leg(B, dev, steps=500, seeds=8, refine=16):
     """Tally error of the mixed build against the FP64 build on the physical
     200x30 slab run from its initial state: the reference is the mean of
     `seeds` FP64 runs with `refine` times more particles (omega_ref/refine);
@@ -326,6 +326,62 @@ def checkerboard_leg(B, dev, flush, steps, warmup, n_particles):
     return out
 
 
+def adjoint_leg(B, dev, steps=200, ckpt_every=20, n_fd=64, h=1e-6):
+    """Gradient of L = sum (T - T_target)^2 after 200 steps of the 2D 128x128x16
+    grid with respect to the 16384 per-cell log-opacity scales s ~ N(0, 0.1):
+    the adjoint (checkpoint every 20 steps) timed against the forward run, and
+    checked on 64 random cells against central differences with common random
+    numbers (the forward is bitwise reproducible, so a small h is usable)."""
+    import torch
+    from paper_2312_16981_gb300 import adjoint as A
+    p = I.adjoint_grid()
+    rng = np.random.Generator(np.random.Philox(5))
+    s = rng.normal(0.0, 0.1, p.ncell)
+    s_target = rng.normal(0.0, 0.1, p.ncell)
+    sim = B.Simulation(A.with_log_opacity(p.replace(seed=p.seed + 1), s_target), device=dev)
+    sim.step(steps)
+    T_target = sim.get_state(cap=0)["T"]
+    sim.close()
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L_plain = A.misfit(p, s, steps, T_target, device=dev)
+    t_fwd = time.perf_counter() - t0
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run = A.forward(A.with_log_opacity(p, s), steps, ckpt_every, dev)
+    t1 = time.perf_counter()
+    Tt = torch.as_tensor(T_target, device=run.T.device)
+    r = run.T - Tt
+    L = float((r * r).sum())
+    ds, iters = A.backward(run, 2.0 * r)
+    g = ds.cpu().numpy()
+    t2 = time.perf_counter()
+    unmatched = run.unmatched
+    n_end = run.sim.tallies()["n_particles"]
+    run.sim.close()
+
+    cells = rng.choice(p.ncell, size=n_fd, replace=False)
+    t3 = time.perf_counter()
+    fd, used, flipped = A.crn_finite_differences(p, s, steps, T_target, list(cells), h=h, device=dev, retries=2)
+    t_fd = time.perf_counter() - t3
+    floor = 1e-6 * float(np.max(np.abs(g)))
+    rel_all = np.abs(g[cells] - fd) / np.maximum(np.abs(fd), floor)
+    rel = rel_all[~flipped] if np.any(~flipped) else rel_all
+    return {"workload": "adjoint_grid_128x128x16, 200 steps, dt = dx/c, 16x16 T_s = 1 source",
+            "params": p.ncell, "loss": L, "loss_plain_forward": L_plain,
+            "forward_s": t_fwd, "forward_with_checkpoints_s": t1 - t0, "backward_s": t2 - t1,
+            "gradient_over_forward": (t2 - t0) / t_fwd, "checkpoint_every": ckpt_every,
+            "particles_at_end": n_end, "unmatched_across_checkpoints": int(unmatched),
+            "fd": {"cells": n_fd, "h": h, "h_min_used": float(np.min(used)),
+                   "decision_flip_unresolved": int(np.sum(flipped)),
+                   "compared": int(rel.size), "within_1e-3": int(np.sum(rel <= 1e-3)),
+                   "median_rel_err": float(np.median(rel)), "max_rel_err": float(np.max(rel)),
+                   "max_rel_err_incl_flipped": float(np.max(rel_all)),
+                   "rel_err_floor": "1e-6 x max |dL/ds|", "seconds": t_fd}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,6 +399,7 @@ def main():
     ap.add_argument("--no-matched-error", action="store_true", help="skip the matched-error leg")
     ap.add_argument("--ensemble-steps", type=int, default=10)
     ap.add_argument("--no-checkerboard", action="store_true", help="skip the 2D checkerboard leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the opacity-gradient leg")
     ap.add_argument("--checkerboard-particles", type=int, default=20_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -471,6 +528,8 @@ def main():
     if extra_legs and not args.no_checkerboard:
         line["checkerboard_2d"] = checkerboard_leg(B, dev, flush, min(K, 10), args.warmup,
                                                    args.checkerboard_particles)
+    if extra_legs and not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(B, dev)
     if extra_legs and not args.no_ensemble:
         line["batched_ensemble"] = ensemble_leg(B, dev, flush, args.ensemble_steps, args.warmup)
 

@@ -122,17 +122,59 @@ def misfit(p: Problem, s, steps: int, T_target, device: str = "cuda:0") -> float
     return float(np.sum((T - np.asarray(T_target)) ** 2))
 
 
+def misfit_with_decisions(p: Problem, s, steps: int, T_target, device: str = "cuda:0"):
+    """(L, fingerprint): the fingerprint lists, per step, the counts of births,
+    collisions, escapes, survivors and flight segments -- two runs with the
+    same fingerprint took the same Monte Carlo decisions (up to an exchange
+    that leaves every count unchanged)."""
+    sim = B.Simulation(with_log_opacity(p, s), device=device)
+    fp = []
+    for _ in range(steps):
+        sim.step(1)
+        t = sim.tallies()
+        fp.append((t["n_born"], t["n_absorbed"], t["n_escaped"], t["n_survived"], t["n_segments"]))
+    T = sim.get_state(cap=0)["T"]
+    st = sim.tallies()["status_bits"]
+    sim.close()
+    if st:
+        raise B.UGKWPError(-3, "forward run reported status bits %d" % st)
+    return float(np.sum((T - np.asarray(T_target)) ** 2)), tuple(fp)
+
+
 def crn_finite_differences(p: Problem, s, steps: int, T_target, cells: Sequence[int], h: float = 1e-6,
-                           device: str = "cuda:0") -> np.ndarray:
+                           device: str = "cuda:0", retries: int = 0):
     """Central differences (L(s + h e_i) - L(s - h e_i))/2h with the same seed
-    (common random numbers) for each listed cell i."""
+    (common random numbers) for each listed cell i.
+
+    With retries = 0, returns the differences.  With retries > 0, also checks
+    that the + and - runs took the same decisions as the unperturbed run (a
+    decision that flips inside [s - h, s + h] makes the difference measure a
+    jump, not a derivative) and, where one flipped, tries again with h/10, up
+    to `retries` times; returns (differences, h used per cell, flipped mask)."""
     s = np.asarray(s, dtype=np.float64)
     out = np.zeros(len(cells))
+    if retries <= 0:
+        for k, c in enumerate(cells):
+            e = np.zeros_like(s)
+            e[c] = h
+            out[k] = (misfit(p, s + e, steps, T_target, device) - misfit(p, s - e, steps, T_target, device)) / (2 * h)
+        return out
+    _, fp0 = misfit_with_decisions(p, s, steps, T_target, device)
+    used = np.zeros(len(cells))
+    flipped = np.zeros(len(cells), dtype=bool)
     for k, c in enumerate(cells):
-        e = np.zeros_like(s)
-        e[c] = h
-        out[k] = (misfit(p, s + e, steps, T_target, device) - misfit(p, s - e, steps, T_target, device)) / (2 * h)
-    return out
+        hk = h
+        for attempt in range(retries + 1):
+            e = np.zeros_like(s)
+            e[c] = hk
+            Lp, fpp = misfit_with_decisions(p, s + e, steps, T_target, device)
+            Lm, fpm = misfit_with_decisions(p, s - e, steps, T_target, device)
+            out[k], used[k] = (Lp - Lm) / (2 * hk), hk
+            flipped[k] = fpp != fp0 or fpm != fp0
+            if not flipped[k]:
+                break
+            hk *= 0.1
+    return out, used, flipped
 
 
 def _autograd():

@@ -122,6 +122,8 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.khat = cv.take<double>(nb);
   d.W = cv.take<double>(ncg);
   d.E_surv = cv.take<double>(ncg);
+  d.Wq = cv.take<unsigned long long>(2 * ncg);
+  d.Esq = cv.take<unsigned long long>(2 * ncg);
   d.esc = cv.take<double>(4 * G);
   d.inflow = cv.take<double>(4 * G);
   d.Fwave = cv.take<double>(nf * G);
@@ -199,6 +201,8 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
   d.capacity = p->particle_capacity;
+  d.tq = (p->omega_ref > 0.0 ? p->omega_ref : 1.0) * 0x1p-40;
+  d.tq_inv = 1.0 / d.tq;
   d.rec = nullptr;
   d.rec_cap = 0;
   d.tape = nullptr;

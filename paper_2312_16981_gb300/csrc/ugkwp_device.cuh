@@ -147,8 +147,11 @@ struct Dev {
   double* omega;    // [nbins]
   double* e_eff;    // [nbins]
   double* khat;     // [nbins] sampler slope in units of B(nu_mid)
-  double* W;        // [ncell*G]
-  double* E_surv;   // [ncell*G]
+  double* W;        // [ncell*G] (FP64 copy written by the source iteration)
+  double* E_surv;   // [ncell*G] (FP64 copy written by the source iteration)
+  unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
+  unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
+  double tq, tq_inv;         // fixed-point quantum omega_ref 2^-40 and its inverse
   double* esc;      // [4*G]
   double* inflow;   // [4*G]
   double* Fwave;    // [nface*G]
@@ -242,6 +245,45 @@ struct TapeRec {
   int c0, c1, slot, g;
   double w;
 };
+
+// Deterministic tallies.  W and E_surv are sums of particle weights added by
+// many threads in an order that changes from run to run; in FP64 that order
+// shows in the last bits, and through T in every later decision.  Each
+// weight is instead rounded once to a fixed quantum q (omega_ref 2^-40, about
+// 1e-12 of a reference weight) and the integers are added in 128 bits with
+// integer atomics, which commute: a run is bitwise reproducible.
+constexpr double kFixedRange = 0x1p57;   // |w/q| below this: a warp's 32 add up without overflow
+
+__device__ __forceinline__ long long to_fixed(double v, double q_inv, unsigned int* status) {
+  const double x = v * q_inv;
+  if (!(fabs(x) < kFixedRange)) {
+    atomicOr(status, 4u);   // ST_NONFINITE: weight out of the tally range
+    return 0;
+  }
+  return __double2ll_rn(x);
+}
+
+// 128-bit two's-complement add of a signed 64-bit increment: c[0] low word,
+// c[1] high word; the carry out of the low word is taken from its old value.
+__device__ __forceinline__ void atomic_add_fixed(unsigned long long* c, long long x) {
+  if (x == 0) return;
+  const unsigned long long ux = (unsigned long long)x;
+  const unsigned long long old = atomicAdd(c, ux);
+  const unsigned long long carry = (old + ux < old) ? 1ull : 0ull;
+  const unsigned long long hinc = (x < 0 ? ~0ull : 0ull) + carry;
+  if (hinc) atomicAdd(c + 1, hinc);
+}
+
+__device__ __forceinline__ double from_fixed(const unsigned long long* c, double q) {
+  unsigned long long lo = __ldcg(c), hi = __ldcg(c + 1);
+  const bool neg = (long long)hi < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  const double v = ((double)hi * 0x1p64 + (double)lo) * q;
+  return neg ? -v : v;
+}
 
 // Device control block: counters, status, barrier and reduction slots.
 struct Ctrl {

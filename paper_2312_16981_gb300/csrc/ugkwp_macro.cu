@@ -112,6 +112,8 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
       d.sigT[b] = sig;
       d.W[b] = 0.0;
       d.E_surv[b] = 0.0;
+      d.Wq[2 * b] = 0ull; d.Wq[2 * b + 1] = 0ull;
+      d.Esq[2 * b] = 0ull; d.Esq[2 * b + 1] = 0ull;
       const double rh = d.rho_h[b];
       E = (rh > 0.0 ? rh : 0.0) * d.vol;
     } else {
@@ -507,7 +509,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           const double r0 = d.rho[i];
           double r = r0 + (dt / d.dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
           if (d.dim == 2) r += (dt / d.dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
-          r += d.W[i] / V;
+          const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
+          d.W[i] = Wd;
+          r += Wd / V;
           if (d.src) { r += d.src[i]; e_src += V * d.src[i] / d.c; }
           d.R[i] = r;
           e_rad0 += V * r0 / d.c;
@@ -719,7 +723,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const double r = __ldcg(d.rho + i);
         // survivors never hold more than rho^{n+1} leaves in their (cell,
         // group): their weights are scaled to it (rho and the energy unchanged)
-        double rp = d.E_surv[i] / V, f = 1.0;
+        const double Es = from_fixed(d.Esq + 2 * i, d.tq);
+        d.E_surv[i] = Es;
+        double rp = Es / V, f = 1.0;
         if (rp > 0.0 && r < rp) {
           f = r > 0.0 ? r / rp : 0.0;
           rp = r > 0.0 ? r : 0.0;

@@ -29,10 +29,12 @@ __device__ __forceinline__ int find_bin(const uint32_t* __restrict__ off, int nb
   return lo;
 }
 
-// Sum v over runs of equal keys among consecutive lanes and add each run's
-// total once (keys < 0 contribute nothing).  Particles are held nearly sorted
-// by (cell, group), so a warp usually issues one atomic per run.
-__device__ __forceinline__ void warp_run_add(double* base, int key, double v) {
+// Sum the fixed-point weights v over runs of equal keys among consecutive
+// lanes and add each run's total once (keys < 0 contribute nothing).
+// Particles are held nearly sorted by (cell, group), so a warp usually
+// issues one 128-bit atomic per run.  Integer sums: the result does not
+// depend on which lanes meet in a warp.
+__device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int key, long long v) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int prev = __shfl_up_sync(full, key, 1);
@@ -41,47 +43,12 @@ __device__ __forceinline__ void warp_run_add(double* base, int key, double v) {
   const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double t = __shfl_up_sync(full, v, o);
+    const long long t = __shfl_up_sync(full, v, o);
     if (lane - o >= start) v += t;
   }
   const int nxt = __shfl_down_sync(full, key, 1);
   const bool tail = lane == 31 || nxt != key;
-  if (tail && key >= 0) atomicAdd(base + key, v);
-}
-
-// The same run aggregation for FP32 weights without FP64 arithmetic in the
-// warp: an error-free two-sum (Knuth) keeps each run's sum as hi + lo in
-// FP32 (about 48 bits), and only the tail lane converts it for the FP64
-// atomic.  On GB300 an FP64 warp instruction costs tens of cycles of an SM
-// sub-partition, so the double-precision version limited the mixed kernel.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void warp_run_add_f(double* base, int key, float v) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int prev = __shfl_up_sync(full, key, 1);
-  const bool head = lane == 0 || prev != key;
-  const unsigned heads = __ballot_sync(full, head);
-  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-  float hi = v, lo = 0.0f;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float th = __shfl_up_sync(full, hi, o);
-    const float tl = __shfl_up_sync(full, lo, o);
-    if (lane - o >= start) {
-      float s, e;
-      two_sum(hi, th, s, e);
-      hi = s;
-      lo = lo + tl + e;
-    }
-  }
-  const int nxt = __shfl_down_sync(full, key, 1);
-  const bool tail = lane == 31 || nxt != key;
-  if (tail && key >= 0) atomicAdd(base + key, (double)hi + (double)lo);
+  if (tail && key >= 0) atomic_add_fixed(base + 2 * (long long)key, v);
 }
 
 // Block compaction: exclusive rank of `flag` within the block plus the start
@@ -329,15 +296,16 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       }
     }
 
-    // ---- tallies
+    // ---- tallies (W and E_surv in fixed point, see to_fixed)
     const int lane = threadIdx.x & 31;
-    warp_run_add(d.E_surv, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, w);
+    const long long wq = valid ? to_fixed(w, d.tq_inv, &ctrl->status) : 0ll;
+    warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq);
     if (valid && fate != FATE_REMOVED) {
       const bool start_in = gside < 0;
       const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
       if (!(start_in && end_in && cell0 == cell)) {
-        if (start_in) atomicAdd(d.W + cell0 * G + g, -w);
-        if (end_in) atomicAdd(d.W + cell * G + g, w);
+        if (start_in) atomic_add_fixed(d.Wq + 2 * (cell0 * G + g), -wq);
+        if (end_in) atomic_add_fixed(d.Wq + 2 * (cell * G + g), wq);
       }
       if (!start_in) atomicAdd(d.inflow + gside * G + g, w);
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, w);
@@ -577,15 +545,16 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     }
     const int cell = cy * nx + cx;
 
-    // ---- tallies (FP64)
+    // ---- tallies (W and E_surv in fixed point, see to_fixed; FP64 side tallies)
     const int lane = threadIdx.x & 31;
-    warp_run_add_f(d.E_surv, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, w);
+    const long long wq = valid ? to_fixed((double)w, d.tq_inv, &ctrl->status) : 0ll;
+    warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq);
     if (valid && fate != FATE_REMOVED && (gside >= 0 || fate == FATE_ESCAPED || cell0 != cell)) {
       const double wd = (double)w;
       const bool start_in = gside < 0;
       const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
-      if (start_in) atomicAdd(d.W + cell0 * G + g, -wd);
-      if (end_in) atomicAdd(d.W + cell * G + g, wd);
+      if (start_in) atomic_add_fixed(d.Wq + 2 * (cell0 * G + g), -wq);
+      if (end_in) atomic_add_fixed(d.Wq + 2 * (cell * G + g), wq);
       if (!start_in) atomicAdd(d.inflow + gside * G + g, wd);
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, wd);
     }

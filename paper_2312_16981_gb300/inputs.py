@@ -141,7 +141,7 @@ def checkerboard_2d(n: int = 256, G: int = 30, block: int = 16, patch: int = 32,
 
 
 def adjoint_grid(n: int = 128, G: int = 16, patch: int = 16, steps: int = 200,
-                 omega_ref: float = 2.4e-8, seed: int = 0) -> Problem:
+                 omega_ref: float = 1e-9, seed: int = 0) -> Problem:
     """2D [0,1]^2 grid for the opacity-gradient workload: n x n cells, G log
     groups on [1e-3, 10], base sigma0 = 1e2 (sigma = sigma0 e^{s_c} nu^-3
     T^-1/2, capped at 1e6; the per-cell scales s_c are the parameters),
