@@ -48,7 +48,12 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def workload(rank: int = 0, n_particles: int = N_PARTICLES):
+def workload(rank: int = 0, n_particles: int = N_PARTICLES, name: str = "slab"):
+    if name == "checkerboard":
+        p = I.checkerboard_2d()
+        p.instance = rank
+        p.particle_capacity = max(p.particle_capacity, int(n_particles * 1.6))
+        return p, I.synthetic_state(p, n_particles, seed=3, front=0.35)
     p = I.multigroup_slab()
     p.instance = rank
     p.particle_capacity = max(p.particle_capacity, int(n_particles * 1.5))
@@ -57,9 +62,10 @@ def workload(rank: int = 0, n_particles: int = N_PARTICLES):
 
 
 def config_dict(p, n_particles, extra=None):
-    d = {"workload": WORKLOAD, "cells": p.ncell, "groups": p.G, "dt": p.dt,
+    d = {"workload": WORKLOAD if p.dim == 1 else p.name, "cells": p.ncell, "groups": p.G, "dt": p.dt,
          "particles_at_start": n_particles, "state": "seeded synthetic Marshak front",
-         "precision": "fp64", "l2": "flushed between timed steps (512 MiB write)"}
+         "precision": "mixed" if p.precision == I.MIXED else "fp64",
+         "l2": "flushed between timed steps (512 MiB write)"}
     if extra:
         d.update(extra)
     return d
@@ -146,12 +152,15 @@ def run_reference(args):
     return 0
 
 
-def algorithmic_bytes(p, phase, n_in, n_out, si_iters, mixed=False):
-    """Algorithmic HBM bytes of one launch of a phase (see the design notes)."""
+def algorithmic_bytes(p, phase, n_read, n_out, si_iters, mixed=False):
+    """Algorithmic HBM bytes of one launch of a phase: the particle kernel reads
+    the state of each particle alive at step start (newborns are born in
+    registers) and writes each survivor once, plus the tallies and bin tables."""
     ncg = p.ncell * p.G
     if phase == "particles":
-        per = (4 * 4 if mixed else 4 * 8) + 8 + 4   # x, mu, nu, w; id; bin key
-        return per * n_in + per * n_out + 3 * 8 * ncg
+        nf = (2 if p.dim == 1 else 4) + 2            # x (, y), mu (, Omega_y), nu, w
+        per = nf * (4 if mixed else 8) + 8 + 4       # + id, bin key
+        return per * n_read + per * n_out + 3 * 8 * ncg + 3 * 8 * p.nbins
     if phase == "source_iteration":
         return si_iters * 10 * 8 * ncg
     return 0
@@ -161,7 +170,7 @@ def timed_steps(sim, steps, flush, sampler=None):
     """Device time per step (CUDA events) with L2 flushed between steps."""
     import torch
     phases = np.zeros(6)
-    segs = n_in = n_out = si = 0
+    segs = n_proc = n_read = n_out = si = 0
     torch.cuda.synchronize()
     for _ in range(steps):
         flush.fill_(1)
@@ -169,12 +178,13 @@ def timed_steps(sim, steps, flush, sampler=None):
         t = sim.tallies()
         phases += np.array(ms)
         segs += t["n_segments"]
-        n_in += t["n_in"] + t["n_born"]
+        n_proc += t["n_in"] + t["n_born"]
+        n_read += t["n_in"]
         n_out += t["n_survived"]
         si += t["si_iters"]
     torch.cuda.synchronize()
     assert t["status_bits"] == 0, t["status_bits"]
-    return phases, segs, n_in, n_out, si
+    return phases, segs, (n_proc, n_read), n_out, si
 
 
 def device_ms(fn, flush=None):
@@ -316,7 +326,7 @@ def checkerboard_leg(B, dev, flush, steps, warmup, n_particles):
         sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
         for _ in range(max(warmup, 3)):
             sim.step(1)
-        ph, segs, n_in, n_out, si = timed_steps(sim, steps, flush)
+        ph, segs, (n_in, _), n_out, si = timed_steps(sim, steps, flush)
         out[name] = {"value": segs / (ph[0] / 1e3), "unit": "segments/s", "ms_per_step": float(ph[0] / steps),
                      "phase_ms_per_step": {n: float(ph[i] / steps) for i, n in enumerate(names)},
                      "particles_per_step": n_in / steps, "si_iters_per_step": si / steps}
@@ -395,6 +405,8 @@ def main():
                     help="timed steps of one precision only (no e2e, mixed or CPU legs): for profiler runs")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="particle precision of the headline (quick) run")
+    ap.add_argument("--workload", default="slab", choices=["slab", "checkerboard"],
+                    help="workload of a --quick run (profiling): the 200x30 slab or the 2D checkerboard")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-matched-error", action="store_true", help="skip the matched-error leg")
     ap.add_argument("--ensemble-steps", type=int, default=10)
@@ -424,7 +436,7 @@ def main():
     K = args.steps
     names = ["total", "birth_scan", "wave", "particles", "source_iteration", "end"]
     pk, src = peaks()
-    p, s = workload(rank, args.particles)
+    p, s = workload(rank, args.particles, args.workload if args.quick else "slab")
     if args.quick and args.precision == "mixed":
         p = p.replace(precision=I.MIXED)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -443,9 +455,9 @@ def main():
     # ---- timed regions: FP64, then mixed precision (device time, CUDA events)
     barrier()
     with ClockSampler(local) as clk:
-        phases, segs, n_in, n_out, si = timed_steps(sim, K, flush)
+        phases, segs, (n_in, n_rd), n_out, si = timed_steps(sim, K, flush)
         if simm is not None:
-            mph, msegs, min_, mout, msi = timed_steps(simm, K, flush)
+            mph, msegs, (min_, mrd), mout, msi = timed_steps(simm, K, flush)
     barrier()
     clocks = clk.summary()
     total_ms = float(phases[0])
@@ -462,7 +474,7 @@ def main():
     # ---- roofline of the dominant kernel (FP64 build)
     dom = int(np.argmax(phases[1:])) + 1
     per_launch_ms = phases[dom] / K
-    abytes = algorithmic_bytes(p, names[dom], n_in / K, n_out / K, si / K, mixed=p.precision == I.MIXED)
+    abytes = algorithmic_bytes(p, names[dom], n_rd / K, n_out / K, si / K, mixed=p.precision == I.MIXED)
     ach = abytes / (per_launch_ms * 1e-3) / 1e9 if abytes else 0.0
     roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
@@ -479,7 +491,7 @@ def main():
             "roofline": roof, "clocks": clocks}
 
     if simm is not None:
-        mb = algorithmic_bytes(p, "particles", min_ / K, mout / K, 0, mixed=True)
+        mb = algorithmic_bytes(p, "particles", mrd / K, mout / K, 0, mixed=True)
         mach = mb / (mph[3] / K * 1e-3) / 1e9
         line["mixed"] = {
             "value": msegs / (mph[0] / 1e3), "unit": "segments/s",

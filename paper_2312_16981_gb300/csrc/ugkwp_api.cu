@@ -1,6 +1,7 @@
 // ugkwp_api.cu -- host runtime behind the C ABI declared in include/ugkwp.h:
 // workspace layout, problem upload, the per-step launch sequence of
 // Algorithm 1, state and tally transfer, and the kernel-level entry points.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -194,6 +195,9 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.eps = p->eps;
   d.dt = p->dt;
   d.v = p->c / p->eps;
+  d.inv_dx = 1.0 / d.dx;
+  d.inv_dy = 1.0 / d.dy;
+  d.inv_c = 1.0 / p->c;
   d.rate_f = p->c / (p->eps * p->eps);
   d.omega_ref = p->omega_ref;
   d.si_tol = p->si_tol;
@@ -201,8 +205,18 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
   d.capacity = p->particle_capacity;
-  d.tq = (p->omega_ref > 0.0 ? p->omega_ref : 1.0) * 0x1p-40;
-  d.tq_inv = 1.0 / d.tq;
+  // fixed-point quantum of the tallies: the power of two just below omega_ref 2^-40
+  d.tq_shift = 40 - (p->omega_ref > 0.0 ? std::ilogb(p->omega_ref) : 0);
+  d.tq = std::ldexp(1.0, -d.tq_shift);
+  d.tq_inv = std::ldexp(1.0, d.tq_shift);
+  // FP32 copies for the mixed-precision particle kernel
+  d.dxf = (float)d.dx;
+  d.dyf = (float)d.dy;
+  d.vf = (float)d.v;
+  d.dtf = (float)d.dt;
+  d.inv_rate_f = (float)(p->eps * p->eps / p->c);
+  d.capf = p->sig_cap > 0.0 ? (float)p->sig_cap : INFINITY;
+  d.spf = (float)d.sig_p;
   d.rec = nullptr;
   d.rec_cap = 0;
   d.tape = nullptr;

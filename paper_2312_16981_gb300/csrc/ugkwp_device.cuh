@@ -151,7 +151,11 @@ struct Dev {
   double* E_surv;   // [ncell*G] (FP64 copy written by the source iteration)
   unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
   unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
-  double tq, tq_inv;         // fixed-point quantum omega_ref 2^-40 and its inverse
+  double inv_dx, inv_dy, inv_c;
+  double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-40) and its inverse
+  int tq_shift;
+  // FP32 copies of scalars (mixed-precision particle kernel)
+  float dxf, dyf, vf, dtf, inv_rate_f, capf, spf;
   double* esc;      // [4*G]
   double* inflow;   // [4*G]
   double* Fwave;    // [nface*G]
@@ -261,6 +265,25 @@ __device__ __forceinline__ long long to_fixed(double v, double q_inv, unsigned i
     return 0;
   }
   return __double2ll_rn(x);
+}
+
+// The same conversion for an FP32 weight without FP64 arithmetic: w = m 2^(e-150)
+// with a 24-bit integer m, so w/q = m 2^(e-150+shift) is formed with integer
+// shifts (exact while q is finer than w's last bit, else rounded half up).
+__device__ __forceinline__ long long to_fixed_f(float w, int shift, unsigned int* status) {
+  const unsigned b = __float_as_uint(w);
+  const int ex = (int)((b >> 23) & 0xffu);
+  if (ex == 0) return 0;                  // zero (or a subnormal weight, below any quantum)
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = ex - 150 + shift;
+  long long r;
+  if (ex == 255 || sh > 33) {             // non-finite or |w/q| >= 2^57
+    atomicOr(status, 4u);
+    return 0;
+  }
+  if (sh >= 0) r = m << sh;
+  else r = sh < -40 ? 0 : ((m + (1ll << (-sh - 1))) >> (-sh));
+  return (b >> 31) ? -r : r;
 }
 
 // 128-bit two's-complement add of a signed 64-bit increment: c[0] low word,
@@ -458,6 +481,18 @@ __device__ __forceinline__ double coef_f2(double x) {
   }
   const double e = exp(-x), E1 = -expm1(-x);
   return 2.0 * E1 / x - 1.0 - e;
+}
+
+// f2(x)/x (= C2/dt): the same series shifted by one power, or the closed form.
+__device__ __forceinline__ double coef_g2(double x) {
+  if (x < 1.0) {
+    double s = kA2[kSer];
+#pragma unroll
+    for (int k = kSer - 1; k >= 2; --k) s = fma(s, x, kA2[k]);
+    return s * x;
+  }
+  const double e = exp(-x), E1 = -expm1(-x);
+  return (2.0 * E1 / x - 1.0 - e) / x;
 }
 
 __device__ __forceinline__ double coef_f4(double x) {

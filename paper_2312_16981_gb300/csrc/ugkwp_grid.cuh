@@ -62,7 +62,7 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
                                             double* dphi) {
   const int lane = threadIdx.x & 31, G = d.G;
   const double sT = sigma_T(d, c, T);
-  const double ac = d.a * d.c, T3 = T * T * T;
+  const double ac = d.a * d.c, T3 = T * T * T, invT = 1.0 / T;
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
     const int g = lane + 32 * j;
@@ -73,13 +73,13 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
       continue;
     }
     EdgeVal lo;
-    if (g <= G && T > 0.0) lo = planck_edge(d.nu_edges[g] / T);
+    if (g <= G && T > 0.0) lo = planck_edge(d.nu_edges[g] * invT);
     else { lo.V = 0.0; lo.g4 = 0.0; lo.lower = true; }
     EdgeVal hi;
     hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
     hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
     hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
-    if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] / T);
+    if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] * invT);
     if (g < G) {
       sig[j] = sigma_group(d, sT, g);
       if (T > 0.0) {

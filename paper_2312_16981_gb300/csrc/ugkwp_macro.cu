@@ -412,10 +412,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
 // harmonic-mean opacity (App. B).  Both adjacent cells evaluate the same
 // expression with the same operand order, so the two copies agree bitwise.
 __device__ __forceinline__ double feq_face(const Dev& d, double sl, double su, double pl, double pu,
-                                           double h) {
-  const double sf = 2.0 * sl * su / (sl + su);
-  const double tau = 1.0 / (d.rate_f * sf);
-  return tau * coef_f2(d.dt / tau) * (d.v * d.v / 3.0) * (pu - pl) / h;
+                                           double inv_h) {
+  // x = dt/tau with 1/tau = rate sigma_f, sigma_f = 2 sl su/(sl + su); tau f2(x) = dt f2(x)/x
+  const double x = 2.0 * d.dt * d.rate_f * (sl * su) / (sl + su);
+  return d.dt * coef_g2(x) * (d.v * d.v / 3.0) * (pu - pl) * inv_h;
 }
 
 // Neighbour values across one face of cell c: opacity and Phi at iterate k,
@@ -558,12 +558,12 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int G = d.G;
       const double dt = d.dt;
       const double Tc = __ldcg(d.Tk[cur] + c), Tn = d.T[c], cv = d.cv[c];
-      double Q[NC], a[NC], phc[NC], dpc[NC];
+      double Q[NC], a[NC], r1[NC], phc[NC], dpc[NC];
       double num = 0.0, den = 0.0;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
-        Q[j] = 0.0; a[j] = 0.0; phc[j] = 0.0; dpc[j] = 0.0;
+        Q[j] = 0.0; a[j] = 0.0; r1[j] = 1.0; phc[j] = 0.0; dpc[j] = 0.0;
         if (g >= G) continue;
         const int i = c * G + g;
         const double sc = __ldcg(d.sigk[cur] + i);
@@ -572,13 +572,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         double q = d.R[i];
         for (int axis = 0; axis < d.dim; ++axis) {
           const double h = axis == 0 ? d.dx : d.dy;
+          const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
             double sn, pn;
             int nc;
             double F = 0.0;
             if (neighbour(d, c, axis, dir, g, cur, sc, &sn, &pn, &nc)) {
-              F = dir < 0 ? feq_face(d, sn, sc, pn, phc[j], h) : feq_face(d, sc, sn, phc[j], pn, h);
+              F = dir < 0 ? feq_face(d, sn, sc, pn, phc[j], inv_h) : feq_face(d, sc, sn, phc[j], pn, inv_h);
             }
             const bool owner = dir > 0 ? true : (nc < 0);   // upper face, or a boundary face
             if (owner) d.Feq[face_index(d, c, axis, dir) * G + g] = F;
@@ -588,7 +589,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         }
         Q[j] = q;
         a[j] = dt * d.rate_f * sc;
-        const double ap = a[j] / d.c / (1.0 + a[j]);
+        r1[j] = 1.0 / (1.0 + a[j]);
+        const double ap = a[j] * d.inv_c * r1[j];
         num += ap * (q - phc[j] + dpc[j] * Tc);
         den += ap * dpc[j];
       }
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const int g = lane + 32 * j;
         if (g >= G) continue;
         const int i = c * G + g;
-        const double r = (Q[j] + a[j] * (phc[j] + dpc[j] * (Tnew - Tc))) / (1.0 + a[j]);
+        const double r = (Q[j] + a[j] * (phc[j] + dpc[j] * (Tnew - Tc))) * r1[j];
         dmax = fmax(dmax, fabs(r - __ldcg(d.rho + i)));
         rsum += fabs(r);
         __stcg(d.rho + i, r);

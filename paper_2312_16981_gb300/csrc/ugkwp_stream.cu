@@ -383,10 +383,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   const long long n_tot = n_surv + (long long)ctrl->n_new;
   const uint32_t step = (uint32_t)ctrl->step;
   const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
-  const float dxf = (float)d.dx, dyf = (float)d.dy, vf = (float)d.v, dtf = (float)d.dt;
-  const float inv_rate = (float)(d.eps * d.eps / d.c);
-  const float capf = d.sig_cap > 0.0 ? (float)d.sig_cap : INFINITY;
-  const float spf = (float)d.sig_p;
+  const float dxf = d.dxf, dyf = d.dyf, vf = d.vf, dtf = d.dtf;
+  const float inv_rate = d.inv_rate_f, capf = d.capf, spf = d.spf;
   const float* __restrict__ in_x = d.fx[cur];
   const float* __restrict__ in_y = d.fy[cur];
   const float* __restrict__ in_ox = d.fox[cur];
@@ -547,7 +545,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
 
     // ---- tallies (W and E_surv in fixed point, see to_fixed; FP64 side tallies)
     const int lane = threadIdx.x & 31;
-    const long long wq = valid ? to_fixed((double)w, d.tq_inv, &ctrl->status) : 0ll;
+    const long long wq = valid ? to_fixed_f(w, d.tq_shift, &ctrl->status) : 0ll;
     warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq);
     if (valid && fate != FATE_REMOVED && (gside >= 0 || fate == FATE_ESCAPED || cell0 != cell)) {
       const double wd = (double)w;
