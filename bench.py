@@ -38,6 +38,11 @@ N_PARTICLES = 1_000_000
 WORKLOAD = "multigroup_slab_200x30_fp64"
 METRIC = "particle segments/s"
 KERNELS_PER_STEP = 9   # birth, scan x3, wave, particles, source iteration, end of step, survivor scaling
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per processed
+# particle of the particle kernels, from one ncu capture of each at 4e6
+# particles on the slab (the traffic grows with the particles processed); the
+# roofline's "traffic" is this times the particles a launch processes.
+TRAFFIC_PER_PROCESSED = {"fp64": 317.39e6 / 4.142e6, "mixed": 183.17e6 / 4.142e6}
 
 
 def peaks():
@@ -476,9 +481,13 @@ def main():
     per_launch_ms = phases[dom] / K
     abytes = algorithmic_bytes(p, names[dom], n_rd / K, n_out / K, si / K, mixed=p.precision == I.MIXED)
     ach = abytes / (per_launch_ms * 1e-3) / 1e9 if abytes else 0.0
+    mixed_run = p.precision == I.MIXED
+    traffic = (TRAFFIC_PER_PROCESSED["mixed" if mixed_run else "fp64"] * n_in / K
+               if names[dom] == "particles" and p.dim == 1 else None)
     roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
-            "peak_source": src, "algorithmic_bytes_per_launch": abytes}
+            "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": traffic,
+            "peak_source": src, "algorithmic_bytes_per_launch": abytes,
+            "traffic_source": "ncu capture at 4e6 particles, scaled by particles processed per launch"}
 
     line = {"metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": total_ms_max / K,
@@ -501,7 +510,8 @@ def main():
             "phase_ms_per_step": {n: float(mph[i] / K) for i, n in enumerate(names)},
             "particle_kernel_roofline": {"bound": "hbm", "achieved": mach, "peak": pk["hbm_gbs"],
                                          "unit": "GB/s", "frac": mach / pk["hbm_gbs"],
-                                         "algorithmic_bytes_per_launch": mb}}
+                                         "algorithmic_bytes_per_launch": mb,
+                                         "traffic": TRAFFIC_PER_PROCESSED["mixed"] * min_ / K}}
         simm.close()
 
         # ---- end to end through the C ABI with host buffers
