@@ -36,6 +36,7 @@ class CProblem(C.Structure):
         ("sig_p", C.c_double), ("sig_q", C.c_double), ("sig_cap", C.c_double),
         ("a", C.c_double), ("c", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
         ("omega_ref", C.c_double), ("si_tol", C.c_double), ("src_on", C.c_double),
+        ("tau_num_C", C.c_double),
         ("bcT", C.c_double * 4),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("_pad1", C.c_uint32),
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("src_T", _dp),
@@ -107,6 +108,8 @@ def lib():
             _dp, _dp, _dp, _dp, C.POINTER(CParticles), C.c_int64, C.POINTER(C.c_int64),
             C.c_void_p, C.c_int64, C.POINTER(CTallies)]
         L.or_init_rho.argtypes = [C.POINTER(CProblem), _dp, _dp]
+        L.or_x_num.argtypes = [C.POINTER(CProblem), _dp, C.c_int, C.c_int]
+        L.or_x_num.restype = C.c_double
         L.or_dsigma_group.argtypes = [C.POINTER(CProblem), C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_double]
         L.or_dsigma_group.restype = C.c_double
@@ -145,6 +148,7 @@ class OracleProblem:
         s.sig_p, s.sig_q, s.sig_cap = p.sig_p, p.sig_q, p.sig_cap
         s.a, s.c, s.eps, s.dt = p.a, p.c, p.eps, p.dt
         s.omega_ref, s.si_tol, s.src_on = p.omega_ref, p.si_tol, p.src_on
+        s.tau_num_C = float(getattr(p, "tau_num_C", 0.0))
         s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
         s.nu_edges, s.sigma0, s.cv = _d(self.nu_edges), _d(self.sigma0), _d(self.cv)
         s.src_T = _d(self.src_T) if self.src_T is not None else None
@@ -493,3 +497,8 @@ def misfit_tangent(p, steps: int, T_target, ds, cap: Optional[int] = None):
             raise RuntimeError("oracle tangent step failed with status %d" % status)
     r = st.T - T_target
     return float(np.sum(r * r)), float(np.sum(2.0 * r * tg.dT)), st
+
+
+def x_num(prob: OracleProblem, T, c: int, g: int) -> float:
+    """Delta t / tau_num of cell c, group g at temperatures T."""
+    return lib().or_x_num(prob.ref, _d(np.ascontiguousarray(T, dtype=np.float64)), c, g)

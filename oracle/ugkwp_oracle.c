@@ -409,6 +409,30 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
  * E = e (c/eps)/4 Phi_g(T_b) dt through the wall (the half-range flux of an
  * isotropic ghost).  They are sampled directly (see or_step).  Bins are
  * ordered interior cells (c*G + g) then ghosts ((ncell + side)*G + g).      */
+/* Numerical collision time for the thin/thick joint (Sec. 3.2, heterogeneous
+ * cases): tau_num = tau + C (T^l - T^r)/(T^l + T^r) dt is written per
+ * interface.  Readings: the magnitude of the temperature contrast (the stated
+ * aim is more sampled particles, tau_num >= tau), and a cell takes the
+ * largest contrast over its interior faces.  Returns dt/tau_num =
+ * x/(1 + C J x) with x = dt/tau. */
+double or_x_num(const or_problem* P, const double* T, int c, int g) {
+  const double rate_f = P->c / (P->eps * P->eps);
+  const double x = P->dt * rate_f * or_sigma_group(P, c, g, T[c]);
+  if (!(P->tau_num_C > 0.0)) return x;
+  const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1;
+  const int ix = c % nx, iy = c / nx;
+  double J = 0.0;
+  const int nb[4][2] = {{ix - 1, iy}, {ix + 1, iy}, {ix, iy - 1}, {ix, iy + 1}};
+  for (int k = 0; k < (P->dim == 2 ? 4 : 2); ++k) {
+    const int jx = nb[k][0], jy = nb[k][1];
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+    const double Tn = T[jy * nx + jx];
+    const double j = fabs(T[c] - Tn) / (T[c] + Tn);
+    if (j > J) J = j;
+  }
+  return x / (1.0 + P->tau_num_C * J * x);
+}
+
 int or_birth_counts(const or_problem* P, const double* T, const double* rho_h,
                     or_tallies* tal, int64_t* n_new) {
   const int ncell = ncell_of(P), G = P->G, nbins = (ncell + 4) * G;
@@ -432,8 +456,10 @@ int or_birth_counts(const or_problem* P, const double* T, const double* rho_h,
       Tb = P->bcT[side];
       E = 0.25 * (P->c / P->eps) * or_phi(P, g, Tb) * P->dt;
     }
-    double sig = or_sigma_group(P, src_cell, g, Tb);
-    double e = exp(-P->dt * rate_f * sig);
+    double x;
+    if (cell < ncell) x = or_x_num(P, T, cell, g);
+    else x = P->dt * rate_f * or_sigma_group(P, src_cell, g, Tb);
+    double e = exp(-x);
     E *= e;
     if (!(P->omega_ref > 0.0) || !(E > 0.0)) continue;
     double q = floor(E / P->omega_ref + 0.5);
@@ -533,14 +559,20 @@ int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
           }
 #undef RHO_AT
           /* side opacities and sampled fractions */
-          double sgl, sgr, el, er;
-          if (lin) { sgl = or_sigma_group(P, CELL_AT(kL), g, T[CELL_AT(kL)]); el = e_eff[CELL_AT(kL) * G + g]; }
-          else if (P->bc[sideL] == OR_BC_BLACKBODY) {
+          double sgl, sgr, el, er, xhl = 0.0, xhr = 0.0;
+          if (lin) {
+            sgl = or_sigma_group(P, CELL_AT(kL), g, T[CELL_AT(kL)]); el = e_eff[CELL_AT(kL) * G + g];
+            xhl = or_x_num(P, T, CELL_AT(kL), g);
+          } else if (P->bc[sideL] == OR_BC_BLACKBODY) {
             sgl = or_sigma_group(P, CELL_AT(0), g, P->bcT[sideL]); el = e_eff[(ncell + sideL) * G + g];
+            xhl = dt * rate_f * sgl;
           } else { sgl = -1.0; el = 0.0; }
-          if (rin) { sgr = or_sigma_group(P, CELL_AT(kR), g, T[CELL_AT(kR)]); er = e_eff[CELL_AT(kR) * G + g]; }
-          else if (P->bc[sideR] == OR_BC_BLACKBODY) {
+          if (rin) {
+            sgr = or_sigma_group(P, CELL_AT(kR), g, T[CELL_AT(kR)]); er = e_eff[CELL_AT(kR) * G + g];
+            xhr = or_x_num(P, T, CELL_AT(kR), g);
+          } else if (P->bc[sideR] == OR_BC_BLACKBODY) {
             sgr = or_sigma_group(P, CELL_AT(nk - 1), g, P->bcT[sideR]); er = e_eff[(ncell + sideR) * G + g];
+            xhr = dt * rate_f * sgr;
           } else { sgr = -1.0; er = 0.0; }
           if (sgl < 0.0) sgl = sgr;          /* vacuum ghost: inner opacity */
           if (sgr < 0.0) sgr = sgl;
@@ -549,8 +581,8 @@ int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
           double tau_f = 1.0 / (rate_f * sf);
           double x_f = dt / tau_f;
           double AL, BL, AR, BR;
-          half_coefs(x_f, tau_f, dt * rate_f * sgl, el, dt, &AL, &BL);
-          half_coefs(x_f, tau_f, dt * rate_f * sgr, er, dt, &AR, &BR);
+          half_coefs(x_f, tau_f, xhl, el, dt, &AL, &BL);
+          half_coefs(x_f, tau_f, xhr, er, dt, &AR, &BR);
           Fwave[fidx * G + g] = AL * (v / 4.0) * fl - AR * (v / 4.0) * fr
                               + (BL * sl + BR * sr) * (v * v / 6.0);
         }

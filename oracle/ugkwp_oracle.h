@@ -40,6 +40,7 @@ typedef struct {
   double omega_ref;               /* reference particle energy (rho*V units) */
   double si_tol;
   double src_on;                  /* multiplies the patch source */
+  double tau_num_C;               /* C of the numerical collision time (0: tau_num = tau) */
   double bcT[4];
   uint64_t seed;
   uint32_t instance;
@@ -111,6 +112,11 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
                        or_tallies* tal, int32_t* nseg, double* t_end,
                        double* trace_x, double* trace_t, int trace_cap, int* n_trace);
 
+/* Delta t / tau_num for cell c, group g at T (Sec. 3.2, thin/thick joint):
+ * tau_num = tau + C J Delta t with J the largest |T_c - T_n|/(T_c + T_n) over
+ * the cell's interior faces; equals Delta t / tau when C = 0. */
+double or_x_num(const or_problem* P, const double* T, int c, int g);
+
 int or_birth_counts(const or_problem* P, const double* T, const double* rho_h,
                     or_tallies* tal, int64_t* n_new);
 
@@ -164,6 +170,7 @@ int    or_wave_flux_tangent(const or_problem* P, const double* T, const double* 
 int    or_source_iteration_tangent(const or_problem* P, const double* dT_n, const double* ds,
                                    const double* dR, const double* T, const double* rho,
                                    double* dT_out, double* drho_out, int* iters);
+/* (tau_num_C must be 0: OR_ERR_ARG otherwise.) */
 int    or_step_tangent(const or_problem* P, int64_t step, const double* ds,
                        const double* T, const double* dT, const double* rho, const double* drho,
                        const double* rho_h, const double* drho_h,
