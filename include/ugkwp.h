@@ -63,7 +63,11 @@ enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
  *   frequency dependence, Phi = a c T^4.
  *   Boundary sides: REFLECT (mirror), VACUUM (no inflow), BLACKBODY at bcT
  *   (1D only in this build).  src_T: a cell with src_T > 0 receives
- *   src_on * c * dt * Phi_g(src_T) in rho_g each step. */
+ *   src_on * c * dt * Phi_g(src_T) in rho_g each step.
+ *   tau_num_C: the numerical collision time of the heterogeneous cases
+ *   (Sec. 3.2), tau_num = tau + C J dt with J the largest temperature contrast
+ *   |T_c - T_n|/(T_c + T_n) over a cell's interior faces, replaces tau in the
+ *   sampled fraction e = exp(-dt/tau_num) (births and wave flux); 0 keeps tau. */
 typedef struct ugkwp_problem {
   int32_t dim;            /* 1 or 2 */
   int32_t nx, ny;         /* cells; ny ignored (1) in 1D */
@@ -80,6 +84,7 @@ typedef struct ugkwp_problem {
   double omega_ref;       /* reference particle energy (rho*V units), <= 0: no particles */
   double si_tol;          /* source-iteration tolerance (relative, max norm) */
   double src_on;
+  double tau_num_C;       /* thin/thick joint sampling: tau_num = tau + C J dt (0: off) */
   double bcT[4];
   uint64_t seed;          /* Philox key = (seed_lo, seed_hi ^ instance) */
   uint32_t instance;

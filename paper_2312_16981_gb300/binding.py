@@ -41,6 +41,7 @@ class CProblem(C.Structure):
         ("sig_p", C.c_double), ("sig_q", C.c_double), ("sig_cap", C.c_double),
         ("a", C.c_double), ("c", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
         ("omega_ref", C.c_double), ("si_tol", C.c_double), ("src_on", C.c_double),
+        ("tau_num_C", C.c_double),
         ("bcT", C.c_double * 4), ("seed", C.c_uint64), ("instance", C.c_uint32),
         ("_pad1", C.c_uint32), ("particle_capacity", C.c_int64),
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("T0", _dp), ("rho0", _dp),
@@ -185,6 +186,7 @@ class _HostProblem:
         s.sig_p, s.sig_q, s.sig_cap = p.sig_p, p.sig_q, p.sig_cap
         s.a, s.c, s.eps, s.dt = p.a, p.c, p.eps, p.dt
         s.omega_ref, s.si_tol, s.src_on = p.omega_ref, p.si_tol, p.src_on
+        s.tau_num_C = float(p.tau_num_C)
         s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
         s.particle_capacity = int(p.particle_capacity)
         s.nu_edges = arr(p.nu_edges, p.G + 1)

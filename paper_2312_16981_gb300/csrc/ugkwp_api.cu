@@ -80,6 +80,7 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
   if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED)
     return fail(h, UGKWP_ERR_ARG, "precision must be UGKWP_FP64 or UGKWP_MIXED");
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
+  if (!(p->tau_num_C >= 0.0)) return fail(h, UGKWP_ERR_ARG, "tau_num_C must be >= 0");
   const long long nbins = (ncell_of(p) + 4) * p->G;
   if (nbins >= (1ll << 24)) return fail(h, UGKWP_ERR_ARG, "(ncell+4)*G must be < 2^24 (particle id layout)");
   return UGKWP_OK;
@@ -115,10 +116,12 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.rho_p = cv.take<double>(ncg);
   d.sigT = cv.take<double>(ncg);
   d.sT = cv.take<double>(nc);
+  d.sTinv = cv.take<double>(nc);
   d.N = cv.take<uint32_t>(nb);
   d.off = cv.take<uint32_t>(nb + 1);
   d.part = cv.take<uint32_t>(ugkwp::scan_parts(nb) + 1);
   d.omega = cv.take<double>(nb);
+  d.xnum = cv.take<double>(nb);
   d.e_eff = cv.take<double>(nb);
   d.khat = cv.take<double>(nb);
   d.W = cv.take<double>(ncg);
@@ -142,6 +145,7 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   *src_T_tmp = d.R;   // scratch during init only
   const bool mixed = p->precision == UGKWP_MIXED;
   d.sT_f = mixed ? cv.take<float>(nc) : nullptr;
+  d.sTinv_f = mixed ? cv.take<float>(nc) : nullptr;
   d.omega_f = mixed ? cv.take<float>(nb) : nullptr;
   d.khat_f = mixed ? cv.take<float>(nb) : nullptr;
   d.particles_begin = nullptr;
@@ -202,11 +206,12 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.omega_ref = p->omega_ref;
   d.si_tol = p->si_tol;
   d.src_on = p->src_on;
+  d.tau_num_C = p->tau_num_C;
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
   d.capacity = p->particle_capacity;
-  // fixed-point quantum of the tallies: the power of two just below omega_ref 2^-40
-  d.tq_shift = 40 - (p->omega_ref > 0.0 ? std::ilogb(p->omega_ref) : 0);
+  // fixed-point quantum of the tallies: the power of two just below omega_ref 2^-48
+  d.tq_shift = 48 - (p->omega_ref > 0.0 ? std::ilogb(p->omega_ref) : 0);
   d.tq = std::ldexp(1.0, -d.tq_shift);
   d.tq_inv = std::ldexp(1.0, d.tq_shift);
   // FP32 copies for the mixed-precision particle kernel
@@ -217,6 +222,8 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.inv_rate_f = (float)(p->eps * p->eps / p->c);
   d.capf = p->sig_cap > 0.0 ? (float)p->sig_cap : INFINITY;
   d.spf = (float)d.sig_p;
+  d.inv_cap = p->sig_cap > 0.0 ? 1.0 / p->sig_cap : 0.0;
+  d.inv_capf = (float)d.inv_cap;
   d.rec = nullptr;
   d.rec_cap = 0;
   d.tape = nullptr;
@@ -771,6 +778,8 @@ int adjoint_check(ugkwp_handle* h) {
   if (h->M > 1) return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint is for single-problem handles");
   if (h->d.precision != UGKWP_FP64)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint tape is written by the FP64 particle kernel");
+  if (h->d.tau_num_C != 0.0)
+    return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates tau, not tau_num (tau_num_C = 0)");
   return UGKWP_OK;
 }
 }  // namespace

@@ -122,7 +122,7 @@ struct Dev {
   double dx, dy, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
   double v;          // c/eps, particle speed
   double rate_f;     // c/eps^2: 1/tau = rate_f * sigma
-  double omega_ref, si_tol, src_on;
+  double omega_ref, si_tol, src_on, tau_num_C;
   double bcT[4];
   uint32_t key0, key1;
   long long capacity;
@@ -141,10 +141,12 @@ struct Dev {
   // per-step work arrays
   double* sigT;     // [ncell*G] sigma_g(T^n)
   double* sT;       // [ncell]   sigma0 T^q
+  double* sTinv;    // [ncell]   1/(sigma0 T^q)
   uint32_t* N;      // [nbins]
   uint32_t* off;    // [nbins+1] exclusive scan of N
   uint32_t* part;   // [scan partials]
   double* omega;    // [nbins]
+  double* xnum;     // [nbins] dt/tau_num of the bin (dt/tau where tau_num_C = 0)
   double* e_eff;    // [nbins]
   double* khat;     // [nbins] sampler slope in units of B(nu_mid)
   double* W;        // [ncell*G] (FP64 copy written by the source iteration)
@@ -152,10 +154,11 @@ struct Dev {
   unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
   unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
   double inv_dx, inv_dy, inv_c;
-  double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-40) and its inverse
+  double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-48) and its inverse
   int tq_shift;
   // FP32 copies of scalars (mixed-precision particle kernel)
-  float dxf, dyf, vf, dtf, inv_rate_f, capf, spf;
+  float dxf, dyf, vf, dtf, inv_rate_f, capf, spf, inv_capf;
+  double inv_cap;            // 1/sig_cap, or 0 without a cap
   double* esc;      // [4*G]
   double* inflow;   // [4*G]
   double* Fwave;    // [nface*G]
@@ -183,6 +186,7 @@ struct Dev {
   float* fnu[2];
   float* fw[2];
   float* sT_f;      // [ncell] sigma0 T^q
+  float* sTinv_f;   // [ncell] 1/(sigma0 T^q)
   float* omega_f;   // [nbins]
   float* khat_f;    // [nbins]
   float* nu_edges_f;       // [G+1] group edges in FP32
@@ -253,9 +257,11 @@ struct TapeRec {
 // Deterministic tallies.  W and E_surv are sums of particle weights added by
 // many threads in an order that changes from run to run; in FP64 that order
 // shows in the last bits, and through T in every later decision.  Each
-// weight is instead rounded once to a fixed quantum q (omega_ref 2^-40, about
-// 1e-12 of a reference weight) and the integers are added in 128 bits with
-// integer atomics, which commute: a run is bitwise reproducible.
+// weight is instead rounded once to a fixed quantum q (a power of two between
+// omega_ref 2^-49 and omega_ref 2^-48, a few 1e-15 of a reference weight) and
+// the integers are added in 128 bits with integer atomics, which commute: a
+// run is bitwise reproducible.  Weights up to 2^57 q (at least 256 omega_ref)
+// are representable; a larger one sets the non-finite status bit.
 constexpr double kFixedRange = 0x1p57;   // |w/q| below this: a warp's 32 add up without overflow
 
 __device__ __forceinline__ long long to_fixed(double v, double q_inv, unsigned int* status) {
@@ -329,6 +335,7 @@ struct Ctrl {
 __device__ __forceinline__ double pow_fast(double b, double e) {
   if (e == 0.0) return 1.0;
   if (e == -3.0) return 1.0 / (b * b * b);
+  if (e == 3.0) return b * b * b;
   if (e == -0.5) return 1.0 / sqrt(b);
   if (e == 1.0) return b;
   return pow(b, e);
@@ -572,6 +579,30 @@ __device__ __forceinline__ CoefDeriv coef_derivs(double x) {
   return r;
 }
 
+// f4, f5 and c4 at one x together (the wave flux needs all three per face):
+// one Horner loop with three accumulators below x = 1, one exp/expm1 above.
+__device__ __forceinline__ void coef_f4_f5_c4(double x, double* f4, double* f5, double* c4) {
+  if (x < 1.0) {
+    double s4 = kA4[kSer], s5 = kA5[kSer], sc = kAC4[kSer];
+#pragma unroll
+    for (int k = kSer - 1; k >= 2; --k) {
+      s4 = fma(s4, x, kA4[k]);
+      s5 = fma(s5, x, kA5[k]);
+      sc = fma(sc, x, kAC4[k]);
+    }
+    s4 = fma(s4, x, kA4[1]);
+    sc = fma(fma(sc, x, kAC4[1]), x, kAC4[0]);
+    *f4 = s4 * x;
+    *f5 = s5 * x * x;
+    *c4 = sc;
+    return;
+  }
+  const double e = exp(-x), m1 = expm1(-x);   // m1 = e - 1
+  *c4 = -m1 / x;
+  *f4 = *c4 - e;
+  *f5 = e * (1.0 + 0.5 * x) - *c4;
+}
+
 // --------------------------------------------------------------------------
 // Linear-frequency sampling (Eqs. Blinear, kg; App. A).  With B in units of
 // B(nu_mid) and slope khat clamped to |khat| <= 2/dnu (non-negative density),
@@ -614,6 +645,7 @@ __device__ __forceinline__ float sample_nu_f(float nlo, float nhi, float khat, f
 __device__ __forceinline__ float pow_fast_f(float b, float e) {
   if (e == 0.0f) return 1.0f;
   if (e == -3.0f) return __frcp_rn(b * b * b);
+  if (e == 3.0f) return b * b * b;
   if (e == -0.5f) return rsqrtf(b);
   if (e == 1.0f) return b;
   return __powf(b, e);

@@ -106,7 +106,11 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
       const double sT = sigma_T(d, cell, Tb);
       if (g == 0) {
         d.sT[cell] = sT;
-        if (d.sT_f) d.sT_f[cell] = (float)sT;
+        d.sTinv[cell] = 1.0 / sT;
+        if (d.sT_f) {
+          d.sT_f[cell] = (float)sT;
+          d.sTinv_f[cell] = (float)(1.0 / sT);
+        }
       }
       sig = sigma_group(d, sT, g);
       d.sigT[b] = sig;
@@ -129,7 +133,23 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
       Tb = d.bcT[side];
       E = 0.25 * d.v * d.ghost_phi[side * G + g] * d.dt;
     }
-    const double e = exp(-d.dt * d.rate_f * sig);
+    // sampled fraction e = exp(-dt/tau_num): tau_num = tau + C J dt at thin/thick
+    // joints (Sec. 3.2), J the largest |T_c - T_n|/(T_c + T_n) over the cell's
+    // interior faces; x = dt/tau when C = 0
+    double x = d.dt * d.rate_f * sig;
+    if (cell < d.ncell && d.tau_num_C > 0.0) {
+      const int ix = cell % d.nx, iy = cell / d.nx, nyy = d.dim == 2 ? d.ny : 1;
+      double J = 0.0;
+      for (int k = 0; k < 2 * d.dim; ++k) {
+        const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0)), jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+        if (jx < 0 || jx >= d.nx || jy < 0 || jy >= nyy) continue;
+        const double Tn = d.T[jy * d.nx + jx];
+        J = fmax(J, fabs(Tb - Tn) / (Tb + Tn));
+      }
+      x = x / (1.0 + d.tau_num_C * J * x);
+    }
+    d.xnum[b] = x;
+    const double e = exp(-x);
     E *= e;
     uint32_t N = 0;
     double w = 0.0, ee = 0.0;
@@ -299,17 +319,18 @@ __global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
   if (threadIdx.x == 0) e.tile0[e.M] = s_carry;
 }
 
-// A = C4_f - e_h, B = C5_f + dt e_h/2 of one half (face coefficients, upwind e).
+// A = C4_f - e_h, B = C5_f + dt e_h/2 of one half (face coefficients f4, f5,
+// c4 at x_f shared by both halves; upwind e).
 __device__ __forceinline__ void half_coefs(double xf, double tauf, double xh, double e_eff,
-                                           double dt, double* A, double* B) {
-  const double f4 = coef_f4(xf);
+                                           double dt, double f4, double f5, double c4,
+                                           double* A, double* B) {
   if (e_eff > 0.0) {
     const double dd = xh - xf;
     const double efh = fabs(dd) < 0.5 ? exp(-xh) * expm1(dd) : exp(-xf) - exp(-xh);
     *A = f4 + efh;
-    *B = tauf * coef_f5(xf) - 0.5 * dt * efh;
+    *B = tauf * f5 - 0.5 * dt * efh;
   } else {
-    *A = coef_c4(xf);
+    *A = c4;
     *B = -tauf * f4;
   }
 }
@@ -350,31 +371,36 @@ __global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
       fl = rl;
       fr = rr;
     }
-    double sgl = -1.0, sgr = -1.0, el = 0.0, er = 0.0;
+    double sgl = -1.0, sgr = -1.0, el = 0.0, er = 0.0, xhl = 0.0, xhr = 0.0;
     if (lin) {
       const int cl = line_cell(d, r, r.k - 1);
       sgl = d.sigT[cl * G + g];
       el = d.e_eff[cl * G + g];
+      xhl = d.xnum[cl * G + g];
     } else if (d.bc[sideL] == BC_BLACKBODY) {
       sgl = d.ghost_sig[sideL * G + g];
       el = d.e_eff[(d.ncell + sideL) * G + g];
+      xhl = d.xnum[(d.ncell + sideL) * G + g];
     }
     if (rin) {
       const int cr = line_cell(d, r, r.k);
       sgr = d.sigT[cr * G + g];
       er = d.e_eff[cr * G + g];
+      xhr = d.xnum[cr * G + g];
     } else if (d.bc[sideR] == BC_BLACKBODY) {
       sgr = d.ghost_sig[sideR * G + g];
       er = d.e_eff[(d.ncell + sideR) * G + g];
+      xhr = d.xnum[(d.ncell + sideR) * G + g];
     }
     if (sgl < 0.0) sgl = sgr;
     if (sgr < 0.0) sgr = sgl;
     const double sf = 2.0 * sgl * sgr / (sgl + sgr);
     const double tauf = 1.0 / (d.rate_f * sf);
     const double xf = d.dt / tauf;
-    double AL, BL, AR, BR;
-    half_coefs(xf, tauf, d.dt * d.rate_f * sgl, el, d.dt, &AL, &BL);
-    half_coefs(xf, tauf, d.dt * d.rate_f * sgr, er, d.dt, &AR, &BR);
+    double AL, BL, AR, BR, f4, f5, c4;
+    coef_f4_f5_c4(xf, &f4, &f5, &c4);
+    half_coefs(xf, tauf, xhl, el, d.dt, f4, f5, c4, &AL, &BL);
+    half_coefs(xf, tauf, xhr, er, d.dt, f4, f5, c4, &AR, &BR);
     d.Fwave[i] = AL * (v * 0.25) * fl - AR * (v * 0.25) * fr + (BL * sl + BR * sr) * (v * v / 6.0);
   }
 }
@@ -817,12 +843,26 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
   const long long n = (long long)ctrl->n_part[cur];
   const uint32_t* __restrict__ key = d.pkey[cur];
   const bool mixed = d.precision == 1;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double f = __ldg(d.wscale + key[i]);
-    if (f == 1.0) continue;
-    if (mixed) d.fw[cur][i] = (float)((double)d.fw[cur][i] * f);
-    else d.pw[cur][i] *= f;
+  // four particles per thread: one 16-byte key load, four independent gathers
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = 4 * q;
+    uint32_t k[4];
+    if (i0 + 3 < n) {
+      const uint4 kk = *reinterpret_cast<const uint4*>(key + i0);
+      k[0] = kk.x; k[1] = kk.y; k[2] = kk.z; k[3] = kk.w;
+    } else {
+      for (int r = 0; r < 4; ++r) k[r] = i0 + r < n ? key[i0 + r] : 0u;
+    }
+    double f[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) f[r] = i0 + r < n ? __ldg(d.wscale + k[r]) : 1.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (f[r] == 1.0) continue;
+      if (mixed) d.fw[cur][i0 + r] = (float)((double)d.fw[cur][i0 + r] * f[r]);
+      else d.pw[cur][i0 + r] *= f[r];
+    }
   }
 }
 

@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
     const int cell0 = cell;
     double t_tra = 0.0;
     if (valid) {
-      const double nup = d.grey ? 1.0 : pow_fast(nu, d.sig_p);
+      // 1/sigma(nu, T^n) = max(1/(sigma0 T^q nu^p), 1/cap): multiplications only
+      const double inup = d.grey ? 1.0 : pow_fast(nu, -d.sig_p);
       double t_rem;
       bool collided;
       if (newborn) {
@@ -222,14 +223,16 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         collided = false;
       } else {
         const double u = rng.next(d.key0, d.key1);
-        const double sig = cap_sigma(d, d.sT[cell] * nup);
-        const double tc = -log(u) * inv_rate / sig;
+        const double sig_inv = fmax(d.sTinv[cell] * inup, d.inv_cap);
+        const double tc = -log(u) * inv_rate * sig_inv;
         collided = tc < dt;
         t_rem = collided ? tc : dt;
       }
       bool ghost = gside >= 0;
       int cx = DIM == 2 ? cell % nx : cell;
       int cy = DIM == 2 ? cell / nx : 0;
+      const double ivx = ox != 0.0 ? 1.0 / (v * fabs(ox)) : 0.0;
+      const double ivy = (DIM == 2 && oy != 0.0) ? 1.0 / (v * fabs(oy)) : 0.0;
       for (int guard = 0;; ++guard) {
         if (guard >= 4096) {            // defensive bound (NaN state)
           atomicOr(&ctrl->status, ST_NONFINITE);
@@ -238,14 +241,14 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         }
         const double xL = cx * d.dx, xR = (cx + 1) * d.dx;
         double tx = INFINITY, ty = INFINITY;
-        if (ox > 0.0) tx = fmax(xR - x, 0.0) / (v * ox);
-        else if (ox < 0.0) tx = fmax(x - xL, 0.0) / (v * -ox);
+        if (ox > 0.0) tx = fmax(xR - x, 0.0) * ivx;
+        else if (ox < 0.0) tx = fmax(x - xL, 0.0) * ivx;
         double yB = 0.0, yT = 0.0;
         if (DIM == 2) {
           yB = cy * d.dy;
           yT = (cy + 1) * d.dy;
-          if (oy > 0.0) ty = fmax(yT - y, 0.0) / (v * oy);
-          else if (oy < 0.0) ty = fmax(y - yB, 0.0) / (v * -oy);
+          if (oy > 0.0) ty = fmax(yT - y, 0.0) * ivy;
+          else if (oy < 0.0) ty = fmax(y - yB, 0.0) * ivy;
         }
         const int axis = (tx <= ty) ? 0 : 1;
         const double tf = axis == 0 ? tx : ty;
@@ -279,8 +282,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           cy = nyc;
           cell = cy * nx + cx;
           const double u = rng.next(d.key0, d.key1);
-          const double sig = cap_sigma(d, d.sT[cell] * nup);
-          const double tc = -log(u) * inv_rate / sig;
+          const double sig_inv = fmax(d.sTinv[cell] * inup, d.inv_cap);
+          const double tc = -log(u) * inv_rate * sig_inv;
           const double avail = dt - t_tra;
           collided = tc < avail;
           t_rem = collided ? tc : avail;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   const uint32_t step = (uint32_t)ctrl->step;
   const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
   const float dxf = d.dxf, dyf = d.dyf, vf = d.vf, dtf = d.dtf;
-  const float inv_rate = d.inv_rate_f, capf = d.capf, spf = d.spf;
+  const float inv_rate = d.inv_rate_f, spf = d.spf;
   const float* __restrict__ in_x = d.fx[cur];
   const float* __restrict__ in_y = d.fy[cur];
   const float* __restrict__ in_ox = d.fox[cur];
@@ -464,7 +467,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     int fate = FATE_REMOVED, nseg = 0, eside = -1;
     float t_tra = 0.0f;
     if (valid) {
-      const float nup = d.grey ? 1.0f : pow_fast_f(nu, spf);
+      const float inup = d.grey ? 1.0f : pow_fast_f(nu, -spf);
+      const float icap = d.inv_capf;
       float t_rem;
       bool collided;
       if (newborn) {
@@ -472,8 +476,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         collided = false;
       } else {
         const UPair u = rng.next2(d.key0, d.key1);
-        const float sig = fminf(__ldg(d.sT_f + cy * nx + cx) * nup, capf);
-        const float tc = neg_log_u(u) * inv_rate / sig;
+        const float sig_inv = fmaxf(__ldg(d.sTinv_f + cy * nx + cx) * inup, icap);
+        const float tc = neg_log_u(u) * inv_rate * sig_inv;
         collided = tc < dtf;
         t_rem = collided ? tc : dtf;
       }
@@ -526,8 +530,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           cx = nxc;
           cy = nyc;
           const UPair u = rng.next2(d.key0, d.key1);
-          const float sig = fminf(__ldg(d.sT_f + cy * nx + cx) * nup, capf);
-          const float tc = neg_log_u(u) * inv_rate / sig;
+          const float sig_inv = fmaxf(__ldg(d.sTinv_f + cy * nx + cx) * inup, icap);
+          const float tc = neg_log_u(u) * inv_rate * sig_inv;
           const float avail = dtf - t_tra;
           collided = tc < avail;
           t_rem = collided ? tc : avail;

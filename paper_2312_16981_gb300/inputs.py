@@ -48,6 +48,7 @@ class Problem:
     bcT: List[float] = field(default_factory=lambda: [0.0] * 4)
     src_T: Optional[np.ndarray] = None   # [ncell] source temperature, 0 = none
     src_on: float = 0.0
+    tau_num_C: float = 0.0   # thin/thick joint sampling constant C of tau_num (0: off)
     omega_ref: float = 1e-6
     seed: int = 0
     instance: int = 0

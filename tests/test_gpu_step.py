@@ -115,6 +115,27 @@ def test_step_parity_checkerboard_2d(B, order):
     assert t["n_born"] > 1000
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_step_parity_thin_thick_joint_with_tau_num(B, dim):
+    # numerical collision time at thin/thick joints (Sec. 3.2): heterogeneous
+    # opacity, a few steps in so the temperature contrast is real, C = 1e3
+    if dim == 1:
+        p = I.small_multigroup(nx=24, G=5, omega_ref=1e-6)
+        sig0 = np.full(p.nx, 10.0)
+        sig0[12:] = 1e4
+        p.sigma0 = sig0
+    else:
+        p = I.small_checkerboard(n=12, G=3, omega_ref=5e-7)
+    p.tau_num_C = 1e3
+    t, tal = check_step(B, p, 3)
+    # more particles than sampling with tau would give
+    _, st = oracle_run(p, 3)
+    _, n_tau, _ = O.birth_counts(O.OracleProblem(p.replace(tau_num_C=0.0)), st.T, st.rho_h)
+    assert t["n_born"] >= n_tau
+    if dim == 2:
+        assert t["n_born"] > n_tau + 100
+
+
 def test_multi_step_trajectory(B):
     p = I.small_multigroup(nx=20, G=5, omega_ref=2e-6)
     op, st = oracle_run(p, 0)
