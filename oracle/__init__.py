@@ -31,7 +31,7 @@ class CProblem(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("G", C.c_int32),
         ("grey", C.c_int32), ("wave_order", C.c_int32), ("si_max_iters", C.c_int32),
-        ("bc", C.c_int32 * 4), ("_pad0", C.c_int32),
+        ("bc", C.c_int32 * 4), ("sig_law", C.c_int32),
         ("dx", C.c_double), ("dy", C.c_double),
         ("sig_p", C.c_double), ("sig_q", C.c_double), ("sig_cap", C.c_double),
         ("a", C.c_double), ("c", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
@@ -149,6 +149,7 @@ class OracleProblem:
         s.a, s.c, s.eps, s.dt = p.a, p.c, p.eps, p.dt
         s.omega_ref, s.si_tol, s.src_on = p.omega_ref, p.si_tol, p.src_on
         s.tau_num_C = float(getattr(p, "tau_num_C", 0.0))
+        s.sig_law = int(getattr(p, "sig_law", 0))
         s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
         s.nu_edges, s.sigma0, s.cv = _d(self.nu_edges), _d(self.sigma0), _d(self.cv)
         s.src_T = _d(self.src_T) if self.src_T is not None else None

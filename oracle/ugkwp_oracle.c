@@ -73,11 +73,14 @@ double or_draw(const or_problem* P, uint64_t id, int64_t step, int64_t j) {
 /* ------------------------------------------------------------------------ */
 /* Opacity.  The paper takes sigma_g^a = sigma_g^e = sigma_g(nu) (Sec. 2.1);
  * the tests use sigma(nu, T) = sigma0 nu^p T^q (Eq. sigmaMarsharkMF has
- * p = -3, q = -1/2), capped pointwise.  Particles use sigma at their own
- * frequency and the cell temperature.                                       */
+ * p = -3, q = -1/2), capped pointwise.  sig_law 1 adds the photo-ionisation
+ * factor (1 - e^{-nu/T}) of the Larsen case (Sec. 3.3: gamma0 (1 -
+ * e^{-h nu/kT})/(h nu)^3, i.e. p = -3, q = 0).  Particles use sigma at their
+ * own frequency and the cell temperature.                                   */
 double or_sigma(const or_problem* P, int c, double nu, double T) {
   double s = P->sigma0[c] * pow(T, P->sig_q);
   if (!P->grey) s *= pow(nu, P->sig_p);
+  if (!P->grey && P->sig_law == 1) s *= -expm1(-nu / T);
   if (P->sig_cap > 0.0 && !(s <= P->sig_cap)) s = P->sig_cap;
   return s;
 }

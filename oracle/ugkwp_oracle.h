@@ -33,7 +33,7 @@ typedef struct {
   int32_t wave_order;    /* 1: cell-average upwind values, 2: van Leer linear reconstruction */
   int32_t si_max_iters;
   int32_t bc[4];
-  int32_t _pad0;
+  int32_t sig_law;       /* 0: sigma0 nu^p T^q; 1: sigma0 nu^p T^q (1 - e^{-nu/T}) (Larsen case) */
   double dx, dy;
   double sig_p, sig_q, sig_cap;   /* sigma = sigma0 * nu^p * T^q, capped (cap <= 0: none) */
   double a, c, eps, dt;

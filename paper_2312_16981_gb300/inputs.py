@@ -49,6 +49,7 @@ class Problem:
     src_T: Optional[np.ndarray] = None   # [ncell] source temperature, 0 = none
     src_on: float = 0.0
     tau_num_C: float = 0.0   # thin/thick joint sampling constant C of tau_num (0: off)
+    sig_law: int = 0         # 0: sigma0 nu^p T^q; 1: times (1 - e^{-nu/T}) (Larsen case)
     omega_ref: float = 1e-6
     seed: int = 0
     instance: int = 0
@@ -158,6 +159,29 @@ def adjoint_grid(n: int = 128, G: int = 16, patch: int = 16, steps: int = 200,
         T0=np.full(n * n, 1e-3), dt=dx, src_T=src.reshape(-1), src_on=1.0,
         bc=[BC_REFLECT] * 4, bcT=[0.0] * 4, omega_ref=omega_ref, seed=seed,
         n_steps=steps, name="adjoint_grid_%dx%dx%d" % (n, n, G), particle_capacity=1 << 23)
+
+
+def larsen_slab(G: int = 24, omega_frac: float = 1e-4, steps: int = 1349) -> Problem:
+    """The Larsen test problem (Sec. 3.3) in the paper's units (cm, ns, keV,
+    GJ; c = 29.98 cm/ns, a = 0.01372 GJ/(cm^3 keV^4)): [0, 4] cm, 200 cells,
+    sigma = gamma0 (1 - e^{-nu/T})/nu^3 with gamma0 = 1, 1000, 1 keV^3/cm on
+    [0, 2], (2, 3], (3, 4] cm, C_v = 0.05109 GJ/(cm^3 keV), T0 = 1e-3 keV,
+    a T_r = 1 keV black body at x = 0, a free (vacuum) side at x = 4, G log
+    groups on [1e-2, 1e2] keV, dt = dx/c (CFL 1), tau_num with C = 1e3 at the
+    thin/thick joints, reference weight omega_frac x V in rho V units
+    (rho = c x energy density); t = 0.9 ns after `steps` steps."""
+    nx, L = 200, 4.0
+    dx = L / nx
+    xc = (np.arange(nx) + 0.5) * dx
+    gamma0 = np.where((xc > 2.0) & (xc <= 3.0), 1000.0, 1.0)
+    c, a = 29.98, 0.01372
+    return Problem(
+        dim=1, nx=nx, ny=1, dx=dx, dy=1.0, G=G, grey=0, nu_edges=log_groups(G, 1e-2, 1e2),
+        sigma0=gamma0, cv=np.full(nx, 0.05109), T0=np.full(nx, 1e-3), dt=dx / c,
+        sig_p=-3.0, sig_q=0.0, sig_cap=1e6, sig_law=1, a=a, c=c, eps=1.0,
+        bc=[BC_BLACKBODY, BC_VACUUM, BC_REFLECT, BC_REFLECT], bcT=[1.0, 0.0, 0.0, 0.0],
+        omega_ref=omega_frac * dx * c, tau_num_C=1e3, n_steps=steps, name="larsen_%dx%d" % (nx, G),
+        particle_capacity=1 << 22)
 
 
 def ensemble_slabs(n_instances: int = 256, seed: int = 0, steps: int = 100) -> List[Problem]:
