@@ -58,7 +58,9 @@ enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
 /* Problem statement (Sec. 3 numerical set-up; all pointers are HOST pointers,
  * read during ugkwp_init only; the caller keeps ownership).
  *   sigma(nu, T) = sigma0[c] * nu^sig_p * T^sig_q, capped at sig_cap (> 0)
- *   (Eq. sigmaMarsharkMF: sig_p = -3, sig_q = -1/2); group opacity by Simpson's
+ *   (Eq. sigmaMarsharkMF: sig_p = -3, sig_q = -1/2); with sig_law = 1 times the
+ *   photo-ionisation factor (1 - e^{-nu/T}) of the Larsen case (Sec. 3.3:
+ *   sig_p = -3, sig_q = 0); group opacity by Simpson's
  *   rule on the edges and midpoint of each group.  grey = 1: one group, no
  *   frequency dependence, Phi = a c T^4.
  *   Boundary sides: REFLECT (mirror), VACUUM (no inflow), BLACKBODY at bcT
@@ -77,7 +79,7 @@ typedef struct ugkwp_problem {
   int32_t si_max_iters;   /* source-iteration cap */
   int32_t precision;      /* UGKWP_FP64 or UGKWP_MIXED (particle state in FP32) */
   int32_t bc[4];
-  int32_t _pad0;
+  int32_t sig_law;        /* 0: sigma0 nu^p T^q; 1: sigma0 nu^p T^q (1 - e^{-nu/T}) (Larsen case) */
   double dx, dy;
   double sig_p, sig_q, sig_cap;
   double a, c, eps, dt;

@@ -36,7 +36,7 @@ class CProblem(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("G", C.c_int32),
         ("grey", C.c_int32), ("wave_order", C.c_int32), ("si_max_iters", C.c_int32),
-        ("precision", C.c_int32), ("bc", C.c_int32 * 4), ("_pad0", C.c_int32),
+        ("precision", C.c_int32), ("bc", C.c_int32 * 4), ("sig_law", C.c_int32),
         ("dx", C.c_double), ("dy", C.c_double),
         ("sig_p", C.c_double), ("sig_q", C.c_double), ("sig_cap", C.c_double),
         ("a", C.c_double), ("c", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
@@ -187,6 +187,7 @@ class _HostProblem:
         s.a, s.c, s.eps, s.dt = p.a, p.c, p.eps, p.dt
         s.omega_ref, s.si_tol, s.src_on = p.omega_ref, p.si_tol, p.src_on
         s.tau_num_C = float(p.tau_num_C)
+        s.sig_law = int(p.sig_law)
         s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
         s.particle_capacity = int(p.particle_capacity)
         s.nu_edges = arr(p.nu_edges, p.G + 1)

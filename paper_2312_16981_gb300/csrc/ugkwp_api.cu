@@ -81,6 +81,7 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_ARG, "precision must be UGKWP_FP64 or UGKWP_MIXED");
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
   if (!(p->tau_num_C >= 0.0)) return fail(h, UGKWP_ERR_ARG, "tau_num_C must be >= 0");
+  if (p->sig_law != 0 && p->sig_law != 1) return fail(h, UGKWP_ERR_ARG, "sig_law must be 0 or 1");
   const long long nbins = (ncell_of(p) + 4) * p->G;
   if (nbins >= (1ll << 24)) return fail(h, UGKWP_ERR_ARG, "(ncell+4)*G must be < 2^24 (particle id layout)");
   return UGKWP_OK;
@@ -146,6 +147,7 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   const bool mixed = p->precision == UGKWP_MIXED;
   d.sT_f = mixed ? cv.take<float>(nc) : nullptr;
   d.sTinv_f = mixed ? cv.take<float>(nc) : nullptr;
+  d.invT_f = mixed ? cv.take<float>(nc) : nullptr;
   d.omega_f = mixed ? cv.take<float>(nb) : nullptr;
   d.khat_f = mixed ? cv.take<float>(nb) : nullptr;
   d.particles_begin = nullptr;
@@ -207,6 +209,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.si_tol = p->si_tol;
   d.src_on = p->src_on;
   d.tau_num_C = p->tau_num_C;
+  d.sig_law = p->sig_law;
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
   d.capacity = p->particle_capacity;
@@ -780,6 +783,8 @@ int adjoint_check(ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint tape is written by the FP64 particle kernel");
   if (h->d.tau_num_C != 0.0)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates tau, not tau_num (tau_num_C = 0)");
+  if (h->d.sig_law != 0)
+    return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the power-law opacity (sig_law = 0)");
   return UGKWP_OK;
 }
 }  // namespace

@@ -117,7 +117,7 @@ struct DrawsF {
 struct Dev {
   // geometry / model
   int dim, nx, ny, G, ncell, nbins, nface, nxface;
-  int grey, wave_order, si_max_iters, precision;
+  int grey, wave_order, si_max_iters, precision, sig_law;
   int bc[4];
   double dx, dy, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
   double v;          // c/eps, particle speed
@@ -187,6 +187,7 @@ struct Dev {
   float* fw[2];
   float* sT_f;      // [ncell] sigma0 T^q
   float* sTinv_f;   // [ncell] 1/(sigma0 T^q)
+  float* invT_f;    // [ncell] 1/T^n (photo-ionisation factor of sig_law 1)
   float* omega_f;   // [nbins]
   float* khat_f;    // [nbins]
   float* nu_edges_f;       // [G+1] group edges in FP32
@@ -358,6 +359,33 @@ __device__ __forceinline__ double sigma_group(const Dev& d, double sT, int g) {
   const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1));
   const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2));
   return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
+}
+
+// Group opacity at temperature T: with sig_law 1 each Simpson point carries
+// the photo-ionisation factor (1 - e^{-nu/T}) of the Larsen case (Sec. 3.3)
+// before the cap.
+__device__ __forceinline__ double sigma_group_at(const Dev& d, double sT, double T, int g) {
+  if (d.sig_law == 0 || d.grey) return sigma_group(d, sT, g);
+  const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b), iT = 1.0 / T;
+  const double sa = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g) * -expm1(-a * iT));
+  const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1) * -expm1(-m * iT));
+  const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2) * -expm1(-b * iT));
+  return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
+}
+
+// 1/sigma(nu, T^n) of a particle in `cell`: max(1/(sigma0 T^q nu^p [1 - e^{-nu/T}]), 1/cap)
+// from the per-cell 1/(sigma0 T^q) and 1/nu^p (inup); multiplications except
+// for the photo-ionisation factor.
+__device__ __forceinline__ double inv_sigma_particle(const Dev& d, int cell, double nu, double inup) {
+  double si = d.sTinv[cell] * inup;
+  if (d.sig_law == 1 && !d.grey) si /= -expm1(-nu / d.T[cell]);
+  return fmax(si, d.inv_cap);
+}
+
+__device__ __forceinline__ float inv_sigma_particle_f(const Dev& d, int cell, float nu, float inup) {
+  float si = __ldg(d.sTinv_f + cell) * inup;
+  if (d.sig_law == 1 && !d.grey) si /= -expm1f(-nu * __ldg(d.invT_f + cell));
+  return fmaxf(si, d.inv_capf);
 }
 
 // d sigma_g / d s for sigma0 -> sigma0 e^s: the Simpson sum of the point

@@ -81,7 +81,7 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
     hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
     if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] * invT);
     if (g < G) {
-      sig[j] = sigma_group(d, sT, g);
+      sig[j] = sigma_group_at(d, sT, T, g);
       if (T > 0.0) {
         const double b = planck_fraction(lo, hi);
         phi[j] = ac * T3 * T * b;

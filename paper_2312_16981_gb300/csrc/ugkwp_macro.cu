@@ -60,7 +60,7 @@ __global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
     if (d.bc[side] == BC_BLACKBODY) {
       const int cin = side == 0 ? 0 : (side == 1 ? d.nx - 1 : 0);
       phi_dphi_cell(d, d.bcT[side], g, &p, nullptr);
-      s = sigma_group(d, sigma_T(d, cin, d.bcT[side]), g);
+      s = sigma_group_at(d, sigma_T(d, cin, d.bcT[side]), d.bcT[side], g);
     }
     const_cast<double*>(d.ghost_phi)[i] = p;
     const_cast<double*>(d.ghost_sig)[i] = s;
@@ -110,9 +110,10 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
         if (d.sT_f) {
           d.sT_f[cell] = (float)sT;
           d.sTinv_f[cell] = (float)(1.0 / sT);
+          d.invT_f[cell] = (float)(1.0 / Tb);
         }
       }
-      sig = sigma_group(d, sT, g);
+      sig = sigma_group_at(d, sT, Tb, g);
       d.sigT[b] = sig;
       d.W[b] = 0.0;
       d.E_surv[b] = 0.0;

@@ -214,7 +214,6 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
     const int cell0 = cell;
     double t_tra = 0.0;
     if (valid) {
-      // 1/sigma(nu, T^n) = max(1/(sigma0 T^q nu^p), 1/cap): multiplications only
       const double inup = d.grey ? 1.0 : pow_fast(nu, -d.sig_p);
       double t_rem;
       bool collided;
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         collided = false;
       } else {
         const double u = rng.next(d.key0, d.key1);
-        const double sig_inv = fmax(d.sTinv[cell] * inup, d.inv_cap);
+        const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
         const double tc = -log(u) * inv_rate * sig_inv;
         collided = tc < dt;
         t_rem = collided ? tc : dt;
@@ -282,7 +281,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           cy = nyc;
           cell = cy * nx + cx;
           const double u = rng.next(d.key0, d.key1);
-          const double sig_inv = fmax(d.sTinv[cell] * inup, d.inv_cap);
+          const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
           const double tc = -log(u) * inv_rate * sig_inv;
           const double avail = dt - t_tra;
           collided = tc < avail;
@@ -468,7 +467,6 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     float t_tra = 0.0f;
     if (valid) {
       const float inup = d.grey ? 1.0f : pow_fast_f(nu, -spf);
-      const float icap = d.inv_capf;
       float t_rem;
       bool collided;
       if (newborn) {
@@ -476,7 +474,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         collided = false;
       } else {
         const UPair u = rng.next2(d.key0, d.key1);
-        const float sig_inv = fmaxf(__ldg(d.sTinv_f + cy * nx + cx) * inup, icap);
+        const float sig_inv = inv_sigma_particle_f(d, cy * nx + cx, nu, inup);
         const float tc = neg_log_u(u) * inv_rate * sig_inv;
         collided = tc < dtf;
         t_rem = collided ? tc : dtf;
@@ -530,7 +528,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           cx = nxc;
           cy = nyc;
           const UPair u = rng.next2(d.key0, d.key1);
-          const float sig_inv = fmaxf(__ldg(d.sTinv_f + cy * nx + cx) * inup, icap);
+          const float sig_inv = inv_sigma_particle_f(d, cy * nx + cx, nu, inup);
           const float tc = neg_log_u(u) * inv_rate * sig_inv;
           const float avail = dtf - t_tra;
           collided = tc < avail;

@@ -86,6 +86,16 @@ def test_mixed_checkerboard_2d(B):
     check(p, *run_pair(B, p, st, op))
 
 
+def test_mixed_larsen_slab(B):
+    # photo-ionisation opacity (Sec. 3.3), paper units, tau_num at the joints
+    p = I.larsen_slab(G=12, omega_frac=2e-5)
+    op = O.OracleProblem(p)
+    st = O.initial_state(op)
+    for _ in range(4):
+        st, _, _, _ = O.step(op, st)
+    check(p, *run_pair(B, p, st, op))
+
+
 def test_mixed_full_size_slab(B):
     p = I.multigroup_slab()
     s = I.synthetic_state(p, 1_000_000, seed=3)

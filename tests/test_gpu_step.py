@@ -136,6 +136,26 @@ def test_step_parity_thin_thick_joint_with_tau_num(B, dim):
         assert t["n_born"] > n_tau + 100
 
 
+def test_step_parity_larsen_slab(B):
+    # photo-ionisation opacity (Sec. 3.3) in the paper's units, free right
+    # side, tau_num at the thin/thick joints
+    p = I.larsen_slab(G=12, omega_frac=2e-5)
+    t, tal = check_step(B, p, 4)
+    assert t["n_born"] > 50
+
+
+def test_larsen_multi_step_trajectory(B):
+    p = I.larsen_slab(G=8, omega_frac=2e-5)
+    op, st = oracle_run(p, 0)
+    sim = B.Simulation(p)
+    for n in range(6):
+        sim.step(1)
+        st, tal, _, _ = O.step(op, st)
+        g = sim.get_state()
+        np.testing.assert_allclose(g["T"], st.T, rtol=T_RTOL, atol=0)
+        assert g["n"] == st.particles.n
+
+
 def test_multi_step_trajectory(B):
     p = I.small_multigroup(nx=20, G=5, omega_ref=2e-6)
     op, st = oracle_run(p, 0)
