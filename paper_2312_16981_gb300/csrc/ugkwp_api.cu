@@ -137,8 +137,8 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.wscale = cv.take<double>(ncg);
   d.Tk[0] = cv.take<double>(nc);
   d.Tk[1] = cv.take<double>(nc);
-  d.sigk[0] = cv.take<double>(ncg);
-  d.sigk[1] = cv.take<double>(ncg);
+  d.tauk[0] = cv.take<double>(ncg);
+  d.tauk[1] = cv.take<double>(ncg);
   d.phik[0] = cv.take<double>(ncg);
   d.phik[1] = cv.take<double>(ncg);
   d.dphik = cv.take<double>(ncg);
@@ -200,6 +200,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.c = p->c;
   d.eps = p->eps;
   d.dt = p->dt;
+  d.inv_2dt = 0.5 / p->dt;
   d.v = p->c / p->eps;
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;

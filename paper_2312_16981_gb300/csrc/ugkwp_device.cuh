@@ -8,6 +8,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ugkwp_planck_table.h"
+
 namespace ugkwp {
 
 constexpr int kMaxG = 64;
@@ -154,6 +156,7 @@ struct Dev {
   unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
   unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
   double inv_dx, inv_dy, inv_c;
+  double inv_2dt;             // 1/(2 dt)
   double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-48) and its inverse
   int tq_shift;
   // FP32 copies of scalars (mixed-precision particle kernel)
@@ -166,7 +169,7 @@ struct Dev {
   double* R;        // [ncell*G] constant part of the rho equation
   double* wscale;   // [ncell*G] end-of-step scaling of the survivors' weights (1: none)
   double* Tk[2];    // [ncell] iterates
-  double* sigk[2];  // [ncell*G]
+  double* tauk[2];  // [ncell*G] relaxation time 1/(rate_f sigma_g(T^k)) of the iterate
   double* phik[2];  // [ncell*G]
   double* dphik;    // [ncell*G]
   // particles: two structure-of-arrays buffers, selected by ctrl->cur
@@ -337,7 +340,7 @@ __device__ __forceinline__ double pow_fast(double b, double e) {
   if (e == 0.0) return 1.0;
   if (e == -3.0) return 1.0 / (b * b * b);
   if (e == 3.0) return b * b * b;
-  if (e == -0.5) return 1.0 / sqrt(b);
+  if (e == -0.5) return rsqrt(b);
   if (e == 1.0) return b;
   return pow(b, e);
 }
@@ -364,13 +367,17 @@ __device__ __forceinline__ double sigma_group(const Dev& d, double sT, int g) {
 // Group opacity at temperature T: with sig_law 1 each Simpson point carries
 // the photo-ionisation factor (1 - e^{-nu/T}) of the Larsen case (Sec. 3.3)
 // before the cap.
-__device__ __forceinline__ double sigma_group_at(const Dev& d, double sT, double T, int g) {
+__device__ __forceinline__ double sigma_group_at(const Dev& d, double sT, double T, double invT, int g) {
   if (d.sig_law == 0 || d.grey) return sigma_group(d, sT, g);
-  const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b), iT = 1.0 / T;
-  const double sa = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g) * -expm1(-a * iT));
-  const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1) * -expm1(-m * iT));
-  const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2) * -expm1(-b * iT));
+  const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b);
+  const double sa = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g) * -expm1(-a * invT));
+  const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1) * -expm1(-m * invT));
+  const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2) * -expm1(-b * invT));
   return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
+}
+
+__device__ __forceinline__ double sigma_group_at(const Dev& d, double sT, double T, int g) {
+  return sigma_group_at(d, sT, T, 1.0 / T, g);
 }
 
 // 1/sigma(nu, T^n) of a particle in `cell`: max(1/(sigma0 T^q nu^p [1 - e^{-nu/T}]), 1/cap)
@@ -401,50 +408,20 @@ __device__ __forceinline__ double sigma_group_ds(const Dev& d, double sT, int g)
 }
 
 // --------------------------------------------------------------------------
-// Planck integrals by series (in place of quadrature):
-//   lower part L(x) = int_0^x t^3/(e^t-1) dt = x^3/3 - x^4/8 + sum_m B_2m x^{2m+3}/((2m+3)(2m)!),
-//     used for x <= 2 (radius of convergence 2 pi; 16 terms reach 1e-17);
-//   upper part U(x) = int_x^inf = sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4),
-//     used for x > 2 (ceil(39/x) terms).
-__host__ __device__ constexpr double fact_d(int n) { return n <= 1 ? 1.0 : n * fact_d(n - 1); }
-__host__ __device__ constexpr double bern_coef(long long num, long long den, int m) {
-  return ((double)num / (double)den) / ((2.0 * m + 3.0) * fact_d(2 * m));
-}
-// B_2 .. B_32 as exact rationals
-__device__ constexpr double kBern[16] = {
-    bern_coef(1, 6, 1),         bern_coef(-1, 30, 2),          bern_coef(1, 42, 3),
-    bern_coef(-1, 30, 4),       bern_coef(5, 66, 5),           bern_coef(-691, 2730, 6),
-    bern_coef(7, 6, 7),         bern_coef(-3617, 510, 8),      bern_coef(43867, 798, 9),
-    bern_coef(-174611, 330, 10), bern_coef(854513, 138, 11),   bern_coef(-236364091, 2730, 12),
-    bern_coef(8553103, 6, 13),  bern_coef(-23749461029LL, 870, 14),
-    bern_coef(8615841276005LL, 14322, 15), bern_coef(-7709321041217LL, 510, 16)};
+// Planck integrals per group edge x = nu/T.  The lower part
+//   L(x) = int_0^x t^3/(e^t-1) dt = x^3/3 - x^4/8 + sum_m B_2m x^{2m+3}/((2m+3)(2m)!)
+// and the upper part
+//   U(x) = int_x^inf t^3/(e^t-1) dt = sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4),
+// with g4(x) = x^4/(e^x - 1), are read from piecewise degree-10 interpolants
+// of these series (ugkwp_planck_table.h, written in 60-digit arithmetic by
+// gen_planck_table.py; relative error 2e-16): one Horner pass over one row
+// for every lane, whatever its x, so a warp whose groups straddle x = 2 no
+// longer runs both series (the upper one needs up to 20 terms near x = 2).
+//   x < 2:       L = x^3 p1(s),  g4 = x^3 p2(s)
+//   2 <= x < 40: U = p1(s),      g4 = p2(s)
+//   x >= 40:     U = e^{-x} (x^3 + 3x^2 + 6x + 6),  g4 = e^{-x} x^4
 
-__device__ __forceinline__ double planck_lower(double x) {
-  const double y = x * x;
-  double s = kBern[15];
-#pragma unroll
-  for (int m = 14; m >= 0; --m) s = fma(s, y, kBern[m]);
-  // x^3 (1/3 - x/8 + y s)
-  return x * x * x * fma(y, s, fma(-0.125, x, 1.0 / 3.0));
-}
-
-__device__ __forceinline__ double planck_upper(double x, double e1) {
-  // e1 = exp(-x); terms n = 1..nt with e^{-nx}
-  const int nt = x >= 39.0 ? 1 : (int)(39.0 / x) + 1;
-  const double x2 = x * x, x3 = x2 * x;
-  double en = e1, s = 0.0;
-#pragma unroll
-  for (int n = 1; n <= 20; ++n) {
-    if (n > nt) break;
-    const double r = 1.0 / (double)n;   // folded at compile time (unrolled)
-    const double poly = r * fma(r, fma(r, fma(6.0, r, 6.0 * x), 3.0 * x2), x3);
-    s = fma(en, poly, s);
-    en *= e1;
-  }
-  return s;
-}
-
-// Per edge: value V (L(x) if x <= 2 else U(x)), flag lower, and x^4/(e^x - 1).
+// Per edge: value V (L(x) if x < 2 else U(x)), flag lower, and x^4/(e^x - 1).
 struct EdgeVal {
   double V, g4;
   bool lower;
@@ -453,19 +430,25 @@ struct EdgeVal {
 __device__ __forceinline__ EdgeVal planck_edge(double x) {
   EdgeVal r;
   if (!(x > 0.0)) { r.V = 0.0; r.g4 = 0.0; r.lower = true; return r; }
-  if (x <= 2.0) {
-    r.lower = true;
-    r.V = planck_lower(x);
-    const double x2 = x * x;
-    r.g4 = x2 * x2 / expm1(x);
-  } else {
-    r.lower = false;
-    if (x > 740.0) { r.V = 0.0; r.g4 = 0.0; return r; }
-    const double e1 = exp(-x);
-    r.V = planck_upper(x, e1);
-    const double x2 = x * x;
-    r.g4 = x2 * x2 * e1 / (1.0 - e1);
+  if (x > 740.0) { r.V = 0.0; r.g4 = 0.0; r.lower = false; return r; }
+  const bool tail = x >= 40.0;
+  const int j = tail ? kPlanckRows : (int)(x * 2.0);
+  const double s = tail ? x : (x - (0.25 + 0.5 * j)) * 4.0;
+  const double2* row = reinterpret_cast<const double2*>(kPlanckTab) + j * (kPlanckDeg + 1);
+  double2 a = __ldg(row + kPlanckDeg);
+  double p1 = a.x, p2 = a.y;
+#pragma unroll
+  for (int k = kPlanckDeg - 1; k >= 0; --k) {
+    a = __ldg(row + k);
+    p1 = fma(p1, s, a.x);
+    p2 = fma(p2, s, a.y);
   }
+  r.lower = j < kPlanckLowerRows;
+  double m = 1.0;
+  if (r.lower) m = x * x * x;
+  else if (tail) m = exp(-x);
+  r.V = m * p1;
+  r.g4 = m * p2;
   return r;
 }
 
@@ -491,6 +474,7 @@ __device__ __forceinline__ double planck_dfraction(double b, const EdgeVal& lo, 
 //   f4 = C4 - e          = sum_{k>=1} (-1)^{k+1} k x^k/(k+1)!
 //   f5 = (C5 + dt e/2)/tau = sum_{k>=2} (-1)^k k(1-k) x^k/(2 (k+1)!)
 //   c4 = C4              = sum_{k>=0} (-1)^k x^k/(k+1)!
+__host__ __device__ constexpr double fact_d(int n) { return n <= 1 ? 1.0 : n * fact_d(n - 1); }
 constexpr int kSer = 22;
 __host__ __device__ constexpr double sgn(int k) { return (k & 1) ? -1.0 : 1.0; }
 __host__ __device__ constexpr double a2(int k) { return sgn(k) * (1.0 - k) / fact_d(k + 1); }
@@ -528,6 +512,23 @@ __device__ __forceinline__ double coef_g2(double x) {
   }
   const double e = exp(-x), E1 = -expm1(-x);
   return (2.0 * E1 / x - 1.0 - e) / x;
+}
+
+// f2(x)/x for the source-iteration faces, given x and 1/x (the caller has
+// both from the face's tau sum, x = 2 dt/(tau_l + tau_u)): the series to
+// x^15 below x = 1/2 (truncation below 1e-18 relative), else the closed form
+// (2(1 - e)/x - 1 - e)/x with one exp and no division (cancellation costs at
+// most ~50 ulp, at x = 1/2).
+constexpr int kSerG2 = 16;
+__device__ __forceinline__ double coef_g2_fast(double x, double ix) {
+  if (x < 0.5) {
+    double s = kA2[kSerG2];
+#pragma unroll
+    for (int k = kSerG2 - 1; k >= 2; --k) s = fma(s, x, kA2[k]);
+    return s * x;
+  }
+  const double e = exp(-x);
+  return fma(2.0 * (1.0 - e), ix, -(1.0 + e)) * ix;
 }
 
 __device__ __forceinline__ double coef_f4(double x) {

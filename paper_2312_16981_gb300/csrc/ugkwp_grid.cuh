@@ -59,10 +59,10 @@ __device__ __forceinline__ double warp_max(double v) {
 // between neighbouring lanes by shuffles.
 template <int NC>
 __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
-                                            double* dphi) {
+                                            double* dphi, double invT) {
   const int lane = threadIdx.x & 31, G = d.G;
   const double sT = sigma_T(d, c, T);
-  const double ac = d.a * d.c, T3 = T * T * T, invT = 1.0 / T;
+  const double ac = d.a * d.c, T3 = T * T * T;
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
     const int g = lane + 32 * j;
@@ -81,7 +81,7 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
     hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
     if (lane == 31 && g + 1 <= G && T > 0.0) hi = planck_edge(d.nu_edges[g + 1] * invT);
     if (g < G) {
-      sig[j] = sigma_group_at(d, sT, T, g);
+      sig[j] = sigma_group_at(d, sT, T, invT, g);
       if (T > 0.0) {
         const double b = planck_fraction(lo, hi);
         phi[j] = ac * T3 * T * b;
@@ -94,6 +94,12 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
       sig[j] = 1.0; phi[j] = 0.0; dphi[j] = 0.0;
     }
   }
+}
+
+template <int NC>
+__device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
+                                            double* dphi) {
+  cell_planck<NC>(d, c, T, sig, phi, dphi, 1.0 / T);
 }
 
 __device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {

@@ -435,20 +435,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
 }
 
 // Equilibrium flux on a face between lower-index side (l) and upper side (u):
-// F = C2 (c/eps)^2/3 (Phi_u - Phi_l)/h, C2 = tau f2(dt/tau), tau from the
-// harmonic-mean opacity (App. B).  Both adjacent cells evaluate the same
-// expression with the same operand order, so the two copies agree bitwise.
-__device__ __forceinline__ double feq_face(const Dev& d, double sl, double su, double pl, double pu,
+// F = C2 (c/eps)^2/3 (Phi_u - Phi_l)/h, C2 = tau_f f2(dt/tau_f), with the
+// harmonic-mean opacity of App. B, i.e. tau_f = (tau_l + tau_u)/2: x =
+// dt/tau_f = 2 dt/(tau_l + tau_u) takes one division and 1/x a
+// multiplication; tau_f f2(x) = dt f2(x)/x.  Both adjacent cells evaluate the
+// same expression (the tau sum commutes), so the two copies agree bitwise.
+__device__ __forceinline__ double feq_face(const Dev& d, double tl, double tu, double pl, double pu,
                                            double inv_h) {
-  // x = dt/tau with 1/tau = rate sigma_f, sigma_f = 2 sl su/(sl + su); tau f2(x) = dt f2(x)/x
-  const double x = 2.0 * d.dt * d.rate_f * (sl * su) / (sl + su);
-  return d.dt * coef_g2(x) * (d.v * d.v / 3.0) * (pu - pl) * inv_h;
+  const double st = tl + tu;
+  const double x = 2.0 * d.dt / st;
+  return d.dt * coef_g2_fast(x, st * d.inv_2dt) * (d.v * d.v / 3.0) * (pu - pl) * inv_h;
 }
 
-// Neighbour values across one face of cell c: opacity and Phi at iterate k,
-// or the ghost's.  Returns false for a reflecting wall (no flux).
+// Neighbour values across one face of cell c: relaxation time and Phi at
+// iterate k, or the ghost's.  Returns false for a reflecting wall (no flux).
 __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir, int g, int cur,
-                                          double sig_c, double* sn, double* pn, int* nc) {
+                                          double tau_c, double* tn, double* pn, int* nc) {
   const int ix = c % d.nx, iy = c / d.nx;
   const int jx = ix + (axis == 0 ? dir : 0), jy = iy + (axis == 1 ? dir : 0);
   const int nyy = d.dim == 2 ? d.ny : 1;
@@ -457,17 +459,17 @@ __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir
     *nc = -1 - side;
     if (d.bc[side] == BC_REFLECT) return false;
     if (d.bc[side] == BC_BLACKBODY) {
-      *sn = d.ghost_sig[side * d.G + g];
+      *tn = 1.0 / (d.rate_f * d.ghost_sig[side * d.G + g]);
       *pn = d.ghost_phi[side * d.G + g];
     } else {
-      *sn = sig_c;
+      *tn = tau_c;
       *pn = 0.0;
     }
     return true;
   }
   const int n = jy * d.nx + jx;
   *nc = n;
-  *sn = __ldcg(d.sigk[cur] + n * d.G + g);
+  *tn = __ldcg(d.tauk[cur] + n * d.G + g);
   *pn = __ldcg(d.phik[cur] + n * d.G + g);
   return true;
 }
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
         if (g < G) {
-          __stcg(d.sigk[0] + c * G + g, sg[j]);
+          __stcg(d.tauk[0] + c * G + g, 1.0 / (d.rate_f * sg[j]));
           __stcg(d.phik[0] + c * G + g, ph[j]);
           __stcg(d.dphik + c * G + g, dp[j]);
         }
@@ -585,15 +587,16 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int G = d.G;
       const double dt = d.dt;
       const double Tc = __ldcg(d.Tk[cur] + c), Tn = d.T[c], cv = d.cv[c];
-      double Q[NC], a[NC], r1[NC], phc[NC], dpc[NC];
+      // with q = 1/(tau + dt): 1/(1 + a_g) = tau q and a_g/(1 + a_g) = dt q
+      double Q[NC], ar[NC], r1[NC], phc[NC], dpc[NC];
       double num = 0.0, den = 0.0;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
-        Q[j] = 0.0; a[j] = 0.0; r1[j] = 1.0; phc[j] = 0.0; dpc[j] = 0.0;
+        Q[j] = 0.0; ar[j] = 0.0; r1[j] = 1.0; phc[j] = 0.0; dpc[j] = 0.0;
         if (g >= G) continue;
         const int i = c * G + g;
-        const double sc = __ldcg(d.sigk[cur] + i);
+        const double tc = __ldcg(d.tauk[cur] + i);
         phc[j] = __ldcg(d.phik[cur] + i);
         dpc[j] = __ldcg(d.dphik + i);
         double q = d.R[i];
@@ -602,11 +605,11 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
-            double sn, pn;
+            double tn, pn;
             int nc;
             double F = 0.0;
-            if (neighbour(d, c, axis, dir, g, cur, sc, &sn, &pn, &nc)) {
-              F = dir < 0 ? feq_face(d, sn, sc, pn, phc[j], inv_h) : feq_face(d, sc, sn, phc[j], pn, inv_h);
+            if (neighbour(d, c, axis, dir, g, cur, tc, &tn, &pn, &nc)) {
+              F = dir < 0 ? feq_face(d, tn, tc, pn, phc[j], inv_h) : feq_face(d, tc, tn, phc[j], pn, inv_h);
             }
             const bool owner = dir > 0 ? true : (nc < 0);   // upper face, or a boundary face
             if (owner) d.Feq[face_index(d, c, axis, dir) * G + g] = F;
@@ -615,9 +618,10 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           q += (dt / h) * (Fin - Fout);
         }
         Q[j] = q;
-        a[j] = dt * d.rate_f * sc;
-        r1[j] = 1.0 / (1.0 + a[j]);
-        const double ap = a[j] * d.inv_c * r1[j];
+        const double qi = 1.0 / (tc + dt);
+        r1[j] = tc * qi;
+        ar[j] = dt * qi;
+        const double ap = ar[j] * d.inv_c;
         num += ap * (q - phc[j] + dpc[j] * Tc);
         den += ap * dpc[j];
       }
@@ -631,7 +635,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const int g = lane + 32 * j;
         if (g >= G) continue;
         const int i = c * G + g;
-        const double r = (Q[j] + a[j] * (phc[j] + dpc[j] * (Tnew - Tc))) * r1[j];
+        const double r = fma(Q[j], r1[j], ar[j] * fma(dpc[j], Tnew - Tc, phc[j]));
         dmax = fmax(dmax, fabs(r - __ldcg(d.rho + i)));
         rsum += fabs(r);
         __stcg(d.rho + i, r);
@@ -639,7 +643,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       dmax = warp_max(dmax);
       rsum = warp_sum(rsum);
       const double eR = rsum > 0.0 ? dmax / rsum : 0.0;
-      const double eT = fabs(Tnew - Tc) / Tnew;
+      const double invTn = 1.0 / Tnew;
+      const double eT = fabs(Tnew - Tc) * invTn;
       if (ENS) {
         // members differ between warps: each warp reports to its own member
         if (lane == 0) {
@@ -652,12 +657,12 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       if (lane == 0) __stcg(d.Tk[nxt] + c, Tnew);
       double sg[NC], ph[NC], dp[NC];
-      cell_planck<NC>(d, c, Tnew, sg, ph, dp);
+      cell_planck<NC>(d, c, Tnew, sg, ph, dp, invTn);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
         if (g < G) {
-          __stcg(d.sigk[nxt] + c * G + g, sg[j]);
+          __stcg(d.tauk[nxt] + c * G + g, 1.0 / (d.rate_f * sg[j]));
           __stcg(d.phik[nxt] + c * G + g, ph[j]);
           __stcg(d.dphik + c * G + g, dp[j]);
         }

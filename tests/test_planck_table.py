@@ -1,0 +1,115 @@
+"""The CUDA path's Planck edge table (ugkwp_planck_table.h), checked on the
+CPU: the committed header is exactly what its generator writes, and the
+device's evaluation of it (one Horner pass per edge, emulated here in float64
+with the same operation order) gives the group fractions b_g(T) and their
+T-derivative of Sec. 2.1 to the accuracy of the oracle's quadrature."""
+import math
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_16981_gb300 import inputs as I
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2312_16981_gb300", "csrc")
+HEADER = os.path.join(CSRC, "ugkwp_planck_table.h")
+
+
+def table():
+    txt = open(HEADER).read()
+    body = txt[txt.index("kPlanckTab["):]
+    vals = [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-f.]+p[-+]?\d+", body)]
+    deg = int(re.search(r"kPlanckDeg = (\d+)", txt).group(1))
+    rows = int(re.search(r"kPlanckRows = (\d+)", txt).group(1))
+    lower = int(re.search(r"kPlanckLowerRows = (\d+)", txt).group(1))
+    return np.array(vals).reshape(rows + 1, deg + 1, 2), rows, lower
+
+
+TAB, ROWS, LOWER = table()
+PI4_15 = math.pi ** 4 / 15
+
+
+def edge(x):
+    """(V, g4, lower) as the device computes them."""
+    if not x > 0:
+        return 0.0, 0.0, True
+    if x > 740.0:
+        return 0.0, 0.0, False
+    tail = x >= 40.0
+    j = ROWS if tail else int(x * 2.0)
+    s = x if tail else (x - (0.25 + 0.5 * j)) * 4.0
+    p1, p2 = TAB[j, -1]
+    for k in range(TAB.shape[1] - 2, -1, -1):
+        p1 = p1 * s + TAB[j, k, 0]
+        p2 = p2 * s + TAB[j, k, 1]
+    lower = j < LOWER
+    m = x * x * x if lower else (math.exp(-x) if tail else 1.0)
+    return m * p1, m * p2, lower
+
+
+def fraction(x1, x2):
+    lo, hi = edge(x1), edge(x2)
+    if hi[2]:
+        I_ = hi[0] - lo[0]
+    elif not lo[2]:
+        I_ = lo[0] - hi[0]
+    else:
+        I_ = (PI4_15 - lo[0]) - hi[0]
+    b = I_ / PI4_15
+    return b, 4.0 * b + (lo[1] - hi[1]) / PI4_15
+
+
+def test_header_is_generator_output(tmp_path):
+    out = tmp_path / "t.h"
+    subprocess.run([sys.executable, os.path.join(CSRC, "gen_planck_table.py"), str(out)], check=True,
+                   capture_output=True)
+    assert out.read_text() == open(HEADER).read()
+
+
+def test_tail_row_is_the_exact_polynomials():
+    np.testing.assert_array_equal(TAB[ROWS, :5, 0], [6.0, 6.0, 3.0, 1.0, 0.0])
+    np.testing.assert_array_equal(TAB[ROWS, :5, 1], [0.0, 0.0, 0.0, 0.0, 1.0])
+    assert not TAB[ROWS, 5:].any()
+
+
+def test_rows_are_continuous_at_their_joints():
+    # adjacent interpolants meet at the shared end point (s = +1 / s = -1)
+    for j in range(ROWS - 1):
+        a1 = np.polynomial.polynomial.polyval(1.0, TAB[j, :, 0])
+        b1 = np.polynomial.polynomial.polyval(-1.0, TAB[j + 1, :, 0])
+        if j + 1 == LOWER:      # L/x^3 against U: L(2) = pi^4/15 - U(2)
+            assert abs(8.0 * a1 - (PI4_15 - b1)) < 1e-15 * PI4_15
+        else:
+            assert abs(a1 - b1) <= 1e-15 * abs(b1)
+
+
+def test_group_fractions_match_quadrature():
+    edges = I.log_groups(30, 1e-3, 10.0)
+    worst_b = worst_d = 0.0
+    for T in np.geomspace(1e-4, 20.0, 41):
+        for g in range(30):
+            x1, x2 = edges[g] / T, edges[g + 1] / T
+            b, d = fraction(x1, x2)
+            wb, wd = O.planck_integral(x1, x2), O.planck_dintegral(x1, x2)
+            if wb > 1e-300:
+                worst_b = max(worst_b, abs(b - wb) / wb)
+            if wd > 1e-300:
+                worst_d = max(worst_d, abs(d - wd) / wd)
+    assert worst_b < 2e-13, worst_b
+    assert worst_d < 2e-12, worst_d
+
+
+@pytest.mark.parametrize("x", [1e-6, 0.3, 1.999999, 2.0, 2.000001, 7.77, 39.99, 40.0, 123.0, 700.0])
+def test_single_edges_against_quadrature(x):
+    # lower part against [0, x], upper part against [x, 800]
+    V, g4, lower = edge(x)
+    if lower:
+        want = O.planck_integral(1e-300, x) * PI4_15
+    else:
+        want = O.planck_integral(x, 800.0) * PI4_15
+    assert abs(V - want) <= 1e-14 * want
+    assert abs(g4 - x ** 4 / math.expm1(x)) <= 1e-15 * g4
