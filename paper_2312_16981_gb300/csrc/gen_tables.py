@@ -1,6 +1,8 @@
 #!/usr/bin/env python
-"""Write ugkwp_planck_table.h: piecewise polynomial interpolants of the
-Planck edge functions used by the CUDA path's group fractions b_g(T).
+"""Write the CUDA path's coefficient tables: ugkwp_planck_table.h
+(piecewise polynomial interpolants of the Planck edge functions used by the
+group fractions b_g(T)) and ugkwp_c2_table.h (the same for the equilibrium
+flux coefficient C2 of the source-iteration faces).
 
 The group fraction (15/pi^4) int_{x_lo}^{x_hi} t^3/(e^t - 1) dt and its
 T-derivative need, per group edge x = nu/T, the lower or upper partial
@@ -28,8 +30,14 @@ constant term first.  The script also checks, in double-precision Horner
 evaluation as the device does it, the worst relative error over 21 points
 per interval and refuses to write a table worse than 1e-15.
 
-Usage: python gen_planck_table.py [output]   (default: ugkwp_planck_table.h
-beside this file).  The committed header is this script's output.
+The C2 table holds g2(x) = C2/(tau x) = f2(x)/x at x = dt/tau, with
+f2(x) = 2 (1 - e^{-x})/x - 1 - e^{-x} (Eq. C2Formula divided by tau), on the
+same intervals: rows 0..3 hold f2(x)/x^2 (-> -1/6 at x = 0; the device
+multiplies by x), rows 4..79 g2 itself, and row 80 (x >= 40) g2 = (2/x - 1)/x
+in powers of s = 1/x (the e^{-x} terms are below e^{-40} of it).
+
+Usage: python gen_tables.py [directory]   (default: this file's directory).
+The committed headers are this script's output.
 """
 from __future__ import annotations
 
@@ -140,6 +148,36 @@ def horner(coef, s):
     return p
 
 
+def f2_over_x2(x: Decimal) -> Decimal:
+    if x == 0:
+        return Decimal(-1) / 6
+    e = (-x).exp()
+    return (2 * (1 - e) / x - 1 - e) / (x * x)
+
+
+def g2(x: Decimal) -> Decimal:
+    e = (-x).exp()
+    return (2 * (1 - e) / x - 1 - e) / x
+
+
+def build_c2():
+    rows = []
+    worst = 0.0
+    for j in range(N_ROWS):
+        lo, hi = j * WIDTH, (j + 1) * WIDTH
+        f = f2_over_x2 if j < N_LOWER else g2
+        a = fit(f, lo, hi)
+        centre = float(lo + WIDTH / 2)
+        for k in range(21):
+            x = float(lo) + float(WIDTH) * k / 20
+            got = horner(a, (x - centre) * 4.0)
+            want = f(Decimal(x))
+            worst = max(worst, float(abs(Decimal(got) - want) / abs(want)))
+        rows.append(a)
+    rows.append([0.0, -1.0, 2.0] + [0.0] * (DEG - 2))
+    return rows, worst
+
+
 def build():
     rows = []
     worst = 0.0
@@ -167,7 +205,7 @@ def write(path):
     if not worst < 1e-15:
         raise RuntimeError("interpolation error %.3g exceeds 1e-15" % worst)
     lines = [
-        "// ugkwp_planck_table.h -- written by gen_planck_table.py (do not edit).",
+        "// ugkwp_planck_table.h -- written by gen_tables.py (do not edit).",
         "// Piecewise degree-%d interpolants of the Planck edge functions on intervals" % DEG,
         "// of width 1/2: rows 0..3 (x < 2) L(x)/x^3 and x/(e^x - 1); rows 4..79",
         "// (2 <= x < 40) U(x) and x^4/(e^x - 1); row 80 (x >= 40) x^3 + 3x^2 + 6x + 6",
@@ -197,7 +235,35 @@ def write(path):
     return worst
 
 
+def write_c2(path):
+    rows, worst = build_c2()
+    if not worst < 1e-15:
+        raise RuntimeError("interpolation error %.3g exceeds 1e-15" % worst)
+    lines = [
+        "// ugkwp_c2_table.h -- written by gen_tables.py (do not edit).",
+        "// Piecewise degree-%d interpolants of g2(x) = f2(x)/x, f2 = C2/tau at" % DEG,
+        "// x = dt/tau, on intervals of width 1/2: rows 0..3 (x < 2) f2(x)/x^2; rows",
+        "// 4..79 (2 <= x < 40) g2(x); row 80 (x >= 40) (2/x - 1)/x in powers of 1/x.",
+        "// Per row: %d coefficients of s^0 .. s^%d, s = 4 (x - centre) (row 80: s = 1/x)." % (DEG + 1, DEG),
+        "// Worst relative error of the double-precision Horner evaluation: %.2e." % worst,
+        "#pragma once",
+        "",
+        "namespace ugkwp {",
+        "",
+        "static __device__ __align__(16) const double kC2Tab[%d] = {" % (len(rows) * (DEG + 1)),
+    ]
+    for j, a in enumerate(rows):
+        vals = [v.hex() for v in a]
+        lines.append("    // row %d" % j)
+        for i in range(0, len(vals), 4):
+            lines.append("    " + ", ".join(vals[i:i + 4]) + ",")
+    lines += ["};", "", "}  // namespace ugkwp", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+    return worst
+
+
 if __name__ == "__main__":
-    out = sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                                                              "ugkwp_planck_table.h")
-    print("worst relative error %.3e -> %s" % (write(out), out))
+    out = sys.argv[1] if len(sys.argv) > 1 else os.path.dirname(os.path.abspath(__file__))
+    print("Planck table: worst relative error %.3e" % write(os.path.join(out, "ugkwp_planck_table.h")))
+    print("C2 table:     worst relative error %.3e" % write_c2(os.path.join(out, "ugkwp_c2_table.h")))

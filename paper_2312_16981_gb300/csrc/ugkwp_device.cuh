@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ugkwp_c2_table.h"
 #include "ugkwp_planck_table.h"
 
 namespace ugkwp {
@@ -414,7 +415,7 @@ __device__ __forceinline__ double sigma_group_ds(const Dev& d, double sT, int g)
 //   U(x) = int_x^inf t^3/(e^t-1) dt = sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4),
 // with g4(x) = x^4/(e^x - 1), are read from piecewise degree-10 interpolants
 // of these series (ugkwp_planck_table.h, written in 60-digit arithmetic by
-// gen_planck_table.py; relative error 2e-16): one Horner pass over one row
+// gen_tables.py; relative error 2e-16): one Horner pass over one row
 // for every lane, whatever its x, so a warp whose groups straddle x = 2 no
 // longer runs both series (the upper one needs up to 20 terms near x = 2).
 //   x < 2:       L = x^3 p1(s),  g4 = x^3 p2(s)
@@ -514,21 +515,22 @@ __device__ __forceinline__ double coef_g2(double x) {
   return (2.0 * E1 / x - 1.0 - e) / x;
 }
 
-// f2(x)/x for the source-iteration faces, given x and 1/x (the caller has
-// both from the face's tau sum, x = 2 dt/(tau_l + tau_u)): the series to
-// x^15 below x = 1/2 (truncation below 1e-18 relative), else the closed form
-// (2(1 - e)/x - 1 - e)/x with one exp and no division (cancellation costs at
-// most ~50 ulp, at x = 1/2).
-constexpr int kSerG2 = 16;
+// f2(x)/x (= C2/(tau x), C2 of Eq. C2Formula) for the source-iteration faces,
+// given x and 1/x (the caller has both from the face's tau sum, x = 2 dt/(tau_l
+// + tau_u)), from piecewise degree-10 interpolants (ugkwp_c2_table.h, written
+// by gen_tables.py in 60-digit arithmetic; relative error 2e-16): one Horner
+// pass for every lane, with no exp and no branch between the series and the
+// closed form.  Rows 0..3 hold f2(x)/x^2, rows 4..79 g2 itself, row 80
+// (x >= 40) (2/x - 1)/x as a polynomial in 1/x.
 __device__ __forceinline__ double coef_g2_fast(double x, double ix) {
-  if (x < 0.5) {
-    double s = kA2[kSerG2];
+  const bool tail = x >= 40.0;
+  const int j = tail ? kPlanckRows : (int)(x * 2.0);
+  const double s = tail ? ix : (x - (0.25 + 0.5 * j)) * 4.0;
+  const double* row = kC2Tab + j * (kPlanckDeg + 1);
+  double p = __ldg(row + kPlanckDeg);
 #pragma unroll
-    for (int k = kSerG2 - 1; k >= 2; --k) s = fma(s, x, kA2[k]);
-    return s * x;
-  }
-  const double e = exp(-x);
-  return fma(2.0 * (1.0 - e), ix, -(1.0 + e)) * ix;
+  for (int k = kPlanckDeg - 1; k >= 0; --k) p = fma(p, s, __ldg(row + k));
+  return j < kPlanckLowerRows ? p * x : p;
 }
 
 __device__ __forceinline__ double coef_f4(double x) {
@@ -609,12 +611,15 @@ __device__ __forceinline__ CoefDeriv coef_derivs(double x) {
 }
 
 // f4, f5 and c4 at one x together (the wave flux needs all three per face):
-// one Horner loop with three accumulators below x = 1, one exp/expm1 above.
-__device__ __forceinline__ void coef_f4_f5_c4(double x, double* f4, double* f5, double* c4) {
-  if (x < 1.0) {
-    double s4 = kA4[kSer], s5 = kA5[kSer], sc = kAC4[kSer];
+// one Horner loop with three accumulators (terms to x^16) below x = 1/2, one
+// exp/expm1 above (cancellation in f5 there costs at most ~30 ulp).
+// Returns e = exp(-x) where it was computed (x >= 1/2), else -1.
+constexpr int kSerW = 16;
+__device__ __forceinline__ double coef_f4_f5_c4(double x, double* f4, double* f5, double* c4) {
+  if (x < 0.5) {
+    double s4 = kA4[kSerW], s5 = kA5[kSerW], sc = kAC4[kSerW];
 #pragma unroll
-    for (int k = kSer - 1; k >= 2; --k) {
+    for (int k = kSerW - 1; k >= 2; --k) {
       s4 = fma(s4, x, kA4[k]);
       s5 = fma(s5, x, kA5[k]);
       sc = fma(sc, x, kAC4[k]);
@@ -624,12 +629,13 @@ __device__ __forceinline__ void coef_f4_f5_c4(double x, double* f4, double* f5, 
     *f4 = s4 * x;
     *f5 = s5 * x * x;
     *c4 = sc;
-    return;
+    return -1.0;
   }
   const double e = exp(-x), m1 = expm1(-x);   // m1 = e - 1
   *c4 = -m1 / x;
   *f4 = *c4 - e;
   *f5 = e * (1.0 + 0.5 * x) - *c4;
+  return e;
 }
 
 // --------------------------------------------------------------------------

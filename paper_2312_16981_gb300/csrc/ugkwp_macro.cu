@@ -321,13 +321,16 @@ __global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
 }
 
 // A = C4_f - e_h, B = C5_f + dt e_h/2 of one half (face coefficients f4, f5,
-// c4 at x_f shared by both halves; upwind e).
-__device__ __forceinline__ void half_coefs(double xf, double tauf, double xh, double e_eff,
+// c4 at x_f shared by both halves; upwind e).  e_eff > 0 is exp(-x_h) itself
+// (the birth kernel's value), so e_f - e_h = e_h expm1(x_h - x_f) takes one
+// expm1, or uses e_f = exp(-x_f) (ef, when the face coefficients computed it;
+// ef < 0 otherwise).
+__device__ __forceinline__ void half_coefs(double xf, double ef, double tauf, double xh, double e_eff,
                                            double dt, double f4, double f5, double c4,
                                            double* A, double* B) {
   if (e_eff > 0.0) {
     const double dd = xh - xf;
-    const double efh = fabs(dd) < 0.5 ? exp(-xh) * expm1(dd) : exp(-xf) - exp(-xh);
+    const double efh = fabs(dd) < 0.5 ? e_eff * expm1(dd) : (ef >= 0.0 ? ef : exp(-xf)) - e_eff;
     *A = f4 + efh;
     *B = tauf * f5 - 0.5 * dt * efh;
   } else {
@@ -363,8 +366,9 @@ __global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
     double sl, sr, fl, fr;
     if (d.wave_order >= 2) {
       const double rll = rho_h_at(d, r, r.k - 2, g), rrr = rho_h_at(d, r, r.k + 1, g);
-      sl = lin ? van_leer((rl - rll) / r.h, (rr - rl) / r.h) : 0.0;
-      sr = rin ? van_leer((rr - rl) / r.h, (rrr - rr) / r.h) : 0.0;
+      const double ih = r.axis == 0 ? d.inv_dx : d.inv_dy;
+      sl = lin ? van_leer((rl - rll) * ih, (rr - rl) * ih) : 0.0;
+      sr = rin ? van_leer((rr - rl) * ih, (rrr - rr) * ih) : 0.0;
       fl = rl + 0.5 * r.h * sl;
       fr = rr - 0.5 * r.h * sr;
     } else {
@@ -395,13 +399,13 @@ __global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
     }
     if (sgl < 0.0) sgl = sgr;
     if (sgr < 0.0) sgr = sgl;
-    const double sf = 2.0 * sgl * sgr / (sgl + sgr);
-    const double tauf = 1.0 / (d.rate_f * sf);
-    const double xf = d.dt / tauf;
+    // harmonic-mean face opacity: x_f = dt rate 2 sl sr/(sl + sr), tau_f = dt/x_f
+    const double xf = d.dt * d.rate_f * (2.0 * sgl * sgr) / (sgl + sgr);
+    const double tauf = d.dt / xf;
     double AL, BL, AR, BR, f4, f5, c4;
-    coef_f4_f5_c4(xf, &f4, &f5, &c4);
-    half_coefs(xf, tauf, xhl, el, d.dt, f4, f5, c4, &AL, &BL);
-    half_coefs(xf, tauf, xhr, er, d.dt, f4, f5, c4, &AR, &BR);
+    const double ef = coef_f4_f5_c4(xf, &f4, &f5, &c4);
+    half_coefs(xf, ef, tauf, xhl, el, d.dt, f4, f5, c4, &AL, &BL);
+    half_coefs(xf, ef, tauf, xhr, er, d.dt, f4, f5, c4, &AR, &BR);
     d.Fwave[i] = AL * (v * 0.25) * fl - AR * (v * 0.25) * fr + (BL * sl + BR * sr) * (v * v / 6.0);
   }
 }

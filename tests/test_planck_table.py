@@ -1,8 +1,10 @@
-"""The CUDA path's Planck edge table (ugkwp_planck_table.h), checked on the
-CPU: the committed header is exactly what its generator writes, and the
-device's evaluation of it (one Horner pass per edge, emulated here in float64
-with the same operation order) gives the group fractions b_g(T) and their
-T-derivative of Sec. 2.1 to the accuracy of the oracle's quadrature."""
+"""The CUDA path's coefficient tables, checked on the CPU: the committed
+headers are exactly what their generator writes, and the device's evaluation
+of them (one Horner pass, emulated here in float64 with the same operation
+order) gives the Planck group fractions b_g(T) and their T-derivative
+(Sec. 2.1) to the accuracy of the oracle's quadrature, and the equilibrium
+flux coefficient C2 (Eq. C2Formula) to that of the oracle's series and closed
+forms."""
 import math
 import os
 import re
@@ -17,6 +19,7 @@ from paper_2312_16981_gb300 import inputs as I
 
 CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2312_16981_gb300", "csrc")
 HEADER = os.path.join(CSRC, "ugkwp_planck_table.h")
+C2HEADER = os.path.join(CSRC, "ugkwp_c2_table.h")
 
 
 def table():
@@ -63,11 +66,45 @@ def fraction(x1, x2):
     return b, 4.0 * b + (lo[1] - hi[1]) / PI4_15
 
 
-def test_header_is_generator_output(tmp_path):
-    out = tmp_path / "t.h"
-    subprocess.run([sys.executable, os.path.join(CSRC, "gen_planck_table.py"), str(out)], check=True,
+def c2_table():
+    txt = open(C2HEADER).read()
+    body = txt[txt.index("kC2Tab["):]
+    vals = [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-f.]+p[-+]?\d+", body)]
+    return np.array(vals).reshape(ROWS + 1, TAB.shape[1])
+
+
+C2TAB = c2_table()
+
+
+def g2(x, ix):
+    """f2(x)/x as the device computes it."""
+    tail = x >= 40.0
+    j = ROWS if tail else int(x * 2.0)
+    s = ix if tail else (x - (0.25 + 0.5 * j)) * 4.0
+    p = C2TAB[j, -1]
+    for k in range(C2TAB.shape[1] - 2, -1, -1):
+        p = p * s + C2TAB[j, k]
+    return p * x if j < LOWER else p
+
+
+def test_headers_are_generator_output(tmp_path):
+    subprocess.run([sys.executable, os.path.join(CSRC, "gen_tables.py"), str(tmp_path)], check=True,
                    capture_output=True)
-    assert out.read_text() == open(HEADER).read()
+    assert (tmp_path / "ugkwp_planck_table.h").read_text() == open(HEADER).read()
+    assert (tmp_path / "ugkwp_c2_table.h").read_text() == open(C2HEADER).read()
+
+
+def test_c2_table_matches_oracle_coefficients():
+    # the oracle's f2 = C2/tau from its own series / closed forms
+    for x in np.concatenate([np.geomspace(1e-9, 1e4, 500), [0.5, 1.999999, 2.0, 39.999, 40.0]]):
+        want = O.coefs(x)[0] / x
+        got = g2(x, 1.0 / x)
+        assert abs(got - want) <= 3e-14 * abs(want), (x, got, want)
+
+
+def test_c2_tail_row_is_the_exact_expansion():
+    np.testing.assert_array_equal(C2TAB[ROWS, :3], [0.0, -1.0, 2.0])
+    assert not C2TAB[ROWS, 3:].any()
 
 
 def test_tail_row_is_the_exact_polynomials():
