@@ -153,7 +153,7 @@ __device__ __forceinline__ bool adj_barrier(AdjCtrl* ctrl, unsigned int limit, u
     unsigned int spins = 0;
     int to = 0;
     while (true) {
-      if (atomicAdd(&ctrl->bar_count, 0u) >= target) break;
+      if (load_acquire_u32(&ctrl->bar_count) >= target) break;
       if (++spins > lim) { to = 1; break; }
       __nanosleep(64);
     }
@@ -421,8 +421,8 @@ __global__ void __launch_bounds__(256) k_adj_si(const __grid_constant__ Dev d, c
       if (blockIdx.x == 0) { a.ctrl->err_slot[(it + 1) % 3][0] = 0ull; a.ctrl->err_slot[(it + 1) % 3][1] = 0ull; }
     }
     if (!adj_barrier(a.ctrl, spin_limit, (++bar) * gridDim.x)) return;
-    const double e = __longlong_as_double((long long)atomicAdd(&a.ctrl->err_slot[it % 3][0], 0ull));
-    const double m = __longlong_as_double((long long)atomicAdd(&a.ctrl->err_slot[it % 3][1], 0ull));
+    const double e = __longlong_as_double((long long)load_acquire_u64(&a.ctrl->err_slot[it % 3][0]));
+    const double m = __longlong_as_double((long long)load_acquire_u64(&a.ctrl->err_slot[it % 3][1]));
     if (e <= d.si_tol * m || m == 0.0) { done = 1; ++it; break; }
   }
   const int fin = it & 1;   // buffer written by the last iterate (mu[0] if none ran)

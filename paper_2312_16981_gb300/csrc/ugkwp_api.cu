@@ -213,6 +213,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.sig_law = p->sig_law;
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
+  d.pk = ugkwp::philox_keys(d.key0, d.key1);
   d.capacity = p->particle_capacity;
   // fixed-point quantum of the tallies: the power of two just below omega_ref 2^-48
   d.tq_shift = 48 - (p->omega_ref > 0.0 ? std::ilogb(p->omega_ref) : 0);
@@ -228,6 +229,10 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.spf = (float)d.sig_p;
   d.inv_cap = p->sig_cap > 0.0 ? 1.0 / p->sig_cap : 0.0;
   d.inv_capf = (float)d.inv_cap;
+  // bin and cell indices below 2^24 divide by G and nx through an FP32 reciprocal
+  d.fastdiv = (long long)d.ncell * d.G < (1ll << 24) ? 1 : 0;
+  d.invG_f = 1.0f / (float)d.G;
+  d.inv_nx_f = 1.0f / (float)d.nx;
   d.rec = nullptr;
   d.rec_cap = 0;
   d.tape = nullptr;

@@ -30,16 +30,38 @@ constexpr uint32_t kMaxPerBin = (1u << 20) - 1u;
 
 // --------------------------------------------------------------------------
 // Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
+// The key schedule (k0 + r W0, k1 + r W1 for rounds r = 0..9) is the same
+// for every draw of a problem, so the particle kernels read it from the
+// problem constants instead of adding the Weyl increments per round.
+struct PhiloxKeys {
+  uint32_t a[10], b[10];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys k;
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k.a[r] = k0;
+    k.b[r] = k1;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
+  return k;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+    c = make_uint4(hi1 ^ c.y ^ k.a[r], lo1, hi0 ^ c.w ^ k.b[r], lo0);
+  }
   return c;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+  return philox4x32_10(c, philox_keys(k0, k1));
 }
 
 // Uniform in (0,1): the 52 top bits m of (a, b), then m 2^-52 + 2^-53 (exact).
@@ -61,10 +83,10 @@ struct Draws {
     j = first;
     held = 0;
   }
-  __device__ __forceinline__ double next(uint32_t k0, uint32_t k1) {
+  __device__ __forceinline__ double next(const PhiloxKeys& pk) {
     const uint32_t b = j >> 1;
     if (held != b + 1u) {
-      blk = philox4x32_10(make_uint4(id_lo, id_hi, step, b), k0, k1);
+      blk = philox4x32_10(make_uint4(id_lo, id_hi, step, b), pk);
       held = b + 1u;
     }
     const double u = (j & 1u) ? u01(blk.z, blk.w) : u01(blk.x, blk.y);
@@ -88,8 +110,42 @@ __device__ __forceinline__ UPair u01f(uint32_t a, uint32_t b) {
   return r;
 }
 
+// -ln u from the pair (u, 1 - u) without branching: ln(1 + x) = 2 atanh(t),
+// t = x/(2 + x), on one argument chosen per lane -- x = -(1 - u) when
+// 1 - u < 1/2 (so u near 1 keeps its relative precision), else u = 2^k m
+// with m in [sqrt(1/2), sqrt(2)) and x = m - 1 (exact) -- and
+// 2 atanh(t) = 2t (1 + t^2/3 + t^4/5 + ... + t^14/15) for |t| <= 1/3
+// (truncation below 2^-24 relative); -ln u = -(k ln 2 + ln(1 + x)).
 __device__ __forceinline__ float neg_log_u(const UPair& p) {
-  return p.v < 0.5f ? -log1pf(-p.v) : -logf(p.u);
+  const bool near1 = p.v < 0.5f;
+  const unsigned b = __float_as_uint(p.u);
+  int k = (int)((b >> 23) & 0xffu) - 127;
+  unsigned mb = (b & 0x7fffffu) | 0x3f800000u;           // m in [1, 2)
+  if (mb > 0x3fb504f3u) { mb -= 0x00800000u; ++k; }      // m in [sqrt(1/2), sqrt(2))
+  const float x = near1 ? -p.v : __uint_as_float(mb) - 1.0f;
+  const float kf = near1 ? 0.0f : (float)k;
+  const float t = __fdividef(x, 2.0f + x);
+  const float t2 = t * t;
+  float s = 1.0f / 15.0f;
+  s = fmaf(s, t2, 1.0f / 13.0f);
+  s = fmaf(s, t2, 1.0f / 11.0f);
+  s = fmaf(s, t2, 1.0f / 9.0f);
+  s = fmaf(s, t2, 1.0f / 7.0f);
+  s = fmaf(s, t2, 1.0f / 5.0f);
+  s = fmaf(s, t2, 1.0f / 3.0f);
+  s = fmaf(s, t2, 1.0f);
+  // ln 2 split so that k ln 2 is exact in the first product
+  return -fmaf(kf, 0x1.62e400p-1f, fmaf(kf, 0x1.7f7d1cp-20f, 2.0f * t * s));
+}
+
+// q = n / d for n < 2^24 with n/d < 2^22 (the caller checks Dev::fastdiv): an
+// FP32 estimate from the reciprocal, within one of the quotient, corrected.
+__device__ __forceinline__ uint32_t div_small(uint32_t n, uint32_t d, float inv_d) {
+  uint32_t q = __float2uint_rz(__uint2float_rn(n) * inv_d);
+  int r = (int)(n - q * d);
+  if (r < 0) { --q; r += (int)d; }
+  if (r >= (int)d) ++q;
+  return q;
 }
 
 struct DrawsF {
@@ -102,17 +158,17 @@ struct DrawsF {
     j = first;
     held = 0;
   }
-  __device__ __forceinline__ UPair next2(uint32_t k0, uint32_t k1) {
+  __device__ __forceinline__ UPair next2(const PhiloxKeys& pk) {
     const uint32_t b = j >> 1;
     if (held != b + 1u) {
-      blk = philox4x32_10(make_uint4(id_lo, id_hi, step, b), k0, k1);
+      blk = philox4x32_10(make_uint4(id_lo, id_hi, step, b), pk);
       held = b + 1u;
     }
     const UPair u = (j & 1u) ? u01f(blk.z, blk.w) : u01f(blk.x, blk.y);
     ++j;
     return u;
   }
-  __device__ __forceinline__ float next(uint32_t k0, uint32_t k1) { return next2(k0, k1).u; }
+  __device__ __forceinline__ float next(const PhiloxKeys& pk) { return next2(pk).u; }
 };
 
 // --------------------------------------------------------------------------
@@ -128,6 +184,7 @@ struct Dev {
   double omega_ref, si_tol, src_on, tau_num_C;
   double bcT[4];
   uint32_t key0, key1;
+  PhiloxKeys pk;     // Philox round keys of (key0, key1)
   long long capacity;
   // constant inputs
   const double* nu_edges;   // [G+1]
@@ -162,6 +219,8 @@ struct Dev {
   int tq_shift;
   // FP32 copies of scalars (mixed-precision particle kernel)
   float dxf, dyf, vf, dtf, inv_rate_f, capf, spf, inv_capf;
+  int fastdiv;               // ncell*G < 2^24: divide by G and nx with div_small
+  float invG_f, inv_nx_f;    // 1/G, 1/nx in FP32
   double inv_cap;            // 1/sig_cap, or 0 without a cap
   double* esc;      // [4*G]
   double* inflow;   // [4*G]
@@ -205,6 +264,14 @@ struct Dev {
   struct TapeRec* tape;
   long long tape_cap;
 };
+
+// Bin -> cell and cell -> grid row, for indices the problem holds.
+__device__ __forceinline__ uint32_t div_bin(const Dev& d, uint32_t key) {
+  return d.fastdiv ? div_small(key, (uint32_t)d.G, d.invG_f) : key / (uint32_t)d.G;
+}
+__device__ __forceinline__ uint32_t div_nx(const Dev& d, uint32_t cell) {
+  return d.fastdiv ? div_small(cell, (uint32_t)d.nx, d.inv_nx_f) : cell / (uint32_t)d.nx;
+}
 
 // Ensemble view (independent problems advanced together): per-member
 // descriptors and prefix tables over the members' index spaces.  Member m
@@ -684,6 +751,23 @@ __device__ __forceinline__ float pow_fast_f(float b, float e) {
   if (e == -0.5f) return rsqrtf(b);
   if (e == 1.0f) return b;
   return __powf(b, e);
+}
+
+// --------------------------------------------------------------------------
+// Acquire loads of words other blocks update with atomics: plain L2 reads for
+// spin-waits and for reading reduction slots after a grid barrier (polling
+// with an atomic would queue behind the arrivals' read-modify-writes on the
+// same address, and every thread of every block reads the slots).
+__device__ __forceinline__ unsigned int load_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long load_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // --------------------------------------------------------------------------

@@ -412,7 +412,8 @@ __global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
 
 // --------------------------------------------------------------------------
 // Grid-wide barrier for the cooperative source-iteration kernel: a
-// monotonically increasing arrival counter, bounded spin.  On timeout the
+// monotonically increasing arrival counter polled with acquire loads, bounded
+// spin.  On timeout the
 // status bit is set and the caller returns.
 __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_ctrl, unsigned int limit_in,
                                              unsigned int target) {
@@ -425,7 +426,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
     unsigned int spins = 0;
     int to = 0;
     while (true) {
-      const unsigned int c = atomicAdd(count, 0u);
+      const unsigned int c = load_acquire_u32(count);
       if (c >= target) break;
       if (++spins > limit) { to = 1; break; }
       __nanosleep(64);
@@ -696,8 +697,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
     if (!ENS) {
       Ctrl* ctrl = d0.ctrl;
-      const double eT = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][0], 0ull));
-      const double eR = __longlong_as_double((long long)atomicAdd(&ctrl->err_slot[it % 3][1], 0ull));
+      const double eT = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][0]));
+      const double eR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][1]));
       if (eT <= d0.si_tol && eR <= d0.si_tol) { s_conv[0] = it + 1; all_done = 1; ++it; break; }
     } else {
       if (threadIdx.x == 0) s_any = 0;
@@ -706,8 +707,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       for (int k = threadIdx.x; k < M; k += blockDim.x) {
         if (s_conv[k]) continue;
         Ctrl* cc = e.devs[k].ctrl;
-        const double eT = __longlong_as_double((long long)atomicAdd(&cc->err_slot[it % 3][0], 0ull));
-        const double eR = __longlong_as_double((long long)atomicAdd(&cc->err_slot[it % 3][1], 0ull));
+        const double eT = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][0]));
+        const double eR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][1]));
         const double tol = e.devs[k].si_tol;
         if (eT <= tol && eR <= tol) s_conv[k] = it + 1; else running = 1;
       }

@@ -33,10 +33,25 @@ __device__ __forceinline__ int find_bin(const uint32_t* __restrict__ off, int nb
 // lanes and add each run's total once (keys < 0 contribute nothing).
 // Particles are held nearly sorted by (cell, group), so a warp usually
 // issues one 128-bit atomic per run.  Integer sums: the result does not
-// depend on which lanes meet in a warp.
+// depend on which lanes meet in a warp.  Common case first: every lane with
+// a key holds the same key and v >= 0; then the warp sums v in three 21-bit
+// pieces with integer warp reductions (each piece's sum stays below 2^26;
+// v < 2^57 by the fixed-point range) instead of the segmented scan.
 __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int key, long long v) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const unsigned keyed = __ballot_sync(full, key >= 0);
+  if (!keyed) return;
+  const int first = __ffs(keyed) - 1;
+  const int k0 = __shfl_sync(full, key, first);
+  if (__all_sync(full, key < 0 || (key == k0 && v >= 0))) {
+    const unsigned long long u = key >= 0 ? (unsigned long long)v : 0ull;
+    const unsigned long long s0 = __reduce_add_sync(full, (unsigned)(u & 0x1fffffull));
+    const unsigned long long s1 = __reduce_add_sync(full, (unsigned)((u >> 21) & 0x1fffffull));
+    const unsigned long long s2 = __reduce_add_sync(full, (unsigned)(u >> 42));
+    if (lane == first) atomic_add_fixed(base + 2 * (long long)k0, (long long)(s0 + (s1 << 21) + (s2 << 42)));
+    return;
+  }
   const int prev = __shfl_up_sync(full, key, 1);
   const bool head = lane == 0 || prev != key;
   const unsigned heads = __ballot_sync(full, head);
@@ -87,24 +102,40 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-struct Counters {
-  unsigned long long seg = 0, abs = 0, esc = 0, surv = 0, rem = 0;
+struct Counters {   // per thread; a thread sees far fewer than 2^32 events
+  unsigned seg = 0, abs = 0, esc = 0, surv = 0, rem = 0;
 };
 
 __device__ __forceinline__ void flush_counters(Ctrl* ctrl, Counters& c) {
-  c.seg = warp_sum_u64(c.seg);
-  c.abs = warp_sum_u64(c.abs);
-  c.esc = warp_sum_u64(c.esc);
-  c.surv = warp_sum_u64(c.surv);
-  c.rem = warp_sum_u64(c.rem);
+  const unsigned long long seg = warp_sum_u64(c.seg), abs = warp_sum_u64(c.abs), esc = warp_sum_u64(c.esc);
+  const unsigned long long surv = warp_sum_u64(c.surv), rem = warp_sum_u64(c.rem);
   if ((threadIdx.x & 31) == 0) {
-    if (c.seg) atomicAdd(&ctrl->n_segments, c.seg);
-    if (c.abs) atomicAdd(&ctrl->n_absorbed, c.abs);
-    if (c.esc) atomicAdd(&ctrl->n_escaped, c.esc);
-    if (c.surv) atomicAdd(&ctrl->n_survived, c.surv);
-    if (c.rem) atomicAdd(&ctrl->n_removed, c.rem);
+    if (seg) atomicAdd(&ctrl->n_segments, seg);
+    if (abs) atomicAdd(&ctrl->n_absorbed, abs);
+    if (esc) atomicAdd(&ctrl->n_escaped, esc);
+    if (surv) atomicAdd(&ctrl->n_survived, surv);
+    if (rem) atomicAdd(&ctrl->n_removed, rem);
   }
   c = Counters();
+}
+
+// Step-constant fields of a single problem's control block, read once per
+// thread (the tile loop would otherwise reload them: atomics on the same
+// block keep the compiler from hoisting the loads).
+struct StepHead {
+  unsigned cur;
+  long long n_surv, n_tot;
+  uint32_t step;
+};
+
+__device__ __forceinline__ StepHead step_head(const Dev& d) {
+  const Ctrl* c = d.ctrl;
+  StepHead h;
+  h.cur = c->cur;
+  h.n_surv = (long long)c->n_part[h.cur];
+  h.n_tot = h.n_surv + (long long)c->n_new;
+  h.step = (uint32_t)c->step;
+  return h;
 }
 
 __device__ __forceinline__ long long tiles_of(const Dev& d, long long tile) {
@@ -120,16 +151,17 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
   const long long tile = (long long)blockDim.x * PPT;   // PPT sub-tiles of one particle per thread
   const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
   int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
+  const StepHead h0 = ENS ? StepHead{} : step_head(d0);
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
   const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
   if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
   const Dev& d = ENS ? e.devs[m] : d0;
   const long long lt = ENS ? t - (long long)e.tile0[m] : t;
   Ctrl* ctrl = d.ctrl;
-  const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
-  const long long n_surv = (long long)ctrl->n_part[cur];
-  const long long n_tot = n_surv + (long long)ctrl->n_new;
-  const uint32_t step = (uint32_t)ctrl->step;
+  const unsigned cur = ENS ? ctrl->cur : h0.cur, nxb = cur ^ 1u;
+  const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
+  const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
+  const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
   const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
   const double v = d.v, dt = d.dt, inv_rate = d.eps * d.eps / d.c;
   const double* __restrict__ in_x = d.px[cur];
@@ -158,7 +190,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         w = in_w[i];
         id = in_id[i];
         const uint32_t key = in_key[i];
-        cell = (int)(key / (uint32_t)G);
+        cell = (int)div_bin(d, key);
         g = (int)(key - (uint32_t)cell * (uint32_t)G);
         rng.init(id, step, 0u);
       } else {
@@ -169,18 +201,18 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
              (unsigned long long)k;
         rng.init(id, step, 0u);
-        const int cb = bin / G;
+        const int cb = (int)div_bin(d, (uint32_t)bin);
         g = bin - cb * G;
         double Tb;
         if (cb < d.ncell) {
-          const int cx = cb % nx, cy = cb / nx;
-          x = cx * d.dx + rng.next(d.key0, d.key1) * d.dx;
-          if (DIM == 2) y = cy * d.dy + rng.next(d.key0, d.key1) * d.dy;
+          const int cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0, cx = cb - cy * nx;
+          x = cx * d.dx + rng.next(d.pk) * d.dx;
+          if (DIM == 2) y = cy * d.dy + rng.next(d.pk) * d.dy;
           if (DIM == 1) {
-            ox = 2.0 * rng.next(d.key0, d.key1) - 1.0;
+            ox = 2.0 * rng.next(d.pk) - 1.0;
           } else {
-            const double muz = 2.0 * rng.next(d.key0, d.key1) - 1.0;
-            const double ph = rng.next(d.key0, d.key1);
+            const double muz = 2.0 * rng.next(d.pk) - 1.0;
+            const double ph = rng.next(d.pk);
             double sp, cp;
             sincospi(2.0 * ph, &sp, &cp);
             const double s = sqrt(fmax(0.0, 1.0 - muz * muz));
@@ -193,8 +225,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           // black-body ghost (1D): the entering set, mu ~ 2 mu dmu, distance
           // uniform within reach v mu dt
           const int side = cb - d.ncell;
-          const double u = rng.next(d.key0, d.key1);
-          const double m = sqrt(rng.next(d.key0, d.key1));
+          const double u = rng.next(d.pk);
+          const double m = sqrt(rng.next(d.pk));
           const double dd = u * v * m * dt;
           x = side == 0 ? -dd : nx * d.dx + dd;
           ox = side == 0 ? m : -m;
@@ -204,7 +236,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         }
         (void)Tb;
         if (!d.grey)
-          nu = sample_nu(d.nu_edges[g], d.nu_edges[g + 1], __ldg(d.khat + bin), rng.next(d.key0, d.key1));
+          nu = sample_nu(d.nu_edges[g], d.nu_edges[g + 1], __ldg(d.khat + bin), rng.next(d.pk));
         w = __ldg(d.omega + bin);
       }
     }
@@ -221,15 +253,15 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         t_rem = dt;
         collided = false;
       } else {
-        const double u = rng.next(d.key0, d.key1);
+        const double u = rng.next(d.pk);
         const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
         const double tc = -log(u) * inv_rate * sig_inv;
         collided = tc < dt;
         t_rem = collided ? tc : dt;
       }
       bool ghost = gside >= 0;
-      int cx = DIM == 2 ? cell % nx : cell;
-      int cy = DIM == 2 ? cell / nx : 0;
+      int cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
+      int cx = DIM == 2 ? cell - cy * nx : cell;
       const double ivx = ox != 0.0 ? 1.0 / (v * fabs(ox)) : 0.0;
       const double ivy = (DIM == 2 && oy != 0.0) ? 1.0 / (v * fabs(oy)) : 0.0;
       for (int guard = 0;; ++guard) {
@@ -280,7 +312,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           cx = nxc;
           cy = nyc;
           cell = cy * nx + cx;
-          const double u = rng.next(d.key0, d.key1);
+          const double u = rng.next(d.pk);
           const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
           const double tc = -log(u) * inv_rate * sig_inv;
           const double avail = dt - t_tra;
@@ -313,7 +345,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, w);
     }
     if (valid) {
-      cnt.seg += (unsigned long long)nseg;
+      cnt.seg += (unsigned)nseg;
       cnt.abs += fate == FATE_ABSORBED;
       cnt.esc += fate == FATE_ESCAPED;
       cnt.surv += fate == FATE_SURVIVED;
@@ -374,16 +406,17 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   const long long tile = (long long)blockDim.x * PPT;   // PPT sub-tiles of one particle per thread
   const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
   int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
+  const StepHead h0 = ENS ? StepHead{} : step_head(d0);
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
   const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
   if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
   const Dev& d = ENS ? e.devs[m] : d0;
   const long long lt = ENS ? t - (long long)e.tile0[m] : t;
   Ctrl* ctrl = d.ctrl;
-  const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
-  const long long n_surv = (long long)ctrl->n_part[cur];
-  const long long n_tot = n_surv + (long long)ctrl->n_new;
-  const uint32_t step = (uint32_t)ctrl->step;
+  const unsigned cur = ENS ? ctrl->cur : h0.cur, nxb = cur ^ 1u;
+  const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
+  const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
+  const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
   const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
   const float dxf = d.dxf, dyf = d.dyf, vf = d.vf, dtf = d.dtf;
   const float inv_rate = d.inv_rate_f, spf = d.spf;
@@ -413,10 +446,10 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         w = in_w[i];
         id = in_id[i];
         const uint32_t key = in_key[i];
-        const int cell = (int)(key / (uint32_t)G);
+        const int cell = (int)div_bin(d, key);
         g = (int)(key - (uint32_t)cell * (uint32_t)G);
-        cx = cell % nx;
-        cy = cell / nx;
+        cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
+        cx = cell - cy * nx;
         rng.init(id, step, 0u);
       } else {
         newborn = true;
@@ -426,18 +459,18 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
              (unsigned long long)k;
         rng.init(id, step, 0u);
-        const int cb = bin / G;
+        const int cb = (int)div_bin(d, (uint32_t)bin);
         g = bin - cb * G;
         if (cb < d.ncell) {
-          cx = cb % nx;
-          cy = cb / nx;
-          xi = rng.next(d.key0, d.key1) * dxf;
-          if (DIM == 2) eta = rng.next(d.key0, d.key1) * dyf;
+          cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0;
+          cx = cb - cy * nx;
+          xi = rng.next(d.pk) * dxf;
+          if (DIM == 2) eta = rng.next(d.pk) * dyf;
           if (DIM == 1) {
-            ox = 2.0f * rng.next(d.key0, d.key1) - 1.0f;
+            ox = 2.0f * rng.next(d.pk) - 1.0f;
           } else {
-            const float muz = 2.0f * rng.next(d.key0, d.key1) - 1.0f;
-            const float ph = rng.next(d.key0, d.key1);
+            const float muz = 2.0f * rng.next(d.pk) - 1.0f;
+            const float ph = rng.next(d.pk);
             float sp, cp;
             sincospif(2.0f * ph, &sp, &cp);
             const float s = sqrtf(fmaxf(0.0f, 1.0f - muz * muz));
@@ -446,8 +479,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           }
         } else {
           const int side = cb - d.ncell;
-          const float u = rng.next(d.key0, d.key1);
-          const float m = sqrtf(rng.next(d.key0, d.key1));
+          const float u = rng.next(d.pk);
+          const float m = sqrtf(rng.next(d.pk));
           const float dd = u * vf * m * dtf;
           cx = side == 0 ? -1 : nx;
           xi = side == 0 ? dxf - dd : dd;
@@ -456,7 +489,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         }
         if (!d.grey)
           nu = sample_nu_f(__ldg(d.nu_edges_f + g), __ldg(d.nu_edges_f + g + 1), __ldg(d.khat_f + bin),
-                           rng.next(d.key0, d.key1));
+                           rng.next(d.pk));
         w = __ldg(d.omega_f + bin);
       }
     }
@@ -473,7 +506,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         t_rem = dtf;
         collided = false;
       } else {
-        const UPair u = rng.next2(d.key0, d.key1);
+        const UPair u = rng.next2(d.pk);
         const float sig_inv = inv_sigma_particle_f(d, cy * nx + cx, nu, inup);
         const float tc = neg_log_u(u) * inv_rate * sig_inv;
         collided = tc < dtf;
@@ -527,7 +560,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           else eta = dir > 0 ? 0.0f : dyf;
           cx = nxc;
           cy = nyc;
-          const UPair u = rng.next2(d.key0, d.key1);
+          const UPair u = rng.next2(d.pk);
           const float sig_inv = inv_sigma_particle_f(d, cy * nx + cx, nu, inup);
           const float tc = neg_log_u(u) * inv_rate * sig_inv;
           const float avail = dtf - t_tra;
@@ -559,7 +592,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
       if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, wd);
     }
     if (valid) {
-      cnt.seg += (unsigned long long)nseg;
+      cnt.seg += (unsigned)nseg;
       cnt.abs += fate == FATE_ABSORBED;
       cnt.esc += fate == FATE_ESCAPED;
       cnt.surv += fate == FATE_SURVIVED;
