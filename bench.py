@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 from paper_2312_16981_gb300 import inputs as I  # noqa: E402
 
 N_PARTICLES = 1_000_000
-WORKLOAD = "multigroup_slab_200x30_fp64"
+WORKLOAD = "multigroup_slab_200x30"
 METRIC = "particle segments/s"
 KERNELS_PER_STEP = 9   # birth, scan x3, wave, particles, source iteration, end of step, survivor scaling
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per processed
@@ -85,7 +85,6 @@ def workload(rank: int = 0, n_particles: int = N_PARTICLES, name: str = "slab"):
 def config_dict(p, n_particles, extra=None):
     d = {"workload": WORKLOAD if p.dim == 1 else p.name, "cells": p.ncell, "groups": p.G, "dt": p.dt,
          "particles_at_start": n_particles, "state": "seeded synthetic Marshak front",
-         "precision": "mixed" if p.precision == I.MIXED else "fp64",
          "l2": "flushed between timed steps (512 MiB write)"}
     if extra:
         d.update(extra)
@@ -187,6 +186,27 @@ def algorithmic_bytes(p, phase, n_read, n_out, si_iters, mixed=False):
     return 0
 
 
+def roofline(p, phase, launch_ms, n_proc, n_read, n_out, si_iters, mixed, pk, src):
+    """Roofline of one kernel launch from its CUDA-event duration: the
+    particle kernel against HBM (algorithmic bytes per launch); the source
+    iteration, bound by the FP64 pipe, against HBM as well (its ~10 arrays of
+    cells x groups per iterate), with the FP64 bound stated beside it."""
+    abytes = algorithmic_bytes(p, phase, n_read, n_out, si_iters, mixed=mixed)
+    ach = abytes / (launch_ms * 1e-3) / 1e9 if abytes else 0.0
+    traffic = (TRAFFIC_PER_PROCESSED["mixed" if mixed else "fp64"] * n_proc
+               if phase == "particles" and p.dim == 1 else None)
+    r = {"kernel": {"particles": "k_stream32" if mixed else "k_stream64",
+                    "source_iteration": "k_si"}.get(phase, phase),
+         "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+         "frac": ach / pk["hbm_gbs"], "traffic": traffic, "peak_source": src,
+         "algorithmic_bytes_per_launch": abytes, "launch_ms": launch_ms}
+    if traffic is not None:
+        r["traffic_source"] = "ncu capture at 4e6 particles, scaled by particles processed per launch"
+    if phase == "source_iteration" or (phase == "particles" and not mixed):
+        r["note"] = "FP64-pipe bound on GB300 (see profiles/): HBM is not the limit of this kernel"
+    return r
+
+
 def timed_steps(sim, steps, flush, sampler=None):
     """Device time per step (CUDA events) with L2 flushed between steps."""
     import torch
@@ -206,6 +226,32 @@ def timed_steps(sim, steps, flush, sampler=None):
     torch.cuda.synchronize()
     assert t["status_bits"] == 0, t["status_bits"]
     return phases, segs, (n_proc, n_read), n_out, si
+
+
+def graph_steps(sim, steps, flush):
+    """Device time of `steps` whole steps replayed as the library's CUDA graph
+    (ugkwp_step), CUDA events on the launching stream around each step, L2
+    flushed before each; counters from the tally report after each step."""
+    import torch
+    ms = 0.0
+    segs = n_proc = n_read = n_out = si = 0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.fill_(1)
+        a.record()
+        sim.step(1)
+        b.record()
+        b.synchronize()
+        ms += a.elapsed_time(b)
+        t = sim.tallies()
+        segs += t["n_segments"]
+        n_proc += t["n_in"] + t["n_born"]
+        n_read += t["n_in"]
+        n_out += t["n_survived"]
+        si += t["si_iters"]
+    assert t["status_bits"] == 0, t["status_bits"]
+    return ms, segs, (n_proc, n_read), n_out, si
 
 
 def device_ms(fn, flush=None):
@@ -336,7 +382,8 @@ def matched_error_leg(B, dev, steps=500, seeds=8, refine=16):
 def checkerboard_leg(B, dev, flush, steps, warmup, n_particles):
     """The 2D 256x256 checkerboard (30 groups, thick/thin 16x16 blocks,
     central T_s = 1 source) from a seeded synthetic state with n_particles
-    particles: FP64 and mixed precision builds, phase times from CUDA events."""
+    particles: FP64 and mixed precision builds, whole steps as CUDA-graph
+    replays, then a few kernel-by-kernel steps for the phase times."""
     p = I.checkerboard_2d()
     p.particle_capacity = max(p.particle_capacity, int(1.6 * n_particles))
     s = I.synthetic_state(p, n_particles, seed=3, front=0.35)
@@ -347,9 +394,10 @@ def checkerboard_leg(B, dev, flush, steps, warmup, n_particles):
         sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
         for _ in range(max(warmup, 3)):
             sim.step(1)
-        ph, segs, (n_in, _), n_out, si = timed_steps(sim, steps, flush)
-        out[name] = {"value": segs / (ph[0] / 1e3), "unit": "segments/s", "ms_per_step": float(ph[0] / steps),
-                     "phase_ms_per_step": {n: float(ph[i] / steps) for i, n in enumerate(names)},
+        ms, segs, (n_in, _), n_out, si = graph_steps(sim, steps, flush)
+        ph, _, _, _, _ = timed_steps(sim, max(2, steps // 2), flush)
+        out[name] = {"value": segs / (ms / 1e3), "unit": "segments/s", "ms_per_step": ms / steps,
+                     "phase_ms_per_step": {n: float(ph[i] / max(2, steps // 2)) for i, n in enumerate(names)},
                      "particles_per_step": n_in / steps, "si_iters_per_step": si / steps}
         sim.close()
         del sim
@@ -466,8 +514,8 @@ def main():
     names = ["total", "birth_scan", "wave", "particles", "source_iteration", "end"]
     pk, src = peaks()
     p, s = workload(rank, args.particles, args.workload if args.quick else "slab")
-    if args.quick and args.precision == "mixed":
-        p = p.replace(precision=I.MIXED)
+    head_mixed = args.precision == "mixed" if args.quick else True
+    p_head = p.replace(precision=I.MIXED if head_mixed else I.FP64)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def prepare(prob):
@@ -478,60 +526,58 @@ def main():
         assert sim.tallies()["status_bits"] == 0
         return sim
 
-    sim = prepare(p)
-    simm = None if args.quick else prepare(p.replace(precision=I.MIXED))
+    sim = prepare(p_head)
+    sim64 = None if args.quick else prepare(p.replace(precision=I.FP64))
 
-    # ---- timed regions: FP64, then mixed precision (device time, CUDA events)
+    # ---- timed region: whole steps as CUDA-graph replays (the headline build,
+    # then the plain FP64 build it is compared with), device time from events
     barrier()
     with ClockSampler(local) as clk:
-        phases, segs, (n_in, n_rd), n_out, si = timed_steps(sim, K, flush)
-        if simm is not None:
-            mph, msegs, (min_, mrd), mout, msi = timed_steps(simm, K, flush)
+        total_ms, segs, (n_in, n_rd), n_out, si = graph_steps(sim, K, flush)
+        if sim64 is not None:
+            ms64, segs64, (n_in64, n_rd64), n_out64, si64 = graph_steps(sim64, K, flush)
     barrier()
     clocks = clk.summary()
-    total_ms = float(phases[0])
     total_ms_max, segs_all = combine_replicas(total_ms, float(segs), world, dev)
     value = segs_all / (total_ms_max / 1e3)
 
-    # ---- roofline of the dominant kernel (FP64 build)
+    # ---- phase breakdown and per-launch kernel durations: the same step
+    # launched kernel by kernel with events between the phases
+    phases, _, (pn_in, pn_rd), pn_out, psi = timed_steps(sim, K, flush)
     dom = int(np.argmax(phases[1:])) + 1
-    per_launch_ms = phases[dom] / K
-    abytes = algorithmic_bytes(p, names[dom], n_rd / K, n_out / K, si / K, mixed=p.precision == I.MIXED)
-    ach = abytes / (per_launch_ms * 1e-3) / 1e9 if abytes else 0.0
-    mixed_run = p.precision == I.MIXED
-    traffic = (TRAFFIC_PER_PROCESSED["mixed" if mixed_run else "fp64"] * n_in / K
-               if names[dom] == "particles" and p.dim == 1 else None)
-    roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": traffic,
-            "peak_source": src, "algorithmic_bytes_per_launch": abytes,
-            "traffic_source": "ncu capture at 4e6 particles, scaled by particles processed per launch"}
+    roof = roofline(p_head, names[dom], phases[dom] / K, pn_in / K, pn_rd / K, pn_out / K, psi / K,
+                    head_mixed, pk, src)
+    roof_p = roofline(p_head, "particles", phases[3] / K, pn_in / K, pn_rd / K, pn_out / K, psi / K,
+                      head_mixed, pk, src)
 
     line = {"metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": total_ms_max / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if head_mixed else "f64",
+            "precision": ("mixed: f32 particle state and arithmetic; f64 tallies, source iteration, "
+                          "Planck integrals and energy ledger" if head_mixed else "f64 throughout"),
             "data": "synthetic",
             "config": config_dict(p, args.particles, {"parallelism": "replicas" if world > 1 else "single"}),
+            "timing": "CUDA events around each whole step (one CUDA-graph replay of all kernels)",
             "steps_per_s": K / (total_ms_max / 1e3),
             "phase_ms_per_step": {n: float(phases[i] / K) for i, n in enumerate(names)},
+            "phase_timing": "the same step launched kernel by kernel, events between phases (%d more steps)" % K,
             "particles_per_step": n_in / K, "si_iters_per_step": si / K,
-            "roofline": roof, "clocks": clocks}
+            "roofline": roof, "particle_kernel_roofline": roof_p, "clocks": clocks}
 
-    if simm is not None:
-        mb = algorithmic_bytes(p, "particles", mrd / K, mout / K, 0, mixed=True)
-        mach = mb / (mph[3] / K * 1e-3) / 1e9
-        line["mixed"] = {
-            "value": msegs / (mph[0] / 1e3), "unit": "segments/s",
-            "dtype": "f32 particle state, f64 tallies and source iteration",
-            "ms_per_step": float(mph[0] / K),
-            "speedup_vs_fp64": (msegs / mph[0]) / (segs / phases[0]),
-            "phase_ms_per_step": {n: float(mph[i] / K) for i, n in enumerate(names)},
-            "particle_kernel_roofline": {"bound": "hbm", "achieved": mach, "peak": pk["hbm_gbs"],
-                                         "unit": "GB/s", "frac": mach / pk["hbm_gbs"],
-                                         "algorithmic_bytes_per_launch": mb,
-                                         "traffic": TRAFFIC_PER_PROCESSED["mixed"] * min_ / K}}
-        simm.close()
+    if sim64 is not None:
+        ph64, _, (qn_in, qn_rd), qn_out, qsi = timed_steps(sim64, K, flush)
+        line["fp64"] = {
+            "value": segs64 / (ms64 / 1e3), "unit": "segments/s", "dtype": "f64",
+            "ms_per_step": ms64 / K, "steps_per_s": K / (ms64 / 1e3),
+            "phase_ms_per_step": {n: float(ph64[i] / K) for i, n in enumerate(names)},
+            "particles_per_step": n_in64 / K, "si_iters_per_step": si64 / K,
+            "particle_kernel_roofline": roofline(p, "particles", ph64[3] / K, qn_in / K, qn_rd / K, qn_out / K,
+                                                 qsi / K, False, pk, src)}
+        line["speedup_vs_fp64"] = value / line["fp64"]["value"]
+        sim64.close()
 
-        # ---- end to end through the C ABI with host buffers
+        # ---- end to end through the C ABI with host buffers (headline build)
         Tdev = sim.device_array("T")
         Rdev = sim.device_array("rho")
         Th = torch.empty(Tdev.shape, dtype=torch.float64, pin_memory=True)
@@ -557,9 +603,10 @@ def main():
                        "d2h_bytes_per_step": int(Th.numel() + Rh.numel()) * 8,
                        "what": "per step: H2D of T and rho from pinned host memory, ugkwp_step "
                                "(CUDA graph), D2H of T, rho and the tally report"}
-        line["gpu_launches"] = KERNELS_PER_STEP * K * 3
+        # timed graph steps of both builds, their phase passes, and the e2e steps
+        line["gpu_launches"] = KERNELS_PER_STEP * K * 5
     else:
-        line["gpu_launches"] = KERNELS_PER_STEP * K
+        line["gpu_launches"] = KERNELS_PER_STEP * K * 2
 
     extra_legs = rank == 0 and world == 1 and not args.quick
     if extra_legs and not args.no_matched_error:

@@ -205,6 +205,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;
   d.inv_c = 1.0 / p->c;
+  d.inv_vol = 1.0 / d.vol;
   d.rate_f = p->c / (p->eps * p->eps);
   d.omega_ref = p->omega_ref;
   d.si_tol = p->si_tol;

@@ -213,7 +213,7 @@ struct Dev {
   double* E_surv;   // [ncell*G] (FP64 copy written by the source iteration)
   unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
   unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
-  double inv_dx, inv_dy, inv_c;
+  double inv_dx, inv_dy, inv_c, inv_vol;
   double inv_2dt;             // 1/(2 dt)
   double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-48) and its inverse
   int tq_shift;

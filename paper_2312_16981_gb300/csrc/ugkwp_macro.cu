@@ -541,14 +541,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (g < G) {
           const int i = c * G + g;
           const double r0 = d.rho[i];
-          double r = r0 + (dt / d.dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
-          if (d.dim == 2) r += (dt / d.dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
+          double r = r0 + (dt * d.inv_dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
+          if (d.dim == 2) r += (dt * d.inv_dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
           const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
           d.W[i] = Wd;
-          r += Wd / V;
-          if (d.src) { r += d.src[i]; e_src += V * d.src[i] / d.c; }
+          r += Wd * d.inv_vol;
+          if (d.src) { r += d.src[i]; e_src += V * d.src[i] * d.inv_c; }
           d.R[i] = r;
-          e_rad0 += V * r0 / d.c;
+          e_rad0 += V * r0 * d.inv_c;
         }
       }
       const double T = d.T[c];
@@ -606,7 +606,6 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         dpc[j] = __ldcg(d.dphik + i);
         double q = d.R[i];
         for (int axis = 0; axis < d.dim; ++axis) {
-          const double h = axis == 0 ? d.dx : d.dy;
           const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
@@ -620,7 +619,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
             if (owner) d.Feq[face_index(d, c, axis, dir) * G + g] = F;
             if (dir < 0) Fin = F; else Fout = F;
           }
-          q += (dt / h) * (Fin - Fout);
+          q += (dt * inv_h) * (Fin - Fout);
         }
         Q[j] = q;
         const double qi = 1.0 / (tc + dt);
@@ -764,7 +763,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         // group): their weights are scaled to it (rho and the energy unchanged)
         const double Es = from_fixed(d.Esq + 2 * i, d.tq);
         d.E_surv[i] = Es;
-        double rp = Es / V, f = 1.0;
+        double rp = Es * d.inv_vol, f = 1.0;
         if (rp > 0.0 && r < rp) {
           f = r > 0.0 ? r / rp : 0.0;
           rp = r > 0.0 ? r : 0.0;
@@ -773,18 +772,18 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         d.wscale[i] = f;
         d.rho_p[i] = rp;
         d.rho_h[i] = r - rp;
-        e_rad1 += V * r / d.c;
+        e_rad1 += V * r * d.inv_c;
         // boundary faces: energy entering the domain
         for (int axis = 0; axis < d.dim; ++axis) {
           const double S = d.dim == 2 ? (axis == 0 ? d.dy : d.dx) : 1.0;
           const int k = axis == 0 ? ix : iy, nk = axis == 0 ? d.nx : d.ny;
           if (k == 0) {
             const int f = face_index(d, c, axis, -1);
-            b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+            b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
           }
           if (k == nk - 1) {
             const int f = face_index(d, c, axis, +1);
-            b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) / d.c;
+            b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
           }
         }
       }
