@@ -38,7 +38,7 @@ class CProblem(C.Structure):
         ("omega_ref", C.c_double), ("si_tol", C.c_double), ("src_on", C.c_double),
         ("tau_num_C", C.c_double),
         ("bcT", C.c_double * 4),
-        ("seed", C.c_uint64), ("instance", C.c_uint32), ("_pad1", C.c_uint32),
+        ("seed", C.c_uint64), ("instance", C.c_uint32), ("method", C.c_int32),
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("src_T", _dp),
     ]
 
@@ -151,6 +151,7 @@ class OracleProblem:
         s.tau_num_C = float(getattr(p, "tau_num_C", 0.0))
         s.sig_law = int(getattr(p, "sig_law", 0))
         s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
+        s.method = int(getattr(p, "method", 0))
         s.nu_edges, s.sigma0, s.cv = _d(self.nu_edges), _d(self.sigma0), _d(self.cv)
         s.src_T = _d(self.src_T) if self.src_T is not None else None
         self.s = s

@@ -282,7 +282,10 @@ double or_sample_nu(double nlo, double nhi, double T, double eta) {
 /* Streaming of one particle (Algorithm 1 steps 3-5 with the t_f reset of the
  * interface remark).  Free time t_f = min(-tau ln eta, dt) (Eq. particle tf
  * formula) for a particle alive at step start; t_f = dt in the birth cell for
- * a newborn (Eq. IhpFormula samples collisionless particles only); on
+ * a newborn (Eq. IhpFormula samples collisionless particles only), except in
+ * the UGKP variant (Sec. 2.2), whose newborns sample all of I^h and so draw
+ * their t_f like every other particle (after their position, direction and
+ * frequency draws; a black-body ghost's entering particles keep t_f = dt); on
  * entering a new cell t_f2 = min(-tau_new ln eta, dt - t_tra).  Trajectory
  * x = x^n + (c/eps) Omega t (Sec. 2.2).  Readings: a face is crossed only if
  * the time to reach it is strictly below the remaining free time; at a
@@ -323,7 +326,7 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
   if (n_trace) *n_trace = 0;
   (void)nu_p_T;
 
-  if (newborn) {
+  if (newborn && (P->method != OR_UGKP || ghost)) {
     t_rem = dt;
     collided = 0;
   } else {
@@ -411,7 +414,11 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
  * those that reach the wall within dt matter, and they carry
  * E = e (c/eps)/4 Phi_g(T_b) dt through the wall (the half-range flux of an
  * isotropic ghost).  They are sampled directly (see or_step).  Bins are
- * ordered interior cells (c*G + g) then ghosts ((ncell + side)*G + g).      */
+ * ordered interior cells (c*G + g) then ghosts ((ncell + side)*G + g).
+ * UGKP variant (Sec. 2.2, the specific intensity fully represented by
+ * particles): an interior bin samples all of its wave part, E = max(rho_h, 0)
+ * V, and marks it with e_eff = -1 (the wave flux then carries none of it);
+ * black-body ghosts are sampled as in UGKWP.                                 */
 /* Numerical collision time for the thin/thick joint (Sec. 3.2, heterogeneous
  * cases): tau_num = tau + C (T^l - T^r)/(T^l + T^r) dt is written per
  * interface.  Readings: the magnitude of the temperature contrast (the stated
@@ -463,13 +470,14 @@ int or_birth_counts(const or_problem* P, const double* T, const double* rho_h,
     if (cell < ncell) x = or_x_num(P, T, cell, g);
     else x = P->dt * rate_f * or_sigma_group(P, src_cell, g, Tb);
     double e = exp(-x);
-    E *= e;
+    const int all = P->method == OR_UGKP && cell < ncell;   /* UGKP: the whole wave part */
+    if (!all) E *= e;
     if (!(P->omega_ref > 0.0) || !(E > 0.0)) continue;
     double q = floor(E / P->omega_ref + 0.5);
     if (q > (double)MAX_K_PER_BIN) { status = OR_ERR_CAPACITY; q = MAX_K_PER_BIN; }
     int N = (int)q;
     tal->N[b] = N;
-    if (N > 0) { tal->omega[b] = E / N; tal->e_eff[b] = e; }
+    if (N > 0) { tal->omega[b] = E / N; tal->e_eff[b] = all ? -1.0 : e; }
     total += N;
   }
   *n_new = total;
@@ -498,12 +506,18 @@ static double van_leer(double dl, double dr) {
 }
 
 /* Coefficients of one half: A = C4_f - e_h, B = C5_f + dt e_h/2, where
- * e_h = exp(-x_h) of the upwind cell (or 0), written without cancellation. */
+ * e_h = exp(-x_h) of the upwind cell (or 0), written without cancellation;
+ * A = B = 0 for a half whose whole wave part was sampled (UGKP, e_eff < 0). */
 static void half_coefs(double x_f, double tau_f, double x_h, double e_eff, double dt,
                        double* A, double* B) {
   double f2, f4, f5, c4;
   or_coefs(x_f, &f2, &f4, &f5, &c4);
-  if (e_eff > 0.0) {
+  if (e_eff < 0.0) {
+    /* UGKP: the particles carry the whole free transport F^{fr,UGKS}(I^h) of
+     * this half, so the wave part contributes nothing */
+    *A = 0.0;
+    *B = 0.0;
+  } else if (e_eff > 0.0) {
     /* e_f - e_h, without cancellation when x_h ~ x_f and without overflow */
     double d = x_h - x_f;
     double ef_minus_eh = fabs(d) < 0.5 ? exp(-x_h) * expm1(d) : exp(-x_f) - exp(-x_h);

@@ -23,6 +23,7 @@ extern "C" {
 #endif
 
 enum { OR_BC_REFLECT = 0, OR_BC_VACUUM = 1, OR_BC_BLACKBODY = 2 };
+enum { OR_UGKWP = 0, OR_UGKP = 1 };
 enum { OR_SURVIVED = 0, OR_ABSORBED = 1, OR_ESCAPED = 2, OR_REMOVED = 3 };
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_CAPACITY = -3, OR_ERR_NOCONV = -4,
        OR_ERR_NONFINITE = -5 };
@@ -44,7 +45,7 @@ typedef struct {
   double bcT[4];
   uint64_t seed;
   uint32_t instance;
-  uint32_t _pad1;
+  int32_t method;                 /* OR_UGKWP (0) or OR_UGKP (1, Sec. 2.2: all of I^h as particles) */
   const double* nu_edges;         /* [G+1] */
   const double* sigma0;           /* [ncell] */
   const double* cv;               /* [ncell] */

@@ -20,6 +20,7 @@ import numpy as np
 
 BC_REFLECT, BC_VACUUM, BC_BLACKBODY = 0, 1, 2
 FP64, MIXED = 0, 1
+UGKWP, UGKP = 0, 1
 
 
 @dataclass
@@ -50,6 +51,7 @@ class Problem:
     src_on: float = 0.0
     tau_num_C: float = 0.0   # thin/thick joint sampling constant C of tau_num (0: off)
     sig_law: int = 0         # 0: sigma0 nu^p T^q; 1: times (1 - e^{-nu/T}) (Larsen case)
+    method: int = 0          # 0: UGKWP (sample the collisionless part); 1: UGKP (sample all of I^h)
     omega_ref: float = 1e-6
     seed: int = 0
     instance: int = 0
