@@ -54,6 +54,12 @@ extern "C" {
 
 enum { UGKWP_BC_REFLECT = 0, UGKWP_BC_VACUUM = 1, UGKWP_BC_BLACKBODY = 2 };
 enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
+/* Method (Sec. 2.2): UGKWP samples the collisionless part e^{-dt/tau} I^h of
+ * the wave part with t_f = dt; UGKP samples all of I^h, every newborn draws
+ * its own free time, and a sampled half carries no wave flux (the particles
+ * carry its whole free transport).  Black-body sides are sampled the UGKWP
+ * way in both.  The adjoint entry points accept UGKWP only. */
+enum { UGKWP_METHOD_UGKWP = 0, UGKWP_METHOD_UGKP = 1 };
 
 /* Problem statement (Sec. 3 numerical set-up; all pointers are HOST pointers,
  * read during ugkwp_init only; the caller keeps ownership).
@@ -90,7 +96,7 @@ typedef struct ugkwp_problem {
   double bcT[4];
   uint64_t seed;          /* Philox key = (seed_lo, seed_hi ^ instance) */
   uint32_t instance;
-  uint32_t _pad1;
+  int32_t method;         /* UGKWP_METHOD_UGKWP (0) or UGKWP_METHOD_UGKP (1) */
   int64_t particle_capacity;   /* maximum surviving particles held between steps */
   const double* nu_edges;      /* [G+1] increasing, > 0 (ignored when grey) */
   const double* sigma0;        /* [ncell] */

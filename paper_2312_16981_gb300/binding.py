@@ -43,7 +43,7 @@ class CProblem(C.Structure):
         ("omega_ref", C.c_double), ("si_tol", C.c_double), ("src_on", C.c_double),
         ("tau_num_C", C.c_double),
         ("bcT", C.c_double * 4), ("seed", C.c_uint64), ("instance", C.c_uint32),
-        ("_pad1", C.c_uint32), ("particle_capacity", C.c_int64),
+        ("method", C.c_int32), ("particle_capacity", C.c_int64),
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("T0", _dp), ("rho0", _dp),
         ("src_T", _dp),
     ]
@@ -189,6 +189,7 @@ class _HostProblem:
         s.tau_num_C = float(p.tau_num_C)
         s.sig_law = int(p.sig_law)
         s.seed, s.instance = p.seed & 0xFFFFFFFFFFFFFFFF, p.instance
+        s.method = int(getattr(p, "method", 0))
         s.particle_capacity = int(p.particle_capacity)
         s.nu_edges = arr(p.nu_edges, p.G + 1)
         s.sigma0 = arr(p.sigma0, p.ncell)

@@ -82,6 +82,8 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
   if (!(p->tau_num_C >= 0.0)) return fail(h, UGKWP_ERR_ARG, "tau_num_C must be >= 0");
   if (p->sig_law != 0 && p->sig_law != 1) return fail(h, UGKWP_ERR_ARG, "sig_law must be 0 or 1");
+  if (p->method != UGKWP_METHOD_UGKWP && p->method != UGKWP_METHOD_UGKP)
+    return fail(h, UGKWP_ERR_ARG, "method must be 0 (UGKWP) or 1 (UGKP)");
   const long long nbins = (ncell_of(p) + 4) * p->G;
   if (nbins >= (1ll << 24)) return fail(h, UGKWP_ERR_ARG, "(ncell+4)*G must be < 2^24 (particle id layout)");
   return UGKWP_OK;
@@ -212,6 +214,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.src_on = p->src_on;
   d.tau_num_C = p->tau_num_C;
   d.sig_law = p->sig_law;
+  d.method = p->method;
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
   d.pk = ugkwp::philox_keys(d.key0, d.key1);
@@ -792,6 +795,8 @@ int adjoint_check(ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates tau, not tau_num (tau_num_C = 0)");
   if (h->d.sig_law != 0)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the power-law opacity (sig_law = 0)");
+  if (h->d.method != UGKWP_METHOD_UGKWP)
+    return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the UGKWP sampling (method = 0)");
   return UGKWP_OK;
 }
 }  // namespace

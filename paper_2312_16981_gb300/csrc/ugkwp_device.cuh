@@ -177,6 +177,7 @@ struct Dev {
   // geometry / model
   int dim, nx, ny, G, ncell, nbins, nface, nxface;
   int grey, wave_order, si_max_iters, precision, sig_law;
+  int method;        // 0 UGKWP, 1 UGKP (all of I^h sampled; newborns draw t_f)
   int bc[4];
   double dx, dy, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
   double v;          // c/eps, particle speed

@@ -71,7 +71,8 @@ __global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
 // Birth counts (Eq. IhpFormula, weight formula of Sec. 2.2): per bin the
 // collisionless part E = e^{-dt/tau} max(rho_h, 0) V, tau from the Simpson
 // group opacity at T^n, N = floor(E/omega_ref + 1/2), omega = E/N, e_eff = e
-// if N > 0 else 0.  Black-body ghost bins (1D) carry the entering part of the
+// if N > 0 else 0 (UGKP: an interior bin samples E = max(rho_h, 0) V and
+// marks e_eff = -1).  Black-body ghost bins (1D) carry the entering part of the
 // ghost's collisionless particles, E = e (c/eps)/4 Phi_g(T_b) dt.  Also
 // stores sigma_g(T^n), sigma0 T^q per cell, the sampler slope per bin, zeroes
 // this step's tallies and resets the per-step counters.
@@ -151,14 +152,15 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     }
     d.xnum[b] = x;
     const double e = exp(-x);
-    E *= e;
+    const bool all = d.method == 1 && cell < d.ncell;   // UGKP: the whole wave part
+    if (!all) E *= e;
     uint32_t N = 0;
     double w = 0.0, ee = 0.0;
     if (d.omega_ref > 0.0 && E > 0.0) {
       double q = floor(E / d.omega_ref + 0.5);
       if (q > (double)kMaxPerBin) { q = (double)kMaxPerBin; atomicOr(&ctrl->status, ST_CAPACITY); }
       N = (uint32_t)q;
-      if (N) { w = E / (double)N; ee = e; }
+      if (N) { w = E / (double)N; ee = all ? -1.0 : e; }
     }
     d.N[b] = N;
     d.omega[b] = w;
@@ -328,7 +330,11 @@ __global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
 __device__ __forceinline__ void half_coefs(double xf, double ef, double tauf, double xh, double e_eff,
                                            double dt, double f4, double f5, double c4,
                                            double* A, double* B) {
-  if (e_eff > 0.0) {
+  if (e_eff < 0.0) {
+    // UGKP: the particles carry this half's whole free transport
+    *A = 0.0;
+    *B = 0.0;
+  } else if (e_eff > 0.0) {
     const double dd = xh - xf;
     const double efh = fabs(dd) < 0.5 ? e_eff * expm1(dd) : (ef >= 0.0 ? ef : exp(-xf)) - e_eff;
     *A = f4 + efh;

@@ -5,8 +5,10 @@
 // time t_f = min(-tau ln eta, dt), Eq. particle-tf-formula), then the
 // particles sampled this step from the wave part's collisionless fraction
 // (Eq. IhpFormula; born in registers with t_f = dt, never stored unless they
-// survive).  Each particle streams cell by cell with the free time reset on
-// entering a new cell (interface remark: t_f2 = min(-tau_i ln eta, dt - t_tra)),
+// survive; in the UGKP variant all of the wave part is sampled and a newborn
+// draws its free time after its birth draws).  Each particle streams cell by
+// cell with the free time reset on entering a new cell (interface remark:
+// t_f2 = min(-tau_i ln eta, dt - t_tra)),
 // reflects at mirror walls, escapes through open sides.  Tallies: the net
 // particle energy per (cell, group) w^{fr,p} (Eq. wfrpFormula, accumulated as
 // end minus start, which telescopes the face crossings), the energy of the
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       const double inup = d.grey ? 1.0 : pow_fast(nu, -d.sig_p);
       double t_rem;
       bool collided;
-      if (newborn) {
+      if (newborn && (d.method == 0 || gside >= 0)) {   // UGKP newborns draw t_f too
         t_rem = dt;
         collided = false;
       } else {
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
       const float inup = d.grey ? 1.0f : pow_fast_f(nu, -spf);
       float t_rem;
       bool collided;
-      if (newborn) {
+      if (newborn && (d.method == 0 || gside >= 0)) {   // UGKP newborns draw t_f too
         t_rem = dtf;
         collided = false;
       } else {
