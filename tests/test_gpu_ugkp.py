@@ -24,11 +24,18 @@ def B():
     return binding
 
 
+def warm_slab(omega_ref=5e-5):
+    # a warm medium, so the interior wave part (not only the black-body
+    # side) is sampled: step 0 samples all of it, later steps the remainder
+    p = I.small_multigroup(nx=24, G=6, omega_ref=omega_ref).replace(method=I.UGKP)
+    p.T0 = np.linspace(1.0, 0.2, p.nx)
+    return p
+
+
 @pytest.mark.parametrize("before", [0, 2])
 def test_ugkp_step_parity_multigroup_slab(B, before):
-    p = I.small_multigroup(nx=24, G=6, omega_ref=2e-6).replace(method=I.UGKP)
-    t, tal = check_step(B, p, before)
-    assert t["n_born"] > 1000 and t["n_absorbed"] > 100
+    t, tal = check_step(B, warm_slab(), before)
+    assert t["n_born"] > (4000 if before == 0 else 200) and t["n_absorbed"] > 100
 
 
 def test_ugkp_step_parity_checkerboard_2d(B):
@@ -39,8 +46,8 @@ def test_ugkp_step_parity_checkerboard_2d(B):
 
 def test_ugkp_wave_flux_matches_oracle(B):
     # the flux of the unsampled remainder, with sampled halves contributing none
-    p = I.small_multigroup(nx=24, G=6, omega_ref=2e-6).replace(method=I.UGKP)
-    op, st = oracle_run(p, 2)
+    p = warm_slab()
+    op, st = oracle_run(p, 0)
     sim = B.Simulation(p)
     sim.set_state(st.T, st.rho, st.rho_h, st.particles.view(), step=st.step)
     sim.step(1)
@@ -55,17 +62,18 @@ def test_ugkp_wave_flux_matches_oracle(B):
     assert both.any() and not inner[both].any()
 
 
-def test_ugkp_mixed_precision_slab(B):
-    p = I.small_multigroup(nx=24, G=6, omega_ref=2e-6).replace(method=I.UGKP)
+@pytest.mark.parametrize("before", [0, 2])
+def test_ugkp_mixed_precision_slab(B, before):
+    p = warm_slab()
     op = O.OracleProblem(p)
     st = O.initial_state(op)
-    for _ in range(3):
+    for _ in range(before):
         st, _, _, _ = O.step(op, st)
     M.check(p, *M.run_pair(B, p, st, op))
 
 
 def test_ugkp_steps_from_initial_state(B):
-    p = I.small_multigroup(nx=16, G=5, omega_ref=5e-6).replace(method=I.UGKP)
+    p = warm_slab(2e-4)
     _, st = oracle_run(p, 4)
     sim = B.Simulation(p)
     sim.step(4)
