@@ -485,6 +485,46 @@ __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir
   return true;
 }
 
+// F^eq on face f at iterate k (lower side l, upper side u), or 0 at a
+// reflecting wall; a black-body ghost takes tau = 1/(rate sigma_g(T_b)) and
+// Phi_g(T_b), a vacuum ghost the inner cell's tau and Phi = 0.  The same
+// expression, with the same operands, as a cell's own evaluation through
+// neighbour(): the two agree bitwise.
+__device__ __forceinline__ double face_feq(const Dev& d, int f, int g, int cur) {
+  const FaceRef r = face_ref(d, f);
+  const int sideL = r.axis * 2, sideR = sideL + 1;
+  const bool lin = r.k - 1 >= 0, rin = r.k < r.nk;
+  if ((!lin && d.bc[sideL] == BC_REFLECT) || (!rin && d.bc[sideR] == BC_REFLECT)) return 0.0;
+  double tl = 0.0, tu = 0.0, pl = 0.0, pu = 0.0;
+  if (lin) {
+    const int i = line_cell(d, r, r.k - 1) * d.G + g;
+    tl = __ldcg(d.tauk[cur] + i);
+    pl = __ldcg(d.phik[cur] + i);
+  }
+  if (rin) {
+    const int i = line_cell(d, r, r.k) * d.G + g;
+    tu = __ldcg(d.tauk[cur] + i);
+    pu = __ldcg(d.phik[cur] + i);
+  }
+  if (!lin) {
+    if (d.bc[sideL] == BC_BLACKBODY) {
+      tl = 1.0 / (d.rate_f * d.ghost_sig[sideL * d.G + g]);
+      pl = d.ghost_phi[sideL * d.G + g];
+    } else {
+      tl = tu;
+    }
+  }
+  if (!rin) {
+    if (d.bc[sideR] == BC_BLACKBODY) {
+      tu = 1.0 / (d.rate_f * d.ghost_sig[sideR * d.G + g]);
+      pu = d.ghost_phi[sideR * d.G + g];
+    } else {
+      tu = tl;
+    }
+  }
+  return feq_face(d, tl, tu, pl, pu, r.axis == 0 ? d.inv_dx : d.inv_dy);
+}
+
 // Source iteration (App. B, Algorithm 2) in 1D and 2D, one warp per cell and
 // one lane per group.  Iterate k: equilibrium fluxes from sigma^k, Phi^k of
 // the cell and its neighbours (Jacobi), then the linearised closed-form update
@@ -587,9 +627,26 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   // ---- iterations
   const int max_it = ENS ? e.devs[0].si_max_iters : d0.si_max_iters;
   int it = 0, all_done = 0;
+  // 2D: every face's F^eq once per iterate (one warp per face, one lane per
+  // group), then a grid barrier, instead of each cell evaluating its four
+  // faces (a face costs a division and the C2 interpolant in FP64, the
+  // scarce unit on this chip; in 1D the extra barrier costs more than the
+  // second evaluation of a face saves)
+  const bool face_pass = !ENS && d0.dim == 2;
   for (; it < max_it; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
     double werrT = 0.0, werrR = 0.0;
+    if (face_pass) {
+      const int G = d0.G;
+      for (long long gf = gw; gf < d0.nface; gf += nw) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const int g = lane + 32 * j;
+          if (g < G) d0.Feq[gf * G + g] = face_feq(d0, (int)gf, g, cur);
+        }
+      }
+      if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+    }
     for (long long gc = gw; gc < total; gc += nw) {
       const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
       if (ENS && s_conv[m]) continue;
@@ -611,7 +668,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         phc[j] = __ldcg(d.phik[cur] + i);
         dpc[j] = __ldcg(d.dphik + i);
         double q = d.R[i];
-        for (int axis = 0; axis < d.dim; ++axis) {
+        if (face_pass) {
+          for (int axis = 0; axis < 2; ++axis) {
+            const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
+            const double Fin = __ldcg(d.Feq + face_index(d, c, axis, -1) * G + g);
+            const double Fout = __ldcg(d.Feq + face_index(d, c, axis, +1) * G + g);
+            q += (dt * inv_h) * (Fin - Fout);
+          }
+        }
+        for (int axis = 0; axis < (face_pass ? 0 : d.dim); ++axis) {
           const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
