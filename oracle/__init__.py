@@ -40,6 +40,8 @@ class CProblem(C.Structure):
         ("bcT", C.c_double * 4),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("method", C.c_int32),
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("src_T", _dp),
+        ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
+        ("cv_chi", C.c_double),
     ]
 
 
@@ -82,6 +84,9 @@ def lib():
         L.or_sigma.restype = C.c_double
         L.or_sigma_group.argtypes = [C.POINTER(CProblem), C.c_int, C.c_int, C.c_double]
         L.or_sigma_group.restype = C.c_double
+        for f in ("or_mat_energy", "or_heat_capacity"):
+            getattr(L, f).argtypes = [C.POINTER(CProblem), C.c_int, C.c_double]
+            getattr(L, f).restype = C.c_double
         for n in ("or_planck_integral", "or_planck_dintegral"):
             getattr(L, n).argtypes = [C.c_double, C.c_double]
             getattr(L, n).restype = C.c_double
@@ -154,6 +159,12 @@ class OracleProblem:
         s.method = int(getattr(p, "method", 0))
         s.nu_edges, s.sigma0, s.cv = _d(self.nu_edges), _d(self.sigma0), _d(self.cv)
         s.src_T = _d(self.src_T) if self.src_T is not None else None
+        amp = getattr(p, "src_amp", None)
+        self.src_amp = None if amp is None else np.ascontiguousarray(amp, dtype=np.float64)
+        s.src_amp = _d(self.src_amp) if self.src_amp is not None else None
+        s.src_t_end = float(getattr(p, "src_t_end", 0.0))
+        s.cv_law = int(getattr(p, "cv_law", 0))
+        s.cv_chi = float(getattr(p, "cv_chi", 0.0))
         self.s = s
 
     @property
@@ -182,6 +193,14 @@ def draw(prob: OracleProblem, pid: int, step: int, j: int) -> float:
 
 def sigma(prob: OracleProblem, c: int, nu: float, T: float) -> float:
     return lib().or_sigma(prob.ref, c, nu, T)
+
+
+def mat_energy(prob: OracleProblem, c: int, T: float) -> float:
+    return lib().or_mat_energy(prob.ref, c, T)
+
+
+def heat_capacity(prob: OracleProblem, c: int, T: float) -> float:
+    return lib().or_heat_capacity(prob.ref, c, T)
 
 
 def sigma_group(prob: OracleProblem, c: int, g: int, T: float) -> float:

@@ -77,12 +77,59 @@ double or_draw(const or_problem* P, uint64_t id, int64_t step, int64_t j) {
  * factor (1 - e^{-nu/T}) of the Larsen case (Sec. 3.3: gamma0 (1 -
  * e^{-h nu/kT})/(h nu)^3, i.e. p = -3, q = 0).  Particles use sigma at their
  * own frequency and the cell temperature.                                   */
+/* sig_law 2: the carbon-hydrogen foam of the Olson case (Sec. 3.5),
+ * sigma = rho kappa with sigma0 = rho and kappa in three frequency bands
+ * (T and h nu in keV):
+ *   h nu <= 0.008: min(1e7, 1e9 T^2);
+ *   0.008 < h nu <= 0.3: 3e6 (0.008/h nu)^2 / (1 + 200 T^1.5);
+ *   h nu > 0.3: the same times (0.3/h nu)^0.5, plus 4e4 (0.3/h nu)^2.5 / (1 + 8000 T^2). */
+static double olson_kappa(double nu, double T) {
+  if (nu <= 0.008) return fmin(1e7, 1e9 * T * T);
+  const double a = 0.008 / nu;
+  const double b = 3e6 * a * a / (1.0 + 200.0 * pow(T, 1.5));
+  if (nu <= 0.3) return b;
+  const double r = 0.3 / nu;
+  return b * sqrt(r) + 4e4 * pow(r, 2.5) / (1.0 + 8000.0 * T * T);
+}
+
 double or_sigma(const or_problem* P, int c, double nu, double T) {
-  double s = P->sigma0[c] * pow(T, P->sig_q);
-  if (!P->grey) s *= pow(nu, P->sig_p);
-  if (!P->grey && P->sig_law == 1) s *= -expm1(-nu / T);
+  double s;
+  if (!P->grey && P->sig_law == 2) {
+    s = P->sigma0[c] * olson_kappa(nu, T);
+  } else {
+    s = P->sigma0[c] * pow(T, P->sig_q);
+    if (!P->grey) s *= pow(nu, P->sig_p);
+    if (!P->grey && P->sig_law == 1) s *= -expm1(-nu / T);
+  }
   if (P->sig_cap > 0.0 && !(s <= P->sig_cap)) s = P->sig_cap;
   return s;
+}
+
+/* Heat capacity and material energy per volume.  cv_law 0: e = cv T.
+ * cv_law 1, the Olson foam (Eq. cvolson): rho C_v = K [1 + alpha + (T + chi)
+ * alpha'], K = cv[c] (the a T_keV^3 H of the paper), with
+ *   alpha = (1/2) e^{-chi/T} (sqrt(1 + 4 e^{chi/T}) - 1)
+ *         = (1/2) (sqrt(u^2 + 4u) - u),  u = e^{-chi/T}   (no overflow as T -> 0),
+ *   alpha' = (chi/T^2) (alpha - 1/sqrt(1 + 4 e^{chi/T})),
+ * whose antiderivative vanishing at T = 0 is e(T) = K [T + (T + chi) alpha]
+ * ((T + chi) alpha has derivative alpha + (T + chi) alpha', and alpha -> 0). */
+static double olson_alpha(double chi, double T, double* dalpha) {
+  const double u = exp(-chi / T);
+  const double al = 0.5 * (sqrt(u * u + 4.0 * u) - u);
+  if (dalpha) *dalpha = chi / (T * T) * (al - sqrt(u / (u + 4.0)));
+  return al;
+}
+
+double or_mat_energy(const or_problem* P, int c, double T) {
+  if (P->cv_law != 1) return P->cv[c] * T;
+  return P->cv[c] * (T + (T + P->cv_chi) * olson_alpha(P->cv_chi, T, NULL));
+}
+
+double or_heat_capacity(const or_problem* P, int c, double T) {
+  if (P->cv_law != 1) return P->cv[c];
+  double da;
+  const double al = olson_alpha(P->cv_chi, T, &da);
+  return P->cv[c] * (1.0 + al + (T + P->cv_chi) * da);
 }
 
 /* Group opacity by Simpson's rule on nu_{g-1/2}, nu_mid, nu_{g+1/2}
@@ -690,7 +737,17 @@ int or_source_iteration(const or_problem* P, const double* T_n, const double* rh
     double errT = 0.0, errR = 0.0;
     for (int c = 0; c < ncell; ++c) {
       int ix = c % nx, iy = c / nx;
-      double num = P->cv[c] * T_n[c], den = P->cv[c];
+      /* e(T^{k+1}) ~ e(T^k) + C_v(T^k) (T^{k+1} - T^k) for a T-dependent heat
+       * capacity (the same fixed point); cv_law 0 is the constant case */
+      double num, den;
+      if (P->cv_law == 1) {
+        const double cvk = or_heat_capacity(P, c, Tk[c]);
+        num = or_mat_energy(P, c, T_n[c]) - or_mat_energy(P, c, Tk[c]) + cvk * Tk[c];
+        den = cvk;
+      } else {
+        num = P->cv[c] * T_n[c];
+        den = P->cv[c];
+      }
       double Q[256];
       double a[256];
       for (int g = 0; g < G; ++g) {
@@ -747,7 +804,9 @@ void or_init_rho(const or_problem* P, const double* T0, double* rho) {
  *   streaming with tallies, source iteration for Eq. macroSysFinal,
  *   removal of collided particles, then the wave/particle split
  *   I^h = I^{n+1} - I^p (Sec. 2.2).  The source of a patch cell adds
- *   c dt Phi_g(T_s) to rho_g each step (reading for the Olson-type source).  */
+ *   src_on amp c dt Phi_g(T_s) to rho_g each step while t^n < src_t_end
+ *   (reading for the Olson-type source, Q = B(T_s) e^{-693 x^3} for ct <= 2:
+ *   amp the profile at the cell centre).                                    */
 int or_step(const or_problem* P, int64_t step,
             const double* T, const double* rho, const double* rho_h,
             int64_t n_in, const or_particles* pin,
@@ -803,7 +862,7 @@ int or_step_core(const or_problem* P, int64_t step,
   tal->E_rad0 = tal->E_mat0 = 0.0;
   for (int c = 0; c < ncell; ++c) {
     for (int g = 0; g < G; ++g) tal->E_rad0 += V * rho[c * G + g] / P->c;
-    tal->E_mat0 += V * P->cv[c] * T[c];
+    tal->E_mat0 += V * or_mat_energy(P, c, T[c]);
   }
 
   /* steps 2: birth counts from the wave part at t^n */
@@ -926,8 +985,9 @@ int or_step_core(const or_problem* P, int64_t step,
         r += (dt / P->dy) * (tal->Fwave[fyl * G + g] - tal->Fwave[fyr * G + g]);
       }
       r += tal->W[c * G + g] / V;
-      if (P->src_T && P->src_T[c] > 0.0 && P->src_on != 0.0) {
-        double s = P->src_on * P->c * dt * or_phi(P, g, P->src_T[c]);
+      if (P->src_T && P->src_T[c] > 0.0 && P->src_on != 0.0 &&
+          (!(P->src_t_end > 0.0) || (double)step * dt < P->src_t_end)) {
+        double s = P->src_on * (P->src_amp ? P->src_amp[c] : 1.0) * P->c * dt * or_phi(P, g, P->src_T[c]);
         r += s;
         tal->src_in += V * s / P->c;
       }
@@ -968,7 +1028,7 @@ int or_step_core(const or_problem* P, int64_t step,
       rho_h_out[i] = r - rp;
       tal->E_rad1 += V * r / P->c;
     }
-    tal->E_mat1 += V * P->cv[c] * T_out[c];
+    tal->E_mat1 += V * or_mat_energy(P, c, T_out[c]);
   }
   if (any_scaled) {
     const int64_t m = nout < cap_out ? nout : cap_out;

@@ -50,6 +50,11 @@ typedef struct {
   const double* sigma0;           /* [ncell] */
   const double* cv;               /* [ncell] */
   const double* src_T;            /* [ncell] or NULL */
+  const double* src_amp;          /* [ncell] source profile factor, or NULL (1) */
+  double src_t_end;               /* the source acts while t^n = step dt < src_t_end (<= 0: always) */
+  int32_t cv_law;                 /* 0: constant cv; 1: Olson CH foam, cv (1 + alpha + (T + chi) alpha') */
+  int32_t _pad2;
+  double cv_chi;                  /* chi of cv_law 1 */
 } or_problem;
 
 /* Structure-of-arrays particle set.  In 1D, ox holds mu and y, oy are 0. */
@@ -93,6 +98,8 @@ double or_uniform(uint32_t wa, uint32_t wb);
 double or_draw(const or_problem* P, uint64_t id, int64_t step, int64_t j);
 double or_sigma(const or_problem* P, int c, double nu, double T);
 double or_sigma_group(const or_problem* P, int c, int g, double T);
+double or_mat_energy(const or_problem* P, int c, double T);   /* material energy per volume e(T) */
+double or_heat_capacity(const or_problem* P, int c, double T); /* de/dT */
 double or_planck_integral(double x1, double x2);      /* (15/pi^4) int_x1^x2 t^3/(e^t-1) dt */
 double or_planck_dintegral(double x1, double x2);     /* (15/pi^4) int_x1^x2 t^4 e^t/(e^t-1)^2 dt */
 double or_phi(const or_problem* P, int g, double T);  /* angle-integrated group equilibrium */

@@ -49,6 +49,10 @@ class Problem:
     bcT: List[float] = field(default_factory=lambda: [0.0] * 4)
     src_T: Optional[np.ndarray] = None   # [ncell] source temperature, 0 = none
     src_on: float = 0.0
+    src_amp: Optional[np.ndarray] = None  # [ncell] source profile factor (None: 1)
+    src_t_end: float = 0.0   # the source acts while t^n < src_t_end (<= 0: always)
+    cv_law: int = 0          # 0: constant cv; 1: Olson CH foam heat capacity (Eq. cvolson)
+    cv_chi: float = 0.0      # chi of cv_law 1
     tau_num_C: float = 0.0   # thin/thick joint sampling constant C of tau_num (0: off)
     sig_law: int = 0         # 0: sigma0 nu^p T^q; 1: times (1 - e^{-nu/T}) (Larsen case)
     method: int = 0          # 0: UGKWP (sample the collisionless part); 1: UGKP (sample all of I^h)
@@ -184,6 +188,29 @@ def larsen_slab(G: int = 24, omega_frac: float = 1e-4, steps: int = 1349) -> Pro
         bc=[BC_BLACKBODY, BC_VACUUM, BC_REFLECT, BC_REFLECT], bcT=[1.0, 0.0, 0.0, 0.0],
         omega_ref=omega_frac * dx * c, tau_num_C=1e3, n_steps=steps, name="larsen_%dx%d" % (nx, G),
         particle_capacity=1 << 22)
+
+
+def olson_slab(G: int = 30, omega_frac: float = 1e-4, steps: int = 107) -> Problem:
+    """The Olson 1D carbon-hydrogen foam (Sec. 3.5), normalised a = c = 1,
+    T and h nu in keV: [0, 4.8] cm in 128 cells (dx = 0.0375), sigma = rho
+    kappa(nu, T) with rho = 1e-3 g/cc (sig_law 2), heat capacity of Eq.
+    cvolson with a T_keV^3 H = 0.1 and chi = 0.1 (cv_law 1), T0 = 0.01,
+    reflecting walls, source B(0.5 keV) e^{-693 x^3} (cell centres) for
+    ct <= 2, dt = dx/c (107 steps reach ct = 4); G log groups on
+    [1e-3, 10] keV (covering both breaks of kappa); reference weight
+    1e-4 c V."""
+    n = 128
+    dx = 4.8 / n
+    xc = (np.arange(n) + 0.5) * dx
+    return Problem(
+        dim=1, nx=n, ny=1, dx=dx, dy=1.0, G=G, grey=0,
+        nu_edges=log_groups(G, 1e-3, 10.0), sigma0=np.full(n, 1e-3), cv=np.full(n, 0.1),
+        T0=np.full(n, 0.01), dt=dx, sig_p=0.0, sig_q=0.0, sig_cap=0.0, sig_law=2,
+        cv_law=1, cv_chi=0.1,
+        bc=[BC_REFLECT] * 4, bcT=[0.0] * 4,
+        src_T=np.full(n, 0.5), src_amp=np.exp(-693.0 * xc ** 3), src_on=1.0, src_t_end=2.0,
+        omega_ref=omega_frac * dx, n_steps=steps, name="olson_slab_128x%d" % G,
+        particle_capacity=1 << 21)
 
 
 def ensemble_slabs(n_instances: int = 256, seed: int = 0, steps: int = 100) -> List[Problem]:
