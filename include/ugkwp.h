@@ -71,7 +71,17 @@ enum { UGKWP_METHOD_UGKWP = 0, UGKWP_METHOD_UGKP = 1 };
  *   frequency dependence, Phi = a c T^4.
  *   Boundary sides: REFLECT (mirror), VACUUM (no inflow), BLACKBODY at bcT
  *   (1D only in this build).  src_T: a cell with src_T > 0 receives
- *   src_on * c * dt * Phi_g(src_T) in rho_g each step.
+ *   src_on * src_amp[c] * c * dt * Phi_g(src_T) in rho_g each step while
+ *   t^n = n dt < src_t_end (src_amp NULL: 1; src_t_end <= 0: always); the
+ *   Olson case (Sec. 3.5) has Q = B(0.5 keV) e^{-693 x^3} for ct <= 2.
+ *   sig_law = 2: the carbon-hydrogen foam of the Olson case, sigma = sigma0
+ *   kappa(nu, T) with kappa = min(1e7, 1e9 T^2) for nu <= 0.008,
+ *   3e6 (0.008/nu)^2/(1 + 200 T^1.5) for 0.008 < nu <= 0.3, and that times
+ *   (0.3/nu)^0.5 plus 4e4 (0.3/nu)^2.5/(1 + 8000 T^2) above (nu, T in keV;
+ *   sig_p and sig_q are not used).
+ *   cv_law = 1: the foam's heat capacity (Eq. cvolson), cv[c] (1 + alpha +
+ *   (T + chi) dalpha/dT) with alpha = (1/2) e^{-chi/T} (sqrt(1 + 4 e^{chi/T})
+ *   - 1), chi = cv_chi; the material energy is cv[c] (T + (T + chi) alpha).
  *   tau_num_C: the numerical collision time of the heterogeneous cases
  *   (Sec. 3.2), tau_num = tau + C J dt with J the largest temperature contrast
  *   |T_c - T_n|/(T_c + T_n) over a cell's interior faces, replaces tau in the
@@ -85,7 +95,7 @@ typedef struct ugkwp_problem {
   int32_t si_max_iters;   /* source-iteration cap */
   int32_t precision;      /* UGKWP_FP64 or UGKWP_MIXED (particle state in FP32) */
   int32_t bc[4];
-  int32_t sig_law;        /* 0: sigma0 nu^p T^q; 1: sigma0 nu^p T^q (1 - e^{-nu/T}) (Larsen case) */
+  int32_t sig_law;        /* 0: sigma0 nu^p T^q; 1: times (1 - e^{-nu/T}) (Larsen case); 2: Olson foam */
   double dx, dy;
   double sig_p, sig_q, sig_cap;
   double a, c, eps, dt;
@@ -104,6 +114,11 @@ typedef struct ugkwp_problem {
   const double* T0;            /* [ncell] initial material temperature */
   const double* rho0;          /* [ncell*G] initial rho_g, or NULL: Phi_g(T0) */
   const double* src_T;         /* [ncell] or NULL */
+  const double* src_amp;       /* [ncell] source profile factor, or NULL (1) */
+  double src_t_end;            /* source active while t^n < src_t_end (<= 0: always) */
+  int32_t cv_law;              /* 0: constant cv; 1: Olson foam heat capacity (Eq. cvolson) */
+  int32_t _pad2;
+  double cv_chi;               /* chi of cv_law 1 */
 } ugkwp_problem;
 
 typedef struct ugkwp_handle ugkwp_handle;

@@ -46,6 +46,8 @@ class CProblem(C.Structure):
         ("method", C.c_int32), ("particle_capacity", C.c_int64),
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("T0", _dp), ("rho0", _dp),
         ("src_T", _dp),
+        ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
+        ("cv_chi", C.c_double),
     ]
 
 
@@ -197,6 +199,10 @@ class _HostProblem:
         s.T0 = arr(p.T0, p.ncell)
         s.rho0 = arr(rho0, p.ncell * p.G)
         s.src_T = arr(p.src_T, p.ncell)
+        s.src_amp = arr(getattr(p, "src_amp", None), p.ncell)
+        s.src_t_end = float(getattr(p, "src_t_end", 0.0))
+        s.cv_law = int(getattr(p, "cv_law", 0))
+        s.cv_chi = float(getattr(p, "cv_chi", 0.0))
         self.s = s
         self._keep = keep
 

@@ -81,7 +81,10 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_ARG, "precision must be UGKWP_FP64 or UGKWP_MIXED");
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
   if (!(p->tau_num_C >= 0.0)) return fail(h, UGKWP_ERR_ARG, "tau_num_C must be >= 0");
-  if (p->sig_law != 0 && p->sig_law != 1) return fail(h, UGKWP_ERR_ARG, "sig_law must be 0 or 1");
+  if (p->sig_law < 0 || p->sig_law > 2) return fail(h, UGKWP_ERR_ARG, "sig_law must be 0, 1 or 2");
+  if (p->sig_law == 2 && p->grey) return fail(h, UGKWP_ERR_ARG, "sig_law 2 (Olson foam) needs groups (grey = 0)");
+  if (p->cv_law != 0 && p->cv_law != 1) return fail(h, UGKWP_ERR_ARG, "cv_law must be 0 or 1");
+  if (p->cv_law == 1 && !(p->cv_chi > 0.0)) return fail(h, UGKWP_ERR_ARG, "cv_law 1 needs cv_chi > 0");
   if (p->method != UGKWP_METHOD_UGKWP && p->method != UGKWP_METHOD_UGKP)
     return fail(h, UGKWP_ERR_ARG, "method must be 0 (UGKWP) or 1 (UGKP)");
   const long long nbins = (ncell_of(p) + 4) * p->G;
@@ -147,6 +150,9 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.ctrl = cv.take<Ctrl>(1);
   *src_T_tmp = d.R;   // scratch during init only
   const bool mixed = p->precision == UGKWP_MIXED;
+  d.olson_c = p->sig_law == 2 ? cv.take<double>(3 * nc) : nullptr;
+  d.olson_nu = p->sig_law == 2 ? cv.take<double>(9 * G) : nullptr;
+  d.olson_cf = (p->sig_law == 2 && mixed) ? cv.take<float>(3 * nc) : nullptr;
   d.sT_f = mixed ? cv.take<float>(nc) : nullptr;
   d.sTinv_f = mixed ? cv.take<float>(nc) : nullptr;
   d.invT_f = mixed ? cv.take<float>(nc) : nullptr;
@@ -196,7 +202,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.dy = p->dim == 2 ? p->dy : 1.0;
   d.vol = p->dim == 2 ? p->dx * p->dy : p->dx;
   d.sig_p = p->grey ? 0.0 : p->sig_p;
-  d.sig_q = p->sig_q;
+  d.sig_q = p->sig_law == 2 ? 0.0 : p->sig_q;   // the foam law has no T^q factor
   d.sig_cap = p->sig_cap;
   d.a = p->a;
   d.c = p->c;
@@ -214,6 +220,9 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.src_on = p->src_on;
   d.tau_num_C = p->tau_num_C;
   d.sig_law = p->sig_law;
+  d.cv_law = p->cv_law;
+  d.cv_chi = p->cv_chi;
+  d.src_t_end = p->src_t_end;
   d.method = p->method;
   d.key0 = (uint32_t)p->seed;
   d.key1 = (uint32_t)(p->seed >> 32) ^ p->instance;
@@ -308,8 +317,11 @@ cudaError_t init_member(const ugkwp_problem* p, char* base, Dev& d, cudaStream_t
   }
   if (p->src_T)
     if ((e = cudaMemcpyAsync(src_T_tmp, p->src_T, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return e;
+  double* src_amp_tmp = (p->src_T && p->src_amp) ? d.W : nullptr;   // scratch during init only
+  if (src_amp_tmp)
+    if ((e = cudaMemcpyAsync(src_amp_tmp, p->src_amp, sizeof(double) * nc, cudaMemcpyHostToDevice, s))) return e;
   *where = "init kernel";
-  if ((e = ugkwp::launch_init_tables(d, p->src_T ? src_T_tmp : nullptr, p->rho0 ? 0 : 1, s))) return e;
+  if ((e = ugkwp::launch_init_tables(d, p->src_T ? src_T_tmp : nullptr, src_amp_tmp, p->rho0 ? 0 : 1, s))) return e;
   // the source temperatures sat in R; wait before the next member's upload reuses host data
   *where = "init sync";
   return cudaStreamSynchronize(s);
@@ -406,7 +418,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   E.max_G = max_G;
   E.tile = h->shape.block * h->shape.ppt;
   h->d = h->members[0];
-  h->p.nu_edges = h->p.sigma0 = h->p.cv = h->p.T0 = h->p.rho0 = h->p.src_T = nullptr;
+  h->p.nu_edges = h->p.sigma0 = h->p.cv = h->p.T0 = h->p.rho0 = h->p.src_T = h->p.src_amp = nullptr;
   *out = h;
   return UGKWP_OK;
 }
@@ -795,6 +807,8 @@ int adjoint_check(ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates tau, not tau_num (tau_num_C = 0)");
   if (h->d.sig_law != 0)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the power-law opacity (sig_law = 0)");
+  if (h->d.cv_law != 0)
+    return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint takes a constant heat capacity (cv_law = 0)");
   if (h->d.method != UGKWP_METHOD_UGKWP)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the UGKWP sampling (method = 0)");
   return UGKWP_OK;

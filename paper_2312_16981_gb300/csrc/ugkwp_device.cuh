@@ -178,6 +178,8 @@ struct Dev {
   int dim, nx, ny, G, ncell, nbins, nface, nxface;
   int grey, wave_order, si_max_iters, precision, sig_law;
   int method;        // 0 UGKWP, 1 UGKP (all of I^h sampled; newborns draw t_f)
+  int cv_law;        // 0 constant cv; 1 Olson foam heat capacity
+  double cv_chi, src_t_end;
   int bc[4];
   double dx, dy, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
   double v;          // c/eps, particle speed
@@ -249,6 +251,9 @@ struct Dev {
   float* foy[2];
   float* fnu[2];
   float* fw[2];
+  double* olson_c;  // [3 ncell] foam opacity T factors A, B, C at T^n (sig_law 2)
+  double* olson_nu; // [9 G] foam opacity nu factors at each Simpson point (sig_law 2)
+  float* olson_cf;  // [3 ncell] A, B, C in FP32 (mixed precision)
   float* sT_f;      // [ncell] sigma0 T^q
   float* sTinv_f;   // [ncell] 1/(sigma0 T^q)
   float* invT_f;    // [ncell] 1/T^n (photo-ionisation factor of sig_law 1)
@@ -265,6 +270,30 @@ struct Dev {
   struct TapeRec* tape;
   long long tape_cap;
 };
+
+// Material energy per volume and heat capacity: cv[c] T and cv[c], or the
+// Olson foam (cv_law 1, Eq. cvolson): cv[c] (T + (T + chi) alpha) and cv[c]
+// (1 + alpha + (T + chi) alpha'), alpha = (sqrt(u^2 + 4u) - u)/2 with
+// u = e^{-chi/T} (the paper's form without its overflow at small T),
+// alpha' = (chi/T^2) (alpha - sqrt(u/(u + 4))).
+__device__ __forceinline__ double foam_alpha(double chi, double T, double* dalpha) {
+  const double u = exp(-chi / T);
+  const double al = 0.5 * (sqrt(fma(u, u, 4.0 * u)) - u);
+  if (dalpha) *dalpha = chi / (T * T) * (al - sqrt(u / (u + 4.0)));
+  return al;
+}
+
+__device__ __forceinline__ double mat_energy(const Dev& d, int c, double T) {
+  if (d.cv_law != 1) return d.cv[c] * T;
+  return d.cv[c] * (T + (T + d.cv_chi) * foam_alpha(d.cv_chi, T, nullptr));
+}
+
+__device__ __forceinline__ double heat_capacity(const Dev& d, int c, double T) {
+  if (d.cv_law != 1) return d.cv[c];
+  double da;
+  const double al = foam_alpha(d.cv_chi, T, &da);
+  return d.cv[c] * (1.0 + al + (T + d.cv_chi) * da);
+}
 
 // Bin -> cell and cell -> grid row, for indices the problem holds.
 __device__ __forceinline__ uint32_t div_bin(const Dev& d, uint32_t key) {
@@ -436,9 +465,48 @@ __device__ __forceinline__ double sigma_group(const Dev& d, double sT, int g) {
 // Group opacity at temperature T: with sig_law 1 each Simpson point carries
 // the photo-ionisation factor (1 - e^{-nu/T}) of the Larsen case (Sec. 3.3)
 // before the cap.
+// Olson foam opacity (sig_law 2, Sec. 3.5): kappa(nu, T) is A(T) for
+// nu <= 0.008, B(T) (0.008/nu)^2 for nu <= 0.3, and B(T) (0.008/nu)^2
+// (0.3/nu)^0.5 + C(T) (0.3/nu)^2.5 above, with A = min(1e7, 1e9 T^2),
+// B = 3e6/(1 + 200 T^1.5), C = 4e4/(1 + 8000 T^2); sigma = sigma0 kappa.
+struct FoamT {
+  double A, B, C;
+};
+
+__device__ __forceinline__ FoamT foam_T(double T) {
+  FoamT f;
+  f.A = fmin(1e7, 1e9 * T * T);
+  f.B = 3e6 / (1.0 + 200.0 * T * sqrt(T));
+  f.C = 4e4 / (1.0 + 8000.0 * T * T);
+  return f;
+}
+
+// nu factors (0.008/nu)^2, (0.008/nu)^2 (0.3/nu)^0.5, (0.3/nu)^2.5
+__device__ __forceinline__ void foam_nu(double nu, double* f1, double* f2, double* f3) {
+  const double inv = 1.0 / nu, a = 0.008 * inv, r = 0.3 * inv, sq = sqrt(r);
+  *f1 = a * a;
+  *f2 = a * a * sq;
+  *f3 = r * r * sq;
+}
+
+__device__ __forceinline__ double foam_kappa(double nu, double A, double B, double C, double f1, double f2,
+                                             double f3) {
+  if (nu <= 0.008) return A;
+  if (nu <= 0.3) return B * f1;
+  return B * f2 + C * f3;
+}
+
 __device__ __forceinline__ double sigma_group_at(const Dev& d, double sT, double T, double invT, int g) {
-  if (d.sig_law == 0 || d.grey) return sigma_group(d, sT, g);
+  if (d.grey || d.sig_law == 0) return sigma_group(d, sT, g);
   const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b);
+  if (d.sig_law == 2) {
+    const FoamT f = foam_T(T);
+    const double* t = d.olson_nu + 9 * g;
+    const double sa = cap_sigma(d, sT * foam_kappa(a, f.A, f.B, f.C, __ldg(t), __ldg(t + 1), __ldg(t + 2)));
+    const double sm = cap_sigma(d, sT * foam_kappa(m, f.A, f.B, f.C, __ldg(t + 3), __ldg(t + 4), __ldg(t + 5)));
+    const double sb = cap_sigma(d, sT * foam_kappa(b, f.A, f.B, f.C, __ldg(t + 6), __ldg(t + 7), __ldg(t + 8)));
+    return (sa + 4.0 * sm + sb) * (1.0 / 6.0);
+  }
   const double sa = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g) * -expm1(-a * invT));
   const double sm = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 1) * -expm1(-m * invT));
   const double sb = cap_sigma(d, sT * __ldg(d.nu_pow + 3 * g + 2) * -expm1(-b * invT));
@@ -453,12 +521,28 @@ __device__ __forceinline__ double sigma_group_at(const Dev& d, double sT, double
 // from the per-cell 1/(sigma0 T^q) and 1/nu^p (inup); multiplications except
 // for the photo-ionisation factor.
 __device__ __forceinline__ double inv_sigma_particle(const Dev& d, int cell, double nu, double inup) {
+  if (d.sig_law == 2 && !d.grey) {
+    double f1, f2, f3;
+    foam_nu(nu, &f1, &f2, &f3);
+    const double* c = d.olson_c + 3 * cell;
+    const double k = foam_kappa(nu, c[0], c[1], c[2], f1, f2, f3);
+    return fmax(d.sTinv[cell] / k, d.inv_cap);
+  }
   double si = d.sTinv[cell] * inup;
   if (d.sig_law == 1 && !d.grey) si /= -expm1(-nu / d.T[cell]);
   return fmax(si, d.inv_cap);
 }
 
 __device__ __forceinline__ float inv_sigma_particle_f(const Dev& d, int cell, float nu, float inup) {
+  if (d.sig_law == 2 && !d.grey) {
+    const float inv = __frcp_rn(nu), a = 0.008f * inv, r = 0.3f * inv, sq = sqrtf(r);
+    const float* c = d.olson_cf + 3 * cell;
+    float k;
+    if (nu <= 0.008f) k = __ldg(c);
+    else if (nu <= 0.3f) k = __ldg(c + 1) * (a * a);
+    else k = __ldg(c + 1) * (a * a * sq) + __ldg(c + 2) * (r * r * sq);
+    return fmaxf(__fdividef(__ldg(d.sTinv_f + cell), k), d.inv_capf);
+  }
   float si = __ldg(d.sTinv_f + cell) * inup;
   if (d.sig_law == 1 && !d.grey) si /= -expm1f(-nu * __ldg(d.invT_f + cell));
   return fmaxf(si, d.inv_capf);

@@ -5,7 +5,8 @@
 
 namespace ugkwp {
 
-cudaError_t launch_init_tables(const Dev& d, const double* src_T, int init_rho, cudaStream_t s);
+cudaError_t launch_init_tables(const Dev& d, const double* src_T, const double* src_amp, int init_rho,
+                               cudaStream_t s);
 cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s);
 int scan_parts(long long n);
 cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t* off,

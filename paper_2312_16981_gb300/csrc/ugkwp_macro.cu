@@ -34,9 +34,16 @@ __global__ void k_init_pow(Dev d) {
   }
   for (int g = tid; g <= d.G; g += stride)
     if (d.nu_edges_f) d.nu_edges_f[g] = (float)d.nu_edges[g];
+  // foam opacity nu factors at the Simpson points (sig_law 2)
+  if (d.olson_nu)
+    for (int g = tid; g < d.G; g += stride) {
+      const double a = d.nu_edges[g], b = d.nu_edges[g + 1], pts[3] = {a, 0.5 * (a + b), b};
+      for (int k = 0; k < 3; ++k)
+        foam_nu(pts[k], d.olson_nu + 9 * g + 3 * k, d.olson_nu + 9 * g + 3 * k + 1, d.olson_nu + 9 * g + 3 * k + 2);
+    }
 }
 
-__global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
+__global__ void k_init_tables(Dev d, const double* src_T, const double* src_amp, int init_rho) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const int n = d.ncell * d.G;
   for (int i = tid; i < n; i += stride) {
@@ -51,7 +58,7 @@ __global__ void k_init_tables(Dev d, const double* src_T, int init_rho) {
     if (d.src) {
       double p = 0.0;
       if (src_T && src_T[c] > 0.0) phi_dphi_cell(d, src_T[c], g, &p, nullptr);
-      const_cast<double*>(d.src)[i] = d.src_on * d.c * d.dt * p;
+      const_cast<double*>(d.src)[i] = d.src_on * (src_amp ? src_amp[c] : 1.0) * d.c * d.dt * p;
     }
   }
   for (int i = tid; i < 4 * d.G; i += stride) {
@@ -112,6 +119,14 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
           d.sT_f[cell] = (float)sT;
           d.sTinv_f[cell] = (float)(1.0 / sT);
           d.invT_f[cell] = (float)(1.0 / Tb);
+        }
+        if (d.olson_c) {   // foam opacity T factors at T^n for the particles
+          const FoamT f = foam_T(Tb);
+          d.olson_c[3 * cell] = f.A; d.olson_c[3 * cell + 1] = f.B; d.olson_c[3 * cell + 2] = f.C;
+          if (d.olson_cf) {
+            d.olson_cf[3 * cell] = (float)f.A; d.olson_cf[3 * cell + 1] = (float)f.B;
+            d.olson_cf[3 * cell + 2] = (float)f.C;
+          }
         }
       }
       sig = sigma_group_at(d, sT, Tb, g);
@@ -581,6 +596,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int ix = c % d.nx, iy = c / d.nx;
       const int fxl = iy * (d.nx + 1) + ix, fxr = fxl + 1;
       const int fyl = d.nxface + iy * d.nx + ix, fyr = fyl + d.nx;
+      // the source acts while t^n = n dt < src_t_end (src_t_end <= 0: always)
+      const bool src_on = d.src && (!(d.src_t_end > 0.0) || (double)d.ctrl->step * dt < d.src_t_end);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
@@ -592,13 +609,13 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
           d.W[i] = Wd;
           r += Wd * d.inv_vol;
-          if (d.src) { r += d.src[i]; e_src += V * d.src[i] * d.inv_c; }
+          if (src_on) { r += d.src[i]; e_src += V * d.src[i] * d.inv_c; }
           d.R[i] = r;
           e_rad0 += V * r0 * d.inv_c;
         }
       }
       const double T = d.T[c];
-      if (lane == 0) e_mat0 += V * d.cv[c] * T;
+      if (lane == 0) e_mat0 += V * mat_energy(d, c, T);
       double sg[NC], ph[NC], dp[NC];
       cell_planck<NC>(d, c, T, sg, ph, dp);
 #pragma unroll
@@ -702,7 +719,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       num = warp_sum(num);
       den = warp_sum(den);
-      double Tnew = (cv * Tn + num) / (cv + den);
+      // a T-dependent heat capacity: e(T^{k+1}) ~ e(T^k) + C_v(T^k) (T^{k+1} - T^k)
+      double Tnew;
+      if (d.cv_law == 1) {
+        const double ck = heat_capacity(d, c, Tc);
+        Tnew = (mat_energy(d, c, Tn) - mat_energy(d, c, Tc) + ck * Tc + num) / (ck + den);
+      } else {
+        Tnew = (cv * Tn + num) / (cv + den);
+      }
       if (!(Tnew > 1e-30)) Tnew = (Tnew == Tnew) ? 1e-30 : Tnew;
       double dmax = 0.0, rsum = 0.0;
 #pragma unroll
@@ -821,7 +845,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       if (!(T == T) || T > 1e300) bad = 1;
       if (lane == 0) {
         d.T[c] = T;
-        e_mat1 += V * d.cv[c] * T;
+        e_mat1 += V * mat_energy(d, c, T);
       }
       const int ix = c % d.nx, iy = c / d.nx;
 #pragma unroll
@@ -1100,9 +1124,9 @@ static int grid_for(long long n, int threads, int cap = 152 * 16) {
   return (int)b;
 }
 
-cudaError_t launch_init_tables(const Dev& d, const double* src_T, int init_rho, cudaStream_t s) {
+cudaError_t launch_init_tables(const Dev& d, const double* src_T, const double* src_amp, int init_rho, cudaStream_t s) {
   k_init_pow<<<1, 64, 0, s>>>(d);
-  k_init_tables<<<grid_for((long long)d.ncell * d.G, 256), 256, 0, s>>>(d, src_T, init_rho);
+  k_init_tables<<<grid_for((long long)d.ncell * d.G, 256), 256, 0, s>>>(d, src_T, src_amp, init_rho);
   return cudaGetLastError();
 }
 
