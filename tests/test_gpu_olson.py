@@ -42,15 +42,14 @@ def test_olson_step_parity_warm(B):
     # a warm foam: the middle and upper opacity bands and the heat capacity's
     # alpha terms all matter, and more particles are sampled
     p = foam(T0=np.linspace(0.5, 0.05, 128))
-    t, tal = check_step(B, p, 1)
-    assert t["n_born"] > 1000
+    t, tal = check_step(B, p, 0)
+    assert t["n_born"] > 10000
 
 
 def test_olson_mixed_precision(B):
     p = foam(T0=np.linspace(0.5, 0.05, 128))
     op = O.OracleProblem(p)
     st = O.initial_state(op)
-    st, _, _, _ = O.step(op, st)
     M.check(p, *M.run_pair(B, p, st, op))
 
 
