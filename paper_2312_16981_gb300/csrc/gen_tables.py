@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Write the CUDA path's coefficient tables: ugkwp_planck_table.h
 (piecewise polynomial interpolants of the Planck edge functions used by the
-group fractions b_g(T)) and ugkwp_c2_table.h (the same for the equilibrium
-flux coefficient C2 of the source-iteration faces).
+group fractions b_g(T)), ugkwp_c2_table.h (the same for the equilibrium
+flux coefficient C2 of the source-iteration faces) and ugkwp_log_table.h
+(the breakpoints of the FP64 particle kernel's logarithm).
 
 The group fraction (15/pi^4) int_{x_lo}^{x_hi} t^3/(e^t - 1) dt and its
 T-derivative need, per group edge x = nu/T, the lower or upper partial
@@ -35,6 +36,13 @@ f2(x) = 2 (1 - e^{-x})/x - 1 - e^{-x} (Eq. C2Formula divided by tau), on the
 same intervals: rows 0..3 hold f2(x)/x^2 (-> -1/6 at x = 0; the device
 multiplies by x), rows 4..79 g2 itself, and row 80 (x >= 40) g2 = (2/x - 1)/x
 in powers of s = 1/x (the e^{-x} terms are below e^{-40} of it).
+
+The log table serves a table-driven ln(1 + x) for x in [-1/2, 0.42]
+(the method of P. T. P. Tang, "Table-driven implementation of the logarithm
+function in IEEE floating-point arithmetic", ACM TOMS 16 (1990)): breakpoints
+c_j = 1 + j/128, j = -64..54, with 1/c_j and ln c_j rounded to double from 60
+digits; on the device ln(1 + x) = ln c_j + ln(1 + r), r = (x - j/128)/c_j,
+|r| <= 1/128, by a degree-7 series.
 
 Usage: python gen_tables.py [directory]   (default: this file's directory).
 The committed headers are this script's output.
@@ -263,7 +271,33 @@ def write_c2(path):
     return worst
 
 
+LOG_JMIN, LOG_JMAX = -64, 54
+
+
+def write_log(path):
+    lines = [
+        "// ugkwp_log_table.h -- written by gen_tables.py (do not edit).",
+        "// Breakpoints c_j = 1 + j/128, j = %d..%d, of the table-driven ln(1 + x):" % (LOG_JMIN, LOG_JMAX),
+        "// pairs (1/c_j, ln c_j) rounded to double from 60-digit values.",
+        "#pragma once",
+        "",
+        "namespace ugkwp {",
+        "",
+        "constexpr int kLogJMin = %d, kLogJMax = %d;" % (LOG_JMIN, LOG_JMAX),
+        "",
+        "static __device__ __align__(16) const double kLogTab[%d] = {" % (2 * (LOG_JMAX - LOG_JMIN + 1)),
+    ]
+    for j in range(LOG_JMIN, LOG_JMAX + 1):
+        c = 1 + Decimal(j) / 128
+        lines.append("    %s, %s,  // j = %d" % (float(1 / c).hex(), float(c.ln()).hex(), j))
+    lines += ["};", "", "}  // namespace ugkwp", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+
+
 if __name__ == "__main__":
     out = sys.argv[1] if len(sys.argv) > 1 else os.path.dirname(os.path.abspath(__file__))
     print("Planck table: worst relative error %.3e" % write(os.path.join(out, "ugkwp_planck_table.h")))
     print("C2 table:     worst relative error %.3e" % write_c2(os.path.join(out, "ugkwp_c2_table.h")))
+    write_log(os.path.join(out, "ugkwp_log_table.h"))
+    print("log table written")

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "ugkwp_c2_table.h"
+#include "ugkwp_log_table.h"
 #include "ugkwp_planck_table.h"
 
 namespace ugkwp {
@@ -68,6 +69,42 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 __device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
   const unsigned long long m = ((unsigned long long)a << 20) | (unsigned long long)(b >> 12);
   return __ll2double_rn((long long)m) * 0x1p-52 + 0x1p-53;
+}
+
+// -ln u for u in (0, 1) in FP64 without the library logarithm (the FP64
+// particle kernel is bound by its FP64 instructions, and a library log costs
+// about thirty FMAs there): ln(1 + x) by the table-driven method of Tang
+// (ACM TOMS 16, 1990) on one argument per lane -- x = u - 1 (exact) for
+// u > 1/2, else u = 2^k m with m in [1/sqrt 2, sqrt 2] and x = m - 1 (exact)
+// -- with breakpoints c_j = 1 + j/128 from ugkwp_log_table.h, r = (x -
+// j/128)/c_j, |r| <= 1/128, ln(1 + r) by its series to r^7, and k ln 2 in two
+// parts.  Within about an ulp of -ln u.
+constexpr double kLn2Hi = 0x1.62e42fefa3800p-1, kLn2Lo = 0x1.ef35793c76730p-45;
+
+__device__ __forceinline__ double neg_log_u64(double u) {
+  double x, kd;
+  if (u > 0.5) {
+    x = u - 1.0;
+    kd = 0.0;
+  } else {
+    const long long b = __double_as_longlong(u);
+    int k = (int)((b >> 52) & 0x7ff) - 1023;
+    long long mb = (b & 0x000fffffffffffffll) | 0x3ff0000000000000ll;   // m in [1, 2)
+    if (mb > 0x3ff6a09e667f3bcdll) { mb -= 0x0010000000000000ll; ++k; }  // m > sqrt 2: halve
+    x = __longlong_as_double(mb) - 1.0;
+    kd = (double)k;
+  }
+  const double jd = rint(x * 128.0);
+  const double2 t = __ldg(reinterpret_cast<const double2*>(kLogTab) + ((int)jd - kLogJMin));
+  const double r = (x - jd * (1.0 / 128.0)) * t.x;
+  double p = 1.0 / 7.0;
+  p = fma(p, r, -1.0 / 6.0);
+  p = fma(p, r, 1.0 / 5.0);
+  p = fma(p, r, -0.25);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  const double l1p = fma(r * r, p, r);
+  return -fma(kd, kLn2Hi, t.y + fma(kd, kLn2Lo, l1p));
 }
 
 // The draw sequence of one particle in one step: draw j comes from Philox

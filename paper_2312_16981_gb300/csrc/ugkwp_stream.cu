@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       } else {
         const double u = rng.next(d.pk);
         const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
-        const double tc = -log(u) * inv_rate * sig_inv;
+        const double tc = neg_log_u64(u) * inv_rate * sig_inv;
         collided = tc < dt;
         t_rem = collided ? tc : dt;
       }
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           cell = cy * nx + cx;
           const double u = rng.next(d.pk);
           const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
-          const double tc = -log(u) * inv_rate * sig_inv;
+          const double tc = neg_log_u64(u) * inv_rate * sig_inv;
           const double avail = dt - t_tra;
           collided = tc < avail;
           t_rem = collided ? tc : avail;

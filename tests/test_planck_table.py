@@ -2,9 +2,10 @@
 headers are exactly what their generator writes, and the device's evaluation
 of them (one Horner pass, emulated here in float64 with the same operation
 order) gives the Planck group fractions b_g(T) and their T-derivative
-(Sec. 2.1) to the accuracy of the oracle's quadrature, and the equilibrium
-flux coefficient C2 (Eq. C2Formula) to that of the oracle's series and closed
-forms."""
+(Sec. 2.1) to the accuracy of the oracle's quadrature, the equilibrium flux
+coefficient C2 (Eq. C2Formula) to that of the oracle's series and closed
+forms, and the FP64 particle kernel's -ln u of a free-time draw (Eq.
+particle-tf-formula) to about an ulp of the library logarithm."""
 import math
 import os
 import re
@@ -20,6 +21,7 @@ from paper_2312_16981_gb300 import inputs as I
 CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2312_16981_gb300", "csrc")
 HEADER = os.path.join(CSRC, "ugkwp_planck_table.h")
 C2HEADER = os.path.join(CSRC, "ugkwp_c2_table.h")
+LOGHEADER = os.path.join(CSRC, "ugkwp_log_table.h")
 
 
 def table():
@@ -92,6 +94,61 @@ def test_headers_are_generator_output(tmp_path):
                    capture_output=True)
     assert (tmp_path / "ugkwp_planck_table.h").read_text() == open(HEADER).read()
     assert (tmp_path / "ugkwp_c2_table.h").read_text() == open(C2HEADER).read()
+    assert (tmp_path / "ugkwp_log_table.h").read_text() == open(LOGHEADER).read()
+
+
+def _log_table():
+    txt = open(LOGHEADER).read()
+    body = txt[txt.index("kLogTab["):]
+    vals = [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-f.]+p[-+]?\d+", body)]
+    jmin = int(re.search(r"kLogJMin = (-?\d+)", txt).group(1))
+    return np.array(vals).reshape(-1, 2), jmin
+
+
+LOGTAB, LOGJMIN = _log_table()
+LN2_HI, LN2_LO = float.fromhex("0x1.62e42fefa3800p-1"), float.fromhex("0x1.ef35793c76730p-45")
+
+
+def neg_log(u):
+    """-ln u as the FP64 particle kernel computes it (same operations)."""
+    if u > 0.5:
+        x, kd = u - 1.0, 0.0
+    else:
+        b = int(np.float64(u).view(np.int64))
+        k = ((b >> 52) & 0x7FF) - 1023
+        mb = (b & 0x000FFFFFFFFFFFFF) | 0x3FF0000000000000
+        if mb > 0x3FF6A09E667F3BCD:
+            mb -= 0x0010000000000000
+            k += 1
+        x = float(np.int64(mb).view(np.float64)) - 1.0
+        kd = float(k)
+    jd = float(np.rint(x * 128.0))
+    ic, lc = LOGTAB[int(jd) - LOGJMIN]
+    r = (x - jd * (1.0 / 128.0)) * ic
+    p = 1.0 / 7.0
+    for c in (-1.0 / 6.0, 1.0 / 5.0, -0.25, 1.0 / 3.0, -0.5):
+        p = math.fma(p, r, c) if hasattr(math, "fma") else p * r + c
+    l1p = (r * r) * p + r
+    return -(kd * LN2_HI + (lc + (kd * LN2_LO + l1p)))
+
+
+def test_log_table_entries():
+    for j in range(LOGJMIN, LOGJMIN + len(LOGTAB)):
+        c = 1.0 + j / 128.0
+        ic, lc = LOGTAB[j - LOGJMIN]
+        assert abs(ic * c - 1.0) <= 2.3e-16
+        assert abs(lc - math.log(c)) <= 1.2e-16 * max(abs(lc), 1e-300) + 1e-300
+
+
+def test_neg_log_within_an_ulp_or_two():
+    rng = np.random.default_rng(7)
+    # draws as the kernel forms them: (m + 1/2) 2^-52, never 0 or 1
+    m = rng.integers(0, 1 << 52, size=20000, dtype=np.int64)
+    us = list((m.astype(np.float64) + 0.5) * 2.0 ** -52)
+    us += [2.0 ** -53, (2 ** 52 - 0.5) * 2.0 ** -52, 0.5, 0.5 + 2 ** -53, 0.25, 2 ** -0.5, 0.75, 1e-300 ** 0 * 0.9999]
+    for u in us:
+        want = -math.log(u)
+        assert abs(neg_log(u) - want) <= 4.5e-16 * want, (u, neg_log(u), want)
 
 
 def test_c2_table_matches_oracle_coefficients():
