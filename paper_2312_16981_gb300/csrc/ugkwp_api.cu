@@ -144,6 +144,7 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.Tk[1] = cv.take<double>(nc);
   d.tauk[0] = cv.take<double>(ncg);
   d.tauk[1] = cv.take<double>(ncg);
+  d.qk = cv.take<double>(ncg);
   d.phik[0] = cv.take<double>(ncg);
   d.phik[1] = cv.take<double>(ncg);
   d.dphik = cv.take<double>(ncg);

@@ -270,6 +270,7 @@ struct Dev {
   double* wscale;   // [ncell*G] end-of-step scaling of the survivors' weights (1: none)
   double* Tk[2];    // [ncell] iterates
   double* tauk[2];  // [ncell*G] relaxation time 1/(rate_f sigma_g(T^k)) of the iterate
+  double* qk;       // [ncell*G] 1/(tau + dt) of the iterate (read by the cell's own warp)
   double* phik[2];  // [ncell*G]
   double* dphik;    // [ncell*G]
   // particles: two structure-of-arrays buffers, selected by ctrl->cur

@@ -59,9 +59,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // between neighbouring lanes by shuffles.
 template <int NC>
 __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
-                                            double* dphi, double invT) {
+                                            double* dphi, double invT, double sT) {
   const int lane = threadIdx.x & 31, G = d.G;
-  const double sT = sigma_T(d, c, T);
   const double ac = d.a * d.c, T3 = T * T * T;
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
@@ -98,8 +97,23 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
 
 template <int NC>
 __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
+                                            double* dphi, double invT) {
+  cell_planck<NC>(d, c, T, sig, phi, dphi, invT, sigma_T(d, c, T));
+}
+
+template <int NC>
+__device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, double* sig, double* phi,
                                             double* dphi) {
   cell_planck<NC>(d, c, T, sig, phi, dphi, 1.0 / T);
+}
+
+// tau = 1/(rate sigma) and q = 1/(tau + dt) of the source iteration with one
+// division: A = rate sigma, D = 1 + dt A, P = 1/(A D), tau = D P, q = A^2 P.
+__device__ __forceinline__ void tau_and_q(const Dev& d, double sig, double* tau, double* q) {
+  const double A = d.rate_f * sig, D = fma(d.dt, A, 1.0);
+  const double P = 1.0 / (A * D);
+  *tau = D * P;
+  *q = A * A * P;
 }
 
 __device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {

@@ -622,7 +622,10 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
         if (g < G) {
-          __stcg(d.tauk[0] + c * G + g, 1.0 / (d.rate_f * sg[j]));
+          double tau, qv;
+          tau_and_q(d, sg[j], &tau, &qv);
+          __stcg(d.tauk[0] + c * G + g, tau);
+          __stcg(d.qk + c * G + g, qv);
           __stcg(d.phik[0] + c * G + g, ph[j]);
           __stcg(d.dphik + c * G + g, dp[j]);
         }
@@ -710,7 +713,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           q += (dt * inv_h) * (Fin - Fout);
         }
         Q[j] = q;
-        const double qi = 1.0 / (tc + dt);
+        const double qi = __ldcg(d.qk + i);   // 1/(tau + dt), stored with tau
         r1[j] = tc * qi;
         ar[j] = dt * qi;
         const double ap = ar[j] * d.inv_c;
@@ -742,7 +745,17 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       dmax = warp_max(dmax);
       rsum = warp_sum(rsum);
       const double eR = rsum > 0.0 ? dmax / rsum : 0.0;
-      const double invTn = 1.0 / Tnew;
+      // 1/T^{k+1} (and sigma0 T^q for q = -1/2) from one rsqrt where the
+      // opacity law has T^{-1/2}, else a division
+      double invTn, sTn;
+      if (d.sig_q == -0.5) {
+        const double rs = rsqrt(Tnew);
+        invTn = rs * rs;
+        sTn = d.sigma0[c] * rs;
+      } else {
+        invTn = 1.0 / Tnew;
+        sTn = sigma_T(d, c, Tnew);
+      }
       const double eT = fabs(Tnew - Tc) * invTn;
       if (ENS) {
         // members differ between warps: each warp reports to its own member
@@ -756,12 +769,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       if (lane == 0) __stcg(d.Tk[nxt] + c, Tnew);
       double sg[NC], ph[NC], dp[NC];
-      cell_planck<NC>(d, c, Tnew, sg, ph, dp, invTn);
+      cell_planck<NC>(d, c, Tnew, sg, ph, dp, invTn, sTn);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
         if (g < G) {
-          __stcg(d.tauk[nxt] + c * G + g, 1.0 / (d.rate_f * sg[j]));
+          double tau, qv;
+          tau_and_q(d, sg[j], &tau, &qv);
+          __stcg(d.tauk[nxt] + c * G + g, tau);
+          __stcg(d.qk + c * G + g, qv);
           __stcg(d.phik[nxt] + c * G + g, ph[j]);
           __stcg(d.dphik + c * G + g, dp[j]);
         }
