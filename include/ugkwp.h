@@ -241,6 +241,16 @@ int ugkwp_restore(ugkwp_handle* h, const void* d_buf, size_t bytes, void* stream
  * block: 128, 256 or 512 threads; particles_per_thread: 1 or 2 (sub-tiles
  * per tile); blocks_per_sm: 0 for as many as fit. */
 int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int blocks_per_sm);
+/* ---- bounded waits ----
+ * The source iteration's grid barrier polls at most `spins` times (0: the
+ * default 2^25) before it gives up, sets UGKWP_ST_TIMEOUT and returns, so a
+ * lost arrival never hangs the device.  extra_arrivals > 0 is a failure
+ * injection for tests: every barrier then also waits for that many arrivals
+ * that never come, so each wait runs out and the step reports the timeout
+ * (the state it leaves is not meaningful; the context stays usable).
+ * Enqueued on `stream`; takes effect from the next step.  No counterpart in
+ * the paper. */
+int ugkwp_set_wait_limit(ugkwp_handle* h, uint32_t spins, uint32_t extra_arrivals, void* stream);
 /* Time every launch shape on `steps` identical steps (the state is saved in
  * d_ckpt, a buffer of ugkwp_checkpoint_size bytes, and restored before each
  * candidate and at the end), keep the fastest particle phase, and report it

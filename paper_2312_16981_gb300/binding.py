@@ -102,6 +102,7 @@ FUNCTIONS = {
     "ugkwp_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ugkwp_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ugkwp_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "ugkwp_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p]),
     "ugkwp_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p,
                                  C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ugkwp_tape_size": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_size_t)]),
@@ -401,6 +402,13 @@ class Simulation:
 
     def set_launch(self, block: int, particles_per_thread: int = 1, blocks_per_sm: int = 0):
         _check(load().ugkwp_set_launch(self.h, block, particles_per_thread, blocks_per_sm), self.h)
+
+    def set_wait_limit(self, spins: int = 0, extra_arrivals: int = 0):
+        """Bound the source iteration's barrier waits to `spins` polls (0: the
+        default); extra_arrivals > 0 makes every wait run out (failure
+        injection for tests)."""
+        _check(load().ugkwp_set_wait_limit(self.h, int(spins), int(extra_arrivals),
+                                           C.c_void_p(_stream_ptr(self.stream))), self.h)
 
     def autotune(self, steps: int = 2, cache: Optional[str] = None):
         """Pick the particle kernel's launch shape by timing each candidate on

@@ -711,6 +711,19 @@ int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int b
   return UGKWP_OK;
 }
 
+int ugkwp_set_wait_limit(ugkwp_handle* h, uint32_t spins, uint32_t extra_arrivals, void* stream) {
+  if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned int v[2] = {spins, extra_arrivals};
+  for (int m = 0; m < h->M; ++m) {
+    Ctrl* c = h->members[m].ctrl;
+    CK(cudaMemcpyAsync(&c->bar_timeout_spins, &v[0], sizeof(unsigned int), cudaMemcpyHostToDevice, s), h);
+    CK(cudaMemcpyAsync(&c->bar_extra, &v[1], sizeof(unsigned int), cudaMemcpyHostToDevice, s), h);
+  }
+  CK(cudaStreamSynchronize(s), h);   // the host values live on this frame
+  return UGKWP_OK;
+}
+
 int ugkwp_checkpoint_size(const ugkwp_handle* h, size_t* bytes) {
   if (!h || !bytes) return fail(nullptr, UGKWP_ERR_ARG, "NULL argument");
   size_t tot = align256(sizeof(size_t) * (size_t)h->M);

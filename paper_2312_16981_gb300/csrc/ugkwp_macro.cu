@@ -444,6 +444,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
     __threadfence();
     atomicAdd(count, 1u);
     const unsigned int limit = limit_in ? limit_in : (1u << 25);
+    target += status_ctrl->bar_extra;   // failure injection: arrivals that never come
     unsigned int spins = 0;
     int to = 0;
     while (true) {
