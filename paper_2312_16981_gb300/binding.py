@@ -270,6 +270,25 @@ class Simulation:
         out["ptr"] = {k: getattr(r, k) for k, _ in CTallyReport._fields_[:9]}
         return out
 
+    def log_tallies(self, out, member: int = 0, **extra) -> Dict:
+        """Append this step's report (counters, iterations, status bits and the
+        energy ledger, with its residual) to `out` -- a path or an open text
+        file -- as one JSON line; returns the record."""
+        import json
+        t = self.tallies(member=member)
+        rec = {k: v for k, v in t.items() if k != "ptr"}
+        rec["ledger_residual"] = ((t["E_rad1"] + t["E_mat1"]) - (t["E_rad0"] + t["E_mat0"])
+                                  - (t["bnd_in_macro"] + t["bnd_in_part"] - t["bnd_out_part"] + t["src_in"]))
+        rec["member"] = member
+        rec.update(extra)
+        line = json.dumps(rec) + "\n"
+        if hasattr(out, "write"):
+            out.write(line)
+        else:
+            with open(out, "a") as f:
+                f.write(line)
+        return rec
+
     def device_array(self, name: str):
         """A torch view (float64, on the device) of a tally array."""
         import torch

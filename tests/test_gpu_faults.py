@@ -73,3 +73,17 @@ def test_non_finite_state_is_reported(B):
         return                     # refused at set-up: also a reported failure
     sim.step(1)
     assert sim.tallies()["status_bits"] & B.ST_NONFINITE
+
+
+def test_tally_log_is_json_lines(B, tmp_path):
+    import json
+    path = tmp_path / "steps.jsonl"
+    sim = B.Simulation(small())
+    for k in range(3):
+        sim.step(1)
+        sim.log_tallies(str(path), run="log-test")
+    rows = [json.loads(line) for line in path.read_text().splitlines()]
+    assert [r["step"] for r in rows] == [1, 2, 3]
+    for r in rows:
+        assert r["status_bits"] == 0 and r["run"] == "log-test"
+        assert abs(r["ledger_residual"]) <= 1e-12 * (r["E_rad1"] + r["E_mat1"])
