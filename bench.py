@@ -469,6 +469,37 @@ def adjoint_leg(B, dev, steps=200, ckpt_every=20, n_fd=64, h=1e-6):
                    "rel_err_floor": "1e-5 x max |dL/ds|", "seconds": t_fd}}
 
 
+def families_leg(B, dev, flush, steps=20):
+    """The paper's other problem families and the UGKP variant, each evolved
+    from its initial state and then timed as CUDA-graph steps (mixed
+    precision and FP64): the Larsen slab (Sec. 3.3, photo-ionisation
+    opacity, tau_num, free side; 400 steps in), the Olson foam (Sec. 3.5,
+    three-band opacity, T-dependent heat capacity; 40 steps in, source on),
+    and the 200x30 slab in the UGKP variant from the synthetic state."""
+    out = {}
+    cases = [("larsen_slab_200x24", I.larsen_slab(), 400, None),
+             ("olson_slab_128x30", I.olson_slab(), 40, None)]
+    pu = I.multigroup_slab().replace(method=I.UGKP)
+    pu.particle_capacity = 1 << 23
+    cases.append(("multigroup_slab_200x30_ugkp", pu, 5, I.synthetic_state(pu, N_PARTICLES, seed=1)))
+    for name, p, evolve, st in cases:
+        row = {}
+        for prec_name, prec in (("mixed", I.MIXED), ("fp64", I.FP64)):
+            sim = B.Simulation(p.replace(precision=prec), device=dev)
+            if st is not None:
+                sim.set_state(st["T"], st["rho"], st["rho_h"], st["particles"], step=st["step"])
+            sim.step(evolve)
+            assert sim.tallies()["status_bits"] == 0
+            ms, segs, (n_in, _), _, si = graph_steps(sim, steps, flush)
+            row[prec_name] = {"value": segs / (ms / 1e3), "unit": "segments/s", "ms_per_step": ms / steps,
+                              "particles_per_step": n_in / steps, "si_iters_per_step": si / steps}
+            sim.close()
+        row["speedup_mixed_vs_fp64"] = row["mixed"]["value"] / row["fp64"]["value"]
+        row["evolved_steps"] = evolve
+        out[name] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,6 +516,8 @@ def main():
     ap.add_argument("--workload", default="slab", choices=["slab", "checkerboard"],
                     help="workload of a --quick run (profiling): the 200x30 slab or the 2D checkerboard")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--no-families", action="store_true",
+                    help="skip the Larsen / Olson / UGKP leg")
     ap.add_argument("--no-matched-error", action="store_true", help="skip the matched-error leg")
     ap.add_argument("--ensemble-steps", type=int, default=10)
     ap.add_argument("--no-checkerboard", action="store_true", help="skip the 2D checkerboard leg")
@@ -616,6 +649,8 @@ def main():
                                                    args.checkerboard_particles)
     if extra_legs and not args.no_adjoint:
         line["adjoint"] = adjoint_leg(B, dev)
+    if extra_legs and not args.no_families:
+        line["families"] = families_leg(B, dev, flush)
     if extra_legs and not args.no_ensemble:
         line["batched_ensemble"] = ensemble_leg(B, dev, flush, args.ensemble_steps, args.warmup)
 
