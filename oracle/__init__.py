@@ -42,19 +42,22 @@ class CProblem(C.Structure):
         ("nu_edges", _dp), ("sigma0", _dp), ("cv", _dp), ("src_T", _dp),
         ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
         ("cv_chi", C.c_double),
+        ("nz", C.c_int32), ("bc_z", C.c_int32 * 2), ("_pad3", C.c_int32), ("dz", C.c_double),
+        ("bcT_z", C.c_double * 2),
     ]
 
 
 class CParticles(C.Structure):
     _fields_ = [("x", _dp), ("y", _dp), ("ox", _dp), ("oy", _dp), ("nu", _dp), ("w", _dp),
-                ("id", _up), ("cell", _ip), ("grp", _ip)]
+                ("id", _up), ("cell", _ip), ("grp", _ip), ("z", _dp), ("oz", _dp)]
 
 
 RECORD_DTYPE = np.dtype([
     ("id", np.uint64), ("fate", np.int32), ("cell0", np.int32), ("cell1", np.int32),
     ("grp", np.int32), ("nseg", np.int32), ("_pad", np.int32),
     ("x", np.float64), ("y", np.float64), ("ox", np.float64), ("oy", np.float64),
-    ("nu", np.float64), ("w", np.float64), ("t_end", np.float64)])
+    ("nu", np.float64), ("w", np.float64), ("t_end", np.float64),
+    ("z", np.float64), ("oz", np.float64)])
 
 
 class CTallies(C.Structure):
@@ -144,7 +147,7 @@ class OracleProblem:
         self.cv = np.ascontiguousarray(p.cv, dtype=np.float64)
         self.src_T = None if p.src_T is None else np.ascontiguousarray(p.src_T, dtype=np.float64)
         s = CProblem()
-        s.dim, s.nx, s.ny, s.G = p.dim, p.nx, (p.ny if p.dim == 2 else 1), p.G
+        s.dim, s.nx, s.ny, s.G = p.dim, p.nx, (p.ny if p.dim >= 2 else 1), p.G
         s.grey, s.wave_order, s.si_max_iters = p.grey, p.wave_order, p.si_max_iters
         for i in range(4):
             s.bc[i] = int(p.bc[i])
@@ -165,6 +168,12 @@ class OracleProblem:
         s.src_t_end = float(getattr(p, "src_t_end", 0.0))
         s.cv_law = int(getattr(p, "cv_law", 0))
         s.cv_chi = float(getattr(p, "cv_chi", 0.0))
+        s.nz = int(getattr(p, "nz", 1))
+        s.dz = float(getattr(p, "dz", 1.0))
+        bc = list(p.bc) + [0] * (6 - len(p.bc))
+        bcT = list(p.bcT) + [0.0] * (6 - len(p.bcT))
+        s.bc_z[0], s.bc_z[1] = int(bc[4]), int(bc[5])
+        s.bcT_z[0], s.bcT_z[1] = float(bcT[4]), float(bcT[5])
         self.s = s
 
     @property
@@ -251,8 +260,8 @@ class Tallies:
         self.W = np.zeros(n)
         self.E_surv = np.zeros(n)
         self.E_abs = np.zeros(n)
-        self.esc = np.zeros(4 * p.G)
-        self.inflow = np.zeros(4 * p.G)
+        self.esc = np.zeros(6 * p.G)
+        self.inflow = np.zeros(6 * p.G)
         self.Fwave = np.zeros(p.nface * p.G)
         self.Feq = np.zeros(p.nface * p.G)
         self.N = np.zeros(p.nbins, dtype=np.int32)
@@ -327,7 +336,7 @@ def source_iteration(prob: OracleProblem, T_n, rho_n, R):
 class ParticleSet:
     """Structure-of-arrays particles (numpy), in the oracle's layout."""
 
-    FIELDS = ("x", "y", "ox", "oy", "nu", "w")
+    FIELDS = ("x", "y", "ox", "oy", "nu", "w", "z", "oz")
 
     def __init__(self, cap: int):
         self.cap = cap
@@ -359,7 +368,8 @@ class ParticleSet:
         n = len(d["id"])
         ps = ParticleSet(max(cap or 0, n, 1))
         for f in ParticleSet.FIELDS:
-            getattr(ps, f)[:n] = d[f]
+            if f in d:
+                getattr(ps, f)[:n] = d[f]
         ps.id[:n] = d["id"]
         ps.cell[:n] = d["cell"]
         ps.grp[:n] = d["grp"]

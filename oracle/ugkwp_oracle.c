@@ -21,12 +21,60 @@
 #define PLANCK_NORM (15.0 / (PI * PI * PI * PI))   /* 15/pi^4 */
 #define MAX_K_PER_BIN ((1 << 20) - 1)
 
-static int ncell_of(const or_problem* P) { return P->nx * (P->dim == 2 ? P->ny : 1); }
-static int nxface_of(const or_problem* P) { return (P->nx + 1) * (P->dim == 2 ? P->ny : 1); }
+/* Grid: cells c = (iz ny + iy) nx + ix; faces along axis a between the line
+ * cells k-1 and k (k = 0..n_a): x-faces (iz ny + iy)(nx+1) + k, y-faces
+ * nxf + (iz (ny+1) + k) nx + ix, z-faces nxf + nyf + (k ny + iy) nx + ix.  A
+ * "line" of axis a is the set of cells sharing the other two coordinates,
+ * numbered with the lower remaining axis fastest.  1D and 2D are the cases
+ * ny = nz = 1 and nz = 1.                                                   */
+static int ny_of(const or_problem* P) { return P->dim >= 2 ? P->ny : 1; }
+static int nz_of(const or_problem* P) { return P->dim == 3 ? P->nz : 1; }
+static int ncell_of(const or_problem* P) { return P->nx * ny_of(P) * nz_of(P); }
+static int nxface_of(const or_problem* P) { return (P->nx + 1) * ny_of(P) * nz_of(P); }
+static int nyface_of(const or_problem* P) { return P->dim >= 2 ? P->nx * (ny_of(P) + 1) * nz_of(P) : 0; }
 static int nface_of(const or_problem* P) {
-  return nxface_of(P) + (P->dim == 2 ? P->nx * (P->ny + 1) : 0);
+  return nxface_of(P) + nyface_of(P) + (P->dim == 3 ? P->nx * ny_of(P) * (nz_of(P) + 1) : 0);
 }
-static double vol_of(const or_problem* P) { return P->dim == 2 ? P->dx * P->dy : P->dx; }
+static double vol_of(const or_problem* P) {
+  return P->dx * (P->dim >= 2 ? P->dy : 1.0) * (P->dim == 3 ? P->dz : 1.0);
+}
+static int bc_of(const or_problem* P, int side) { return side < 4 ? P->bc[side] : P->bc_z[side - 4]; }
+static double bcT_of(const or_problem* P, int side) { return side < 4 ? P->bcT[side] : P->bcT_z[side - 4]; }
+static double h_of(const or_problem* P, int axis) { return axis == 0 ? P->dx : (axis == 1 ? P->dy : P->dz); }
+/* area of a face normal to `axis` (1D: 1; 2D: the other cell width) */
+static double area_of(const or_problem* P, int axis) {
+  if (P->dim == 1) return 1.0;
+  if (P->dim == 2) return axis == 0 ? P->dy : P->dx;
+  return axis == 0 ? P->dy * P->dz : (axis == 1 ? P->dx * P->dz : P->dx * P->dy);
+}
+static int n_along(const or_problem* P, int axis) { return axis == 0 ? P->nx : (axis == 1 ? ny_of(P) : nz_of(P)); }
+static int n_lines(const or_problem* P, int axis) { return ncell_of(P) / n_along(P, axis); }
+static int line_cell(const or_problem* P, int axis, int line, int k) {
+  const int nx = P->nx, ny = ny_of(P);
+  if (axis == 0) return line * nx + k;
+  if (axis == 1) return ((line / nx) * ny + k) * nx + line % nx;
+  return k * nx * ny + line;
+}
+static int line_face(const or_problem* P, int axis, int line, int k) {
+  const int nx = P->nx, ny = ny_of(P);
+  if (axis == 0) return line * (nx + 1) + k;
+  if (axis == 1) return nxface_of(P) + ((line / nx) * (ny + 1) + k) * nx + line % nx;
+  return nxface_of(P) + nyface_of(P) + k * nx * ny + line;
+}
+static void cell_coords(const or_problem* P, int c, int* ix, int* iy, int* iz) {
+  const int nx = P->nx, ny = ny_of(P);
+  *ix = c % nx;
+  *iy = (c / nx) % ny;
+  *iz = c / (nx * ny);
+}
+/* the face of cell c on `axis`, lower (dir < 0) or upper side */
+static int cell_face(const or_problem* P, int c, int axis, int dir) {
+  int i[3];
+  cell_coords(P, c, &i[0], &i[1], &i[2]);
+  const int nx = P->nx;
+  const int line = axis == 0 ? i[1] + ny_of(P) * i[2] : (axis == 1 ? i[0] + nx * i[2] : i[0] + nx * i[1]);
+  return line_face(P, axis, line, i[axis] + (dir > 0 ? 1 : 0));
+}
 
 /* ------------------------------------------------------------------------ */
 /* Counter-based random numbers: Philox4x32-10 as published by Salmon,
@@ -339,7 +387,8 @@ double or_sample_nu(double nlo, double nhi, double T, double eta) {
  * reflecting wall the direction flips and t_f is not reset; a particle that
  * leaves through a vacuum or black-body side escapes; a particle born in a
  * black-body ghost cell that does not reach the domain is removed; on a tie
- * between an x- and a y-face the x-face is taken first.  Energy crossing
+ * between faces of different axes the lower axis (x, then y, then z) is
+ * taken first.  Energy crossing
  * faces is tallied as in Eq. wfrpFormula (in minus out).                    */
 static double draw_j(const or_problem* P, uint64_t id, int64_t step, int64_t j,
                      const double* draws, int64_t n_draws, int* bad) {
@@ -350,28 +399,30 @@ static double draw_j(const or_problem* P, uint64_t id, int64_t step, int64_t j,
   return or_draw(P, id, step, j);
 }
 
-int or_stream_particle(const or_problem* P, const double* T, int64_t step,
-                       double* px, double* py, double* pox, double* poy, double nu,
-                       double w, uint64_t id, int32_t* pcell, int32_t g,
-                       int newborn, int64_t first_draw,
-                       const double* draws, int64_t n_draws,
-                       or_tallies* tal, int32_t* nseg_out, double* t_end,
-                       double* trace_x, double* trace_t, int trace_cap, int* n_trace) {
-  const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1, G = P->G;
+int or_stream_particle3(const or_problem* P, const double* T, int64_t step,
+                        double* px, double* py, double* pz, double* pox, double* poy, double* poz,
+                        double nu, double w, uint64_t id, int32_t* pcell, int32_t g,
+                        int newborn, int64_t first_draw,
+                        const double* draws, int64_t n_draws,
+                        or_tallies* tal, int32_t* nseg_out, double* t_end,
+                        double* trace_x, double* trace_t, int trace_cap, int* n_trace) {
+  const int nx = P->nx, ny = ny_of(P), nz = nz_of(P), G = P->G;
   const double v = P->c / P->eps, dt = P->dt;
   const double inv_rate = P->eps * P->eps / P->c;   /* tau = eps^2/(c sigma) */
-  double x = *px, y = *py, ox = *pox, oy = *poy;
+  double p[3] = {*px, *py, *pz}, o[3] = {*pox, *poy, *poz};
+  const double h[3] = {P->dx, P->dy, P->dz};
+  const int n[3] = {nx, ny, nz};
   int cell = *pcell;
-  int ix = P->dim == 2 ? (cell >= 0 && cell < nx * ny ? cell % nx : 0) : cell;
-  int iy = P->dim == 2 ? (cell >= 0 && cell < nx * ny ? cell / nx : 0) : 0;
+  int ic[3] = {0, 0, 0};
+  if (P->dim == 1) ic[0] = cell;
+  else cell_coords(P, cell, &ic[0], &ic[1], &ic[2]);
   int ghost = (P->dim == 1) && (cell < 0 || cell >= nx);
   int ghost_side = (cell < 0) ? 0 : 1;
   int bad = 0, nseg = 0, fate;
   int64_t j = first_draw;
-  double t_tra = 0.0, t_rem, nu_p_T;
+  double t_tra = 0.0, t_rem;
   int collided;
   if (n_trace) *n_trace = 0;
-  (void)nu_p_T;
 
   if (newborn && (P->method != OR_UGKP || ghost)) {
     t_rem = dt;
@@ -384,31 +435,33 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
   }
 
   for (;;) {
-    double xL = ix * P->dx, xR = (ix + 1) * P->dx;
-    double yB = iy * P->dy, yT = (iy + 1) * P->dy;
-    double tx = INFINITY, ty = INFINITY;
-    if (ox > 0) tx = fmax(xR - x, 0.0) / (v * ox);
-    else if (ox < 0) tx = fmax(x - xL, 0.0) / (v * -ox);
-    if (P->dim == 2) {
-      if (oy > 0) ty = fmax(yT - y, 0.0) / (v * oy);
-      else if (oy < 0) ty = fmax(y - yB, 0.0) / (v * -oy);
+    /* time to the nearest face along each axis; ties go to the lower axis */
+    int axis = 0;
+    double tf = INFINITY;
+    for (int a = 0; a < P->dim; ++a) {
+      const double lo = ic[a] * h[a], hi = (ic[a] + 1) * h[a];
+      double ta = INFINITY;
+      if (o[a] > 0) ta = fmax(hi - p[a], 0.0) / (v * o[a]);
+      else if (o[a] < 0) ta = fmax(p[a] - lo, 0.0) / (v * -o[a]);
+      if (a == 0 || ta < tf) { tf = ta; axis = a; }
     }
-    int axis = (tx <= ty) ? 0 : 1;
-    double tf = axis == 0 ? tx : ty;
     if (tf < t_rem) {
       ++nseg;
       t_tra += tf;
       t_rem -= tf;
-      int dir;
-      if (axis == 0) { dir = ox > 0 ? 1 : -1; x = dir > 0 ? xR : xL; y += v * oy * tf; }
-      else           { dir = oy > 0 ? 1 : -1; y = dir > 0 ? yT : yB; x += v * ox * tf; }
-      if (trace_x && n_trace && *n_trace < trace_cap) { trace_x[*n_trace] = x; trace_t[*n_trace] = t_tra; ++*n_trace; }
-      int nix = ix + (axis == 0 ? dir : 0), niy = iy + (axis == 1 ? dir : 0);
-      int outside = nix < 0 || nix >= nx || niy < 0 || niy >= ny;
+      const int dir = o[axis] > 0 ? 1 : -1;
+      for (int a = 0; a < 3; ++a) {
+        if (a == axis) p[a] = dir > 0 ? (ic[a] + 1) * h[a] : ic[a] * h[a];
+        else if (a < P->dim || a == 1) p[a] += v * o[a] * tf;
+      }
+      if (trace_x && n_trace && *n_trace < trace_cap) { trace_x[*n_trace] = p[0]; trace_t[*n_trace] = t_tra; ++*n_trace; }
+      int ni[3] = {ic[0], ic[1], ic[2]};
+      ni[axis] += dir;
+      const int outside = ni[axis] < 0 || ni[axis] >= n[axis];
       if (outside) {
-        int side = axis * 2 + (dir > 0 ? 1 : 0);
-        if (P->bc[side] == OR_BC_REFLECT) {
-          if (axis == 0) ox = -ox; else oy = -oy;
+        const int side = axis * 2 + (dir > 0 ? 1 : 0);
+        if (bc_of(P, side) == OR_BC_REFLECT) {
+          o[axis] = -o[axis];
           continue;
         }
         if (tal) {
@@ -418,14 +471,15 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
         fate = OR_ESCAPED;
         break;
       }
-      int ncell = niy * nx + nix;
+      const int ncell = (ni[2] * ny + ni[1]) * nx + ni[0];
       if (tal) {
         if (ghost) tal->inflow[ghost_side * G + g] += w;
         else tal->W[cell * G + g] -= w;
         tal->W[ncell * G + g] += w;
       }
       ghost = 0;
-      cell = ncell; ix = nix; iy = niy;
+      cell = ncell;
+      ic[0] = ni[0]; ic[1] = ni[1]; ic[2] = ni[2];
       double u = draw_j(P, id, step, j++, draws, n_draws, &bad);
       double tc = -log(u) * inv_rate / or_sigma(P, cell, nu, T[cell]);
       double avail = dt - t_tra;
@@ -434,20 +488,33 @@ int or_stream_particle(const or_problem* P, const double* T, int64_t step,
       continue;
     }
     ++nseg;
-    x += v * ox * t_rem;
-    y += v * oy * t_rem;
+    p[0] += v * o[0] * t_rem;
+    p[1] += v * o[1] * t_rem;
+    if (P->dim == 3) p[2] += v * o[2] * t_rem;
     t_tra += t_rem;
     t_rem = 0.0;
-    if (trace_x && n_trace && *n_trace < trace_cap) { trace_x[*n_trace] = x; trace_t[*n_trace] = t_tra; ++*n_trace; }
+    if (trace_x && n_trace && *n_trace < trace_cap) { trace_x[*n_trace] = p[0]; trace_t[*n_trace] = t_tra; ++*n_trace; }
     if (ghost) fate = OR_REMOVED;
     else if (collided) { fate = OR_ABSORBED; if (tal) tal->E_abs[cell * G + g] += w; }
     else { fate = OR_SURVIVED; if (tal) tal->E_surv[cell * G + g] += w; }
     break;
   }
-  *px = x; *py = y; *pox = ox; *poy = oy; *pcell = cell;
+  *px = p[0]; *py = p[1]; *pz = p[2]; *pox = o[0]; *poy = o[1]; *poz = o[2]; *pcell = cell;
   if (nseg_out) *nseg_out = nseg;
   if (t_end) *t_end = t_tra;
   return bad ? -1 : fate;
+}
+
+int or_stream_particle(const or_problem* P, const double* T, int64_t step,
+                       double* px, double* py, double* pox, double* poy, double nu,
+                       double w, uint64_t id, int32_t* pcell, int32_t g,
+                       int newborn, int64_t first_draw,
+                       const double* draws, int64_t n_draws,
+                       or_tallies* tal, int32_t* nseg_out, double* t_end,
+                       double* trace_x, double* trace_t, int trace_cap, int* n_trace) {
+  double z = 0.0, oz = 0.0;
+  return or_stream_particle3(P, T, step, px, py, &z, pox, poy, &oz, nu, w, id, pcell, g, newborn, first_draw,
+                             draws, n_draws, tal, nseg_out, t_end, trace_x, trace_t, trace_cap, n_trace);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -476,14 +543,16 @@ double or_x_num(const or_problem* P, const double* T, int c, int g) {
   const double rate_f = P->c / (P->eps * P->eps);
   const double x = P->dt * rate_f * or_sigma_group(P, c, g, T[c]);
   if (!(P->tau_num_C > 0.0)) return x;
-  const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1;
-  const int ix = c % nx, iy = c / nx;
+  const int nx = P->nx, ny = ny_of(P), nz = nz_of(P);
+  int ix, iy, iz;
+  cell_coords(P, c, &ix, &iy, &iz);
   double J = 0.0;
-  const int nb[4][2] = {{ix - 1, iy}, {ix + 1, iy}, {ix, iy - 1}, {ix, iy + 1}};
-  for (int k = 0; k < (P->dim == 2 ? 4 : 2); ++k) {
-    const int jx = nb[k][0], jy = nb[k][1];
-    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
-    const double Tn = T[jy * nx + jx];
+  const int nb[6][3] = {{ix - 1, iy, iz}, {ix + 1, iy, iz}, {ix, iy - 1, iz},
+                        {ix, iy + 1, iz}, {ix, iy, iz - 1}, {ix, iy, iz + 1}};
+  for (int k = 0; k < 2 * P->dim; ++k) {
+    const int jx = nb[k][0], jy = nb[k][1], jz = nb[k][2];
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+    const double Tn = T[(jz * ny + jy) * nx + jx];
     const double j = fabs(T[c] - Tn) / (T[c] + Tn);
     if (j > J) J = j;
   }
@@ -578,22 +647,21 @@ static void half_coefs(double x_f, double tau_f, double x_h, double e_eff, doubl
 
 int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
                  const double* e_eff, double* Fwave) {
-  const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1, G = P->G, ncell = nx * ny;
+  const int G = P->G, ncell = ncell_of(P);
   const double v = P->c / P->eps, rate_f = P->c / (P->eps * P->eps), dt = P->dt;
-  const int nxf = nxface_of(P);
   for (int axis = 0; axis < P->dim; ++axis) {
-    const double h = axis == 0 ? P->dx : P->dy;
-    const int nk = axis == 0 ? nx : ny;                /* cells along the axis */
-    const int nlines = axis == 0 ? ny : nx;
+    const double h = h_of(P, axis);
+    const int nk = n_along(P, axis);                   /* cells along the axis */
+    const int nlines = n_lines(P, axis);
     const int sideL = axis * 2, sideR = axis * 2 + 1;
     for (int line = 0; line < nlines; ++line) {
       for (int f = 0; f <= nk; ++f) {
-        int fidx = axis == 0 ? line * (nx + 1) + f : nxf + f * nx + line;
+        int fidx = line_face(P, axis, line, f);
         for (int g = 0; g < G; ++g) {
-#define CELL_AT(k) (axis == 0 ? line * nx + (k) : (k) * nx + line)
+#define CELL_AT(k) line_cell(P, axis, line, (k))
           int kL = f - 1, kR = f;
           int lin = kL >= 0, rin = kR < nk;
-          if ((!lin && P->bc[sideL] == OR_BC_REFLECT) || (!rin && P->bc[sideR] == OR_BC_REFLECT)) {
+          if ((!lin && bc_of(P, sideL) == OR_BC_REFLECT) || (!rin && bc_of(P, sideR) == OR_BC_REFLECT)) {
             Fwave[fidx * G + g] = 0.0;
             continue;
           }
@@ -604,8 +672,8 @@ int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
             else {                                                                   \
               int s_ = kk_ < 0 ? sideL : sideR;                                      \
               int kin_ = kk_ < 0 ? 0 : nk - 1;                                       \
-              if (P->bc[s_] == OR_BC_REFLECT) out = rho_h[CELL_AT(kin_) * G + g];   \
-              else if (P->bc[s_] == OR_BC_BLACKBODY) out = or_phi(P, g, P->bcT[s_]); \
+              if (bc_of(P, s_) == OR_BC_REFLECT) out = rho_h[CELL_AT(kin_) * G + g];  \
+              else if (bc_of(P, s_) == OR_BC_BLACKBODY) out = or_phi(P, g, bcT_of(P, s_)); \
               else out = 0.0;                                                        \
             }                                                                        \
           } while (0)
@@ -627,15 +695,15 @@ int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
           if (lin) {
             sgl = or_sigma_group(P, CELL_AT(kL), g, T[CELL_AT(kL)]); el = e_eff[CELL_AT(kL) * G + g];
             xhl = or_x_num(P, T, CELL_AT(kL), g);
-          } else if (P->bc[sideL] == OR_BC_BLACKBODY) {
-            sgl = or_sigma_group(P, CELL_AT(0), g, P->bcT[sideL]); el = e_eff[(ncell + sideL) * G + g];
+          } else if (bc_of(P, sideL) == OR_BC_BLACKBODY) {
+            sgl = or_sigma_group(P, CELL_AT(0), g, bcT_of(P, sideL)); el = e_eff[(ncell + sideL) * G + g];
             xhl = dt * rate_f * sgl;
           } else { sgl = -1.0; el = 0.0; }
           if (rin) {
             sgr = or_sigma_group(P, CELL_AT(kR), g, T[CELL_AT(kR)]); er = e_eff[CELL_AT(kR) * G + g];
             xhr = or_x_num(P, T, CELL_AT(kR), g);
-          } else if (P->bc[sideR] == OR_BC_BLACKBODY) {
-            sgr = or_sigma_group(P, CELL_AT(nk - 1), g, P->bcT[sideR]); er = e_eff[(ncell + sideR) * G + g];
+          } else if (bc_of(P, sideR) == OR_BC_BLACKBODY) {
+            sgr = or_sigma_group(P, CELL_AT(nk - 1), g, bcT_of(P, sideR)); er = e_eff[(ncell + sideR) * G + g];
             xhr = dt * rate_f * sgr;
           } else { sgr = -1.0; er = 0.0; }
           if (sgl < 0.0) sgl = sgr;          /* vacuum ghost: inner opacity */
@@ -679,8 +747,8 @@ int or_wave_flux(const or_problem* P, const double* T, const double* rho_h,
 int or_source_iteration(const or_problem* P, const double* T_n, const double* rho_n,
                         const double* R, double* T_out, double* rho_out,
                         double* Feq_out, int* iters) {
-  const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1, G = P->G, ncell = nx * ny;
-  const int nxf = nxface_of(P), nface = nface_of(P);
+  const int G = P->G, ncell = ncell_of(P);
+  const int nface = nface_of(P);
   const double v = P->c / P->eps, dt = P->dt;
   const double rate_f = P->c / (P->eps * P->eps);
   double* Tk = malloc(sizeof(double) * ncell);
@@ -701,23 +769,23 @@ int or_source_iteration(const or_problem* P, const double* T_n, const double* rh
       }
     /* equilibrium flux on every face */
     for (int axis = 0; axis < P->dim; ++axis) {
-      const double h = axis == 0 ? P->dx : P->dy;
-      const int nk = axis == 0 ? nx : ny, nlines = axis == 0 ? ny : nx;
+      const double h = h_of(P, axis);
+      const int nk = n_along(P, axis), nlines = n_lines(P, axis);
       for (int line = 0; line < nlines; ++line)
         for (int f = 0; f <= nk; ++f) {
-          int fidx = axis == 0 ? line * (nx + 1) + f : nxf + f * nx + line;
+          int fidx = line_face(P, axis, line, f);
           for (int g = 0; g < G; ++g) {
-            int cl = f - 1 >= 0 ? (axis == 0 ? line * nx + f - 1 : (f - 1) * nx + line) : -1;
-            int cr = f < nk ? (axis == 0 ? line * nx + f : f * nx + line) : -1;
+            int cl = f - 1 >= 0 ? line_cell(P, axis, line, f - 1) : -1;
+            int cr = f < nk ? line_cell(P, axis, line, f) : -1;
             double sl, sr, pl, pr;
             if (cl < 0 || cr < 0) {
               int side = axis * 2 + (cl < 0 ? 0 : 1);
               int cin = cl < 0 ? cr : cl;
-              if (P->bc[side] == OR_BC_REFLECT) { Feq[fidx * G + g] = 0.0; continue; }
+              if (bc_of(P, side) == OR_BC_REFLECT) { Feq[fidx * G + g] = 0.0; continue; }
               double sg, pg;
-              if (P->bc[side] == OR_BC_BLACKBODY) {
-                sg = or_sigma_group(P, cin, g, P->bcT[side]);
-                pg = or_phi(P, g, P->bcT[side]);
+              if (bc_of(P, side) == OR_BC_BLACKBODY) {
+                sg = or_sigma_group(P, cin, g, bcT_of(P, side));
+                pg = or_phi(P, g, bcT_of(P, side));
               } else { sg = sig[cin * G + g]; pg = 0.0; }
               if (cl < 0) { sl = sg; pl = pg; sr = sig[cr * G + g]; pr = phi[cr * G + g]; }
               else        { sr = sg; pr = pg; sl = sig[cl * G + g]; pl = phi[cl * G + g]; }
@@ -736,7 +804,6 @@ int or_source_iteration(const or_problem* P, const double* T_n, const double* rh
     /* per-cell linearised update */
     double errT = 0.0, errR = 0.0;
     for (int c = 0; c < ncell; ++c) {
-      int ix = c % nx, iy = c / nx;
       /* e(T^{k+1}) ~ e(T^k) + C_v(T^k) (T^{k+1} - T^k) for a T-dependent heat
        * capacity (the same fixed point); cv_law 0 is the constant case */
       double num, den;
@@ -752,11 +819,9 @@ int or_source_iteration(const or_problem* P, const double* T_n, const double* rh
       double a[256];
       for (int g = 0; g < G; ++g) {
         double q = R[c * G + g];
-        int fxl = iy * (nx + 1) + ix, fxr = fxl + 1;
-        q += (dt / P->dx) * (Feq[fxl * G + g] - Feq[fxr * G + g]);
-        if (P->dim == 2) {
-          int fyl = nxf + iy * nx + ix, fyr = nxf + (iy + 1) * nx + ix;
-          q += (dt / P->dy) * (Feq[fyl * G + g] - Feq[fyr * G + g]);
+        for (int axis = 0; axis < P->dim; ++axis) {
+          const int fl = cell_face(P, c, axis, -1), fu = cell_face(P, c, axis, +1);
+          q += (dt / h_of(P, axis)) * (Feq[fl * G + g] - Feq[fu * G + g]);
         }
         Q[g] = q;
         a[g] = dt * rate_f * sig[c * G + g];
@@ -839,21 +904,21 @@ int or_step_core(const or_problem* P, int64_t step,
                  or_tallies* tal,
                  const double* w2_in, const double* w2_bins, double* w2_out, or_tallies* tal2,
                  double* w2_scale) {
-  const int nx = P->nx, ny = P->dim == 2 ? P->ny : 1, G = P->G, ncell = nx * ny;
-  const int nface = nface_of(P), nxf = nxface_of(P);
+  const int nx = P->nx, G = P->G, ncell = ncell_of(P);
+  const int nface = nface_of(P);
   const double V = vol_of(P), dt = P->dt;
   int status = OR_OK;
-  if (P->dim != 1 && P->dim != 2) return OR_ERR_ARG;
+  if (P->dim < 1 || P->dim > 3) return OR_ERR_ARG;
   if (G < 1 || G > 256 || (P->grey && G != 1)) return OR_ERR_ARG;
-  if (P->dim == 2)
-    for (int s = 0; s < 4; ++s)
-      if (P->bc[s] == OR_BC_BLACKBODY) return OR_ERR_ARG;
+  if (P->dim >= 2)
+    for (int s = 0; s < 2 * P->dim; ++s)
+      if (bc_of(P, s) == OR_BC_BLACKBODY) return OR_ERR_ARG;
 
   memset(tal->W, 0, sizeof(double) * ncell * G);
   memset(tal->E_surv, 0, sizeof(double) * ncell * G);
   memset(tal->E_abs, 0, sizeof(double) * ncell * G);
-  memset(tal->esc, 0, sizeof(double) * 4 * G);
-  memset(tal->inflow, 0, sizeof(double) * 4 * G);
+  memset(tal->esc, 0, sizeof(double) * 6 * G);
+  memset(tal->inflow, 0, sizeof(double) * 6 * G);
   tal->n_in = n_in;
   tal->n_born = tal->n_survived = tal->n_absorbed = tal->n_escaped = tal->n_removed = 0;
   tal->n_segments = 0;
@@ -875,18 +940,20 @@ int or_step_core(const or_problem* P, int64_t step,
   int64_t nrec = 0, nout = 0;
   for (int64_t i = 0; i < n_in; ++i) {
     double x = pin->x[i], y = pin->y[i], ox = pin->ox[i], oy = pin->oy[i];
+    double z = pin->z ? pin->z[i] : 0.0, oz = pin->oz ? pin->oz[i] : 0.0;
     int32_t cell = pin->cell[i], cell0 = cell, nseg;
     double tend;
     if (tal2)
       restream(P, T, step, x, y, ox, oy, pin->nu[i], w2_in[i], pin->id[i], cell, pin->grp[i], 0, 0, tal2);
-    int fate = or_stream_particle(P, T, step, &x, &y, &ox, &oy, pin->nu[i], pin->w[i], pin->id[i],
-                                  &cell, pin->grp[i], 0, 0, NULL, 0, tal, &nseg, &tend,
-                                  NULL, NULL, 0, NULL);
+    int fate = or_stream_particle3(P, T, step, &x, &y, &z, &ox, &oy, &oz, pin->nu[i], pin->w[i], pin->id[i],
+                                   &cell, pin->grp[i], 0, 0, NULL, 0, tal, &nseg, &tend,
+                                   NULL, NULL, 0, NULL);
     tal->n_segments += nseg;
     if (fate == OR_SURVIVED) {
       ++tal->n_survived;
       if (nout < cap_out) {
         pout->x[nout] = x; pout->y[nout] = y; pout->ox[nout] = ox; pout->oy[nout] = oy;
+        if (pout->z) { pout->z[nout] = z; pout->oz[nout] = oz; }
         pout->nu[nout] = pin->nu[i]; pout->w[nout] = pin->w[i]; pout->id[nout] = pin->id[i];
         pout->cell[nout] = cell; pout->grp[nout] = pin->grp[i];
         if (w2_out) w2_out[nout] = w2_in[i];
@@ -899,7 +966,7 @@ int or_step_core(const or_problem* P, int64_t step,
       or_record* r = &rec[nrec];
       r->id = pin->id[i]; r->fate = fate; r->cell0 = cell0; r->cell1 = cell; r->grp = pin->grp[i];
       r->nseg = nseg; r->_pad = 0; r->x = x; r->y = y; r->ox = ox; r->oy = oy; r->nu = pin->nu[i];
-      r->w = pin->w[i]; r->t_end = tend;
+      r->w = pin->w[i]; r->t_end = tend; r->z = z; r->oz = oz;
     }
     ++nrec;
   }
@@ -909,20 +976,24 @@ int or_step_core(const or_problem* P, int64_t step,
     for (int k = 0; k < tal->N[b]; ++k) {
       uint64_t id = ((uint64_t)step << 44) | ((uint64_t)b << 20) | (uint64_t)k;
       int64_t j = 0;
-      double x, y = 0.0, ox, oy = 0.0, nu = 0.0, Tb;
+      double x, y = 0.0, z = 0.0, ox, oy = 0.0, oz = 0.0, nu = 0.0, Tb;
       int32_t cell;
       if (bc_cell < ncell) {
-        int ix = bc_cell % nx, iy = bc_cell / nx;
+        int ix, iy, iz;
+        cell_coords(P, bc_cell, &ix, &iy, &iz);
         x = ix * P->dx + or_draw(P, id, step, j++) * P->dx;
-        if (P->dim == 2) y = iy * P->dy + or_draw(P, id, step, j++) * P->dy;
+        if (P->dim >= 2) y = iy * P->dy + or_draw(P, id, step, j++) * P->dy;
+        if (P->dim == 3) z = iz * P->dz + or_draw(P, id, step, j++) * P->dz;
         if (P->dim == 1) {
           ox = 2.0 * or_draw(P, id, step, j++) - 1.0;
         } else {
+          /* 3D isotropic directions (2D keeps their x and y components) */
           double muz = 2.0 * or_draw(P, id, step, j++) - 1.0;
           double phi = 2.0 * PI * or_draw(P, id, step, j++);
           double s = sqrt(fmax(0.0, 1.0 - muz * muz));
           ox = s * cos(phi);
           oy = s * sin(phi);
+          if (P->dim == 3) oz = muz;
         }
         cell = bc_cell;
         Tb = T[bc_cell];
@@ -944,13 +1015,14 @@ int or_step_core(const or_problem* P, int64_t step,
       int32_t cell0 = cell, nseg;
       double tend, w = tal->omega[b];
       if (tal2) restream(P, T, step, x, y, ox, oy, nu, w2_bins[b], id, cell, g, 1, j, tal2);
-      int fate = or_stream_particle(P, T, step, &x, &y, &ox, &oy, nu, w, id, &cell, g, 1, j,
-                                    NULL, 0, tal, &nseg, &tend, NULL, NULL, 0, NULL);
+      int fate = or_stream_particle3(P, T, step, &x, &y, &z, &ox, &oy, &oz, nu, w, id, &cell, g, 1, j,
+                                     NULL, 0, tal, &nseg, &tend, NULL, NULL, 0, NULL);
       tal->n_segments += nseg;
       if (fate == OR_SURVIVED) {
         ++tal->n_survived;
         if (nout < cap_out) {
           pout->x[nout] = x; pout->y[nout] = y; pout->ox[nout] = ox; pout->oy[nout] = oy;
+          if (pout->z) { pout->z[nout] = z; pout->oz[nout] = oz; }
           pout->nu[nout] = nu; pout->w[nout] = w; pout->id[nout] = id;
           pout->cell[nout] = cell; pout->grp[nout] = g;
           if (w2_out) w2_out[nout] = w2_bins[b];
@@ -963,6 +1035,7 @@ int or_step_core(const or_problem* P, int64_t step,
         or_record* r = &rec[nrec];
         r->id = id; r->fate = fate; r->cell0 = cell0; r->cell1 = cell; r->grp = g; r->nseg = nseg;
         r->_pad = 0; r->x = x; r->y = y; r->ox = ox; r->oy = oy; r->nu = nu; r->w = w; r->t_end = tend;
+        r->z = z; r->oz = oz;
       }
       ++nrec;
     }
@@ -976,13 +1049,11 @@ int or_step_core(const or_problem* P, int64_t step,
   double* R = malloc(sizeof(double) * ncell * G);
   tal->src_in = 0.0;
   for (int c = 0; c < ncell; ++c) {
-    int ix = c % nx, iy = c / nx;
     for (int g = 0; g < G; ++g) {
-      int fxl = iy * (nx + 1) + ix, fxr = fxl + 1;
-      double r = rho[c * G + g] + (dt / P->dx) * (tal->Fwave[fxl * G + g] - tal->Fwave[fxr * G + g]);
-      if (P->dim == 2) {
-        int fyl = nxf + iy * nx + ix, fyr = nxf + (iy + 1) * nx + ix;
-        r += (dt / P->dy) * (tal->Fwave[fyl * G + g] - tal->Fwave[fyr * G + g]);
+      double r = rho[c * G + g];
+      for (int axis = 0; axis < P->dim; ++axis) {
+        const int fl = cell_face(P, c, axis, -1), fu = cell_face(P, c, axis, +1);
+        r += (dt / h_of(P, axis)) * (tal->Fwave[fl * G + g] - tal->Fwave[fu * G + g]);
       }
       r += tal->W[c * G + g] / V;
       if (P->src_T && P->src_T[c] > 0.0 && P->src_on != 0.0 &&
@@ -1041,12 +1112,12 @@ int or_step_core(const or_problem* P, int64_t step,
   free(fscale);
   double bin = 0.0;
   for (int axis = 0; axis < P->dim; ++axis) {
-    const int nk = axis == 0 ? nx : ny, nlines = axis == 0 ? ny : nx;
-    const double S = P->dim == 2 ? (axis == 0 ? P->dy : P->dx) : 1.0;
+    const int nk = n_along(P, axis), nlines = n_lines(P, axis);
+    const double S = area_of(P, axis);
     for (int line = 0; line < nlines; ++line)
       for (int g = 0; g < G; ++g) {
-        int f0 = axis == 0 ? line * (nx + 1) : nxf + line;
-        int f1 = axis == 0 ? line * (nx + 1) + nk : nxf + nk * nx + line;
+        int f0 = line_face(P, axis, line, 0);
+        int f1 = line_face(P, axis, line, nk);
         bin += dt * S * ((tal->Feq[f0 * G + g] + tal->Fwave[f0 * G + g]) -
                          (tal->Feq[f1 * G + g] + tal->Fwave[f1 * G + g])) / P->c;
       }
@@ -1054,7 +1125,7 @@ int or_step_core(const or_problem* P, int64_t step,
   tal->bnd_in_macro = bin;
   tal->bnd_out_macro = 0.0;
   double pin_e = 0.0, pout_e = 0.0;
-  for (int i = 0; i < 4 * G; ++i) { pin_e += tal->inflow[i]; pout_e += tal->esc[i]; }
+  for (int i = 0; i < 6 * G; ++i) { pin_e += tal->inflow[i]; pout_e += tal->esc[i]; }
   tal->bnd_in_part = pin_e / P->c;
   tal->bnd_out_part = pout_e / P->c;
   (void)nface;

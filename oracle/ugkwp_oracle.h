@@ -9,10 +9,11 @@
  * CUDA path: it is a plain, slow, step-by-step restatement of the method.
  *
  * Conventions (same meaning as the C ABI of the product, declared separately):
- *   cells are indexed c = iy*nx + ix; (cell, group) arrays are [c*G + g];
- *   x-faces f = iy*(nx+1) + fx (face fx sits at x = fx*dx);
- *   y-faces f = fy*nx + ix (face fy sits at y = fy*dy);
- *   sides: 0 = x-, 1 = x+, 2 = y-, 3 = y+.
+ *   cells are indexed c = (iz*ny + iy)*nx + ix; (cell, group) arrays are [c*G + g];
+ *   x-faces f = (iz*ny + iy)*(nx+1) + fx (face fx sits at x = fx*dx);
+ *   y-faces f = nxf + (iz*(ny+1) + fy)*nx + ix (face fy sits at y = fy*dy);
+ *   z-faces f = nxf + nyf + (fz*ny + iy)*nx + ix;
+ *   sides: 0 = x-, 1 = x+, 2 = y-, 3 = y+, 4 = z-, 5 = z+.
  */
 #ifndef UGKWP_ORACLE_H
 #define UGKWP_ORACLE_H
@@ -55,6 +56,11 @@ typedef struct {
   int32_t cv_law;                 /* 0: constant cv; 1: Olson CH foam, cv (1 + alpha + (T + chi) alpha') */
   int32_t _pad2;
   double cv_chi;                  /* chi of cv_law 1 */
+  int32_t nz;                     /* 3D: cells along z (dim 3) */
+  int32_t bc_z[2];                /* sides 4 (z-) and 5 (z+) */
+  int32_t _pad3;
+  double dz;
+  double bcT_z[2];
 } or_problem;
 
 /* Structure-of-arrays particle set.  In 1D, ox holds mu and y, oy are 0. */
@@ -62,6 +68,7 @@ typedef struct {
   double *x, *y, *ox, *oy, *nu, *w;
   uint64_t* id;
   int32_t *cell, *grp;
+  double *z, *oz;                 /* 3D only (may be NULL otherwise) */
 } or_particles;
 
 /* One record per particle processed in a step (survivors in, then newborns). */
@@ -69,6 +76,7 @@ typedef struct {
   uint64_t id;
   int32_t fate, cell0, cell1, grp, nseg, _pad;
   double x, y, ox, oy, nu, w, t_end;
+  double z, oz;
 } or_record;
 
 typedef struct {
@@ -114,6 +122,14 @@ double or_sample_nu(double nlo, double nhi, double T, double eta);
  * position and elapsed time at the end of every flight segment. */
 int or_stream_particle(const or_problem* P, const double* T, int64_t step,
                        double* x, double* y, double* ox, double* oy, double nu,
+                       double w, uint64_t id, int32_t* cell, int32_t g,
+                       int newborn, int64_t first_draw,
+                       const double* draws, int64_t n_draws,
+                       or_tallies* tal, int32_t* nseg, double* t_end,
+                       double* trace_x, double* trace_t, int trace_cap, int* n_trace);
+/* The same in 3D (z and Omega_z too; 1D and 2D leave them untouched). */
+int or_stream_particle3(const or_problem* P, const double* T, int64_t step,
+                       double* x, double* y, double* z, double* ox, double* oy, double* oz, double nu,
                        double w, uint64_t id, int32_t* cell, int32_t g,
                        int newborn, int64_t first_draw,
                        const double* draws, int64_t n_draws,

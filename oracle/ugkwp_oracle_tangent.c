@@ -366,6 +366,7 @@ int or_step_tangent(const or_problem* P, int64_t step, const double* ds,
   if (P->tau_num_C > 0.0) return OR_ERR_ARG;   /* tangent of tau = tau_num only */
   if (P->sig_law != 0) return OR_ERR_ARG;      /* and of the power-law opacity */
   if (P->method != OR_UGKWP) return OR_ERR_ARG;  /* and of the UGKWP sampling */
+  if (P->dim == 3) return OR_ERR_ARG;           /* in 1D and 2D */
   if (P->cv_law != 0) return OR_ERR_ARG;        /* and of a constant heat capacity */
 
   /* births: N and e as the step takes them, and d(E/N) per bin */

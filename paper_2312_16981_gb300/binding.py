@@ -180,7 +180,7 @@ class _HostProblem:
             return a.ctypes.data_as(_dp)
 
         s = CProblem()
-        s.dim, s.nx, s.ny, s.G = p.dim, p.nx, (p.ny if p.dim == 2 else 1), p.G
+        s.dim, s.nx, s.ny, s.G = p.dim, p.nx, (p.ny if p.dim >= 2 else 1), p.G
         s.grey, s.wave_order, s.si_max_iters, s.precision = p.grey, p.wave_order, p.si_max_iters, p.precision
         for i in range(4):
             s.bc[i] = int(p.bc[i])

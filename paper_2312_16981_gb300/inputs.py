@@ -56,6 +56,8 @@ class Problem:
     tau_num_C: float = 0.0   # thin/thick joint sampling constant C of tau_num (0: off)
     sig_law: int = 0         # 0: sigma0 nu^p T^q; 1: times (1 - e^{-nu/T}) (Larsen case)
     method: int = 0          # 0: UGKWP (sample the collisionless part); 1: UGKP (sample all of I^h)
+    nz: int = 1              # 3D: cells along z (dim 3); sides 4, 5 of bc/bcT are z- and z+
+    dz: float = 1.0
     omega_ref: float = 1e-6
     seed: int = 0
     instance: int = 0
@@ -69,14 +71,17 @@ class Problem:
 
     @property
     def ncell(self) -> int:
-        return self.nx * (self.ny if self.dim == 2 else 1)
+        return self.nx * (self.ny if self.dim >= 2 else 1) * (self.nz if self.dim == 3 else 1)
 
     @property
     def nface(self) -> int:
-        ny = self.ny if self.dim == 2 else 1
-        n = (self.nx + 1) * ny
-        if self.dim == 2:
-            n += self.nx * (self.ny + 1)
+        ny = self.ny if self.dim >= 2 else 1
+        nz = self.nz if self.dim == 3 else 1
+        n = (self.nx + 1) * ny * nz
+        if self.dim >= 2:
+            n += self.nx * (ny + 1) * nz
+        if self.dim == 3:
+            n += self.nx * ny * (nz + 1)
         return n
 
     @property
@@ -146,6 +151,30 @@ def checkerboard_2d(n: int = 256, G: int = 30, block: int = 16, patch: int = 32,
         bc=[BC_REFLECT] * 4, bcT=[0.0] * 4, omega_ref=omega_ref, seed=seed,
         n_steps=steps, precision=precision, name="checkerboard_%dx%dx%d" % (n, n, G),
         particle_capacity=1 << 25)
+
+
+def checkerboard_3d(n: int = 32, G: int = 8, block: int = 8, patch: int = 8,
+                    steps: int = 20, omega_ref: float = 1e-8, seed: int = 0,
+                    precision: int = FP64) -> Problem:
+    """3D [0,1]^3 checkerboard of block^3 cells alternating sigma0 = 1e3 and 1
+    (the 2D checkerboard's law, groups and source extended by a z axis):
+    central patch^3 T_s = 1 source, T0 = 1e-3, reflecting walls on all six
+    sides, dt = dx/c."""
+    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    thick = ((ix // block) + (iy // block) + (iz // block)) % 2 == 0
+    # cell order c = (iz n + iy) n + ix
+    sig0 = np.where(thick, 1e3, 1.0).transpose(2, 1, 0).reshape(-1).astype(np.float64)
+    lo, hi = n // 2 - patch // 2, n // 2 + patch // 2
+    src = np.zeros((n, n, n))
+    src[lo:hi, lo:hi, lo:hi] = 1.0
+    dx = 1.0 / n
+    return Problem(
+        dim=3, nx=n, ny=n, nz=n, dx=dx, dy=dx, dz=dx, G=G, grey=0,
+        nu_edges=log_groups(G, 1e-3, 10.0), sigma0=sig0, cv=np.ones(n ** 3),
+        T0=np.full(n ** 3, 1e-3), dt=dx, src_T=src.reshape(-1), src_on=1.0,
+        bc=[BC_REFLECT] * 6, bcT=[0.0] * 6, omega_ref=omega_ref, seed=seed,
+        n_steps=steps, precision=precision, name="checkerboard3d_%dx%dx%dx%d" % (n, n, n, G),
+        particle_capacity=1 << 22)
 
 
 def adjoint_grid(n: int = 128, G: int = 16, patch: int = 16, steps: int = 200,
