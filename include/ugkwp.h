@@ -19,9 +19,11 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued asynchronously; only ugkwp_tallies, ugkwp_get_state and
  *    ugkwp_set_state synchronise the stream.
- *  - Layout: cells c = iy*nx + ix; per (cell, group) arrays [c*G + g];
- *    x-faces f = iy*(nx+1) + fx (at x = fx*dx), then y-faces nxface + fy*nx + ix;
- *    sides 0 = x-, 1 = x+, 2 = y-, 3 = y+.  Normalised units h = k = 1.
+ *  - Layout: cells c = (iz*ny + iy)*nx + ix (ny = 1 in 1D, nz = 1 below 3D);
+ *    per (cell, group) arrays [c*G + g]; x-faces f = (iz*ny + iy)*(nx+1) + fx
+ *    (at x = fx*dx), then y-faces nxface + (iz*(ny+1) + fy)*nx + ix, then
+ *    z-faces nxface + nyface + (fz*ny + iy)*nx + ix; sides 0 = x-, 1 = x+,
+ *    2 = y-, 3 = y+, 4 = z-, 5 = z+.  Normalised units h = k = 1.
  *  - Errors found on the device during a step (particle capacity exceeded,
  *    source iteration not converged, non-finite state, a bounded wait that
  *    timed out) are latched in a status word and returned by ugkwp_tallies.
@@ -87,7 +89,7 @@ enum { UGKWP_METHOD_UGKWP = 0, UGKWP_METHOD_UGKP = 1 };
  *   |T_c - T_n|/(T_c + T_n) over a cell's interior faces, replaces tau in the
  *   sampled fraction e = exp(-dt/tau_num) (births and wave flux); 0 keeps tau. */
 typedef struct ugkwp_problem {
-  int32_t dim;            /* 1 or 2 */
+  int32_t dim;            /* 1, 2 or 3 */
   int32_t nx, ny;         /* cells; ny ignored (1) in 1D */
   int32_t G;              /* groups, 1..64 */
   int32_t grey;           /* 1: grey (G == 1) */
@@ -119,6 +121,13 @@ typedef struct ugkwp_problem {
   int32_t cv_law;              /* 0: constant cv; 1: Olson foam heat capacity (Eq. cvolson) */
   int32_t _pad2;
   double cv_chi;               /* chi of cv_law 1 */
+  /* 3D (dim 3): cells along z, the z sides (4: z-, 5: z+; reflecting or
+   * vacuum) and the cell height.  Ignored for dim 1 and 2. */
+  int32_t nz;
+  int32_t bc_z[2];
+  int32_t _pad3;
+  double dz;
+  double bcT_z[2];
 } ugkwp_problem;
 
 typedef struct ugkwp_handle ugkwp_handle;
@@ -133,8 +142,8 @@ typedef struct ugkwp_tally_report {
   const double* W;        /* [ncell*G] w^{fr,p}, particle energy in minus out (Eq. wfrpFormula) */
   const double* Fwave;    /* [nface*G] wave-part flux F^{fr,wave} */
   const double* Feq;      /* [nface*G] equilibrium flux of the last source iterate */
-  const double* esc;      /* [4*G] particle energy escaped per side */
-  const double* inflow;   /* [4*G] particle energy entering per side */
+  const double* esc;      /* [6*G] particle energy escaped per side (x-, x+, y-, y+, z-, z+) */
+  const double* inflow;   /* [6*G] particle energy entering per side */
   int64_t step;           /* steps completed */
   int64_t n_particles;    /* particles alive after the last step */
   int64_t n_in, n_born, n_survived, n_absorbed, n_escaped, n_removed, n_segments;
@@ -150,6 +159,7 @@ typedef struct ugkwp_particles_host {
   double *x, *y, *ox, *oy, *nu, *w;
   uint64_t* id;
   int32_t *cell, *grp;
+  double *z, *oz;         /* dim 3 only (may be NULL otherwise) */
 } ugkwp_particles_host;
 
 /* Per-particle end record written when a record buffer is attached
@@ -160,6 +170,7 @@ typedef struct ugkwp_record {
   int32_t fate;           /* 0 survived, 1 absorbed (collided), 2 escaped, 3 removed */
   int32_t cell0, cell1, grp, nseg, _pad;
   double x, y, ox, oy, nu, w, t_end;
+  double z, oz;           /* dim 3 (0 otherwise) */
 } ugkwp_record;
 
 /* Workspace bytes for problem p (256-byte aligned pieces). */

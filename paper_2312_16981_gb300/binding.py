@@ -48,6 +48,8 @@ class CProblem(C.Structure):
         ("src_T", _dp),
         ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
         ("cv_chi", C.c_double),
+        ("nz", C.c_int32), ("bc_z", C.c_int32 * 2), ("_pad3", C.c_int32), ("dz", C.c_double),
+        ("bcT_z", C.c_double * 2),
     ]
 
 
@@ -69,14 +71,15 @@ class CTallyReport(C.Structure):
 class CParticlesHost(C.Structure):
     _fields_ = [("x", _dp), ("y", _dp), ("ox", _dp), ("oy", _dp), ("nu", _dp), ("w", _dp),
                 ("id", C.POINTER(C.c_uint64)), ("cell", C.POINTER(C.c_int32)),
-                ("grp", C.POINTER(C.c_int32))]
+                ("grp", C.POINTER(C.c_int32)), ("z", _dp), ("oz", _dp)]
 
 
 RECORD = np.dtype([
     ("id", np.uint64), ("fate", np.int32), ("cell0", np.int32), ("cell1", np.int32),
     ("grp", np.int32), ("nseg", np.int32), ("_pad", np.int32),
     ("x", np.float64), ("y", np.float64), ("ox", np.float64), ("oy", np.float64),
-    ("nu", np.float64), ("w", np.float64), ("t_end", np.float64)])
+    ("nu", np.float64), ("w", np.float64), ("t_end", np.float64),
+    ("z", np.float64), ("oz", np.float64)])
 
 FUNCTIONS = {
     "ugkwp_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -204,6 +207,12 @@ class _HostProblem:
         s.src_t_end = float(getattr(p, "src_t_end", 0.0))
         s.cv_law = int(getattr(p, "cv_law", 0))
         s.cv_chi = float(getattr(p, "cv_chi", 0.0))
+        s.nz = int(p.nz) if p.dim == 3 else 1
+        s.dz = float(p.dz) if p.dim == 3 else 1.0
+        bc = list(p.bc) + [0] * (6 - len(p.bc))
+        bcT = list(p.bcT) + [0.0] * (6 - len(p.bcT))
+        s.bc_z[0], s.bc_z[1] = int(bc[4]), int(bc[5])
+        s.bcT_z[0], s.bcT_z[1] = float(bcT[4]), float(bcT[5])
         self.s = s
         self._keep = keep
 
@@ -295,8 +304,8 @@ class Simulation:
         r = self.tallies()
         p = self.p
         n = {"T": p.ncell, "rho": p.ncell * p.G, "rho_h": p.ncell * p.G, "rho_p": p.ncell * p.G,
-             "W": p.ncell * p.G, "Fwave": p.nface * p.G, "Feq": p.nface * p.G, "esc": 4 * p.G,
-             "inflow": 4 * p.G}[name]
+             "W": p.ncell * p.G, "Fwave": p.nface * p.G, "Feq": p.nface * p.G, "esc": 6 * p.G,
+             "inflow": 6 * p.G}[name]
         off = r["ptr"][name] - _ptr(self.workspace)
         return self.workspace[off: off + 8 * n].view(torch.float64)
 
@@ -313,14 +322,15 @@ class Simulation:
                                         rho_h.ctypes.data_as(_dp), rho_p.ctypes.data_as(_dp), None, 0,
                                         C.byref(n), sp), self.h)
         m = n.value if cap is None else min(cap, n.value)
-        parts = {f: np.zeros(max(m, 1)) for f in ("x", "y", "ox", "oy", "nu", "w")}
+        parts = {f: np.zeros(max(m, 1)) for f in ("x", "y", "ox", "oy", "nu", "w", "z", "oz")}
         parts["id"] = np.zeros(max(m, 1), dtype=np.uint64)
         parts["cell"] = np.zeros(max(m, 1), dtype=np.int32)
         parts["grp"] = np.zeros(max(m, 1), dtype=np.int32)
         cs = CParticlesHost(*[parts[f].ctypes.data_as(_dp) for f in ("x", "y", "ox", "oy", "nu", "w")],
                             parts["id"].ctypes.data_as(C.POINTER(C.c_uint64)),
                             parts["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
-                            parts["grp"].ctypes.data_as(C.POINTER(C.c_int32)))
+                            parts["grp"].ctypes.data_as(C.POINTER(C.c_int32)),
+                            parts["z"].ctypes.data_as(_dp), parts["oz"].ctypes.data_as(_dp))
         if m > 0:
             _check(L.ugkwp_get_state_member(self.h, member, None, None, None, None, C.byref(cs), m,
                                             C.byref(n), sp), self.h)
@@ -338,8 +348,11 @@ class Simulation:
         cs = None
         if n:
             arrs = {}
-            for f in ("x", "y", "ox", "oy", "nu", "w"):
-                arrs[f] = np.ascontiguousarray(particles[f], dtype=np.float64)
+            for f in ("x", "y", "ox", "oy", "nu", "w", "z", "oz"):
+                if f in particles:
+                    arrs[f] = np.ascontiguousarray(particles[f], dtype=np.float64)
+                else:
+                    arrs[f] = np.zeros(n)
             arrs["id"] = np.ascontiguousarray(particles["id"], dtype=np.uint64)
             arrs["cell"] = np.ascontiguousarray(particles["cell"], dtype=np.int32)
             arrs["grp"] = np.ascontiguousarray(particles["grp"], dtype=np.int32)
@@ -347,7 +360,8 @@ class Simulation:
             cs = CParticlesHost(*[arrs[f].ctypes.data_as(_dp) for f in ("x", "y", "ox", "oy", "nu", "w")],
                                 arrs["id"].ctypes.data_as(C.POINTER(C.c_uint64)),
                                 arrs["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
-                                arrs["grp"].ctypes.data_as(C.POINTER(C.c_int32)))
+                                arrs["grp"].ctypes.data_as(C.POINTER(C.c_int32)),
+                                arrs["z"].ctypes.data_as(_dp), arrs["oz"].ctypes.data_as(_dp))
         _check(L.ugkwp_set_state_member(self.h, member, T.ctypes.data_as(_dp), rho.ctypes.data_as(_dp),
                                         rho_h.ctypes.data_as(_dp), None if cs is None else C.byref(cs), n,
                                         int(step), C.c_void_p(_stream_ptr(self.stream))), self.h)

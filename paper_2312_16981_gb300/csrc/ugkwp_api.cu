@@ -51,19 +51,28 @@ int cuda_fail(ugkwp_handle* h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
-long long ncell_of(const ugkwp_problem* p) { return (long long)p->nx * (p->dim == 2 ? p->ny : 1); }
-long long nxface_of(const ugkwp_problem* p) { return (long long)(p->nx + 1) * (p->dim == 2 ? p->ny : 1); }
+long long ny_of(const ugkwp_problem* p) { return p->dim >= 2 ? p->ny : 1; }
+long long nz_of(const ugkwp_problem* p) { return p->dim == 3 ? p->nz : 1; }
+long long ncell_of(const ugkwp_problem* p) { return (long long)p->nx * ny_of(p) * nz_of(p); }
+long long nxface_of(const ugkwp_problem* p) { return (long long)(p->nx + 1) * ny_of(p) * nz_of(p); }
+long long nyface_of(const ugkwp_problem* p) {
+  return p->dim >= 2 ? (long long)p->nx * (ny_of(p) + 1) * nz_of(p) : 0;
+}
 long long nface_of(const ugkwp_problem* p) {
-  return nxface_of(p) + (p->dim == 2 ? (long long)p->nx * (p->ny + 1) : 0);
+  return nxface_of(p) + nyface_of(p) + (p->dim == 3 ? (long long)p->nx * ny_of(p) * (nz_of(p) + 1) : 0);
 }
 
 int validate(const ugkwp_problem* p, ugkwp_handle* h) {
   if (!p) return fail(h, UGKWP_ERR_ARG, "problem is NULL");
-  if (p->dim != 1 && p->dim != 2) return fail(h, UGKWP_ERR_ARG, "dim must be 1 or 2");
-  if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) return fail(h, UGKWP_ERR_ARG, "nx, ny must be >= 1");
+  if (p->dim < 1 || p->dim > 3) return fail(h, UGKWP_ERR_ARG, "dim must be 1, 2 or 3");
+  if (p->nx < 1 || (p->dim >= 2 && p->ny < 1) || (p->dim == 3 && p->nz < 1))
+    return fail(h, UGKWP_ERR_ARG, "nx, ny, nz must be >= 1");
+  if (ncell_of(p) * (long long)(p->G > 0 ? p->G : 1) >= (1ll << 31))
+    return fail(h, UGKWP_ERR_ARG, "ncell*G must be < 2^31");
   if (p->G < 1 || p->G > ugkwp::kMaxG) return fail(h, UGKWP_ERR_ARG, "G must be in 1..64");
   if (p->grey && p->G != 1) return fail(h, UGKWP_ERR_ARG, "grey requires G == 1");
-  if (!(p->dx > 0) || (p->dim == 2 && !(p->dy > 0))) return fail(h, UGKWP_ERR_ARG, "dx, dy must be > 0");
+  if (!(p->dx > 0) || (p->dim >= 2 && !(p->dy > 0)) || (p->dim == 3 && !(p->dz > 0)))
+    return fail(h, UGKWP_ERR_ARG, "dx, dy, dz must be > 0");
   if (!(p->dt > 0) || !(p->c > 0) || !(p->eps > 0) || !(p->a > 0))
     return fail(h, UGKWP_ERR_ARG, "dt, c, eps, a must be > 0");
   if (!p->sigma0 || !p->cv || !p->T0) return fail(h, UGKWP_ERR_ARG, "sigma0, cv, T0 are required");
@@ -72,9 +81,15 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
     if (p->bc[s] < 0 || p->bc[s] > 2) return fail(h, UGKWP_ERR_ARG, "bad boundary condition");
     if (p->dim == 1 && s < 2 && p->bc[s] == UGKWP_BC_BLACKBODY && !(p->bcT[s] > 0))
       return fail(h, UGKWP_ERR_ARG, "black-body side needs bcT > 0");
-    if (p->dim == 2 && p->bc[s] == UGKWP_BC_BLACKBODY)
+    if (p->dim >= 2 && p->bc[s] == UGKWP_BC_BLACKBODY)
       return fail(h, UGKWP_ERR_UNSUPPORTED, "black-body sides are 1D only in this build");
   }
+  if (p->dim == 3)
+    for (int s = 0; s < 2; ++s) {
+      if (p->bc_z[s] < 0 || p->bc_z[s] > 2) return fail(h, UGKWP_ERR_ARG, "bad boundary condition");
+      if (p->bc_z[s] == UGKWP_BC_BLACKBODY)
+        return fail(h, UGKWP_ERR_UNSUPPORTED, "black-body sides are 1D only in this build");
+    }
   if (p->wave_order != 1 && p->wave_order != 2) return fail(h, UGKWP_ERR_ARG, "wave_order must be 1 or 2");
   if (p->si_max_iters < 1) return fail(h, UGKWP_ERR_ARG, "si_max_iters must be >= 1");
   if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED)
@@ -114,8 +129,8 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.sigma0 = cv.take<double>(nc);
   d.cv = cv.take<double>(nc);
   d.src = p->src_T ? cv.take<double>(ncg) : nullptr;
-  d.ghost_phi = cv.take<double>(4 * G);
-  d.ghost_sig = cv.take<double>(4 * G);
+  d.ghost_phi = cv.take<double>(6 * G);
+  d.ghost_sig = cv.take<double>(6 * G);
   d.T = cv.take<double>(nc);
   d.rho = cv.take<double>(ncg);
   d.rho_h = cv.take<double>(ncg);
@@ -134,8 +149,8 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.E_surv = cv.take<double>(ncg);
   d.Wq = cv.take<unsigned long long>(2 * ncg);
   d.Esq = cv.take<unsigned long long>(2 * ncg);
-  d.esc = cv.take<double>(4 * G);
-  d.inflow = cv.take<double>(4 * G);
+  d.esc = cv.take<double>(6 * G);
+  d.inflow = cv.take<double>(6 * G);
   d.Fwave = cv.take<double>(nf * G);
   d.Feq = cv.take<double>(nf * G);
   d.R = cv.take<double>(ncg);
@@ -165,20 +180,24 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
       d.fx[b] = cv.take<float>(P);
       if (!b) d.particles_begin = d.fx[0];
       d.fox[b] = cv.take<float>(P);
-      d.fy[b] = p->dim == 2 ? cv.take<float>(P) : nullptr;
-      d.foy[b] = p->dim == 2 ? cv.take<float>(P) : nullptr;
+      d.fy[b] = p->dim >= 2 ? cv.take<float>(P) : nullptr;
+      d.foy[b] = p->dim >= 2 ? cv.take<float>(P) : nullptr;
+      d.fz[b] = p->dim == 3 ? cv.take<float>(P) : nullptr;
+      d.foz[b] = p->dim == 3 ? cv.take<float>(P) : nullptr;
       d.fnu[b] = cv.take<float>(P);
       d.fw[b] = cv.take<float>(P);
-      d.px[b] = d.pox[b] = d.py[b] = d.poy[b] = d.pnu[b] = d.pw[b] = nullptr;
+      d.px[b] = d.pox[b] = d.py[b] = d.poy[b] = d.pz[b] = d.poz[b] = d.pnu[b] = d.pw[b] = nullptr;
     } else {
       d.px[b] = cv.take<double>(P);
       if (!b) d.particles_begin = d.px[0];
       d.pox[b] = cv.take<double>(P);
-      d.py[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
-      d.poy[b] = p->dim == 2 ? cv.take<double>(P) : nullptr;
+      d.py[b] = p->dim >= 2 ? cv.take<double>(P) : nullptr;
+      d.poy[b] = p->dim >= 2 ? cv.take<double>(P) : nullptr;
+      d.pz[b] = p->dim == 3 ? cv.take<double>(P) : nullptr;
+      d.poz[b] = p->dim == 3 ? cv.take<double>(P) : nullptr;
       d.pnu[b] = cv.take<double>(P);
       d.pw[b] = cv.take<double>(P);
-      d.fx[b] = d.fox[b] = d.fy[b] = d.foy[b] = d.fnu[b] = d.fw[b] = nullptr;
+      d.fx[b] = d.fox[b] = d.fy[b] = d.foy[b] = d.fz[b] = d.foz[b] = d.fnu[b] = d.fw[b] = nullptr;
     }
     d.pid[b] = cv.take<unsigned long long>(P);
     d.pkey[b] = cv.take<uint32_t>(P);
@@ -188,7 +207,9 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
 void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.dim = p->dim;
   d.nx = p->nx;
-  d.ny = p->dim == 2 ? p->ny : 1;
+  d.ny = (int)ny_of(p);
+  d.nz = (int)nz_of(p);
+  d.nyface = (int)nyface_of(p);
   d.G = p->G;
   d.ncell = (int)ncell_of(p);
   d.nbins = (d.ncell + 4) * p->G;
@@ -199,9 +220,17 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.si_max_iters = p->si_max_iters;
   d.precision = p->precision;
   for (int s = 0; s < 4; ++s) { d.bc[s] = p->bc[s]; d.bcT[s] = p->bcT[s]; }
+  for (int s = 0; s < 2; ++s) {
+    d.bc[4 + s] = p->dim == 3 ? p->bc_z[s] : ugkwp::BC_REFLECT;
+    d.bcT[4 + s] = p->dim == 3 ? p->bcT_z[s] : 0.0;
+  }
   d.dx = p->dx;
-  d.dy = p->dim == 2 ? p->dy : 1.0;
-  d.vol = p->dim == 2 ? p->dx * p->dy : p->dx;
+  d.dy = p->dim >= 2 ? p->dy : 1.0;
+  d.dz = p->dim == 3 ? p->dz : 1.0;
+  d.vol = p->dx * (p->dim >= 2 ? p->dy : 1.0) * (p->dim == 3 ? p->dz : 1.0);
+  if (p->dim == 1) { d.area[0] = d.area[1] = d.area[2] = 1.0; }
+  else if (p->dim == 2) { d.area[0] = d.dy; d.area[1] = d.dx; d.area[2] = 1.0; }
+  else { d.area[0] = d.dy * d.dz; d.area[1] = d.dx * d.dz; d.area[2] = d.dx * d.dy; }
   d.sig_p = p->grey ? 0.0 : p->sig_p;
   d.sig_q = p->sig_law == 2 ? 0.0 : p->sig_q;   // the foam law has no T^q factor
   d.sig_cap = p->sig_cap;
@@ -213,6 +242,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.v = p->c / p->eps;
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;
+  d.inv_dz = 1.0 / d.dz;
   d.inv_c = 1.0 / p->c;
   d.inv_vol = 1.0 / d.vol;
   d.rate_f = p->c / (p->eps * p->eps);
@@ -236,6 +266,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   // FP32 copies for the mixed-precision particle kernel
   d.dxf = (float)d.dx;
   d.dyf = (float)d.dy;
+  d.dzf = (float)d.dz;
   d.vf = (float)d.v;
   d.dtf = (float)d.dt;
   d.inv_rate_f = (float)(p->eps * p->eps / p->c);
@@ -287,6 +318,8 @@ int validate_members(const ugkwp_problem* probs, int M) {
       return fail(nullptr, UGKWP_ERR_ARG, "ensemble members must share dim and precision");
     if (probs[m].si_max_iters != probs[0].si_max_iters)
       return fail(nullptr, UGKWP_ERR_ARG, "ensemble members must share si_max_iters");
+    if (M > 1 && probs[m].dim == 3)
+      return fail(nullptr, UGKWP_ERR_UNSUPPORTED, "ensembles are built for 1D and 2D members");
   }
   return UGKWP_OK;
 }
@@ -562,15 +595,20 @@ int ugkwp_get_state_member(ugkwp_handle* h, int member, double* T, double* rho, 
     const unsigned b = c.cur;
     std::vector<uint32_t> key(m > 0 ? m : 1);
     const bool mixed = d.precision == UGKWP_MIXED;
-    std::vector<float> fb(mixed && m > 0 ? (size_t)m * 6 : 1);
+    if (d.dim == 3 && (!parts->z || !parts->oz)) return fail(h, UGKWP_ERR_ARG, "3D particles need z and oz");
+    std::vector<float> fb(mixed && m > 0 ? (size_t)m * 8 : 1);
     if (m > 0 && !mixed) {
       CK(cudaMemcpyAsync(parts->x, d.px[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(parts->ox, d.pox[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(parts->nu, d.pnu[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(parts->w, d.pw[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
-      if (d.dim == 2) {
+      if (d.dim >= 2) {
         CK(cudaMemcpyAsync(parts->y, d.py[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
         CK(cudaMemcpyAsync(parts->oy, d.poy[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+      }
+      if (d.dim == 3) {
+        CK(cudaMemcpyAsync(parts->z, d.pz[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
+        CK(cudaMemcpyAsync(parts->oz, d.poz[b], sizeof(double) * m, cudaMemcpyDeviceToHost, s), h);
       }
     } else if (m > 0) {
       float* f = fb.data();
@@ -578,9 +616,13 @@ int ugkwp_get_state_member(ugkwp_handle* h, int member, double* T, double* rho, 
       CK(cudaMemcpyAsync(f + m, d.fox[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(f + 2 * m, d.fnu[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
       CK(cudaMemcpyAsync(f + 3 * m, d.fw[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
-      if (d.dim == 2) {
+      if (d.dim >= 2) {
         CK(cudaMemcpyAsync(f + 4 * m, d.fy[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
         CK(cudaMemcpyAsync(f + 5 * m, d.foy[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+      }
+      if (d.dim == 3) {
+        CK(cudaMemcpyAsync(f + 6 * m, d.fz[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
+        CK(cudaMemcpyAsync(f + 7 * m, d.foz[b], sizeof(float) * m, cudaMemcpyDeviceToHost, s), h);
       }
     }
     if (m > 0) {
@@ -594,16 +636,24 @@ int ugkwp_get_state_member(ugkwp_handle* h, int member, double* T, double* rho, 
       parts->grp[i] = (int32_t)(key[i] % (uint32_t)d.G);
       if (mixed) {
         const float* f = fb.data();
-        const int ix = cell % d.nx, iy = cell / d.nx;
+        const int ix = cell % d.nx, iy = (cell / d.nx) % d.ny, iz = cell / (d.nx * d.ny);
         parts->x[i] = ix * d.dx + (double)f[i];
         parts->ox[i] = f[m + i];
         parts->nu[i] = f[2 * m + i];
         parts->w[i] = f[3 * m + i];
-        parts->y[i] = d.dim == 2 ? iy * d.dy + (double)f[4 * m + i] : 0.0;
-        parts->oy[i] = d.dim == 2 ? (double)f[5 * m + i] : 0.0;
+        parts->y[i] = d.dim >= 2 ? iy * d.dy + (double)f[4 * m + i] : 0.0;
+        parts->oy[i] = d.dim >= 2 ? (double)f[5 * m + i] : 0.0;
+        if (d.dim == 3) {
+          parts->z[i] = iz * d.dz + (double)f[6 * m + i];
+          parts->oz[i] = (double)f[7 * m + i];
+        }
       } else if (d.dim == 1) {
         parts->y[i] = 0.0;
         parts->oy[i] = 0.0;
+      }
+      if (d.dim < 3) {
+        if (parts->z) parts->z[i] = 0.0;
+        if (parts->oz) parts->oz[i] = 0.0;
       }
     }
   }
@@ -635,35 +685,47 @@ int ugkwp_set_state_member(ugkwp_handle* h, int member, const double* T, const d
       return fail(h, UGKWP_ERR_ARG, "particle cell or group out of range");
     key[i] = (uint32_t)(parts->cell[i] * d.G + parts->grp[i]);
   }
-  std::vector<float> fb(d.precision == UGKWP_MIXED && n > 0 ? (size_t)n * 6 : 1);
+  if (n > 0 && d.dim == 3 && (!parts->z || !parts->oz)) return fail(h, UGKWP_ERR_ARG, "3D particles need z and oz");
+  std::vector<float> fb(d.precision == UGKWP_MIXED && n > 0 ? (size_t)n * 8 : 1);
   if (n > 0 && d.precision != UGKWP_MIXED) {
     CK(cudaMemcpyAsync(d.px[0], parts->x, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.pox[0], parts->ox, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.pnu[0], parts->nu, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.pw[0], parts->w, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
-    if (d.dim == 2) {
+    if (d.dim >= 2) {
       CK(cudaMemcpyAsync(d.py[0], parts->y, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
       CK(cudaMemcpyAsync(d.poy[0], parts->oy, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+    }
+    if (d.dim == 3) {
+      CK(cudaMemcpyAsync(d.pz[0], parts->z, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
+      CK(cudaMemcpyAsync(d.poz[0], parts->oz, sizeof(double) * n, cudaMemcpyHostToDevice, s), h);
     }
   } else if (n > 0) {
     // positions relative to the particle's cell, in FP32
     float* f = fb.data();
     for (long long i = 0; i < n; ++i) {
-      const int ix = parts->cell[i] % d.nx, iy = parts->cell[i] / d.nx;
+      const int cell = parts->cell[i];
+      const int ix = cell % d.nx, iy = (cell / d.nx) % d.ny, iz = cell / (d.nx * d.ny);
       f[i] = (float)(parts->x[i] - ix * d.dx);
       f[n + i] = (float)parts->ox[i];
       f[2 * n + i] = (float)parts->nu[i];
       f[3 * n + i] = (float)parts->w[i];
-      f[4 * n + i] = d.dim == 2 ? (float)(parts->y[i] - iy * d.dy) : 0.0f;
-      f[5 * n + i] = d.dim == 2 ? (float)parts->oy[i] : 0.0f;
+      f[4 * n + i] = d.dim >= 2 ? (float)(parts->y[i] - iy * d.dy) : 0.0f;
+      f[5 * n + i] = d.dim >= 2 ? (float)parts->oy[i] : 0.0f;
+      f[6 * n + i] = d.dim == 3 ? (float)(parts->z[i] - iz * d.dz) : 0.0f;
+      f[7 * n + i] = d.dim == 3 ? (float)parts->oz[i] : 0.0f;
     }
     CK(cudaMemcpyAsync(d.fx[0], f, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.fox[0], f + n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.fnu[0], f + 2 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
     CK(cudaMemcpyAsync(d.fw[0], f + 3 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
-    if (d.dim == 2) {
+    if (d.dim >= 2) {
       CK(cudaMemcpyAsync(d.fy[0], f + 4 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
       CK(cudaMemcpyAsync(d.foy[0], f + 5 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+    }
+    if (d.dim == 3) {
+      CK(cudaMemcpyAsync(d.fz[0], f + 6 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
+      CK(cudaMemcpyAsync(d.foz[0], f + 7 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), h);
     }
   }
   if (n > 0) {
@@ -825,6 +887,7 @@ int adjoint_check(ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint takes a constant heat capacity (cv_law = 0)");
   if (h->d.method != UGKWP_METHOD_UGKWP)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the UGKWP sampling (method = 0)");
+  if (h->d.dim == 3) return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint is built for 1D and 2D grids");
   return UGKWP_OK;
 }
 }  // namespace

@@ -213,16 +213,18 @@ struct DrawsF {
 struct Dev {
   // geometry / model
   int dim, nx, ny, G, ncell, nbins, nface, nxface;
+  int nz, nyface;    // nz = 1 below 3D; nyface = 0 in 1D
   int grey, wave_order, si_max_iters, precision, sig_law;
   int method;        // 0 UGKWP, 1 UGKP (all of I^h sampled; newborns draw t_f)
   int cv_law;        // 0 constant cv; 1 Olson foam heat capacity
   double cv_chi, src_t_end;
-  int bc[4];
-  double dx, dy, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
+  int bc[6];          // sides x-, x+, y-, y+, z-, z+
+  double dx, dy, dz, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
   double v;          // c/eps, particle speed
   double rate_f;     // c/eps^2: 1/tau = rate_f * sigma
   double omega_ref, si_tol, src_on, tau_num_C;
-  double bcT[4];
+  double bcT[6];
+  double area[3];    // face area normal to each axis (1D: 1; 2D: the other width)
   uint32_t key0, key1;
   PhiloxKeys pk;     // Philox round keys of (key0, key1)
   long long capacity;
@@ -231,8 +233,8 @@ struct Dev {
   const double* sigma0;     // [ncell]
   const double* cv;         // [ncell]
   const double* src;        // [ncell*G] per-step source increment of rho (or null)
-  const double* ghost_phi;  // [4*G] Phi_g(T_b) per side
-  const double* ghost_sig;  // [4*G] sigma_g(T_b) per side (sigma0 of the adjacent cell)
+  const double* ghost_phi;  // [6*G] Phi_g(T_b) per side
+  const double* ghost_sig;  // [6*G] sigma_g(T_b) per side (sigma0 of the adjacent cell)
   // state
   double* T;        // [ncell]   T^n, then T^{n+1}
   double* rho;      // [ncell*G] rho^n, then rho^{n+1}
@@ -253,17 +255,17 @@ struct Dev {
   double* E_surv;   // [ncell*G] (FP64 copy written by the source iteration)
   unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
   unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
-  double inv_dx, inv_dy, inv_c, inv_vol;
+  double inv_dx, inv_dy, inv_dz, inv_c, inv_vol;
   double inv_2dt;             // 1/(2 dt)
   double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-48) and its inverse
   int tq_shift;
   // FP32 copies of scalars (mixed-precision particle kernel)
-  float dxf, dyf, vf, dtf, inv_rate_f, capf, spf, inv_capf;
+  float dxf, dyf, dzf, vf, dtf, inv_rate_f, capf, spf, inv_capf;
   int fastdiv;               // ncell*G < 2^24: divide by G and nx with div_small
   float invG_f, inv_nx_f;    // 1/G, 1/nx in FP32
   double inv_cap;            // 1/sig_cap, or 0 without a cap
-  double* esc;      // [4*G]
-  double* inflow;   // [4*G]
+  double* esc;      // [6*G]
+  double* inflow;   // [6*G]
   double* Fwave;    // [nface*G]
   double* Feq;      // [nface*G]
   double* R;        // [ncell*G] constant part of the rho equation
@@ -278,6 +280,8 @@ struct Dev {
   double* py[2];
   double* pox[2];
   double* poy[2];
+  double* pz[2];        // 3D only
+  double* poz[2];
   double* pnu[2];
   double* pw[2];
   unsigned long long* pid[2];
@@ -287,6 +291,8 @@ struct Dev {
   float* fy[2];
   float* fox[2];
   float* foy[2];
+  float* fz[2];         // 3D only
+  float* foz[2];
   float* fnu[2];
   float* fw[2];
   double* olson_c;  // [3 ncell] foam opacity T factors A, B, C at T^n (sig_law 2)
@@ -381,6 +387,7 @@ struct RecordOut {
   unsigned long long id;
   int fate, cell0, cell1, grp, nseg, pad;
   double x, y, ox, oy, nu, w, t_end;
+  double z, oz;
 };
 
 // Adjoint tape entry of one processed particle: where its weight was counted

@@ -9,25 +9,56 @@ namespace ugkwp {
 
 // --------------------------------------------------------------------------
 // Face walk helpers: face f -> axis, the line of cells through it and its
-// position along the line.
+// position along the line.  A line of axis a is the set of cells sharing the
+// other two coordinates; its cells are base + k*stride, k = 0..nk-1.
 struct FaceRef {
-  int axis, line, k, nk;   // face between line cells k-1 and k, 0..nk
+  int axis, k, nk;   // face between line cells k-1 and k, 0..nk
+  int base, stride;
   double h;
 };
 
 __device__ __forceinline__ FaceRef face_ref(const Dev& d, int f) {
   FaceRef r;
   if (f < d.nxface) {
-    r.axis = 0; r.line = f / (d.nx + 1); r.k = f - r.line * (d.nx + 1); r.nk = d.nx; r.h = d.dx;
-  } else {
+    const int line = f / (d.nx + 1);
+    r.axis = 0; r.k = f - line * (d.nx + 1); r.nk = d.nx; r.h = d.dx;
+    r.base = line * d.nx; r.stride = 1;
+  } else if (f < d.nxface + d.nyface) {
+    // y-faces (iz (ny+1) + k) nx + ix
     const int q = f - d.nxface;
-    r.axis = 1; r.k = q / d.nx; r.line = q - r.k * d.nx; r.nk = d.ny; r.h = d.dy;
+    const int t = q / d.nx, ix = q - t * d.nx;
+    const int iz = d.nz > 1 ? t / (d.ny + 1) : 0;
+    r.axis = 1; r.k = t - iz * (d.ny + 1); r.nk = d.ny; r.h = d.dy;
+    r.base = iz * d.nx * d.ny + ix; r.stride = d.nx;
+  } else {
+    // z-faces k nx ny + (iy nx + ix)
+    const int q = f - d.nxface - d.nyface, nxy = d.nx * d.ny;
+    r.axis = 2; r.k = q / nxy; r.nk = d.nz; r.h = d.dz;
+    r.base = q - r.k * nxy; r.stride = nxy;
   }
   return r;
 }
 
 __device__ __forceinline__ int line_cell(const Dev& d, const FaceRef& r, int k) {
-  return r.axis == 0 ? r.line * d.nx + k : k * d.nx + r.line;
+  (void)d;
+  return r.base + k * r.stride;
+}
+
+__device__ __forceinline__ double inv_h_of(const Dev& d, int axis) {
+  return axis == 0 ? d.inv_dx : (axis == 1 ? d.inv_dy : d.inv_dz);
+}
+
+// cell c -> (ix, iy, iz)
+__device__ __forceinline__ void cell_xyz(const Dev& d, int c, int* ix, int* iy, int* iz) {
+  if (d.nz > 1) {
+    const int nxy = d.nx * d.ny;
+    *iz = c / nxy;
+    c -= *iz * nxy;
+  } else {
+    *iz = 0;
+  }
+  *iy = c / d.nx;
+  *ix = c - *iy * d.nx;
 }
 
 // rho_h at line position k including ghosts (mirror / black body / vacuum)
@@ -116,10 +147,14 @@ __device__ __forceinline__ void tau_and_q(const Dev& d, double sig, double* tau,
   *q = A * A * P;
 }
 
+// the face of cell c on `axis`, lower (dir < 0) or upper side
 __device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {
-  const int ix = c % d.nx, iy = c / d.nx;
-  if (axis == 0) return iy * (d.nx + 1) + ix + (dir > 0 ? 1 : 0);
-  return d.nxface + (iy + (dir > 0 ? 1 : 0)) * d.nx + ix;
+  int ix, iy, iz;
+  cell_xyz(d, c, &ix, &iy, &iz);
+  const int up = dir > 0 ? 1 : 0;
+  if (axis == 0) return (iz * d.ny + iy) * (d.nx + 1) + ix + up;
+  if (axis == 1) return d.nxface + (iz * (d.ny + 1) + iy + up) * d.nx + ix;
+  return d.nxface + d.nyface + ((iz + up) * d.ny + iy) * d.nx + ix;
 }
 
 }  // namespace ugkwp

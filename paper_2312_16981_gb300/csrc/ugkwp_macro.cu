@@ -61,7 +61,7 @@ __global__ void k_init_tables(Dev d, const double* src_T, const double* src_amp,
       const_cast<double*>(d.src)[i] = d.src_on * (src_amp ? src_amp[c] : 1.0) * d.c * d.dt * p;
     }
   }
-  for (int i = tid; i < 4 * d.G; i += stride) {
+  for (int i = tid; i < 6 * d.G; i += stride) {
     const int side = i / d.G, g = i - side * d.G;
     double p = 0.0, s = 0.0;
     if (d.bc[side] == BC_BLACKBODY) {
@@ -141,6 +141,10 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
       const int side = cell - d.ncell;
       d.esc[side * G + g] = 0.0;
       d.inflow[side * G + g] = 0.0;
+      if (side < 2) {   // the z sides' tallies (bins hold four ghost slots)
+        d.esc[(side + 4) * G + g] = 0.0;
+        d.inflow[(side + 4) * G + g] = 0.0;
+      }
       if (d.dim != 1 || side > 1 || d.bc[side] != BC_BLACKBODY) {
         d.N[b] = 0; d.omega[b] = 0.0; d.e_eff[b] = 0.0; d.khat[b] = 0.0;
         if (d.omega_f) { d.omega_f[b] = 0.0f; d.khat_f[b] = 0.0f; }
@@ -155,12 +159,14 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     // interior faces; x = dt/tau when C = 0
     double x = d.dt * d.rate_f * sig;
     if (cell < d.ncell && d.tau_num_C > 0.0) {
-      const int ix = cell % d.nx, iy = cell / d.nx, nyy = d.dim == 2 ? d.ny : 1;
+      int ix, iy, iz;
+      cell_xyz(d, cell, &ix, &iy, &iz);
       double J = 0.0;
       for (int k = 0; k < 2 * d.dim; ++k) {
-        const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0)), jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-        if (jx < 0 || jx >= d.nx || jy < 0 || jy >= nyy) continue;
-        const double Tn = d.T[jy * d.nx + jx];
+        const int s = (k & 1) ? 1 : -1;
+        const int jx = ix + (k < 2 ? s : 0), jy = iy + (k >> 1 == 1 ? s : 0), jz = iz + (k >> 1 == 2 ? s : 0);
+        if (jx < 0 || jx >= d.nx || jy < 0 || jy >= d.ny || jz < 0 || jz >= d.nz) continue;
+        const double Tn = d.T[(jz * d.ny + jy) * d.nx + jx];
         J = fmax(J, fabs(Tb - Tn) / (Tb + Tn));
       }
       x = x / (1.0 + d.tau_num_C * J * x);
@@ -387,7 +393,7 @@ __global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
     double sl, sr, fl, fr;
     if (d.wave_order >= 2) {
       const double rll = rho_h_at(d, r, r.k - 2, g), rrr = rho_h_at(d, r, r.k + 1, g);
-      const double ih = r.axis == 0 ? d.inv_dx : d.inv_dy;
+      const double ih = inv_h_of(d, r.axis);
       sl = lin ? van_leer((rl - rll) * ih, (rr - rl) * ih) : 0.0;
       sr = rin ? van_leer((rr - rl) * ih, (rrr - rr) * ih) : 0.0;
       fl = rl + 0.5 * r.h * sl;
@@ -478,10 +484,10 @@ __device__ __forceinline__ double feq_face(const Dev& d, double tl, double tu, d
 // iterate k, or the ghost's.  Returns false for a reflecting wall (no flux).
 __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir, int g, int cur,
                                           double tau_c, double* tn, double* pn, int* nc) {
-  const int ix = c % d.nx, iy = c / d.nx;
-  const int jx = ix + (axis == 0 ? dir : 0), jy = iy + (axis == 1 ? dir : 0);
-  const int nyy = d.dim == 2 ? d.ny : 1;
-  if (jx < 0 || jx >= d.nx || jy < 0 || jy >= nyy) {
+  int ix, iy, iz;
+  cell_xyz(d, c, &ix, &iy, &iz);
+  const int jx = ix + (axis == 0 ? dir : 0), jy = iy + (axis == 1 ? dir : 0), jz = iz + (axis == 2 ? dir : 0);
+  if (jx < 0 || jx >= d.nx || jy < 0 || jy >= d.ny || jz < 0 || jz >= d.nz) {
     const int side = axis * 2 + (dir > 0 ? 1 : 0);
     *nc = -1 - side;
     if (d.bc[side] == BC_REFLECT) return false;
@@ -494,7 +500,7 @@ __device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir
     }
     return true;
   }
-  const int n = jy * d.nx + jx;
+  const int n = (jz * d.ny + jy) * d.nx + jx;
   *nc = n;
   *tn = __ldcg(d.tauk[cur] + n * d.G + g);
   *pn = __ldcg(d.phik[cur] + n * d.G + g);
@@ -538,7 +544,7 @@ __device__ __forceinline__ double face_feq(const Dev& d, int f, int g, int cur) 
       tu = tl;
     }
   }
-  return feq_face(d, tl, tu, pl, pu, r.axis == 0 ? d.inv_dx : d.inv_dy);
+  return feq_face(d, tl, tu, pl, pu, inv_h_of(d, r.axis));
 }
 
 // Source iteration (App. B, Algorithm 2) in 1D and 2D, one warp per cell and
@@ -594,9 +600,6 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int c = (int)(ENS ? gc - e.cell0[m] : gc);
       const int G = d.G;
       const double dt = d.dt, V = d.vol;
-      const int ix = c % d.nx, iy = c / d.nx;
-      const int fxl = iy * (d.nx + 1) + ix, fxr = fxl + 1;
-      const int fyl = d.nxface + iy * d.nx + ix, fyr = fyl + d.nx;
       // the source acts while t^n = n dt < src_t_end (src_t_end <= 0: always)
       const bool src_on = d.src && (!(d.src_t_end > 0.0) || (double)d.ctrl->step * dt < d.src_t_end);
 #pragma unroll
@@ -605,8 +608,11 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (g < G) {
           const int i = c * G + g;
           const double r0 = d.rho[i];
-          double r = r0 + (dt * d.inv_dx) * (d.Fwave[fxl * G + g] - d.Fwave[fxr * G + g]);
-          if (d.dim == 2) r += (dt * d.inv_dy) * (d.Fwave[fyl * G + g] - d.Fwave[fyr * G + g]);
+          double r = r0;
+          for (int axis = 0; axis < d.dim; ++axis) {
+            const int fl = face_index(d, c, axis, -1), fr = face_index(d, c, axis, +1);
+            r += (dt * inv_h_of(d, axis)) * (d.Fwave[fl * G + g] - d.Fwave[fr * G + g]);
+          }
           const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
           d.W[i] = Wd;
           r += Wd * d.inv_vol;
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   // faces (a face costs a division and the C2 interpolant in FP64, the
   // scarce unit on this chip; in 1D the extra barrier costs more than the
   // second evaluation of a face saves)
-  const bool face_pass = !ENS && d0.dim == 2;
+  const bool face_pass = !ENS && d0.dim >= 2;
   for (; it < max_it; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
     double werrT = 0.0, werrR = 0.0;
@@ -690,15 +696,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         dpc[j] = __ldcg(d.dphik + i);
         double q = d.R[i];
         if (face_pass) {
-          for (int axis = 0; axis < 2; ++axis) {
-            const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
+          for (int axis = 0; axis < d.dim; ++axis) {
+            const double inv_h = inv_h_of(d, axis);
             const double Fin = __ldcg(d.Feq + face_index(d, c, axis, -1) * G + g);
             const double Fout = __ldcg(d.Feq + face_index(d, c, axis, +1) * G + g);
             q += (dt * inv_h) * (Fin - Fout);
           }
         }
         for (int axis = 0; axis < (face_pass ? 0 : d.dim); ++axis) {
-          const double inv_h = axis == 0 ? d.inv_dx : d.inv_dy;
+          const double inv_h = inv_h_of(d, axis);
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
             double tn, pn;
@@ -864,7 +870,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         d.T[c] = T;
         e_mat1 += V * mat_energy(d, c, T);
       }
-      const int ix = c % d.nx, iy = c / d.nx;
+      int ixyz[3];
+      cell_xyz(d, c, &ixyz[0], &ixyz[1], &ixyz[2]);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
@@ -887,8 +894,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         e_rad1 += V * r * d.inv_c;
         // boundary faces: energy entering the domain
         for (int axis = 0; axis < d.dim; ++axis) {
-          const double S = d.dim == 2 ? (axis == 0 ? d.dy : d.dx) : 1.0;
-          const int k = axis == 0 ? ix : iy, nk = axis == 0 ? d.nx : d.ny;
+          const double S = d.area[axis];
+          const int k = ixyz[axis], nk = axis == 0 ? d.nx : (axis == 1 ? d.ny : d.nz);
           if (k == 0) {
             const int f = face_index(d, c, axis, -1);
             b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
@@ -942,7 +949,7 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
   __syncthreads();
   if (threadIdx.x < 32) {
     double pin = 0.0, pout = 0.0;
-    for (int i = threadIdx.x; i < 4 * d.G; i += 32) { pin += d.inflow[i]; pout += d.esc[i]; }
+    for (int i = threadIdx.x; i < 6 * d.G; i += 32) { pin += d.inflow[i]; pout += d.esc[i]; }
     pin = warp_sum(pin);
     pout = warp_sum(pout);
     if (threadIdx.x == 0) {
@@ -995,7 +1002,7 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
 // read on the device (from the live control block when saving, from the
 // saved one when restoring), so neither direction synchronises the host.
 struct CkptLayout {
-  size_t ctrl, T, rho, rho_h, rho_p, part[8], total;
+  size_t ctrl, T, rho, rho_h, rho_p, part[10], total;
 };
 
 __host__ __device__ inline size_t ckpt_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -1013,6 +1020,9 @@ __host__ __device__ inline CkptLayout ckpt_layout(const Dev& d) {
   for (int k = 0; k < 6; ++k) { L.part[k] = o; o = ckpt_align(o + fs * P); }   // x y ox oy nu w
   L.part[6] = o; o = ckpt_align(o + 8 * P);                                   // id
   L.part[7] = o; o = ckpt_align(o + 4 * P);                                   // key
+  const size_t zs = d.dim == 3 ? fs * P : 0;
+  L.part[8] = o; o = ckpt_align(o + zs);                                      // z (3D)
+  L.part[9] = o; o = ckpt_align(o + zs);                                      // oz (3D)
   L.total = o;
   return L;
 }
@@ -1054,15 +1064,15 @@ __global__ void k_checkpoint(const Ens e, const __grid_constant__ Dev d0, char* 
     copy_n(d.rho_p, (const double*)rho_p, ncg);
   }
   if (d.precision == 1) {
-    float* live[6] = {d.fx[cur], d.fy[cur], d.fox[cur], d.foy[cur], d.fnu[cur], d.fw[cur]};
-    for (int k = 0; k < 6; ++k) {
-      float* c = reinterpret_cast<float*>(b + L.part[k]);
+    float* live[8] = {d.fx[cur], d.fy[cur], d.fox[cur], d.foy[cur], d.fnu[cur], d.fw[cur], d.fz[cur], d.foz[cur]};
+    for (int k = 0; k < 8; ++k) {
+      float* c = reinterpret_cast<float*>(b + L.part[k < 6 ? k : k + 2]);
       if (save) copy_n(c, (const float*)live[k], n); else copy_n(live[k], (const float*)c, n);
     }
   } else {
-    double* live[6] = {d.px[cur], d.py[cur], d.pox[cur], d.poy[cur], d.pnu[cur], d.pw[cur]};
-    for (int k = 0; k < 6; ++k) {
-      double* c = reinterpret_cast<double*>(b + L.part[k]);
+    double* live[8] = {d.px[cur], d.py[cur], d.pox[cur], d.poy[cur], d.pnu[cur], d.pw[cur], d.pz[cur], d.poz[cur]};
+    for (int k = 0; k < 8; ++k) {
+      double* c = reinterpret_cast<double*>(b + L.part[k < 6 ? k : k + 2]);
       if (save) copy_n(c, (const double*)live[k], n); else copy_n(live[k], (const double*)c, n);
     }
   }

@@ -164,12 +164,14 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
   const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
   const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
   const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
-  const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
+  const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1, nz = DIM == 3 ? d.nz : 1;
   const double v = d.v, dt = d.dt, inv_rate = d.eps * d.eps / d.c;
   const double* __restrict__ in_x = d.px[cur];
   const double* __restrict__ in_y = d.py[cur];
   const double* __restrict__ in_ox = d.pox[cur];
   const double* __restrict__ in_oy = d.poy[cur];
+  const double* __restrict__ in_z = d.pz[cur];
+  const double* __restrict__ in_oz = d.poz[cur];
   const double* __restrict__ in_nu = d.pnu[cur];
   const double* __restrict__ in_w = d.pw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
   for (int sub = 0; sub < PPT; ++sub, ++tile_iter) {
     const long long i = lt * tile + (long long)sub * blockDim.x + threadIdx.x;
     const bool valid = i < n_tot;
-    double x = 0.0, y = 0.0, ox = 0.0, oy = 0.0, nu = 0.0, w = 0.0;
+    double x = 0.0, y = 0.0, z = 0.0, ox = 0.0, oy = 0.0, oz = 0.0, nu = 0.0, w = 0.0;
     unsigned long long id = 0ull;
     int cell = 0, g = 0, gside = -1;
     bool newborn = false;
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       if (i < n_surv) {
         x = in_x[i];
         ox = in_ox[i];
-        if (DIM == 2) { y = in_y[i]; oy = in_oy[i]; }
+        if (DIM >= 2) { y = in_y[i]; oy = in_oy[i]; }
+        if (DIM == 3) { z = in_z[i]; oz = in_oz[i]; }
         nu = in_nu[i];
         w = in_w[i];
         id = in_id[i];
@@ -207,9 +210,19 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         g = bin - cb * G;
         double Tb;
         if (cb < d.ncell) {
-          const int cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0, cx = cb - cy * nx;
+          int cx, cy, cz = 0;
+          if (DIM == 3) {
+            cz = cb / (nx * ny);
+            const int rem = cb - cz * nx * ny;
+            cy = rem / nx;
+            cx = rem - cy * nx;
+          } else {
+            cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0;
+            cx = cb - cy * nx;
+          }
           x = cx * d.dx + rng.next(d.pk) * d.dx;
-          if (DIM == 2) y = cy * d.dy + rng.next(d.pk) * d.dy;
+          if (DIM >= 2) y = cy * d.dy + rng.next(d.pk) * d.dy;
+          if (DIM == 3) z = cz * d.dz + rng.next(d.pk) * d.dz;
           if (DIM == 1) {
             ox = 2.0 * rng.next(d.pk) - 1.0;
           } else {
@@ -220,6 +233,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
             const double s = sqrt(fmax(0.0, 1.0 - muz * muz));
             ox = s * cp;
             oy = s * sp;
+            if (DIM == 3) oz = muz;
           }
           cell = cb;
           Tb = d.T[cb];
@@ -262,10 +276,19 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         t_rem = collided ? tc : dt;
       }
       bool ghost = gside >= 0;
-      int cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
-      int cx = DIM == 2 ? cell - cy * nx : cell;
+      int cx, cy, cz = 0;
+      if (DIM == 3) {
+        cz = cell / (nx * ny);
+        const int rem = cell - cz * nx * ny;
+        cy = rem / nx;
+        cx = rem - cy * nx;
+      } else {
+        cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
+        cx = DIM == 2 ? cell - cy * nx : cell;
+      }
       const double ivx = ox != 0.0 ? 1.0 / (v * fabs(ox)) : 0.0;
-      const double ivy = (DIM == 2 && oy != 0.0) ? 1.0 / (v * fabs(oy)) : 0.0;
+      const double ivy = (DIM >= 2 && oy != 0.0) ? 1.0 / (v * fabs(oy)) : 0.0;
+      const double ivz = (DIM == 3 && oz != 0.0) ? 1.0 / (v * fabs(oz)) : 0.0;
       for (int guard = 0;; ++guard) {
         if (guard >= 4096) {            // defensive bound (NaN state)
           atomicOr(&ctrl->status, ST_NONFINITE);
@@ -276,15 +299,23 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         double tx = INFINITY, ty = INFINITY;
         if (ox > 0.0) tx = fmax(xR - x, 0.0) * ivx;
         else if (ox < 0.0) tx = fmax(x - xL, 0.0) * ivx;
-        double yB = 0.0, yT = 0.0;
-        if (DIM == 2) {
+        double yB = 0.0, yT = 0.0, zB = 0.0, zT = 0.0, tz = INFINITY;
+        if (DIM >= 2) {
           yB = cy * d.dy;
           yT = (cy + 1) * d.dy;
           if (oy > 0.0) ty = fmax(yT - y, 0.0) * ivy;
           else if (oy < 0.0) ty = fmax(y - yB, 0.0) * ivy;
         }
-        const int axis = (tx <= ty) ? 0 : 1;
-        const double tf = axis == 0 ? tx : ty;
+        if (DIM == 3) {
+          zB = cz * d.dz;
+          zT = (cz + 1) * d.dz;
+          if (oz > 0.0) tz = fmax(zT - z, 0.0) * ivz;
+          else if (oz < 0.0) tz = fmax(z - zB, 0.0) * ivz;
+        }
+        // nearest face; ties go to the lower axis
+        int axis = (tx <= ty) ? 0 : 1;
+        double tf = axis == 0 ? tx : ty;
+        if (DIM == 3 && tz < tf) { axis = 2; tf = tz; }
         if (tf < t_rem) {
           ++nseg;
           t_tra += tf;
@@ -293,17 +324,25 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           if (axis == 0) {
             dir = ox > 0.0 ? 1 : -1;
             x = dir > 0 ? xR : xL;
-            if (DIM == 2) y += v * oy * tf;
-          } else {
+            if (DIM >= 2) y += v * oy * tf;
+            if (DIM == 3) z += v * oz * tf;
+          } else if (DIM < 3 || axis == 1) {
             dir = oy > 0.0 ? 1 : -1;
             y = dir > 0 ? yT : yB;
             x += v * ox * tf;
+            if (DIM == 3) z += v * oz * tf;
+          } else {
+            dir = oz > 0.0 ? 1 : -1;
+            z = dir > 0 ? zT : zB;
+            x += v * ox * tf;
+            y += v * oy * tf;
           }
           const int nxc = cx + (axis == 0 ? dir : 0), nyc = cy + (axis == 1 ? dir : 0);
-          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny) {
+          const int nzc = cz + (axis == 2 ? dir : 0);
+          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny || (DIM == 3 && (nzc < 0 || nzc >= nz))) {
             const int side = axis * 2 + (dir > 0 ? 1 : 0);
             if (d.bc[side] == BC_REFLECT) {
-              if (axis == 0) ox = -ox; else oy = -oy;
+              if (axis == 0) ox = -ox; else if (axis == 1) oy = -oy; else oz = -oz;
               continue;
             }
             fate = FATE_ESCAPED;
@@ -313,7 +352,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
           ghost = false;
           cx = nxc;
           cy = nyc;
-          cell = cy * nx + cx;
+          cz = nzc;
+          cell = (cz * ny + cy) * nx + cx;
           const double u = rng.next(d.pk);
           const double sig_inv = inv_sigma_particle(d, cell, nu, inup);
           const double tc = neg_log_u64(u) * inv_rate * sig_inv;
@@ -324,7 +364,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         }
         ++nseg;
         x += v * ox * t_rem;
-        if (DIM == 2) y += v * oy * t_rem;
+        if (DIM >= 2) y += v * oy * t_rem;
+        if (DIM == 3) z += v * oz * t_rem;
         t_tra += t_rem;
         t_rem = 0.0;
         fate = ghost ? FATE_REMOVED : (collided ? FATE_ABSORBED : FATE_SURVIVED);
@@ -356,6 +397,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         RecordOut& r = d.rec[i];
         r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = cell; r.grp = g; r.nseg = nseg; r.pad = 0;
         r.x = x; r.y = y; r.ox = ox; r.oy = oy; r.nu = nu; r.w = w; r.t_end = t_tra;
+        r.z = z; r.oz = oz;
       }
     }
 
@@ -369,7 +411,8 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       if (o < (unsigned long long)d.capacity) {
         d.px[nxb][o] = x;
         d.pox[nxb][o] = ox;
-        if (DIM == 2) { d.py[nxb][o] = y; d.poy[nxb][o] = oy; }
+        if (DIM >= 2) { d.py[nxb][o] = y; d.poy[nxb][o] = oy; }
+        if (DIM == 3) { d.pz[nxb][o] = z; d.poz[nxb][o] = oz; }
         d.pnu[nxb][o] = nu;
         d.pw[nxb][o] = w;
         d.pid[nxb][o] = id;
@@ -419,13 +462,15 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
   const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
   const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
-  const int G = d.G, nx = d.nx, ny = DIM == 2 ? d.ny : 1;
-  const float dxf = d.dxf, dyf = d.dyf, vf = d.vf, dtf = d.dtf;
+  const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1, nz = DIM == 3 ? d.nz : 1;
+  const float dxf = d.dxf, dyf = d.dyf, dzf = d.dzf, vf = d.vf, dtf = d.dtf;
   const float inv_rate = d.inv_rate_f, spf = d.spf;
   const float* __restrict__ in_x = d.fx[cur];
   const float* __restrict__ in_y = d.fy[cur];
   const float* __restrict__ in_ox = d.fox[cur];
   const float* __restrict__ in_oy = d.foy[cur];
+  const float* __restrict__ in_z = d.fz[cur];
+  const float* __restrict__ in_oz = d.foz[cur];
   const float* __restrict__ in_nu = d.fnu[cur];
   const float* __restrict__ in_w = d.fw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
@@ -433,9 +478,9 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   for (int sub = 0; sub < PPT; ++sub, ++tile_iter) {
     const long long i = lt * tile + (long long)sub * blockDim.x + threadIdx.x;
     const bool valid = i < n_tot;
-    float xi = 0.f, eta = 0.f, ox = 0.f, oy = 0.f, nu = 0.f, w = 0.f;
+    float xi = 0.f, eta = 0.f, zeta = 0.f, ox = 0.f, oy = 0.f, oz = 0.f, nu = 0.f, w = 0.f;
     unsigned long long id = 0ull;
-    int cx = 0, cy = 0, g = 0, gside = -1;
+    int cx = 0, cy = 0, cz = 0, g = 0, gside = -1;
     bool newborn = false;
     DrawsF rng;
     rng.init(0ull, step, 0u);
@@ -443,15 +488,23 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
       if (i < n_surv) {
         xi = in_x[i];
         ox = in_ox[i];
-        if (DIM == 2) { eta = in_y[i]; oy = in_oy[i]; }
+        if (DIM >= 2) { eta = in_y[i]; oy = in_oy[i]; }
+        if (DIM == 3) { zeta = in_z[i]; oz = in_oz[i]; }
         nu = in_nu[i];
         w = in_w[i];
         id = in_id[i];
         const uint32_t key = in_key[i];
         const int cell = (int)div_bin(d, key);
         g = (int)(key - (uint32_t)cell * (uint32_t)G);
-        cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
-        cx = cell - cy * nx;
+        if (DIM == 3) {
+          cz = cell / (nx * ny);
+          const int rem = cell - cz * nx * ny;
+          cy = rem / nx;
+          cx = rem - cy * nx;
+        } else {
+          cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
+          cx = cell - cy * nx;
+        }
         rng.init(id, step, 0u);
       } else {
         newborn = true;
@@ -464,10 +517,18 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         const int cb = (int)div_bin(d, (uint32_t)bin);
         g = bin - cb * G;
         if (cb < d.ncell) {
-          cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0;
-          cx = cb - cy * nx;
+          if (DIM == 3) {
+            cz = cb / (nx * ny);
+            const int rem = cb - cz * nx * ny;
+            cy = rem / nx;
+            cx = rem - cy * nx;
+          } else {
+            cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0;
+            cx = cb - cy * nx;
+          }
           xi = rng.next(d.pk) * dxf;
-          if (DIM == 2) eta = rng.next(d.pk) * dyf;
+          if (DIM >= 2) eta = rng.next(d.pk) * dyf;
+          if (DIM == 3) zeta = rng.next(d.pk) * dzf;
           if (DIM == 1) {
             ox = 2.0f * rng.next(d.pk) - 1.0f;
           } else {
@@ -478,6 +539,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
             const float s = sqrtf(fmaxf(0.0f, 1.0f - muz * muz));
             ox = s * cp;
             oy = s * sp;
+            if (DIM == 3) oz = muz;
           }
         } else {
           const int side = cb - d.ncell;
@@ -495,7 +557,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         w = __ldg(d.omega_f + bin);
       }
     }
-    const int cell0 = gside >= 0 ? cx : cy * nx + cx;
+    const int cell0 = gside >= 0 ? cx : (cz * ny + cy) * nx + cx;
 
     // ---- streaming
     int fate = FATE_REMOVED, nseg = 0, eside = -1;
@@ -509,29 +571,36 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         collided = false;
       } else {
         const UPair u = rng.next2(d.pk);
-        const float sig_inv = inv_sigma_particle_f(d, cy * nx + cx, nu, inup);
+        const float sig_inv = inv_sigma_particle_f(d, (cz * ny + cy) * nx + cx, nu, inup);
         const float tc = neg_log_u(u) * inv_rate * sig_inv;
         collided = tc < dtf;
         t_rem = collided ? tc : dtf;
       }
       bool ghost = gside >= 0;
       const float ivx = ox != 0.0f ? __frcp_rn(vf * fabsf(ox)) : 0.0f;
-      const float ivy = (DIM == 2 && oy != 0.0f) ? __frcp_rn(vf * fabsf(oy)) : 0.0f;
+      const float ivy = (DIM >= 2 && oy != 0.0f) ? __frcp_rn(vf * fabsf(oy)) : 0.0f;
+      const float ivz = (DIM == 3 && oz != 0.0f) ? __frcp_rn(vf * fabsf(oz)) : 0.0f;
       for (int guard = 0;; ++guard) {
         if (guard >= 4096) {
           atomicOr(&ctrl->status, ST_NONFINITE);
           fate = FATE_REMOVED;
           break;
         }
-        float tx = INFINITY, ty = INFINITY;
+        float tx = INFINITY, ty = INFINITY, tz = INFINITY;
         if (ox > 0.0f) tx = fmaxf(dxf - xi, 0.0f) * ivx;
         else if (ox < 0.0f) tx = fmaxf(xi, 0.0f) * ivx;
-        if (DIM == 2) {
+        if (DIM >= 2) {
           if (oy > 0.0f) ty = fmaxf(dyf - eta, 0.0f) * ivy;
           else if (oy < 0.0f) ty = fmaxf(eta, 0.0f) * ivy;
         }
-        const int axis = (tx <= ty) ? 0 : 1;
-        const float tf = axis == 0 ? tx : ty;
+        if (DIM == 3) {
+          if (oz > 0.0f) tz = fmaxf(dzf - zeta, 0.0f) * ivz;
+          else if (oz < 0.0f) tz = fmaxf(zeta, 0.0f) * ivz;
+        }
+        // nearest face; ties go to the lower axis
+        int axis = (tx <= ty) ? 0 : 1;
+        float tf = axis == 0 ? tx : ty;
+        if (DIM == 3 && tz < tf) { axis = 2; tf = tz; }
         if (tf < t_rem) {
           ++nseg;
           t_tra += tf;
@@ -540,17 +609,25 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           if (axis == 0) {
             dir = ox > 0.0f ? 1 : -1;
             xi = dir > 0 ? dxf : 0.0f;
-            if (DIM == 2) eta = fminf(fmaxf(fmaf(vf * oy, tf, eta), 0.0f), dyf);
-          } else {
+            if (DIM >= 2) eta = fminf(fmaxf(fmaf(vf * oy, tf, eta), 0.0f), dyf);
+            if (DIM == 3) zeta = fminf(fmaxf(fmaf(vf * oz, tf, zeta), 0.0f), dzf);
+          } else if (DIM < 3 || axis == 1) {
             dir = oy > 0.0f ? 1 : -1;
             eta = dir > 0 ? dyf : 0.0f;
             xi = fminf(fmaxf(fmaf(vf * ox, tf, xi), 0.0f), dxf);
+            if (DIM == 3) zeta = fminf(fmaxf(fmaf(vf * oz, tf, zeta), 0.0f), dzf);
+          } else {
+            dir = oz > 0.0f ? 1 : -1;
+            zeta = dir > 0 ? dzf : 0.0f;
+            xi = fminf(fmaxf(fmaf(vf * ox, tf, xi), 0.0f), dxf);
+            eta = fminf(fmaxf(fmaf(vf * oy, tf, eta), 0.0f), dyf);
           }
           const int nxc = cx + (axis == 0 ? dir : 0), nyc = cy + (axis == 1 ? dir : 0);
-          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny) {
+          const int nzc = cz + (axis == 2 ? dir : 0);
+          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny || (DIM == 3 && (nzc < 0 || nzc >= nz))) {
             const int side = axis * 2 + (dir > 0 ? 1 : 0);
             if (d.bc[side] == BC_REFLECT) {
-              if (axis == 0) ox = -ox; else oy = -oy;
+              if (axis == 0) ox = -ox; else if (axis == 1) oy = -oy; else oz = -oz;
               continue;
             }
             fate = FATE_ESCAPED;
@@ -559,11 +636,13 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           }
           ghost = false;
           if (axis == 0) xi = dir > 0 ? 0.0f : dxf;
-          else eta = dir > 0 ? 0.0f : dyf;
+          else if (axis == 1) eta = dir > 0 ? 0.0f : dyf;
+          else zeta = dir > 0 ? 0.0f : dzf;
           cx = nxc;
           cy = nyc;
+          cz = nzc;
           const UPair u = rng.next2(d.pk);
-          const float sig_inv = inv_sigma_particle_f(d, cy * nx + cx, nu, inup);
+          const float sig_inv = inv_sigma_particle_f(d, (cz * ny + cy) * nx + cx, nu, inup);
           const float tc = neg_log_u(u) * inv_rate * sig_inv;
           const float avail = dtf - t_tra;
           collided = tc < avail;
@@ -572,13 +651,14 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         }
         ++nseg;
         xi = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
-        if (DIM == 2) eta = fminf(fmaxf(fmaf(vf * oy, t_rem, eta), 0.0f), dyf);
+        if (DIM >= 2) eta = fminf(fmaxf(fmaf(vf * oy, t_rem, eta), 0.0f), dyf);
+        if (DIM == 3) zeta = fminf(fmaxf(fmaf(vf * oz, t_rem, zeta), 0.0f), dzf);
         t_tra += t_rem;
         fate = ghost ? FATE_REMOVED : (collided ? FATE_ABSORBED : FATE_SURVIVED);
         break;
       }
     }
-    const int cell = cy * nx + cx;
+    const int cell = (cz * ny + cy) * nx + cx;
 
     // ---- tallies (W and E_surv in fixed point, see to_fixed; FP64 side tallies)
     const int lane = threadIdx.x & 31;
@@ -604,8 +684,10 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = (fate == FATE_REMOVED && gside >= 0) ? cx : cell;
         r.grp = g; r.nseg = nseg; r.pad = 0;
         r.x = cx * d.dx + (double)xi;
-        r.y = DIM == 2 ? cy * d.dy + (double)eta : 0.0;
+        r.y = DIM >= 2 ? cy * d.dy + (double)eta : 0.0;
         r.ox = ox; r.oy = oy; r.nu = nu; r.w = (double)w; r.t_end = t_tra;
+        r.z = DIM == 3 ? cz * d.dz + (double)zeta : 0.0;
+        r.oz = oz;
       }
     }
 
@@ -618,7 +700,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
       if (o < (unsigned long long)d.capacity) {
         d.fx[nxb][o] = xi;
         d.fox[nxb][o] = ox;
-        if (DIM == 2) { d.fy[nxb][o] = eta; d.foy[nxb][o] = oy; }
+        if (DIM >= 2) { d.fy[nxb][o] = eta; d.foy[nxb][o] = oy; }
+        if (DIM == 3) { d.fz[nxb][o] = zeta; d.foz[nxb][o] = oz; }
         d.fnu[nxb][o] = nu;
         d.fw[nxb][o] = w;
         d.pid[nxb][o] = id;
@@ -632,7 +715,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
-static int g_stream_occ[2][3][2][3][3] = {};   // [mixed][dim][ens][ppt][block index]
+static int g_stream_occ[2][4][2][3][3] = {};   // [mixed][dim][ens][ppt][block index]
 
 template <int DIM, bool ENS, int PPT>
 static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, const StreamShape& sh,
@@ -656,6 +739,10 @@ static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, const 
 
 template <bool ENS>
 static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s) {
+  if (d.dim == 3) {   // single problems only (ensembles are 1D/2D)
+    if (ENS) return cudaErrorNotSupported;
+    return launch_stream_t<3, false, 1>(d, e, mixed, sh, s);
+  }
   if (d.dim == 2) {
     if (sh.ppt == 2) return launch_stream_t<2, ENS, 2>(d, e, mixed, sh, s);
     return launch_stream_t<2, ENS, 1>(d, e, mixed, sh, s);

@@ -61,4 +61,22 @@ def test_init_rejects_small_workspace_without_touching_device(lib):
 
 
 def test_record_layout_matches_header():
-    assert B.RECORD.itemsize == 8 + 6 * 4 + 7 * 8
+    assert B.RECORD.itemsize == 8 + 6 * 4 + 9 * 8
+
+
+def test_3d_validation_and_sizing(lib):
+    p = I.checkerboard_3d(n=8, G=3, block=2, patch=2)
+    n3 = B.workspace_bytes(p)
+    # z positions and directions of both particle buffers on top of the 2D layout
+    assert n3 > 2 * p.particle_capacity * (6 * 8 + 8 + 4 + 2 * 8)
+    for bad, code in [(p.replace(nz=0), -1), (p.replace(dz=0.0), -1),
+                      (p.replace(bc=[0, 0, 0, 0, 3, 0]), -1),
+                      (p.replace(bc=[0, 0, 0, 0, I.BC_BLACKBODY, 0], bcT=[0.0] * 4 + [1.0, 0.0]), -8)]:
+        with pytest.raises(B.UGKWPError) as e:
+            B.workspace_bytes(bad)
+        assert e.value.code == code
+    # ensembles are built for 1D and 2D members
+    hps = [B._HostProblem(q) for q in (p, p.replace(seed=1))]
+    arr = (B.CProblem * 2)(*[hp.s for hp in hps])
+    n = ctypes.c_size_t()
+    assert lib.ugkwp_workspace_size_ensemble(arr, 2, ctypes.byref(n)) == -8

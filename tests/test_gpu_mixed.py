@@ -52,10 +52,13 @@ def check(p, t, g, rg, st2, tal, ro):
     assert flips <= max(2, FLIPS * len(rg)), (flips, len(rg))
     L = p.nx * p.dx
     assert np.abs(rg["x"][same] - ro["x"][same]).max() <= X_TOL * L
-    if p.dim == 2:
+    if p.dim >= 2:
         assert np.abs(rg["y"][same] - ro["y"][same]).max() <= X_TOL * L
+    if p.dim == 3:
+        assert np.abs(rg["z"][same] - ro["z"][same]).max() <= X_TOL * L
+        assert np.abs(rg["oz"][same] - ro["oz"][same]).max() <= DIR_TOL
     assert np.abs(rg["ox"][same] - ro["ox"][same]).max() <= DIR_TOL
-    if p.dim == 2:
+    if p.dim >= 2:
         assert np.abs(rg["oy"][same] - ro["oy"][same]).max() <= DIR_TOL
     if not p.grey:
         np.testing.assert_allclose(rg["nu"][same], ro["nu"][same], rtol=REL_TOL)

@@ -46,10 +46,11 @@ def compare_records(p, rg, ro):
     same = (rg["fate"] == ro["fate"]) & (rg["cell1"] == ro["cell1"]) & (rg["nseg"] == ro["nseg"])
     flips = int((~same).sum())
     assert flips <= max(1, FLIP_FRACTION * len(rg)), flips
-    L = max(p.nx * p.dx, (p.ny * p.dy) if p.dim == 2 else 0.0)
-    for f in ("x", "y", "ox", "oy", "nu", "w", "t_end"):
+    L = max(p.nx * p.dx, (p.ny * p.dy) if p.dim >= 2 else 0.0, (p.nz * p.dz) if p.dim == 3 else 0.0)
+    fields = ("x", "y", "ox", "oy", "nu", "w", "t_end") + (("z", "oz") if p.dim == 3 else ())
+    for f in fields:
         a, b = rg[f][same], ro[f][same]
-        scale = {"x": L, "y": L, "t_end": p.dt, "ox": 1.0, "oy": 1.0}.get(f, None)
+        scale = {"x": L, "y": L, "z": L, "t_end": p.dt, "ox": 1.0, "oy": 1.0, "oz": 1.0}.get(f, None)
         tol = POS_RTOL * (scale if scale is not None else np.abs(b))
         bad = np.abs(a - b) > tol + 1e-300
         assert not bad.any(), (f, a[bad][:5], b[bad][:5])
