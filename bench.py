@@ -475,13 +475,15 @@ def families_leg(B, dev, flush, steps=20):
     precision and FP64): the Larsen slab (Sec. 3.3, photo-ionisation
     opacity, tau_num, free side; 400 steps in), the Olson foam (Sec. 3.5,
     three-band opacity, T-dependent heat capacity; 40 steps in, source on),
-    and the 200x30 slab in the UGKP variant from the synthetic state."""
+    the 200x30 slab in the UGKP variant from the synthetic state, and the
+    32^3 x 8 3D checkerboard (20 steps in)."""
     out = {}
     cases = [("larsen_slab_200x24", I.larsen_slab(), 400, None),
              ("olson_slab_128x30", I.olson_slab(), 40, None)]
     pu = I.multigroup_slab().replace(method=I.UGKP)
     pu.particle_capacity = 1 << 23
     cases.append(("multigroup_slab_200x30_ugkp", pu, 5, I.synthetic_state(pu, N_PARTICLES, seed=1)))
+    cases.append(("checkerboard_3d_32x32x32x8", I.checkerboard_3d(), 20, None))
     for name, p, evolve, st in cases:
         row = {}
         for prec_name, prec in (("mixed", I.MIXED), ("fp64", I.FP64)):

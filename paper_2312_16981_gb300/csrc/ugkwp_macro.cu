@@ -547,7 +547,7 @@ __device__ __forceinline__ double face_feq(const Dev& d, int f, int g, int cur) 
   return feq_face(d, tl, tu, pl, pu, inv_h_of(d, r.axis));
 }
 
-// Source iteration (App. B, Algorithm 2) in 1D and 2D, one warp per cell and
+// Source iteration (App. B, Algorithm 2) in 1D, 2D and 3D, one warp per cell and
 // one lane per group.  Iterate k: equilibrium fluxes from sigma^k, Phi^k of
 // the cell and its neighbours (Jacobi), then the linearised closed-form update
 //   T^{k+1} = [Cv T^n + sum_g (a_g/c)(Q_g - Phi_g + Phi'_g T^k)/(1 + a_g)]
@@ -654,8 +654,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   // ---- iterations
   const int max_it = ENS ? e.devs[0].si_max_iters : d0.si_max_iters;
   int it = 0, all_done = 0;
-  // 2D: every face's F^eq once per iterate (one warp per face, one lane per
-  // group), then a grid barrier, instead of each cell evaluating its four
+  // 2D and 3D: every face's F^eq once per iterate (one warp per face, one lane per
+  // group), then a grid barrier, instead of each cell evaluating its 2 dim
   // faces (a face costs a division and the C2 interpolant in FP64, the
   // scarce unit on this chip; in 1D the extra barrier costs more than the
   // second evaluation of a face saves)
