@@ -202,6 +202,9 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
     d.pid[b] = cv.take<unsigned long long>(P);
     d.pkey[b] = cv.take<uint32_t>(P);
   }
+  // tail pad: the particle kernel's bulk copies round a tile's survivor count
+  // up to whole 16-byte chunks and may read up to 12 bytes past an array
+  cv.take<char>(256);
 }
 
 void fill_scalars(const ugkwp_problem* p, Dev& d) {

@@ -14,7 +14,11 @@
 // end minus start, which telescopes the face crossings), the energy of the
 // collisionless survivors per end cell, escapes and inflow per side.
 // Collided particles are dropped (Algorithm 1, last step); survivors are
-// compacted block by block into the other particle buffer.
+// compacted into the other particle buffer (per block in the FP32 kernel,
+// per warp in the FP64 kernel).  The FP32 kernel of a single problem reads
+// its survivors from shared memory: one thread per block starts bulk copies
+// (cp.async.bulk, completion counted on an mbarrier) of the block's next tile
+// into the other of two stages while the block streams the current one.
 #include "ugkwp_device.cuh"
 #include "ugkwp_launch.h"
 
@@ -98,10 +102,90 @@ __device__ __forceinline__ unsigned long long block_slots(bool flag, int parity,
   return s_base[parity];
 }
 
+// Warp compaction: rank of `flag` among the warp's lanes and the start of the
+// warp's slots, reserved with one atomic by the warp's first flagged lane.
+// No block barrier: the FP64 kernel's particles differ widely in their cost
+// (segments), and block compaction left warps waiting on the block's slowest.
+// (The FP32 kernel keeps block compaction: at its rate one atomic per warp
+// contends, and block-contiguous survivors keep the bins' runs longer.)
+__device__ __forceinline__ unsigned long long warp_slots(bool flag, unsigned long long* counter, unsigned* rank) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(full, flag);
+  unsigned long long base = 0ull;
+  if (b) {
+    const int leader = __ffs(b) - 1;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(b));
+    base = __shfl_sync(full, base, leader);
+  }
+  *rank = __popc(b & ((1u << lane) - 1u));
+  return base;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// --------------------------------------------------------------------------
+// Bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) that
+// stage the next tile's particle arrays in shared memory while the block
+// streams the current tile.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase `parity` of `bar`; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (unsigned k = 0; k < (1u << 22); ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared-memory stage of one tile of FP32 survivors: id (8 B), then x, ox,
+// nu, w, key (, y, oy (, z, oz)) (4 B each), `tile` entries per array.
+template <int DIM>
+struct StageF {
+  static constexpr int kArr4 = 5 + (DIM >= 2 ? 2 : 0) + (DIM == 3 ? 2 : 0);
+  static constexpr int kBytesPer = 8 + 4 * kArr4;
+  unsigned long long* id;
+  float *x, *ox, *nu, *w, *y, *oy, *z, *oz;
+  uint32_t* key;
+  __device__ __forceinline__ StageF(unsigned char* base, int tile) {
+    id = reinterpret_cast<unsigned long long*>(base);
+    float* f = reinterpret_cast<float*>(base + 8 * (size_t)tile);
+    x = f; ox = f + tile; nu = f + 2 * tile; w = f + 3 * tile;
+    key = reinterpret_cast<uint32_t*>(f + 4 * tile);
+    y = f + 5 * tile; oy = f + 6 * tile; z = f + 7 * tile; oz = f + 8 * tile;
+  }
+};
+
+size_t stream32_stage_bytes(int dim, int tile) {
+  const int per = dim == 3 ? StageF<3>::kBytesPer : (dim == 2 ? StageF<2>::kBytesPer : StageF<1>::kBytesPer);
+  return 2 * (size_t)tile * per;
 }
 
 struct Counters {   // per thread; a thread sees far fewer than 2^32 events
@@ -152,7 +236,6 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
   int acc_m = 0;
   const long long tile = (long long)blockDim.x * PPT;   // PPT sub-tiles of one particle per thread
   const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
-  int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
   const StepHead h0 = ENS ? StepHead{} : step_head(d0);
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
   const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
@@ -176,7 +259,7 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
   const double* __restrict__ in_w = d.pw[cur];
   const unsigned long long* __restrict__ in_id = d.pid[cur];
   const uint32_t* __restrict__ in_key = d.pkey[cur];
-  for (int sub = 0; sub < PPT; ++sub, ++tile_iter) {
+  for (int sub = 0; sub < PPT; ++sub) {
     const long long i = lt * tile + (long long)sub * blockDim.x + threadIdx.x;
     const bool valid = i < n_tot;
     double x = 0.0, y = 0.0, z = 0.0, ox = 0.0, oy = 0.0, oz = 0.0, nu = 0.0, w = 0.0;
@@ -401,10 +484,10 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       }
     }
 
-    // ---- compaction of the collisionless survivors
+    // ---- compaction of the collisionless survivors (per warp)
     const bool keep = valid && fate == FATE_SURVIVED;
     unsigned rank;
-    const unsigned long long base = block_slots(keep, tile_iter & 1, &ctrl->n_out, &rank);
+    const unsigned long long base = warp_slots(keep, &ctrl->n_out, &rank);
     int slot = -1;
     if (keep) {
       const unsigned long long o = base + rank;
@@ -452,7 +535,60 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
   const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
   int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
   const StepHead h0 = ENS ? StepHead{} : step_head(d0);
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // single problems: the survivors of the block's next tile are copied into
+  // the other of two shared-memory stages while this tile streams
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  __shared__ uint64_t s_bar[2];
+  const size_t stage_sz = (size_t)tile * StageF<DIM>::kBytesPer;
+  bool wait_failed = false;
+  auto issue = [&](long long lt_next, int st) {   // one thread: expect the bytes, start the copies
+    const unsigned cb = h0.cur;
+    const long long first = lt_next * tile;
+    long long n = h0.n_surv - first;
+    n = n < 0 ? 0 : (n > tile ? tile : n);
+    const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
+    const unsigned bytes = n ? c4 * 4u * StageF<DIM>::kArr4 + c2 * 8u : 0u;
+    StageF<DIM> sg(s_dyn + st * stage_sz, (int)tile);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(&s_bar[st], bytes);
+    if (n) {
+      bulk_g2s(sg.id, d0.pid[cb] + first, c2 * 8u, &s_bar[st]);
+      bulk_g2s(sg.x, d0.fx[cb] + first, c4 * 4u, &s_bar[st]);
+      bulk_g2s(sg.ox, d0.fox[cb] + first, c4 * 4u, &s_bar[st]);
+      bulk_g2s(sg.nu, d0.fnu[cb] + first, c4 * 4u, &s_bar[st]);
+      bulk_g2s(sg.w, d0.fw[cb] + first, c4 * 4u, &s_bar[st]);
+      bulk_g2s(sg.key, d0.pkey[cb] + first, c4 * 4u, &s_bar[st]);
+      if (DIM >= 2) {
+        bulk_g2s(sg.y, d0.fy[cb] + first, c4 * 4u, &s_bar[st]);
+        bulk_g2s(sg.oy, d0.foy[cb] + first, c4 * 4u, &s_bar[st]);
+      }
+      if (DIM == 3) {
+        bulk_g2s(sg.z, d0.fz[cb] + first, c4 * 4u, &s_bar[st]);
+        bulk_g2s(sg.oz, d0.foz[cb] + first, c4 * 4u, &s_bar[st]);
+      }
+    }
+  };
+  if (!ENS) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (long long)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  }
+  int it = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+  const int st = it & 1;
+  if (!ENS) {
+    // all threads left the stage st^1 (read last tile) behind at its block barriers
+    if (threadIdx.x == 0 && t + gridDim.x < ntiles) issue(t + gridDim.x, st ^ 1);
+    if (!wait_failed && !mbar_wait_bounded(&s_bar[st], (unsigned)(it >> 1) & 1u)) {
+      wait_failed = true;
+      atomicOr(&d0.ctrl->status, ST_TIMEOUT);
+    }
+  }
+  const StageF<DIM> sgt(s_dyn + st * stage_sz, (int)tile);
   const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
   if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
   const Dev& d = ENS ? e.devs[m] : d0;
@@ -486,14 +622,28 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     rng.init(0ull, step, 0u);
     if (valid) {
       if (i < n_surv) {
-        xi = in_x[i];
-        ox = in_ox[i];
-        if (DIM >= 2) { eta = in_y[i]; oy = in_oy[i]; }
-        if (DIM == 3) { zeta = in_z[i]; oz = in_oz[i]; }
-        nu = in_nu[i];
-        w = in_w[i];
-        id = in_id[i];
-        const uint32_t key = in_key[i];
+        uint32_t key;
+        if (ENS) {
+          xi = in_x[i];
+          ox = in_ox[i];
+          if (DIM >= 2) { eta = in_y[i]; oy = in_oy[i]; }
+          if (DIM == 3) { zeta = in_z[i]; oz = in_oz[i]; }
+          nu = in_nu[i];
+          w = in_w[i];
+          id = in_id[i];
+          key = in_key[i];
+        } else {
+          const int li = (int)(i - lt * tile);
+          xi = sgt.x[li];
+          ox = sgt.ox[li];
+          if (DIM >= 2) { eta = sgt.y[li]; oy = sgt.oy[li]; }
+          if (DIM == 3) { zeta = sgt.z[li]; oz = sgt.oz[li]; }
+          nu = sgt.nu[li];
+          w = sgt.w[li];
+          id = sgt.id[li];
+          key = sgt.key[li];
+          if (wait_failed) key = 0u;   // the stage never arrived: the step is flagged, stay in range
+        }
         const int cell = (int)div_bin(d, key);
         g = (int)(key - (uint32_t)cell * (uint32_t)G);
         if (DIM == 3) {
@@ -712,6 +862,11 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     }
   }
   }
+  if (!ENS && wait_failed && threadIdx.x == 0) {
+    // copies may still be in flight into the stages: wait (bounded) for both
+    mbar_wait_bounded(&s_bar[0], (unsigned)((it + 1) >> 1) & 1u);
+    mbar_wait_bounded(&s_bar[1], (unsigned)(it >> 1) & 1u);
+  }
   flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
@@ -725,14 +880,16 @@ static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, const 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const void* fn = mixed ? (const void*)k_stream32<DIM, ENS, PPT> : (const void*)k_stream64<DIM, ENS, PPT>;
   const int bi = sh.block == 128 ? 0 : (sh.block == 512 ? 2 : 1);
+  const size_t dyn = (mixed && !ENS) ? stream32_stage_bytes(DIM, sh.block * PPT) : 0;
   int& occ = g_stream_occ[mixed][DIM][ENS][PPT][bi];
   if (!occ) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.block, 0);
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.block, dyn);
     if (occ < 1) occ = 1;
   }
   int per = sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ;
   const int blocks = sms * per;
-  if (mixed) k_stream32<DIM, ENS, PPT><<<blocks, sh.block, 0, s>>>(d, e);
+  if (mixed) k_stream32<DIM, ENS, PPT><<<blocks, sh.block, dyn, s>>>(d, e);
   else k_stream64<DIM, ENS, PPT><<<blocks, sh.block, 0, s>>>(d, e);
   return cudaGetLastError();
 }
