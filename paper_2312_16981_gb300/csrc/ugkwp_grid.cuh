@@ -147,14 +147,18 @@ __device__ __forceinline__ void tau_and_q(const Dev& d, double sig, double* tau,
   *q = A * A * P;
 }
 
-// the face of cell c on `axis`, lower (dir < 0) or upper side
-__device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {
-  int ix, iy, iz;
-  cell_xyz(d, c, &ix, &iy, &iz);
+// the face on `axis` of the cell at (ix, iy, iz), lower (dir < 0) or upper side
+__device__ __forceinline__ int face_index_xyz(const Dev& d, int ix, int iy, int iz, int axis, int dir) {
   const int up = dir > 0 ? 1 : 0;
   if (axis == 0) return (iz * d.ny + iy) * (d.nx + 1) + ix + up;
   if (axis == 1) return d.nxface + (iz * (d.ny + 1) + iy + up) * d.nx + ix;
   return d.nxface + d.nyface + ((iz + up) * d.ny + iy) * d.nx + ix;
+}
+
+__device__ __forceinline__ int face_index(const Dev& d, int c, int axis, int dir) {
+  int ix, iy, iz;
+  cell_xyz(d, c, &ix, &iy, &iz);
+  return face_index_xyz(d, ix, iy, iz, axis, dir);
 }
 
 }  // namespace ugkwp

@@ -480,12 +480,11 @@ __device__ __forceinline__ double feq_face(const Dev& d, double tl, double tu, d
   return d.dt * coef_g2_fast(x, st * d.inv_2dt) * (d.v * d.v / 3.0) * (pu - pl) * inv_h;
 }
 
-// Neighbour values across one face of cell c: relaxation time and Phi at
-// iterate k, or the ghost's.  Returns false for a reflecting wall (no flux).
-__device__ __forceinline__ bool neighbour(const Dev& d, int c, int axis, int dir, int g, int cur,
+// Neighbour values across one face of the cell at (ix, iy, iz): relaxation
+// time and Phi at iterate k, or the ghost's.  Returns false for a reflecting
+// wall (no flux).
+__device__ __forceinline__ bool neighbour(const Dev& d, int ix, int iy, int iz, int axis, int dir, int g, int cur,
                                           double tau_c, double* tn, double* pn, int* nc) {
-  int ix, iy, iz;
-  cell_xyz(d, c, &ix, &iy, &iz);
   const int jx = ix + (axis == 0 ? dir : 0), jy = iy + (axis == 1 ? dir : 0), jz = iz + (axis == 2 ? dir : 0);
   if (jx < 0 || jx >= d.nx || jy < 0 || jy >= d.ny || jz < 0 || jz >= d.nz) {
     const int side = axis * 2 + (dir > 0 ? 1 : 0);
@@ -602,6 +601,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const double dt = d.dt, V = d.vol;
       // the source acts while t^n = n dt < src_t_end (src_t_end <= 0: always)
       const bool src_on = d.src && (!(d.src_t_end > 0.0) || (double)d.ctrl->step * dt < d.src_t_end);
+      int ix, iy, iz;
+      cell_xyz(d, c, &ix, &iy, &iz);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
@@ -610,7 +611,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           const double r0 = d.rho[i];
           double r = r0;
           for (int axis = 0; axis < d.dim; ++axis) {
-            const int fl = face_index(d, c, axis, -1), fr = face_index(d, c, axis, +1);
+            const int fl = face_index_xyz(d, ix, iy, iz, axis, -1), fr = face_index_xyz(d, ix, iy, iz, axis, +1);
             r += (dt * inv_h_of(d, axis)) * (d.Fwave[fl * G + g] - d.Fwave[fr * G + g]);
           }
           const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
@@ -685,6 +686,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       // with q = 1/(tau + dt): 1/(1 + a_g) = tau q and a_g/(1 + a_g) = dt q
       double Q[NC], ar[NC], r1[NC], phc[NC], dpc[NC];
       double num = 0.0, den = 0.0;
+      int ix, iy, iz;
+      cell_xyz(d, c, &ix, &iy, &iz);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
@@ -698,8 +701,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (face_pass) {
           for (int axis = 0; axis < d.dim; ++axis) {
             const double inv_h = inv_h_of(d, axis);
-            const double Fin = __ldcg(d.Feq + face_index(d, c, axis, -1) * G + g);
-            const double Fout = __ldcg(d.Feq + face_index(d, c, axis, +1) * G + g);
+            const double Fin = __ldcg(d.Feq + face_index_xyz(d, ix, iy, iz, axis, -1) * G + g);
+            const double Fout = __ldcg(d.Feq + face_index_xyz(d, ix, iy, iz, axis, +1) * G + g);
             q += (dt * inv_h) * (Fin - Fout);
           }
         }
@@ -710,11 +713,11 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
             double tn, pn;
             int nc;
             double F = 0.0;
-            if (neighbour(d, c, axis, dir, g, cur, tc, &tn, &pn, &nc)) {
+            if (neighbour(d, ix, iy, iz, axis, dir, g, cur, tc, &tn, &pn, &nc)) {
               F = dir < 0 ? feq_face(d, tn, tc, pn, phc[j], inv_h) : feq_face(d, tc, tn, phc[j], pn, inv_h);
             }
             const bool owner = dir > 0 ? true : (nc < 0);   // upper face, or a boundary face
-            if (owner) d.Feq[face_index(d, c, axis, dir) * G + g] = F;
+            if (owner) d.Feq[face_index_xyz(d, ix, iy, iz, axis, dir) * G + g] = F;
             if (dir < 0) Fin = F; else Fout = F;
           }
           q += (dt * inv_h) * (Fin - Fout);
