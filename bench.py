@@ -42,7 +42,7 @@ KERNELS_PER_STEP = 9   # birth, scan x3, wave, particles, source iteration, end 
 # particle of the particle kernels, from one ncu capture of each at 4e6
 # particles on the slab (the traffic grows with the particles processed); the
 # roofline's "traffic" is this times the particles a launch processes.
-TRAFFIC_PER_PROCESSED = {"fp64": 317.13e6 / 4.142e6, "mixed": 182.99e6 / 4.142e6}
+TRAFFIC_PER_PROCESSED = {"fp64": 315.90e6 / 4.142e6, "mixed": 180.51e6 / 4.142e6}
 
 
 def combine_replicas(ms: float, segments: float, world: int, device):
