@@ -112,10 +112,12 @@ def test_mixed_energy_conserved_over_steps(B):
     p = I.small_checkerboard(n=16, G=4, omega_ref=2e-7).replace(precision=I.MIXED)
     p.src_on = 0.0
     p.T0 = np.linspace(0.2, 1.0, p.ncell)
+    p.particle_capacity = 1 << 21      # ~5.7e5 births in the first step
     sim = B.Simulation(p)
     for _ in range(4):
         sim.step(1)
         t = sim.tallies()
+        assert t["status_bits"] == 0
         E0, E1 = t["E_rad0"] + t["E_mat0"], t["E_rad1"] + t["E_mat1"]
         assert abs(E1 - E0) <= 1e-12 * E0
     assert t["n_in"] > 1000
