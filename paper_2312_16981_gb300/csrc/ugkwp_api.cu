@@ -26,6 +26,9 @@ struct ugkwp_handle {
   char err[512];
   // one step captured as a CUDA graph, replayed by ugkwp_step
   cudaStream_t cap_stream = nullptr;
+  // the wave flux runs beside the particle kernel in the captured step
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -469,18 +472,32 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
 
 namespace {
 
+// One step.  With a side stream (and its two events) the wave flux, which
+// needs only the birth kernel's sampled fractions, runs beside the particle
+// kernel; the source iteration waits for both.
 cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::StreamShape& sh,
-                             cudaStream_t s) {
+                             cudaStream_t s, cudaStream_t side = nullptr, cudaEvent_t ev_fork = nullptr,
+                             cudaEvent_t ev_join = nullptr) {
   cudaError_t r = ugkwp::launch_birth_and_scan(d, e, s);
-  if (!r) r = ugkwp::launch_wave(d, e, s);
-  if (!r) r = ugkwp::launch_stream(d, e, sh, s);
+  if (side) {
+    if (!r) r = cudaEventRecord(ev_fork, s);
+    if (!r) r = cudaStreamWaitEvent(side, ev_fork, 0);
+    if (!r) r = ugkwp::launch_wave(d, e, side);
+    if (!r) r = cudaEventRecord(ev_join, side);
+    if (!r) r = ugkwp::launch_stream(d, e, sh, s);
+    if (!r) r = cudaStreamWaitEvent(s, ev_join, 0);
+  } else {
+    if (!r) r = ugkwp::launch_wave(d, e, s);
+    if (!r) r = ugkwp::launch_stream(d, e, sh, s);
+  }
   if (!r) r = ugkwp::launch_si(d, e, s);
   if (!r) r = ugkwp::launch_end_step(d, e, s);
   return r;
 }
 
 cudaError_t enqueue_step(const ugkwp_handle* h, cudaStream_t s) {
-  return enqueue_step_dev(h->d, h->M > 1 ? &h->ens : nullptr, h->shape, s);
+  return enqueue_step_dev(h->d, h->M > 1 ? &h->ens : nullptr, h->shape, s, h->side_stream, h->ev_fork,
+                          h->ev_join);
 }
 
 void drop_graph(ugkwp_handle* h) {
@@ -492,6 +509,11 @@ void drop_graph(ugkwp_handle* h) {
 // control block, so the same graph serves every step).
 int capture_step(ugkwp_handle* h) {
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), h);
+  if (!h->side_stream) {
+    CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking), h);
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), h);
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), h);
+  }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
   cudaError_t e = enqueue_step(h, h->cap_stream);
@@ -1010,6 +1032,9 @@ void ugkwp_destroy(ugkwp_handle* h) {
   if (!h) return;
   drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

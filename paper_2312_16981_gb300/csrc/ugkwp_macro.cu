@@ -1171,6 +1171,34 @@ cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t
   return cudaGetLastError();
 }
 
+// One-block exclusive scan of n <= 16 tiles of counts (grids of modest size):
+// one launch instead of three; the total goes to off[n] and the two counters.
+__global__ void __launch_bounds__(kScanThreads) k_scan_small(const uint32_t* __restrict__ N, long long n,
+                                                            uint32_t* __restrict__ off,
+                                                            unsigned long long* total_a,
+                                                            unsigned long long* total_b) {
+  uint32_t carry = 0;
+  for (long long t = 0; t * kScanTile < n; ++t) {
+    const long long base = t * kScanTile + (long long)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) { v[k] = base + k < n ? N[base + k] : 0u; s += v[k]; }
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan(s, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (base + k < n) off[base + k] = ex;
+      ex += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    off[n] = carry;
+    if (total_a) *total_a = carry;
+    if (total_b) *total_b = carry;
+  }
+}
+
 cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
     k_birth<true><<<grid_for(e->total_bins, 64, 152 * 64), 64, 0, s>>>(d, *e);
@@ -1183,6 +1211,10 @@ cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s) {
   }
   const Ens none{};
   k_birth<false><<<grid_for(d.nbins, 64), 64, 0, s>>>(d, none);
+  if (d.nbins <= 16 * kScanTile) {
+    k_scan_small<<<1, kScanThreads, 0, s>>>(d.N, d.nbins, d.off, &d.ctrl->n_new, &d.ctrl->n_born);
+    return cudaGetLastError();
+  }
   return launch_scan(d.N, d.nbins, d.part, d.off, &d.ctrl->n_new, &d.ctrl->n_born, s);
 }
 
