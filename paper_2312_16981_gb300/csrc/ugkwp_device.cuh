@@ -474,6 +474,7 @@ struct Ctrl {
   unsigned int bar_timeout_spins; // bounded-wait limit (0: default)
   unsigned int bar_extra;         // arrivals a barrier also waits for (failure injection; 0)
   unsigned int scaled;            // some survivors' weights need scaling this step
+  unsigned int fin_count;         // blocks done in the end-of-step kernel (0 between steps)
   unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)
   double E_rad0, E_mat0, E_rad1, E_mat1, bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
 };

@@ -966,14 +966,9 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
 // for their (cell, group) (a reading where the paper is silent: the particle
 // part never exceeds rho^{n+1}).  Runs after the buffer swap; a member with
 // nothing to scale returns at once.
-template <bool ENS>
-__global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__ Dev d0, const Ens e) {
-  const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
-  const Ctrl* ctrl = d.ctrl;
-  if (!ctrl->scaled) return;
-  const unsigned cur = ctrl->cur;
-  const long long n = (long long)ctrl->n_part[cur];
-  const uint32_t* __restrict__ key = d.pkey[cur];
+// Scale the weights of buffer b's first n particles by their bins' factors.
+__device__ __forceinline__ void scale_weights(const Dev& d, unsigned b, long long n) {
+  const uint32_t* __restrict__ key = d.pkey[b];
   const bool mixed = d.precision == 1;
   // four particles per thread: one 16-byte key load, four independent gathers
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * q < n;
@@ -992,8 +987,54 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (f[r] == 1.0) continue;
-      if (mixed) d.fw[cur][i0 + r] = (float)((double)d.fw[cur][i0 + r] * f[r]);
-      else d.pw[cur][i0 + r] *= f[r];
+      if (mixed) d.fw[b][i0 + r] = (float)((double)d.fw[b][i0 + r] * f[r]);
+      else d.pw[b][i0 + r] *= f[r];
+    }
+  }
+}
+
+template <bool ENS>
+__global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__ Dev d0, const Ens e) {
+  const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
+  const Ctrl* ctrl = d.ctrl;
+  if (!ctrl->scaled) return;
+  const unsigned cur = ctrl->cur;
+  scale_weights(d, cur, (long long)ctrl->n_part[cur]);
+}
+
+// End of step of a single problem in one launch: the survivors' weights are
+// scaled in their output buffer, then the last block to finish swaps the
+// buffers, advances the step and sums the particle ledger (every block has
+// read the control block before it counts itself done).
+__global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  const unsigned out = ctrl->cur ^ 1u;
+  const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
+  const long long n = (long long)(no < cap ? no : cap);
+  if (ctrl->scaled) scale_weights(d, out, n);
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->fin_count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (threadIdx.x == 0) {
+    ctrl->n_part[out] = (unsigned long long)n;
+    ctrl->n_part[out ^ 1u] = 0;
+    ctrl->cur = out;
+    ctrl->step += 1;
+    ctrl->fin_count = 0;
+  }
+  if (threadIdx.x < 32) {
+    double pin = 0.0, pout = 0.0;
+    for (int i = threadIdx.x; i < 6 * d.G; i += 32) { pin += d.inflow[i]; pout += d.esc[i]; }
+    pin = warp_sum(pin);
+    pout = warp_sum(pout);
+    if (threadIdx.x == 0) {
+      ctrl->bnd_in_part = pin / d.c;
+      ctrl->bnd_out_part = pout / d.c;
     }
   }
 }
@@ -1278,9 +1319,7 @@ cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
     k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e);
     k_scale_survivors<true><<<dim3(8, e->M), 256, 0, s>>>(d, *e);
   } else {
-    const Ens none{};
-    k_end_step<false><<<1, 32, 0, s>>>(d, none);
-    k_scale_survivors<false><<<152 * 4, 256, 0, s>>>(d, none);
+    k_finish_step<<<152 * 4, 256, 0, s>>>(d);
   }
   return cudaGetLastError();
 }

@@ -120,3 +120,25 @@ def test_3d_adjoint_rejected(B):
     with pytest.raises(B.UGKWPError) as e:
         sim.tape_buffer(16)
     assert e.value.code == -8
+
+
+@pytest.mark.parametrize("precision", [I.FP64, I.MIXED])
+def test_3d_checkpoint_restore_repeats_the_steps(B, precision):
+    # z positions and directions are part of the checkpointed particle state
+    sim = B.Simulation(box(precision=precision))
+    sim.step(2)
+    buf = sim.checkpoint_buffer()
+    sim.checkpoint(buf)
+    sim.step(2)
+    first = sim.get_state()
+    sim.restore(buf)
+    sim.step(2)
+    second = sim.get_state()
+    assert first["n"] == second["n"] and first["n"] > 1000
+    np.testing.assert_allclose(second["T"], first["T"], rtol=1e-10)
+    a, b = first["particles"], second["particles"]
+    ia, ib = np.argsort(a["id"]), np.argsort(b["id"])
+    np.testing.assert_array_equal(a["id"][ia], b["id"][ib])
+    for f in ("z", "oz", "x", "y"):
+        np.testing.assert_allclose(b[f][ib], a[f][ia], rtol=0, atol=1e-9)
+    assert np.abs(a["oz"]).max() > 0.5 and (a["z"] > 0).all() and (a["z"] < 1).all()
