@@ -151,6 +151,43 @@ def oracle_segments_per_s(p, s, n_sample, steps):
     return segs, t
 
 
+def _oracle_replica(args):
+    """One oracle replica for the parallel CPU baseline: its own slice of the
+    workload's particles, 3 steps (the full source iteration each step)."""
+    k, n_sample, particles = args
+    p, s = workload(0, particles)
+    sl = slice(k * n_sample, (k + 1) * n_sample)
+    s = dict(s, particles={f: v[sl] for f, v in s["particles"].items()})
+    return oracle_segments_per_s(p, s, 0, 3)
+
+
+def host_cpu():
+    """Core count and CPU model of this host (for the CPU baseline)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part"):
+                    model = "%s (%s %s)" % (platform.machine(), key, line.split(":", 1)[1].strip())
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count() or 1, "model": model}
+
+
+def oracle_parallel(n_sample, particles):
+    """The oracle as N independent replicas (one per host core, processes
+    started with spawn), each on its own particle slice: total segments over
+    the slowest replica's compute time."""
+    import multiprocessing as mp
+    n = max(1, min(os.cpu_count() or 1, particles // n_sample))
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_replica, [(k, n_sample, particles) for k in range(n)])
+    return sum(r[0] for r in res) / max(r[1] for r in res), n
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -662,7 +699,16 @@ def main():
         line["cpu_baseline"] = {
             "value": osegs / ot, "unit": "segments/s", "cores": 1, "kind": "oracle",
             "sample": "3 oracle steps of the same workload with the first %d of %d particles "
-                      "(full 200x30 source iteration each step)" % (n_sample, args.particles)}
+                      "(full 200x30 source iteration each step)" % (n_sample, args.particles),
+            "host": host_cpu()}
+        try:
+            pv, pn = oracle_parallel(n_sample, args.particles)
+            line["cpu_baseline"]["parallel"] = {
+                "value": pv, "unit": "segments/s", "cores": pn,
+                "what": "%d oracle replicas in spawned processes, each 3 steps on its own %d-particle "
+                        "slice of the workload (each with the full source iteration)" % (pn, n_sample)}
+        except Exception as exc:   # the single-core figure stands
+            line["cpu_baseline"]["parallel"] = {"unavailable": str(exc)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
