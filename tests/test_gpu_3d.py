@@ -142,3 +142,37 @@ def test_3d_checkpoint_restore_repeats_the_steps(B, precision):
     for f in ("z", "oz", "x", "y"):
         np.testing.assert_allclose(b[f][ib], a[f][ia], rtol=0, atol=1e-9)
     assert np.abs(a["oz"]).max() > 0.5 and (a["z"] > 0).all() and (a["z"] < 1).all()
+
+
+def ragged(G=40, **kw):
+    # nx != ny != nz, dx != dy != dz, G > 32 (two groups per lane in the
+    # source iteration), a hot corner and a thick slab of cells
+    nx, ny, nz = 6, 5, 4
+    n = nx * ny * nz
+    T0 = np.full(n, 0.02)
+    T0.reshape(nz, ny, nx)[:2, :2, :3] = 0.6
+    sig0 = np.full(n, 3.0)
+    sig0.reshape(nz, ny, nx)[:, 3:, :] = 300.0
+    p = I.checkerboard_3d(n=4, G=G, block=2, patch=0, omega_ref=4e-7).replace(
+        nx=nx, ny=ny, nz=nz, dx=0.11, dy=0.17, dz=0.23, sigma0=sig0, cv=np.ones(n), T0=T0,
+        src_T=None, src_on=0.0, dt=0.05, bc=[I.BC_REFLECT, I.BC_VACUUM, I.BC_VACUUM, I.BC_REFLECT,
+                                            I.BC_REFLECT, I.BC_VACUUM], bcT=[0.0] * 6)
+    p.particle_capacity = 1 << 19
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_step_parity_ragged_3d_box(B, order):
+    t, tal = check_step(B, ragged(wave_order=order), 2)
+    assert t["n_born"] > 500 and t["n_in"] > 10000 and t["n_escaped"] > 0
+
+
+def test_mixed_ragged_3d_box(B):
+    p = ragged(G=12)
+    op = O.OracleProblem(p)
+    st = O.initial_state(op)
+    for _ in range(2):
+        st, _, _, _ = O.step(op, st)
+    M.check(p, *M.run_pair(B, p, st, op))
