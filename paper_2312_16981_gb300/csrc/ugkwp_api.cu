@@ -30,6 +30,10 @@ struct ugkwp_handle {
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // single problems in mixed precision: every kSortEvery-th step replays a
+  // second graph whose end of step sorts the survivors by bin
+  cudaGraphExec_t exec_sort = nullptr;
+  unsigned long long launches = 0;
 };
 
 namespace {
@@ -144,6 +148,9 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.N = cv.take<uint32_t>(nb);
   d.off = cv.take<uint32_t>(nb + 1);
   d.part = cv.take<uint32_t>(ugkwp::scan_parts(nb) + 1);
+  d.sort_cnt = cv.take<uint32_t>(nb);
+  d.sort_off = cv.take<uint32_t>(nb + 1);
+  d.sort_part = cv.take<uint32_t>(ugkwp::scan_parts(nb) + 1);
   d.omega = cv.take<double>(nb);
   d.xnum = cv.take<double>(nb);
   d.e_eff = cv.take<double>(nb);
@@ -284,6 +291,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.fastdiv = (long long)d.ncell * d.G < (1ll << 24) ? 1 : 0;
   d.invG_f = 1.0f / (float)d.G;
   d.inv_nx_f = 1.0f / (float)d.nx;
+  d.sorting = 0;
   d.rec = nullptr;
   d.rec_cap = 0;
   d.tape = nullptr;
@@ -495,18 +503,36 @@ cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::Str
   return r;
 }
 
-cudaError_t enqueue_step(const ugkwp_handle* h, cudaStream_t s) {
-  return enqueue_step_dev(h->d, h->M > 1 ? &h->ens : nullptr, h->shape, s, h->side_stream, h->ev_fork,
-                          h->ev_join);
-}
-
 void drop_graph(ugkwp_handle* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->exec_sort) cudaGraphExecDestroy(h->exec_sort);
   h->exec = nullptr;
+  h->exec_sort = nullptr;
 }
 
+constexpr unsigned kSortEvery = 8;
+
+bool sorts(const ugkwp_handle* h) { return h->M == 1 && h->d.precision == UGKWP_MIXED; }
+
 // Capture one step (every kernel reads the step's counts from the device
-// control block, so the same graph serves every step).
+// control block, so the same graph serves every step); with sorted = true
+// the step whose end sorts the survivors.
+int capture_one(ugkwp_handle* h, bool sorted, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
+  Dev d = h->d;
+  d.sorting = sorted ? 1 : 0;
+  cudaError_t e = enqueue_step_dev(d, h->M > 1 ? &h->ens : nullptr, h->shape, h->cap_stream, h->side_stream,
+                                   h->ev_fork, h->ev_join);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capturing the step"); }
+  if (e2) return cuda_fail(h, e2, "end of capture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e) { *out = nullptr; return cuda_fail(h, e, "instantiating the step graph"); }
+  return UGKWP_OK;
+}
+
 int capture_step(ugkwp_handle* h) {
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), h);
   if (!h->side_stream) {
@@ -514,16 +540,10 @@ int capture_step(ugkwp_handle* h) {
     CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), h);
     CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), h);
   }
-  cudaGraph_t g = nullptr;
-  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
-  cudaError_t e = enqueue_step(h, h->cap_stream);
-  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
-  if (e) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capturing the step"); }
-  if (e2) return cuda_fail(h, e2, "end of capture");
-  e = cudaGraphInstantiate(&h->exec, g, 0);
-  cudaGraphDestroy(g);
-  if (e) { h->exec = nullptr; return cuda_fail(h, e, "instantiating the step graph"); }
-  return UGKWP_OK;
+  int st = capture_one(h, false, &h->exec);
+  if (!st && sorts(h)) st = capture_one(h, true, &h->exec_sort);
+  if (st) drop_graph(h);
+  return st;
 }
 
 }  // namespace
@@ -538,7 +558,10 @@ int ugkwp_step(ugkwp_handle* h, int nsteps, void* stream) {
     int st = capture_step(h);
     if (st) return st;
   }
-  for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->exec, s), h);
+  for (int n = 0; n < nsteps; ++n) {
+    const bool sort_now = h->exec_sort && ++h->launches % kSortEvery == 0;
+    CK(cudaGraphLaunch(sort_now ? h->exec_sort : h->exec, s), h);
+  }
   return UGKWP_OK;
 }
 

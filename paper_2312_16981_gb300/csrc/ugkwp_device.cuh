@@ -247,6 +247,12 @@ struct Dev {
   uint32_t* N;      // [nbins]
   uint32_t* off;    // [nbins+1] exclusive scan of N
   uint32_t* part;   // [scan partials]
+  // counting sort of the survivors by bin (single problems, mixed precision,
+  // the steps of the sorting graph: sorting = 1)
+  int sorting;
+  uint32_t* sort_cnt;   // [nbins] survivors per bin this step
+  uint32_t* sort_off;   // [nbins+1] their exclusive scan, then the bins' write cursors
+  uint32_t* sort_part;  // [scan partials]
   double* omega;    // [nbins]
   double* xnum;     // [nbins] dt/tau_num of the bin (dt/tau where tau_num_C = 0)
   double* e_eff;    // [nbins]

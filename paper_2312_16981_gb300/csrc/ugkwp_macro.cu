@@ -106,6 +106,7 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     ctrl->bnd_in_macro = ctrl->bnd_in_part = ctrl->bnd_out_part = ctrl->src_in = 0.0;
   }
   const int G = d.G;
+  if (d.sorting) d.sort_cnt[b] = 0u;   // the particle kernel counts the survivors per bin
   {
     const int cell = b / G, g = b - cell * G;
     double E, sig, Tb;
@@ -938,15 +939,16 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
 // End of step: swap particle buffers, advance the step counter, particle
 // ledger from the side tallies.
 template <bool ENS>
-__global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
+__global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e, int sorted) {
   const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
   Ctrl* ctrl = d.ctrl;
   if (threadIdx.x == 0) {
     const unsigned long long n = ctrl->n_out;
     const unsigned long long cap = (unsigned long long)d.capacity;
-    ctrl->n_part[ctrl->cur ^ 1u] = n < cap ? n : cap;
-    ctrl->n_part[ctrl->cur] = 0;
-    ctrl->cur ^= 1u;
+    const unsigned live = sorted ? ctrl->cur : ctrl->cur ^ 1u;   // sorted: back in the input buffer
+    ctrl->n_part[live] = n < cap ? n : cap;
+    ctrl->n_part[live ^ 1u] = 0;
+    ctrl->cur = live;
     ctrl->step += 1;
   }
   __syncthreads();
@@ -1036,6 +1038,89 @@ __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev
       ctrl->bnd_in_part = pin / d.c;
       ctrl->bnd_out_part = pout / d.c;
     }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Counting sort of the survivors by bin (cell, group), in the steps of the
+// sorting graph (single problems, mixed precision, one step in eight).  The
+// compaction leaves survivors in block order, and the particles that cross a
+// face keep their slot while each step's newborns are appended, so within a
+// few steps the lanes of a warp hold different bins (the warp tallies lose
+// their one-bin path, the per-cell tables are gathered).  The particle kernel
+// counts the survivors per bin with its survivor tallies; the counts are
+// scanned; the scatter moves the survivors from the output buffer back into
+// the input buffer in bin order, scaling each weight by its bin's factor from
+// the source iteration (the job of k_finish_step).  The order inside a bin
+// follows the cursor atomics: nothing depends on it (random streams are keyed
+// by particle identity, tallies are integer sums).  After a capacity overflow
+// the counts include survivors that were dropped, so that step copies in
+// place order instead.
+
+// Runs of equal keys among the warp's lanes: start lane of this lane's run
+// and its length (at every lane of the run).
+__device__ __forceinline__ void warp_runs(uint32_t key, int* start, int* len) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint32_t prev = __shfl_up_sync(full, key, 1);
+  const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
+  *start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  const unsigned after = heads & ~(0xffffffffu >> (31 - lane));   // heads above this lane
+  *len = (after ? __ffs(after) - 1 : 32) - *start;
+}
+
+// One contiguous chunk of whole 32-slices per warp, so that warps running at
+// the same time work on different bins of the (nearly sorted) survivors.
+__device__ __forceinline__ void warp_chunk(long long n, long long* lo, long long* hi) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long per = ((n + nw - 1) / nw + 31) & ~31ll;
+  *lo = w * per;
+  *hi = *lo + per < n ? *lo + per : n;
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(const __grid_constant__ Dev d) {
+  const Ctrl* ctrl = d.ctrl;
+  const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
+  const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
+  const long long n = (long long)(no < cap ? no : cap);
+  const bool scaled = ctrl->scaled != 0;
+  const bool ordered = no <= cap;
+  const int dim = d.dim;
+  const uint32_t* __restrict__ key = d.pkey[nxb];
+  const int lane = threadIdx.x & 31;
+  long long lo, hi;
+  warp_chunk(n, &lo, &hi);
+  for (long long base = lo; base < hi; base += 32) {
+    const long long i = base + lane;
+    const bool valid = i < hi;
+    uint32_t k = 0xffffffffu;
+    unsigned long long id = 0ull;
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      k = __ldg(key + i);
+      id = d.pid[nxb][i];
+      a[0] = d.fx[nxb][i]; a[1] = d.fox[nxb][i]; a[2] = d.fnu[nxb][i]; a[3] = d.fw[nxb][i];
+      if (dim >= 2) { a[4] = d.fy[nxb][i]; a[5] = d.foy[nxb][i]; }
+      if (dim == 3) { a[6] = d.fz[nxb][i]; a[7] = d.foz[nxb][i]; }
+    }
+    long long o = i;
+    if (ordered) {
+      int start, len;
+      warp_runs(k, &start, &len);
+      unsigned long long b = 0ull;
+      if (lane == start && valid) b = atomicAdd(d.sort_off + k, (unsigned)len);
+      b = __shfl_sync(0xffffffffu, b, start);
+      o = (long long)b + (lane - start);
+    }
+    if (!valid || o >= n) continue;
+    const double f = scaled ? __ldg(d.wscale + k) : 1.0;
+    d.fx[cur][o] = a[0]; d.fox[cur][o] = a[1]; d.fnu[cur][o] = a[2];
+    d.fw[cur][o] = f == 1.0 ? a[3] : (float)((double)a[3] * f);
+    if (dim >= 2) { d.fy[cur][o] = a[4]; d.foy[cur][o] = a[5]; }
+    if (dim == 3) { d.fz[cur][o] = a[6]; d.foz[cur][o] = a[7]; }
+    d.pid[cur][o] = id;
+    d.pkey[cur][o] = k;
   }
 }
 
@@ -1316,8 +1401,18 @@ cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s) {
 
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
-    k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e);
+    k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e, 0);
     k_scale_survivors<true><<<dim3(8, e->M), 256, 0, s>>>(d, *e);
+  } else if (d.sorting) {
+    if (d.nbins <= 16 * kScanTile) {
+      k_scan_small<<<1, kScanThreads, 0, s>>>(d.sort_cnt, d.nbins, d.sort_off, nullptr, nullptr);
+    } else {
+      cudaError_t r = launch_scan(d.sort_cnt, d.nbins, d.sort_part, d.sort_off, nullptr, nullptr, s);
+      if (r) return r;
+    }
+    k_sort_scatter<<<152 * 8, 256, 0, s>>>(d);
+    const Ens none{};
+    k_end_step<false><<<1, 32, 0, s>>>(d, none, 1);
   } else {
     k_finish_step<<<152 * 4, 256, 0, s>>>(d);
   }

@@ -42,8 +42,11 @@ __device__ __forceinline__ int find_bin(const uint32_t* __restrict__ off, int nb
 // depend on which lanes meet in a warp.  Common case first: every lane with
 // a key holds the same key and v >= 0; then the warp sums v in three 21-bit
 // pieces with integer warp reductions (each piece's sum stays below 2^26;
-// v < 2^57 by the fixed-point range) instead of the segmented scan.
-__device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int key, long long v) {
+// v < 2^57 by the fixed-point range) instead of the segmented scan.  With
+// `cnt`, each run also adds its length to cnt[key] (the survivors per bin of
+// a sorting step).
+__device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int key, long long v,
+                                                   uint32_t* cnt = nullptr) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned keyed = __ballot_sync(full, key >= 0);
@@ -55,7 +58,10 @@ __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int
     const unsigned long long s0 = __reduce_add_sync(full, (unsigned)(u & 0x1fffffull));
     const unsigned long long s1 = __reduce_add_sync(full, (unsigned)((u >> 21) & 0x1fffffull));
     const unsigned long long s2 = __reduce_add_sync(full, (unsigned)(u >> 42));
-    if (lane == first) atomic_add_fixed(base + 2 * (long long)k0, (long long)(s0 + (s1 << 21) + (s2 << 42)));
+    if (lane == first) {
+      atomic_add_fixed(base + 2 * (long long)k0, (long long)(s0 + (s1 << 21) + (s2 << 42)));
+      if (cnt) atomicAdd(cnt + k0, (unsigned)__popc(keyed));
+    }
     return;
   }
   const int prev = __shfl_up_sync(full, key, 1);
@@ -69,7 +75,10 @@ __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int
   }
   const int nxt = __shfl_down_sync(full, key, 1);
   const bool tail = lane == 31 || nxt != key;
-  if (tail && key >= 0) atomic_add_fixed(base + 2 * (long long)key, v);
+  if (tail && key >= 0) {
+    atomic_add_fixed(base + 2 * (long long)key, v);
+    if (cnt) atomicAdd(cnt + key, (unsigned)(lane - start + 1));
+  }
 }
 
 // Block compaction: exclusive rank of `flag` within the block plus the start
@@ -813,7 +822,8 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     // ---- tallies (W and E_surv in fixed point, see to_fixed; FP64 side tallies)
     const int lane = threadIdx.x & 31;
     const long long wq = valid ? to_fixed_f(w, d.tq_shift, &ctrl->status) : 0ll;
-    warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq);
+    warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq,
+                       (!ENS && d.sorting) ? d.sort_cnt : nullptr);
     if (valid && fate != FATE_REMOVED && (gside >= 0 || fate == FATE_ESCAPED || cell0 != cell)) {
       const double wd = (double)w;
       const bool start_in = gside < 0;
