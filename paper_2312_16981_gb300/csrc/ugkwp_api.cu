@@ -510,7 +510,7 @@ void drop_graph(ugkwp_handle* h) {
   h->exec_sort = nullptr;
 }
 
-constexpr unsigned kSortEvery = 8;
+constexpr unsigned kSortEvery = 4;
 
 bool sorts(const ugkwp_handle* h) { return h->M == 1 && h->d.precision == UGKWP_MIXED; }
 

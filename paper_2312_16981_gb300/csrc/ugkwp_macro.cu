@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev
 
 // --------------------------------------------------------------------------
 // Counting sort of the survivors by bin (cell, group), in the steps of the
-// sorting graph (single problems, mixed precision, one step in eight).  The
+// sorting graph (single problems, mixed precision, one step in four).  The
 // compaction leaves survivors in block order, and the particles that cross a
 // face keep their slot while each step's newborns are appended, so within a
 // few steps the lanes of a warp hold different bins (the warp tallies lose
