@@ -200,6 +200,9 @@ int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream);
 
 /* Copy the state to host arrays: T [ncell], rho, rho_h, rho_p [ncell*G] (any
  * may be NULL) and up to `cap` particles; *n receives the particle count.
+ * The particles' order is unspecified (survivors are compacted per block or
+ * warp, and in mixed precision sorted by bin every fourth ugkwp_step, with
+ * the order inside a bin set by atomics); identify them by `id`.
  * Synchronises `stream`. */
 int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, double* rho_p,
                     ugkwp_particles_host* parts, int64_t cap, int64_t* n, void* stream);
