@@ -40,9 +40,11 @@ METRIC = "particle segments/s"
 KERNELS_PER_STEP = 9   # birth, scan x3, wave, particles, source iteration, end of step, survivor scaling
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per processed
 # particle of the particle kernels, from one ncu capture of each at 4e6
-# particles on the slab (the traffic grows with the particles processed); the
-# roofline's "traffic" is this times the particles a launch processes.
-TRAFFIC_PER_PROCESSED = {"fp64": 315.90e6 / 4.142e6, "mixed": 180.51e6 / 4.142e6}
+# particles on the slab (the traffic grows with the particles processed; the
+# FP32 figure from the current kernel on a sorting step, within 0.3 % of its
+# plain launches); the roofline's "traffic" is this times the particles a
+# launch processes.
+TRAFFIC_PER_PROCESSED = {"fp64": 315.90e6 / 4.142e6, "mixed": 180.99e6 / 4.142e6}
 
 
 def combine_replicas(ms: float, segments: float, world: int, device):
