@@ -37,7 +37,12 @@ from paper_2312_16981_gb300 import inputs as I  # noqa: E402
 N_PARTICLES = 1_000_000
 WORKLOAD = "multigroup_slab_200x30"
 METRIC = "particle segments/s"
-KERNELS_PER_STEP = 9   # birth, scan x3, wave, particles, source iteration, end of step, survivor scaling
+# kernels of one slab step: birth, one-block scan, wave flux, particles,
+# source iteration, end of step; a mixed-precision step that sorts the
+# survivors (every fourth graph replay) runs a second scan, the scatter and
+# the end of step in place of the last one (two more)
+KERNELS_PER_STEP = 6
+SORT_EXTRA_PER_STEP = 2 / 4
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per processed
 # particle of the particle kernels, from one ncu capture of each at 4e6
 # particles on the slab (the traffic grows with the particles processed; the
@@ -678,9 +683,10 @@ def main():
                        "what": "per step: H2D of T and rho from pinned host memory, ugkwp_step "
                                "(CUDA graph), D2H of T, rho and the tally report"}
         # timed graph steps of both builds, their phase passes, and the e2e steps
-        line["gpu_launches"] = KERNELS_PER_STEP * K * 5
+        # (mixed graph steps: the timed ones and the e2e ones also sort)
+        line["gpu_launches"] = int(round(KERNELS_PER_STEP * K * 5 + SORT_EXTRA_PER_STEP * K * 2))
     else:
-        line["gpu_launches"] = KERNELS_PER_STEP * K * 2
+        line["gpu_launches"] = int(round(KERNELS_PER_STEP * K * 2 + (SORT_EXTRA_PER_STEP * K if head_mixed else 0)))
 
     extra_legs = rank == 0 and world == 1 and not args.quick
     if extra_legs and not args.no_matched_error:
