@@ -121,3 +121,34 @@ def test_mixed_energy_conserved_over_steps(B):
         E0, E1 = t["E_rad0"] + t["E_mat0"], t["E_rad1"] + t["E_mat1"]
         assert abs(E1 - E0) <= 1e-12 * E0
     assert t["n_in"] > 1000
+
+
+def test_mixed_steps_across_the_survivor_sort(B):
+    # every fourth step of a mixed-precision problem sorts the survivors by
+    # bin: after two sorts (8 steps) the particles still match the oracle's
+    # one by one (by identity: position, direction, frequency, weight, cell)
+    p = I.small_multigroup(nx=24, G=6, omega_ref=1e-6).replace(precision=I.MIXED)
+    p.particle_capacity = 1 << 20
+    op = O.OracleProblem(p.replace(precision=I.FP64))
+    st = O.initial_state(op)
+    sim = B.Simulation(p)
+    for n in range(8):
+        sim.step(1)
+        st, tal, _, status = O.step(op, st)
+        assert status == 0 and sim.tallies()["status_bits"] == 0
+    g = sim.get_state()
+    np.testing.assert_allclose(g["T"], st.T, rtol=T_TOL * 10)
+    pg, po = g["particles"], st.particles.view()
+    assert abs(g["n"] - st.particles.n) <= max(2, FLIPS * st.particles.n)
+    common, ig, io = np.intersect1d(pg["id"], po["id"], return_indices=True)
+    assert len(common) >= (1 - FLIPS) * st.particles.n and len(common) > 1000
+    assert (pg["cell"][ig] == po["cell"][io]).mean() > 1 - FLIPS
+    same = pg["cell"][ig] == po["cell"][io]
+    L = p.nx * p.dx
+    assert np.abs(pg["x"][ig][same] - po["x"][io][same]).max() <= 10 * X_TOL * L
+    np.testing.assert_allclose(pg["ox"][ig], po["ox"][io], rtol=0, atol=10 * DIR_TOL)
+    np.testing.assert_allclose(pg["nu"][ig], po["nu"][io], rtol=10 * REL_TOL)
+    np.testing.assert_allclose(pg["w"][ig], po["w"][io], rtol=REL_TOL)   # scaled survivors: the bin factor to mixed precision
+    # the survivors are held in bin order right after a sorting step
+    key = pg["cell"] * p.G + pg["grp"]
+    assert (np.diff(key) >= 0).mean() > 0.99
