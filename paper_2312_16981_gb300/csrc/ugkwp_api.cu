@@ -29,6 +29,9 @@ struct ugkwp_handle {
   // the wave flux runs beside the particle kernel in the captured step
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the survivor sort runs beside the source iteration in a sorting step
+  cudaStream_t sort_stream = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaGraphExec_t exec = nullptr;
   // single problems in mixed precision: every kSortEvery-th step replays a
   // second graph whose end of step sorts the survivors by bin
@@ -480,25 +483,45 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
 
 namespace {
 
-// One step.  With a side stream (and its two events) the wave flux, which
-// needs only the birth kernel's sampled fractions, runs beside the particle
-// kernel; the source iteration waits for both.
+// Side branches of a captured step: the wave flux (it needs only the birth
+// kernel's sampled fractions) beside the particle kernel, and in a sorting
+// step the survivor sort (it needs only the particle kernel's counts)
+// beside the source iteration, which touches no particle.
+struct Branches {
+  cudaStream_t side = nullptr, sort = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
+};
+
+// One step (in stream order without branches).
 cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::StreamShape& sh,
-                             cudaStream_t s, cudaStream_t side = nullptr, cudaEvent_t ev_fork = nullptr,
-                             cudaEvent_t ev_join = nullptr) {
+                             cudaStream_t s, const Branches& b = Branches()) {
   cudaError_t r = ugkwp::launch_birth_and_scan(d, e, s);
-  if (side) {
-    if (!r) r = cudaEventRecord(ev_fork, s);
-    if (!r) r = cudaStreamWaitEvent(side, ev_fork, 0);
-    if (!r) r = ugkwp::launch_wave(d, e, side);
-    if (!r) r = cudaEventRecord(ev_join, side);
+  if (b.side) {
+    if (!r) r = cudaEventRecord(b.fork, s);
+    if (!r) r = cudaStreamWaitEvent(b.side, b.fork, 0);
+    if (!r) r = ugkwp::launch_wave(d, e, b.side);
+    if (!r) r = cudaEventRecord(b.join, b.side);
     if (!r) r = ugkwp::launch_stream(d, e, sh, s);
-    if (!r) r = cudaStreamWaitEvent(s, ev_join, 0);
+    if (!r) r = cudaStreamWaitEvent(s, b.join, 0);
   } else {
     if (!r) r = ugkwp::launch_wave(d, e, s);
     if (!r) r = ugkwp::launch_stream(d, e, sh, s);
   }
-  if (!r) r = ugkwp::launch_si(d, e, s);
+  if (d.sorting) {
+    if (b.sort) {
+      if (!r) r = cudaEventRecord(b.fork2, s);
+      if (!r) r = cudaStreamWaitEvent(b.sort, b.fork2, 0);
+      if (!r) r = ugkwp::launch_sort(d, b.sort);
+      if (!r) r = cudaEventRecord(b.join2, b.sort);
+      if (!r) r = ugkwp::launch_si(d, e, s);
+      if (!r) r = cudaStreamWaitEvent(s, b.join2, 0);
+    } else {
+      if (!r) r = ugkwp::launch_si(d, e, s);
+      if (!r) r = ugkwp::launch_sort(d, s);
+    }
+  } else {
+    if (!r) r = ugkwp::launch_si(d, e, s);
+  }
   if (!r) r = ugkwp::launch_end_step(d, e, s);
   return r;
 }
@@ -522,8 +545,10 @@ int capture_one(ugkwp_handle* h, bool sorted, cudaGraphExec_t* out) {
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
   Dev d = h->d;
   d.sorting = sorted ? 1 : 0;
-  cudaError_t e = enqueue_step_dev(d, h->M > 1 ? &h->ens : nullptr, h->shape, h->cap_stream, h->side_stream,
-                                   h->ev_fork, h->ev_join);
+  Branches b;
+  b.side = h->side_stream; b.fork = h->ev_fork; b.join = h->ev_join;
+  b.sort = h->sort_stream; b.fork2 = h->ev_fork2; b.join2 = h->ev_join2;
+  cudaError_t e = enqueue_step_dev(d, h->M > 1 ? &h->ens : nullptr, h->shape, h->cap_stream, b);
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
   if (e) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capturing the step"); }
   if (e2) return cuda_fail(h, e2, "end of capture");
@@ -539,6 +564,9 @@ int capture_step(ugkwp_handle* h) {
     CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking), h);
     CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), h);
     CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), h);
+    CK(cudaStreamCreateWithFlags(&h->sort_stream, cudaStreamNonBlocking), h);
+    CK(cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming), h);
+    CK(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming), h);
   }
   int st = capture_one(h, false, &h->exec);
   if (!st && sorts(h)) st = capture_one(h, true, &h->exec_sort);
@@ -1058,6 +1086,9 @@ void ugkwp_destroy(ugkwp_handle* h) {
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->sort_stream) cudaStreamDestroy(h->sort_stream);
+  if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
+  if (h->ev_join2) cudaEventDestroy(h->ev_join2);
   delete h;
 }
 

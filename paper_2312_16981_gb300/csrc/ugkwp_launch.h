@@ -15,6 +15,8 @@ cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s);
 cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s);
 cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s);
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s);
+// survivor sort of a sorting step (d.sorting): scan of the counts, scatter
+cudaError_t launch_sort(const Dev& d, cudaStream_t s);
 
 size_t ckpt_bytes(const Dev& d);
 cudaError_t launch_checkpoint(const Dev& d, const Ens* e, char* buf, const size_t* d_offs, int save,

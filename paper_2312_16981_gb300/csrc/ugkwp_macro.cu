@@ -1005,12 +1005,13 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
 }
 
 // End of step of a single problem in one launch: the survivors' weights are
-// scaled in their output buffer, then the last block to finish swaps the
-// buffers, advances the step and sums the particle ledger (every block has
+// scaled in their buffer (the output buffer, or the input buffer the sort
+// moved them back to), then the last block to finish makes that buffer the
+// live one, advances the step and sums the particle ledger (every block has
 // read the control block before it counts itself done).
-__global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev d, int sorted) {
   Ctrl* ctrl = d.ctrl;
-  const unsigned out = ctrl->cur ^ 1u;
+  const unsigned out = sorted ? ctrl->cur : ctrl->cur ^ 1u;
   const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
   const long long n = (long long)(no < cap ? no : cap);
   if (ctrl->scaled) scale_weights(d, out, n);
@@ -1050,8 +1051,9 @@ __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev
 // their one-bin path, the per-cell tables are gathered).  The particle kernel
 // counts the survivors per bin with its survivor tallies; the counts are
 // scanned; the scatter moves the survivors from the output buffer back into
-// the input buffer in bin order, scaling each weight by its bin's factor from
-// the source iteration (the job of k_finish_step).  The order inside a bin
+// the input buffer in bin order, beside the source iteration (which touches
+// no particle); k_finish_step then scales the sorted survivors.  The order
+// inside a bin
 // follows the cursor atomics: nothing depends on it (random streams are keyed
 // by particle identity, tallies are integer sums).  After a capacity overflow
 // the counts include survivors that were dropped, so that step copies in
@@ -1084,7 +1086,6 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const __grid_constant__ De
   const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
   const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
   const long long n = (long long)(no < cap ? no : cap);
-  const bool scaled = ctrl->scaled != 0;
   const bool ordered = no <= cap;
   const int dim = d.dim;
   const uint32_t* __restrict__ key = d.pkey[nxb];
@@ -1114,9 +1115,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const __grid_constant__ De
       o = (long long)b + (lane - start);
     }
     if (!valid || o >= n) continue;
-    const double f = scaled ? __ldg(d.wscale + k) : 1.0;
-    d.fx[cur][o] = a[0]; d.fox[cur][o] = a[1]; d.fnu[cur][o] = a[2];
-    d.fw[cur][o] = f == 1.0 ? a[3] : (float)((double)a[3] * f);
+    d.fx[cur][o] = a[0]; d.fox[cur][o] = a[1]; d.fnu[cur][o] = a[2]; d.fw[cur][o] = a[3];
     if (dim >= 2) { d.fy[cur][o] = a[4]; d.foy[cur][o] = a[5]; }
     if (dim == 3) { d.fz[cur][o] = a[6]; d.foz[cur][o] = a[7]; }
     d.pid[cur][o] = id;
@@ -1403,19 +1402,22 @@ cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
     k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e, 0);
     k_scale_survivors<true><<<dim3(8, e->M), 256, 0, s>>>(d, *e);
-  } else if (d.sorting) {
-    if (d.nbins <= 16 * kScanTile) {
-      k_scan_small<<<1, kScanThreads, 0, s>>>(d.sort_cnt, d.nbins, d.sort_off, nullptr, nullptr);
-    } else {
-      cudaError_t r = launch_scan(d.sort_cnt, d.nbins, d.sort_part, d.sort_off, nullptr, nullptr, s);
-      if (r) return r;
-    }
-    k_sort_scatter<<<152 * 8, 256, 0, s>>>(d);
-    const Ens none{};
-    k_end_step<false><<<1, 32, 0, s>>>(d, none, 1);
   } else {
-    k_finish_step<<<152 * 4, 256, 0, s>>>(d);
+    k_finish_step<<<152 * 4, 256, 0, s>>>(d, d.sorting);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const Dev& d, cudaStream_t s) {
+  if (d.nbins <= 16 * kScanTile) {
+    k_scan_small<<<1, kScanThreads, 0, s>>>(d.sort_cnt, d.nbins, d.sort_off, nullptr, nullptr);
+  } else {
+    cudaError_t r = launch_scan(d.sort_cnt, d.nbins, d.sort_part, d.sort_off, nullptr, nullptr, s);
+    if (r) return r;
+  }
+  // a quarter of the SM threads: the scatter runs beside the source iteration,
+  // whose cooperative blocks must find room on every SM
+  k_sort_scatter<<<152 * 2, 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 
