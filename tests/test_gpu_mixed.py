@@ -152,3 +152,27 @@ def test_mixed_steps_across_the_survivor_sort(B):
     # the survivors are held in bin order right after a sorting step
     key = pg["cell"] * p.G + pg["grp"]
     assert (np.diff(key) >= 0).mean() > 0.99
+
+
+def test_capacity_overflow_across_sorting_steps_stays_consistent(B):
+    # more survivors than the particle buffers hold: the step is flagged
+    # (status bit) and the sorting steps copy in place order, so the live
+    # particles stay a consistent set (valid bins, no slot left unwritten)
+    p = I.small_checkerboard(n=16, G=4, omega_ref=2e-7).replace(precision=I.MIXED)
+    p.src_on = 0.0
+    p.T0 = np.linspace(0.2, 1.0, p.ncell)
+    p.particle_capacity = 1 << 16
+    sim = B.Simulation(p)
+    bits = 0
+    for _ in range(8):
+        sim.step(1)
+        bits |= sim.tallies()["status_bits"]
+    assert bits & 1   # UGKWP_ST_CAPACITY
+    g = sim.get_state()
+    assert 0 < g["n"] <= p.particle_capacity
+    par = g["particles"]
+    assert (par["cell"] >= 0).all() and (par["cell"] < p.ncell).all()
+    assert (par["grp"] >= 0).all() and (par["grp"] < p.G).all()
+    assert np.isfinite(par["w"]).all() and (par["w"] > 0).all()
+    assert len(np.unique(par["id"])) == g["n"]
+    assert np.isfinite(g["T"]).all() and (g["T"] > 0).all()
