@@ -53,6 +53,8 @@ extern "C" {
 #define UGKWP_ST_NOCONV 2u
 #define UGKWP_ST_NONFINITE 4u
 #define UGKWP_ST_TIMEOUT 8u
+#define UGKWP_ST_IDSPACE 16u   /* step past 2^20 - 1: a newborn's identity (birth step << 44 |
+                                  bin << 20 | k) has no room, so nothing was sampled */
 
 enum { UGKWP_BC_REFLECT = 0, UGKWP_BC_VACUUM = 1, UGKWP_BC_BLACKBODY = 2 };
 enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
@@ -109,7 +111,9 @@ typedef struct ugkwp_problem {
   uint64_t seed;          /* Philox key = (seed_lo, seed_hi ^ instance) */
   uint32_t instance;
   int32_t method;         /* UGKWP_METHOD_UGKWP (0) or UGKWP_METHOD_UGKP (1) */
-  int64_t particle_capacity;   /* maximum surviving particles held between steps */
+  int64_t particle_capacity;   /* particles one step may process (survivors in + newborns): each of
+                                  the two particle buffers holds that many; a particle beyond it
+                                  is dropped (UGKWP_ST_CAPACITY), its energy left to the wave part */
   const double* nu_edges;      /* [G+1] increasing, > 0 (ignored when grey) */
   const double* sigma0;        /* [ncell] */
   const double* cv;            /* [ncell] */
@@ -128,6 +132,14 @@ typedef struct ugkwp_problem {
   int32_t _pad3;
   double dz;
   double bcT_z[2];
+  /* Wave/particle split after the source iteration (Sec. 2.2, I^h = I^{n+1}
+   * - I^p).  0 (default): where the collisionless survivors of a (cell,
+   * group) hold more than rho^{n+1} V, their weights are scaled down to it,
+   * so rho^h never goes below min(rho^{n+1}, 0) (a reading where the paper is
+   * silent; the scaled bins are counted in n_scaled_bins).  1: the split as
+   * written, rho^h = rho^{n+1} - E_surv/V, nothing scaled. */
+  int32_t split_literal;
+  int32_t _pad4;
 } ugkwp_problem;
 
 typedef struct ugkwp_handle ugkwp_handle;
@@ -151,6 +163,7 @@ typedef struct ugkwp_tally_report {
   uint32_t status_bits;   /* UGKWP_ST_* latched since init */
   double E_rad0, E_mat0, E_rad1, E_mat1;      /* sum V rho/c, sum V Cv T before/after */
   double bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
+  int64_t n_scaled_bins;  /* (cell, group) bins whose survivors' weights were scaled (split_literal 0) */
 } ugkwp_tally_report;
 
 /* Host-side structure-of-arrays particle buffers for ugkwp_get_state /
@@ -185,12 +198,16 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
 /* Advance nsteps time steps (Algorithm 1), asynchronously on `stream`:
  * birth counts and scan (Eq. IhpFormula), streaming of survivors and
  * newborns with t_f reset and tallies (Eqs. particle-tf-formula, wfrpFormula),
- * wave flux (Sec. 2.2), source iteration (App. B), compaction. */
+ * wave flux (Sec. 2.2), source iteration (App. B), removal of the collided
+ * particles with the survivors sorted by (cell, group) bin.  Each step is
+ * one replay of a CUDA graph captured on the first call. */
 int ugkwp_step(ugkwp_handle* h, int nsteps, void* stream);
 
-/* One step like ugkwp_step, bracketed by CUDA events on `stream`, then
- * synchronise: phase_ms[0] the whole step, [1] birth counts and their scan,
- * [2] wave flux, [3] particle kernel, [4] source iteration, [5] end of step
+/* One step like ugkwp_step, launched kernel by kernel and bracketed by CUDA
+ * events on `stream`, then synchronise: phase_ms[0] the whole step, [1]
+ * birth counts and their scan, [2] wave flux, [3] particle kernel, [4] source
+ * iteration, [5] end of step (the survivor sort, which ugkwp_step runs
+ * beside the source iteration, then the weight scaling and counters)
  * (device milliseconds).  For measurement; the events are created and
  * destroyed per call. */
 int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms);
@@ -200,10 +217,10 @@ int ugkwp_tallies(ugkwp_handle* h, ugkwp_tally_report* out, void* stream);
 
 /* Copy the state to host arrays: T [ncell], rho, rho_h, rho_p [ncell*G] (any
  * may be NULL) and up to `cap` particles; *n receives the particle count.
- * The particles' order is unspecified (survivors are compacted per block or
- * warp, and in mixed precision sorted by bin every fourth ugkwp_step, with
- * the order inside a bin set by atomics); identify them by `id`.
- * Synchronises `stream`. */
+ * After a step the particles are sorted by bin (cell c, group g: c*G + g);
+ * the order inside a bin is set by atomics, so identify particles by `id`.
+ * (After ugkwp_set_state they are in the order given.)  Synchronises
+ * `stream`. */
 int ugkwp_get_state(ugkwp_handle* h, double* T, double* rho, double* rho_h, double* rho_p,
                     ugkwp_particles_host* parts, int64_t cap, int64_t* n, void* stream);
 
@@ -252,8 +269,10 @@ int ugkwp_checkpoint(ugkwp_handle* h, void* d_buf, size_t bytes, void* stream);
 int ugkwp_restore(ugkwp_handle* h, const void* d_buf, size_t bytes, void* stream);
 
 /* ---- launch shape of the particle kernel ----
- * block: 128, 256 or 512 threads; particles_per_thread: 1 or 2 (sub-tiles
- * per tile); blocks_per_sm: 0 for as many as fit. */
+ * block: 128, 256 or 512 streaming threads (the mixed-precision kernel adds
+ * one producer warp that stages the tiles); particles_per_thread: 1 or 2
+ * (tile = block x particles_per_thread particles); blocks_per_sm: 0 for as
+ * many as fit. */
 int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int blocks_per_sm);
 /* ---- bounded waits ----
  * The source iteration's grid barrier polls at most `spins` times (0: the
@@ -314,8 +333,8 @@ int ugkwp_adjoint_seed(ugkwp_handle* h, void* d_adj, size_t bytes, const double*
 int ugkwp_adjoint_step(ugkwp_handle* h, const void* d_tape, size_t tape_bytes, int64_t rec_cap, void* d_adj,
                        size_t adj_bytes, void* stream);
 /* Before reversing a recomputed segment whose end is the start of the
- * segment reversed last: survivors are compacted in a thread-order-dependent
- * order, so re-index the particles' weight adjoints from the order held in
+ * segment reversed last: the order of survivors inside a bin depends on
+ * thread timing, so re-index the particles' weight adjoints from the order held in
  * d_ckpt (that later segment's checkpoint) to the handle's current particle
  * order (the recomputed segment's end), matching particle identities.  A
  * particle present on one side only gets 0 and is counted in the result's

@@ -21,6 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 
 SURVIVED, ABSORBED, ESCAPED, REMOVED = 0, 1, 2, 3
+# step status codes of ugkwp_oracle.h (OR_ERR_IDSPACE: a step past the 20
+# bits of the birth step in a particle identity samples nothing)
+OR_ERR_CAPACITY, OR_ERR_NOCONV, OR_ERR_NONFINITE, OR_ERR_IDSPACE = -3, -4, -5, -9
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -43,7 +46,7 @@ class CProblem(C.Structure):
         ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
         ("cv_chi", C.c_double),
         ("nz", C.c_int32), ("bc_z", C.c_int32 * 2), ("_pad3", C.c_int32), ("dz", C.c_double),
-        ("bcT_z", C.c_double * 2),
+        ("bcT_z", C.c_double * 2), ("split_literal", C.c_int32), ("_pad4", C.c_int32),
     ]
 
 
@@ -70,6 +73,7 @@ class CTallies(C.Structure):
         ("E_rad0", C.c_double), ("E_mat0", C.c_double), ("E_rad1", C.c_double),
         ("E_mat1", C.c_double), ("bnd_in_macro", C.c_double), ("bnd_out_macro", C.c_double),
         ("bnd_in_part", C.c_double), ("bnd_out_part", C.c_double), ("src_in", C.c_double),
+        ("n_scaled_bins", C.c_int64),
     ]
 
 
@@ -174,6 +178,7 @@ class OracleProblem:
         bcT = list(p.bcT) + [0.0] * (6 - len(p.bcT))
         s.bc_z[0], s.bc_z[1] = int(bc[4]), int(bc[5])
         s.bcT_z[0], s.bcT_z[1] = float(bcT[4]), float(bcT[5])
+        s.split_literal = int(getattr(p, "split_literal", 0))
         self.s = s
 
     @property

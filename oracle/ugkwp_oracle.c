@@ -934,6 +934,11 @@ int or_step_core(const or_problem* P, int64_t step,
   int64_t n_new = 0;
   int st = or_birth_counts(P, T, rho_h, tal, &n_new);
   if (st) status = st;
+  if (step > OR_MAX_STEP) {   /* identities exhausted: nothing is sampled */
+    for (int b = 0; b < (ncell + 4) * G; ++b) { tal->N[b] = 0; tal->omega[b] = 0.0; tal->e_eff[b] = 0.0; }
+    n_new = 0;
+    status = OR_ERR_IDSPACE;
+  }
   tal->n_born = n_new;
 
   /* steps 1, 3: remaining particles, then newborns */
@@ -1081,19 +1086,22 @@ int or_step_core(const or_problem* P, int64_t step,
    * rho^{n+1} and the energy are unchanged.  Without it a cold cell crossed by
    * many survivors accumulates a negative wave part that the source
    * iteration takes out of the material, until T^{n+1} has no positive
-   * solution. */
+   * solution.  With split_literal the split is I^h = I^{n+1} - I^p as the
+   * paper writes it (Sec. 2.2) and nothing is scaled. */
   double* fscale = malloc(sizeof(double) * (size_t)ncell * G);
   int any_scaled = 0;
+  tal->n_scaled_bins = 0;
   tal->E_rad1 = tal->E_mat1 = 0.0;
   for (int c = 0; c < ncell; ++c) {
     for (int g = 0; g < G; ++g) {
       const int i = c * G + g;
       double rp = tal->E_surv[i] / V, r = rho_out[i];
       fscale[i] = 1.0;
-      if (rp > 0.0 && r < rp) {
+      if (!P->split_literal && rp > 0.0 && r < rp) {
         fscale[i] = r > 0.0 ? r / rp : 0.0;
         rp = r > 0.0 ? r : 0.0;
         any_scaled = 1;
+        ++tal->n_scaled_bins;
       }
       rho_p_out[i] = rp;
       rho_h_out[i] = r - rp;

@@ -27,7 +27,12 @@ enum { OR_BC_REFLECT = 0, OR_BC_VACUUM = 1, OR_BC_BLACKBODY = 2 };
 enum { OR_UGKWP = 0, OR_UGKP = 1 };
 enum { OR_SURVIVED = 0, OR_ABSORBED = 1, OR_ESCAPED = 2, OR_REMOVED = 3 };
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_CAPACITY = -3, OR_ERR_NOCONV = -4,
-       OR_ERR_NONFINITE = -5 };
+       OR_ERR_NONFINITE = -5, OR_ERR_IDSPACE = -9 };
+/* A newborn's identity is (birth step << 44) | (bin << 20) | k: the birth
+ * step has 20 bits.  A step past OR_MAX_STEP samples no particle and returns
+ * OR_ERR_IDSPACE (its identities, and with them its random streams, would
+ * repeat those of an earlier step). */
+#define OR_MAX_STEP ((int64_t)((1 << 20) - 1))
 
 typedef struct {
   int32_t dim, nx, ny, G;
@@ -61,6 +66,8 @@ typedef struct {
   int32_t _pad3;
   double dz;
   double bcT_z[2];
+  int32_t split_literal;          /* 1: rho^h = rho^{n+1} - E_surv/V as written; 0: survivors scaled */
+  int32_t _pad4;
 } or_problem;
 
 /* Structure-of-arrays particle set.  In 1D, ox holds mu and y, oy are 0. */
@@ -98,6 +105,7 @@ typedef struct {
   double bnd_in_macro, bnd_out_macro;      /* through boundary faces, energy units */
   double bnd_in_part, bnd_out_part;        /* particles, energy units */
   double src_in;
+  int64_t n_scaled_bins;                   /* (cell, group) bins whose survivors were scaled */
 } or_tallies;
 
 /* --- building blocks (each is pinned separately by the tests) --- */

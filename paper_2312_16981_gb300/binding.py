@@ -21,7 +21,7 @@ _lib = None
 OK = 0
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "CAPACITY", -4: "NOCONV", -5: "NONFINITE", -6: "TIMEOUT",
           -7: "WORKSPACE", -8: "UNSUPPORTED"}
-ST_CAPACITY, ST_NOCONV, ST_NONFINITE, ST_TIMEOUT = 1, 2, 4, 8
+ST_CAPACITY, ST_NOCONV, ST_NONFINITE, ST_TIMEOUT, ST_IDSPACE = 1, 2, 4, 8, 16
 
 _dp = C.POINTER(C.c_double)
 
@@ -49,7 +49,7 @@ class CProblem(C.Structure):
         ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
         ("cv_chi", C.c_double),
         ("nz", C.c_int32), ("bc_z", C.c_int32 * 2), ("_pad3", C.c_int32), ("dz", C.c_double),
-        ("bcT_z", C.c_double * 2),
+        ("bcT_z", C.c_double * 2), ("split_literal", C.c_int32), ("_pad4", C.c_int32),
     ]
 
 
@@ -64,7 +64,7 @@ class CTallyReport(C.Structure):
         ("status_bits", C.c_uint32),
         ("E_rad0", C.c_double), ("E_mat0", C.c_double), ("E_rad1", C.c_double), ("E_mat1", C.c_double),
         ("bnd_in_macro", C.c_double), ("bnd_in_part", C.c_double), ("bnd_out_part", C.c_double),
-        ("src_in", C.c_double),
+        ("src_in", C.c_double), ("n_scaled_bins", C.c_int64),
     ]
 
 
@@ -213,6 +213,7 @@ class _HostProblem:
         bcT = list(p.bcT) + [0.0] * (6 - len(p.bcT))
         s.bc_z[0], s.bc_z[1] = int(bc[4]), int(bc[5])
         s.bcT_z[0], s.bcT_z[1] = float(bcT[4]), float(bcT[5])
+        s.split_literal = int(getattr(p, "split_literal", 0))
         self.s = s
         self._keep = keep
 

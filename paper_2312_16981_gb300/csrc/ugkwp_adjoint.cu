@@ -869,9 +869,9 @@ __global__ void k_adj_flip(AdjView a) { a.ctrl->cur ^= 1u; }
 cudaError_t launch_adjoint_remap(const Dev& d, const AdjView& a, const char* ckpt_member, cudaStream_t s) {
   const Ctrl* saved = reinterpret_cast<const Ctrl*>(ckpt_member + ckpt_ctrl_offset(d));
   const unsigned long long* ids = reinterpret_cast<const unsigned long long*>(ckpt_member + ckpt_ids_offset(d));
-  k_hash_clear<<<152 * 8, 256, 0, s>>>(a);
-  k_hash_insert<<<152 * 8, 256, 0, s>>>(a, saved, ids);
-  k_hash_lookup<<<152 * 8, 256, 0, s>>>(d, a);
+  k_hash_clear<<<sm_count() * 8, 256, 0, s>>>(a);
+  k_hash_insert<<<sm_count() * 8, 256, 0, s>>>(a, saved, ids);
+  k_hash_lookup<<<sm_count() * 8, 256, 0, s>>>(d, a);
   k_adj_flip<<<1, 1, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -917,16 +917,16 @@ cudaError_t launch_adjoint_step(const Dev& d, const TapeView& t, const AdjView& 
   if (r) return r;
   r = cudaMemsetAsync(a.Sb, 0, sizeof(double) * (size_t)d.ncell * d.G, s);
   if (r) return r;
-  k_adj_scale_sums<<<152 * 4, 256, 0, s>>>(d, t, a);
+  k_adj_scale_sums<<<sm_count() * 4, 256, 0, s>>>(d, t, a);
   r = d.G > 32 ? launch_adj_si_t<2>(d, t, a, s) : launch_adj_si_t<1>(d, t, a, s);
   if (r) return r;
   const long long nfg = (long long)d.nface * d.G;
   long long wb = (nfg + 127) / 128;
-  if (wb > 152 * 32) wb = 152 * 32;
+  if (wb > sm_count() * 32) wb = sm_count() * 32;
   k_adj_wave<<<(int)(wb > 0 ? wb : 1), 128, 0, s>>>(d, t, a);
-  k_adj_particles<<<152 * 8, 256, 0, s>>>(d, t, a);
+  k_adj_particles<<<sm_count() * 8, 256, 0, s>>>(d, t, a);
   long long cb = ((long long)d.ncell * 32 + 255) / 256;
-  if (cb > 152 * 16) cb = 152 * 16;
+  if (cb > sm_count() * 16) cb = sm_count() * 16;
   if (d.G > 32) k_adj_birth<2><<<(int)cb, 256, 0, s>>>(d, t, a);
   else k_adj_birth<1><<<(int)cb, 256, 0, s>>>(d, t, a);
   return cudaGetLastError();

@@ -29,14 +29,10 @@ struct ugkwp_handle {
   // the wave flux runs beside the particle kernel in the captured step
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // the survivor sort runs beside the source iteration in a sorting step
+  // the survivor sort runs beside the source iteration
   cudaStream_t sort_stream = nullptr;
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // single problems in mixed precision: every kSortEvery-th step replays a
-  // second graph whose end of step sorts the survivors by bin
-  cudaGraphExec_t exec_sort = nullptr;
-  unsigned long long launches = 0;
 };
 
 namespace {
@@ -268,6 +264,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.tau_num_C = p->tau_num_C;
   d.sig_law = p->sig_law;
   d.cv_law = p->cv_law;
+  d.split_literal = p->split_literal ? 1 : 0;
   d.cv_chi = p->cv_chi;
   d.src_t_end = p->src_t_end;
   d.method = p->method;
@@ -294,7 +291,6 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.fastdiv = (long long)d.ncell * d.G < (1ll << 24) ? 1 : 0;
   d.invG_f = 1.0f / (float)d.G;
   d.inv_nx_f = 1.0f / (float)d.nx;
-  d.sorting = 0;
   d.rec = nullptr;
   d.rec_cap = 0;
   d.tape = nullptr;
@@ -445,14 +441,14 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   int* d_bin0 = cv.take<int>(n + 1);
   int* d_fg0 = cv.take<int>(n + 1);
   int* d_tile0 = cv.take<int>(n + 1);
-  unsigned int* d_bar = cv.take<unsigned int>(1);
+  unsigned int* d_bar = cv.take<unsigned int>(4);   // barrier arrivals, then the tile counter (8-byte aligned)
   cudaError_t e;
   if ((e = cudaMemcpyAsync(d_devs, h->members.data(), sizeof(Dev) * n, cudaMemcpyHostToDevice, s))) return bad(e, "member table");
   if ((e = cudaMemcpyAsync(d_cell0, cell0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
   if ((e = cudaMemcpyAsync(d_bin0, bin0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
   if ((e = cudaMemcpyAsync(d_fg0, fg0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
   if ((e = cudaMemsetAsync(d_tile0, 0, sizeof(int) * (n + 1), s))) return bad(e, "tables");
-  if ((e = cudaMemsetAsync(d_bar, 0, sizeof(unsigned int), s))) return bad(e, "tables");
+  if ((e = cudaMemsetAsync(d_bar, 0, 4 * sizeof(unsigned int), s))) return bad(e, "tables");
   if ((e = cudaStreamSynchronize(s))) return bad(e, "init sync");
   ugkwp::Ens& E = h->ens;
   E.M = n;
@@ -462,6 +458,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   E.fg0 = d_fg0;
   E.tile0 = d_tile0;
   E.bar = d_bar;
+  E.tile_next = reinterpret_cast<unsigned long long*>(d_bar + 2);
   E.total_bins = bin0[n];
   E.total_fg = fg0[n];
   E.total_cells = cell0[n];
@@ -484,9 +481,9 @@ int ugkwp_init(const ugkwp_problem* p, void* d_workspace, size_t bytes, void* st
 namespace {
 
 // Side branches of a captured step: the wave flux (it needs only the birth
-// kernel's sampled fractions) beside the particle kernel, and in a sorting
-// step the survivor sort (it needs only the particle kernel's counts)
-// beside the source iteration, which touches no particle.
+// kernel's sampled fractions) beside the particle kernel, and the survivor
+// sort (it needs only the particle kernel's slots and counts) beside the
+// source iteration, which touches no particle.
 struct Branches {
   cudaStream_t side = nullptr, sort = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
@@ -507,20 +504,16 @@ cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::Str
     if (!r) r = ugkwp::launch_wave(d, e, s);
     if (!r) r = ugkwp::launch_stream(d, e, sh, s);
   }
-  if (d.sorting) {
-    if (b.sort) {
-      if (!r) r = cudaEventRecord(b.fork2, s);
-      if (!r) r = cudaStreamWaitEvent(b.sort, b.fork2, 0);
-      if (!r) r = ugkwp::launch_sort(d, b.sort);
-      if (!r) r = cudaEventRecord(b.join2, b.sort);
-      if (!r) r = ugkwp::launch_si(d, e, s);
-      if (!r) r = cudaStreamWaitEvent(s, b.join2, 0);
-    } else {
-      if (!r) r = ugkwp::launch_si(d, e, s);
-      if (!r) r = ugkwp::launch_sort(d, s);
-    }
+  if (b.sort) {
+    if (!r) r = cudaEventRecord(b.fork2, s);
+    if (!r) r = cudaStreamWaitEvent(b.sort, b.fork2, 0);
+    if (!r) r = ugkwp::launch_sort(d, e, b.sort);
+    if (!r) r = cudaEventRecord(b.join2, b.sort);
+    if (!r) r = ugkwp::launch_si(d, e, s);
+    if (!r) r = cudaStreamWaitEvent(s, b.join2, 0);
   } else {
     if (!r) r = ugkwp::launch_si(d, e, s);
+    if (!r) r = ugkwp::launch_sort(d, e, s);
   }
   if (!r) r = ugkwp::launch_end_step(d, e, s);
   return r;
@@ -528,27 +521,18 @@ cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::Str
 
 void drop_graph(ugkwp_handle* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
-  if (h->exec_sort) cudaGraphExecDestroy(h->exec_sort);
   h->exec = nullptr;
-  h->exec_sort = nullptr;
 }
 
-constexpr unsigned kSortEvery = 4;
-
-bool sorts(const ugkwp_handle* h) { return h->M == 1 && h->d.precision == UGKWP_MIXED; }
-
 // Capture one step (every kernel reads the step's counts from the device
-// control block, so the same graph serves every step); with sorted = true
-// the step whose end sorts the survivors.
-int capture_one(ugkwp_handle* h, bool sorted, cudaGraphExec_t* out) {
+// control block, so the same graph serves every step).
+int capture_one(ugkwp_handle* h, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), h);
-  Dev d = h->d;
-  d.sorting = sorted ? 1 : 0;
   Branches b;
   b.side = h->side_stream; b.fork = h->ev_fork; b.join = h->ev_join;
   b.sort = h->sort_stream; b.fork2 = h->ev_fork2; b.join2 = h->ev_join2;
-  cudaError_t e = enqueue_step_dev(d, h->M > 1 ? &h->ens : nullptr, h->shape, h->cap_stream, b);
+  cudaError_t e = enqueue_step_dev(h->d, h->M > 1 ? &h->ens : nullptr, h->shape, h->cap_stream, b);
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
   if (e) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capturing the step"); }
   if (e2) return cuda_fail(h, e2, "end of capture");
@@ -568,8 +552,7 @@ int capture_step(ugkwp_handle* h) {
     CK(cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming), h);
     CK(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming), h);
   }
-  int st = capture_one(h, false, &h->exec);
-  if (!st && sorts(h)) st = capture_one(h, true, &h->exec_sort);
+  int st = capture_one(h, &h->exec);
   if (st) drop_graph(h);
   return st;
 }
@@ -586,10 +569,7 @@ int ugkwp_step(ugkwp_handle* h, int nsteps, void* stream) {
     int st = capture_step(h);
     if (st) return st;
   }
-  for (int n = 0; n < nsteps; ++n) {
-    const bool sort_now = h->exec_sort && ++h->launches % kSortEvery == 0;
-    CK(cudaGraphLaunch(sort_now ? h->exec_sort : h->exec, s), h);
-  }
+  for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->exec, s), h);
   return UGKWP_OK;
 }
 
@@ -609,6 +589,7 @@ int ugkwp_step_timed(ugkwp_handle* h, void* stream, float* phase_ms) {
   if (!e) e = cudaEventRecord(ev[3], s);
   if (!e) e = ugkwp::launch_si(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[4], s);
+  if (!e) e = ugkwp::launch_sort(h->d, en, s);
   if (!e) e = ugkwp::launch_end_step(h->d, en, s);
   if (!e) e = cudaEventRecord(ev[5], s);
   if (!e) e = cudaEventSynchronize(ev[5]);
@@ -638,6 +619,7 @@ int ugkwp_tallies_member(ugkwp_handle* h, int m, ugkwp_tally_report* out, void* 
   out->n_absorbed = (int64_t)c.n_absorbed; out->n_escaped = (int64_t)c.n_escaped;
   out->n_removed = (int64_t)c.n_removed; out->n_segments = (int64_t)c.n_segments;
   out->si_iters = (int32_t)c.si_iters;
+  out->n_scaled_bins = (int64_t)c.n_scaled_bins;
   out->status_bits = c.status;
   out->E_rad0 = c.E_rad0; out->E_mat0 = c.E_mat0; out->E_rad1 = c.E_rad1; out->E_mat1 = c.E_mat1;
   out->bnd_in_macro = c.bnd_in_macro; out->bnd_in_part = c.bnd_in_part;
@@ -957,6 +939,8 @@ int adjoint_check(ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint tape is written by the FP64 particle kernel");
   if (h->d.tau_num_C != 0.0)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates tau, not tau_num (tau_num_C = 0)");
+  if (h->d.split_literal)
+    return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint is checked with the default wave/particle split (split_literal = 0)");
   if (h->d.sig_law != 0)
     return fail(h, UGKWP_ERR_UNSUPPORTED, "the adjoint differentiates the power-law opacity (sig_law = 0)");
   if (h->d.cv_law != 0)

@@ -22,12 +22,19 @@ constexpr double k15overPi4 = 15.0 / (kPi * kPi * kPi * kPi);
 
 enum { BC_REFLECT = 0, BC_VACUUM = 1, BC_BLACKBODY = 2 };
 enum { FATE_SURVIVED = 0, FATE_ABSORBED = 1, FATE_ESCAPED = 2, FATE_REMOVED = 3 };
-enum : uint32_t { ST_CAPACITY = 1u, ST_NOCONV = 2u, ST_NONFINITE = 4u, ST_TIMEOUT = 8u };
+enum : uint32_t { ST_CAPACITY = 1u, ST_NOCONV = 2u, ST_NONFINITE = 4u, ST_TIMEOUT = 8u, ST_IDSPACE = 16u };
 
 // Bits of a newborn's 64-bit identity: (birth step << 44) | (bin << 20) | k.
+// The step takes the top 20 bits: a handle refuses to step past 2^20 - 1
+// (identities, and with them the random streams, would repeat).
 constexpr int kIdBinShift = 20;
 constexpr int kIdStepShift = 44;
 constexpr uint32_t kMaxPerBin = (1u << 20) - 1u;
+constexpr unsigned long long kMaxStep = (1ull << 20) - 1ull;
+
+// Key of a slot the particle kernel leaves empty (a particle that did not
+// survive, written in place); the survivor sort skips it.
+constexpr uint32_t kDeadKey = 0xffffffffu;
 
 // --------------------------------------------------------------------------
 // Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
@@ -217,6 +224,7 @@ struct Dev {
   int grey, wave_order, si_max_iters, precision, sig_law;
   int method;        // 0 UGKWP, 1 UGKP (all of I^h sampled; newborns draw t_f)
   int cv_law;        // 0 constant cv; 1 Olson foam heat capacity
+  int split_literal; // 1: rho^h = rho^{n+1} - E_surv/V as written (no survivor scaling)
   double cv_chi, src_t_end;
   int bc[6];          // sides x-, x+, y-, y+, z-, z+
   double dx, dy, dz, vol, sig_p, sig_q, sig_cap, a, c, eps, dt;
@@ -247,9 +255,7 @@ struct Dev {
   uint32_t* N;      // [nbins]
   uint32_t* off;    // [nbins+1] exclusive scan of N
   uint32_t* part;   // [scan partials]
-  // counting sort of the survivors by bin (single problems, mixed precision,
-  // the steps of the sorting graph: sorting = 1)
-  int sorting;
+  // counting sort of the survivors by bin (every step)
   uint32_t* sort_cnt;   // [nbins] survivors per bin this step
   uint32_t* sort_off;   // [nbins+1] their exclusive scan, then the bins' write cursors
   uint32_t* sort_part;  // [scan partials]
@@ -259,8 +265,8 @@ struct Dev {
   double* khat;     // [nbins] sampler slope in units of B(nu_mid)
   double* W;        // [ncell*G] (FP64 copy written by the source iteration)
   double* E_surv;   // [ncell*G] (FP64 copy written by the source iteration)
-  unsigned long long* Wq;    // [ncell*G][2] W in 128-bit fixed point (accumulated)
-  unsigned long long* Esq;   // [ncell*G][2] E_surv in 128-bit fixed point (accumulated)
+  unsigned long long* Wq;    // [ncell*G][2] W in fixed point (accumulated, see atomic_add_fixed)
+  unsigned long long* Esq;   // [ncell*G][2] E_surv in fixed point (accumulated)
   double inv_dx, inv_dy, inv_dz, inv_c, inv_vol;
   double inv_2dt;             // 1/(2 dt)
   double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-48) and its inverse
@@ -365,15 +371,18 @@ struct Ens {
   const int* fg0;         // [M+1] prefix of nface*G
   int* tile0;             // [M+1] prefix of this step's particle tiles (written on the device)
   unsigned int* bar;      // grid-barrier arrivals of the ensemble source iteration
+  unsigned long long* tile_next;   // next particle tile to hand out (reset with bar each step)
   // totals known on the host (launch shapes)
   long long total_bins, total_fg, total_cells;
   int max_parts, max_G;
   int tile;               // particles per tile of the particle kernel (block x particles per thread)
 };
 
-// Launch shape of the particle kernel (picked by the autotuner).
+// Launch shape of the particle kernel (picked by the autotuner).  The
+// mixed-precision kernel adds one producer warp to `block` streaming threads
+// and streams tiles of block x ppt particles.
 struct StreamShape {
-  int block = 256;        // threads per block: 128, 256 or 512
+  int block = 256;        // streaming threads per block: 128, 256 or 512
   int ppt = 1;            // particles per thread per tile: 1 or 2
   int blocks_per_sm = 0;  // 0: as many as fit
 };
@@ -412,8 +421,9 @@ struct TapeRec {
 // shows in the last bits, and through T in every later decision.  Each
 // weight is instead rounded once to a fixed quantum q (a power of two between
 // omega_ref 2^-49 and omega_ref 2^-48, a few 1e-15 of a reference weight) and
-// the integers are added in 128 bits with integer atomics, which commute: a
-// run is bitwise reproducible.  Weights up to 2^57 q (at least 256 omega_ref)
+// the integers are added with integer atomics (a 32-bit low part and a
+// signed high part per tally, atomic_add_fixed), which commute: a run is
+// bitwise reproducible.  Weights up to 2^57 q (at least 256 omega_ref)
 // are representable; a larger one sets the non-finite status bit.
 constexpr double kFixedRange = 0x1p57;   // |w/q| below this: a warp's 32 add up without overflow
 
@@ -445,26 +455,28 @@ __device__ __forceinline__ long long to_fixed_f(float w, int shift, unsigned int
   return (b >> 31) ? -r : r;
 }
 
-// 128-bit two's-complement add of a signed 64-bit increment: c[0] low word,
-// c[1] high word; the carry out of the low word is taken from its old value.
+// Carry-free 96-bit accumulation of signed 64-bit increments x = xh 2^32 + xl
+// (xl = the low 32 bits, unsigned; xh = x >> 32, signed): c[0] sums the xl
+// (below 2^32 each, so 2^32 of them cannot overflow 64 bits) and c[1] the xh
+// in two's complement.  Both adds are fire-and-forget reductions: nothing
+// waits for an old value, and the integer sums still commute, so a run stays
+// bitwise reproducible.  The value is c[1] 2^32 + c[0].
 __device__ __forceinline__ void atomic_add_fixed(unsigned long long* c, long long x) {
   if (x == 0) return;
-  const unsigned long long ux = (unsigned long long)x;
-  const unsigned long long old = atomicAdd(c, ux);
-  const unsigned long long carry = (old + ux < old) ? 1ull : 0ull;
-  const unsigned long long hinc = (x < 0 ? ~0ull : 0ull) + carry;
-  if (hinc) atomicAdd(c + 1, hinc);
+  const unsigned long long lo = (unsigned long long)x & 0xffffffffull;
+  const unsigned long long hi = (unsigned long long)(x >> 32);
+  if (lo) atomicAdd(c, lo);
+  if (hi) atomicAdd(c + 1, hi);
 }
 
+// The accumulated value times q, rounded once: c[1] 2^32 + c[0] is formed
+// exactly as H 2^32 + L with L < 2^32 (H = c[1] + (c[0] >> 32), |H| < 2^53 for
+// any tally this code holds), so only the final addition rounds.
 __device__ __forceinline__ double from_fixed(const unsigned long long* c, double q) {
-  unsigned long long lo = __ldcg(c), hi = __ldcg(c + 1);
-  const bool neg = (long long)hi < 0;
-  if (neg) {
-    lo = ~lo + 1ull;
-    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-  }
-  const double v = ((double)hi * 0x1p64 + (double)lo) * q;
-  return neg ? -v : v;
+  const unsigned long long lo = __ldcg(c), hi = __ldcg(c + 1);
+  const long long H = (long long)hi + (long long)(lo >> 32);
+  const double L = (double)(lo & 0xffffffffull);
+  return fma((double)H, 0x1p32, L) * q;
 }
 
 // Device control block: counters, status, barrier and reduction slots.
@@ -481,6 +493,9 @@ struct Ctrl {
   unsigned int bar_extra;         // arrivals a barrier also waits for (failure injection; 0)
   unsigned int scaled;            // some survivors' weights need scaling this step
   unsigned int fin_count;         // blocks done in the end-of-step kernel (0 between steps)
+  unsigned long long tile_next;   // next particle tile to hand out (particle kernel; 0 at step start)
+  unsigned int n_scaled_bins;     // (cell, group) bins whose survivors were scaled this step
+  unsigned int pad_;
   unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)
   double E_rad0, E_mat0, E_rad1, E_mat1, bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
 };

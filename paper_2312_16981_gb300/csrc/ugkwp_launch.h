@@ -1,9 +1,17 @@
 // ugkwp_launch.h -- host-side launchers of the device kernels (internal).
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include "ugkwp_device.cuh"
 
 namespace ugkwp {
+
+constexpr int kMaxDevices = 64;
+// multiprocessors of the current device (looked up once per device)
+int sm_count();
+// counts per block of the three-kernel scan (launch_scan): its scratch holds
+// one partial sum per (n + kScanTileCounts - 1) / kScanTileCounts
+constexpr long long kScanTileCounts = 4096;
 
 cudaError_t launch_init_tables(const Dev& d, const double* src_T, const double* src_amp, int init_rho,
                                cudaStream_t s);
@@ -15,8 +23,9 @@ cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s);
 cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s);
 cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s);
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s);
-// survivor sort of a sorting step (d.sorting): scan of the counts, scatter
-cudaError_t launch_sort(const Dev& d, cudaStream_t s);
+// survivor sort of every step: scan of the survivors per bin, scatter back
+// into the input buffer in bin order
+cudaError_t launch_sort(const Dev& d, const Ens* e, cudaStream_t s);
 
 size_t ckpt_bytes(const Dev& d);
 cudaError_t launch_checkpoint(const Dev& d, const Ens* e, char* buf, const size_t* d_offs, int save,

@@ -101,12 +101,14 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     ctrl->n_removed = ctrl->n_segments = 0;
     ctrl->bar_count = 0;
     ctrl->scaled = 0;
+    ctrl->tile_next = 0;
+    ctrl->n_scaled_bins = 0;
     for (int s = 0; s < 3; ++s) ctrl->err_slot[s][0] = ctrl->err_slot[s][1] = 0ull;
     ctrl->E_rad0 = ctrl->E_mat0 = ctrl->E_rad1 = ctrl->E_mat1 = 0.0;
     ctrl->bnd_in_macro = ctrl->bnd_in_part = ctrl->bnd_out_part = ctrl->src_in = 0.0;
   }
   const int G = d.G;
-  if (d.sorting) d.sort_cnt[b] = 0u;   // the particle kernel counts the survivors per bin
+  d.sort_cnt[b] = 0u;   // the particle kernel counts the survivors it stores per bin
   {
     const int cell = b / G, g = b - cell * G;
     double E, sig, Tb;
@@ -178,7 +180,11 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     if (!all) E *= e;
     uint32_t N = 0;
     double w = 0.0, ee = 0.0;
-    if (d.omega_ref > 0.0 && E > 0.0) {
+    // a newborn's identity holds its birth step in 20 bits: past that no
+    // particle is sampled (the step is flagged)
+    const bool id_ok = d.ctrl->step <= kMaxStep;
+    if (!id_ok && b == 0) atomicOr(&ctrl->status, ST_IDSPACE);
+    if (id_ok && d.omega_ref > 0.0 && E > 0.0) {
       double q = floor(E / d.omega_ref + 0.5);
       if (q > (double)kMaxPerBin) { q = (double)kMaxPerBin; atomicOr(&ctrl->status, ST_CAPACITY); }
       N = (uint32_t)q;
@@ -201,6 +207,7 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
 // Exclusive scan of the birth counts: per-block sums, a one-block scan of
 // the sums, then per-block scans with their offsets.  Tile = 4096 bins.
 constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+static_assert(kScanTile == kScanTileCounts, "scan tile and the scratch size it implies");
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
   __shared__ uint32_t s_warp[32];
@@ -300,23 +307,38 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
   scan_apply_body(N, n, part, off, blockIdx.x);
 }
 
-// Ensemble: one scan per member, member = blockIdx.y.
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_ens(const Ens e) {
-  const Dev& d = e.devs[blockIdx.y];
-  if ((long long)blockIdx.x * kScanTile >= d.nbins) return;
-  scan_reduce_body(d.N, d.nbins, d.part, blockIdx.x);
+// Ensemble: one scan per member, member = blockIdx.y; which = 0 scans the
+// birth counts (totals to n_new, n_born), which = 1 the survivors per bin of
+// the sort (total to n_out).
+struct ScanArrays {
+  const uint32_t* cnt;
+  uint32_t *off, *part;
+  unsigned long long *total_a, *total_b;
+};
+
+__device__ __forceinline__ ScanArrays scan_arrays(const Dev& d, int which) {
+  if (which) return ScanArrays{d.sort_cnt, d.sort_off, d.sort_part, &d.ctrl->n_out, nullptr};
+  return ScanArrays{d.N, d.off, d.part, &d.ctrl->n_new, &d.ctrl->n_born};
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials_ens(const Ens e) {
-  const Dev& d = e.devs[blockIdx.y];
-  scan_partials_body(d.part, (d.nbins + kScanTile - 1) / kScanTile, d.off + d.nbins, &d.ctrl->n_new,
-                     &d.ctrl->n_born);
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply_ens(const Ens e) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_ens(const Ens e, int which) {
   const Dev& d = e.devs[blockIdx.y];
   if ((long long)blockIdx.x * kScanTile >= d.nbins) return;
-  scan_apply_body(d.N, d.nbins, d.part, d.off, blockIdx.x);
+  const ScanArrays a = scan_arrays(d, which);
+  scan_reduce_body(a.cnt, d.nbins, a.part, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials_ens(const Ens e, int which) {
+  const Dev& d = e.devs[blockIdx.y];
+  const ScanArrays a = scan_arrays(d, which);
+  scan_partials_body(a.part, (d.nbins + kScanTile - 1) / kScanTile, a.off + d.nbins, a.total_a, a.total_b);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply_ens(const Ens e, int which) {
+  const Dev& d = e.devs[blockIdx.y];
+  if ((long long)blockIdx.x * kScanTile >= d.nbins) return;
+  const ScanArrays a = scan_arrays(d, which);
+  scan_apply_body(a.cnt, d.nbins, a.part, a.off, blockIdx.x);
 }
 
 // Ensemble: prefix over members of this step's particle tiles (survivors +
@@ -324,7 +346,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply_ens(const Ens e) {
 __global__ void __launch_bounds__(1024) k_tiles(const Ens e) {
   const unsigned long long kParticleTile = (unsigned long long)e.tile;
   __shared__ int s_carry;
-  if (threadIdx.x == 0) { s_carry = 0; *e.bar = 0u; }
+  if (threadIdx.x == 0) { s_carry = 0; *e.bar = 0u; *e.tile_next = 0ull; }
   __syncthreads();
   for (int base = 0; base < e.M; base += blockDim.x) {
     const int m = base + threadIdx.x;
@@ -848,14 +870,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       if (ENS && m != acc_m && acc_m >= 0) {
         e_rad1 = warp_sum(e_rad1);
         b_in = warp_sum(b_in);
-        const bool sc_any = __any_sync(0xffffffffu, scaled);
+        const unsigned sc_n = __reduce_add_sync(0xffffffffu, (unsigned)scaled);
         if (lane == 0) {
           Ctrl* cc = e.devs[acc_m].ctrl;
           atomicAdd(&cc->E_rad1, e_rad1);
           atomicAdd(&cc->E_mat1, e_mat1);
           if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
           if (bad) atomicOr(&cc->status, ST_NONFINITE);
-          if (sc_any) atomicOr(&cc->scaled, 1u);
+          if (sc_n) { atomicOr(&cc->scaled, 1u); atomicAdd(&cc->n_scaled_bins, sc_n); }
         }
         e_rad1 = e_mat1 = b_in = 0.0;
         bad = 0;
@@ -887,10 +909,10 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const double Es = from_fixed(d.Esq + 2 * i, d.tq);
         d.E_surv[i] = Es;
         double rp = Es * d.inv_vol, f = 1.0;
-        if (rp > 0.0 && r < rp) {
+        if (!d.split_literal && rp > 0.0 && r < rp) {
           f = r > 0.0 ? r / rp : 0.0;
           rp = r > 0.0 ? r : 0.0;
-          scaled = 1;
+          scaled += 1;
         }
         d.wscale[i] = f;
         d.rho_p[i] = rp;
@@ -920,9 +942,11 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
       if (bad) atomicOr(&cc->status, ST_NONFINITE);
     }
-    if (__any_sync(0xffffffffu, scaled) && lane == 0 && acc_m >= 0) {
+    const unsigned sc_n = __reduce_add_sync(0xffffffffu, (unsigned)scaled);
+    if (sc_n && lane == 0 && acc_m >= 0) {
       Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
       atomicOr(&cc->scaled, 1u);
+      atomicAdd(&cc->n_scaled_bins, sc_n);
     }
   }
   if (blockIdx.x == 0) {
@@ -936,19 +960,19 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   (void)all_done;
 }
 
-// End of step: swap particle buffers, advance the step counter, particle
-// ledger from the side tallies.
+// End of step (ensembles): the sorted survivors are back in the input buffer,
+// which stays the live one; advance the step counter, particle ledger from
+// the side tallies.
 template <bool ENS>
-__global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e, int sorted) {
+__global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
   const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
   Ctrl* ctrl = d.ctrl;
   if (threadIdx.x == 0) {
     const unsigned long long n = ctrl->n_out;
     const unsigned long long cap = (unsigned long long)d.capacity;
-    const unsigned live = sorted ? ctrl->cur : ctrl->cur ^ 1u;   // sorted: back in the input buffer
+    const unsigned live = ctrl->cur;
     ctrl->n_part[live] = n < cap ? n : cap;
     ctrl->n_part[live ^ 1u] = 0;
-    ctrl->cur = live;
     ctrl->step += 1;
   }
   __syncthreads();
@@ -966,7 +990,7 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e, int sort
 
 // Survivors' weights scaled by the factor the source-iteration epilogue set
 // for their (cell, group) (a reading where the paper is silent: the particle
-// part never exceeds rho^{n+1}).  Runs after the buffer swap; a member with
+// part never exceeds rho^{n+1}).  Runs after the survivor sort; a member with
 // nothing to scale returns at once.
 // Scale the weights of buffer b's first n particles by their bins' factors.
 __device__ __forceinline__ void scale_weights(const Dev& d, unsigned b, long long n) {
@@ -1004,17 +1028,16 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
   scale_weights(d, cur, (long long)ctrl->n_part[cur]);
 }
 
-// End of step of a single problem in one launch: the survivors' weights are
-// scaled in their buffer (the output buffer, or the input buffer the sort
-// moved them back to), then the last block to finish makes that buffer the
-// live one, advances the step and sums the particle ledger (every block has
-// read the control block before it counts itself done).
-__global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev d, int sorted) {
+// End of step of a single problem in one launch: the sorted survivors'
+// weights are scaled in the input buffer, then the last block to finish
+// records their count, advances the step and sums the particle ledger (every
+// block has read the control block before it counts itself done).
+__global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev d) {
   Ctrl* ctrl = d.ctrl;
-  const unsigned out = sorted ? ctrl->cur : ctrl->cur ^ 1u;
+  const unsigned live = ctrl->cur;
   const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
   const long long n = (long long)(no < cap ? no : cap);
-  if (ctrl->scaled) scale_weights(d, out, n);
+  if (ctrl->scaled) scale_weights(d, live, n);
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1024,9 +1047,8 @@ __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev
   __syncthreads();
   if (!s_last) return;
   if (threadIdx.x == 0) {
-    ctrl->n_part[out] = (unsigned long long)n;
-    ctrl->n_part[out ^ 1u] = 0;
-    ctrl->cur = out;
+    ctrl->n_part[live] = (unsigned long long)n;
+    ctrl->n_part[live ^ 1u] = 0;
     ctrl->step += 1;
     ctrl->fin_count = 0;
   }
@@ -1043,21 +1065,18 @@ __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev
 }
 
 // --------------------------------------------------------------------------
-// Counting sort of the survivors by bin (cell, group), in the steps of the
-// sorting graph (single problems, mixed precision, one step in four).  The
-// compaction leaves survivors in block order, and the particles that cross a
-// face keep their slot while each step's newborns are appended, so within a
-// few steps the lanes of a warp hold different bins (the warp tallies lose
-// their one-bin path, the per-cell tables are gathered).  The particle kernel
-// counts the survivors per bin with its survivor tallies; the counts are
-// scanned; the scatter moves the survivors from the output buffer back into
-// the input buffer in bin order, beside the source iteration (which touches
-// no particle); k_finish_step then scales the sorted survivors.  The order
-// inside a bin
-// follows the cursor atomics: nothing depends on it (random streams are keyed
-// by particle identity, tallies are integer sums).  After a capacity overflow
-// the counts include survivors that were dropped, so that step copies in
-// place order instead.
+// Survivor sort by bin (cell, group), every step and in every build.  The
+// particle kernel left each particle of the step in its slot of the other
+// buffer, survivors with their end bin and the rest marked kDeadKey, and
+// counted the stored survivors per bin; the counts are scanned into write
+// cursors (their total is the step's survivor count, n_out), and this
+// scatter moves every survivor into the input buffer at its bin's cursor.
+// It runs beside the source iteration, which touches no particle; the end
+// of step then scales the sorted survivors.  The order inside a bin follows
+// the cursor atomics: nothing depends on it (random streams are keyed by
+// particle identity, tallies are integer sums).  A taped FP64 step also
+// records each survivor's new slot in its tape entry (where the adjoint
+// finds the particle in the next step's input).
 
 // Runs of equal keys among the warp's lanes: start lane of this lane's run
 // and its length (at every lane of the run).
@@ -1071,55 +1090,111 @@ __device__ __forceinline__ void warp_runs(uint32_t key, int* start, int* len) {
   *len = (after ? __ffs(after) - 1 : 32) - *start;
 }
 
-// One contiguous chunk of whole 32-slices per warp, so that warps running at
-// the same time work on different bins of the (nearly sorted) survivors.
-__device__ __forceinline__ void warp_chunk(long long n, long long* lo, long long* hi) {
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long per = ((n + nw - 1) / nw + 31) & ~31ll;
-  *lo = w * per;
-  *hi = *lo + per < n ? *lo + per : n;
+template <typename F>
+struct PartBufs {
+  F *x, *ox, *nu, *w, *y, *oy, *z, *oz;
+  unsigned long long* id;
+  uint32_t* key;
+};
+
+template <typename F>
+__device__ __forceinline__ PartBufs<F> part_bufs(const Dev& d, unsigned b);
+template <>
+__device__ __forceinline__ PartBufs<float> part_bufs<float>(const Dev& d, unsigned b) {
+  return PartBufs<float>{d.fx[b], d.fox[b], d.fnu[b], d.fw[b], d.fy[b], d.foy[b], d.fz[b], d.foz[b],
+                         d.pid[b], d.pkey[b]};
+}
+template <>
+__device__ __forceinline__ PartBufs<double> part_bufs<double>(const Dev& d, unsigned b) {
+  return PartBufs<double>{d.px[b], d.pox[b], d.pnu[b], d.pw[b], d.py[b], d.poy[b], d.pz[b], d.poz[b],
+                          d.pid[b], d.pkey[b]};
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(const __grid_constant__ Dev d) {
-  const Ctrl* ctrl = d.ctrl;
-  const unsigned cur = ctrl->cur, nxb = cur ^ 1u;
-  const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
-  const long long n = (long long)(no < cap ? no : cap);
-  const bool ordered = no <= cap;
-  const int dim = d.dim;
-  const uint32_t* __restrict__ key = d.pkey[nxb];
+// Two 32-slices [i0, i0 + 64) of the step's slots (below n): loads of both
+// first, then both cursor atomics, then the stores, so a warp has two
+// round trips in flight.
+template <typename F, int DIM>
+__device__ __forceinline__ void scatter_two(const Dev& d, unsigned cur, long long i0, long long n) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  long long lo, hi;
-  warp_chunk(n, &lo, &hi);
-  for (long long base = lo; base < hi; base += 32) {
-    const long long i = base + lane;
-    const bool valid = i < hi;
-    uint32_t k = 0xffffffffu;
-    unsigned long long id = 0ull;
-    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (valid) {
-      k = __ldg(key + i);
-      id = d.pid[nxb][i];
-      a[0] = d.fx[nxb][i]; a[1] = d.fox[nxb][i]; a[2] = d.fnu[nxb][i]; a[3] = d.fw[nxb][i];
-      if (dim >= 2) { a[4] = d.fy[nxb][i]; a[5] = d.foy[nxb][i]; }
-      if (dim == 3) { a[6] = d.fz[nxb][i]; a[7] = d.foz[nxb][i]; }
+  const PartBufs<F> src = part_bufs<F>(d, cur ^ 1u), dst = part_bufs<F>(d, cur);
+  uint32_t k[2];
+  unsigned long long id[2];
+  F a[2][8];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const long long i = i0 + 32 * q + lane;
+    k[q] = i < n ? __ldcs(src.key + i) : kDeadKey;
+    id[q] = 0ull;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) a[q][f] = F(0);
+    if (k[q] != kDeadKey) {
+      id[q] = __ldcs(src.id + i);
+      a[q][0] = __ldcs(src.x + i); a[q][1] = __ldcs(src.ox + i);
+      a[q][2] = __ldcs(src.nu + i); a[q][3] = __ldcs(src.w + i);
+      if (DIM >= 2) { a[q][4] = __ldcs(src.y + i); a[q][5] = __ldcs(src.oy + i); }
+      if (DIM == 3) { a[q][6] = __ldcs(src.z + i); a[q][7] = __ldcs(src.oz + i); }
     }
-    long long o = i;
-    if (ordered) {
-      int start, len;
-      warp_runs(k, &start, &len);
-      unsigned long long b = 0ull;
-      if (lane == start && valid) b = atomicAdd(d.sort_off + k, (unsigned)len);
-      b = __shfl_sync(0xffffffffu, b, start);
-      o = (long long)b + (lane - start);
+  }
+  long long o[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int start, len;
+    warp_runs(k[q], &start, &len);
+    unsigned b = 0u;
+    if (lane == start && k[q] != kDeadKey) b = atomicAdd(d.sort_off + k[q], (unsigned)len);
+    b = __shfl_sync(full, b, start);
+    o[q] = (long long)b + (lane - start);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (k[q] == kDeadKey) continue;
+    if (o[q] >= d.capacity) {   // counts and slots disagree: never expected
+      atomicOr(&d.ctrl->status, ST_CAPACITY);
+      continue;
     }
-    if (!valid || o >= n) continue;
-    d.fx[cur][o] = a[0]; d.fox[cur][o] = a[1]; d.fnu[cur][o] = a[2]; d.fw[cur][o] = a[3];
-    if (dim >= 2) { d.fy[cur][o] = a[4]; d.foy[cur][o] = a[5]; }
-    if (dim == 3) { d.fz[cur][o] = a[6]; d.foz[cur][o] = a[7]; }
-    d.pid[cur][o] = id;
-    d.pkey[cur][o] = k;
+    const long long j = o[q];
+    dst.x[j] = a[q][0]; dst.ox[j] = a[q][1]; dst.nu[j] = a[q][2]; dst.w[j] = a[q][3];
+    if (DIM >= 2) { dst.y[j] = a[q][4]; dst.oy[j] = a[q][5]; }
+    if (DIM == 3) { dst.z[j] = a[q][6]; dst.oz[j] = a[q][7]; }
+    dst.id[j] = id[q];
+    dst.key[j] = k[q];
+    const long long i = i0 + 32 * q + lane;
+    if (d.tape && i < d.tape_cap) d.tape[i].slot = (int)j;
+  }
+}
+
+template <typename F, int DIM, bool ENS>
+__global__ void __launch_bounds__(256) k_sort_scatter(const __grid_constant__ Dev d0, const Ens e) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  if (!ENS) {
+    const Ctrl* ctrl = d0.ctrl;
+    const unsigned cur = ctrl->cur;
+    const unsigned long long nt = ctrl->n_part[cur] + ctrl->n_new, cap = (unsigned long long)d0.capacity;
+    const long long n = (long long)(nt < cap ? nt : cap);
+    // one contiguous chunk of whole 64-slot pairs per warp, so warps running
+    // at the same time work on different bins of the (nearly sorted) slots
+    const long long per = ((n + nw - 1) / nw + 63) & ~63ll;
+    const long long lo = w * per, hi = lo + per < n ? lo + per : n;
+    for (long long i0 = lo; i0 < hi; i0 += 64) scatter_two<F, DIM>(d0, cur, i0, hi);
+    return;
+  }
+  // ensembles: the particle kernel's tiles (e.tile slots each), one warp per
+  // 64-slot pair of a tile
+  const long long tile = e.tile, pairs = (tile + 63) / 64;
+  const long long ntiles = (long long)e.tile0[e.M];
+  for (long long u = w; u < ntiles * pairs; u += nw) {
+    const long long t = u / pairs, pr = u - t * pairs;
+    const int m = find_member(e.tile0, e.M, t);
+    const Dev& d = e.devs[m];
+    const Ctrl* ctrl = d.ctrl;
+    const unsigned cur = ctrl->cur;
+    const unsigned long long nt = ctrl->n_part[cur] + ctrl->n_new, cap = (unsigned long long)d.capacity;
+    const long long n = (long long)(nt < cap ? nt : cap);
+    const long long base = (t - (long long)e.tile0[m]) * tile, i0 = base + 64 * pr;
+    const long long hi = base + tile < n ? base + tile : n;
+    if (i0 < hi) scatter_two<F, DIM>(d, cur, i0, hi);
   }
 }
 
@@ -1222,7 +1297,7 @@ cudaError_t launch_checkpoint(const Dev& d, const Ens* e, char* buf, const size_
                               cudaStream_t s) {
   const Ens none{};
   const int M = e && e->M > 1 ? e->M : 1;
-  k_checkpoint<<<dim3(152 * 4, M), 256, 0, s>>>(e && e->M > 1 ? *e : none, d, buf, d_offs, save);
+  k_checkpoint<<<dim3(sm_count() * 4, M), 256, 0, s>>>(e && e->M > 1 ? *e : none, d, buf, d_offs, save);
   return cudaGetLastError();
 }
 
@@ -1272,8 +1347,25 @@ __global__ void k_unit_sample(const double* eta, long long n, double nlo, double
 
 // --------------------------------------------------------------------------
 // host launchers
-static int grid_for(long long n, int threads, int cap = 152 * 16) {
+int sm_count() {
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev < kMaxDevices) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (n < 1) n = 1;
+  if (dev < kMaxDevices) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+// blocks for n items of `threads` each, at most `per_sm` blocks per SM
+static int grid_for(long long n, int threads, int per_sm = 16) {
   long long b = (n + threads - 1) / threads;
+  const long long cap = (long long)sm_count() * per_sm;
   if (b < 1) b = 1;
   if (b > cap) b = cap;
   return (int)b;
@@ -1326,11 +1418,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_small(const uint32_t* __r
 
 cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
-    k_birth<true><<<grid_for(e->total_bins, 64, 152 * 64), 64, 0, s>>>(d, *e);
+    k_birth<true><<<grid_for(e->total_bins, 64, 64), 64, 0, s>>>(d, *e);
     const dim3 g(e->max_parts, e->M);
-    k_scan_reduce_ens<<<g, kScanThreads, 0, s>>>(*e);
-    k_scan_partials_ens<<<dim3(1, e->M), kScanThreads, 0, s>>>(*e);
-    k_scan_apply_ens<<<g, kScanThreads, 0, s>>>(*e);
+    k_scan_reduce_ens<<<g, kScanThreads, 0, s>>>(*e, 0);
+    k_scan_partials_ens<<<dim3(1, e->M), kScanThreads, 0, s>>>(*e, 0);
+    k_scan_apply_ens<<<g, kScanThreads, 0, s>>>(*e, 0);
     k_tiles<<<1, 1024, 0, s>>>(*e);
     return cudaGetLastError();
   }
@@ -1345,7 +1437,7 @@ cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s) {
 
 cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
-    k_wave<true><<<grid_for(e->total_fg, 64, 152 * 64), 64, 0, s>>>(d, *e);
+    k_wave<true><<<grid_for(e->total_fg, 64, 64), 64, 0, s>>>(d, *e);
   } else {
     const Ens none{};
     k_wave<false><<<grid_for((long long)d.nface * d.G, 64), 64, 0, s>>>(d, none);
@@ -1400,24 +1492,44 @@ cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s) {
 
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
-    k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e, 0);
+    k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e);
     k_scale_survivors<true><<<dim3(8, e->M), 256, 0, s>>>(d, *e);
   } else {
-    k_finish_step<<<152 * 4, 256, 0, s>>>(d, d.sorting);
+    k_finish_step<<<sm_count() * 4, 256, 0, s>>>(d);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const Dev& d, cudaStream_t s) {
-  if (d.nbins <= 16 * kScanTile) {
-    k_scan_small<<<1, kScanThreads, 0, s>>>(d.sort_cnt, d.nbins, d.sort_off, nullptr, nullptr);
-  } else {
-    cudaError_t r = launch_scan(d.sort_cnt, d.nbins, d.sort_part, d.sort_off, nullptr, nullptr, s);
-    if (r) return r;
-  }
+template <typename F, bool ENS>
+static void launch_scatter(const Dev& d, const Ens& e, int blocks, cudaStream_t s) {
+  if (d.dim == 3) k_sort_scatter<F, 3, ENS><<<blocks, 256, 0, s>>>(d, e);
+  else if (d.dim == 2) k_sort_scatter<F, 2, ENS><<<blocks, 256, 0, s>>>(d, e);
+  else k_sort_scatter<F, 1, ENS><<<blocks, 256, 0, s>>>(d, e);
+}
+
+cudaError_t launch_sort(const Dev& d, const Ens* e, cudaStream_t s) {
   // a quarter of the SM threads: the scatter runs beside the source iteration,
   // whose cooperative blocks must find room on every SM
-  k_sort_scatter<<<152 * 2, 256, 0, s>>>(d);
+  const int blocks = sm_count() * 2;
+  const bool mixed = d.precision == 1;
+  if (e && e->M > 1) {
+    const dim3 g(e->max_parts, e->M);
+    k_scan_reduce_ens<<<g, kScanThreads, 0, s>>>(*e, 1);
+    k_scan_partials_ens<<<dim3(1, e->M), kScanThreads, 0, s>>>(*e, 1);
+    k_scan_apply_ens<<<g, kScanThreads, 0, s>>>(*e, 1);
+    if (mixed) launch_scatter<float, true>(d, *e, blocks, s);
+    else launch_scatter<double, true>(d, *e, blocks, s);
+    return cudaGetLastError();
+  }
+  if (d.nbins <= 16 * kScanTile) {
+    k_scan_small<<<1, kScanThreads, 0, s>>>(d.sort_cnt, d.nbins, d.sort_off, &d.ctrl->n_out, nullptr);
+  } else {
+    cudaError_t r = launch_scan(d.sort_cnt, d.nbins, d.sort_part, d.sort_off, &d.ctrl->n_out, nullptr, s);
+    if (r) return r;
+  }
+  const Ens none{};
+  if (mixed) launch_scatter<float, false>(d, none, blocks, s);
+  else launch_scatter<double, false>(d, none, blocks, s);
   return cudaGetLastError();
 }
 

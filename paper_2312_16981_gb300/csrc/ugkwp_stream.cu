@@ -1,24 +1,35 @@
-// ugkwp_stream.cu -- the particle kernel of the UGKWP step on sm_103a.
+// ugkwp_stream.cu -- the particle kernels of the UGKWP step on sm_103a.
 //
 // One persistent launch processes a virtual index space [0, n_surv + n_new):
 // first the particles that survived the previous step (Algorithm 1: a free
 // time t_f = min(-tau ln eta, dt), Eq. particle-tf-formula), then the
 // particles sampled this step from the wave part's collisionless fraction
-// (Eq. IhpFormula; born in registers with t_f = dt, never stored unless they
-// survive; in the UGKP variant all of the wave part is sampled and a newborn
-// draws its free time after its birth draws).  Each particle streams cell by
-// cell with the free time reset on entering a new cell (interface remark:
-// t_f2 = min(-tau_i ln eta, dt - t_tra)),
-// reflects at mirror walls, escapes through open sides.  Tallies: the net
-// particle energy per (cell, group) w^{fr,p} (Eq. wfrpFormula, accumulated as
-// end minus start, which telescopes the face crossings), the energy of the
-// collisionless survivors per end cell, escapes and inflow per side.
-// Collided particles are dropped (Algorithm 1, last step); survivors are
-// compacted into the other particle buffer (per block in the FP32 kernel,
-// per warp in the FP64 kernel).  The FP32 kernel of a single problem reads
-// its survivors from shared memory: one thread per block starts bulk copies
-// (cp.async.bulk, completion counted on an mbarrier) of the block's next tile
-// into the other of two stages while the block streams the current one.
+// (Eq. IhpFormula; born in registers with t_f = dt; in the UGKP variant all
+// of the wave part is sampled and a newborn draws its free time after its
+// birth draws).  Each particle streams cell by cell with the free time reset
+// on entering a new cell (interface remark: t_f2 = min(-tau_i ln eta,
+// dt - t_tra)), reflects at mirror walls, escapes through open sides.
+// Tallies: the net particle energy per (cell, group) w^{fr,p} (Eq.
+// wfrpFormula, accumulated as end minus start, which telescopes the face
+// crossings), the energy of the collisionless survivors per end bin, escapes
+// and inflow per side.
+//
+// Every processed particle is written in place: particle i of the step goes
+// to slot i of the other buffer, a particle that collided, escaped or left a
+// ghost leaves its slot marked dead (kDeadKey).  There is no compaction here,
+// so no atomics and no block barrier decide where a survivor goes; instead
+// the kernel counts the survivors per end bin, and the survivor sort (a scan
+// of the counts and a scatter, beside the source iteration) moves them back
+// into the input buffer in bin order.  That is Algorithm 1's last step
+// (collided particles removed) with the survivors kept cell-sorted.
+//
+// The FP32 kernel streams tiles of survivors staged in shared memory: one
+// producer warp per block takes the next tile from a global counter and
+// starts bulk copies (cp.async.bulk, completion counted on an mbarrier) of
+// its arrays into one of three stages; the streaming warps wait on a stage's
+// "full" barrier, process it and arrive on its "empty" barrier, so no warp
+// waits for another.  Per-cell opacity factors of single problems are held
+// in shared memory when they fit.
 #include "ugkwp_device.cuh"
 #include "ugkwp_launch.h"
 
@@ -36,17 +47,16 @@ __device__ __forceinline__ int find_bin(const uint32_t* __restrict__ off, int nb
 }
 
 // Sum the fixed-point weights v over runs of equal keys among consecutive
-// lanes and add each run's total once (keys < 0 contribute nothing).
-// Particles are held nearly sorted by (cell, group), so a warp usually
-// issues one 128-bit atomic per run.  Integer sums: the result does not
-// depend on which lanes meet in a warp.  Common case first: every lane with
-// a key holds the same key and v >= 0; then the warp sums v in three 21-bit
-// pieces with integer warp reductions (each piece's sum stays below 2^26;
-// v < 2^57 by the fixed-point range) instead of the segmented scan.  With
-// `cnt`, each run also adds its length to cnt[key] (the survivors per bin of
-// a sorting step).
+// lanes and add each run's total once (keys < 0 contribute nothing), and each
+// run's length to cnt[key] (the survivors per bin that the sort moves).
+// Particles are held sorted by (cell, group), so a warp usually issues one
+// add per run.  Integer sums: the result does not depend on which lanes meet
+// in a warp.  Common case first: every lane with a key holds the same key and
+// v >= 0; then the warp sums v in three 21-bit pieces with integer warp
+// reductions (each piece's sum stays below 2^26; v < 2^57 by the fixed-point
+// range) instead of the segmented scan.
 __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int key, long long v,
-                                                   uint32_t* cnt = nullptr) {
+                                                   uint32_t* cnt) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned keyed = __ballot_sync(full, key >= 0);
@@ -60,7 +70,7 @@ __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int
     const unsigned long long s2 = __reduce_add_sync(full, (unsigned)(u >> 42));
     if (lane == first) {
       atomic_add_fixed(base + 2 * (long long)k0, (long long)(s0 + (s1 << 21) + (s2 << 42)));
-      if (cnt) atomicAdd(cnt + k0, (unsigned)__popc(keyed));
+      atomicAdd(cnt + k0, (unsigned)__popc(keyed));
     }
     return;
   }
@@ -77,58 +87,8 @@ __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int
   const bool tail = lane == 31 || nxt != key;
   if (tail && key >= 0) {
     atomic_add_fixed(base + 2 * (long long)key, v);
-    if (cnt) atomicAdd(cnt + key, (unsigned)(lane - start + 1));
+    atomicAdd(cnt + key, (unsigned)(lane - start + 1));
   }
-}
-
-// Block compaction: exclusive rank of `flag` within the block plus the start
-// of the block's slots in the output buffer, reserved with one atomic by warp
-// 0.  Two barriers per tile; the shared slots are double-buffered by tile
-// parity, so a warp still reading this tile's values never sees the next
-// tile's writes (those happen after the next tile's first barrier).
-__device__ __forceinline__ unsigned long long block_slots(bool flag, int parity, unsigned long long* counter,
-                                                          unsigned* rank) {
-  __shared__ unsigned s_cnt[2][32];
-  __shared__ unsigned long long s_base[2];
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const unsigned b = __ballot_sync(full, flag);
-  if (lane == 0) s_cnt[parity][wid] = __popc(b);
-  __syncthreads();
-  if (wid == 0) {
-    const unsigned x = lane < nw ? s_cnt[parity][lane] : 0u;
-    unsigned inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned t = __shfl_up_sync(full, inc, o);
-      if (lane >= o) inc += t;
-    }
-    if (lane < nw) s_cnt[parity][lane] = inc - x;
-    if (lane == nw - 1) s_base[parity] = inc ? atomicAdd(counter, (unsigned long long)inc) : 0ull;
-  }
-  __syncthreads();
-  *rank = s_cnt[parity][wid] + __popc(b & ((1u << lane) - 1u));
-  return s_base[parity];
-}
-
-// Warp compaction: rank of `flag` among the warp's lanes and the start of the
-// warp's slots, reserved with one atomic by the warp's first flagged lane.
-// No block barrier: the FP64 kernel's particles differ widely in their cost
-// (segments), and block compaction left warps waiting on the block's slowest.
-// (The FP32 kernel keeps block compaction: at its rate one atomic per warp
-// contends, and block-contiguous survivors keep the bins' runs longer.)
-__device__ __forceinline__ unsigned long long warp_slots(bool flag, unsigned long long* counter, unsigned* rank) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const unsigned b = __ballot_sync(full, flag);
-  unsigned long long base = 0ull;
-  if (b) {
-    const int leader = __ffs(b) - 1;
-    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(b));
-    base = __shfl_sync(full, base, leader);
-  }
-  *rank = __popc(b & ((1u << lane) - 1u));
-  return base;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -139,8 +99,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // --------------------------------------------------------------------------
 // Bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) that
-// stage the next tile's particle arrays in shared memory while the block
-// streams the current tile.
+// stage tiles of particle arrays in shared memory.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -152,6 +111,9 @@ __device__ __forceinline__ void mbar_init_fence() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
@@ -192,9 +154,20 @@ struct StageF {
   }
 };
 
-size_t stream32_stage_bytes(int dim, int tile) {
+constexpr int kStages = 3;          // shared-memory stages of the FP32 kernel
+constexpr int kSmemCells = 4096;    // per-cell opacity factors held in shared memory up to this many cells
+
+static size_t stream32_stage_bytes(int dim, int tile) {
   const int per = dim == 3 ? StageF<3>::kBytesPer : (dim == 2 ? StageF<2>::kBytesPer : StageF<1>::kBytesPer);
-  return 2 * (size_t)tile * per;
+  return (size_t)tile * per;
+}
+
+// Shared-memory opacity table of a single problem: 1/(sigma0 T^q) per cell,
+// then 1/T per cell for the photo-ionisation law; none for the foam law or
+// grids above kSmemCells.
+static int stream32_table_floats(const Dev& d) {
+  if (d.sig_law == 2 || d.ncell > kSmemCells) return 0;
+  return d.ncell * (d.sig_law == 1 && !d.grey ? 2 : 1);
 }
 
 struct Counters {   // per thread; a thread sees far fewer than 2^32 events
@@ -215,8 +188,7 @@ __device__ __forceinline__ void flush_counters(Ctrl* ctrl, Counters& c) {
 }
 
 // Step-constant fields of a single problem's control block, read once per
-// thread (the tile loop would otherwise reload them: atomics on the same
-// block keep the compiler from hoisting the loads).
+// thread.
 struct StepHead {
   unsigned cur;
   long long n_surv, n_tot;
@@ -465,10 +437,28 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
       }
     }
 
-    // ---- tallies (W and E_surv in fixed point, see to_fixed)
+    // ---- in place: slot i of the other buffer (kDeadKey unless it survived)
+    const bool keep = valid && fate == FATE_SURVIVED;
+    const bool room = i < d.capacity;
+    const bool stored = keep && room;
+    if (valid && room) {
+      d.px[nxb][i] = x;
+      d.pox[nxb][i] = ox;
+      if (DIM >= 2) { d.py[nxb][i] = y; d.poy[nxb][i] = oy; }
+      if (DIM == 3) { d.pz[nxb][i] = z; d.poz[nxb][i] = oz; }
+      d.pnu[nxb][i] = nu;
+      d.pw[nxb][i] = w;
+      d.pid[nxb][i] = id;
+      d.pkey[nxb][i] = stored ? (uint32_t)(cell * G + g) : kDeadKey;
+    }
+    if (keep && !room) atomicOr(&ctrl->status, ST_CAPACITY);
+
+    // ---- tallies (W and E_surv in fixed point, see to_fixed).  A survivor
+    // that found no slot is counted in W but not in E_surv: its energy stays
+    // with the wave part.
     const int lane = threadIdx.x & 31;
     const long long wq = valid ? to_fixed(w, d.tq_inv, &ctrl->status) : 0ll;
-    warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq);
+    warp_run_add_fixed(d.Esq, stored ? cell * G + g : -1 - lane, wq, d.sort_cnt);
     if (valid && fate != FATE_REMOVED) {
       const bool start_in = gside < 0;
       const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
@@ -492,35 +482,14 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
         r.z = z; r.oz = oz;
       }
     }
-
-    // ---- compaction of the collisionless survivors (per warp)
-    const bool keep = valid && fate == FATE_SURVIVED;
-    unsigned rank;
-    const unsigned long long base = warp_slots(keep, &ctrl->n_out, &rank);
-    int slot = -1;
-    if (keep) {
-      const unsigned long long o = base + rank;
-      if (o < (unsigned long long)d.capacity) {
-        d.px[nxb][o] = x;
-        d.pox[nxb][o] = ox;
-        if (DIM >= 2) { d.py[nxb][o] = y; d.poy[nxb][o] = oy; }
-        if (DIM == 3) { d.pz[nxb][o] = z; d.poz[nxb][o] = oz; }
-        d.pnu[nxb][o] = nu;
-        d.pw[nxb][o] = w;
-        d.pid[nxb][o] = id;
-        d.pkey[nxb][o] = (uint32_t)(cell * G + g);
-        slot = (int)o;
-      } else {
-        atomicOr(&ctrl->status, ST_CAPACITY);
-      }
-    }
-    // adjoint tape: where this particle's weight was counted
+    // adjoint tape: where this particle's weight was counted (its slot in the
+    // next step's input is filled in by the survivor sort)
     if (!ENS && d.tape && valid) {
       if (i < d.tape_cap) {
         TapeRec tr;
         tr.c0 = gside >= 0 ? -1 - gside : cell0;
         tr.c1 = (fate == FATE_SURVIVED || fate == FATE_ABSORBED) ? cell : -1;
-        tr.slot = slot;
+        tr.slot = -1;
         tr.g = g;
         tr.w = w;
         d.tape[i] = tr;
@@ -533,95 +502,141 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
   flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
-// Mixed precision (FP32 particle state and arithmetic, FP64 tallies): the
-// same algorithm as k_stream64 with positions held relative to the cell
-// (0 <= xi <= dx) and FP32 uniforms from the same Philox words.  A survivor costs 28 B read and 28 B written in 1D.
-template <int DIM, bool ENS, int PPT>
-__global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_constant__ Dev d0, const Ens e) {
+// --------------------------------------------------------------------------
+// Mixed precision (FP32 particle state and arithmetic, fixed-point tallies):
+// the same algorithm as k_stream64 with positions held relative to the cell
+// (0 <= xi <= dx) and FP32 uniforms from the same Philox words.  A survivor
+// costs 28 B read and 28 B written in 1D.
+//
+// Block = NT streaming threads + one producer warp.  Tiles of NT x rounds
+// particles; a streaming warp takes 32 x rounds consecutive particles of a
+// tile (so its lanes share bins and its stores are whole 128-byte lines).
+template <int DIM, bool ENS, int NT>
+__global__ void __launch_bounds__(NT + 32, NT >= 512 ? 1 : (NT >= 256 ? 3 : 6))
+    k_stream32(const __grid_constant__ Dev d0, const Ens e, int rounds) {
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  __shared__ uint64_t s_full[kStages], s_empty[kStages];
+  __shared__ long long s_tile[kStages];
+  const long long tile = (long long)NT * rounds;
+  const size_t stage_sz = (size_t)tile * StageF<DIM>::kBytesPer;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-cell opacity factors of a single problem in shared memory
+  const int tab_n = ENS ? 0 : ((d0.sig_law == 2 || d0.ncell > kSmemCells) ? 0 : d0.ncell);
+  const bool tab_invT = !ENS && tab_n && d0.sig_law == 1 && !d0.grey;
+  float* s_sinv = reinterpret_cast<float*>(s_dyn + kStages * stage_sz);
+  float* s_invT = s_sinv + tab_n;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&s_full[k], 1);
+      mbar_init(&s_empty[k], NT / 32);
+    }
+    mbar_init_fence();
+  }
+  if (!ENS) {
+    for (int c = threadIdx.x; c < tab_n; c += blockDim.x) {
+      s_sinv[c] = __ldg(d0.sTinv_f + c);
+      if (tab_invT) s_invT[c] = __ldg(d0.invT_f + c);
+    }
+  }
+  __syncthreads();
+  const StepHead h0 = ENS ? StepHead{} : step_head(d0);
+
+  if (warp == NT / 32) {
+    // ---- producer: hand out tiles, stage their survivors
+    if (lane != 0) return;
+    unsigned long long* ctr = ENS ? e.tile_next : &d0.ctrl->tile_next;
+    unsigned int* status = ENS ? &e.devs[0].ctrl->status : &d0.ctrl->status;
+    const long long ntiles = ENS ? (long long)e.tile0[e.M] : (h0.n_tot + tile - 1) / tile;
+    bool gave_up = false;
+    unsigned issued = 0, lastpar = 0;
+    for (int it = 0;; ++it) {
+      const int s = it % kStages;
+      if (it >= kStages) {
+        const unsigned par = (unsigned)((it / kStages) - 1) & 1u;
+        // the previous copy into this stage has landed (it needs no other warp) ...
+        if (!mbar_wait_bounded(&s_full[s], par)) { atomicOr(status, ST_TIMEOUT); gave_up = true; }
+        // ... and every streaming warp is done with it
+        if (!gave_up && !mbar_wait_bounded(&s_empty[s], par)) { atomicOr(status, ST_TIMEOUT); gave_up = true; }
+      }
+      long long t = (long long)atomicAdd(ctr, 1ull);
+      if (t >= ntiles) t = -1;
+      s_tile[s] = t;
+      unsigned bytes = 0;
+      const Dev* dm = &d0;
+      long long first = 0, n = 0;
+      unsigned cb = h0.cur;
+      if (t >= 0) {
+        long long lt = t, n_surv = h0.n_surv;
+        if (ENS) {
+          const int m = find_member(e.tile0, e.M, t);
+          dm = &e.devs[m];
+          lt = t - (long long)e.tile0[m];
+          cb = dm->ctrl->cur;
+          n_surv = (long long)dm->ctrl->n_part[cb];
+        }
+        first = lt * tile;
+        n = n_surv - first;
+        n = n < 0 ? 0 : (n > tile ? tile : n);
+        const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
+        bytes = n ? c4 * 4u * StageF<DIM>::kArr4 + c2 * 8u : 0u;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(&s_full[s], bytes);
+      issued |= 1u << s;
+      lastpar = (lastpar & ~(1u << s)) | ((unsigned)((it / kStages) & 1) << s);
+      if (bytes) {
+        const StageF<DIM> sg(s_dyn + s * stage_sz, (int)tile);
+        const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
+        bulk_g2s(sg.id, dm->pid[cb] + first, c2 * 8u, &s_full[s]);
+        bulk_g2s(sg.x, dm->fx[cb] + first, c4 * 4u, &s_full[s]);
+        bulk_g2s(sg.ox, dm->fox[cb] + first, c4 * 4u, &s_full[s]);
+        bulk_g2s(sg.nu, dm->fnu[cb] + first, c4 * 4u, &s_full[s]);
+        bulk_g2s(sg.w, dm->fw[cb] + first, c4 * 4u, &s_full[s]);
+        bulk_g2s(sg.key, dm->pkey[cb] + first, c4 * 4u, &s_full[s]);
+        if (DIM >= 2) {
+          bulk_g2s(sg.y, dm->fy[cb] + first, c4 * 4u, &s_full[s]);
+          bulk_g2s(sg.oy, dm->foy[cb] + first, c4 * 4u, &s_full[s]);
+        }
+        if (DIM == 3) {
+          bulk_g2s(sg.z, dm->fz[cb] + first, c4 * 4u, &s_full[s]);
+          bulk_g2s(sg.oz, dm->foz[cb] + first, c4 * 4u, &s_full[s]);
+        }
+      }
+      if (t < 0) break;
+    }
+    // no copy may still be landing when the block's last warp leaves
+    for (int s = 0; s < kStages; ++s)
+      if ((issued >> s) & 1u) mbar_wait_bounded(&s_full[s], (lastpar >> s) & 1u);
+    return;
+  }
+
+  // ---- streaming warps
   Counters cnt;
   int acc_m = 0;
-  const long long tile = (long long)blockDim.x * PPT;   // PPT sub-tiles of one particle per thread
-  const long long ntiles = ENS ? (long long)e.tile0[e.M] : tiles_of(d0, tile);
-  int tile_iter = 0;   // per-block count of sub-tiles: parity of the shared slots
-  const StepHead h0 = ENS ? StepHead{} : step_head(d0);
-  // single problems: the survivors of the block's next tile are copied into
-  // the other of two shared-memory stages while this tile streams
-  extern __shared__ __align__(128) unsigned char s_dyn[];
-  __shared__ uint64_t s_bar[2];
-  const size_t stage_sz = (size_t)tile * StageF<DIM>::kBytesPer;
-  bool wait_failed = false;
-  auto issue = [&](long long lt_next, int st) {   // one thread: expect the bytes, start the copies
-    const unsigned cb = h0.cur;
-    const long long first = lt_next * tile;
-    long long n = h0.n_surv - first;
-    n = n < 0 ? 0 : (n > tile ? tile : n);
-    const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
-    const unsigned bytes = n ? c4 * 4u * StageF<DIM>::kArr4 + c2 * 8u : 0u;
-    StageF<DIM> sg(s_dyn + st * stage_sz, (int)tile);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&s_bar[st], bytes);
-    if (n) {
-      bulk_g2s(sg.id, d0.pid[cb] + first, c2 * 8u, &s_bar[st]);
-      bulk_g2s(sg.x, d0.fx[cb] + first, c4 * 4u, &s_bar[st]);
-      bulk_g2s(sg.ox, d0.fox[cb] + first, c4 * 4u, &s_bar[st]);
-      bulk_g2s(sg.nu, d0.fnu[cb] + first, c4 * 4u, &s_bar[st]);
-      bulk_g2s(sg.w, d0.fw[cb] + first, c4 * 4u, &s_bar[st]);
-      bulk_g2s(sg.key, d0.pkey[cb] + first, c4 * 4u, &s_bar[st]);
-      if (DIM >= 2) {
-        bulk_g2s(sg.y, d0.fy[cb] + first, c4 * 4u, &s_bar[st]);
-        bulk_g2s(sg.oy, d0.foy[cb] + first, c4 * 4u, &s_bar[st]);
-      }
-      if (DIM == 3) {
-        bulk_g2s(sg.z, d0.fz[cb] + first, c4 * 4u, &s_bar[st]);
-        bulk_g2s(sg.oz, d0.foz[cb] + first, c4 * 4u, &s_bar[st]);
-      }
+  for (int it = 0;; ++it) {
+    const int st = it % kStages;
+    if (!mbar_wait_bounded(&s_full[st], (unsigned)(it / kStages) & 1u)) {
+      atomicOr(ENS ? &e.devs[0].ctrl->status : &d0.ctrl->status, ST_TIMEOUT);
+      break;
     }
-  };
-  if (!ENS) {
-    if (threadIdx.x == 0) {
-      mbar_init(&s_bar[0], 1);
-      mbar_init(&s_bar[1], 1);
-      mbar_init_fence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && (long long)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-  }
-  int it = 0;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-  const int st = it & 1;
-  if (!ENS) {
-    // all threads left the stage st^1 (read last tile) behind at its block barriers
-    if (threadIdx.x == 0 && t + gridDim.x < ntiles) issue(t + gridDim.x, st ^ 1);
-    if (!wait_failed && !mbar_wait_bounded(&s_bar[st], (unsigned)(it >> 1) & 1u)) {
-      wait_failed = true;
-      atomicOr(&d0.ctrl->status, ST_TIMEOUT);
-    }
-  }
-  const StageF<DIM> sgt(s_dyn + st * stage_sz, (int)tile);
-  const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
-  if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
-  const Dev& d = ENS ? e.devs[m] : d0;
-  const long long lt = ENS ? t - (long long)e.tile0[m] : t;
-  Ctrl* ctrl = d.ctrl;
-  const unsigned cur = ENS ? ctrl->cur : h0.cur, nxb = cur ^ 1u;
-  const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
-  const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
-  const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
-  const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1, nz = DIM == 3 ? d.nz : 1;
-  const float dxf = d.dxf, dyf = d.dyf, dzf = d.dzf, vf = d.vf, dtf = d.dtf;
-  const float inv_rate = d.inv_rate_f, spf = d.spf;
-  const float* __restrict__ in_x = d.fx[cur];
-  const float* __restrict__ in_y = d.fy[cur];
-  const float* __restrict__ in_ox = d.fox[cur];
-  const float* __restrict__ in_oy = d.foy[cur];
-  const float* __restrict__ in_z = d.fz[cur];
-  const float* __restrict__ in_oz = d.foz[cur];
-  const float* __restrict__ in_nu = d.fnu[cur];
-  const float* __restrict__ in_w = d.fw[cur];
-  const unsigned long long* __restrict__ in_id = d.pid[cur];
-  const uint32_t* __restrict__ in_key = d.pkey[cur];
-  for (int sub = 0; sub < PPT; ++sub, ++tile_iter) {
-    const long long i = lt * tile + (long long)sub * blockDim.x + threadIdx.x;
+    const long long t = *reinterpret_cast<volatile long long*>(&s_tile[st]);
+    if (t < 0) break;
+    const StageF<DIM> sgt(s_dyn + st * stage_sz, (int)tile);
+    const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
+    if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
+    const Dev& d = ENS ? e.devs[m] : d0;
+    const long long lt = ENS ? t - (long long)e.tile0[m] : t;
+    Ctrl* ctrl = d.ctrl;
+    const unsigned cur = ENS ? ctrl->cur : h0.cur, nxb = cur ^ 1u;
+    const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
+    const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
+    const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
+    const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1, nz = DIM == 3 ? d.nz : 1;
+    const float dxf = d.dxf, dyf = d.dyf, dzf = d.dzf, vf = d.vf, dtf = d.dtf;
+    const float inv_rate = d.inv_rate_f, spf = d.spf;
+    for (int r = 0; r < rounds; ++r) {
+    const int li = (warp * rounds + r) * 32 + lane;
+    const long long i = lt * tile + li;
     const bool valid = i < n_tot;
     float xi = 0.f, eta = 0.f, zeta = 0.f, ox = 0.f, oy = 0.f, oz = 0.f, nu = 0.f, w = 0.f;
     unsigned long long id = 0ull;
@@ -631,28 +646,15 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     rng.init(0ull, step, 0u);
     if (valid) {
       if (i < n_surv) {
-        uint32_t key;
-        if (ENS) {
-          xi = in_x[i];
-          ox = in_ox[i];
-          if (DIM >= 2) { eta = in_y[i]; oy = in_oy[i]; }
-          if (DIM == 3) { zeta = in_z[i]; oz = in_oz[i]; }
-          nu = in_nu[i];
-          w = in_w[i];
-          id = in_id[i];
-          key = in_key[i];
-        } else {
-          const int li = (int)(i - lt * tile);
-          xi = sgt.x[li];
-          ox = sgt.ox[li];
-          if (DIM >= 2) { eta = sgt.y[li]; oy = sgt.oy[li]; }
-          if (DIM == 3) { zeta = sgt.z[li]; oz = sgt.oz[li]; }
-          nu = sgt.nu[li];
-          w = sgt.w[li];
-          id = sgt.id[li];
-          key = sgt.key[li];
-          if (wait_failed) key = 0u;   // the stage never arrived: the step is flagged, stay in range
-        }
+        xi = sgt.x[li];
+        ox = sgt.ox[li];
+        if (DIM >= 2) { eta = sgt.y[li]; oy = sgt.oy[li]; }
+        if (DIM == 3) { zeta = sgt.z[li]; oz = sgt.oz[li]; }
+        nu = sgt.nu[li];
+        w = sgt.w[li];
+        id = sgt.id[li];
+        uint32_t key = sgt.key[li];
+        if (key >= (uint32_t)d.nbins) key = 0u;   // only after a failed wait (flagged): stay in range
         const int cell = (int)div_bin(d, key);
         g = (int)(key - (uint32_t)cell * (uint32_t)G);
         if (DIM == 3) {
@@ -718,6 +720,17 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     }
     const int cell0 = gside >= 0 ? cx : (cz * ny + cy) * nx + cx;
 
+    // 1/sigma(nu, T^n) in the particle's cell: the per-cell factors from
+    // shared memory when the problem's table is there
+    auto inv_sigma = [&](int c, float inup) -> float {
+      if (!ENS && tab_n) {
+        float si = s_sinv[c] * inup;
+        if (tab_invT) si /= -expm1f(-nu * s_invT[c]);
+        return fmaxf(si, d.inv_capf);
+      }
+      return inv_sigma_particle_f(d, c, nu, inup);
+    };
+
     // ---- streaming
     int fate = FATE_REMOVED, nseg = 0, eside = -1;
     float t_tra = 0.0f;
@@ -730,7 +743,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
         collided = false;
       } else {
         const UPair u = rng.next2(d.pk);
-        const float sig_inv = inv_sigma_particle_f(d, (cz * ny + cy) * nx + cx, nu, inup);
+        const float sig_inv = inv_sigma((cz * ny + cy) * nx + cx, inup);
         const float tc = neg_log_u(u) * inv_rate * sig_inv;
         collided = tc < dtf;
         t_rem = collided ? tc : dtf;
@@ -801,7 +814,7 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
           cy = nyc;
           cz = nzc;
           const UPair u = rng.next2(d.pk);
-          const float sig_inv = inv_sigma_particle_f(d, (cz * ny + cy) * nx + cx, nu, inup);
+          const float sig_inv = inv_sigma((cz * ny + cy) * nx + cx, inup);
           const float tc = neg_log_u(u) * inv_rate * sig_inv;
           const float avail = dtf - t_tra;
           collided = tc < avail;
@@ -819,11 +832,27 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
     }
     const int cell = (cz * ny + cy) * nx + cx;
 
-    // ---- tallies (W and E_surv in fixed point, see to_fixed; FP64 side tallies)
-    const int lane = threadIdx.x & 31;
+    // ---- in place: slot i of the other buffer (kDeadKey unless it survived)
+    const bool keep = valid && fate == FATE_SURVIVED;
+    const bool room = i < d.capacity;
+    const bool stored = keep && room;
+    if (valid && room) {
+      d.fx[nxb][i] = xi;
+      d.fox[nxb][i] = ox;
+      if (DIM >= 2) { d.fy[nxb][i] = eta; d.foy[nxb][i] = oy; }
+      if (DIM == 3) { d.fz[nxb][i] = zeta; d.foz[nxb][i] = oz; }
+      d.fnu[nxb][i] = nu;
+      d.fw[nxb][i] = w;
+      d.pid[nxb][i] = id;
+      d.pkey[nxb][i] = stored ? (uint32_t)(cell * G + g) : kDeadKey;
+    }
+    if (keep && !room) atomicOr(&ctrl->status, ST_CAPACITY);
+
+    // ---- tallies (W and E_surv in fixed point, see to_fixed_f; FP64 side
+    // tallies).  A survivor that found no slot is counted in W but not in
+    // E_surv: its energy stays with the wave part.
     const long long wq = valid ? to_fixed_f(w, d.tq_shift, &ctrl->status) : 0ll;
-    warp_run_add_fixed(d.Esq, (valid && fate == FATE_SURVIVED) ? cell * G + g : -1 - lane, wq,
-                       (!ENS && d.sorting) ? d.sort_cnt : nullptr);
+    warp_run_add_fixed(d.Esq, stored ? cell * G + g : -1 - lane, wq, d.sort_cnt);
     if (valid && fate != FATE_REMOVED && (gside >= 0 || fate == FATE_ESCAPED || cell0 != cell)) {
       const double wd = (double)w;
       const bool start_in = gside < 0;
@@ -839,83 +868,84 @@ __global__ void __launch_bounds__(512, ENS ? 1 : 2) k_stream32(const __grid_cons
       cnt.esc += fate == FATE_ESCAPED;
       cnt.surv += fate == FATE_SURVIVED;
       cnt.rem += fate == FATE_REMOVED;
-      if (d.rec && i < d.rec_cap) {
-        RecordOut& r = d.rec[i];
-        r.id = id; r.fate = fate; r.cell0 = cell0; r.cell1 = (fate == FATE_REMOVED && gside >= 0) ? cx : cell;
-        r.grp = g; r.nseg = nseg; r.pad = 0;
-        r.x = cx * d.dx + (double)xi;
-        r.y = DIM >= 2 ? cy * d.dy + (double)eta : 0.0;
-        r.ox = ox; r.oy = oy; r.nu = nu; r.w = (double)w; r.t_end = t_tra;
-        r.z = DIM == 3 ? cz * d.dz + (double)zeta : 0.0;
-        r.oz = oz;
+      if (!ENS && d.rec && i < d.rec_cap) {
+        RecordOut& rr = d.rec[i];
+        rr.id = id; rr.fate = fate; rr.cell0 = cell0; rr.cell1 = (fate == FATE_REMOVED && gside >= 0) ? cx : cell;
+        rr.grp = g; rr.nseg = nseg; rr.pad = 0;
+        rr.x = cx * d.dx + (double)xi;
+        rr.y = DIM >= 2 ? cy * d.dy + (double)eta : 0.0;
+        rr.ox = ox; rr.oy = oy; rr.nu = nu; rr.w = (double)w; rr.t_end = t_tra;
+        rr.z = DIM == 3 ? cz * d.dz + (double)zeta : 0.0;
+        rr.oz = oz;
       }
     }
-
-    // ---- compaction
-    const bool keep = valid && fate == FATE_SURVIVED;
-    unsigned rank;
-    const unsigned long long base = block_slots(keep, tile_iter & 1, &ctrl->n_out, &rank);
-    if (keep) {
-      const unsigned long long o = base + rank;
-      if (o < (unsigned long long)d.capacity) {
-        d.fx[nxb][o] = xi;
-        d.fox[nxb][o] = ox;
-        if (DIM >= 2) { d.fy[nxb][o] = eta; d.foy[nxb][o] = oy; }
-        if (DIM == 3) { d.fz[nxb][o] = zeta; d.foz[nxb][o] = oz; }
-        d.fnu[nxb][o] = nu;
-        d.fw[nxb][o] = w;
-        d.pid[nxb][o] = id;
-        d.pkey[nxb][o] = (uint32_t)(cell * G + g);
-      } else {
-        atomicOr(&ctrl->status, ST_CAPACITY);
-      }
     }
-  }
-  }
-  if (!ENS && wait_failed && threadIdx.x == 0) {
-    // copies may still be in flight into the stages: wait (bounded) for both
-    mbar_wait_bounded(&s_bar[0], (unsigned)((it + 1) >> 1) & 1u);
-    mbar_wait_bounded(&s_bar[1], (unsigned)(it >> 1) & 1u);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s_empty[st]);
   }
   flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
 }
 
-static int g_stream_occ[2][4][2][3][3] = {};   // [mixed][dim][ens][ppt][block index]
+static int g_stream64_occ[4][2][3][3] = {};   // [dim][ens][ppt][block index]
+static int g_stream32_occ[4][2][3] = {};      // [dim][ens][block index] (at the table size last used)
+static int g_stream32_occ_dyn[4][2][3] = {};
 
 template <int DIM, bool ENS, int PPT>
-static cudaError_t launch_stream_t(const Dev& d, const Ens& e, int mixed, const StreamShape& sh,
-                                   cudaStream_t s) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = mixed ? (const void*)k_stream32<DIM, ENS, PPT> : (const void*)k_stream64<DIM, ENS, PPT>;
+static cudaError_t launch_stream64_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
+  const int sms = sm_count();
+  const void* fn = (const void*)k_stream64<DIM, ENS, PPT>;
   const int bi = sh.block == 128 ? 0 : (sh.block == 512 ? 2 : 1);
-  const size_t dyn = (mixed && !ENS) ? stream32_stage_bytes(DIM, sh.block * PPT) : 0;
-  int& occ = g_stream_occ[mixed][DIM][ENS][PPT][bi];
+  int& occ = g_stream64_occ[DIM][ENS][PPT][bi];
   if (!occ) {
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.block, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sh.block, 0);
     if (occ < 1) occ = 1;
   }
-  int per = sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ;
-  const int blocks = sms * per;
-  if (mixed) k_stream32<DIM, ENS, PPT><<<blocks, sh.block, dyn, s>>>(d, e);
-  else k_stream64<DIM, ENS, PPT><<<blocks, sh.block, 0, s>>>(d, e);
+  const int per = sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ;
+  k_stream64<DIM, ENS, PPT><<<sms * per, sh.block, 0, s>>>(d, e);
   return cudaGetLastError();
+}
+
+template <int DIM, bool ENS, int NT>
+static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
+  const int sms = sm_count();
+  const void* fn = (const void*)k_stream32<DIM, ENS, NT>;
+  const int tile = NT * sh.ppt;
+  const size_t dyn = kStages * stream32_stage_bytes(DIM, tile) + (ENS ? 0 : 4 * (size_t)stream32_table_floats(d));
+  const int bi = NT == 128 ? 0 : (NT == 512 ? 2 : 1);
+  int& occ = g_stream32_occ[DIM][ENS][bi];
+  int& occ_dyn = g_stream32_occ_dyn[DIM][ENS][bi];
+  if (!occ || occ_dyn != (int)dyn) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT + 32, dyn);
+    if (occ < 1) occ = 1;
+    occ_dyn = (int)dyn;
+  }
+  const int per = sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ;
+  k_stream32<DIM, ENS, NT><<<sms * per, NT + 32, dyn, s>>>(d, e, sh.ppt);
+  return cudaGetLastError();
+}
+
+template <int DIM, bool ENS>
+static cudaError_t launch_stream32_nt(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
+  if (sh.block == 128) return launch_stream32_t<DIM, ENS, 128>(d, e, sh, s);
+  if (sh.block == 512) return launch_stream32_t<DIM, ENS, 512>(d, e, sh, s);
+  return launch_stream32_t<DIM, ENS, 256>(d, e, sh, s);
 }
 
 template <bool ENS>
 static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s) {
   if (d.dim == 3) {   // single problems only (ensembles are 1D/2D)
     if (ENS) return cudaErrorNotSupported;
-    return launch_stream_t<3, false, 1>(d, e, mixed, sh, s);
+    return mixed ? launch_stream32_nt<3, false>(d, e, sh, s) : launch_stream64_t<3, false, 1>(d, e, sh, s);
   }
   if (d.dim == 2) {
-    if (sh.ppt == 2) return launch_stream_t<2, ENS, 2>(d, e, mixed, sh, s);
-    return launch_stream_t<2, ENS, 1>(d, e, mixed, sh, s);
+    if (mixed) return launch_stream32_nt<2, ENS>(d, e, sh, s);
+    if (sh.ppt == 2) return launch_stream64_t<2, ENS, 2>(d, e, sh, s);
+    return launch_stream64_t<2, ENS, 1>(d, e, sh, s);
   }
-  if (sh.ppt == 2) return launch_stream_t<1, ENS, 2>(d, e, mixed, sh, s);
-  return launch_stream_t<1, ENS, 1>(d, e, mixed, sh, s);
+  if (mixed) return launch_stream32_nt<1, ENS>(d, e, sh, s);
+  if (sh.ppt == 2) return launch_stream64_t<1, ENS, 2>(d, e, sh, s);
+  return launch_stream64_t<1, ENS, 1>(d, e, sh, s);
 }
 
 cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s) {

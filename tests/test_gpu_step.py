@@ -228,3 +228,23 @@ def test_full_size_multigroup_slab_one_step(B):
     np.testing.assert_allclose(gg["T"], st2.T, rtol=T_RTOL, atol=0)
     rs = np.abs(st2.rho.reshape(p.ncell, p.G)).sum(1, keepdims=True)
     assert (np.abs(gg["rho"] - st2.rho).reshape(p.ncell, p.G) <= 1e-9 * rs).all()
+
+
+@pytest.mark.parametrize("literal", [0, 1])
+def test_wave_particle_split_options(B, literal):
+    # default: survivors scaled where they would exceed rho^{n+1} (the count
+    # of such bins agrees with the oracle's); split_literal: I^h = I^{n+1} -
+    # I^p as written, nothing scaled, rho_h free to go negative
+    p = I.small_checkerboard(n=8, G=3, omega_ref=2e-6).replace(split_literal=literal)
+    sim, t, g, rg, st2, tal, ro = one_step(B, p, 3)
+    flips = compare_records(p, rg, ro)
+    assert flips == 0
+    assert t["n_scaled_bins"] == tal.c.n_scaled_bins
+    if literal:
+        assert t["n_scaled_bins"] == 0
+    else:
+        assert t["n_scaled_bins"] > 0
+    np.testing.assert_allclose(g["T"], st2.T, rtol=T_RTOL, atol=0)
+    scale = np.abs(st2.rho).max()
+    assert np.abs(g["rho_h"] - st2.rho_h).max() <= 1e-9 * scale
+    assert np.abs(g["rho_p"] - st2.rho_p).max() <= 1e-9 * scale

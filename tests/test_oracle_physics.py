@@ -304,3 +304,40 @@ def test_particle_part_never_exceeds_the_total():
             np.testing.assert_allclose(sums / V, st.rho_p, rtol=1e-12, atol=1e-300)
             scaled += int(np.sum(st.rho_p != tal.E_surv / V))
         assert scaled > 0   # the case exercises the scaling
+
+
+def test_literal_split_and_the_scaled_bin_count():
+    """The split as the paper writes it (Sec. 2.2, I^h = I^{n+1} - I^p) under
+    split_literal = 1: rho_p is exactly the survivors' energy E_surv/V, their
+    weights are untouched (so they add up to E_surv), rho_h = rho^{n+1} - rho_p
+    may go negative, nothing is counted as scaled, and the energy still
+    closes.  Under the default the count equals the bins where rho_p differs
+    from E_surv/V."""
+    p = I.small_checkerboard(n=8, G=3, omega_ref=2e-6)
+    V = p.dx * p.dy
+    for literal in (0, 1):
+        q = p.replace(split_literal=literal)
+        prob = O.OracleProblem(q)
+        st = O.initial_state(prob)
+        n_scaled = neg = 0
+        for _ in range(4):
+            st, tal, _, status = O.step(prob, st)
+            assert status == 0
+            changed = int(np.sum(st.rho_p != tal.E_surv / V))
+            assert tal.c.n_scaled_bins == changed
+            n_scaled += tal.c.n_scaled_bins
+            # rho_h = rho - rho_p: one rounding of the larger of the two
+            assert np.all(np.abs(st.rho_h + st.rho_p - st.rho) <= 1e-15 * (np.abs(st.rho) + np.abs(st.rho_p)))
+            parts = st.particles.view()
+            sums = np.bincount(parts["cell"] * q.G + parts["grp"], weights=parts["w"], minlength=q.ncell * q.G)
+            np.testing.assert_allclose(sums / V, st.rho_p, rtol=1e-12, atol=1e-300)
+            if literal:
+                np.testing.assert_array_equal(st.rho_p, tal.E_surv / V)
+                neg += int(np.sum(st.rho_h < 0.0))
+            # reflecting walls: the only energy entering is the patch source
+            E0, E1 = tal.c.E_rad0 + tal.c.E_mat0, tal.c.E_rad1 + tal.c.E_mat1
+            assert abs(E1 - E0 - tal.c.src_in) <= 1e-12 * E1
+        if literal:
+            assert n_scaled == 0 and neg > 0
+        else:
+            assert n_scaled > 0

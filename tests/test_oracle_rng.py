@@ -85,3 +85,23 @@ def test_uniform_moments():
     assert rng_words.dtype == np.uint32
     assert abs(us.mean() - 0.5) < 4 * (1 / np.sqrt(12 * len(us)))
     assert abs(us.var() - 1 / 12) < 0.005
+
+
+def test_identity_space_ends_at_step_2_pow_20():
+    # a newborn's identity holds its birth step in 20 bits: the last step
+    # that may sample is 2^20 - 1; the next samples nothing and says so
+    # (otherwise its identities and random streams would repeat step 0's)
+    p = I.small_multigroup(nx=12, G=4, omega_ref=1e-6)
+    op = O.OracleProblem(p)
+    st = O.initial_state(op)
+    st, tal, _, status = O.step(op, st)
+    assert status == 0 and tal.c.n_born > 100
+    born0 = tal.c.n_born
+    st.step = (1 << 20) - 1
+    st1, tal, _, status = O.step(op, st)
+    assert status == 0 and tal.c.n_born > 100
+    assert (st1.particles.view()["id"] >> 44 == (1 << 20) - 1).sum() > 0
+    st.step = 1 << 20
+    st2, tal, _, status = O.step(op, st)
+    assert status == O.OR_ERR_IDSPACE and tal.c.n_born == 0
+    assert int(np.sum(tal.N)) == 0 and born0 > 0
