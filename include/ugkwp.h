@@ -269,10 +269,10 @@ int ugkwp_checkpoint(ugkwp_handle* h, void* d_buf, size_t bytes, void* stream);
 int ugkwp_restore(ugkwp_handle* h, const void* d_buf, size_t bytes, void* stream);
 
 /* ---- launch shape of the particle kernel ----
- * block: 128, 256 or 512 streaming threads (the mixed-precision kernel adds
- * one producer warp that stages the tiles); particles_per_thread: 1 or 2
- * (tile = block x particles_per_thread particles); blocks_per_sm: 0 for as
- * many as fit. */
+ * block: 128, 256 or 512 threads; particles_per_thread: 1, 2 or 4 (the
+ * mixed-precision kernel streams chunks of 32 x particles_per_thread
+ * particles per warp, the FP64 kernel tiles of block x min(it, 2));
+ * blocks_per_sm: 0 for as many as fit. */
 int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int blocks_per_sm);
 /* ---- bounded waits ----
  * The source iteration's grid barrier polls at most `spins` times (0: the

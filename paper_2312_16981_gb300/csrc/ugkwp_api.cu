@@ -39,6 +39,13 @@ namespace {
 
 thread_local char g_err[512] = "";
 
+// Particles per tile of an ensemble's tile table: the FP32 kernel streams
+// chunks of 32 x ppt particles per warp, the FP64 kernel tiles of block x ppt.
+int ens_tile(const ugkwp_handle* h) {
+  const int prec = h->members.empty() ? h->d.precision : h->members[0].precision;
+  return prec == UGKWP_MIXED ? 32 * h->shape.ppt : h->shape.block * (h->shape.ppt >= 2 ? 2 : 1);
+}
+
 int fail(ugkwp_handle* h, int code, const char* msg) {
   char* dst = h ? h->err : g_err;
   snprintf(dst, 512, "%s", msg);
@@ -183,6 +190,8 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.invT_f = mixed ? cv.take<float>(nc) : nullptr;
   d.omega_f = mixed ? cv.take<float>(nb) : nullptr;
   d.khat_f = mixed ? cv.take<float>(nb) : nullptr;
+  d.slow_i = mixed ? cv.take<uint32_t>(P) : nullptr;
+  d.slow_t = mixed ? cv.take<float>(P) : nullptr;
   d.particles_begin = nullptr;
   for (int b = 0; b < 2; ++b) {
     if (mixed) {
@@ -464,7 +473,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   E.total_cells = cell0[n];
   E.max_parts = ugkwp::scan_parts(max_bins);
   E.max_G = max_G;
-  E.tile = h->shape.block * h->shape.ppt;
+  E.tile = ens_tile(h);
   h->d = h->members[0];
   h->p.nu_edges = h->p.sigma0 = h->p.cv = h->p.T0 = h->p.rho0 = h->p.src_T = h->p.src_amp = nullptr;
   *out = h;
@@ -820,13 +829,13 @@ int ugkwp_set_records(ugkwp_handle* h, ugkwp_record* d_records, int64_t cap) {
 
 int ugkwp_set_launch(ugkwp_handle* h, int block, int particles_per_thread, int blocks_per_sm) {
   if (!h) return fail(nullptr, UGKWP_ERR_ARG, "handle is NULL");
-  if ((block != 128 && block != 256 && block != 512) || (particles_per_thread != 1 && particles_per_thread != 2) ||
-      blocks_per_sm < 0)
-    return fail(h, UGKWP_ERR_ARG, "block must be 128, 256 or 512; particles per thread 1 or 2");
+  if ((block != 128 && block != 256 && block != 512) ||
+      (particles_per_thread != 1 && particles_per_thread != 2 && particles_per_thread != 4) || blocks_per_sm < 0)
+    return fail(h, UGKWP_ERR_ARG, "block must be 128, 256 or 512; particles per thread 1, 2 or 4");
   h->shape.block = block;
   h->shape.ppt = particles_per_thread;
   h->shape.blocks_per_sm = blocks_per_sm;
-  h->ens.tile = block * particles_per_thread;
+  h->ens.tile = ens_tile(h);
   drop_graph(h);
   return UGKWP_OK;
 }
@@ -888,11 +897,11 @@ int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void*
   int st = ugkwp_checkpoint(h, d_ckpt, bytes, stream);
   if (st) return st;
   const ugkwp::StreamShape keep = h->shape;
-  const int blocks[3] = {128, 256, 512}, ppts[2] = {1, 2}, pers[2] = {0, -1};
+  const int blocks[3] = {128, 256, 512}, ppts[3] = {1, 2, 4}, pers[2] = {0, -1};
   float best_t = 1e30f;
   ugkwp::StreamShape best_s = keep;
   for (int bi = 0; bi < 3; ++bi)
-    for (int pi = 0; pi < 2; ++pi)
+    for (int pi = 0; pi < 3; ++pi)
       for (int qi = 0; qi < 2; ++qi) {
         ugkwp::StreamShape sh;
         sh.block = blocks[bi];
@@ -907,7 +916,7 @@ int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void*
         }
         sh.blocks_per_sm = pers[qi] < 0 ? occ : 0;
         h->shape = sh;
-        h->ens.tile = sh.block * sh.ppt;
+        h->ens.tile = ens_tile(h);
         if ((st = ugkwp_restore(h, d_ckpt, bytes, stream))) return st;
         float total = 0.f;
         for (int k = 0; k < steps; ++k) {
@@ -918,7 +927,7 @@ int ugkwp_autotune(ugkwp_handle* h, void* d_ckpt, size_t bytes, int steps, void*
         if (total < best_t) { best_t = total; best_s = sh; }
       }
   h->shape = best_s;
-  h->ens.tile = best_s.block * best_s.ppt;
+  h->ens.tile = ens_tile(h);
   drop_graph(h);
   if ((st = ugkwp_restore(h, d_ckpt, bytes, stream))) return st;
   CK(cudaStreamSynchronize(s), h);

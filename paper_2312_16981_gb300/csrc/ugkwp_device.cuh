@@ -316,6 +316,12 @@ struct Dev {
   float* omega_f;   // [nbins]
   float* khat_f;    // [nbins]
   float* nu_edges_f;       // [G+1] group edges in FP32
+  // mixed precision, single problems with few face crossings: the survivors
+  // whose first flight ends at a face, listed by the survivor kernel for the
+  // general one (slot in the input, remaining free time, negative if it ends
+  // in a collision)
+  uint32_t* slow_i;        // [capacity]
+  float* slow_t;           // [capacity]
   const double* nu_pow;    // [3*G] nu^p at the lower edge, midpoint and upper edge of each group
   void* particles_begin;   // first particle buffer (start of the part left uninitialised)
   // control block and optional records
@@ -375,15 +381,15 @@ struct Ens {
   // totals known on the host (launch shapes)
   long long total_bins, total_fg, total_cells;
   int max_parts, max_G;
-  int tile;               // particles per tile of the particle kernel (block x particles per thread)
+  int tile;               // particles per tile of the particle kernel's tile table
 };
 
 // Launch shape of the particle kernel (picked by the autotuner).  The
-// mixed-precision kernel adds one producer warp to `block` streaming threads
-// and streams tiles of block x ppt particles.
+// mixed-precision kernel streams chunks of 32 x ppt particles per warp, the
+// FP64 kernel tiles of block x ppt.
 struct StreamShape {
-  int block = 256;        // streaming threads per block: 128, 256 or 512
-  int ppt = 1;            // particles per thread per tile: 1 or 2
+  int block = 256;        // threads per block: 128, 256 or 512
+  int ppt = 4;            // particles per thread per tile: 1, 2 or 4 (the FP64 kernel takes 2 for 4)
   int blocks_per_sm = 0;  // 0: as many as fit
 };
 
@@ -494,6 +500,7 @@ struct Ctrl {
   unsigned int scaled;            // some survivors' weights need scaling this step
   unsigned int fin_count;         // blocks done in the end-of-step kernel (0 between steps)
   unsigned long long tile_next;   // next particle tile to hand out (particle kernel; 0 at step start)
+  unsigned long long n_slow;      // survivors listed for the general particle kernel (0 at step start)
   unsigned int n_scaled_bins;     // (cell, group) bins whose survivors were scaled this step
   unsigned int pad_;
   unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)

@@ -23,13 +23,11 @@
 // into the input buffer in bin order.  That is Algorithm 1's last step
 // (collided particles removed) with the survivors kept cell-sorted.
 //
-// The FP32 kernel streams tiles of survivors staged in shared memory: one
-// producer warp per block takes the next tile from a global counter and
-// starts bulk copies (cp.async.bulk, completion counted on an mbarrier) of
-// its arrays into one of three stages; the streaming warps wait on a stage's
-// "full" barrier, process it and arrive on its "empty" barrier, so no warp
-// waits for another.  Per-cell opacity factors of single problems are held
-// in shared memory when they fit.
+// The FP32 kernel streams chunks of survivors staged in shared memory: each
+// warp starts bulk copies (cp.async.bulk, completion counted on an mbarrier)
+// of its next chunks' arrays into a ring of three stages of its own while it
+// streams the current one, so no warp waits for another.  Per-cell opacity
+// factors of single problems are held in shared memory when they fit.
 #include "ugkwp_device.cuh"
 #include "ugkwp_launch.h"
 
@@ -112,9 +110,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
   asm volatile(
@@ -183,6 +178,33 @@ __device__ __forceinline__ void flush_counters(Ctrl* ctrl, Counters& c) {
     if (esc) atomicAdd(&ctrl->n_escaped, esc);
     if (surv) atomicAdd(&ctrl->n_survived, surv);
     if (rem) atomicAdd(&ctrl->n_removed, rem);
+  }
+  c = Counters();
+}
+
+// The same once per block: the warps' sums meet in shared memory and one
+// thread adds them to the control block (many warps adding to the same five
+// words serialise at the L2).  Every thread of the block must call it.
+__device__ __forceinline__ void flush_counters_block(Ctrl* ctrl, Counters& c) {
+  __shared__ unsigned long long s_c[5];
+  if (threadIdx.x < 5) s_c[threadIdx.x] = 0ull;
+  __syncthreads();
+  const unsigned long long seg = warp_sum_u64(c.seg), abs = warp_sum_u64(c.abs), esc = warp_sum_u64(c.esc);
+  const unsigned long long surv = warp_sum_u64(c.surv), rem = warp_sum_u64(c.rem);
+  if ((threadIdx.x & 31) == 0) {
+    if (seg) atomicAdd(&s_c[0], seg);
+    if (abs) atomicAdd(&s_c[1], abs);
+    if (esc) atomicAdd(&s_c[2], esc);
+    if (surv) atomicAdd(&s_c[3], surv);
+    if (rem) atomicAdd(&s_c[4], rem);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_c[0]) atomicAdd(&ctrl->n_segments, s_c[0]);
+    if (s_c[1]) atomicAdd(&ctrl->n_absorbed, s_c[1]);
+    if (s_c[2]) atomicAdd(&ctrl->n_escaped, s_c[2]);
+    if (s_c[3]) atomicAdd(&ctrl->n_survived, s_c[3]);
+    if (s_c[4]) atomicAdd(&ctrl->n_removed, s_c[4]);
   }
   c = Counters();
 }
@@ -508,382 +530,766 @@ __global__ void __launch_bounds__(512, 1) k_stream64(const __grid_constant__ Dev
 // (0 <= xi <= dx) and FP32 uniforms from the same Philox words.  A survivor
 // costs 28 B read and 28 B written in 1D.
 //
-// Block = NT streaming threads + one producer warp.  Tiles of NT x rounds
-// particles; a streaming warp takes 32 x rounds consecutive particles of a
-// tile (so its lanes share bins and its stores are whole 128-byte lines).
+// A warp streams chunks of 32 x rounds consecutive particles (so its lanes
+// share bins and its stores are whole 128-byte lines).
+
+// State of one particle in the FP32 kernel.
+struct P32 {
+  float xi, eta, zeta, ox, oy, oz, nu, w, t_rem, t_tra;
+  unsigned long long id;
+  int cx, cy, cz, g, gside, fate, nseg, eside, cell0;
+  bool collided, ghost, newborn;
+};
+
+// 1/sigma(nu, T^n) of a particle in cell c: the per-cell factors from shared
+// memory when the problem's table is there (tab_n > 0), else from the device
+__device__ __forceinline__ float inv_sigma32(const Dev& d, int c, float nu, float inup, int tab_n,
+                                             bool tab_invT, const float* s_sinv, const float* s_invT) {
+  if (tab_n) {
+    float si = s_sinv[c] * inup;
+    if (tab_invT) si /= -expm1f(-nu * s_invT[c]);
+    return fmaxf(si, d.inv_capf);
+  }
+  return inv_sigma_particle_f(d, c, nu, inup);
+}
+
+// The streaming loop from a particle's current state (free time t_rem in its
+// cell) to the end of the step: faces crossed with the free time reset,
+// reflections, escapes, the final flight.
+template <int DIM>
+__device__ __forceinline__ void stream_loop32(const Dev& d, P32& q, DrawsF& rng, float inup, int tab_n,
+                                              bool tab_invT, const float* s_sinv, const float* s_invT) {
+  const int nx = d.nx, ny = DIM >= 2 ? d.ny : 1, nz = DIM == 3 ? d.nz : 1;
+  const float dxf = d.dxf, dyf = d.dyf, dzf = d.dzf, vf = d.vf, dtf = d.dtf, inv_rate = d.inv_rate_f;
+  const float ivx = q.ox != 0.0f ? __frcp_rn(vf * fabsf(q.ox)) : 0.0f;
+  const float ivy = (DIM >= 2 && q.oy != 0.0f) ? __frcp_rn(vf * fabsf(q.oy)) : 0.0f;
+  const float ivz = (DIM == 3 && q.oz != 0.0f) ? __frcp_rn(vf * fabsf(q.oz)) : 0.0f;
+  for (int guard = 0;; ++guard) {
+    if (guard >= 4096) {
+      atomicOr(&d.ctrl->status, ST_NONFINITE);
+      q.fate = FATE_REMOVED;
+      break;
+    }
+    float tx = INFINITY, ty = INFINITY, tz = INFINITY;
+    if (q.ox > 0.0f) tx = fmaxf(dxf - q.xi, 0.0f) * ivx;
+    else if (q.ox < 0.0f) tx = fmaxf(q.xi, 0.0f) * ivx;
+    if (DIM >= 2) {
+      if (q.oy > 0.0f) ty = fmaxf(dyf - q.eta, 0.0f) * ivy;
+      else if (q.oy < 0.0f) ty = fmaxf(q.eta, 0.0f) * ivy;
+    }
+    if (DIM == 3) {
+      if (q.oz > 0.0f) tz = fmaxf(dzf - q.zeta, 0.0f) * ivz;
+      else if (q.oz < 0.0f) tz = fmaxf(q.zeta, 0.0f) * ivz;
+    }
+    // nearest face; ties go to the lower axis
+    int axis = (tx <= ty) ? 0 : 1;
+    float tf = axis == 0 ? tx : ty;
+    if (DIM == 3 && tz < tf) { axis = 2; tf = tz; }
+    if (tf < q.t_rem) {
+      ++q.nseg;
+      q.t_tra += tf;
+      q.t_rem -= tf;
+      int dir;
+      if (axis == 0) {
+        dir = q.ox > 0.0f ? 1 : -1;
+        q.xi = dir > 0 ? dxf : 0.0f;
+        if (DIM >= 2) q.eta = fminf(fmaxf(fmaf(vf * q.oy, tf, q.eta), 0.0f), dyf);
+        if (DIM == 3) q.zeta = fminf(fmaxf(fmaf(vf * q.oz, tf, q.zeta), 0.0f), dzf);
+      } else if (DIM < 3 || axis == 1) {
+        dir = q.oy > 0.0f ? 1 : -1;
+        q.eta = dir > 0 ? dyf : 0.0f;
+        q.xi = fminf(fmaxf(fmaf(vf * q.ox, tf, q.xi), 0.0f), dxf);
+        if (DIM == 3) q.zeta = fminf(fmaxf(fmaf(vf * q.oz, tf, q.zeta), 0.0f), dzf);
+      } else {
+        dir = q.oz > 0.0f ? 1 : -1;
+        q.zeta = dir > 0 ? dzf : 0.0f;
+        q.xi = fminf(fmaxf(fmaf(vf * q.ox, tf, q.xi), 0.0f), dxf);
+        q.eta = fminf(fmaxf(fmaf(vf * q.oy, tf, q.eta), 0.0f), dyf);
+      }
+      const int nxc = q.cx + (axis == 0 ? dir : 0), nyc = q.cy + (axis == 1 ? dir : 0);
+      const int nzc = q.cz + (axis == 2 ? dir : 0);
+      if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny || (DIM == 3 && (nzc < 0 || nzc >= nz))) {
+        const int side = axis * 2 + (dir > 0 ? 1 : 0);
+        if (d.bc[side] == BC_REFLECT) {
+          if (axis == 0) q.ox = -q.ox; else if (axis == 1) q.oy = -q.oy; else q.oz = -q.oz;
+          continue;
+        }
+        q.fate = FATE_ESCAPED;
+        q.eside = side;
+        break;
+      }
+      q.ghost = false;
+      if (axis == 0) q.xi = dir > 0 ? 0.0f : dxf;
+      else if (axis == 1) q.eta = dir > 0 ? 0.0f : dyf;
+      else q.zeta = dir > 0 ? 0.0f : dzf;
+      q.cx = nxc;
+      q.cy = nyc;
+      q.cz = nzc;
+      const UPair u = rng.next2(d.pk);
+      const float sig_inv = inv_sigma32(d, (q.cz * ny + q.cy) * nx + q.cx, q.nu, inup, tab_n, tab_invT, s_sinv, s_invT);
+      const float tc = neg_log_u(u) * inv_rate * sig_inv;
+      const float avail = dtf - q.t_tra;
+      q.collided = tc < avail;
+      q.t_rem = q.collided ? tc : avail;
+      continue;
+    }
+    ++q.nseg;
+    q.xi = fminf(fmaxf(fmaf(vf * q.ox, q.t_rem, q.xi), 0.0f), dxf);
+    if (DIM >= 2) q.eta = fminf(fmaxf(fmaf(vf * q.oy, q.t_rem, q.eta), 0.0f), dyf);
+    if (DIM == 3) q.zeta = fminf(fmaxf(fmaf(vf * q.oz, q.t_rem, q.zeta), 0.0f), dzf);
+    q.t_tra += q.t_rem;
+    q.fate = q.ghost ? FATE_REMOVED : (q.collided ? FATE_ABSORBED : FATE_SURVIVED);
+    break;
+  }
+}
+
+// The W and side tallies of a particle that changed cell, entered from a
+// ghost or escaped (end minus start of Eq. wfrpFormula; FP64 side tallies).
+__device__ __forceinline__ void cross_tallies32(const Dev& d, const P32& q, int cell, long long wq) {
+  if (q.fate != FATE_REMOVED && (q.gside >= 0 || q.fate == FATE_ESCAPED || q.cell0 != cell)) {
+    const int G = d.G;
+    const double wd = (double)q.w;
+    const bool start_in = q.gside < 0;
+    const bool end_in = q.fate == FATE_SURVIVED || q.fate == FATE_ABSORBED;
+    if (start_in) atomic_add_fixed(d.Wq + 2 * (q.cell0 * G + q.g), -wq);
+    if (end_in) atomic_add_fixed(d.Wq + 2 * (cell * G + q.g), wq);
+    if (!start_in) atomicAdd(d.inflow + q.gside * G + q.g, wd);
+    if (q.fate == FATE_ESCAPED) atomicAdd(d.esc + q.eside * G + q.g, wd);
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ void record32(const Dev& d, const P32& q, long long i, int cell) {
+  if (d.rec && i < d.rec_cap) {
+    RecordOut& rr = d.rec[i];
+    rr.id = q.id; rr.fate = q.fate; rr.cell0 = q.cell0;
+    rr.cell1 = (q.fate == FATE_REMOVED && q.gside >= 0) ? q.cx : cell;
+    rr.grp = q.g; rr.nseg = q.nseg; rr.pad = 0;
+    rr.x = q.cx * d.dx + (double)q.xi;
+    rr.y = DIM >= 2 ? q.cy * d.dy + (double)q.eta : 0.0;
+    rr.ox = q.ox; rr.oy = q.oy; rr.nu = q.nu; rr.w = (double)q.w; rr.t_end = q.t_tra;
+    rr.z = DIM == 3 ? q.cz * d.dz + (double)q.zeta : 0.0;
+    rr.oz = q.oz;
+  }
+}
+
+// Slot i of the other buffer (kDeadKey unless the particle survived); false
+// for a survivor that found no slot (counted in W but not in E_surv: its
+// energy stays with the wave part).
+template <int DIM>
+__device__ __forceinline__ bool store32(const Dev& d, unsigned nxb, const P32& q, long long i, int cell) {
+  const bool keep = q.fate == FATE_SURVIVED;
+  if (i >= d.capacity) {
+    if (keep) atomicOr(&d.ctrl->status, ST_CAPACITY);
+    return false;
+  }
+  d.fx[nxb][i] = q.xi;
+  d.fox[nxb][i] = q.ox;
+  if (DIM >= 2) { d.fy[nxb][i] = q.eta; d.foy[nxb][i] = q.oy; }
+  if (DIM == 3) { d.fz[nxb][i] = q.zeta; d.foz[nxb][i] = q.oz; }
+  d.fnu[nxb][i] = q.nu;
+  d.fw[nxb][i] = q.w;
+  d.pid[nxb][i] = q.id;
+  d.pkey[nxb][i] = keep ? (uint32_t)(cell * d.G + q.g) : kDeadKey;
+  return keep;
+}
+
+// A newborn of the virtual index j = i - n_surv (Eq. IhpFormula): its bin
+// from the birth scan, identity, position uniform in its cell (or, in a
+// black-body ghost, the entering set), isotropic direction, frequency by
+// the linear sampler (App. A) and weight.
+template <int DIM>
+__device__ __forceinline__ void birth32(const Dev& d, P32& q, DrawsF& rng, uint32_t j, uint32_t step) {
+  const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
+  q.newborn = true;
+  const int bin = find_bin(d.off, d.nbins, j);
+  const uint32_t kk = j - __ldg(d.off + bin);
+  q.id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
+         (unsigned long long)kk;
+  rng.init(q.id, step, 0u);
+  const int cb = (int)div_bin(d, (uint32_t)bin);
+  q.g = bin - cb * G;
+  if (cb < d.ncell) {
+    if (DIM == 3) {
+      q.cz = cb / (nx * ny);
+      const int rem = cb - q.cz * nx * ny;
+      q.cy = rem / nx;
+      q.cx = rem - q.cy * nx;
+    } else {
+      q.cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0;
+      q.cx = cb - q.cy * nx;
+    }
+    q.xi = rng.next(d.pk) * d.dxf;
+    if (DIM >= 2) q.eta = rng.next(d.pk) * d.dyf;
+    if (DIM == 3) q.zeta = rng.next(d.pk) * d.dzf;
+    if (DIM == 1) {
+      q.ox = 2.0f * rng.next(d.pk) - 1.0f;
+    } else {
+      const float muz = 2.0f * rng.next(d.pk) - 1.0f;
+      const float ph = rng.next(d.pk);
+      float sp, cp;
+      sincospif(2.0f * ph, &sp, &cp);
+      const float sq = sqrtf(fmaxf(0.0f, 1.0f - muz * muz));
+      q.ox = sq * cp;
+      q.oy = sq * sp;
+      if (DIM == 3) q.oz = muz;
+    }
+  } else {
+    const int side = cb - d.ncell;
+    const float u = rng.next(d.pk);
+    const float mm = sqrtf(rng.next(d.pk));
+    const float dd = u * d.vf * mm * d.dtf;
+    q.cx = side == 0 ? -1 : nx;
+    q.xi = side == 0 ? d.dxf - dd : dd;
+    q.ox = side == 0 ? mm : -mm;
+    q.gside = side;
+  }
+  if (!d.grey)
+    q.nu = sample_nu_f(__ldg(d.nu_edges_f + q.g), __ldg(d.nu_edges_f + q.g + 1), __ldg(d.khat_f + bin),
+                       rng.next(d.pk));
+  q.w = __ldg(d.omega_f + bin);
+}
+
+// Cell coordinates of a survivor from its bin key (cell c * G + group g).
+template <int DIM>
+__device__ __forceinline__ void decode_key32(const Dev& d, uint32_t key, P32& q) {
+  const int nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
+  if (key >= (uint32_t)d.nbins) key = 0u;   // only after a failed wait (flagged): stay in range
+  const int cell = (int)div_bin(d, key);
+  q.g = (int)(key - (uint32_t)cell * (uint32_t)d.G);
+  if (DIM == 3) {
+    q.cz = cell / (nx * ny);
+    const int rem = cell - q.cz * nx * ny;
+    q.cy = rem / nx;
+    q.cx = rem - q.cy * nx;
+  } else {
+    q.cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
+    q.cx = cell - q.cy * nx;
+  }
+}
+
+__device__ __forceinline__ void clear32(P32& q) {
+  q.xi = q.eta = q.zeta = q.ox = q.oy = q.oz = q.nu = q.w = 0.f;
+  q.t_rem = q.t_tra = 0.0f;
+  q.id = 0ull;
+  q.cx = q.cy = q.cz = q.g = 0;
+  q.gside = -1;
+  q.newborn = false;
+  q.collided = false;
+  q.fate = FATE_REMOVED;
+  q.nseg = 0;
+  q.eside = -1;
+}
+
+// Free time of the particle in its cell (a survivor draws it; a UGKWP
+// newborn has t_f = dt) and its first flight: if that flight ends the step
+// (no face first), finish it and return false; else return true with t_rem
+// and collided set for stream_loop32 (the same arithmetic as its first pass).
+template <int DIM>
+__device__ __forceinline__ bool first_flight32(const Dev& d, P32& q, DrawsF& rng, float inup, int tab_n,
+                                               bool tab_invT, const float* s_sinv, const float* s_invT) {
+  const int nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
+  const float dxf = d.dxf, dyf = d.dyf, dzf = d.dzf, vf = d.vf, dtf = d.dtf;
+  if (q.newborn && (d.method == 0 || q.gside >= 0)) {   // UGKP newborns draw t_f too
+    q.t_rem = dtf;
+    q.collided = false;
+  } else {
+    const UPair u = rng.next2(d.pk);
+    const float sig_inv = inv_sigma32(d, (q.cz * ny + q.cy) * nx + q.cx, q.nu, inup, tab_n, tab_invT, s_sinv, s_invT);
+    const float tc = neg_log_u(u) * d.inv_rate_f * sig_inv;
+    q.collided = tc < dtf;
+    q.t_rem = q.collided ? tc : dtf;
+  }
+  const float ivx = q.ox != 0.0f ? __frcp_rn(vf * fabsf(q.ox)) : 0.0f;
+  const float ivy = (DIM >= 2 && q.oy != 0.0f) ? __frcp_rn(vf * fabsf(q.oy)) : 0.0f;
+  const float ivz = (DIM == 3 && q.oz != 0.0f) ? __frcp_rn(vf * fabsf(q.oz)) : 0.0f;
+  float tx = INFINITY, ty = INFINITY, tz = INFINITY;
+  if (q.ox > 0.0f) tx = fmaxf(dxf - q.xi, 0.0f) * ivx;
+  else if (q.ox < 0.0f) tx = fmaxf(q.xi, 0.0f) * ivx;
+  if (DIM >= 2) {
+    if (q.oy > 0.0f) ty = fmaxf(dyf - q.eta, 0.0f) * ivy;
+    else if (q.oy < 0.0f) ty = fmaxf(q.eta, 0.0f) * ivy;
+  }
+  if (DIM == 3) {
+    if (q.oz > 0.0f) tz = fmaxf(dzf - q.zeta, 0.0f) * ivz;
+    else if (q.oz < 0.0f) tz = fmaxf(q.zeta, 0.0f) * ivz;
+  }
+  const float tf = fminf(fminf(tx, ty), tz);
+  if (tf < q.t_rem) return true;
+  q.nseg = 1;
+  q.xi = fminf(fmaxf(fmaf(vf * q.ox, q.t_rem, q.xi), 0.0f), dxf);
+  if (DIM >= 2) q.eta = fminf(fmaxf(fmaf(vf * q.oy, q.t_rem, q.eta), 0.0f), dyf);
+  if (DIM == 3) q.zeta = fminf(fmaxf(fmaf(vf * q.oz, q.t_rem, q.zeta), 0.0f), dzf);
+  q.t_tra = q.t_rem;
+  q.fate = q.ghost ? FATE_REMOVED : (q.collided ? FATE_ABSORBED : FATE_SURVIVED);
+  return false;
+}
+
+// Shared set-up of the FP32 kernels of a single problem: the per-cell opacity
+// factors in shared memory (when they fit) at the start of the dynamic area.
+struct Tab32 {
+  int n;
+  bool invT;
+  float *sinv, *sinvT;
+};
+
+template <bool ENS>
+__device__ __forceinline__ Tab32 load_tab32(const Dev& d0, unsigned char* s_dyn) {
+  Tab32 t;
+  t.n = ENS ? 0 : ((d0.sig_law == 2 || d0.ncell > kSmemCells) ? 0 : d0.ncell);
+  t.invT = !ENS && t.n && d0.sig_law == 1 && !d0.grey;
+  t.sinv = reinterpret_cast<float*>(s_dyn);
+  t.sinvT = t.sinv + t.n;
+  if (!ENS) {
+    for (int c = threadIdx.x; c < t.n; c += blockDim.x) {
+      t.sinv[c] = __ldg(d0.sTinv_f + c);
+      if (t.invT) t.sinvT[c] = __ldg(d0.invT_f + c);
+    }
+  }
+  return t;
+}
+
+__device__ __forceinline__ size_t tab32_bytes(const Tab32& t) {
+  return (4 * (size_t)t.n * (t.invT ? 2 : 1) + 127) & ~(size_t)127;
+}
+
+// Every warp stages its own chunks: chunk k of global warp gw is chunk
+// gw + k * (warps in the grid) of the kernel's particles (C = 32 x rounds
+// particles each), so no warp waits for another and no atomic hands out work.
+// Lane 0 keeps kStages chunks in flight: it starts the bulk copies of a
+// chunk's survivors into a stage of the warp's ring (completion counted on
+// that stage's mbarrier), and after the warp has streamed a chunk it reuses
+// the stage for the chunk kStages further on.
+template <int DIM, bool ENS>
+struct Ring32 {
+  unsigned char* ring;
+  uint64_t* bar;
+  int C;
+  size_t stage_sz;
+  // lane 0: expect the bytes of chunk c's survivors (below n_surv of member
+  // dm's buffer cb) on stage s and start their copies
+  __device__ __forceinline__ void issue(const Dev* dm, unsigned cb, long long lc, long long n_surv, int s) const {
+    const long long first = lc * C;
+    long long n = n_surv - first;
+    n = n < 0 ? 0 : (n > C ? C : n);
+    const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
+    const unsigned bytes = n ? c4 * 4u * StageF<DIM>::kArr4 + c2 * 8u : 0u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(&bar[s], bytes);
+    if (bytes) {
+      const StageF<DIM> sg(ring + s * stage_sz, C);
+      bulk_g2s(sg.id, dm->pid[cb] + first, c2 * 8u, &bar[s]);
+      bulk_g2s(sg.x, dm->fx[cb] + first, c4 * 4u, &bar[s]);
+      bulk_g2s(sg.ox, dm->fox[cb] + first, c4 * 4u, &bar[s]);
+      bulk_g2s(sg.nu, dm->fnu[cb] + first, c4 * 4u, &bar[s]);
+      bulk_g2s(sg.w, dm->fw[cb] + first, c4 * 4u, &bar[s]);
+      bulk_g2s(sg.key, dm->pkey[cb] + first, c4 * 4u, &bar[s]);
+      if (DIM >= 2) {
+        bulk_g2s(sg.y, dm->fy[cb] + first, c4 * 4u, &bar[s]);
+        bulk_g2s(sg.oy, dm->foy[cb] + first, c4 * 4u, &bar[s]);
+      }
+      if (DIM == 3) {
+        bulk_g2s(sg.z, dm->fz[cb] + first, c4 * 4u, &bar[s]);
+        bulk_g2s(sg.oz, dm->foz[cb] + first, c4 * 4u, &bar[s]);
+      }
+    }
+  }
+};
+
+// A survivor from slot li of a staged chunk.
+template <int DIM>
+__device__ __forceinline__ void from_stage32(const Dev& d, const StageF<DIM>& sg, int li, P32& q) {
+  q.xi = sg.x[li];
+  q.ox = sg.ox[li];
+  if (DIM >= 2) { q.eta = sg.y[li]; q.oy = sg.oy[li]; }
+  if (DIM == 3) { q.zeta = sg.z[li]; q.oz = sg.oz[li]; }
+  q.nu = sg.nu[li];
+  q.w = sg.w[li];
+  q.id = sg.id[li];
+  decode_key32<DIM>(d, sg.key[li], q);
+}
+
+// The general FP32 kernel: every particle of the step (survivors staged,
+// newborns born in registers), first flight and streaming loop in place.
 template <int DIM, bool ENS, int NT>
-__global__ void __launch_bounds__(NT + 32, NT >= 512 ? 1 : (NT >= 256 ? 3 : 6))
+__global__ void __launch_bounds__(NT, (ENS || DIM == 3) ? (NT >= 512 ? 1 : (NT >= 256 ? 2 : 4)) : (NT >= 512 ? 2 : (NT >= 256 ? 4 : 8)))
     k_stream32(const __grid_constant__ Dev d0, const Ens e, int rounds) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
-  __shared__ uint64_t s_full[kStages], s_empty[kStages];
-  __shared__ long long s_tile[kStages];
-  const long long tile = (long long)NT * rounds;
-  const size_t stage_sz = (size_t)tile * StageF<DIM>::kBytesPer;
+  __shared__ uint64_t s_full[NT / 32][kStages];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per-cell opacity factors of a single problem in shared memory
-  const int tab_n = ENS ? 0 : ((d0.sig_law == 2 || d0.ncell > kSmemCells) ? 0 : d0.ncell);
-  const bool tab_invT = !ENS && tab_n && d0.sig_law == 1 && !d0.grey;
-  float* s_sinv = reinterpret_cast<float*>(s_dyn + kStages * stage_sz);
-  float* s_invT = s_sinv + tab_n;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < kStages; ++k) {
-      mbar_init(&s_full[k], 1);
-      mbar_init(&s_empty[k], NT / 32);
-    }
+  const Tab32 tab = load_tab32<ENS>(d0, s_dyn);
+  Ring32<DIM, ENS> rg;
+  rg.C = 32 * rounds;
+  rg.stage_sz = (size_t)rg.C * StageF<DIM>::kBytesPer;
+  rg.ring = s_dyn + tab32_bytes(tab) + (size_t)warp * kStages * rg.stage_sz;
+  rg.bar = s_full[warp];
+  const int C = rg.C;
+  if (lane == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&rg.bar[k], 1);
     mbar_init_fence();
-  }
-  if (!ENS) {
-    for (int c = threadIdx.x; c < tab_n; c += blockDim.x) {
-      s_sinv[c] = __ldg(d0.sTinv_f + c);
-      if (tab_invT) s_invT[c] = __ldg(d0.invT_f + c);
-    }
   }
   __syncthreads();
   const StepHead h0 = ENS ? StepHead{} : step_head(d0);
-
-  if (warp == NT / 32) {
-    // ---- producer: hand out tiles, stage their survivors
-    if (lane != 0) return;
-    unsigned long long* ctr = ENS ? e.tile_next : &d0.ctrl->tile_next;
-    unsigned int* status = ENS ? &e.devs[0].ctrl->status : &d0.ctrl->status;
-    const long long ntiles = ENS ? (long long)e.tile0[e.M] : (h0.n_tot + tile - 1) / tile;
-    bool gave_up = false;
-    unsigned issued = 0, lastpar = 0;
-    for (int it = 0;; ++it) {
-      const int s = it % kStages;
-      if (it >= kStages) {
-        const unsigned par = (unsigned)((it / kStages) - 1) & 1u;
-        // the previous copy into this stage has landed (it needs no other warp) ...
-        if (!mbar_wait_bounded(&s_full[s], par)) { atomicOr(status, ST_TIMEOUT); gave_up = true; }
-        // ... and every streaming warp is done with it
-        if (!gave_up && !mbar_wait_bounded(&s_empty[s], par)) { atomicOr(status, ST_TIMEOUT); gave_up = true; }
-      }
-      long long t = (long long)atomicAdd(ctr, 1ull);
-      if (t >= ntiles) t = -1;
-      s_tile[s] = t;
-      unsigned bytes = 0;
-      const Dev* dm = &d0;
-      long long first = 0, n = 0;
-      unsigned cb = h0.cur;
-      if (t >= 0) {
-        long long lt = t, n_surv = h0.n_surv;
-        if (ENS) {
-          const int m = find_member(e.tile0, e.M, t);
-          dm = &e.devs[m];
-          lt = t - (long long)e.tile0[m];
-          cb = dm->ctrl->cur;
-          n_surv = (long long)dm->ctrl->n_part[cb];
-        }
-        first = lt * tile;
-        n = n_surv - first;
-        n = n < 0 ? 0 : (n > tile ? tile : n);
-        const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
-        bytes = n ? c4 * 4u * StageF<DIM>::kArr4 + c2 * 8u : 0u;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(&s_full[s], bytes);
-      issued |= 1u << s;
-      lastpar = (lastpar & ~(1u << s)) | ((unsigned)((it / kStages) & 1) << s);
-      if (bytes) {
-        const StageF<DIM> sg(s_dyn + s * stage_sz, (int)tile);
-        const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
-        bulk_g2s(sg.id, dm->pid[cb] + first, c2 * 8u, &s_full[s]);
-        bulk_g2s(sg.x, dm->fx[cb] + first, c4 * 4u, &s_full[s]);
-        bulk_g2s(sg.ox, dm->fox[cb] + first, c4 * 4u, &s_full[s]);
-        bulk_g2s(sg.nu, dm->fnu[cb] + first, c4 * 4u, &s_full[s]);
-        bulk_g2s(sg.w, dm->fw[cb] + first, c4 * 4u, &s_full[s]);
-        bulk_g2s(sg.key, dm->pkey[cb] + first, c4 * 4u, &s_full[s]);
-        if (DIM >= 2) {
-          bulk_g2s(sg.y, dm->fy[cb] + first, c4 * 4u, &s_full[s]);
-          bulk_g2s(sg.oy, dm->foy[cb] + first, c4 * 4u, &s_full[s]);
-        }
-        if (DIM == 3) {
-          bulk_g2s(sg.z, dm->fz[cb] + first, c4 * 4u, &s_full[s]);
-          bulk_g2s(sg.oz, dm->foz[cb] + first, c4 * 4u, &s_full[s]);
-        }
-      }
-      if (t < 0) break;
+  const long long gw = (long long)blockIdx.x * (NT / 32) + warp, tw = (long long)gridDim.x * (NT / 32);
+  const long long nchunks = ENS ? (long long)e.tile0[e.M] : (h0.n_tot + C - 1) / C;
+  unsigned* status0 = ENS ? &e.devs[0].ctrl->status : &d0.ctrl->status;
+  auto issue = [&](long long c, int s) {
+    if (ENS) {
+      const int m = find_member(e.tile0, e.M, c);
+      const Dev* dm = &e.devs[m];
+      const unsigned cb = dm->ctrl->cur;
+      rg.issue(dm, cb, c - (long long)e.tile0[m], (long long)dm->ctrl->n_part[cb], s);
+    } else {
+      rg.issue(&d0, h0.cur, c, h0.n_surv, s);
     }
-    // no copy may still be landing when the block's last warp leaves
-    for (int s = 0; s < kStages; ++s)
-      if ((issued >> s) & 1u) mbar_wait_bounded(&s_full[s], (lastpar >> s) & 1u);
-    return;
-  }
+  };
+  int issued = 0;   // chunks of this warp whose copies were started
+  for (; issued < kStages && gw + issued * tw < nchunks; ++issued)
+    if (lane == 0) issue(gw + issued * tw, issued);
+  __syncwarp();
 
-  // ---- streaming warps
   Counters cnt;
   int acc_m = 0;
-  for (int it = 0;; ++it) {
-    const int st = it % kStages;
-    if (!mbar_wait_bounded(&s_full[st], (unsigned)(it / kStages) & 1u)) {
-      atomicOr(ENS ? &e.devs[0].ctrl->status : &d0.ctrl->status, ST_TIMEOUT);
+  int k = 0, st = 0;
+  unsigned par = 0u;   // stage st of chunk k, and the phase parity it waits for
+  for (long long c = gw; c < nchunks; c += tw, ++k, st = st + 1 == kStages ? 0 : st + 1, par ^= st == 0 ? 1u : 0u) {
+    if (!mbar_wait_bounded(&rg.bar[st], par)) {
+      atomicOr(status0, ST_TIMEOUT);
       break;
     }
-    const long long t = *reinterpret_cast<volatile long long*>(&s_tile[st]);
-    if (t < 0) break;
-    const StageF<DIM> sgt(s_dyn + st * stage_sz, (int)tile);
-    const int m = ENS ? find_member(e.tile0, e.M, t) : 0;
+    const StageF<DIM> sgt(rg.ring + st * rg.stage_sz, C);
+    const int m = ENS ? find_member(e.tile0, e.M, c) : 0;
     if (ENS && m != acc_m) { flush_counters(e.devs[acc_m].ctrl, cnt); acc_m = m; }
     const Dev& d = ENS ? e.devs[m] : d0;
-    const long long lt = ENS ? t - (long long)e.tile0[m] : t;
+    const long long lc = ENS ? c - (long long)e.tile0[m] : c;
     Ctrl* ctrl = d.ctrl;
     const unsigned cur = ENS ? ctrl->cur : h0.cur, nxb = cur ^ 1u;
     const long long n_surv = ENS ? (long long)ctrl->n_part[cur] : h0.n_surv;
     const long long n_tot = ENS ? n_surv + (long long)ctrl->n_new : h0.n_tot;
     const uint32_t step = ENS ? (uint32_t)ctrl->step : h0.step;
-    const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1, nz = DIM == 3 ? d.nz : 1;
-    const float dxf = d.dxf, dyf = d.dyf, dzf = d.dzf, vf = d.vf, dtf = d.dtf;
-    const float inv_rate = d.inv_rate_f, spf = d.spf;
+    const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
     for (int r = 0; r < rounds; ++r) {
-    const int li = (warp * rounds + r) * 32 + lane;
-    const long long i = lt * tile + li;
-    const bool valid = i < n_tot;
-    float xi = 0.f, eta = 0.f, zeta = 0.f, ox = 0.f, oy = 0.f, oz = 0.f, nu = 0.f, w = 0.f;
-    unsigned long long id = 0ull;
-    int cx = 0, cy = 0, cz = 0, g = 0, gside = -1;
-    bool newborn = false;
-    DrawsF rng;
-    rng.init(0ull, step, 0u);
-    if (valid) {
-      if (i < n_surv) {
-        xi = sgt.x[li];
-        ox = sgt.ox[li];
-        if (DIM >= 2) { eta = sgt.y[li]; oy = sgt.oy[li]; }
-        if (DIM == 3) { zeta = sgt.z[li]; oz = sgt.oz[li]; }
-        nu = sgt.nu[li];
-        w = sgt.w[li];
-        id = sgt.id[li];
-        uint32_t key = sgt.key[li];
-        if (key >= (uint32_t)d.nbins) key = 0u;   // only after a failed wait (flagged): stay in range
-        const int cell = (int)div_bin(d, key);
-        g = (int)(key - (uint32_t)cell * (uint32_t)G);
-        if (DIM == 3) {
-          cz = cell / (nx * ny);
-          const int rem = cell - cz * nx * ny;
-          cy = rem / nx;
-          cx = rem - cy * nx;
-        } else {
-          cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cell) : 0;
-          cx = cell - cy * nx;
-        }
-        rng.init(id, step, 0u);
+      const int li = r * 32 + lane;
+      const long long i = lc * C + li;
+      // every lane of this pass holds a survivor of the previous step (the
+      // common case: no newborn code, every lane valid)
+      const bool surv_pass = lc * C + (long long)r * 32 + 32 <= n_surv;
+      const bool valid = i < n_tot;
+      P32 q;
+      clear32(q);
+      DrawsF rng;
+      if (surv_pass || (valid && i < n_surv)) {
+        from_stage32<DIM>(d, sgt, li, q);
+        rng.init(q.id, step, 0u);
+      } else if (valid) {
+        birth32<DIM>(d, q, rng, (uint32_t)(i - n_surv), step);
       } else {
-        newborn = true;
-        const uint32_t j = (uint32_t)(i - n_surv);
-        const int bin = find_bin(d.off, d.nbins, j);
-        const uint32_t k = j - __ldg(d.off + bin);
-        id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
-             (unsigned long long)k;
-        rng.init(id, step, 0u);
-        const int cb = (int)div_bin(d, (uint32_t)bin);
-        g = bin - cb * G;
-        if (cb < d.ncell) {
-          if (DIM == 3) {
-            cz = cb / (nx * ny);
-            const int rem = cb - cz * nx * ny;
-            cy = rem / nx;
-            cx = rem - cy * nx;
-          } else {
-            cy = DIM == 2 ? (int)div_nx(d, (uint32_t)cb) : 0;
-            cx = cb - cy * nx;
-          }
-          xi = rng.next(d.pk) * dxf;
-          if (DIM >= 2) eta = rng.next(d.pk) * dyf;
-          if (DIM == 3) zeta = rng.next(d.pk) * dzf;
-          if (DIM == 1) {
-            ox = 2.0f * rng.next(d.pk) - 1.0f;
-          } else {
-            const float muz = 2.0f * rng.next(d.pk) - 1.0f;
-            const float ph = rng.next(d.pk);
-            float sp, cp;
-            sincospif(2.0f * ph, &sp, &cp);
-            const float s = sqrtf(fmaxf(0.0f, 1.0f - muz * muz));
-            ox = s * cp;
-            oy = s * sp;
-            if (DIM == 3) oz = muz;
-          }
-        } else {
-          const int side = cb - d.ncell;
-          const float u = rng.next(d.pk);
-          const float m = sqrtf(rng.next(d.pk));
-          const float dd = u * vf * m * dtf;
-          cx = side == 0 ? -1 : nx;
-          xi = side == 0 ? dxf - dd : dd;
-          ox = side == 0 ? m : -m;
-          gside = side;
-        }
-        if (!d.grey)
-          nu = sample_nu_f(__ldg(d.nu_edges_f + g), __ldg(d.nu_edges_f + g + 1), __ldg(d.khat_f + bin),
-                           rng.next(d.pk));
-        w = __ldg(d.omega_f + bin);
+        rng.init(0ull, step, 0u);
+      }
+      q.cell0 = q.gside >= 0 ? q.cx : (q.cz * ny + q.cy) * nx + q.cx;
+      q.ghost = q.gside >= 0;
+      // ---- streaming
+      float inup = 1.0f;
+      bool more = false;
+      if (valid) {
+        inup = d.grey ? 1.0f : pow_fast_f(q.nu, -d.spf);
+        more = first_flight32<DIM>(d, q, rng, inup, ENS ? 0 : tab.n, tab.invT, tab.sinv, tab.sinvT);
+      }
+      if (more) stream_loop32<DIM>(d, q, rng, inup, ENS ? 0 : tab.n, tab.invT, tab.sinv, tab.sinvT);
+      const int cell = (q.cz * ny + q.cy) * nx + q.cx;
+      bool stored = false;
+      if (valid) stored = store32<DIM>(d, nxb, q, i, cell);
+      // ---- tallies (W and E_surv in fixed point, see to_fixed_f)
+      const long long wq = valid ? to_fixed_f(q.w, d.tq_shift, &ctrl->status) : 0ll;
+      warp_run_add_fixed(d.Esq, stored ? cell * G + q.g : -1 - lane, wq, d.sort_cnt);
+      if (valid) {
+        cross_tallies32(d, q, cell, wq);
+        cnt.seg += (unsigned)q.nseg;
+        cnt.abs += q.fate == FATE_ABSORBED;
+        cnt.esc += q.fate == FATE_ESCAPED;
+        cnt.surv += q.fate == FATE_SURVIVED;
+        cnt.rem += q.fate == FATE_REMOVED;
+        if (!ENS) record32<DIM>(d, q, i, cell);
       }
     }
-    const int cell0 = gside >= 0 ? cx : (cz * ny + cy) * nx + cx;
-
-    // 1/sigma(nu, T^n) in the particle's cell: the per-cell factors from
-    // shared memory when the problem's table is there
-    auto inv_sigma = [&](int c, float inup) -> float {
-      if (!ENS && tab_n) {
-        float si = s_sinv[c] * inup;
-        if (tab_invT) si /= -expm1f(-nu * s_invT[c]);
-        return fmaxf(si, d.inv_capf);
-      }
-      return inv_sigma_particle_f(d, c, nu, inup);
-    };
-
-    // ---- streaming
-    int fate = FATE_REMOVED, nseg = 0, eside = -1;
-    float t_tra = 0.0f;
-    if (valid) {
-      const float inup = d.grey ? 1.0f : pow_fast_f(nu, -spf);
-      float t_rem;
-      bool collided;
-      if (newborn && (d.method == 0 || gside >= 0)) {   // UGKP newborns draw t_f too
-        t_rem = dtf;
-        collided = false;
-      } else {
-        const UPair u = rng.next2(d.pk);
-        const float sig_inv = inv_sigma((cz * ny + cy) * nx + cx, inup);
-        const float tc = neg_log_u(u) * inv_rate * sig_inv;
-        collided = tc < dtf;
-        t_rem = collided ? tc : dtf;
-      }
-      bool ghost = gside >= 0;
-      const float ivx = ox != 0.0f ? __frcp_rn(vf * fabsf(ox)) : 0.0f;
-      const float ivy = (DIM >= 2 && oy != 0.0f) ? __frcp_rn(vf * fabsf(oy)) : 0.0f;
-      const float ivz = (DIM == 3 && oz != 0.0f) ? __frcp_rn(vf * fabsf(oz)) : 0.0f;
-      for (int guard = 0;; ++guard) {
-        if (guard >= 4096) {
-          atomicOr(&ctrl->status, ST_NONFINITE);
-          fate = FATE_REMOVED;
-          break;
-        }
-        float tx = INFINITY, ty = INFINITY, tz = INFINITY;
-        if (ox > 0.0f) tx = fmaxf(dxf - xi, 0.0f) * ivx;
-        else if (ox < 0.0f) tx = fmaxf(xi, 0.0f) * ivx;
-        if (DIM >= 2) {
-          if (oy > 0.0f) ty = fmaxf(dyf - eta, 0.0f) * ivy;
-          else if (oy < 0.0f) ty = fmaxf(eta, 0.0f) * ivy;
-        }
-        if (DIM == 3) {
-          if (oz > 0.0f) tz = fmaxf(dzf - zeta, 0.0f) * ivz;
-          else if (oz < 0.0f) tz = fmaxf(zeta, 0.0f) * ivz;
-        }
-        // nearest face; ties go to the lower axis
-        int axis = (tx <= ty) ? 0 : 1;
-        float tf = axis == 0 ? tx : ty;
-        if (DIM == 3 && tz < tf) { axis = 2; tf = tz; }
-        if (tf < t_rem) {
-          ++nseg;
-          t_tra += tf;
-          t_rem -= tf;
-          int dir;
-          if (axis == 0) {
-            dir = ox > 0.0f ? 1 : -1;
-            xi = dir > 0 ? dxf : 0.0f;
-            if (DIM >= 2) eta = fminf(fmaxf(fmaf(vf * oy, tf, eta), 0.0f), dyf);
-            if (DIM == 3) zeta = fminf(fmaxf(fmaf(vf * oz, tf, zeta), 0.0f), dzf);
-          } else if (DIM < 3 || axis == 1) {
-            dir = oy > 0.0f ? 1 : -1;
-            eta = dir > 0 ? dyf : 0.0f;
-            xi = fminf(fmaxf(fmaf(vf * ox, tf, xi), 0.0f), dxf);
-            if (DIM == 3) zeta = fminf(fmaxf(fmaf(vf * oz, tf, zeta), 0.0f), dzf);
-          } else {
-            dir = oz > 0.0f ? 1 : -1;
-            zeta = dir > 0 ? dzf : 0.0f;
-            xi = fminf(fmaxf(fmaf(vf * ox, tf, xi), 0.0f), dxf);
-            eta = fminf(fmaxf(fmaf(vf * oy, tf, eta), 0.0f), dyf);
-          }
-          const int nxc = cx + (axis == 0 ? dir : 0), nyc = cy + (axis == 1 ? dir : 0);
-          const int nzc = cz + (axis == 2 ? dir : 0);
-          if (nxc < 0 || nxc >= nx || nyc < 0 || nyc >= ny || (DIM == 3 && (nzc < 0 || nzc >= nz))) {
-            const int side = axis * 2 + (dir > 0 ? 1 : 0);
-            if (d.bc[side] == BC_REFLECT) {
-              if (axis == 0) ox = -ox; else if (axis == 1) oy = -oy; else oz = -oz;
-              continue;
-            }
-            fate = FATE_ESCAPED;
-            eside = side;
-            break;
-          }
-          ghost = false;
-          if (axis == 0) xi = dir > 0 ? 0.0f : dxf;
-          else if (axis == 1) eta = dir > 0 ? 0.0f : dyf;
-          else zeta = dir > 0 ? 0.0f : dzf;
-          cx = nxc;
-          cy = nyc;
-          cz = nzc;
-          const UPair u = rng.next2(d.pk);
-          const float sig_inv = inv_sigma((cz * ny + cy) * nx + cx, inup);
-          const float tc = neg_log_u(u) * inv_rate * sig_inv;
-          const float avail = dtf - t_tra;
-          collided = tc < avail;
-          t_rem = collided ? tc : avail;
-          continue;
-        }
-        ++nseg;
-        xi = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
-        if (DIM >= 2) eta = fminf(fmaxf(fmaf(vf * oy, t_rem, eta), 0.0f), dyf);
-        if (DIM == 3) zeta = fminf(fmaxf(fmaf(vf * oz, t_rem, zeta), 0.0f), dzf);
-        t_tra += t_rem;
-        fate = ghost ? FATE_REMOVED : (collided ? FATE_ABSORBED : FATE_SURVIVED);
-        break;
-      }
-    }
-    const int cell = (cz * ny + cy) * nx + cx;
-
-    // ---- in place: slot i of the other buffer (kDeadKey unless it survived)
-    const bool keep = valid && fate == FATE_SURVIVED;
-    const bool room = i < d.capacity;
-    const bool stored = keep && room;
-    if (valid && room) {
-      d.fx[nxb][i] = xi;
-      d.fox[nxb][i] = ox;
-      if (DIM >= 2) { d.fy[nxb][i] = eta; d.foy[nxb][i] = oy; }
-      if (DIM == 3) { d.fz[nxb][i] = zeta; d.foz[nxb][i] = oz; }
-      d.fnu[nxb][i] = nu;
-      d.fw[nxb][i] = w;
-      d.pid[nxb][i] = id;
-      d.pkey[nxb][i] = stored ? (uint32_t)(cell * G + g) : kDeadKey;
-    }
-    if (keep && !room) atomicOr(&ctrl->status, ST_CAPACITY);
-
-    // ---- tallies (W and E_surv in fixed point, see to_fixed_f; FP64 side
-    // tallies).  A survivor that found no slot is counted in W but not in
-    // E_surv: its energy stays with the wave part.
-    const long long wq = valid ? to_fixed_f(w, d.tq_shift, &ctrl->status) : 0ll;
-    warp_run_add_fixed(d.Esq, stored ? cell * G + g : -1 - lane, wq, d.sort_cnt);
-    if (valid && fate != FATE_REMOVED && (gside >= 0 || fate == FATE_ESCAPED || cell0 != cell)) {
-      const double wd = (double)w;
-      const bool start_in = gside < 0;
-      const bool end_in = fate == FATE_SURVIVED || fate == FATE_ABSORBED;
-      if (start_in) atomic_add_fixed(d.Wq + 2 * (cell0 * G + g), -wq);
-      if (end_in) atomic_add_fixed(d.Wq + 2 * (cell * G + g), wq);
-      if (!start_in) atomicAdd(d.inflow + gside * G + g, wd);
-      if (fate == FATE_ESCAPED) atomicAdd(d.esc + eside * G + g, wd);
-    }
-    if (valid) {
-      cnt.seg += (unsigned)nseg;
-      cnt.abs += fate == FATE_ABSORBED;
-      cnt.esc += fate == FATE_ESCAPED;
-      cnt.surv += fate == FATE_SURVIVED;
-      cnt.rem += fate == FATE_REMOVED;
-      if (!ENS && d.rec && i < d.rec_cap) {
-        RecordOut& rr = d.rec[i];
-        rr.id = id; rr.fate = fate; rr.cell0 = cell0; rr.cell1 = (fate == FATE_REMOVED && gside >= 0) ? cx : cell;
-        rr.grp = g; rr.nseg = nseg; rr.pad = 0;
-        rr.x = cx * d.dx + (double)xi;
-        rr.y = DIM >= 2 ? cy * d.dy + (double)eta : 0.0;
-        rr.ox = ox; rr.oy = oy; rr.nu = nu; rr.w = (double)w; rr.t_end = t_tra;
-        rr.z = DIM == 3 ? cz * d.dz + (double)zeta : 0.0;
-        rr.oz = oz;
-      }
-    }
+    // the stage is free: the chunk kStages further on goes into it
+    __syncwarp();
+    if (c + kStages * tw < nchunks) {
+      if (lane == 0) issue(c + kStages * tw, st);
+      ++issued;
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&s_empty[st]);
   }
+  // after a failed wait: no copy may still be landing when the warp leaves
+  if (lane == 0)
+    for (int kk = k; kk < issued; ++kk) mbar_wait_bounded(&rg.bar[kk % kStages], (unsigned)(kk / kStages) & 1u);
   flush_counters(ENS ? e.devs[acc_m].ctrl : d0.ctrl, cnt);
+}
+
+// 1/x to about an ulp (rcp.approx): for the survivor kernel's face test,
+// a decision that needs no correct rounding
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Survivor kernel of a 1D problem whose particles seldom reach a face in a
+// step (v dt / dx small: the slabs), with the power-law opacity and its
+// per-cell factors in shared memory: every survivor draws its free time
+// (Eq. particle-tf-formula) and takes its first flight; one that ends the
+// step there is finished in place (no face crossed, so only E_surv and the
+// counters are tallied); one that reaches a face first is listed (slot,
+// remaining free time) for k_stream32_rest, which streams it with the
+// newborns.  The code a survivor runs here has no crossing loop, no birth
+// sampling and no per-particle branching on the problem's options, so a
+// warp's lanes stay together.  The list is filled through a per-warp buffer
+// in shared memory, 32 entries (one atomic) at a time.  P3: sigma ~ nu^-3.
+template <int NT, bool P3>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
+    k_stream32_fast(const __grid_constant__ Dev d, int rounds) {
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  __shared__ uint64_t s_full[NT / 32][kStages];
+  __shared__ uint32_t s_li[NT / 32][64];
+  __shared__ float s_lt[NT / 32][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int ncell = d.ncell;
+  float* s_sinv = reinterpret_cast<float*>(s_dyn);
+  for (int c = threadIdx.x; c < ncell; c += NT) s_sinv[c] = __ldg(d.sTinv_f + c);
+  Ring32<1, false> rg;
+  rg.C = 32 * rounds;
+  rg.stage_sz = (size_t)rg.C * StageF<1>::kBytesPer;
+  rg.ring = s_dyn + ((4 * (size_t)ncell + 127) & ~(size_t)127) + (size_t)warp * kStages * rg.stage_sz;
+  rg.bar = s_full[warp];
+  const int C = rg.C;
+  if (lane == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&rg.bar[k], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const StepHead h0 = step_head(d);
+  Ctrl* ctrl = d.ctrl;
+  // a contiguous range of chunks per warp (bins run on across its chunks)
+  const long long gw = (long long)blockIdx.x * (NT / 32) + warp, tw = (long long)gridDim.x * (NT / 32);
+  const long long nall = (h0.n_surv + C - 1) / C, per = (nall + tw - 1) / tw;
+  const long long c0 = gw * per < nall ? gw * per : nall;
+  const long long nchunks = c0 + per < nall ? c0 + per : nall;
+  const unsigned nxb = h0.cur ^ 1u;
+  const uint32_t G = (uint32_t)d.G;
+  const float invG = d.invG_f;
+  const float dxf = d.dxf, vf = d.vf, dtf = d.dtf, inv_rate = d.inv_rate_f, inv_capf = d.inv_capf, spf = d.spf;
+  const int tq_shift = d.tq_shift;
+  const bool grey = d.grey;
+  int issued = 0;
+  for (; issued < kStages && c0 + issued < nchunks; ++issued)
+    if (lane == 0) rg.issue(&d, h0.cur, c0 + issued, h0.n_surv, issued);
+  __syncwarp();
+
+  // this thread's run of E_surv (fixed point, at most 32 weights below
+  // 2^57 each) and survivor count in bin acc_key
+  int acc_key = -1;
+  long long acc_w = 0;
+  unsigned acc_n = 0u;
+  unsigned nl = 0;   // entries in the warp's list buffer (same in every lane)
+  auto flush_list = [&](unsigned k) {   // the first k buffered entries to the global list
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&ctrl->n_slow, (unsigned long long)k);
+    base = __shfl_sync(full, base, 0);
+    if ((unsigned)lane < k) {
+      d.slow_i[base + lane] = s_li[warp][lane];
+      d.slow_t[base + lane] = s_lt[warp][lane];
+    }
+    __syncwarp();
+    uint32_t a = 0u;
+    float b = 0.0f;
+    const bool mv = (unsigned)lane < nl - k;   // keep the rest at the front
+    if (mv) { a = s_li[warp][k + lane]; b = s_lt[warp][k + lane]; }
+    __syncwarp();
+    if (mv) { s_li[warp][lane] = a; s_lt[warp][lane] = b; }
+    __syncwarp();
+    nl -= k;
+  };
+
+  Counters cnt;
+  int k = 0, st = 0;
+  unsigned par = 0u;   // stage st of chunk k, and the phase parity it waits for
+  for (long long c = c0; c < nchunks; ++c, ++k, st = st + 1 == kStages ? 0 : st + 1, par ^= st == 0 ? 1u : 0u) {
+    if (!mbar_wait_bounded(&rg.bar[st], par)) {
+      atomicOr(&ctrl->status, ST_TIMEOUT);
+      break;
+    }
+    const StageF<1> sg(rg.ring + st * rg.stage_sz, C);
+    const long long base = c * C;
+    const int nval = (int)(h0.n_surv - base < C ? h0.n_surv - base : C);
+    float* __restrict__ o_x = d.fx[nxb] + base;
+    float* __restrict__ o_ox = d.fox[nxb] + base;
+    float* __restrict__ o_nu = d.fnu[nxb] + base;
+    float* __restrict__ o_w = d.fw[nxb] + base;
+    unsigned long long* __restrict__ o_id = d.pid[nxb] + base;
+    uint32_t* __restrict__ o_key = d.pkey[nxb] + base;
+    for (int r = 0; r < rounds; ++r) {
+      const int li = r * 32 + lane;
+      const bool valid = li < nval;
+      const float xi = sg.x[li], ox = sg.ox[li], nu = sg.nu[li], w = sg.w[li];
+      const unsigned long long id = sg.id[li];
+      const uint32_t key = valid ? sg.key[li] : 0u;
+      // cell = key / G through an FP32 reciprocal, corrected (key < 2^24)
+      uint32_t cell = __float2uint_rz(__uint2float_rn(key) * invG);
+      const int rem = (int)(key - cell * G);
+      cell = rem < 0 ? cell - 1u : (rem >= (int)G ? cell + 1u : cell);
+      // free time: draw 0 of this step's stream of the particle
+      const uint4 blk = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), h0.step, 0u), d.pk);
+      const UPair u = u01f(blk.x, blk.y);
+      // 1/sigma carries nu^{-p}: nu^3 for the nu^-3 law
+      float inup;
+      if (P3) inup = nu * nu * nu;
+      else inup = grey ? 1.0f : pow_fast_f(nu, -spf);
+      const float sig_inv = fmaxf(s_sinv[cell] * inup, inv_capf);
+      const float tc = neg_log_u(u) * inv_rate * sig_inv;
+      const bool collided = tc < dtf;
+      const float t_rem = collided ? tc : dtf;
+      // first flight: the face ahead comes first?
+      const float dist = ox > 0.0f ? dxf - xi : xi;
+      const float tf = fmaxf(dist, 0.0f) * rcp_approx(vf * fabsf(ox));
+      const bool later = valid && tf < t_rem;
+      // listed for the general kernel: the slot and t_rem, negative when the
+      // flight ends in a collision
+      const unsigned lmask = __ballot_sync(full, later);
+      if (later) {
+        const unsigned pos = nl + __popc(lmask & ((1u << lane) - 1u));
+        s_li[warp][pos] = (uint32_t)(base + li);
+        s_lt[warp][pos] = collided ? -t_rem : t_rem;
+      }
+      __syncwarp();
+      nl += __popc(lmask);
+      if (nl >= 32u) flush_list(32u);
+      const bool fin = valid && !later;
+      const float xn = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
+      if (fin) {   // in place: slot i of the other buffer (i < n_surv <= capacity)
+        o_x[li] = xn;
+        o_ox[li] = ox;
+        o_nu[li] = nu;
+        o_w[li] = w;
+        o_id[li] = id;
+        o_key[li] = collided ? kDeadKey : key;
+      }
+      // E_surv and the sort counts of the survivors (the particle stayed in
+      // its cell, so W is unchanged), summed per thread while its bin stays
+      // the same: a lane's successive particles are 32 slots apart in the
+      // bin-sorted input, so nearly always in one bin
+      if (fin && !collided) {
+        const long long wq = to_fixed_f(w, tq_shift, &ctrl->status);
+        if ((int)key != acc_key || acc_n == 32u) {
+          if (acc_n) {
+            atomic_add_fixed(d.Esq + 2 * (long long)acc_key, acc_w);
+            atomicAdd(d.sort_cnt + acc_key, acc_n);
+          }
+          acc_key = (int)key;
+          acc_w = 0;
+          acc_n = 0u;
+        }
+        acc_w += wq;
+        ++acc_n;
+      }
+      cnt.seg += fin;
+      cnt.abs += fin && collided;
+      cnt.surv += fin && !collided;
+      if (d.rec && fin && base + li < d.rec_cap) {
+        P32 q;
+        clear32(q);
+        q.xi = xn; q.ox = ox; q.nu = nu; q.w = w; q.id = id;
+        q.cx = (int)cell; q.g = (int)(key - cell * G);
+        q.fate = collided ? FATE_ABSORBED : FATE_SURVIVED; q.nseg = 1; q.t_tra = t_rem; q.cell0 = (int)cell;
+        record32<1>(d, q, base + li, (int)cell);
+      }
+    }
+    __syncwarp();
+    if (c + kStages < nchunks) {
+      if (lane == 0) rg.issue(&d, h0.cur, c + kStages, h0.n_surv, st);
+      ++issued;
+    }
+    __syncwarp();
+  }
+  if (nl) flush_list(nl);
+  if (acc_n) {
+    atomic_add_fixed(d.Esq + 2 * (long long)acc_key, acc_w);
+    atomicAdd(d.sort_cnt + acc_key, acc_n);
+  }
+  if (lane == 0)
+    for (int kk = k; kk < issued; ++kk) mbar_wait_bounded(&rg.bar[kk % kStages], (unsigned)(kk / kStages) & 1u);
+  flush_counters_block(ctrl, cnt);
+}
+
+// The rest of a step after k_stream32_fast: the listed survivors (their
+// state from the input buffer, their free time from the list, the streaming
+// loop from their first face) and the newborns, one particle per thread.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ Dev d) {
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  const int lane = threadIdx.x & 31;
+  const Tab32 tab = load_tab32<false>(d, s_dyn);
+  __syncthreads();
+  const StepHead h0 = step_head(d);
+  Ctrl* ctrl = d.ctrl;
+  const long long n_slow = (long long)ctrl->n_slow, n_new = h0.n_tot - h0.n_surv;
+  const long long total = n_slow + n_new;
+  const unsigned cur = h0.cur, nxb = cur ^ 1u;
+  const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
+  Counters cnt;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // whole warps to the loop bound, so the warp intrinsics see every lane
+  const long long bound = (total + 31) & ~31ll;
+  for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < bound; jj += stride) {
+    const bool valid = jj < total;
+    P32 q;
+    clear32(q);
+    DrawsF rng;
+    long long i = 0;
+    bool listed = false;
+    if (valid && jj < n_slow) {
+      listed = true;
+      i = (long long)d.slow_i[jj];
+      const float tl = d.slow_t[jj];
+      q.xi = d.fx[cur][i];
+      q.ox = d.fox[cur][i];
+      if (DIM >= 2) { q.eta = d.fy[cur][i]; q.oy = d.foy[cur][i]; }
+      if (DIM == 3) { q.zeta = d.fz[cur][i]; q.oz = d.foz[cur][i]; }
+      q.nu = d.fnu[cur][i];
+      q.w = d.fw[cur][i];
+      q.id = d.pid[cur][i];
+      decode_key32<DIM>(d, d.pkey[cur][i], q);
+      q.collided = tl < 0.0f;
+      q.t_rem = fabsf(tl);
+      rng.init(q.id, h0.step, 1u);   // the free-time draw was draw 0
+    } else if (valid) {
+      i = h0.n_surv + (jj - n_slow);
+      birth32<DIM>(d, q, rng, (uint32_t)(jj - n_slow), h0.step);
+    } else {
+      rng.init(0ull, h0.step, 0u);
+    }
+    q.cell0 = q.gside >= 0 ? q.cx : (q.cz * ny + q.cy) * nx + q.cx;
+    q.ghost = q.gside >= 0;
+    const float inup = (!valid || d.grey) ? 1.0f : pow_fast_f(q.nu, -d.spf);
+    bool more = listed;
+    if (valid && !listed) more = first_flight32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
+    if (more) stream_loop32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
+    const int cell = (q.cz * ny + q.cy) * nx + q.cx;
+    bool stored = false;
+    if (valid) stored = store32<DIM>(d, nxb, q, i, cell);
+    const long long wq = valid ? to_fixed_f(q.w, d.tq_shift, &ctrl->status) : 0ll;
+    warp_run_add_fixed(d.Esq, stored ? cell * G + q.g : -1 - lane, wq, d.sort_cnt);
+    if (valid) {
+      cross_tallies32(d, q, cell, wq);
+      cnt.seg += (unsigned)q.nseg;
+      cnt.abs += q.fate == FATE_ABSORBED;
+      cnt.esc += q.fate == FATE_ESCAPED;
+      cnt.surv += q.fate == FATE_SURVIVED;
+      cnt.rem += q.fate == FATE_REMOVED;
+      record32<DIM>(d, q, i, cell);
+    }
+  }
+  flush_counters_block(ctrl, cnt);
 }
 
 static int g_stream64_occ[4][2][3][3] = {};   // [dim][ens][ppt][block index]
@@ -905,23 +1311,45 @@ static cudaError_t launch_stream64_t(const Dev& d, const Ens& e, const StreamSha
   return cudaGetLastError();
 }
 
+static size_t table32_bytes(const Dev& d) { return (4 * (size_t)stream32_table_floats(d) + 127) & ~(size_t)127; }
+
 template <int DIM, bool ENS, int NT>
 static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
   const int sms = sm_count();
-  const void* fn = (const void*)k_stream32<DIM, ENS, NT>;
-  const int tile = NT * sh.ppt;
-  const size_t dyn = kStages * stream32_stage_bytes(DIM, tile) + (ENS ? 0 : 4 * (size_t)stream32_table_floats(d));
+  const int C = 32 * sh.ppt;
+  const size_t tab = ENS ? 0 : table32_bytes(d);
+  const size_t dyn = tab + (size_t)(NT / 32) * kStages * stream32_stage_bytes(DIM, C);
   const int bi = NT == 128 ? 0 : (NT == 512 ? 2 : 1);
+  // a 1D problem whose particles seldom reach a face in a step (a particle
+  // crosses at most v dt / dx cells) with the power-law opacity held in
+  // shared memory: the survivor kernel, then the general kernel for the
+  // listed survivors and the newborns
+  const bool split = !ENS && DIM == 1 && d.v * d.dt / d.dx < 0.25 && d.sig_law == 0 && d.ncell <= kSmemCells;
+  const bool p3 = !d.grey && d.sig_p == -3.0;
+  const void* fn = !split ? (const void*)k_stream32<DIM, ENS, NT>
+                          : (p3 ? (const void*)k_stream32_fast<NT, true> : (const void*)k_stream32_fast<NT, false>);
   int& occ = g_stream32_occ[DIM][ENS][bi];
   int& occ_dyn = g_stream32_occ_dyn[DIM][ENS][bi];
-  if (!occ || occ_dyn != (int)dyn) {
+  const int key = (int)dyn * 4 + (split ? 1 : 0) + (p3 ? 2 : 0);
+  if (!occ || occ_dyn != key) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT + 32, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, dyn);
     if (occ < 1) occ = 1;
-    occ_dyn = (int)dyn;
+    occ_dyn = key;
   }
   const int per = sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ;
-  k_stream32<DIM, ENS, NT><<<sms * per, NT + 32, dyn, s>>>(d, e, sh.ppt);
+  if (!split) {
+    k_stream32<DIM, ENS, NT><<<sms * per, NT, dyn, s>>>(d, e, sh.ppt);
+    return cudaGetLastError();
+  }
+  if (p3) k_stream32_fast<NT, true><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
+  else k_stream32_fast<NT, false><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
+  cudaError_t r = cudaGetLastError();
+  if (r) return r;
+  if (tab > 48 * 1024) cudaFuncSetAttribute(k_stream32_rest<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
+  // one thread per listed survivor or newborn in flight (their chains are
+  // latency-bound: many warps)
+  k_stream32_rest<DIM><<<sms * 16, 256, tab, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -940,11 +1368,11 @@ static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, cons
   }
   if (d.dim == 2) {
     if (mixed) return launch_stream32_nt<2, ENS>(d, e, sh, s);
-    if (sh.ppt == 2) return launch_stream64_t<2, ENS, 2>(d, e, sh, s);
+    if (sh.ppt >= 2) return launch_stream64_t<2, ENS, 2>(d, e, sh, s);
     return launch_stream64_t<2, ENS, 1>(d, e, sh, s);
   }
   if (mixed) return launch_stream32_nt<1, ENS>(d, e, sh, s);
-  if (sh.ppt == 2) return launch_stream64_t<1, ENS, 2>(d, e, sh, s);
+  if (sh.ppt >= 2) return launch_stream64_t<1, ENS, 2>(d, e, sh, s);
   return launch_stream64_t<1, ENS, 1>(d, e, sh, s);
 }
 
