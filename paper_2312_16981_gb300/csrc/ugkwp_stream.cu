@@ -89,6 +89,46 @@ __device__ __forceinline__ void warp_run_add_fixed(unsigned long long* base, int
   }
 }
 
+// The same with a count per lane (n survivors summed in v by this lane):
+// each run adds its v total to base[key] and its n total to cnt[key].
+__device__ __forceinline__ void warp_run_add_fixed_n(unsigned long long* base, int key, long long v, unsigned n,
+                                                     uint32_t* cnt) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned keyed = __ballot_sync(full, key >= 0);
+  if (!keyed) return;
+  const int first = __ffs(keyed) - 1;
+  const int k0 = __shfl_sync(full, key, first);
+  if (__all_sync(full, key < 0 || (key == k0 && v >= 0))) {
+    const unsigned long long u = key >= 0 ? (unsigned long long)v : 0ull;
+    const unsigned long long s0 = __reduce_add_sync(full, (unsigned)(u & 0x1fffffull));
+    const unsigned long long s1 = __reduce_add_sync(full, (unsigned)((u >> 21) & 0x1fffffull));
+    const unsigned long long s2 = __reduce_add_sync(full, (unsigned)(u >> 42));
+    const unsigned sn = __reduce_add_sync(full, key >= 0 ? n : 0u);
+    if (lane == first) {
+      atomic_add_fixed(base + 2 * (long long)k0, (long long)(s0 + (s1 << 21) + (s2 << 42)));
+      atomicAdd(cnt + k0, sn);
+    }
+    return;
+  }
+  const int prev = __shfl_up_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(full, head);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(full, v, o);
+    const unsigned tn = __shfl_up_sync(full, n, o);
+    if (lane - o >= start) { v += t; n += tn; }
+  }
+  const int nxt = __shfl_down_sync(full, key, 1);
+  const bool tail = lane == 31 || nxt != key;
+  if (tail && key >= 0) {
+    atomic_add_fixed(base + 2 * (long long)key, v);
+    atomicAdd(cnt + key, n);
+  }
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -699,11 +739,17 @@ __device__ __forceinline__ bool store32(const Dev& d, unsigned nxb, const P32& q
 // black-body ghost, the entering set), isotropic direction, frequency by
 // the linear sampler (App. A) and weight.
 template <int DIM>
-__device__ __forceinline__ void birth32(const Dev& d, P32& q, DrawsF& rng, uint32_t j, uint32_t step) {
+__device__ __forceinline__ void birth32(const Dev& d, P32& q, DrawsF& rng, uint32_t j, uint32_t step,
+                                       const uint32_t* off) {
   const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
   q.newborn = true;
-  const int bin = find_bin(d.off, d.nbins, j);
-  const uint32_t kk = j - __ldg(d.off + bin);
+  int lo = 0, hi = d.nbins;   // largest bin with off[bin] <= j
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= j) lo = mid; else hi = mid;
+  }
+  const int bin = lo;
+  const uint32_t kk = j - off[bin];
   q.id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
          (unsigned long long)kk;
   rng.init(q.id, step, 0u);
@@ -982,7 +1028,7 @@ __global__ void __launch_bounds__(NT, (ENS || DIM == 3) ? (NT >= 512 ? 1 : (NT >
         from_stage32<DIM>(d, sgt, li, q);
         rng.init(q.id, step, 0u);
       } else if (valid) {
-        birth32<DIM>(d, q, rng, (uint32_t)(i - n_surv), step);
+        birth32<DIM>(d, q, rng, (uint32_t)(i - n_surv), step, d.off);
       } else {
         rng.init(0ull, step, 0u);
       }
@@ -1212,10 +1258,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
     __syncwarp();
   }
   if (nl) flush_list(nl);
-  if (acc_n) {
-    atomic_add_fixed(d.Esq + 2 * (long long)acc_key, acc_w);
-    atomicAdd(d.sort_cnt + acc_key, acc_n);
-  }
+  // the last runs: the warp's lanes mostly end in the same bin
+  warp_run_add_fixed_n(d.Esq, acc_n ? acc_key : -1 - lane, acc_w, acc_n, d.sort_cnt);
   if (lane == 0)
     for (int kk = k; kk < issued; ++kk) mbar_wait_bounded(&rg.bar[kk % kStages], (unsigned)(kk / kStages) & 1u);
   flush_counters_block(ctrl, cnt);
@@ -1224,15 +1268,26 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
 // The rest of a step after k_stream32_fast: the listed survivors (their
 // state from the input buffer, their free time from the list, the streaming
 // loop from their first face) and the newborns, one particle per thread.
+// mode 0: both; 1: the newborns only (they need nothing from the survivor
+// kernel, so a step graph runs them beside it); 2: the listed survivors
+// only.  The birth offsets are searched in shared memory when they fit.
+constexpr int kSmemBins = 8192;
+
 template <int DIM>
-__global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ Dev d, int mode) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   const int lane = threadIdx.x & 31;
   const Tab32 tab = load_tab32<false>(d, s_dyn);
+  const bool off_sm = mode != 2 && d.nbins + 1 <= kSmemBins;
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dyn + tab32_bytes(tab));
+  if (off_sm)
+    for (int b = threadIdx.x; b <= d.nbins; b += blockDim.x) s_off[b] = __ldg(d.off + b);
   __syncthreads();
+  const uint32_t* off = off_sm ? s_off : d.off;
   const StepHead h0 = step_head(d);
   Ctrl* ctrl = d.ctrl;
-  const long long n_slow = (long long)ctrl->n_slow, n_new = h0.n_tot - h0.n_surv;
+  const long long n_slow = mode == 1 ? 0 : (long long)ctrl->n_slow;
+  const long long n_new = mode == 2 ? 0 : h0.n_tot - h0.n_surv;
   const long long total = n_slow + n_new;
   const unsigned cur = h0.cur, nxb = cur ^ 1u;
   const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
@@ -1264,7 +1319,7 @@ __global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ D
       rng.init(q.id, h0.step, 1u);   // the free-time draw was draw 0
     } else if (valid) {
       i = h0.n_surv + (jj - n_slow);
-      birth32<DIM>(d, q, rng, (uint32_t)(jj - n_slow), h0.step);
+      birth32<DIM>(d, q, rng, (uint32_t)(jj - n_slow), h0.step, off);
     } else {
       rng.init(0ull, h0.step, 0u);
     }
@@ -1313,8 +1368,28 @@ static cudaError_t launch_stream64_t(const Dev& d, const Ens& e, const StreamSha
 
 static size_t table32_bytes(const Dev& d) { return (4 * (size_t)stream32_table_floats(d) + 127) & ~(size_t)127; }
 
+// the survivor kernel's companion: mode 0 listed survivors and newborns, 1
+// newborns only, 2 listed survivors only
+template <int DIM>
+static cudaError_t launch_rest32(const Dev& d, int mode, cudaStream_t s) {
+  const size_t tab = table32_bytes(d);
+  const size_t offb = (mode != 2 && d.nbins + 1 <= kSmemBins) ? 4 * (size_t)(d.nbins + 1) : 0;
+  const size_t dyn = tab + offb;
+  if (dyn > 48 * 1024) cudaFuncSetAttribute(k_stream32_rest<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  // enough threads to hold every listed survivor and newborn of a typical
+  // step at once (their chains are latency-bound)
+  k_stream32_rest<DIM><<<sm_count() * 4, 256, dyn, s>>>(d, mode);
+  return cudaGetLastError();
+}
+
+// 1D problems that take the survivor kernel (see launch_stream32_t)
+static bool split32(const Dev& d) {
+  return d.dim == 1 && d.v * d.dt / d.dx < 0.25 && d.sig_law == 0 && d.ncell <= kSmemCells;
+}
+
 template <int DIM, bool ENS, int NT>
-static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
+static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s,
+                                     bool newborns_elsewhere) {
   const int sms = sm_count();
   const int C = 32 * sh.ppt;
   const size_t tab = ENS ? 0 : table32_bytes(d);
@@ -1324,7 +1399,7 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
   // crosses at most v dt / dx cells) with the power-law opacity held in
   // shared memory: the survivor kernel, then the general kernel for the
   // listed survivors and the newborns
-  const bool split = !ENS && DIM == 1 && d.v * d.dt / d.dx < 0.25 && d.sig_law == 0 && d.ncell <= kSmemCells;
+  const bool split = !ENS && DIM == 1 && split32(d);
   const bool p3 = !d.grey && d.sig_p == -3.0;
   const void* fn = !split ? (const void*)k_stream32<DIM, ENS, NT>
                           : (p3 ? (const void*)k_stream32_fast<NT, true> : (const void*)k_stream32_fast<NT, false>);
@@ -1346,41 +1421,45 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
   else k_stream32_fast<NT, false><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
   cudaError_t r = cudaGetLastError();
   if (r) return r;
-  if (tab > 48 * 1024) cudaFuncSetAttribute(k_stream32_rest<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
-  // one thread per listed survivor or newborn in flight (their chains are
-  // latency-bound: many warps)
-  k_stream32_rest<DIM><<<sms * 16, 256, tab, s>>>(d);
-  return cudaGetLastError();
+  return launch_rest32<DIM>(d, newborns_elsewhere ? 2 : 0, s);
 }
 
 template <int DIM, bool ENS>
-static cudaError_t launch_stream32_nt(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
-  if (sh.block == 128) return launch_stream32_t<DIM, ENS, 128>(d, e, sh, s);
-  if (sh.block == 512) return launch_stream32_t<DIM, ENS, 512>(d, e, sh, s);
-  return launch_stream32_t<DIM, ENS, 256>(d, e, sh, s);
+static cudaError_t launch_stream32_nt(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s,
+                                      bool newborns_elsewhere) {
+  if (sh.block == 128) return launch_stream32_t<DIM, ENS, 128>(d, e, sh, s, newborns_elsewhere);
+  if (sh.block == 512) return launch_stream32_t<DIM, ENS, 512>(d, e, sh, s, newborns_elsewhere);
+  return launch_stream32_t<DIM, ENS, 256>(d, e, sh, s, newborns_elsewhere);
 }
 
 template <bool ENS>
-static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s) {
+static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s,
+                                     bool newborns_elsewhere) {
   if (d.dim == 3) {   // single problems only (ensembles are 1D/2D)
     if (ENS) return cudaErrorNotSupported;
-    return mixed ? launch_stream32_nt<3, false>(d, e, sh, s) : launch_stream64_t<3, false, 1>(d, e, sh, s);
+    return mixed ? launch_stream32_nt<3, false>(d, e, sh, s, false) : launch_stream64_t<3, false, 1>(d, e, sh, s);
   }
   if (d.dim == 2) {
-    if (mixed) return launch_stream32_nt<2, ENS>(d, e, sh, s);
+    if (mixed) return launch_stream32_nt<2, ENS>(d, e, sh, s, false);
     if (sh.ppt >= 2) return launch_stream64_t<2, ENS, 2>(d, e, sh, s);
     return launch_stream64_t<2, ENS, 1>(d, e, sh, s);
   }
-  if (mixed) return launch_stream32_nt<1, ENS>(d, e, sh, s);
+  if (mixed) return launch_stream32_nt<1, ENS>(d, e, sh, s, newborns_elsewhere);
   if (sh.ppt >= 2) return launch_stream64_t<1, ENS, 2>(d, e, sh, s);
   return launch_stream64_t<1, ENS, 1>(d, e, sh, s);
 }
 
-cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s) {
+bool stream_newborns_apart(const Dev& d, const Ens* e) {
+  return !(e && e->M > 1) && d.precision == 1 && split32(d);
+}
+
+cudaError_t launch_stream_newborns(const Dev& d, cudaStream_t s) { return launch_rest32<1>(d, 1, s); }
+
+cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s, bool newborns_elsewhere) {
   const int mixed = d.precision == 1;
-  if (e && e->M > 1) return launch_stream_dim<true>(d, *e, mixed, sh, s);
+  if (e && e->M > 1) return launch_stream_dim<true>(d, *e, mixed, sh, s, false);
   const Ens none{};
-  return launch_stream_dim<false>(d, none, mixed, sh, s);
+  return launch_stream_dim<false>(d, none, mixed, sh, s, newborns_elsewhere);
 }
 
 }  // namespace ugkwp
