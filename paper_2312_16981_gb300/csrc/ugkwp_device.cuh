@@ -518,8 +518,27 @@ __device__ __forceinline__ double pow_fast(double b, double e) {
   return pow(b, e);
 }
 
+// min(s, cap) for s >= 0 (or NaN: the cap), compared as bit patterns (the
+// order of non-negative doubles) on the integer pipes: an FP64 compare costs
+// an FP64 instruction, the scarce unit on this chip
 __device__ __forceinline__ double cap_sigma(const Dev& d, double s) {
-  return (d.sig_cap > 0.0 && !(s <= d.sig_cap)) ? d.sig_cap : s;
+  const long long cap_bits = d.sig_cap > 0.0 ? __double_as_longlong(d.sig_cap) : 0x7fffffffffffffffll;
+  return __double_as_longlong(s) > cap_bits ? d.sig_cap : s;
+}
+
+// 1/x for finite x > 0 away from the under- and overflow limits, to about an
+// ulp: the hardware reciprocal approximation (rcp.approx.ftz.f64) and two
+// Newton steps e = 1 - x r, r += r e, each doubling the correct bits.  Four
+// FP64 FMAs where a correctly rounded division takes about twice as many
+// FP64 instructions; the source iteration's fixed point does not need the
+// last bit.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 // sigma0*T^q for cell c at temperature T
@@ -886,6 +905,25 @@ __device__ __forceinline__ double sampler_khat(double nlo, double nhi, double T)
   const double kmax = 2.0 / dnu;
   k = fmin(fmax(k, -kmax), kmax);
   return k == k ? k : 0.0;
+}
+
+// The same slope in FP32 for the mixed-precision build, whose sampler runs
+// in FP32 (the exponent is clamped where FP32 e^x overflows; the clamp on
+// |khat| saturates first there).
+__device__ __forceinline__ float planck_ratio_f(float nu, float nmid, float T) {
+  const float r = __fdividef(nu, nmid);
+  float ex = __fdividef(nmid - nu, T);
+  if (ex > 80.0f) ex = 80.0f;
+  return r * r * r * expf(ex) * __fdividef(expm1f(-nmid / T), expm1f(-nu / T));
+}
+
+__device__ __forceinline__ float sampler_khat_f(float nlo, float nhi, float T) {
+  if (!(T > 0.0f)) return 0.0f;
+  const float dnu = nhi - nlo, nmid = 0.5f * (nlo + nhi);
+  float k = (planck_ratio_f(nhi, nmid, T) - planck_ratio_f(nlo, nmid, T)) / dnu;
+  const float kmax = 2.0f / dnu;
+  k = fminf(fmaxf(k, -kmax), kmax);
+  return k == k ? k : 0.0f;
 }
 
 __device__ __forceinline__ double sample_nu(double nlo, double nhi, double khat, double eta) {

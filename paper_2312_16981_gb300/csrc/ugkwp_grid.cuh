@@ -139,10 +139,10 @@ __device__ __forceinline__ void cell_planck(const Dev& d, int c, double T, doubl
 }
 
 // tau = 1/(rate sigma) and q = 1/(tau + dt) of the source iteration with one
-// division: A = rate sigma, D = 1 + dt A, P = 1/(A D), tau = D P, q = A^2 P.
+// reciprocal: A = rate sigma, D = 1 + dt A, P = 1/(A D), tau = D P, q = A^2 P.
 __device__ __forceinline__ void tau_and_q(const Dev& d, double sig, double* tau, double* q) {
   const double A = d.rate_f * sig, D = fma(d.dt, A, 1.0);
-  const double P = 1.0 / (A * D);
+  const double P = rcp_nr(A * D);
   *tau = D * P;
   *q = A * A * P;
 }

@@ -194,11 +194,15 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     d.N[b] = N;
     d.omega[b] = w;
     d.e_eff[b] = ee;
-    const double kh = (N && !d.grey) ? sampler_khat(d.nu_edges[g], d.nu_edges[g + 1], Tb) : 0.0;
-    d.khat[b] = kh;
+    // the sampler slope: FP64 for the FP64 particle kernel; the FP32 kernel
+    // samples in FP32 and takes it from FP32 arithmetic (the FP64 exp and
+    // expm1 cost tens of FP64 instructions each on this chip)
     if (d.omega_f) {
+      d.khat[b] = 0.0;
       d.omega_f[b] = (float)w;
-      d.khat_f[b] = (float)kh;
+      d.khat_f[b] = (N && !d.grey) ? sampler_khat_f(d.nu_edges_f[g], d.nu_edges_f[g + 1], (float)Tb) : 0.0f;
+    } else {
+      d.khat[b] = (N && !d.grey) ? sampler_khat(d.nu_edges[g], d.nu_edges[g + 1], Tb) : 0.0;
     }
   }
   }
@@ -494,13 +498,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
 // Equilibrium flux on a face between lower-index side (l) and upper side (u):
 // F = C2 (c/eps)^2/3 (Phi_u - Phi_l)/h, C2 = tau_f f2(dt/tau_f), with the
 // harmonic-mean opacity of App. B, i.e. tau_f = (tau_l + tau_u)/2: x =
-// dt/tau_f = 2 dt/(tau_l + tau_u) takes one division and 1/x a
+// dt/tau_f = 2 dt/(tau_l + tau_u) takes one reciprocal and 1/x a
 // multiplication; tau_f f2(x) = dt f2(x)/x.  Both adjacent cells evaluate the
 // same expression (the tau sum commutes), so the two copies agree bitwise.
 __device__ __forceinline__ double feq_face(const Dev& d, double tl, double tu, double pl, double pu,
                                            double inv_h) {
   const double st = tl + tu;
-  const double x = 2.0 * d.dt / st;
+  const double x = 2.0 * d.dt * rcp_nr(st);
   return d.dt * coef_g2_fast(x, st * d.inv_2dt) * (d.v * d.v / 3.0) * (pu - pl) * inv_h;
 }
 
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const double ck = heat_capacity(d, c, Tc);
         Tnew = (mat_energy(d, c, Tn) - mat_energy(d, c, Tc) + ck * Tc + num) / (ck + den);
       } else {
-        Tnew = (cv * Tn + num) / (cv + den);
+        Tnew = (cv * Tn + num) * rcp_nr(cv + den);
       }
       if (!(Tnew > 1e-30)) Tnew = (Tnew == Tnew) ? 1e-30 : Tnew;
       double dmax = 0.0, rsum = 0.0;
@@ -778,7 +782,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       dmax = warp_max(dmax);
       rsum = warp_sum(rsum);
-      const double eR = rsum > 0.0 ? dmax / rsum : 0.0;
+      const double eR = rsum > 0.0 ? dmax * rcp_nr(rsum) : 0.0;
       // 1/T^{k+1} (and sigma0 T^q for q = -1/2) from one rsqrt where the
       // opacity law has T^{-1/2}, else a division
       double invTn, sTn;
@@ -787,7 +791,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         invTn = rs * rs;
         sTn = d.sigma0[c] * rs;
       } else {
-        invTn = 1.0 / Tnew;
+        invTn = rcp_nr(Tnew);
         sTn = sigma_T(d, c, Tnew);
       }
       const double eT = fabs(Tnew - Tc) * invTn;
