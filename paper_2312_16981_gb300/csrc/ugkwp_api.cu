@@ -743,6 +743,8 @@ int ugkwp_set_state_member(ugkwp_handle* h, int member, const double* T, const d
   if (!h || !T || !rho || !rho_h) return fail(h, UGKWP_ERR_ARG, "NULL argument");
   if (member < 0 || member >= h->M) return fail(h, UGKWP_ERR_ARG, "member index out of range");
   if (n < 0 || n > h->members[member].capacity) return fail(h, UGKWP_ERR_CAPACITY, "n exceeds particle capacity");
+  if (step < 0 || (unsigned long long)step > ugkwp::kMaxStep)
+    return fail(h, UGKWP_ERR_ARG, "step must be in 0..2^20-1 (a newborn's identity holds its birth step in 20 bits)");
   if (n > 0 && !parts) return fail(h, UGKWP_ERR_ARG, "particles missing");
   cudaStream_t s = (cudaStream_t)stream;
   const Dev& d = h->members[member];

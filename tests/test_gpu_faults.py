@@ -87,3 +87,24 @@ def test_tally_log_is_json_lines(B, tmp_path):
     for r in rows:
         assert r["status_bits"] == 0 and r["run"] == "log-test"
         assert abs(r["ledger_residual"]) <= 1e-12 * (r["E_rad1"] + r["E_mat1"])
+
+
+def test_identity_space_limit_is_flagged(B):
+    # a newborn's identity holds its birth step in 20 bits: step 2^20 - 1 still
+    # samples; the next step samples nothing and sets the status bit (the
+    # oracle does the same); a state may not be set past the limit
+    p = I.small_multigroup(nx=12, G=4, omega_ref=1e-6)
+    op = O.OracleProblem(p)
+    st = O.initial_state(op)
+    st, _, _, _ = O.step(op, st)
+    sim = B.Simulation(p)
+    last = (1 << 20) - 1
+    sim.set_state(st.T, st.rho, st.rho_h, st.particles.view(), step=last)
+    sim.step(1)
+    t = sim.tallies()
+    assert t["n_born"] > 100 and not (t["status_bits"] & B.ST_IDSPACE)
+    sim.step(1)
+    t = sim.tallies()
+    assert t["n_born"] == 0 and (t["status_bits"] & B.ST_IDSPACE)
+    with pytest.raises(Exception):
+        sim.set_state(st.T, st.rho, st.rho_h, st.particles.view(), step=1 << 20)
