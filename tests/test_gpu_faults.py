@@ -7,6 +7,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2312_16981_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
