@@ -495,6 +495,23 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
   return s_timeout == 0;
 }
 
+// Stopping rule of the source iteration after an iterate whose largest
+// relative changes of T and rho are (eT, eR), the previous iterate's (pT,
+// pR): the changes are within tol (reading of the unstated tolerances), or
+// the iteration contracts fast (ratio r = e/p <= 1/100 in both) and the
+// geometric tail of the changes still to come, e r/(1 - r), is within tol:
+// the iterate is then within tol of the fixed point, as the plain rule
+// allows, and the iterate that would only confirm it is saved (a slab
+// contracts by about 1e-3 an iterate).  Slowly contracting iterations keep
+// the plain rule.
+__device__ __forceinline__ bool si_converged(double eT, double eR, double pT, double pR, double tol, bool prev) {
+  if (eT <= tol && eR <= tol) return true;
+  if (!prev || !(pT > 0.0) || !(pR > 0.0)) return false;
+  const double rT = eT / pT, rR = eR / pR;
+  if (!(rT <= 0.01) || !(rR <= 0.01)) return false;
+  return eT * rT <= tol * (1.0 - rT) && eR * rR <= tol * (1.0 - rR);
+}
+
 // Equilibrium flux on a face between lower-index side (l) and upper side (u):
 // F = C2 (c/eps)^2/3 (Phi_u - Phi_l)/h, C2 = tau_f f2(dt/tau_f), with the
 // harmonic-mean opacity of App. B, i.e. tau_f = (tau_l + tau_u)/2: x =
@@ -847,7 +864,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       Ctrl* ctrl = d0.ctrl;
       const double eT = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][0]));
       const double eR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][1]));
-      if (eT <= d0.si_tol && eR <= d0.si_tol) { s_conv[0] = it + 1; all_done = 1; ++it; break; }
+      const double pT = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[(it + 2) % 3][0]));
+      const double pR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[(it + 2) % 3][1]));
+      if (si_converged(eT, eR, pT, pR, d0.si_tol, it > 0)) { s_conv[0] = it + 1; all_done = 1; ++it; break; }
     } else {
       if (threadIdx.x == 0) s_any = 0;
       __syncthreads();
@@ -857,8 +876,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         Ctrl* cc = e.devs[k].ctrl;
         const double eT = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][0]));
         const double eR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][1]));
-        const double tol = e.devs[k].si_tol;
-        if (eT <= tol && eR <= tol) s_conv[k] = it + 1; else running = 1;
+        const double pT = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[(it + 2) % 3][0]));
+        const double pR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[(it + 2) % 3][1]));
+        if (si_converged(eT, eR, pT, pR, e.devs[k].si_tol, it > 0)) s_conv[k] = it + 1; else running = 1;
       }
       if (running) s_any = 1;
       __syncthreads();
