@@ -178,7 +178,7 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.qk = cv.take<double>(ncg);
   d.phik[0] = cv.take<double>(ncg);
   d.phik[1] = cv.take<double>(ncg);
-  d.dphik = cv.take<double>(ncg);
+  d.dphik = cv.take<float>(ncg);
   d.ctrl = cv.take<Ctrl>(1);
   *src_T_tmp = d.R;   // scratch during init only
   const bool mixed = p->precision == UGKWP_MIXED;
@@ -260,11 +260,19 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.eps = p->eps;
   d.dt = p->dt;
   d.inv_2dt = 0.5 / p->dt;
+  d.two_dt = 2.0 * p->dt;
   d.v = p->c / p->eps;
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;
   d.inv_dz = 1.0 / d.dz;
   d.inv_c = 1.0 / p->c;
+  {
+    const double inv_h[3] = {d.inv_dx, d.inv_dy, d.inv_dz};
+    for (int a = 0; a < 3; ++a) {
+      d.feq_k[a] = p->dt * (d.v * d.v / 3.0) * inv_h[a];
+      d.dt_h[a] = p->dt * inv_h[a];
+    }
+  }
   d.inv_vol = 1.0 / d.vol;
   d.rate_f = p->c / (p->eps * p->eps);
   d.omega_ref = p->omega_ref;

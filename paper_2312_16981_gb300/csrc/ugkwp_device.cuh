@@ -269,6 +269,9 @@ struct Dev {
   unsigned long long* Esq;   // [ncell*G][2] E_surv in fixed point (accumulated)
   double inv_dx, inv_dy, inv_dz, inv_c, inv_vol;
   double inv_2dt;             // 1/(2 dt)
+  double two_dt;              // 2 dt
+  double feq_k[3];            // dt (v^2/3)/h per axis: F^eq = C2/dt feq_k (Phi_u - Phi_l)
+  double dt_h[3];             // dt/h per axis
   double tq, tq_inv;         // fixed-point quantum 2^-tq_shift (about omega_ref 2^-48) and its inverse
   int tq_shift;
   // FP32 copies of scalars (mixed-precision particle kernel)
@@ -286,7 +289,7 @@ struct Dev {
   double* tauk[2];  // [ncell*G] relaxation time 1/(rate_f sigma_g(T^k)) of the iterate
   double* qk;       // [ncell*G] 1/(tau + dt) of the iterate (read by the cell's own warp)
   double* phik[2];  // [ncell*G]
-  double* dphik;    // [ncell*G]
+  float* dphik;     // [ncell*G] dPhi_g/dT of the iterate (FP32: it sets only the contraction rate)
   // particles: two structure-of-arrays buffers, selected by ctrl->cur
   double* px[2];
   double* py[2];
@@ -527,18 +530,17 @@ __device__ __forceinline__ double cap_sigma(const Dev& d, double s) {
 }
 
 // 1/x for finite x > 0 away from the under- and overflow limits, to about an
-// ulp: the hardware reciprocal approximation (rcp.approx.ftz.f64) and two
-// Newton steps e = 1 - x r, r += r e, each doubling the correct bits.  Four
-// FP64 FMAs where a correctly rounded division takes about twice as many
-// FP64 instructions; the source iteration's fixed point does not need the
-// last bit.
+// ulp: the hardware reciprocal approximation (rcp.approx.ftz.f64, relative
+// error below 2^-19.9 as measured on sm_103a) and one third-order step:
+// with e = 1 - x r, r (1 + e + e^2) = (1 - e^3)/x, an error below 2^-59.
+// Three FP64 FMAs where a correctly rounded division takes about three times
+// as many FP64 instructions; the source iteration's fixed point does not
+// need the last bit.
 __device__ __forceinline__ double rcp_nr(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 // sigma0*T^q for cell c at temperature T

@@ -6,6 +6,7 @@
 #include "ugkwp_device.cuh"
 #include "ugkwp_grid.cuh"
 #include "ugkwp_launch.h"
+#include "ugkwp_si.cuh"
 
 namespace ugkwp {
 
@@ -34,6 +35,8 @@ __global__ void k_init_pow(Dev d) {
   }
   for (int g = tid; g <= d.G; g += stride)
     if (d.nu_edges_f) d.nu_edges_f[g] = (float)d.nu_edges[g];
+  // FP32 copy of the g4 column of the Planck table (the same on every call)
+  for (int i = tid; i < (kPlanckRows + 1) * (kPlanckDeg + 1); i += stride) kG4TabF[i] = (float)kPlanckTab[2 * i + 1];
   // foam opacity nu factors at the Simpson points (sig_law 2)
   if (d.olson_nu)
     for (int g = tid; g < d.G; g += stride) {
@@ -498,31 +501,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
 // Stopping rule of the source iteration after an iterate whose largest
 // relative changes of T and rho are (eT, eR), the previous iterate's (pT,
 // pR): the changes are within tol (reading of the unstated tolerances), or
-// the iteration contracts fast (ratio r = e/p <= 1/100 in both) and the
+// the iteration contracts fast (ratio r = e/p <= 1/10 in both) and the
 // geometric tail of the changes still to come, e r/(1 - r), is within tol:
 // the iterate is then within tol of the fixed point, as the plain rule
 // allows, and the iterate that would only confirm it is saved (a slab
-// contracts by about 1e-3 an iterate).  Slowly contracting iterations keep
-// the plain rule.
+// contracts by about 1e-3 an iterate, the 2D checkerboard by about 3e-2).
+// Slowly contracting iterations keep the plain rule.
 __device__ __forceinline__ bool si_converged(double eT, double eR, double pT, double pR, double tol, bool prev) {
   if (eT <= tol && eR <= tol) return true;
   if (!prev || !(pT > 0.0) || !(pR > 0.0)) return false;
   const double rT = eT / pT, rR = eR / pR;
-  if (!(rT <= 0.01) || !(rR <= 0.01)) return false;
+  if (!(rT <= 0.1) || !(rR <= 0.1)) return false;
   return eT * rT <= tol * (1.0 - rT) && eR * rR <= tol * (1.0 - rR);
-}
-
-// Equilibrium flux on a face between lower-index side (l) and upper side (u):
-// F = C2 (c/eps)^2/3 (Phi_u - Phi_l)/h, C2 = tau_f f2(dt/tau_f), with the
-// harmonic-mean opacity of App. B, i.e. tau_f = (tau_l + tau_u)/2: x =
-// dt/tau_f = 2 dt/(tau_l + tau_u) takes one reciprocal and 1/x a
-// multiplication; tau_f f2(x) = dt f2(x)/x.  Both adjacent cells evaluate the
-// same expression (the tau sum commutes), so the two copies agree bitwise.
-__device__ __forceinline__ double feq_face(const Dev& d, double tl, double tu, double pl, double pu,
-                                           double inv_h) {
-  const double st = tl + tu;
-  const double x = 2.0 * d.dt * rcp_nr(st);
-  return d.dt * coef_g2_fast(x, st * d.inv_2dt) * (d.v * d.v / 3.0) * (pu - pl) * inv_h;
 }
 
 // Neighbour values across one face of the cell at (ix, iy, iz): relaxation
@@ -588,7 +578,7 @@ __device__ __forceinline__ double face_feq(const Dev& d, int f, int g, int cur) 
       tu = tl;
     }
   }
-  return feq_face(d, tl, tu, pl, pu, inv_h_of(d, r.axis));
+  return feq_face_si(d, tl, tu, pl, pu, r.axis);
 }
 
 // Source iteration (App. B, Algorithm 2) in 1D, 2D and 3D, one warp per cell and
@@ -617,7 +607,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   unsigned int* bar_count = ENS ? e.bar : &d0.ctrl->bar_count;
   Ctrl* st_ctrl = ENS ? e.devs[0].ctrl : d0.ctrl;
   const unsigned int spin_limit = st_ctrl->bar_timeout_spins;
-  __shared__ double s_red[8][4];
+  __shared__ float s_err[8][2];
   __shared__ int s_conv[ENS ? kMaxEnsemble : 1];   // iterate count at convergence, 0 = still running
   __shared__ int s_any;
   unsigned int bar = 0;
@@ -669,8 +659,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       const double T = d.T[c];
       if (lane == 0) e_mat0 += V * mat_energy(d, c, T);
-      double sg[NC], ph[NC], dp[NC];
-      cell_planck<NC>(d, c, T, sg, ph, dp);
+      double sg[NC], ph[NC];
+      float dp[NC];
+      si_planck<NC>(d, T, 1.0 / T, sigma_T(d, c, T), sg, ph, dp);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
@@ -708,7 +699,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   const bool face_pass = !ENS && d0.dim >= 2;
   for (; it < max_it; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
-    double werrT = 0.0, werrR = 0.0;
+    float werrT = 0.0f, werrR = 0.0f;
     if (face_pass) {
       const int G = d0.G;
       for (long long gf = gw; gf < d0.nface; gf += nw) {
@@ -741,67 +732,80 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const int i = c * G + g;
         const double tc = __ldcg(d.tauk[cur] + i);
         phc[j] = __ldcg(d.phik[cur] + i);
-        dpc[j] = __ldcg(d.dphik + i);
+        dpc[j] = f2d_bits(__ldcg(d.dphik + i));
         double q = d.R[i];
         if (face_pass) {
           for (int axis = 0; axis < d.dim; ++axis) {
-            const double inv_h = inv_h_of(d, axis);
             const double Fin = __ldcg(d.Feq + face_index_xyz(d, ix, iy, iz, axis, -1) * G + g);
             const double Fout = __ldcg(d.Feq + face_index_xyz(d, ix, iy, iz, axis, +1) * G + g);
-            q += (dt * inv_h) * (Fin - Fout);
+            q = fma(d.dt_h[axis], Fin - Fout, q);
           }
         }
         for (int axis = 0; axis < (face_pass ? 0 : d.dim); ++axis) {
-          const double inv_h = inv_h_of(d, axis);
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
             double tn, pn;
             int nc;
             double F = 0.0;
             if (neighbour(d, ix, iy, iz, axis, dir, g, cur, tc, &tn, &pn, &nc)) {
-              F = dir < 0 ? feq_face(d, tn, tc, pn, phc[j], inv_h) : feq_face(d, tc, tn, phc[j], pn, inv_h);
+              F = dir < 0 ? feq_face_si(d, tn, tc, pn, phc[j], axis) : feq_face_si(d, tc, tn, phc[j], pn, axis);
             }
             const bool owner = dir > 0 ? true : (nc < 0);   // upper face, or a boundary face
             if (owner) d.Feq[face_index_xyz(d, ix, iy, iz, axis, dir) * G + g] = F;
             if (dir < 0) Fin = F; else Fout = F;
           }
-          q += (dt * inv_h) * (Fin - Fout);
+          q = fma(d.dt_h[axis], Fin - Fout, q);
         }
         Q[j] = q;
         const double qi = __ldcg(d.qk + i);   // 1/(tau + dt), stored with tau
         r1[j] = tc * qi;
         ar[j] = dt * qi;
         const double ap = ar[j] * d.inv_c;
-        num += ap * (q - phc[j] + dpc[j] * Tc);
-        den += ap * dpc[j];
+        num = fma(ap, fma(dpc[j], Tc, q - phc[j]), num);
+        den = fma(ap, dpc[j], den);
       }
-      num = warp_sum(num);
-      den = warp_sum(den);
+      warp_sum2(num, den);
       // a T-dependent heat capacity: e(T^{k+1}) ~ e(T^k) + C_v(T^k) (T^{k+1} - T^k)
       double Tnew;
       if (d.cv_law == 1) {
         const double ck = heat_capacity(d, c, Tc);
         Tnew = (mat_energy(d, c, Tn) - mat_energy(d, c, Tc) + ck * Tc + num) / (ck + den);
       } else {
-        Tnew = (cv * Tn + num) * rcp_nr(cv + den);
+        Tnew = fma(cv, Tn, num) * rcp_nr(cv + den);
       }
-      if (!(Tnew > 1e-30)) Tnew = (Tnew == Tnew) ? 1e-30 : Tnew;
-      double dmax = 0.0, rsum = 0.0;
+      {
+        // T >= 1e-30 (NaN kept), compared as bit patterns
+        const long long tb = __double_as_longlong(Tnew);
+        const bool nan = (tb & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
+        if (!nan && tb < kBits1em30) Tnew = 1e-30;
+      }
+      const double dT = Tnew - Tc;
+      double r[NC], dr[NC];
+      int ex = 0;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
+        r[j] = 0.0; dr[j] = 0.0;
         if (g >= G) continue;
         const int i = c * G + g;
-        const double r = fma(Q[j], r1[j], ar[j] * fma(dpc[j], Tnew - Tc, phc[j]));
-        dmax = fmax(dmax, fabs(r - __ldcg(d.rho + i)));
-        rsum += fabs(r);
-        __stcg(d.rho + i, r);
+        r[j] = fma(Q[j], r1[j], ar[j] * fma(dpc[j], dT, phc[j]));
+        dr[j] = r[j] - __ldcg(d.rho + i);
+        __stcg(d.rho + i, r[j]);
+        ex = max(ex, biased_exp(r[j]));
       }
-      dmax = warp_max(dmax);
-      rsum = warp_sum(rsum);
-      const double eR = rsum > 0.0 ? dmax * rcp_nr(rsum) : 0.0;
+      // max_g |d rho_g| / sum_g |rho_g| in FP32, both scaled by the cell's largest |rho_g|
+      const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)ex);
+      float dmax = 0.0f, rsum = 0.0f;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        dmax = fmaxf(dmax, scaled_mag(dr[j], E));
+        rsum += scaled_mag(r[j], E);
+      }
+      dmax = warp_max_nonneg_f(dmax);
+      rsum = warp_sum_f(rsum);
+      float eR = rsum > 0.0f ? dmax / rsum : 0.0f;
       // 1/T^{k+1} (and sigma0 T^q for q = -1/2) from one rsqrt where the
-      // opacity law has T^{-1/2}, else a division
+      // opacity law has T^{-1/2}, else a reciprocal
       double invTn, sTn;
       if (d.sig_q == -0.5) {
         const double rs = rsqrt(Tnew);
@@ -811,20 +815,25 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         invTn = rcp_nr(Tnew);
         sTn = sigma_T(d, c, Tnew);
       }
-      const double eT = fabs(Tnew - Tc) * invTn;
+      const int ET = biased_exp(Tnew);
+      const float fT = scaled_mag(Tnew, ET);
+      float eT = fT < INFINITY ? scaled_mag(dT, ET) / fT : INFINITY;
+      if (!(eT <= 3.0e38f)) eT = INFINITY;
+      if (!(eR <= 3.0e38f)) eR = INFINITY;
       if (ENS) {
         // members differ between warps: each warp reports to its own member
         if (lane == 0) {
-          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][0], (eT == eT) ? eT : 1e300);
-          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][1], (eR == eR) ? eR : 1e300);
+          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][0], f2d_bits(eT));
+          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][1], f2d_bits(eR));
         }
       } else {
-        werrT = fmax(werrT, (eT == eT) ? eT : 1e300);
-        werrR = fmax(werrR, (eR == eR) ? eR : 1e300);
+        werrT = fmaxf(werrT, eT);
+        werrR = fmaxf(werrR, eR);
       }
       if (lane == 0) __stcg(d.Tk[nxt] + c, Tnew);
-      double sg[NC], ph[NC], dp[NC];
-      cell_planck<NC>(d, c, Tnew, sg, ph, dp, invTn, sTn);
+      double sg[NC], ph[NC];
+      float dp[NC];
+      si_planck<NC>(d, Tnew, invTn, sTn, sg, ph, dp);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int g = lane + 32 * j;
@@ -840,13 +849,13 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     }
     if (!ENS) {
       Ctrl* ctrl = d0.ctrl;
-      if (lane == 0) { s_red[wib][0] = werrT; s_red[wib][1] = werrR; }
+      if (lane == 0) { s_err[wib][0] = werrT; s_err[wib][1] = werrR; }
       __syncthreads();
       if (threadIdx.x == 0) {
-        double mT = 0.0, mR = 0.0;
-        for (int w = 0; w < nwb; ++w) { mT = fmax(mT, s_red[w][0]); mR = fmax(mR, s_red[w][1]); }
-        atomic_max_nonneg(&ctrl->err_slot[it % 3][0], mT);
-        atomic_max_nonneg(&ctrl->err_slot[it % 3][1], mR);
+        float mT = 0.0f, mR = 0.0f;
+        for (int w = 0; w < nwb; ++w) { mT = fmaxf(mT, s_err[w][0]); mR = fmaxf(mR, s_err[w][1]); }
+        atomic_max_nonneg(&ctrl->err_slot[it % 3][0], f2d_bits(mT));
+        atomic_max_nonneg(&ctrl->err_slot[it % 3][1], f2d_bits(mR));
         if (blockIdx.x == 0) {
           ctrl->err_slot[(it + 1) % 3][0] = 0ull;
           ctrl->err_slot[(it + 1) % 3][1] = 0ull;

@@ -1,0 +1,216 @@
+// Arithmetic of the source iteration (App. B, Algorithm 2) arranged for the
+// FP64 pipe of sm_103a, the scarce unit of that kernel: a warp instruction of
+// FP64 add, multiply, FMA, compare, min/max or f64->f32 conversion holds the
+// pipe for 64 cycles whatever the number of active lanes.
+//
+// What fixes the iteration's fixed point stays FP64, in the same operations
+// as before: sigma_g, Phi_g (the Planck group integrals), the face fluxes
+// F^eq, Q, the T and rho updates.  What does not is moved off the pipe:
+//   - dPhi_g/dT, the slope of the linearised emission, only sets the
+//     contraction rate (at T^{k+1} = T^k the slope cancels from both
+//     updates), so it is evaluated and stored in FP32;
+//   - the convergence measures |dT|/T and max_g |d rho_g| / sum_g |rho_g|
+//     are formed in FP32 from the doubles' bit fields (relative error below
+//     2^-20 in a measure compared with si_tol);
+//   - table rows, range tests and the clamp of T are integer operations on
+//     bit patterns.
+#pragma once
+
+#include "ugkwp_device.cuh"
+#include "ugkwp_grid.cuh"
+
+namespace ugkwp {
+
+// bit patterns of the constants the range tests compare with (positive doubles
+// order as their bit patterns)
+constexpr long long kBits40 = 0x4044000000000000ll;     // 40.0
+constexpr long long kBits740 = 0x4087200000000000ll;    // 740.0
+constexpr long long kBits1em30 = 0x39b4484bfeebc2a0ll;  // 1e-30
+
+// biased exponent field of a double
+__device__ __forceinline__ int biased_exp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// x as a float, mantissa truncated to 23 bits; below the float range +-0,
+// above it (and inf, NaN) +-inf.  Integer operations only.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// a float as a double, exactly (subnormal floats as zero).  Integer operations only.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu, sign = b & 0x80000000u, m = b & 0x7fffffu;
+  if (ex == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned e64 = ex == 0xffu ? 0x7ffu : ex + 896u;   // 896 = 1023 - 127
+  return __hiloint2double((int)(sign | (e64 << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// |x| 2^(1023 - E) as a float, for a scale E (a biased exponent) at or above
+// that of most operands: mantissa truncated to 23 bits, zero below the float
+// range (and for zero or subnormal x), +inf above it and for inf or NaN.
+__device__ __forceinline__ float scaled_mag(double x, int E) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  if (ex == 0) return 0.0f;
+  const int ef = ex - E + 127;
+  if (ex == 0x7ff || ef >= 255) return __uint_as_float(0x7f800000u);
+  if (ef <= 0) return 0.0f;
+  return __uint_as_float(((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// floor(2 x) for 0 <= x < 2^50 from the bit pattern (the row of the
+// half-unit-wide interpolant tables)
+__device__ __forceinline__ int half_index(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;   // x = 1.m 2^e
+  if (e < -1) return 0;
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+  return (int)(m >> (51 - e));
+}
+
+// -(2 j + 1) as a double, exactly, for 0 <= j < 2^30
+__device__ __forceinline__ double neg_odd(int j) {
+  const unsigned n = 2u * (unsigned)j + 1u;
+  const int p = 31 - __clz(n);   // 2^p <= n < 2^(p+1)
+  const unsigned long long mant = ((unsigned long long)n << (52 - p)) & 0xfffffffffffffull;
+  return __longlong_as_double((long long)((1ull << 63) | ((unsigned long long)(p + 1023) << 52) | mant));
+}
+
+// sums of a and b over the warp with one FP64 add per level: after the first
+// exchange the even lanes carry partial sums of a and the odd lanes of b;
+// every lane returns both totals (bitwise the same in all lanes)
+__device__ __forceinline__ void warp_sum2(double& a, double& b) {
+  const bool odd = threadIdx.x & 1;
+  double keep = odd ? b : a;
+  const double send = odd ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, send, 1);
+#pragma unroll
+  for (int o = 2; o < 32; o <<= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  a = __shfl_sync(0xffffffffu, keep, 0);
+  b = __shfl_sync(0xffffffffu, keep, 1);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max_nonneg_f(float v) {
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+}
+
+// the g4 column of the Planck interpolant table in FP32 (filled once from the
+// FP64 table by k_fill_si_tables)
+static __device__ float kG4TabF[(kPlanckRows + 1) * (kPlanckDeg + 1)];
+
+// Planck edge value (as planck_edge) with g4 = x^4/(e^x - 1) in FP32
+struct EdgeSI {
+  double V;
+  float g4;
+  bool lower;
+};
+
+__device__ __forceinline__ EdgeSI planck_edge_si(double x) {
+  EdgeSI r;
+  const long long xb = __double_as_longlong(x);
+  if (xb <= 0) { r.V = 0.0; r.g4 = 0.0f; r.lower = true; return r; }
+  if (xb > kBits740) { r.V = 0.0; r.g4 = 0.0f; r.lower = false; return r; }
+  const bool tail = xb >= kBits40;
+  const int j = tail ? kPlanckRows : half_index(x);
+  const double s = tail ? x : fma(x, 4.0, neg_odd(j));   // (x - (j/2 + 1/4)) 4
+  const double* row = kPlanckTab + 2 * j * (kPlanckDeg + 1);
+  const float* rowf = kG4TabF + j * (kPlanckDeg + 1);
+  const float sf = d2f_trunc(s);
+  double p1 = __ldg(row + 2 * kPlanckDeg);
+  float p2 = __ldg(rowf + kPlanckDeg);
+#pragma unroll
+  for (int k = kPlanckDeg - 1; k >= 0; --k) {
+    p1 = fma(p1, s, __ldg(row + 2 * k));
+    p2 = fmaf(p2, sf, __ldg(rowf + k));
+  }
+  r.lower = j < kPlanckLowerRows;
+  double m = 1.0;
+  if (r.lower) m = x * x * x;
+  else if (tail) m = exp(-x);
+  r.V = m * p1;
+  r.g4 = d2f_trunc(m) * p2;
+  return r;
+}
+
+// Planck quantities of one cell at temperature T (> 0 or not) for the lane's
+// groups g = lane + 32 j: sigma_g and Phi_g in FP64, dPhi_g/dT in FP32.
+// The same operations as cell_planck for sigma_g and Phi_g.
+template <int NC>
+__device__ __forceinline__ void si_planck(const Dev& d, double T, double invT, double sT, double* sig,
+                                          double* phi, float* dphi) {
+  const int lane = threadIdx.x & 31, G = d.G;
+  const bool Tpos = __double_as_longlong(T) > 0;
+  const double ac = d.a * d.c, T3 = T * T * T;
+  const double acT3 = ac * T3, acT4 = acT3 * T;
+  const float acT3f = d2f_trunc(acT3);
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (d.grey) {
+      sig[j] = cap_sigma(d, sT);
+      phi[j] = Tpos ? acT4 : 0.0;
+      dphi[j] = Tpos ? 4.0f * acT3f : 0.0f;
+      continue;
+    }
+    EdgeSI lo;
+    if (g <= G && Tpos) lo = planck_edge_si(d.nu_edges[g] * invT);
+    else { lo.V = 0.0; lo.g4 = 0.0f; lo.lower = true; }
+    EdgeSI hi;
+    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
+    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
+    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
+    if (lane == 31 && g + 1 <= G && Tpos) hi = planck_edge_si(d.nu_edges[g + 1] * invT);
+    if (g < G) {
+      sig[j] = sigma_group_at(d, sT, T, invT, g);
+      if (Tpos) {
+        double I;
+        if (hi.lower) I = hi.V - lo.V;
+        else if (!lo.lower) I = lo.V - hi.V;
+        else I = (kPi4over15 - lo.V) - hi.V;
+        const double b = k15overPi4 * I;
+        phi[j] = acT4 * b;
+        dphi[j] = acT3f * fmaf((float)k15overPi4, lo.g4 - hi.g4, 4.0f * d2f_trunc(b));
+      } else {
+        phi[j] = 0.0;
+        dphi[j] = 0.0f;
+      }
+    } else {
+      sig[j] = 1.0; phi[j] = 0.0; dphi[j] = 0.0f;
+    }
+  }
+}
+
+// C2(x)/dt of the face flux (as coef_g2_fast) with the row chosen on the integer pipes
+__device__ __forceinline__ double coef_g2_si(double x, double ix) {
+  const bool tail = __double_as_longlong(x) >= kBits40;
+  const int j = tail ? kPlanckRows : half_index(x);
+  const double s = tail ? ix : fma(x, 4.0, neg_odd(j));
+  const double* row = kC2Tab + j * (kPlanckDeg + 1);
+  double p = __ldg(row + kPlanckDeg);
+#pragma unroll
+  for (int k = kPlanckDeg - 1; k >= 0; --k) p = fma(p, s, __ldg(row + k));
+  return j < kPlanckLowerRows ? p * x : p;
+}
+
+// F^eq on a face between relaxation times tl, tu and Phi values pl, pu (lower,
+// upper side) along `axis`: C2 (v^2/3) (Phi_u - Phi_l)/h with the harmonic-mean
+// face opacity, tau_f = (tl + tu)/2 (App. B).  A pure function of its
+// operands, so the two cells of a face evaluate it bitwise alike.
+__device__ __forceinline__ double feq_face_si(const Dev& d, double tl, double tu, double pl, double pu, int axis) {
+  const double st = tl + tu;
+  const double x = d.two_dt * rcp_nr(st);
+  return coef_g2_si(x, st * d.inv_2dt) * (d.feq_k[axis] * (pu - pl));
+}
+
+}  // namespace ugkwp
