@@ -252,7 +252,7 @@ def run_reference(args):
 # faces (tau sum, reciprocal, C2 interpolant, difference), the closed-form
 # T update and the rho update, the Planck edge interpolants, group fractions
 # and derivatives, the Simpson group opacity and tau, q
-SI_FLOPS_PER_CELL_GROUP = 190
+SI_FLOPS_PER_CELL_GROUP = 235
 # FP64 peak of the chip: 152 SMs x 4 sub-partitions x 0.5 FMA lanes a cycle
 # x 2 flops x the maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12

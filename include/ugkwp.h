@@ -139,7 +139,13 @@ typedef struct ugkwp_problem {
    * silent; the scaled bins are counted in n_scaled_bins).  1: the split as
    * written, rho^h = rho^{n+1} - E_surv/V, nothing scaled. */
   int32_t split_literal;
-  int32_t _pad4;
+  /* Source iteration of a UGKWP_MIXED problem (App. B, Algorithm 2): FP32
+   * iterates of the same linearised update first, from T^n until the change
+   * of T is near FP32 resolution, then FP64 iterates from there to si_tol --
+   * the fixed point reached is the FP64 one, only the starting point differs.
+   * 0 (default): on where the iteration has at least 2^17 (cell, group)
+   * pairs (over all ensemble members); 1: on; -1: off.  Ignored in FP64. */
+  int32_t si_warm32;
 } ugkwp_problem;
 
 typedef struct ugkwp_handle ugkwp_handle;
@@ -164,6 +170,8 @@ typedef struct ugkwp_tally_report {
   double E_rad0, E_mat0, E_rad1, E_mat1;      /* sum V rho/c, sum V Cv T before/after */
   double bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
   int64_t n_scaled_bins;  /* (cell, group) bins whose survivors' weights were scaled (split_literal 0) */
+  int32_t si_iters32;     /* FP32 warm-start iterates before the si_iters FP64 ones (si_warm32) */
+  int32_t _pad5;
 } ugkwp_tally_report;
 
 /* Host-side structure-of-arrays particle buffers for ugkwp_get_state /

@@ -49,7 +49,7 @@ class CProblem(C.Structure):
         ("src_amp", _dp), ("src_t_end", C.c_double), ("cv_law", C.c_int32), ("_pad2", C.c_int32),
         ("cv_chi", C.c_double),
         ("nz", C.c_int32), ("bc_z", C.c_int32 * 2), ("_pad3", C.c_int32), ("dz", C.c_double),
-        ("bcT_z", C.c_double * 2), ("split_literal", C.c_int32), ("_pad4", C.c_int32),
+        ("bcT_z", C.c_double * 2), ("split_literal", C.c_int32), ("si_warm32", C.c_int32),
     ]
 
 
@@ -64,7 +64,8 @@ class CTallyReport(C.Structure):
         ("status_bits", C.c_uint32),
         ("E_rad0", C.c_double), ("E_mat0", C.c_double), ("E_rad1", C.c_double), ("E_mat1", C.c_double),
         ("bnd_in_macro", C.c_double), ("bnd_in_part", C.c_double), ("bnd_out_part", C.c_double),
-        ("src_in", C.c_double), ("n_scaled_bins", C.c_int64),
+        ("src_in", C.c_double), ("n_scaled_bins", C.c_int64), ("si_iters32", C.c_int32),
+        ("_pad5", C.c_int32),
     ]
 
 
@@ -214,6 +215,7 @@ class _HostProblem:
         s.bc_z[0], s.bc_z[1] = int(bc[4]), int(bc[5])
         s.bcT_z[0], s.bcT_z[1] = float(bcT[4]), float(bcT[5])
         s.split_literal = int(getattr(p, "split_literal", 0))
+        s.si_warm32 = int(getattr(p, "si_warm32", 0))
         self.s = s
         self._keep = keep
 
@@ -276,7 +278,7 @@ class Simulation:
         r = CTallyReport()
         _check(load().ugkwp_tallies_member(self.h, member, C.byref(r),
                                            C.c_void_p(_stream_ptr(self.stream))), self.h)
-        out = {k: getattr(r, k) for k, _ in CTallyReport._fields_[9:]}
+        out = {k: getattr(r, k) for k, _ in CTallyReport._fields_[9:] if not k.startswith("_")}
         out["ptr"] = {k: getattr(r, k) for k, _ in CTallyReport._fields_[:9]}
         return out
 

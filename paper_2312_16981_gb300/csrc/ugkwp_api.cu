@@ -14,6 +14,10 @@
 using ugkwp::Ctrl;
 using ugkwp::Dev;
 
+// (cell, group) pairs from which a mixed-precision source iteration starts
+// with FP32 iterates by default (si_warm32 = 0)
+constexpr long long kWarmMinPairs = 1ll << 17;
+
 struct ugkwp_handle {
   Dev d;                        // member 0 (what the single-problem calls address)
   std::vector<Dev> members;     // every member's descriptor (host copy of the device table)
@@ -108,6 +112,7 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
   if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED)
     return fail(h, UGKWP_ERR_ARG, "precision must be UGKWP_FP64 or UGKWP_MIXED");
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
+  if (p->si_warm32 < -1 || p->si_warm32 > 1) return fail(h, UGKWP_ERR_ARG, "si_warm32 must be -1, 0 or 1");
   if (!(p->tau_num_C >= 0.0)) return fail(h, UGKWP_ERR_ARG, "tau_num_C must be >= 0");
   if (p->sig_law < 0 || p->sig_law > 2) return fail(h, UGKWP_ERR_ARG, "sig_law must be 0, 1 or 2");
   if (p->sig_law == 2 && p->grey) return fail(h, UGKWP_ERR_ARG, "sig_law 2 (Olson foam) needs groups (grey = 0)");
@@ -192,6 +197,16 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.khat_f = mixed ? cv.take<float>(nb) : nullptr;
   d.slow_i = mixed ? cv.take<uint32_t>(P) : nullptr;
   d.slow_t = mixed ? cv.take<float>(P) : nullptr;
+  for (int k = 0; k < 2; ++k) {
+    d.Tk_f[k] = mixed ? cv.take<float>(nc) : nullptr;
+    d.tau_f[k] = mixed ? cv.take<float>(ncg) : nullptr;
+    d.phi_f[k] = mixed ? cv.take<float>(ncg) : nullptr;
+  }
+  d.q_f = mixed ? cv.take<float>(ncg) : nullptr;
+  d.R_f = mixed ? cv.take<float>(ncg) : nullptr;
+  d.Feq_f = (mixed && p->dim >= 2) ? cv.take<float>(nf * G) : nullptr;
+  d.nu_pow_f = mixed ? cv.take<float>(3 * G) : nullptr;
+  d.olson_nu_f = (mixed && p->sig_law == 2) ? cv.take<float>(9 * G) : nullptr;
   d.particles_begin = nullptr;
   for (int b = 0; b < 2; ++b) {
     if (mixed) {
@@ -304,6 +319,13 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.spf = (float)d.sig_p;
   d.inv_cap = p->sig_cap > 0.0 ? 1.0 / p->sig_cap : 0.0;
   d.inv_capf = (float)d.inv_cap;
+  d.two_dtf = (float)d.two_dt;
+  d.inv_2dtf = (float)d.inv_2dt;
+  d.ratef = (float)d.rate_f;
+  d.acf = (float)(d.a * d.c);
+  d.inv_cf = (float)d.inv_c;
+  for (int a = 0; a < 3; ++a) d.feq_kf[a] = (float)d.feq_k[a];
+  d.si_warm = 0;   // set once the ensemble's size is known
   // bin and cell indices below 2^24 divide by G and nx through an FP32 reciprocal
   d.fastdiv = (long long)d.ncell * d.G < (1ll << 24) ? 1 : 0;
   d.invG_f = 1.0f / (float)d.G;
@@ -450,6 +472,17 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
     fg0[m + 1] = fg0[m] + d.nface * d.G;
     if (d.nbins > max_bins) max_bins = d.nbins;
     if (d.G > max_G) max_G = d.G;
+  }
+  // FP32 warm start of the source iteration: mixed precision, and on by
+  // default where the iteration has enough (cell, group) pairs to be bound by
+  // the FP64 pipe (about 2^17: 24 per lane of every SM); a small latency-bound
+  // iteration gains nothing from it
+  {
+    long long ncg = 0;
+    for (int m = 0; m < n; ++m) ncg += (long long)h->members[m].ncell * h->members[m].G;
+    const int want = probs[0].si_warm32;
+    const bool on = probs[0].precision == UGKWP_MIXED && (want == 1 || (want == 0 && ncg >= kWarmMinPairs));
+    for (int m = 0; m < n; ++m) h->members[m].si_warm = on ? 1 : 0;
   }
   // device tables
   Carver cv{base};
@@ -641,6 +674,7 @@ int ugkwp_tallies_member(ugkwp_handle* h, int m, ugkwp_tally_report* out, void* 
   out->n_removed = (int64_t)c.n_removed; out->n_segments = (int64_t)c.n_segments;
   out->si_iters = (int32_t)c.si_iters;
   out->n_scaled_bins = (int64_t)c.n_scaled_bins;
+  out->si_iters32 = (int32_t)c.si_iters32;
   out->status_bits = c.status;
   out->E_rad0 = c.E_rad0; out->E_mat0 = c.E_mat0; out->E_rad1 = c.E_rad1; out->E_mat1 = c.E_mat1;
   out->bnd_in_macro = c.bnd_in_macro; out->bnd_in_part = c.bnd_in_part;

@@ -290,6 +290,17 @@ struct Dev {
   double* qk;       // [ncell*G] 1/(tau + dt) of the iterate (read by the cell's own warp)
   double* phik[2];  // [ncell*G]
   float* dphik;     // [ncell*G] dPhi_g/dT of the iterate (FP32: it sets only the contraction rate)
+  // FP32 warm start of the source iteration (mixed precision; null otherwise)
+  int si_warm;      // 1: FP32 iterates before the FP64 ones this step
+  float* Tk_f[2];   // [ncell]
+  float* tau_f[2];  // [ncell*G]
+  float* phi_f[2];  // [ncell*G]
+  float* q_f;       // [ncell*G]
+  float* R_f;       // [ncell*G]
+  float* Feq_f;     // [nface*G] (2D and 3D face pass)
+  float* nu_pow_f;  // [3G]
+  float* olson_nu_f;  // [9G] (sig_law 2)
+  float feq_kf[3], two_dtf, inv_2dtf, ratef, acf, inv_cf;
   // particles: two structure-of-arrays buffers, selected by ctrl->cur
   double* px[2];
   double* py[2];
@@ -505,7 +516,7 @@ struct Ctrl {
   unsigned long long tile_next;   // next particle tile to hand out (particle kernel; 0 at step start)
   unsigned long long n_slow;      // survivors listed for the general particle kernel (0 at step start)
   unsigned int n_scaled_bins;     // (cell, group) bins whose survivors were scaled this step
-  unsigned int pad_;
+  unsigned int si_iters32;        // FP32 warm-start iterates of the last source iteration
   unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)
   double E_rad0, E_mat0, E_rad1, E_mat1, bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
 };

@@ -35,14 +35,29 @@ __global__ void k_init_pow(Dev d) {
   }
   for (int g = tid; g <= d.G; g += stride)
     if (d.nu_edges_f) d.nu_edges_f[g] = (float)d.nu_edges[g];
-  // FP32 copy of the g4 column of the Planck table (the same on every call)
-  for (int i = tid; i < (kPlanckRows + 1) * (kPlanckDeg + 1); i += stride) kG4TabF[i] = (float)kPlanckTab[2 * i + 1];
+  // FP32 copies of the interpolant tables (the same on every call)
+  for (int i = tid; i < (kPlanckRows + 1) * (kPlanckDeg + 1); i += stride) {
+    kP1TabF[i] = (float)kPlanckTab[2 * i];
+    kG4TabF[i] = (float)kPlanckTab[2 * i + 1];
+    kC2TabF[i] = (float)kC2Tab[i];
+  }
+  if (d.nu_pow_f)
+    for (int g = tid; g < d.G; g += stride) {
+      const double a = d.nu_edges[g], b = d.nu_edges[g + 1], m = 0.5 * (a + b);
+      d.nu_pow_f[3 * g] = d.grey ? 1.0f : (float)pow_fast(a, d.sig_p);
+      d.nu_pow_f[3 * g + 1] = d.grey ? 1.0f : (float)pow_fast(m, d.sig_p);
+      d.nu_pow_f[3 * g + 2] = d.grey ? 1.0f : (float)pow_fast(b, d.sig_p);
+    }
   // foam opacity nu factors at the Simpson points (sig_law 2)
   if (d.olson_nu)
     for (int g = tid; g < d.G; g += stride) {
       const double a = d.nu_edges[g], b = d.nu_edges[g + 1], pts[3] = {a, 0.5 * (a + b), b};
-      for (int k = 0; k < 3; ++k)
-        foam_nu(pts[k], d.olson_nu + 9 * g + 3 * k, d.olson_nu + 9 * g + 3 * k + 1, d.olson_nu + 9 * g + 3 * k + 2);
+      for (int k = 0; k < 3; ++k) {
+        double* t = d.olson_nu + 9 * g + 3 * k;
+        foam_nu(pts[k], t, t + 1, t + 2);
+        if (d.olson_nu_f)
+          for (int q = 0; q < 3; ++q) d.olson_nu_f[9 * g + 3 * k + q] = (float)t[q];
+      }
     }
 }
 
@@ -598,6 +613,172 @@ __device__ __forceinline__ double face_feq(const Dev& d, int f, int g, int cur) 
 // rule stops updating while the others go on (every block keeps the same
 // per-member record, so all blocks leave the loop together).
 
+// FP64 state of cell c at temperature T for the next iterate (slot): T^k,
+// tau = 1/(rate sigma_g), q = 1/(tau + dt), Phi_g, dPhi_g/dT (FP32)
+template <int NC>
+__device__ __forceinline__ void si_state(const Dev& d, int c, double T, double invT, double sT, int slot = 0) {
+  const int lane = threadIdx.x & 31, G = d.G;
+  double sg[NC], ph[NC];
+  float dp[NC];
+  si_planck<NC>(d, T, invT, sT, sg, ph, dp);
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (g < G) {
+      double tau, qv;
+      tau_and_q(d, sg[j], &tau, &qv);
+      __stcg(d.tauk[slot] + c * G + g, tau);
+      __stcg(d.qk + c * G + g, qv);
+      __stcg(d.phik[slot] + c * G + g, ph[j]);
+      __stcg(d.dphik + c * G + g, dp[j]);
+    }
+  }
+  if (lane == 0) __stcg(d.Tk[slot] + c, T);
+}
+
+// ---- FP32 warm start (mixed precision)
+constexpr double kWarmTol = 3e-6;   // largest |dT|/T at which the FP32 iterates hand over
+constexpr int kWarmMaxIters = 100;
+
+// the same state in FP32
+template <int NC>
+__device__ __forceinline__ void si_state_f(const Dev& d, int c, float T, int slot) {
+  const int lane = threadIdx.x & 31, G = d.G;
+  const float invT = __frcp_rn(T);
+  const float sT = d2f_trunc(d.sigma0[c]) * pow_fast_f(T, d2f_trunc(d.sig_q));
+  float sg[NC], ph[NC], dp[NC];
+  si_planck_f<NC>(d, T, invT, sT, sg, ph, dp);
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (g < G) {
+      float tau, qv;
+      tau_and_q_f(d, sg[j], &tau, &qv);
+      __stcg(d.tau_f[slot] + c * G + g, tau);
+      __stcg(d.q_f + c * G + g, qv);
+      __stcg(d.phi_f[slot] + c * G + g, ph[j]);
+      __stcg(d.dphik + c * G + g, dp[j]);
+    }
+  }
+  if (lane == 0) __stcg(d.Tk_f[slot] + c, T);
+}
+
+// neighbour values across one face in FP32 (as neighbour()); false at a reflecting wall
+__device__ __forceinline__ bool neighbour_f(const Dev& d, int ix, int iy, int iz, int axis, int dir, int g, int cur,
+                                            float tau_c, float* tn, float* pn) {
+  const int jx = ix + (axis == 0 ? dir : 0), jy = iy + (axis == 1 ? dir : 0), jz = iz + (axis == 2 ? dir : 0);
+  if (jx < 0 || jx >= d.nx || jy < 0 || jy >= d.ny || jz < 0 || jz >= d.nz) {
+    const int side = axis * 2 + (dir > 0 ? 1 : 0);
+    if (d.bc[side] == BC_REFLECT) return false;
+    if (d.bc[side] == BC_BLACKBODY) {
+      *tn = __frcp_rn(d.ratef * d2f_trunc(d.ghost_sig[side * d.G + g]));
+      *pn = d2f_trunc(d.ghost_phi[side * d.G + g]);
+    } else {
+      *tn = tau_c;
+      *pn = 0.0f;
+    }
+    return true;
+  }
+  const int n = (jz * d.ny + jy) * d.nx + jx;
+  *tn = __ldcg(d.tau_f[cur] + n * d.G + g);
+  *pn = __ldcg(d.phi_f[cur] + n * d.G + g);
+  return true;
+}
+
+// F^eq on face f in FP32 (as face_feq)
+__device__ __forceinline__ float face_feq_f(const Dev& d, int f, int g, int cur) {
+  const FaceRef r = face_ref(d, f);
+  const int sideL = r.axis * 2, sideR = sideL + 1;
+  const bool lin = r.k - 1 >= 0, rin = r.k < r.nk;
+  if ((!lin && d.bc[sideL] == BC_REFLECT) || (!rin && d.bc[sideR] == BC_REFLECT)) return 0.0f;
+  float tl = 0.0f, tu = 0.0f, pl = 0.0f, pu = 0.0f;
+  if (lin) {
+    const int i = line_cell(d, r, r.k - 1) * d.G + g;
+    tl = __ldcg(d.tau_f[cur] + i);
+    pl = __ldcg(d.phi_f[cur] + i);
+  }
+  if (rin) {
+    const int i = line_cell(d, r, r.k) * d.G + g;
+    tu = __ldcg(d.tau_f[cur] + i);
+    pu = __ldcg(d.phi_f[cur] + i);
+  }
+  if (!lin) {
+    if (d.bc[sideL] == BC_BLACKBODY) {
+      tl = __frcp_rn(d.ratef * d2f_trunc(d.ghost_sig[sideL * d.G + g]));
+      pl = d2f_trunc(d.ghost_phi[sideL * d.G + g]);
+    } else {
+      tl = tu;
+    }
+  }
+  if (!rin) {
+    if (d.bc[sideR] == BC_BLACKBODY) {
+      tu = __frcp_rn(d.ratef * d2f_trunc(d.ghost_sig[sideR * d.G + g]));
+      pu = d2f_trunc(d.ghost_phi[sideR * d.G + g]);
+    } else {
+      tu = tl;
+    }
+  }
+  return feq_face_f(d, tl, tu, pl, pu, r.axis);
+}
+
+// One FP32 iterate of cell c (the linearised update of the FP64 iterate, no
+// rho written): T^{k+1} and the cell's state at it into slot cur ^ 1.
+// Returns |dT|/T (+inf where not finite).
+template <int NC>
+__device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool face_pass) {
+  const int lane = threadIdx.x & 31, G = d.G, nxt = cur ^ 1;
+  const float dt = d.dtf;
+  const float Tc = __ldcg(d.Tk_f[cur] + c);
+  float num = 0.0f, den = 0.0f;
+  int ix, iy, iz;
+  cell_xyz(d, c, &ix, &iy, &iz);
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (g >= G) continue;
+    const int i = c * G + g;
+    const float tc = __ldcg(d.tau_f[cur] + i), phc = __ldcg(d.phi_f[cur] + i), dpc = __ldcg(d.dphik + i);
+    float q = d.R_f[i];
+    for (int axis = 0; axis < d.dim; ++axis) {
+      float Fin = 0.0f, Fout = 0.0f;
+      if (face_pass) {
+        Fin = __ldcg(d.Feq_f + face_index_xyz(d, ix, iy, iz, axis, -1) * G + g);
+        Fout = __ldcg(d.Feq_f + face_index_xyz(d, ix, iy, iz, axis, +1) * G + g);
+      } else {
+        float tn, pn;
+        if (neighbour_f(d, ix, iy, iz, axis, -1, g, cur, tc, &tn, &pn)) Fin = feq_face_f(d, tn, tc, pn, phc, axis);
+        if (neighbour_f(d, ix, iy, iz, axis, +1, g, cur, tc, &tn, &pn)) Fout = feq_face_f(d, tc, tn, phc, pn, axis);
+      }
+      q = fmaf(d2f_trunc(d.dt_h[axis]), Fin - Fout, q);
+    }
+    const float qi = __ldcg(d.q_f + i);
+    const float ap = dt * qi * d.inv_cf;
+    num = fmaf(ap, fmaf(dpc, Tc, q - phc), num);
+    den = fmaf(ap, dpc, den);
+  }
+  num = warp_sum_f(num);
+  den = warp_sum_f(den);
+  float Tnew;
+  if (d.cv_law == 1) {
+    const double Tcd = f2d_bits(Tc), Tnd = d.T[c];
+    const double ck = heat_capacity(d, c, Tcd);
+    Tnew = d2f_trunc((mat_energy(d, c, Tnd) - mat_energy(d, c, Tcd) + ck * Tcd + f2d_bits(num)) /
+                     (ck + f2d_bits(den)));
+  } else {
+    const float cv = d2f_trunc(d.cv[c]);
+    Tnew = __fdiv_rn(fmaf(cv, d2f_trunc(d.T[c]), num), cv + den);
+  }
+  if (!(Tnew > 1e-30f)) Tnew = (Tnew == Tnew) ? 1e-30f : Tnew;
+  float eT = __fdiv_rn(fabsf(Tnew - Tc), Tnew);
+  if (!(eT <= 3.0e38f)) eT = INFINITY;
+  if (Tnew == Tnew && Tnew < INFINITY) si_state_f<NC>(d, c, Tnew, nxt);
+  else {
+    // not finite: the cell keeps its temperature (the hand-over falls back to T^n)
+    if (lane == 0) __stcg(d.Tk_f[nxt] + c, Tnew);
+  }
+  return eT;
+}
+
 template <int NC, bool ENS>
 __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, const Ens e) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
@@ -607,6 +788,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   unsigned int* bar_count = ENS ? e.bar : &d0.ctrl->bar_count;
   Ctrl* st_ctrl = ENS ? e.devs[0].ctrl : d0.ctrl;
   const unsigned int spin_limit = st_ctrl->bar_timeout_spins;
+  const bool warm = ENS ? e.devs[0].si_warm : d0.si_warm;
   __shared__ float s_err[8][2];
   __shared__ int s_conv[ENS ? kMaxEnsemble : 1];   // iterate count at convergence, 0 = still running
   __shared__ int s_any;
@@ -654,27 +836,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           r += Wd * d.inv_vol;
           if (src_on) { r += d.src[i]; e_src += V * d.src[i] * d.inv_c; }
           d.R[i] = r;
+          if (warm) d.R_f[i] = d2f_trunc(r);
           e_rad0 += V * r0 * d.inv_c;
         }
       }
       const double T = d.T[c];
       if (lane == 0) e_mat0 += V * mat_energy(d, c, T);
-      double sg[NC], ph[NC];
-      float dp[NC];
-      si_planck<NC>(d, T, 1.0 / T, sigma_T(d, c, T), sg, ph, dp);
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        const int g = lane + 32 * j;
-        if (g < G) {
-          double tau, qv;
-          tau_and_q(d, sg[j], &tau, &qv);
-          __stcg(d.tauk[0] + c * G + g, tau);
-          __stcg(d.qk + c * G + g, qv);
-          __stcg(d.phik[0] + c * G + g, ph[j]);
-          __stcg(d.dphik + c * G + g, dp[j]);
-        }
-      }
-      if (lane == 0) __stcg(d.Tk[0] + c, T);
+      if (warm) si_state_f<NC>(d, c, d2f_trunc(T), 0);
+      else si_state<NC>(d, c, T, 1.0 / T, sigma_T(d, c, T));
     }
     e_rad0 = warp_sum(e_rad0);
     e_src = warp_sum(e_src);
@@ -688,17 +857,74 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   for (int k = threadIdx.x; k < (ENS ? M : 1); k += blockDim.x) s_conv[k] = 0;
   if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
 
-  // ---- iterations
+  // ---- iterations.  `it` counts all iterates (it indexes the error slots),
+  // itA the FP32 warm-start iterates, itB the FP64 ones.
   const int max_it = ENS ? e.devs[0].si_max_iters : d0.si_max_iters;
-  int it = 0, all_done = 0;
+  int it = 0, itA = 0, itB = 0, all_done = 0;
   // 2D and 3D: every face's F^eq once per iterate (one warp per face, one lane per
   // group), then a grid barrier, instead of each cell evaluating its 2 dim
   // faces (a face costs a division and the C2 interpolant in FP64, the
   // scarce unit on this chip; in 1D the extra barrier costs more than the
   // second evaluation of a face saves)
   const bool face_pass = !ENS && d0.dim >= 2;
-  for (; it < max_it; ++it) {
-    const int cur = it & 1, nxt = cur ^ 1;
+  if (warm) {
+    // FP32 iterates from T^n while the largest |dT|/T falls: until it is
+    // within kWarmTol, stalls near FP32 resolution, or kWarmMaxIters pass
+    Ctrl* const ctrlA = ENS ? e.devs[0].ctrl : d0.ctrl;
+    const int maxA = max_it < kWarmMaxIters ? max_it : kWarmMaxIters;
+    for (; itA < maxA; ++itA, ++it) {
+      const int cur = itA & 1, nxt = cur ^ 1;
+      if (face_pass) {
+        const int G = d0.G;
+        for (long long gf = gw; gf < d0.nface; gf += nw) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            const int g = lane + 32 * j;
+            if (g < G) d0.Feq_f[gf * G + g] = face_feq_f(d0, (int)gf, g, cur);
+          }
+        }
+        if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+      }
+      float werr = 0.0f;
+      for (long long gc = gw; gc < total; gc += nw) {
+        const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+        const Dev& d = ENS ? e.devs[m] : d0;
+        const int c = (int)(ENS ? gc - e.cell0[m] : gc);
+        werr = fmaxf(werr, si_iterate_f<NC>(d, c, cur, face_pass));
+      }
+      if (lane == 0) s_err[wib][0] = werr;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float mx = 0.0f;
+        for (int w = 0; w < nwb; ++w) mx = fmaxf(mx, s_err[w][0]);
+        atomic_max_nonneg(&ctrlA->err_slot[it % 3][0], f2d_bits(mx));
+      }
+      if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+          Ctrl* cc = ENS ? e.devs[k].ctrl : d0.ctrl;
+          cc->err_slot[(it + 1) % 3][0] = 0ull;
+          cc->err_slot[(it + 1) % 3][1] = 0ull;
+        }
+      if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+      const double eA = __longlong_as_double((long long)load_acquire_u64(&ctrlA->err_slot[it % 3][0]));
+      const double pA = __longlong_as_double((long long)load_acquire_u64(&ctrlA->err_slot[(it + 2) % 3][0]));
+      const bool stalled = itA > 0 && eA <= 1e-4 && eA > 0.5 * pA;
+      if (!(eA <= 1e30) || eA <= kWarmTol || stalled || itA + 1 >= maxA) { ++itA; ++it; break; }
+    }
+    // hand-over: the FP64 state at the last FP32 temperature (at T^n in a
+    // cell where that is not finite and positive)
+    for (long long gc = gw; gc < total; gc += nw) {
+      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+      const Dev& d = ENS ? e.devs[m] : d0;
+      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
+      const float Tf = __ldcg(d.Tk_f[itA & 1] + c);
+      const double T0 = (Tf > 0.0f && Tf < INFINITY) ? f2d_bits(Tf) : d.T[c];
+      si_state<NC>(d, c, T0, rcp_nr(T0), sigma_T(d, c, T0));
+    }
+    if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+  }
+  for (; itB < max_it; ++itB, ++it) {
+    const int cur = itB & 1, nxt = cur ^ 1;
     float werrT = 0.0f, werrR = 0.0f;
     if (face_pass) {
       const int G = d0.G;
@@ -830,22 +1056,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         werrT = fmaxf(werrT, eT);
         werrR = fmaxf(werrR, eR);
       }
-      if (lane == 0) __stcg(d.Tk[nxt] + c, Tnew);
-      double sg[NC], ph[NC];
-      float dp[NC];
-      si_planck<NC>(d, Tnew, invTn, sTn, sg, ph, dp);
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        const int g = lane + 32 * j;
-        if (g < G) {
-          double tau, qv;
-          tau_and_q(d, sg[j], &tau, &qv);
-          __stcg(d.tauk[nxt] + c * G + g, tau);
-          __stcg(d.qk + c * G + g, qv);
-          __stcg(d.phik[nxt] + c * G + g, ph[j]);
-          __stcg(d.dphik + c * G + g, dp[j]);
-        }
-      }
+      si_state<NC>(d, c, Tnew, invTn, sTn, nxt);
     }
     if (!ENS) {
       Ctrl* ctrl = d0.ctrl;
@@ -875,7 +1086,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const double eR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][1]));
       const double pT = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[(it + 2) % 3][0]));
       const double pR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[(it + 2) % 3][1]));
-      if (si_converged(eT, eR, pT, pR, d0.si_tol, it > 0)) { s_conv[0] = it + 1; all_done = 1; ++it; break; }
+      if (si_converged(eT, eR, pT, pR, d0.si_tol, itB > 0)) { s_conv[0] = itB + 1; all_done = 1; ++itB; ++it; break; }
     } else {
       if (threadIdx.x == 0) s_any = 0;
       __syncthreads();
@@ -887,15 +1098,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const double eR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][1]));
         const double pT = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[(it + 2) % 3][0]));
         const double pR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[(it + 2) % 3][1]));
-        if (si_converged(eT, eR, pT, pR, e.devs[k].si_tol, it > 0)) s_conv[k] = it + 1; else running = 1;
+        if (si_converged(eT, eR, pT, pR, e.devs[k].si_tol, itB > 0)) s_conv[k] = itB + 1; else running = 1;
       }
       if (running) s_any = 1;
       __syncthreads();
-      if (!s_any) { all_done = 1; ++it; break; }
+      if (!s_any) { all_done = 1; ++itB; ++it; break; }
     }
   }
 
-  // ---- epilogue: member m's last iterate wrote Tk[s_conv[m] & 1] (or Tk[it & 1])
+  // ---- epilogue: member m's last iterate wrote Tk[s_conv[m] & 1] (or Tk[itB & 1])
   {
     double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
     int bad = 0, scaled = 0, acc_m = -1;
@@ -922,7 +1133,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int c = (int)(ENS ? gc - e.cell0[m] : gc);
       const int G = d.G;
       const double dt = d.dt, V = d.vol;
-      const int ran = s_conv[ENS ? m : 0] ? s_conv[ENS ? m : 0] : it;
+      const int ran = s_conv[ENS ? m : 0] ? s_conv[ENS ? m : 0] : itB;
       const int fin = ran > 0 ? (ran & 1) : 0;
       const double T = __ldcg(d.Tk[fin] + c);
       if (!(T == T) || T > 1e300) bad = 1;
@@ -987,7 +1198,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
       Ctrl* cc = ENS ? e.devs[k].ctrl : d0.ctrl;
       const int ran = s_conv[ENS ? k : 0];
-      cc->si_iters = (unsigned int)(ran ? ran : it);
+      cc->si_iters = (unsigned int)(ran ? ran : itB);
+      cc->si_iters32 = (unsigned int)itA;
       if (!ran) atomicOr(&cc->status, ST_NOCONV);
     }
   }

@@ -106,7 +106,7 @@ __device__ __forceinline__ float warp_max_nonneg_f(float v) {
 }
 
 // the g4 column of the Planck interpolant table in FP32 (filled once from the
-// FP64 table by k_fill_si_tables)
+// FP64 table by k_init_pow)
 static __device__ float kG4TabF[(kPlanckRows + 1) * (kPlanckDeg + 1)];
 
 // Planck edge value (as planck_edge) with g4 = x^4/(e^x - 1) in FP32
@@ -211,6 +211,140 @@ __device__ __forceinline__ double feq_face_si(const Dev& d, double tl, double tu
   const double st = tl + tu;
   const double x = d.two_dt * rcp_nr(st);
   return coef_g2_si(x, st * d.inv_2dt) * (d.feq_k[axis] * (pu - pl));
+}
+
+// --------------------------------------------------------------------------
+// FP32 warm start (mixed precision).  The same linearised Jacobi update in
+// FP32 gives the FP64 iterates a starting temperature within about 1e-6 of
+// the fixed point; the FP64 iterates then converge to si_tol exactly as from
+// T^n, and the fixed point they reach is the FP64 one.  FP32 copies of the
+// interpolant tables (filled once from the FP64 tables by k_init_pow):
+static __device__ float kP1TabF[(kPlanckRows + 1) * (kPlanckDeg + 1)];
+static __device__ float kC2TabF[(kPlanckRows + 1) * (kPlanckDeg + 1)];
+
+struct EdgeF {
+  float V, g4;
+  bool lower;
+};
+
+__device__ __forceinline__ EdgeF planck_edge_f(float x) {
+  EdgeF r;
+  if (!(x > 0.0f)) { r.V = 0.0f; r.g4 = 0.0f; r.lower = true; return r; }
+  if (x > 740.0f) { r.V = 0.0f; r.g4 = 0.0f; r.lower = false; return r; }
+  const bool tail = x >= 40.0f;
+  const int j = tail ? kPlanckRows : (int)(2.0f * x);
+  const float s = tail ? x : fmaf(x, 4.0f, -(float)(2 * j + 1));
+  const float* r1 = kP1TabF + j * (kPlanckDeg + 1);
+  const float* r2 = kG4TabF + j * (kPlanckDeg + 1);
+  float p1 = __ldg(r1 + kPlanckDeg), p2 = __ldg(r2 + kPlanckDeg);
+#pragma unroll
+  for (int k = kPlanckDeg - 1; k >= 0; --k) {
+    p1 = fmaf(p1, s, __ldg(r1 + k));
+    p2 = fmaf(p2, s, __ldg(r2 + k));
+  }
+  r.lower = j < kPlanckLowerRows;
+  float m = 1.0f;
+  if (r.lower) m = x * x * x;
+  else if (tail) m = __expf(-x);
+  r.V = m * p1;
+  r.g4 = m * p2;
+  return r;
+}
+
+// group opacity in FP32 (the three laws of sigma_group_at)
+__device__ __forceinline__ float sigma_group_f(const Dev& d, float sT, float T, float invT, int g) {
+  const float cap = d.capf;
+  if (d.grey) return fminf(sT, cap);
+  const float a = __ldg(d.nu_edges_f + g), b = __ldg(d.nu_edges_f + g + 1), m = 0.5f * (a + b);
+  if (d.sig_law == 2) {
+    const float A = fminf(1e7f, 1e9f * T * T);
+    const float B = __fdividef(3e6f, 1.0f + 200.0f * T * sqrtf(T));
+    const float C = __fdividef(4e4f, 1.0f + 8000.0f * T * T);
+    const float* t = d.olson_nu_f + 9 * g;
+    auto kap = [&](float nu, const float* f) {
+      if (nu <= 0.008f) return A;
+      if (nu <= 0.3f) return B * __ldg(f);
+      return B * __ldg(f + 1) + C * __ldg(f + 2);
+    };
+    const float sa = fminf(sT * kap(a, t), cap), sm = fminf(sT * kap(m, t + 3), cap), sb = fminf(sT * kap(b, t + 6), cap);
+    return (sa + 4.0f * sm + sb) * (1.0f / 6.0f);
+  }
+  const float* np = d.nu_pow_f + 3 * g;
+  float fa = 1.0f, fm = 1.0f, fb = 1.0f;
+  if (d.sig_law == 1) { fa = -expm1f(-a * invT); fm = -expm1f(-m * invT); fb = -expm1f(-b * invT); }
+  const float sa = fminf(sT * __ldg(np) * fa, cap), sm = fminf(sT * __ldg(np + 1) * fm, cap);
+  const float sb = fminf(sT * __ldg(np + 2) * fb, cap);
+  return (sa + 4.0f * sm + sb) * (1.0f / 6.0f);
+}
+
+// sigma_g, Phi_g, dPhi_g/dT of one cell at T in FP32 (lanes as si_planck)
+template <int NC>
+__device__ __forceinline__ void si_planck_f(const Dev& d, float T, float invT, float sT, float* sig, float* phi,
+                                            float* dphi) {
+  const int lane = threadIdx.x & 31, G = d.G;
+  const bool Tpos = T > 0.0f;
+  const float acT3 = d.acf * (T * T * T), acT4 = acT3 * T;
+  const float k15 = (float)k15overPi4, kpi = (float)kPi4over15;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int g = lane + 32 * j;
+    if (d.grey) {
+      sig[j] = fminf(sT, d.capf);
+      phi[j] = Tpos ? acT4 : 0.0f;
+      dphi[j] = Tpos ? 4.0f * acT3 : 0.0f;
+      continue;
+    }
+    EdgeF lo;
+    if (g <= G && Tpos) lo = planck_edge_f(__ldg(d.nu_edges_f + g) * invT);
+    else { lo.V = 0.0f; lo.g4 = 0.0f; lo.lower = true; }
+    EdgeF hi;
+    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
+    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
+    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
+    if (lane == 31 && g + 1 <= G && Tpos) hi = planck_edge_f(__ldg(d.nu_edges_f + g + 1) * invT);
+    if (g < G) {
+      sig[j] = sigma_group_f(d, sT, T, invT, g);
+      if (Tpos) {
+        float I;
+        if (hi.lower) I = hi.V - lo.V;
+        else if (!lo.lower) I = lo.V - hi.V;
+        else I = (kpi - lo.V) - hi.V;
+        const float b = k15 * I;
+        phi[j] = acT4 * b;
+        dphi[j] = acT3 * fmaf(k15, lo.g4 - hi.g4, 4.0f * b);
+      } else {
+        phi[j] = 0.0f;
+        dphi[j] = 0.0f;
+      }
+    } else {
+      sig[j] = 1.0f; phi[j] = 0.0f; dphi[j] = 0.0f;
+    }
+  }
+}
+
+// tau = 1/(rate sigma) and q = 1/(tau + dt) = A/(1 + dt A), A = rate sigma, in FP32
+__device__ __forceinline__ void tau_and_q_f(const Dev& d, float sig, float* tau, float* q) {
+  const float A = d.ratef * sig;
+  *tau = __frcp_rn(A);
+  *q = A * __frcp_rn(fmaf(d.dtf, A, 1.0f));
+}
+
+__device__ __forceinline__ float coef_g2_f(float x, float ix) {
+  const bool tail = x >= 40.0f;
+  const int j = tail ? kPlanckRows : (int)(2.0f * x);
+  const float s = tail ? ix : fmaf(x, 4.0f, -(float)(2 * j + 1));
+  const float* row = kC2TabF + j * (kPlanckDeg + 1);
+  float p = __ldg(row + kPlanckDeg);
+#pragma unroll
+  for (int k = kPlanckDeg - 1; k >= 0; --k) p = fmaf(p, s, __ldg(row + k));
+  return j < kPlanckLowerRows ? p * x : p;
+}
+
+// F^eq of a face in FP32 (feq_face_si)
+__device__ __forceinline__ float feq_face_f(const Dev& d, float tl, float tu, float pl, float pu, int axis) {
+  const float st = tl + tu;
+  const float x = d.two_dtf * __frcp_rn(st);
+  return coef_g2_f(x, st * d.inv_2dtf) * (d.feq_kf[axis] * (pu - pl));
 }
 
 }  // namespace ugkwp
