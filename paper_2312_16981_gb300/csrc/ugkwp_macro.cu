@@ -483,6 +483,140 @@ __global__ void k_wave(const __grid_constant__ Dev d0, const Ens e) {
   }
 }
 
+// The wave-part flux of the mixed-precision build in FP32: the same upwind
+// half-range expression as k_wave, from FP32 copies of rho^h, sigma_g(T^n),
+// the sampled fractions and dt/tau_num, with the C4, C5 series (below x = 1,
+// 12 terms) or closed forms in FP32; stored as a double.  Each face keeps
+// one flux that both cells use, so the energy ledger still closes to
+// roundoff; the flux itself carries FP32 rounding (relative error about
+// 1e-6 where C5's closed form cancels near x = 1).
+constexpr int kSerF = 12;
+__device__ constexpr float kA4F[kSerF + 1] = {(float)a4(0), (float)a4(1), (float)a4(2), (float)a4(3), (float)a4(4),
+                                              (float)a4(5), (float)a4(6), (float)a4(7), (float)a4(8), (float)a4(9),
+                                              (float)a4(10), (float)a4(11), (float)a4(12)};
+__device__ constexpr float kA5F[kSerF + 1] = {(float)a5(0), (float)a5(1), (float)a5(2), (float)a5(3), (float)a5(4),
+                                              (float)a5(5), (float)a5(6), (float)a5(7), (float)a5(8), (float)a5(9),
+                                              (float)a5(10), (float)a5(11), (float)a5(12)};
+__device__ constexpr float kAC4F[kSerF + 1] = {(float)ac4(0), (float)ac4(1), (float)ac4(2), (float)ac4(3), (float)ac4(4),
+                                               (float)ac4(5), (float)ac4(6), (float)ac4(7), (float)ac4(8), (float)ac4(9),
+                                               (float)ac4(10), (float)ac4(11), (float)ac4(12)};
+
+__device__ __forceinline__ float coef_f4_f5_c4_f(float x, float* f4, float* f5, float* c4) {
+  if (x < 1.0f) {
+    float s4 = kA4F[kSerF], s5 = kA5F[kSerF], sc = kAC4F[kSerF];
+#pragma unroll
+    for (int k = kSerF - 1; k >= 2; --k) {
+      s4 = fmaf(s4, x, kA4F[k]);
+      s5 = fmaf(s5, x, kA5F[k]);
+      sc = fmaf(sc, x, kAC4F[k]);
+    }
+    s4 = fmaf(s4, x, kA4F[1]);
+    sc = fmaf(fmaf(sc, x, kAC4F[1]), x, kAC4F[0]);
+    *f4 = s4 * x;
+    *f5 = s5 * x * x;
+    *c4 = sc;
+    return -1.0f;
+  }
+  const float e = __expf(-x);
+  *c4 = (1.0f - e) / x;   // 1 - e has no cancellation for x >= 1
+  *f4 = *c4 - e;
+  *f5 = e * (1.0f + 0.5f * x) - *c4;
+  return e;
+}
+
+__device__ __forceinline__ void half_coefs_f(float xf, float ef, float tauf, float xh, float e_eff, float dt, float f4,
+                                             float f5, float c4, float* A, float* B) {
+  if (e_eff < 0.0f) {
+    *A = 0.0f;
+    *B = 0.0f;
+  } else if (e_eff > 0.0f) {
+    const float dd = xh - xf;
+    const float efh = fabsf(dd) < 0.5f ? e_eff * expm1f(dd) : (ef >= 0.0f ? ef : __expf(-xf)) - e_eff;
+    *A = f4 + efh;
+    *B = tauf * f5 - 0.5f * dt * efh;
+  } else {
+    *A = c4;
+    *B = -tauf * f4;
+  }
+}
+
+__device__ __forceinline__ float van_leer_f(float a, float b) {
+  return a * b > 0.0f ? 2.0f * a * (b / (a + b)) : 0.0f;
+}
+
+__device__ __forceinline__ float rho_h_at_f(const Dev& d, const FaceRef& r, int k, int g) {
+  return d2f_trunc(rho_h_at(d, r, k, g));
+}
+
+template <bool ENS>
+__global__ void k_wave32(const __grid_constant__ Dev d0, const Ens e) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long total = ENS ? e.total_fg : (long long)d0.nface * d0.G;
+  for (long long gi = tid; gi < total; gi += stride) {
+    const int m = ENS ? find_member(e.fg0, e.M, gi) : 0;
+    const Dev& d = ENS ? e.devs[m] : d0;
+    const int i = (int)(ENS ? gi - e.fg0[m] : gi);
+    const int G = d.G;
+    const float v = d.vf, dt = d.dtf;
+    const int f = i / G, g = i - f * G;
+    const FaceRef r = face_ref(d, f);
+    const int sideL = r.axis * 2, sideR = sideL + 1;
+    const bool lin = r.k - 1 >= 0, rin = r.k < r.nk;
+    if ((!lin && d.bc[sideL] == BC_REFLECT) || (!rin && d.bc[sideR] == BC_REFLECT)) {
+      d.Fwave[i] = 0.0;
+      continue;
+    }
+    const float rl = rho_h_at_f(d, r, r.k - 1, g), rr = rho_h_at_f(d, r, r.k, g);
+    const float h = d2f_trunc(r.h);
+    float sl, sr, fl, fr;
+    if (d.wave_order >= 2) {
+      const float rll = rho_h_at_f(d, r, r.k - 2, g), rrr = rho_h_at_f(d, r, r.k + 1, g);
+      const float ih = __frcp_rn(h);
+      sl = lin ? van_leer_f((rl - rll) * ih, (rr - rl) * ih) : 0.0f;
+      sr = rin ? van_leer_f((rr - rl) * ih, (rrr - rr) * ih) : 0.0f;
+      fl = rl + 0.5f * h * sl;
+      fr = rr - 0.5f * h * sr;
+    } else {
+      sl = sr = (rr - rl) / h;
+      fl = rl;
+      fr = rr;
+    }
+    float sgl = -1.0f, sgr = -1.0f, el = 0.0f, er = 0.0f, xhl = 0.0f, xhr = 0.0f;
+    if (lin) {
+      const int cl = line_cell(d, r, r.k - 1);
+      sgl = d2f_trunc(d.sigT[cl * G + g]);
+      el = d2f_trunc(d.e_eff[cl * G + g]);
+      xhl = d2f_trunc(d.xnum[cl * G + g]);
+    } else if (d.bc[sideL] == BC_BLACKBODY) {
+      sgl = d2f_trunc(d.ghost_sig[sideL * G + g]);
+      el = d2f_trunc(d.e_eff[(d.ncell + sideL) * G + g]);
+      xhl = d2f_trunc(d.xnum[(d.ncell + sideL) * G + g]);
+    }
+    if (rin) {
+      const int cr = line_cell(d, r, r.k);
+      sgr = d2f_trunc(d.sigT[cr * G + g]);
+      er = d2f_trunc(d.e_eff[cr * G + g]);
+      xhr = d2f_trunc(d.xnum[cr * G + g]);
+    } else if (d.bc[sideR] == BC_BLACKBODY) {
+      sgr = d2f_trunc(d.ghost_sig[sideR * G + g]);
+      er = d2f_trunc(d.e_eff[(d.ncell + sideR) * G + g]);
+      xhr = d2f_trunc(d.xnum[(d.ncell + sideR) * G + g]);
+    }
+    if (sgl < 0.0f) sgl = sgr;
+    if (sgr < 0.0f) sgr = sgl;
+    // harmonic-mean face opacity: x_f = dt rate 2 sl sr/(sl + sr), tau_f = dt/x_f
+    const float xf = dt * d.ratef * 2.0f * sgl * (sgr / (sgl + sgr));
+    const float tauf = dt / xf;
+    float AL, BL, AR, BR, f4, f5, c4;
+    const float ef = coef_f4_f5_c4_f(xf, &f4, &f5, &c4);
+    half_coefs_f(xf, ef, tauf, xhl, el, dt, f4, f5, c4, &AL, &BL);
+    half_coefs_f(xf, ef, tauf, xhr, er, dt, f4, f5, c4, &AR, &BR);
+    const float F = AL * (v * 0.25f) * fl - AR * (v * 0.25f) * fr + (BL * sl + BR * sr) * (v * v * (1.0f / 6.0f));
+    d.Fwave[i] = f2d_bits(F);
+  }
+}
+
 // --------------------------------------------------------------------------
 // Grid-wide barrier for the cooperative source-iteration kernel: a
 // monotonically increasing arrival counter polled with acquire loads, bounded
@@ -1682,11 +1816,14 @@ cudaError_t launch_birth_and_scan(const Dev& d, const Ens* e, cudaStream_t s) {
 }
 
 cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s) {
+  const bool f32 = d.precision == 1;   // mixed precision
   if (e && e->M > 1) {
-    k_wave<true><<<grid_for(e->total_fg, 64, 64), 64, 0, s>>>(d, *e);
+    if (f32) k_wave32<true><<<grid_for(e->total_fg, 128, 64), 128, 0, s>>>(d, *e);
+    else k_wave<true><<<grid_for(e->total_fg, 64, 64), 64, 0, s>>>(d, *e);
   } else {
     const Ens none{};
-    k_wave<false><<<grid_for((long long)d.nface * d.G, 64), 64, 0, s>>>(d, none);
+    if (f32) k_wave32<false><<<grid_for((long long)d.nface * d.G, 128), 128, 0, s>>>(d, none);
+    else k_wave<false><<<grid_for((long long)d.nface * d.G, 64), 64, 0, s>>>(d, none);
   }
   return cudaGetLastError();
 }
