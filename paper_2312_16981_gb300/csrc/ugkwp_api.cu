@@ -854,6 +854,7 @@ int ugkwp_set_state_member(ugkwp_handle* h, int member, const double* T, const d
   c.n_part[0] = (unsigned long long)n;
   c.n_part[1] = 0;
   c.step = (unsigned long long)step;
+  c.si_state_ok = 0;   // T changed: the stored iterate state is stale
   CK(cudaMemcpyAsync(d.ctrl, &c, sizeof c, cudaMemcpyHostToDevice, s), h);
   CK(cudaStreamSynchronize(s), h);
   return UGKWP_OK;

@@ -517,6 +517,9 @@ struct Ctrl {
   unsigned long long n_slow;      // survivors listed for the general particle kernel (0 at step start)
   unsigned int n_scaled_bins;     // (cell, group) bins whose survivors were scaled this step
   unsigned int si_iters32;        // FP32 warm-start iterates of the last source iteration
+  unsigned int si_state_ok;       // 1: slot 0 of the iterate state holds T^n's (the last iteration's
+                                  // final state; cleared where T changes outside the step)
+  unsigned int pad2_;
   unsigned long long err_slot[3][2];  // per-iteration max errors (double bit patterns)
   double E_rad0, E_mat0, E_rad1, E_mat1, bnd_in_macro, bnd_in_part, bnd_out_part, src_in;
 };

@@ -747,6 +747,21 @@ __device__ __forceinline__ double face_feq(const Dev& d, int f, int g, int cur) 
 // rule stops updating while the others go on (every block keeps the same
 // per-member record, so all blocks leave the loop together).
 
+// 1/T and sigma0 T^q of cell c: one rsqrt where the opacity law has T^{-1/2},
+// else a reciprocal.  Every evaluation of the iterate state takes them from
+// here, so a state computed at a temperature is bitwise the same whichever
+// pass computed it.
+__device__ __forceinline__ void inv_and_sigma_T(const Dev& d, int c, double T, double* invT, double* sT) {
+  if (d.sig_q == -0.5) {
+    const double rs = rsqrt(T);
+    *invT = rs * rs;
+    *sT = d.sigma0[c] * rs;
+  } else {
+    *invT = rcp_nr(T);
+    *sT = sigma_T(d, c, T);
+  }
+}
+
 // FP64 state of cell c at temperature T for the next iterate (slot): T^k,
 // tau = 1/(rate sigma_g), q = 1/(tau + dt), Phi_g, dPhi_g/dT (FP32)
 template <int NC>
@@ -977,7 +992,11 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const double T = d.T[c];
       if (lane == 0) e_mat0 += V * mat_energy(d, c, T);
       if (warm) si_state_f<NC>(d, c, d2f_trunc(T), 0);
-      else si_state<NC>(d, c, T, 1.0 / T, sigma_T(d, c, T));
+      else if (!d.ctrl->si_state_ok) {
+        double invT, sT;
+        inv_and_sigma_T(d, c, T, &invT, &sT);
+        si_state<NC>(d, c, T, invT, sT);
+      }
     }
     e_rad0 = warp_sum(e_rad0);
     e_src = warp_sum(e_src);
@@ -1053,7 +1072,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int c = (int)(ENS ? gc - e.cell0[m] : gc);
       const float Tf = __ldcg(d.Tk_f[itA & 1] + c);
       const double T0 = (Tf > 0.0f && Tf < INFINITY) ? f2d_bits(Tf) : d.T[c];
-      si_state<NC>(d, c, T0, rcp_nr(T0), sigma_T(d, c, T0));
+      double invT, sT;
+      inv_and_sigma_T(d, c, T0, &invT, &sT);
+      si_state<NC>(d, c, T0, invT, sT);
     }
     if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
   }
@@ -1164,17 +1185,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       dmax = warp_max_nonneg_f(dmax);
       rsum = warp_sum_f(rsum);
       float eR = rsum > 0.0f ? dmax / rsum : 0.0f;
-      // 1/T^{k+1} (and sigma0 T^q for q = -1/2) from one rsqrt where the
-      // opacity law has T^{-1/2}, else a reciprocal
       double invTn, sTn;
-      if (d.sig_q == -0.5) {
-        const double rs = rsqrt(Tnew);
-        invTn = rs * rs;
-        sTn = d.sigma0[c] * rs;
-      } else {
-        invTn = rcp_nr(Tnew);
-        sTn = sigma_T(d, c, Tnew);
-      }
+      inv_and_sigma_T(d, c, Tnew, &invTn, &sTn);
       const int ET = biased_exp(Tnew);
       const float fT = scaled_mag(Tnew, ET);
       float eT = fT < INFINITY ? scaled_mag(dT, ET) / fT : INFINITY;
@@ -1270,6 +1282,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int ran = s_conv[ENS ? m : 0] ? s_conv[ENS ? m : 0] : itB;
       const int fin = ran > 0 ? (ran & 1) : 0;
       const double T = __ldcg(d.Tk[fin] + c);
+      // the last iterate's state (at T^{n+1}) into slot 0, where the next
+      // step's iteration starts from it instead of re-evaluating it
+      if (fin == 1 && !warm) {
+        if (lane == 0) __stcg(d.Tk[0] + c, T);
+        for (int g = lane; g < G; g += 32) {
+          __stcg(d.tauk[0] + c * G + g, __ldcg(d.tauk[1] + c * G + g));
+          __stcg(d.phik[0] + c * G + g, __ldcg(d.phik[1] + c * G + g));
+        }
+      }
       if (!(T == T) || T > 1e300) bad = 1;
       if (lane == 0) {
         d.T[c] = T;
@@ -1334,6 +1355,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int ran = s_conv[ENS ? k : 0];
       cc->si_iters = (unsigned int)(ran ? ran : itB);
       cc->si_iters32 = (unsigned int)itA;
+      cc->si_state_ok = warm ? 0u : 1u;
       if (!ran) atomicOr(&cc->status, ST_NOCONV);
     }
   }
@@ -1669,7 +1691,11 @@ __global__ void k_checkpoint(const Ens e, const __grid_constant__ Dev d0, char* 
     copy_n(d.pkey[cur], (const uint32_t*)ckey, n);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (save) *saved = *d.ctrl; else *d.ctrl = *saved;
+    if (save) *saved = *d.ctrl;
+    else {
+      *d.ctrl = *saved;
+      d.ctrl->si_state_ok = 0;   // the iterate state is not part of a checkpoint
+    }
   }
 }
 
