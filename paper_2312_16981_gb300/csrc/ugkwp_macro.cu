@@ -1026,7 +1026,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     Ctrl* const ctrlA = ENS ? e.devs[0].ctrl : d0.ctrl;
     const int maxA = max_it < kWarmMaxIters ? max_it : kWarmMaxIters;
     for (; itA < maxA; ++itA, ++it) {
-      const int cur = itA & 1, nxt = cur ^ 1;
+      const int cur = itA & 1;
       if (face_pass) {
         const int G = d0.G;
         for (long long gf = gw; gf < d0.nface; gf += nw) {
@@ -1394,29 +1394,29 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
 // for their (cell, group) (a reading where the paper is silent: the particle
 // part never exceeds rho^{n+1}).  Runs after the survivor sort; a member with
 // nothing to scale returns at once.
-// Scale the weights of buffer b's first n particles by their bins' factors.
-__device__ __forceinline__ void scale_weights(const Dev& d, unsigned b, long long n) {
-  const uint32_t* __restrict__ key = d.pkey[b];
+// Scale the weights of buffer b's survivors by their bins' factors.  The
+// survivors are sorted by bin: after the scatter, bin k holds the slots
+// [sort_off[k] - sort_cnt[k], sort_off[k]), so only the bins whose factor
+// is not 1 are touched (a warp checks 32 bins, then scales each such bin's
+// run with all its lanes).  Warp w of nw over the member's bins.
+__device__ __forceinline__ void scale_weights(const Dev& d, unsigned b, long long w, long long nw) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long nb = (long long)d.ncell * d.G;
   const bool mixed = d.precision == 1;
-  // four particles per thread: one 16-byte key load, four independent gathers
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = 4 * q;
-    uint32_t k[4];
-    if (i0 + 3 < n) {
-      const uint4 kk = *reinterpret_cast<const uint4*>(key + i0);
-      k[0] = kk.x; k[1] = kk.y; k[2] = kk.z; k[3] = kk.w;
-    } else {
-      for (int r = 0; r < 4; ++r) k[r] = i0 + r < n ? key[i0 + r] : 0u;
-    }
-    double f[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) f[r] = i0 + r < n ? __ldg(d.wscale + k[r]) : 1.0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      if (f[r] == 1.0) continue;
-      if (mixed) d.fw[b][i0 + r] = (float)((double)d.fw[b][i0 + r] * f[r]);
-      else d.pw[b][i0 + r] *= f[r];
+  for (long long k0 = 32 * w; k0 < nb; k0 += 32 * nw) {
+    const long long k = k0 + lane;
+    const double f = k < nb ? d.wscale[k] : 1.0;
+    unsigned todo = __ballot_sync(full, f != 1.0);
+    while (todo) {
+      const int l = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const double fk = __shfl_sync(full, f, l);
+      const long long end = (long long)d.sort_off[k0 + l], begin = end - (long long)d.sort_cnt[k0 + l];
+      for (long long i = begin + lane; i < end; i += 32) {
+        if (mixed) d.fw[b][i] = (float)((double)d.fw[b][i] * fk);
+        else d.pw[b][i] *= fk;
+      }
     }
   }
 }
@@ -1426,8 +1426,8 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
   const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
   const Ctrl* ctrl = d.ctrl;
   if (!ctrl->scaled) return;
-  const unsigned cur = ctrl->cur;
-  scale_weights(d, cur, (long long)ctrl->n_part[cur]);
+  scale_weights(d, ctrl->cur, (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5,
+                ((long long)gridDim.x * blockDim.x) >> 5);
 }
 
 // End of step of a single problem in one launch: the sorted survivors'
@@ -1439,7 +1439,9 @@ __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev
   const unsigned live = ctrl->cur;
   const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
   const long long n = (long long)(no < cap ? no : cap);
-  if (ctrl->scaled) scale_weights(d, live, n);
+  if (ctrl->scaled)
+    scale_weights(d, live, (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5,
+                  ((long long)gridDim.x * blockDim.x) >> 5);
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
