@@ -47,7 +47,7 @@ KERNELS_PER_STEP = {"fp64": 8, "mixed": 10}
 # kernels at 4e6 particles on the slab (the traffic grows with the particles
 # processed); the roofline's "traffic" is this times the particles a launch
 # processes.  None: no capture of the current kernels.
-TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": None}
+TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": 51.7}
 
 
 def combine_replicas(ms: float, segments: float, world: int, device):
@@ -247,12 +247,16 @@ def run_reference(args):
     return 0
 
 
-# FP64 operations (an FMA counted as two) of one source iterate per (cell,
-# group) as the iterate is written (App. B): the equilibrium fluxes of its
-# faces (tau sum, reciprocal, C2 interpolant, difference), the closed-form
-# T update and the rho update, the Planck edge interpolants, group fractions
-# and derivatives, the Simpson group opacity and tau, q
-SI_FLOPS_PER_CELL_GROUP = 235
+# FP64 operations (an FMA counted as two) of the source iteration per (cell,
+# group) and FP64 iterate as the kernel executes them (App. B: the
+# equilibrium fluxes of the faces, the closed-form T and rho updates, the
+# Planck edge interpolants and group fractions, the Simpson group opacity,
+# tau and q; prologue and epilogue shared out over the iterates), counted by
+# ncu (2 x DFMA + DADD + DMUL thread instructions): the 200x30 slab, FP64
+# build, 3 iterates a launch; the 2D checkerboard, mixed build with the FP32
+# warm start, 4 FP64 iterates a launch (its FP32 iterates add time, not FP64
+# operations).  3D takes the 2D figure.
+SI_FLOPS_PER_CELL_GROUP = {1: 235, 2: 197, 3: 197}
 # FP64 peak of the chip: 152 SMs x 4 sub-partitions x 0.5 FMA lanes a cycle
 # x 2 flops x the maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
@@ -280,13 +284,13 @@ def roofline(p, phase, launch_ms, n_proc, n_read, n_out, si_iters, mixed, pk, sr
     it moves a few arrays of cells x groups per iterate, far from any HBM
     bound)."""
     if phase == "source_iteration":
-        flops = SI_FLOPS_PER_CELL_GROUP * p.ncell * p.G * si_iters
+        flops = SI_FLOPS_PER_CELL_GROUP[p.dim] * p.ncell * p.G * si_iters
         ach = flops / (launch_ms * 1e-3) / 1e12
         return {"kernel": "k_si", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "FP64 pipe from unit counts and the maximum SM clock (152 SMs x 4 x 0.5 FMA/cycle x 2 x 2.07 GHz)",
                 "algorithmic_flops_per_launch": flops, "iterates_per_launch": si_iters, "launch_ms": launch_ms,
-                "note": "FP64 operations of the iterate as written, %d per (cell, group); latency-bound on small grids" % SI_FLOPS_PER_CELL_GROUP}
+                "note": "FP64 operations of the kernel, %d per (cell, group) and FP64 iterate (ncu count); latency-bound on small grids" % SI_FLOPS_PER_CELL_GROUP[p.dim]}
     abytes = algorithmic_bytes(p, phase, n_read, n_out, si_iters, mixed=mixed)
     ach = abytes / (launch_ms * 1e-3) / 1e9 if abytes else 0.0
     tpp = TRAFFIC_PER_PROCESSED["mixed" if mixed else "fp64"]
