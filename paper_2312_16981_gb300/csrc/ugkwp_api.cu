@@ -195,8 +195,6 @@ void carve(const ugkwp_problem* p, Carver& cv, Dev& d, double** src_T_tmp) {
   d.invT_f = mixed ? cv.take<float>(nc) : nullptr;
   d.omega_f = mixed ? cv.take<float>(nb) : nullptr;
   d.khat_f = mixed ? cv.take<float>(nb) : nullptr;
-  d.slow_i = mixed ? cv.take<uint32_t>(P) : nullptr;
-  d.slow_t = mixed ? cv.take<float>(P) : nullptr;
   for (int k = 0; k < 2; ++k) {
     d.Tk_f[k] = mixed ? cv.take<float>(nc) : nullptr;
     d.tau_f[k] = mixed ? cv.take<float>(ncg) : nullptr;

@@ -330,12 +330,6 @@ struct Dev {
   float* omega_f;   // [nbins]
   float* khat_f;    // [nbins]
   float* nu_edges_f;       // [G+1] group edges in FP32
-  // mixed precision, single problems with few face crossings: the survivors
-  // whose first flight ends at a face, listed by the survivor kernel for the
-  // general one (slot in the input, remaining free time, negative if it ends
-  // in a collision)
-  uint32_t* slow_i;        // [capacity]
-  float* slow_t;           // [capacity]
   const double* nu_pow;    // [3*G] nu^p at the lower edge, midpoint and upper edge of each group
   void* particles_begin;   // first particle buffer (start of the part left uninitialised)
   // control block and optional records
@@ -514,7 +508,7 @@ struct Ctrl {
   unsigned int scaled;            // some survivors' weights need scaling this step
   unsigned int fin_count;         // blocks done in the end-of-step kernel (0 between steps)
   unsigned long long tile_next;   // next particle tile to hand out (particle kernel; 0 at step start)
-  unsigned long long n_slow;      // survivors listed for the general particle kernel (0 at step start)
+  unsigned long long pad3_;
   unsigned int n_scaled_bins;     // (cell, group) bins whose survivors were scaled this step
   unsigned int si_iters32;        // FP32 warm-start iterates of the last source iteration
   unsigned int si_state_ok;       // 1: slot 0 of the iterate state holds T^n's (the last iteration's

@@ -120,7 +120,6 @@ __global__ void k_birth(const __grid_constant__ Dev d0, const Ens e) {
     ctrl->bar_count = 0;
     ctrl->scaled = 0;
     ctrl->tile_next = 0;
-    ctrl->n_slow = 0;
     ctrl->n_scaled_bins = 0;
     for (int s = 0; s < 3; ++s) ctrl->err_slot[s][0] = ctrl->err_slot[s][1] = 0ull;
     ctrl->E_rad0 = ctrl->E_mat0 = ctrl->E_rad1 = ctrl->E_mat1 = 0.0;

@@ -1085,14 +1085,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // per-cell factors in shared memory: every survivor draws its free time
 // (Eq. particle-tf-formula) and takes its first flight; one that ends the
 // step there is finished in place (no face crossed, so only E_surv and the
-// counters are tallied); one that reaches a face first is listed (slot,
-// remaining free time) for k_stream32_rest, which streams it with the
-// newborns.  The code a survivor runs here has no crossing loop, no birth
-// sampling and no per-particle branching on the problem's options, so a
-// warp's lanes stay together.  The list is filled through a per-warp buffer
-// in shared memory, 32 entries (one atomic) at a time.  P3: sigma ~ nu^-3.
+// counters are tallied); one that reaches a face first is set aside (slot,
+// remaining free time) in a per-warp buffer in shared memory.  The code of
+// that first flight has no crossing loop, no birth sampling and no
+// per-particle branching on the problem's options, so a warp's lanes stay
+// together; whenever 32 survivors are set aside, the warp streams them
+// through their faces, one per lane (and the rest after its last chunk).
+// P3: sigma ~ nu^-3.
 template <int NT, bool P3>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
     k_stream32_fast(const __grid_constant__ Dev d, int rounds) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ uint64_t s_full[NT / 32][kStages];
@@ -1137,19 +1138,54 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
   int acc_key = -1;
   long long acc_w = 0;
   unsigned acc_n = 0u;
-  unsigned nl = 0;   // entries in the warp's list buffer (same in every lane)
-  auto flush_list = [&](unsigned k) {   // the first k buffered entries to the global list
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&ctrl->n_slow, (unsigned long long)k);
-    base = __shfl_sync(full, base, 0);
-    if ((unsigned)lane < k) {
-      d.slow_i[base + lane] = s_li[warp][lane];
-      d.slow_t[base + lane] = s_lt[warp][lane];
+  unsigned nl = 0;   // entries in the warp's buffer of set-aside survivors (same in every lane)
+  Counters cnt;
+  // the first k set-aside survivors, one per lane: state from the input
+  // buffer, the free time from the buffer, the streaming loop from their
+  // first face (draw 0 of the step was the free time), stored, tallied and
+  // counted like every other particle; the rest of the buffer moves to the front
+  auto run_set_aside = [&](unsigned k) {
+    const bool act = (unsigned)lane < k;
+    P32 q;
+    clear32(q);
+    DrawsF rng;
+    long long i = 0;
+    if (act) {
+      i = (long long)s_li[warp][lane];
+      const float tl = s_lt[warp][lane];
+      q.xi = d.fx[h0.cur][i];
+      q.ox = d.fox[h0.cur][i];
+      q.nu = d.fnu[h0.cur][i];
+      q.w = d.fw[h0.cur][i];
+      q.id = d.pid[h0.cur][i];
+      decode_key32<1>(d, d.pkey[h0.cur][i], q);
+      q.collided = tl < 0.0f;
+      q.t_rem = fabsf(tl);
+      rng.init(q.id, h0.step, 1u);
+    } else {
+      rng.init(0ull, h0.step, 0u);
+    }
+    q.cell0 = q.cx;
+    const float inup = (!act || grey) ? 1.0f : pow_fast_f(q.nu, -spf);
+    if (act) stream_loop32<1>(d, q, rng, inup, ncell, false, s_sinv, s_sinv + ncell);
+    const int cell = q.cx;
+    bool stored = false;
+    if (act) stored = store32<1>(d, nxb, q, i, cell);
+    const long long wq = act ? to_fixed_f(q.w, tq_shift, &ctrl->status) : 0ll;
+    warp_run_add_fixed(d.Esq, stored ? cell * (int)G + q.g : -1 - lane, wq, d.sort_cnt);
+    if (act) {
+      cross_tallies32(d, q, cell, wq);
+      cnt.seg += (unsigned)q.nseg;
+      cnt.abs += q.fate == FATE_ABSORBED;
+      cnt.esc += q.fate == FATE_ESCAPED;
+      cnt.surv += q.fate == FATE_SURVIVED;
+      cnt.rem += q.fate == FATE_REMOVED;
+      record32<1>(d, q, i, cell);
     }
     __syncwarp();
     uint32_t a = 0u;
     float b = 0.0f;
-    const bool mv = (unsigned)lane < nl - k;   // keep the rest at the front
+    const bool mv = (unsigned)lane < nl - k;
     if (mv) { a = s_li[warp][k + lane]; b = s_lt[warp][k + lane]; }
     __syncwarp();
     if (mv) { s_li[warp][lane] = a; s_lt[warp][lane] = b; }
@@ -1157,7 +1193,6 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
     nl -= k;
   };
 
-  Counters cnt;
   int k = 0, st = 0;
   unsigned par = 0u;   // stage st of chunk k, and the phase parity it waits for
   for (long long c = c0; c < nchunks; ++c, ++k, st = st + 1 == kStages ? 0 : st + 1, par ^= st == 0 ? 1u : 0u) {
@@ -1199,8 +1234,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
       const float dist = ox > 0.0f ? dxf - xi : xi;
       const float tf = fmaxf(dist, 0.0f) * rcp_approx(vf * fabsf(ox));
       const bool later = valid && tf < t_rem;
-      // listed for the general kernel: the slot and t_rem, negative when the
-      // flight ends in a collision
+      // set aside: the slot and t_rem, negative when the flight ends in a collision
       const unsigned lmask = __ballot_sync(full, later);
       if (later) {
         const unsigned pos = nl + __popc(lmask & ((1u << lane) - 1u));
@@ -1209,7 +1243,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
       }
       __syncwarp();
       nl += __popc(lmask);
-      if (nl >= 32u) flush_list(32u);
+      if (nl >= 32u) run_set_aside(32u);
       const bool fin = valid && !later;
       const float xn = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
       if (fin) {   // in place: slot i of the other buffer (i < n_surv <= capacity)
@@ -1257,7 +1291,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
     }
     __syncwarp();
   }
-  if (nl) flush_list(nl);
+  if (nl) run_set_aside(nl);
   // the last runs: the warp's lanes mostly end in the same bin
   warp_run_add_fixed_n(d.Esq, acc_n ? acc_key : -1 - lane, acc_w, acc_n, d.sort_cnt);
   if (lane == 0)
@@ -1265,20 +1299,18 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (NT >= 256 ? 4 : 8))
   flush_counters_block(ctrl, cnt);
 }
 
-// The rest of a step after k_stream32_fast: the listed survivors (their
-// state from the input buffer, their free time from the list, the streaming
-// loop from their first face) and the newborns, one particle per thread.
-// mode 0: both; 1: the newborns only (they need nothing from the survivor
-// kernel, so a step graph runs them beside it); 2: the listed survivors
-// only.  The birth offsets are searched in shared memory when they fit.
+// The newborns of a step whose survivors take k_stream32_fast, one per
+// thread (they need nothing from the survivor kernel, so a step graph runs
+// them beside it).  The birth offsets are searched in shared memory when
+// they fit.
 constexpr int kSmemBins = 8192;
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ Dev d, int mode) {
+__global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ Dev d) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   const int lane = threadIdx.x & 31;
   const Tab32 tab = load_tab32<false>(d, s_dyn);
-  const bool off_sm = mode != 2 && d.nbins + 1 <= kSmemBins;
+  const bool off_sm = d.nbins + 1 <= kSmemBins;
   uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dyn + tab32_bytes(tab));
   if (off_sm)
     for (int b = threadIdx.x; b <= d.nbins; b += blockDim.x) s_off[b] = __ldg(d.off + b);
@@ -1286,48 +1318,31 @@ __global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ D
   const uint32_t* off = off_sm ? s_off : d.off;
   const StepHead h0 = step_head(d);
   Ctrl* ctrl = d.ctrl;
-  const long long n_slow = mode == 1 ? 0 : (long long)ctrl->n_slow;
-  const long long n_new = mode == 2 ? 0 : h0.n_tot - h0.n_surv;
-  const long long total = n_slow + n_new;
+  const long long total = h0.n_tot - h0.n_surv;
   const unsigned cur = h0.cur, nxb = cur ^ 1u;
   const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
   Counters cnt;
   const long long stride = (long long)gridDim.x * blockDim.x;
   // whole warps to the loop bound, so the warp intrinsics see every lane
   const long long bound = (total + 31) & ~31ll;
+  (void)cur;
   for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < bound; jj += stride) {
     const bool valid = jj < total;
     P32 q;
     clear32(q);
     DrawsF rng;
     long long i = 0;
-    bool listed = false;
-    if (valid && jj < n_slow) {
-      listed = true;
-      i = (long long)d.slow_i[jj];
-      const float tl = d.slow_t[jj];
-      q.xi = d.fx[cur][i];
-      q.ox = d.fox[cur][i];
-      if (DIM >= 2) { q.eta = d.fy[cur][i]; q.oy = d.foy[cur][i]; }
-      if (DIM == 3) { q.zeta = d.fz[cur][i]; q.oz = d.foz[cur][i]; }
-      q.nu = d.fnu[cur][i];
-      q.w = d.fw[cur][i];
-      q.id = d.pid[cur][i];
-      decode_key32<DIM>(d, d.pkey[cur][i], q);
-      q.collided = tl < 0.0f;
-      q.t_rem = fabsf(tl);
-      rng.init(q.id, h0.step, 1u);   // the free-time draw was draw 0
-    } else if (valid) {
-      i = h0.n_surv + (jj - n_slow);
-      birth32<DIM>(d, q, rng, (uint32_t)(jj - n_slow), h0.step, off);
+    if (valid) {
+      i = h0.n_surv + jj;
+      birth32<DIM>(d, q, rng, (uint32_t)jj, h0.step, off);
     } else {
       rng.init(0ull, h0.step, 0u);
     }
     q.cell0 = q.gside >= 0 ? q.cx : (q.cz * ny + q.cy) * nx + q.cx;
     q.ghost = q.gside >= 0;
     const float inup = (!valid || d.grey) ? 1.0f : pow_fast_f(q.nu, -d.spf);
-    bool more = listed;
-    if (valid && !listed) more = first_flight32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
+    bool more = false;
+    if (valid) more = first_flight32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
     if (more) stream_loop32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
     const int cell = (q.cz * ny + q.cy) * nx + q.cx;
     bool stored = false;
@@ -1368,17 +1383,16 @@ static cudaError_t launch_stream64_t(const Dev& d, const Ens& e, const StreamSha
 
 static size_t table32_bytes(const Dev& d) { return (4 * (size_t)stream32_table_floats(d) + 127) & ~(size_t)127; }
 
-// the survivor kernel's companion: mode 0 listed survivors and newborns, 1
-// newborns only, 2 listed survivors only
+// the survivor kernel's companion: the newborns
 template <int DIM>
-static cudaError_t launch_rest32(const Dev& d, int mode, cudaStream_t s) {
+static cudaError_t launch_rest32(const Dev& d, cudaStream_t s) {
   const size_t tab = table32_bytes(d);
-  const size_t offb = (mode != 2 && d.nbins + 1 <= kSmemBins) ? 4 * (size_t)(d.nbins + 1) : 0;
+  const size_t offb = d.nbins + 1 <= kSmemBins ? 4 * (size_t)(d.nbins + 1) : 0;
   const size_t dyn = tab + offb;
   if (dyn > 48 * 1024) cudaFuncSetAttribute(k_stream32_rest<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  // enough threads to hold every listed survivor and newborn of a typical
-  // step at once (their chains are latency-bound)
-  k_stream32_rest<DIM><<<sm_count() * 4, 256, dyn, s>>>(d, mode);
+  // enough threads to hold every newborn of a typical step at once (their
+  // chains are latency-bound)
+  k_stream32_rest<DIM><<<sm_count() * 4, 256, dyn, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -1397,8 +1411,8 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
   const int bi = NT == 128 ? 0 : (NT == 512 ? 2 : 1);
   // a 1D problem whose particles seldom reach a face in a step (a particle
   // crosses at most v dt / dx cells) with the power-law opacity held in
-  // shared memory: the survivor kernel, then the general kernel for the
-  // listed survivors and the newborns
+  // shared memory: the survivor kernel, and the newborns' kernel (on a side
+  // stream of the step graph, else after it)
   const bool split = !ENS && DIM == 1 && split32(d);
   const bool p3 = !d.grey && d.sig_p == -3.0;
   const void* fn = !split ? (const void*)k_stream32<DIM, ENS, NT>
@@ -1420,8 +1434,8 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
   if (p3) k_stream32_fast<NT, true><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
   else k_stream32_fast<NT, false><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
   cudaError_t r = cudaGetLastError();
-  if (r) return r;
-  return launch_rest32<DIM>(d, newborns_elsewhere ? 2 : 0, s);
+  if (r || newborns_elsewhere) return r;
+  return launch_rest32<DIM>(d, s);
 }
 
 template <int DIM, bool ENS>
@@ -1453,7 +1467,7 @@ bool stream_newborns_apart(const Dev& d, const Ens* e) {
   return !(e && e->M > 1) && d.precision == 1 && split32(d);
 }
 
-cudaError_t launch_stream_newborns(const Dev& d, cudaStream_t s) { return launch_rest32<1>(d, 1, s); }
+cudaError_t launch_stream_newborns(const Dev& d, cudaStream_t s) { return launch_rest32<1>(d, s); }
 
 cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s, bool newborns_elsewhere) {
   const int mixed = d.precision == 1;
