@@ -146,6 +146,12 @@ typedef struct ugkwp_problem {
    * 0 (default): on where the iteration has at least 2^17 (cell, group)
    * pairs (over all ensemble members); 1: on; -1: off.  Ignored in FP64. */
   int32_t si_warm32;
+  /* Source iteration of a single 1D problem of at most two cells per SM
+   * (without the FP32 warm start): 0 (default): two warps per cell, which
+   * share each iterate's work (the same results, bit for bit); -1: one warp
+   * per cell. */
+  int32_t si_pair;
+  int32_t _pad6;
 } ugkwp_problem;
 
 typedef struct ugkwp_handle ugkwp_handle;

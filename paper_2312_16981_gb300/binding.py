@@ -50,6 +50,7 @@ class CProblem(C.Structure):
         ("cv_chi", C.c_double),
         ("nz", C.c_int32), ("bc_z", C.c_int32 * 2), ("_pad3", C.c_int32), ("dz", C.c_double),
         ("bcT_z", C.c_double * 2), ("split_literal", C.c_int32), ("si_warm32", C.c_int32),
+        ("si_pair", C.c_int32), ("_pad6", C.c_int32),
     ]
 
 
@@ -216,6 +217,7 @@ class _HostProblem:
         s.bcT_z[0], s.bcT_z[1] = float(bcT[4]), float(bcT[5])
         s.split_literal = int(getattr(p, "split_literal", 0))
         s.si_warm32 = int(getattr(p, "si_warm32", 0))
+        s.si_pair = int(getattr(p, "si_pair", 0))
         self.s = s
         self._keep = keep
 

@@ -113,6 +113,7 @@ int validate(const ugkwp_problem* p, ugkwp_handle* h) {
     return fail(h, UGKWP_ERR_ARG, "precision must be UGKWP_FP64 or UGKWP_MIXED");
   if (p->particle_capacity < 1) return fail(h, UGKWP_ERR_ARG, "particle_capacity must be >= 1");
   if (p->si_warm32 < -1 || p->si_warm32 > 1) return fail(h, UGKWP_ERR_ARG, "si_warm32 must be -1, 0 or 1");
+  if (p->si_pair != 0 && p->si_pair != -1) return fail(h, UGKWP_ERR_ARG, "si_pair must be 0 or -1");
   if (!(p->tau_num_C >= 0.0)) return fail(h, UGKWP_ERR_ARG, "tau_num_C must be >= 0");
   if (p->sig_law < 0 || p->sig_law > 2) return fail(h, UGKWP_ERR_ARG, "sig_law must be 0, 1 or 2");
   if (p->sig_law == 2 && p->grey) return fail(h, UGKWP_ERR_ARG, "sig_law 2 (Olson foam) needs groups (grey = 0)");
@@ -324,6 +325,7 @@ void fill_scalars(const ugkwp_problem* p, Dev& d) {
   d.inv_cf = (float)d.inv_c;
   for (int a = 0; a < 3; ++a) d.feq_kf[a] = (float)d.feq_k[a];
   d.si_warm = 0;   // set once the ensemble's size is known
+  d.pair_si = p->si_pair == -1 ? 0 : 1;
   // bin and cell indices below 2^24 divide by G and nx through an FP32 reciprocal
   d.fastdiv = (long long)d.ncell * d.G < (1ll << 24) ? 1 : 0;
   d.invG_f = 1.0f / (float)d.G;

@@ -292,6 +292,7 @@ struct Dev {
   float* dphik;     // [ncell*G] dPhi_g/dT of the iterate (FP32: it sets only the contraction rate)
   // FP32 warm start of the source iteration (mixed precision; null otherwise)
   int si_warm;      // 1: FP32 iterates before the FP64 ones this step
+  int pair_si;      // 1: two warps per cell where the source iteration allows it
   float* Tk_f[2];   // [ncell]
   float* tau_f[2];  // [ncell*G]
   float* phi_f[2];  // [ncell*G]

@@ -762,26 +762,31 @@ __device__ __forceinline__ void inv_and_sigma_T(const Dev& d, int c, double T, d
 }
 
 // FP64 state of cell c at temperature T for the next iterate (slot): T^k,
-// tau = 1/(rate sigma_g), q = 1/(tau + dt), Phi_g, dPhi_g/dT (FP32)
-template <int NC>
+// tau = 1/(rate sigma_g), q = 1/(tau + dt), Phi_g, dPhi_g/dT (FP32).
+// PART 1: T^k, Phi_g, dPhi_g/dT; 2: tau, q (two warps of a cell share it).
+template <int NC, int PART = 0>
 __device__ __forceinline__ void si_state(const Dev& d, int c, double T, double invT, double sT, int slot = 0) {
   const int lane = threadIdx.x & 31, G = d.G;
   double sg[NC], ph[NC];
   float dp[NC];
-  si_planck<NC>(d, T, invT, sT, sg, ph, dp);
+  si_planck<NC, PART>(d, T, invT, sT, sg, ph, dp);
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
     const int g = lane + 32 * j;
     if (g < G) {
-      double tau, qv;
-      tau_and_q(d, sg[j], &tau, &qv);
-      __stcg(d.tauk[slot] + c * G + g, tau);
-      __stcg(d.qk + c * G + g, qv);
-      __stcg(d.phik[slot] + c * G + g, ph[j]);
-      __stcg(d.dphik + c * G + g, dp[j]);
+      if (PART != 1) {
+        double tau, qv;
+        tau_and_q(d, sg[j], &tau, &qv);
+        __stcg(d.tauk[slot] + c * G + g, tau);
+        __stcg(d.qk + c * G + g, qv);
+      }
+      if (PART != 2) {
+        __stcg(d.phik[slot] + c * G + g, ph[j]);
+        __stcg(d.dphik + c * G + g, dp[j]);
+      }
     }
   }
-  if (lane == 0) __stcg(d.Tk[slot] + c, T);
+  if (lane == 0 && PART != 2) __stcg(d.Tk[slot] + c, T);
 }
 
 // ---- FP32 warm start (mixed precision)
@@ -927,10 +932,21 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
   return eT;
 }
 
-template <int NC, bool ENS>
+// PAIR (single 1D problems of at most two cells per SM, FP64 iterates
+// only): two warps per cell, one block each, so that a cell's chain of
+// dependent FP64 instructions is split over two SM sub-partitions.  In an
+// iterate each warp evaluates one of the cell's two faces and they exchange
+// the fluxes through shared memory; both form Q, the sums and T^{k+1} (the
+// same operations, so the same bits); then warp 0 updates rho and evaluates
+// the Planck values while warp 1 evaluates the opacities, tau and q.
+// Outside the iterates warp 0 does the cell's work.  The results are
+// bitwise those of one warp per cell.
+template <int NC, bool ENS, bool PAIR>
 __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, const Ens e) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-  const long long gw = blockIdx.x * (long long)nwb + wib, nw = (long long)gridDim.x * nwb;
+  const long long gw = PAIR ? (long long)blockIdx.x : blockIdx.x * (long long)nwb + wib;
+  const long long nw = PAIR ? (long long)gridDim.x : (long long)gridDim.x * nwb;
+  const bool lead = !PAIR || wib == 0;
   const long long total = ENS ? e.total_cells : (long long)d0.ncell;
   const int M = ENS ? e.M : 1;
   unsigned int* bar_count = ENS ? e.bar : &d0.ctrl->bar_count;
@@ -940,13 +956,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   __shared__ float s_err[8][2];
   __shared__ int s_conv[ENS ? kMaxEnsemble : 1];   // iterate count at convergence, 0 = still running
   __shared__ int s_any;
+  __shared__ double s_pair[PAIR ? 2 : 1][PAIR ? 32 * NC : 1];   // PAIR: the two faces' fluxes
   unsigned int bar = 0;
 
   // ---- prologue
   {
     double e_rad0 = 0.0, e_mat0 = 0.0, e_src = 0.0;
     int acc_m = -1;
-    for (long long gc = gw; gc < total; gc += nw) {
+    for (long long gc = lead ? gw : total; gc < total; gc += nw) {
       const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
       if (ENS && m != acc_m && acc_m >= 0) {
         e_rad0 = warp_sum(e_rad0);
@@ -1019,7 +1036,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   // scarce unit on this chip; in 1D the extra barrier costs more than the
   // second evaluation of a face saves)
   const bool face_pass = !ENS && d0.dim >= 2;
-  if (warm) {
+  if (warm && !PAIR) {
     // FP32 iterates from T^n while the largest |dT|/T falls: until it is
     // within kWarmTol, stalls near FP32 resolution, or kWarmMaxIters pass
     Ctrl* const ctrlA = ENS ? e.devs[0].ctrl : d0.ctrl;
@@ -1121,7 +1138,18 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
             q = fma(d.dt_h[axis], Fin - Fout, q);
           }
         }
-        for (int axis = 0; axis < (face_pass ? 0 : d.dim); ++axis) {
+        if (PAIR) {
+          // this warp's face: warp 0 the lower, warp 1 the upper
+          const int dir = wib ? 1 : -1;
+          double tn, pn;
+          int nc;
+          double F = 0.0;
+          if (neighbour(d, ix, iy, iz, 0, dir, g, cur, tc, &tn, &pn, &nc))
+            F = dir < 0 ? feq_face_si(d, tn, tc, pn, phc[j], 0) : feq_face_si(d, tc, tn, phc[j], pn, 0);
+          if (dir > 0 || nc < 0) d.Feq[face_index_xyz(d, ix, iy, iz, 0, dir) * G + g] = F;
+          s_pair[PAIR ? wib : 0][PAIR ? 32 * j + lane : 0] = F;
+        }
+        for (int axis = 0; axis < ((face_pass || PAIR) ? 0 : d.dim); ++axis) {
           double Fin = 0.0, Fout = 0.0;
           for (int dir = -1; dir <= 1; dir += 2) {
             double tn, pn;
@@ -1140,9 +1168,24 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         const double qi = __ldcg(d.qk + i);   // 1/(tau + dt), stored with tau
         r1[j] = tc * qi;
         ar[j] = dt * qi;
-        const double ap = ar[j] * d.inv_c;
-        num = fma(ap, fma(dpc[j], Tc, q - phc[j]), num);
-        den = fma(ap, dpc[j], den);
+        if (!PAIR) {
+          const double ap = ar[j] * d.inv_c;
+          num = fma(ap, fma(dpc[j], Tc, q - phc[j]), num);
+          den = fma(ap, dpc[j], den);
+        }
+      }
+      if (PAIR) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          if (lane + 32 * j >= G) continue;
+          const int k = PAIR ? 32 * j + lane : 0;
+          Q[j] = fma(d.dt_h[0], s_pair[0][k] - s_pair[PAIR ? 1 : 0][k], Q[j]);
+          const double ap = ar[j] * d.inv_c;
+          num = fma(ap, fma(dpc[j], Tc, Q[j] - phc[j]), num);
+          den = fma(ap, dpc[j], den);
+        }
+        __syncthreads();   // both warps have read the exchange before a next cell writes it
       }
       warp_sum2(num, den);
       // a T-dependent heat capacity: e(T^{k+1}) ~ e(T^k) + C_v(T^k) (T^{k+1} - T^k)
@@ -1160,6 +1203,13 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (!nan && tb < kBits1em30) Tnew = 1e-30;
       }
       const double dT = Tnew - Tc;
+      double invTn, sTn;
+      inv_and_sigma_T(d, c, Tnew, &invTn, &sTn);
+      if (PAIR && wib) {
+        // warp 1 of the pair: the opacities, tau and q at T^{k+1}
+        si_state<NC, 2>(d, c, Tnew, invTn, sTn, nxt);
+        continue;
+      }
       double r[NC], dr[NC];
       int ex = 0;
 #pragma unroll
@@ -1184,8 +1234,6 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       dmax = warp_max_nonneg_f(dmax);
       rsum = warp_sum_f(rsum);
       float eR = rsum > 0.0f ? dmax / rsum : 0.0f;
-      double invTn, sTn;
-      inv_and_sigma_T(d, c, Tnew, &invTn, &sTn);
       const int ET = biased_exp(Tnew);
       const float fT = scaled_mag(Tnew, ET);
       float eT = fT < INFINITY ? scaled_mag(dT, ET) / fT : INFINITY;
@@ -1201,7 +1249,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         werrT = fmaxf(werrT, eT);
         werrR = fmaxf(werrR, eR);
       }
-      si_state<NC>(d, c, Tnew, invTn, sTn, nxt);
+      if (PAIR) si_state<NC, 1>(d, c, Tnew, invTn, sTn, nxt);
+      else si_state<NC>(d, c, Tnew, invTn, sTn, nxt);
     }
     if (!ENS) {
       Ctrl* ctrl = d0.ctrl;
@@ -1255,7 +1304,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   {
     double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
     int bad = 0, scaled = 0, acc_m = -1;
-    for (long long gc = gw; gc < total; gc += nw) {
+    for (long long gc = lead ? gw : total; gc < total; gc += nw) {
       const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
       if (ENS && m != acc_m && acc_m >= 0) {
         e_rad1 = warp_sum(e_rad1);
@@ -1855,24 +1904,22 @@ cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-static int g_si_blocks[2][2][2] = {};
+static int g_si_blocks[2][2][3] = {};
 
 // One warp per cell.  On GB300 the FP64 pipe of an SM is the limit of this
 // kernel, so a small grid is spread one warp per block over all SMs; a large
 // grid uses 8-warp blocks (fewer arrivals at the grid barrier).
-template <int NC, bool ENS>
+template <int NC, bool ENS, bool PAIR>
 static cudaError_t launch_si_t(const Dev& d, const Ens& e, long long ncell, cudaStream_t s) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int small = ncell <= 8 * sms;
-  const int threads = small ? 32 : 256;
-  int& per = g_si_blocks[NC - 1][ENS][small];
+  const int threads = PAIR ? 64 : (small ? 32 : 256);
+  int& per = g_si_blocks[NC - 1][ENS][PAIR ? 2 : small];
   if (!per) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_si<NC, ENS>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_si<NC, ENS, PAIR>, threads, 0);
     if (per < 1) per = 1;
   }
-  const long long want = (ncell * 32 + threads - 1) / threads;
+  const long long want = PAIR ? ncell : (ncell * 32 + threads - 1) / threads;
   const long long maxb = (long long)sms * per;
   int blocks = (int)(want < maxb ? want : maxb);
   if (blocks < 1) blocks = 1;
@@ -1886,18 +1933,25 @@ static cudaError_t launch_si_t(const Dev& d, const Ens& e, long long ncell, cuda
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_si<NC, ENS>, d, e);
+  return cudaLaunchKernelEx(&cfg, k_si<NC, ENS, PAIR>, d, e);
 }
 
 cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
     if (e->M > kMaxEnsemble) return cudaErrorInvalidValue;
-    if (e->max_G > 32) return launch_si_t<2, true>(d, *e, e->total_cells, s);
-    return launch_si_t<1, true>(d, *e, e->total_cells, s);
+    if (e->max_G > 32) return launch_si_t<2, true, false>(d, *e, e->total_cells, s);
+    return launch_si_t<1, true, false>(d, *e, e->total_cells, s);
   }
   const Ens none{};
-  if (d.G > 32) return launch_si_t<2, false>(d, none, d.ncell, s);
-  return launch_si_t<1, false>(d, none, d.ncell, s);
+  // a 1D grid of at most two cells per SM, FP64 iterates only: two warps per
+  // cell (one warp per cell would leave most SM sub-partitions idle)
+  const bool pair = d.dim == 1 && !d.si_warm && d.ncell <= 2 * sm_count() && d.pair_si;
+  if (d.G > 32) {
+    if (pair) return launch_si_t<2, false, true>(d, none, d.ncell, s);
+    return launch_si_t<2, false, false>(d, none, d.ncell, s);
+  }
+  if (pair) return launch_si_t<1, false, true>(d, none, d.ncell, s);
+  return launch_si_t<1, false, false>(d, none, d.ncell, s);
 }
 
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {

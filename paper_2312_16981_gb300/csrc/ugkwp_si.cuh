@@ -145,8 +145,9 @@ __device__ __forceinline__ EdgeSI planck_edge_si(double x) {
 
 // Planck quantities of one cell at temperature T (> 0 or not) for the lane's
 // groups g = lane + 32 j: sigma_g and Phi_g in FP64, dPhi_g/dT in FP32.
-// The same operations as cell_planck for sigma_g and Phi_g.
-template <int NC>
+// The same operations as cell_planck for sigma_g and Phi_g.  PART 1: Phi_g
+// and dPhi_g/dT only; 2: sigma_g only (two warps of a cell share the work).
+template <int NC, int PART = 0>
 __device__ __forceinline__ void si_planck(const Dev& d, double T, double invT, double sT, double* sig,
                                           double* phi, float* dphi) {
   const int lane = threadIdx.x & 31, G = d.G;
@@ -163,6 +164,10 @@ __device__ __forceinline__ void si_planck(const Dev& d, double T, double invT, d
       dphi[j] = Tpos ? 4.0f * acT3f : 0.0f;
       continue;
     }
+    if (PART == 2) {
+      sig[j] = g < G ? sigma_group_at(d, sT, T, invT, g) : 1.0;
+      continue;
+    }
     EdgeSI lo;
     if (g <= G && Tpos) lo = planck_edge_si(d.nu_edges[g] * invT);
     else { lo.V = 0.0; lo.g4 = 0.0f; lo.lower = true; }
@@ -172,7 +177,7 @@ __device__ __forceinline__ void si_planck(const Dev& d, double T, double invT, d
     hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
     if (lane == 31 && g + 1 <= G && Tpos) hi = planck_edge_si(d.nu_edges[g + 1] * invT);
     if (g < G) {
-      sig[j] = sigma_group_at(d, sT, T, invT, g);
+      sig[j] = PART == 1 ? 1.0 : sigma_group_at(d, sT, T, invT, g);
       if (Tpos) {
         double I;
         if (hi.lower) I = hi.V - lo.V;

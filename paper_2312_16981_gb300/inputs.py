@@ -57,6 +57,7 @@ class Problem:
     sig_law: int = 0         # 0: sigma0 nu^p T^q; 1: times (1 - e^{-nu/T}) (Larsen case)
     split_literal: int = 0   # 1: I^h = I^{n+1} - I^p as written (no survivor weight scaling)
     si_warm32: int = 0       # mixed precision: FP32 iterates before the FP64 ones (0 auto, 1 on, -1 off)
+    si_pair: int = 0         # small 1D grids: two warps per cell in the source iteration (0 auto, -1 off)
     method: int = 0          # 0: UGKWP (sample the collisionless part); 1: UGKP (sample all of I^h)
     nz: int = 1              # 3D: cells along z (dim 3); sides 4, 5 of bc/bcT are z- and z+
     dz: float = 1.0
