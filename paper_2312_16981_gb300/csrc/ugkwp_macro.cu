@@ -937,8 +937,8 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
 // dependent FP64 instructions is split over two SM sub-partitions.  In an
 // iterate each warp evaluates one of the cell's two faces and they exchange
 // the fluxes through shared memory; both form Q, the sums and T^{k+1} (the
-// same operations, so the same bits); then warp 0 updates rho and evaluates
-// the Planck values while warp 1 evaluates the opacities, tau and q.
+// same operations, so the same bits); then warp 0 evaluates the Planck
+// values while warp 1 updates rho and evaluates the opacities, tau and q.
 // Outside the iterates warp 0 does the cell's work.  The results are
 // bitwise those of one warp per cell.
 template <int NC, bool ENS, bool PAIR>
@@ -966,8 +966,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     for (long long gc = lead ? gw : total; gc < total; gc += nw) {
       const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
       if (ENS && m != acc_m && acc_m >= 0) {
-        e_rad0 = warp_sum(e_rad0);
-        e_src = warp_sum(e_src);
+        warp_sum2(e_rad0, e_src);
         if (lane == 0) {
           Ctrl* cc = e.devs[acc_m].ctrl;
           atomicAdd(&cc->E_rad0, e_rad0);
@@ -1014,8 +1013,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         si_state<NC>(d, c, T, invT, sT);
       }
     }
-    e_rad0 = warp_sum(e_rad0);
-    e_src = warp_sum(e_src);
+    warp_sum2(e_rad0, e_src);
     if (lane == 0 && acc_m >= 0) {
       Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
       atomicAdd(&cc->E_rad0, e_rad0);
@@ -1205,9 +1203,9 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const double dT = Tnew - Tc;
       double invTn, sTn;
       inv_and_sigma_T(d, c, Tnew, &invTn, &sTn);
-      if (PAIR && wib) {
-        // warp 1 of the pair: the opacities, tau and q at T^{k+1}
-        si_state<NC, 2>(d, c, Tnew, invTn, sTn, nxt);
+      if (PAIR && !wib) {
+        // warp 0 of the pair: Phi, dPhi/dT and T at T^{k+1}
+        si_state<NC, 1>(d, c, Tnew, invTn, sTn, nxt);
         continue;
       }
       double r[NC], dr[NC];
@@ -1249,7 +1247,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         werrT = fmaxf(werrT, eT);
         werrR = fmaxf(werrR, eR);
       }
-      if (PAIR) si_state<NC, 1>(d, c, Tnew, invTn, sTn, nxt);
+      // warp 1 of a pair: the opacities, tau and q
+      if (PAIR) si_state<NC, 2>(d, c, Tnew, invTn, sTn, nxt);
       else si_state<NC>(d, c, Tnew, invTn, sTn, nxt);
     }
     if (!ENS) {
@@ -1307,8 +1306,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     for (long long gc = lead ? gw : total; gc < total; gc += nw) {
       const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
       if (ENS && m != acc_m && acc_m >= 0) {
-        e_rad1 = warp_sum(e_rad1);
-        b_in = warp_sum(b_in);
+        warp_sum2(e_rad1, b_in);
         const unsigned sc_n = __reduce_add_sync(0xffffffffu, (unsigned)scaled);
         if (lane == 0) {
           Ctrl* cc = e.devs[acc_m].ctrl;
@@ -1381,8 +1379,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         }
       }
     }
-    e_rad1 = warp_sum(e_rad1);
-    b_in = warp_sum(b_in);
+    warp_sum2(e_rad1, b_in);
     if (lane == 0 && acc_m >= 0) {
       Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
       atomicAdd(&cc->E_rad1, e_rad1);
