@@ -1022,7 +1022,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     }
   }
   for (int k = threadIdx.x; k < (ENS ? M : 1); k += blockDim.x) s_conv[k] = 0;
-  if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+  // The first iterate reads the neighbours' state at T^n.  Where the
+  // previous step left it, the prologue wrote nothing another cell reads (R
+  // is the cell's own), so no grid barrier is needed before the iterates.
+  if (ENS || warm || !d0.ctrl->si_state_ok) {
+    if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
+  } else {
+    __syncthreads();
+  }
 
   // ---- iterations.  `it` counts all iterates (it indexes the error slots),
   // itA the FP32 warm-start iterates, itB the FP64 ones.
