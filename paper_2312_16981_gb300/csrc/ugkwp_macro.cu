@@ -1446,11 +1446,41 @@ __global__ void k_end_step(const __grid_constant__ Dev d0, const Ens e) {
 // for their (cell, group) (a reading where the paper is silent: the particle
 // part never exceeds rho^{n+1}).  Runs after the survivor sort; a member with
 // nothing to scale returns at once.
+// Scale the first n survivors of buffer b by their bins' factors, four
+// particles a thread (one 16-byte key load, four independent factor
+// gathers); only the particles whose factor is not 1 are written.  For
+// ensembles: many members, each with many scaled bins of a few particles.
+__device__ __forceinline__ void scale_weights_flat(const Dev& d, unsigned b, long long n) {
+  const uint32_t* __restrict__ key = d.pkey[b];
+  const bool mixed = d.precision == 1;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = 4 * q;
+    uint32_t k[4];
+    if (i0 + 3 < n) {
+      const uint4 kk = *reinterpret_cast<const uint4*>(key + i0);
+      k[0] = kk.x; k[1] = kk.y; k[2] = kk.z; k[3] = kk.w;
+    } else {
+      for (int r = 0; r < 4; ++r) k[r] = i0 + r < n ? key[i0 + r] : 0u;
+    }
+    double f[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) f[r] = i0 + r < n ? __ldg(d.wscale + k[r]) : 1.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (f[r] == 1.0) continue;
+      if (mixed) d.fw[b][i0 + r] = (float)((double)d.fw[b][i0 + r] * f[r]);
+      else d.pw[b][i0 + r] *= f[r];
+    }
+  }
+}
+
 // Scale the weights of buffer b's survivors by their bins' factors.  The
 // survivors are sorted by bin: after the scatter, bin k holds the slots
 // [sort_off[k] - sort_cnt[k], sort_off[k]), so only the bins whose factor
 // is not 1 are touched (a warp checks 32 bins, then scales each such bin's
-// run with all its lanes).  Warp w of nw over the member's bins.
+// run with all its lanes).  Warp w of nw over the problem's bins; for a
+// single problem, whose grid has thousands of warps and few scaled bins.
 __device__ __forceinline__ void scale_weights(const Dev& d, unsigned b, long long w, long long nw) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -1478,8 +1508,7 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
   const Dev& d = ENS ? e.devs[blockIdx.y] : d0;
   const Ctrl* ctrl = d.ctrl;
   if (!ctrl->scaled) return;
-  scale_weights(d, ctrl->cur, (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5,
-                ((long long)gridDim.x * blockDim.x) >> 5);
+  scale_weights_flat(d, ctrl->cur, (long long)ctrl->n_part[ctrl->cur]);
 }
 
 // End of step of a single problem in one launch: the sorted survivors'
