@@ -357,7 +357,7 @@ size_t member_bytes(const ugkwp_problem* p) {
 }
 
 size_t table_bytes(int M) {
-  return align256(sizeof(Dev) * (size_t)M) + 4 * align256(sizeof(int) * (size_t)(M + 1)) + 256;
+  return align256(sizeof(Dev) * (size_t)M) + 5 * align256(sizeof(int) * (size_t)(M + 1)) + 256;
 }
 
 int validate_members(const ugkwp_problem* probs, int M) {
@@ -458,7 +458,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
     return r;
   };
   char* base = static_cast<char*>(d_workspace);
-  std::vector<int> cell0(n + 1, 0), bin0(n + 1, 0), fg0(n + 1, 0);
+  std::vector<int> cell0(n + 1, 0), bin0(n + 1, 0), fg0(n + 1, 0), item0(n + 1, 0);
   long long max_bins = 0;
   int max_G = 0;
   for (int m = 0; m < n; ++m) {
@@ -470,6 +470,8 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
     cell0[m + 1] = cell0[m] + d.ncell;
     bin0[m + 1] = bin0[m] + d.nbins;
     fg0[m + 1] = fg0[m] + d.nface * d.G;
+    const int cpw = 32 / ugkwp::seg_width(d.G);
+    item0[m + 1] = item0[m] + (d.ncell + cpw - 1) / cpw;
     if (d.nbins > max_bins) max_bins = d.nbins;
     if (d.G > max_G) max_G = d.G;
   }
@@ -490,6 +492,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   int* d_cell0 = cv.take<int>(n + 1);
   int* d_bin0 = cv.take<int>(n + 1);
   int* d_fg0 = cv.take<int>(n + 1);
+  int* d_item0 = cv.take<int>(n + 1);
   int* d_tile0 = cv.take<int>(n + 1);
   unsigned int* d_bar = cv.take<unsigned int>(4);   // barrier arrivals, then the tile counter (8-byte aligned)
   cudaError_t e;
@@ -497,6 +500,7 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   if ((e = cudaMemcpyAsync(d_cell0, cell0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
   if ((e = cudaMemcpyAsync(d_bin0, bin0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
   if ((e = cudaMemcpyAsync(d_fg0, fg0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
+  if ((e = cudaMemcpyAsync(d_item0, item0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s))) return bad(e, "tables");
   if ((e = cudaMemsetAsync(d_tile0, 0, sizeof(int) * (n + 1), s))) return bad(e, "tables");
   if ((e = cudaMemsetAsync(d_bar, 0, 4 * sizeof(unsigned int), s))) return bad(e, "tables");
   if ((e = cudaStreamSynchronize(s))) return bad(e, "init sync");
@@ -506,12 +510,14 @@ int ugkwp_init_ensemble(const ugkwp_problem* probs, int n, void* d_workspace, si
   E.cell0 = d_cell0;
   E.bin0 = d_bin0;
   E.fg0 = d_fg0;
+  E.item0 = d_item0;
   E.tile0 = d_tile0;
   E.bar = d_bar;
   E.tile_next = reinterpret_cast<unsigned long long*>(d_bar + 2);
   E.total_bins = bin0[n];
   E.total_fg = fg0[n];
   E.total_cells = cell0[n];
+  E.total_items = item0[n];
   E.max_parts = ugkwp::scan_parts(max_bins);
   E.max_G = max_G;
   E.tile = ens_tile(h);

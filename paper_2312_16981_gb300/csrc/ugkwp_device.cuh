@@ -378,17 +378,22 @@ __device__ __forceinline__ uint32_t div_nx(const Dev& d, uint32_t cell) {
 // descriptors and prefix tables over the members' index spaces.  Member m
 // owns global indices [tab[m], tab[m+1]).  A single problem uses M = 1 and the
 // kernels' non-ensemble instantiation, which never reads these tables.
+// Lanes per cell in the source iteration: the smallest of 8, 16, 32 that
+// holds G groups (32 above 16); a warp serves 32 / seg_width(G) cells.
+__host__ __device__ inline int seg_width(int G) { return G <= 8 ? 8 : (G <= 16 ? 16 : 32); }
+
 struct Ens {
   int M;
   const Dev* devs;        // [M] member descriptors (device copy)
   const int* cell0;       // [M+1] prefix of ncell
   const int* bin0;        // [M+1] prefix of nbins
   const int* fg0;         // [M+1] prefix of nface*G
+  const int* item0;       // [M+1] prefix of the source iteration's work items (warps' cells)
   int* tile0;             // [M+1] prefix of this step's particle tiles (written on the device)
   unsigned int* bar;      // grid-barrier arrivals of the ensemble source iteration
   unsigned long long* tile_next;   // next particle tile to hand out (reset with bar each step)
   // totals known on the host (launch shapes)
-  long long total_bins, total_fg, total_cells;
+  long long total_bins, total_fg, total_cells, total_items;
   int max_parts, max_G;
   int tile;               // particles per tile of the particle kernel's tile table
 };

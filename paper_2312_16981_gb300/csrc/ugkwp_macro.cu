@@ -764,15 +764,16 @@ __device__ __forceinline__ void inv_and_sigma_T(const Dev& d, int c, double T, d
 // FP64 state of cell c at temperature T for the next iterate (slot): T^k,
 // tau = 1/(rate sigma_g), q = 1/(tau + dt), Phi_g, dPhi_g/dT (FP32).
 // PART 1: T^k, Phi_g, dPhi_g/dT; 2: tau, q (two warps of a cell share it).
+// L: the cell's lanes; G: its group count, 0 for a segment past the last cell.
 template <int NC, int PART = 0>
-__device__ __forceinline__ void si_state(const Dev& d, int c, double T, double invT, double sT, int slot = 0) {
-  const int lane = threadIdx.x & 31, G = d.G;
+__device__ __forceinline__ void si_state(const Dev& d, int c, double T, double invT, double sT, int slot,
+                                         const Lanes& L, int G) {
   double sg[NC], ph[NC];
   float dp[NC];
-  si_planck<NC, PART>(d, T, invT, sT, sg, ph, dp);
+  si_planck<NC, PART>(d, T, invT, sT, sg, ph, dp, L, G);
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
-    const int g = lane + 32 * j;
+    const int g = L.sl + L.seg * j;
     if (g < G) {
       if (PART != 1) {
         double tau, qv;
@@ -786,7 +787,7 @@ __device__ __forceinline__ void si_state(const Dev& d, int c, double T, double i
       }
     }
   }
-  if (lane == 0 && PART != 2) __stcg(d.Tk[slot] + c, T);
+  if (L.sl == 0 && G > 0 && PART != 2) __stcg(d.Tk[slot] + c, T);
 }
 
 // ---- FP32 warm start (mixed precision)
@@ -795,15 +796,14 @@ constexpr int kWarmMaxIters = 100;
 
 // the same state in FP32
 template <int NC>
-__device__ __forceinline__ void si_state_f(const Dev& d, int c, float T, int slot) {
-  const int lane = threadIdx.x & 31, G = d.G;
+__device__ __forceinline__ void si_state_f(const Dev& d, int c, float T, int slot, const Lanes& L, int G) {
   const float invT = __frcp_rn(T);
   const float sT = d2f_trunc(d.sigma0[c]) * pow_fast_f(T, d2f_trunc(d.sig_q));
   float sg[NC], ph[NC], dp[NC];
-  si_planck_f<NC>(d, T, invT, sT, sg, ph, dp);
+  si_planck_f<NC>(d, T, invT, sT, sg, ph, dp, L, G);
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
-    const int g = lane + 32 * j;
+    const int g = L.sl + L.seg * j;
     if (g < G) {
       float tau, qv;
       tau_and_q_f(d, sg[j], &tau, &qv);
@@ -813,7 +813,7 @@ __device__ __forceinline__ void si_state_f(const Dev& d, int c, float T, int slo
       __stcg(d.dphik + c * G + g, dp[j]);
     }
   }
-  if (lane == 0) __stcg(d.Tk_f[slot] + c, T);
+  if (L.sl == 0 && G > 0) __stcg(d.Tk_f[slot] + c, T);
 }
 
 // neighbour values across one face in FP32 (as neighbour()); false at a reflecting wall
@@ -876,10 +876,11 @@ __device__ __forceinline__ float face_feq_f(const Dev& d, int f, int g, int cur)
 
 // One FP32 iterate of cell c (the linearised update of the FP64 iterate, no
 // rho written): T^{k+1} and the cell's state at it into slot cur ^ 1.
-// Returns |dT|/T (+inf where not finite).
+// Returns |dT|/T (+inf where not finite; 0 for a segment past the last
+// cell, G = 0).
 template <int NC>
-__device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool face_pass) {
-  const int lane = threadIdx.x & 31, G = d.G, nxt = cur ^ 1;
+__device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool face_pass, const Lanes& L, int G) {
+  const int nxt = cur ^ 1;
   const float dt = d.dtf;
   const float Tc = __ldcg(d.Tk_f[cur] + c);
   float num = 0.0f, den = 0.0f;
@@ -887,7 +888,7 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
   cell_xyz(d, c, &ix, &iy, &iz);
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
-    const int g = lane + 32 * j;
+    const int g = L.sl + L.seg * j;
     if (g >= G) continue;
     const int i = c * G + g;
     const float tc = __ldcg(d.tau_f[cur] + i), phc = __ldcg(d.phi_f[cur] + i), dpc = __ldcg(d.dphik + i);
@@ -909,8 +910,8 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
     num = fmaf(ap, fmaf(dpc, Tc, q - phc), num);
     den = fmaf(ap, dpc, den);
   }
-  num = warp_sum_f(num);
-  den = warp_sum_f(den);
+  num = seg_sum_f(num, L);
+  den = seg_sum_f(den, L);
   float Tnew;
   if (d.cv_law == 1) {
     const double Tcd = f2d_bits(Tc), Tnd = d.T[c];
@@ -924,12 +925,13 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
   if (!(Tnew > 1e-30f)) Tnew = (Tnew == Tnew) ? 1e-30f : Tnew;
   float eT = __fdiv_rn(fabsf(Tnew - Tc), Tnew);
   if (!(eT <= 3.0e38f)) eT = INFINITY;
-  if (Tnew == Tnew && Tnew < INFINITY) si_state_f<NC>(d, c, Tnew, nxt);
-  else {
-    // not finite: the cell keeps its temperature (the hand-over falls back to T^n)
-    if (lane == 0) __stcg(d.Tk_f[nxt] + c, Tnew);
-  }
-  return eT;
+  // a T^{k+1} that is not finite is stored as it is, without a state (the
+  // hand-over falls back to T^n there); every segment takes the call, whose
+  // shuffles need the whole warp
+  const bool fin = Tnew == Tnew && Tnew < INFINITY;
+  si_state_f<NC>(d, c, fin ? Tnew : 1.0f, nxt, L, fin ? G : 0);
+  if (!fin && L.sl == 0 && G > 0) __stcg(d.Tk_f[nxt] + c, Tnew);
+  return G > 0 ? eT : 0.0f;
 }
 
 // PAIR (single 1D problems of at most two cells per SM, FP64 iterates
@@ -941,13 +943,37 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
 // values while warp 1 updates rho and evaluates the opacities, tau and q.
 // Outside the iterates warp 0 does the cell's work.  The results are
 // bitwise those of one warp per cell.
+// The cell a lane serves in work item q: an item is one warp's 32/seg
+// cells of one member (seg from the member's G, 32 in pair mode); a segment
+// past the member's last cell gets its last cell and G = 0 (no group work,
+// nothing stored).
+struct SiCell {
+  int m, c, G;
+  Lanes L;
+};
+
+template <bool ENS, bool PAIR>
+__device__ __forceinline__ SiCell si_cell(const Dev& d0, const Ens& e, long long q) {
+  SiCell r;
+  r.m = ENS ? find_member(e.item0, e.M, q) : 0;
+  const Dev& d = ENS ? e.devs[r.m] : d0;
+  r.L = lanes_of(PAIR ? 32 : seg_width(d.G));
+  const long long t = ENS ? q - (long long)e.item0[r.m] : q;
+  const long long c = t * (32 / r.L.seg) + r.L.sub;
+  r.c = c < d.ncell ? (int)c : d.ncell - 1;
+  r.G = c < d.ncell ? d.G : 0;
+  return r;
+}
+
 template <int NC, bool ENS, bool PAIR>
 __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, const Ens e) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const long long gw = PAIR ? (long long)blockIdx.x : blockIdx.x * (long long)nwb + wib;
   const long long nw = PAIR ? (long long)gridDim.x : (long long)gridDim.x * nwb;
   const bool lead = !PAIR || wib == 0;
-  const long long total = ENS ? e.total_cells : (long long)d0.ncell;
+  // work items: one warp's cells (several per warp where G <= 16)
+  const int cpw0 = PAIR ? 1 : 32 / seg_width(d0.G);
+  const long long nitems = ENS ? e.total_items : ((long long)d0.ncell + cpw0 - 1) / cpw0;
   const int M = ENS ? e.M : 1;
   unsigned int* bar_count = ENS ? e.bar : &d0.ctrl->bar_count;
   Ctrl* st_ctrl = ENS ? e.devs[0].ctrl : d0.ctrl;
@@ -963,10 +989,12 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   {
     double e_rad0 = 0.0, e_mat0 = 0.0, e_src = 0.0;
     int acc_m = -1;
-    for (long long gc = lead ? gw : total; gc < total; gc += nw) {
-      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+    for (long long gq = lead ? gw : nitems; gq < nitems; gq += nw) {
+      const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
+      const int m = sc.m;
       if (ENS && m != acc_m && acc_m >= 0) {
         warp_sum2(e_rad0, e_src);
+        e_mat0 = warp_sum(e_mat0);   // a warp carries several cells where G <= 16
         if (lane == 0) {
           Ctrl* cc = e.devs[acc_m].ctrl;
           atomicAdd(&cc->E_rad0, e_rad0);
@@ -977,8 +1005,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       acc_m = m;
       const Dev& d = ENS ? e.devs[m] : d0;
-      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
-      const int G = d.G;
+      const int c = sc.c, G = sc.G;
+      const Lanes& L = sc.L;
       const double dt = d.dt, V = d.vol;
       // the source acts while t^n = n dt < src_t_end (src_t_end <= 0: always)
       const bool src_on = d.src && (!(d.src_t_end > 0.0) || (double)d.ctrl->step * dt < d.src_t_end);
@@ -986,7 +1014,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       cell_xyz(d, c, &ix, &iy, &iz);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        const int g = lane + 32 * j;
+        const int g = L.sl + L.seg * j;
         if (g < G) {
           const int i = c * G + g;
           const double r0 = d.rho[i];
@@ -1005,15 +1033,16 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         }
       }
       const double T = d.T[c];
-      if (lane == 0) e_mat0 += V * mat_energy(d, c, T);
-      if (warm) si_state_f<NC>(d, c, d2f_trunc(T), 0);
+      if (L.sl == 0 && G > 0) e_mat0 += V * mat_energy(d, c, T);
+      if (warm) si_state_f<NC>(d, c, d2f_trunc(T), 0, L, G);
       else if (!d.ctrl->si_state_ok) {
         double invT, sT;
         inv_and_sigma_T(d, c, T, &invT, &sT);
-        si_state<NC>(d, c, T, invT, sT);
+        si_state<NC>(d, c, T, invT, sT, 0, L, G);
       }
     }
     warp_sum2(e_rad0, e_src);
+    e_mat0 = warp_sum(e_mat0);   // a warp carries several cells where G <= 16
     if (lane == 0 && acc_m >= 0) {
       Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
       atomicAdd(&cc->E_rad0, e_rad0);
@@ -1050,22 +1079,26 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const int cur = itA & 1;
       if (face_pass) {
         const int G = d0.G;
-        for (long long gf = gw; gf < d0.nface; gf += nw) {
+        const Lanes L = lanes_of(seg_width(G));
+        const long long nfi = ((long long)d0.nface + cpw0 - 1) / cpw0;
+        for (long long gq = gw; gq < nfi; gq += nw) {
+          const long long f = gq * cpw0 + L.sub;
+          if (f >= d0.nface) continue;
 #pragma unroll
           for (int j = 0; j < NC; ++j) {
-            const int g = lane + 32 * j;
-            if (g < G) d0.Feq_f[gf * G + g] = face_feq_f(d0, (int)gf, g, cur);
+            const int g = L.sl + L.seg * j;
+            if (g < G) d0.Feq_f[f * G + g] = face_feq_f(d0, (int)f, g, cur);
           }
         }
         if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
       }
       float werr = 0.0f;
-      for (long long gc = gw; gc < total; gc += nw) {
-        const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
-        const Dev& d = ENS ? e.devs[m] : d0;
-        const int c = (int)(ENS ? gc - e.cell0[m] : gc);
-        werr = fmaxf(werr, si_iterate_f<NC>(d, c, cur, face_pass));
+      for (long long gq = gw; gq < nitems; gq += nw) {
+        const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
+        const Dev& d = ENS ? e.devs[sc.m] : d0;
+        werr = fmaxf(werr, si_iterate_f<NC>(d, sc.c, cur, face_pass, sc.L, sc.G));
       }
+      werr = warp_max_nonneg_f(werr);
       if (lane == 0) s_err[wib][0] = werr;
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -1087,15 +1120,15 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     }
     // hand-over: the FP64 state at the last FP32 temperature (at T^n in a
     // cell where that is not finite and positive)
-    for (long long gc = gw; gc < total; gc += nw) {
-      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
-      const Dev& d = ENS ? e.devs[m] : d0;
-      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
+    for (long long gq = gw; gq < nitems; gq += nw) {
+      const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
+      const Dev& d = ENS ? e.devs[sc.m] : d0;
+      const int c = sc.c;
       const float Tf = __ldcg(d.Tk_f[itA & 1] + c);
       const double T0 = (Tf > 0.0f && Tf < INFINITY) ? f2d_bits(Tf) : d.T[c];
       double invT, sT;
       inv_and_sigma_T(d, c, T0, &invT, &sT);
-      si_state<NC>(d, c, T0, invT, sT);
+      si_state<NC>(d, c, T0, invT, sT, 0, sc.L, sc.G);
     }
     if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
   }
@@ -1104,21 +1137,26 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     float werrT = 0.0f, werrR = 0.0f;
     if (face_pass) {
       const int G = d0.G;
-      for (long long gf = gw; gf < d0.nface; gf += nw) {
+      const Lanes L = lanes_of(seg_width(G));
+      const long long nfi = ((long long)d0.nface + cpw0 - 1) / cpw0;
+      for (long long gq = gw; gq < nfi; gq += nw) {
+        const long long f = gq * cpw0 + L.sub;
+        if (f >= d0.nface) continue;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
-          const int g = lane + 32 * j;
-          if (g < G) d0.Feq[gf * G + g] = face_feq(d0, (int)gf, g, cur);
+          const int g = L.sl + L.seg * j;
+          if (g < G) d0.Feq[f * G + g] = face_feq(d0, (int)f, g, cur);
         }
       }
       if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
     }
-    for (long long gc = gw; gc < total; gc += nw) {
-      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+    for (long long gq = gw; gq < nitems; gq += nw) {
+      const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
+      const int m = sc.m;
       if (ENS && s_conv[m]) continue;
       const Dev& d = ENS ? e.devs[m] : d0;
-      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
-      const int G = d.G;
+      const int c = sc.c, G = sc.G;
+      const Lanes& L = sc.L;
       const double dt = d.dt;
       const double Tc = __ldcg(d.Tk[cur] + c), Tn = d.T[c], cv = d.cv[c];
       // with q = 1/(tau + dt): 1/(1 + a_g) = tau q and a_g/(1 + a_g) = dt q
@@ -1128,7 +1166,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       cell_xyz(d, c, &ix, &iy, &iz);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        const int g = lane + 32 * j;
+        const int g = L.sl + L.seg * j;
         Q[j] = 0.0; ar[j] = 0.0; r1[j] = 1.0; phc[j] = 0.0; dpc[j] = 0.0;
         if (g >= G) continue;
         const int i = c * G + g;
@@ -1152,7 +1190,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           if (neighbour(d, ix, iy, iz, 0, dir, g, cur, tc, &tn, &pn, &nc))
             F = dir < 0 ? feq_face_si(d, tn, tc, pn, phc[j], 0) : feq_face_si(d, tc, tn, phc[j], pn, 0);
           if (dir > 0 || nc < 0) d.Feq[face_index_xyz(d, ix, iy, iz, 0, dir) * G + g] = F;
-          s_pair[PAIR ? wib : 0][PAIR ? 32 * j + lane : 0] = F;
+          s_pair[PAIR ? wib : 0][PAIR ? g : 0] = F;
         }
         for (int axis = 0; axis < ((face_pass || PAIR) ? 0 : d.dim); ++axis) {
           double Fin = 0.0, Fout = 0.0;
@@ -1183,8 +1221,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
-          if (lane + 32 * j >= G) continue;
-          const int k = PAIR ? 32 * j + lane : 0;
+          const int k = PAIR ? L.sl + L.seg * j : 0;
+          if (k >= G) continue;
           Q[j] = fma(d.dt_h[0], s_pair[0][k] - s_pair[PAIR ? 1 : 0][k], Q[j]);
           const double ap = ar[j] * d.inv_c;
           num = fma(ap, fma(dpc[j], Tc, Q[j] - phc[j]), num);
@@ -1192,7 +1230,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         }
         __syncthreads();   // both warps have read the exchange before a next cell writes it
       }
-      warp_sum2(num, den);
+      seg_sum2(num, den, L);
       // a T-dependent heat capacity: e(T^{k+1}) ~ e(T^k) + C_v(T^k) (T^{k+1} - T^k)
       double Tnew;
       if (d.cv_law == 1) {
@@ -1212,14 +1250,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       inv_and_sigma_T(d, c, Tnew, &invTn, &sTn);
       if (PAIR && !wib) {
         // warp 0 of the pair: Phi, dPhi/dT and T at T^{k+1}
-        si_state<NC, 1>(d, c, Tnew, invTn, sTn, nxt);
+        si_state<NC, 1>(d, c, Tnew, invTn, sTn, nxt, L, G);
         continue;
       }
       double r[NC], dr[NC];
       int ex = 0;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        const int g = lane + 32 * j;
+        const int g = L.sl + L.seg * j;
         r[j] = 0.0; dr[j] = 0.0;
         if (g >= G) continue;
         const int i = c * G + g;
@@ -1229,37 +1267,42 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         ex = max(ex, biased_exp(r[j]));
       }
       // max_g |d rho_g| / sum_g |rho_g| in FP32, both scaled by the cell's largest |rho_g|
-      const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)ex);
+      const int E = (int)seg_max_u((unsigned)ex, L);
       float dmax = 0.0f, rsum = 0.0f;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         dmax = fmaxf(dmax, scaled_mag(dr[j], E));
         rsum += scaled_mag(r[j], E);
       }
-      dmax = warp_max_nonneg_f(dmax);
-      rsum = warp_sum_f(rsum);
+      dmax = __uint_as_float(seg_max_u(__float_as_uint(dmax), L));
+      rsum = seg_sum_f(rsum, L);
       float eR = rsum > 0.0f ? dmax / rsum : 0.0f;
       const int ET = biased_exp(Tnew);
       const float fT = scaled_mag(Tnew, ET);
       float eT = fT < INFINITY ? scaled_mag(dT, ET) / fT : INFINITY;
       if (!(eT <= 3.0e38f)) eT = INFINITY;
       if (!(eR <= 3.0e38f)) eR = INFINITY;
+      if (G == 0) eT = eR = 0.0f;   // a segment past the last cell
       if (ENS) {
-        // members differ between warps: each warp reports to its own member
+        // members differ between warps (a warp's cells are one member's):
+        // each warp reports to its own member
+        const float wT = warp_max_nonneg_f(eT), wR = warp_max_nonneg_f(eR);
         if (lane == 0) {
-          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][0], f2d_bits(eT));
-          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][1], f2d_bits(eR));
+          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][0], f2d_bits(wT));
+          atomic_max_nonneg(&d.ctrl->err_slot[it % 3][1], f2d_bits(wR));
         }
       } else {
         werrT = fmaxf(werrT, eT);
         werrR = fmaxf(werrR, eR);
       }
       // warp 1 of a pair: the opacities, tau and q
-      if (PAIR) si_state<NC, 2>(d, c, Tnew, invTn, sTn, nxt);
-      else si_state<NC>(d, c, Tnew, invTn, sTn, nxt);
+      if (PAIR) si_state<NC, 2>(d, c, Tnew, invTn, sTn, nxt, L, G);
+      else si_state<NC>(d, c, Tnew, invTn, sTn, nxt, L, G);
     }
     if (!ENS) {
       Ctrl* ctrl = d0.ctrl;
+      werrT = warp_max_nonneg_f(werrT);
+      werrR = warp_max_nonneg_f(werrR);
       if (lane == 0) { s_err[wib][0] = werrT; s_err[wib][1] = werrR; }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -1310,11 +1353,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   {
     double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
     int bad = 0, scaled = 0, acc_m = -1;
-    for (long long gc = lead ? gw : total; gc < total; gc += nw) {
-      const int m = ENS ? find_member(e.cell0, e.M, gc) : 0;
+    for (long long gq = lead ? gw : nitems; gq < nitems; gq += nw) {
+      const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
+      const int m = sc.m;
       if (ENS && m != acc_m && acc_m >= 0) {
         warp_sum2(e_rad1, b_in);
+        e_mat1 = warp_sum(e_mat1);
         const unsigned sc_n = __reduce_add_sync(0xffffffffu, (unsigned)scaled);
+        bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
         if (lane == 0) {
           Ctrl* cc = e.devs[acc_m].ctrl;
           atomicAdd(&cc->E_rad1, e_rad1);
@@ -1329,8 +1375,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
       acc_m = m;
       const Dev& d = ENS ? e.devs[m] : d0;
-      const int c = (int)(ENS ? gc - e.cell0[m] : gc);
-      const int G = d.G;
+      const int c = sc.c, G = sc.G;
+      const Lanes& L = sc.L;
       const double dt = d.dt, V = d.vol;
       const int ran = s_conv[ENS ? m : 0] ? s_conv[ENS ? m : 0] : itB;
       const int fin = ran > 0 ? (ran & 1) : 0;
@@ -1338,14 +1384,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       // the last iterate's state (at T^{n+1}) into slot 0, where the next
       // step's iteration starts from it instead of re-evaluating it
       if (fin == 1 && !warm) {
-        if (lane == 0) __stcg(d.Tk[0] + c, T);
-        for (int g = lane; g < G; g += 32) {
+        if (L.sl == 0 && G > 0) __stcg(d.Tk[0] + c, T);
+        for (int g = L.sl; g < G; g += L.seg) {
           __stcg(d.tauk[0] + c * G + g, __ldcg(d.tauk[1] + c * G + g));
           __stcg(d.phik[0] + c * G + g, __ldcg(d.phik[1] + c * G + g));
         }
       }
-      if (!(T == T) || T > 1e300) bad = 1;
-      if (lane == 0) {
+      if (G > 0 && (!(T == T) || T > 1e300)) bad = 1;
+      if (L.sl == 0 && G > 0) {
         d.T[c] = T;
         e_mat1 += V * mat_energy(d, c, T);
       }
@@ -1353,7 +1399,7 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       cell_xyz(d, c, &ixyz[0], &ixyz[1], &ixyz[2]);
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        const int g = lane + 32 * j;
+        const int g = L.sl + L.seg * j;
         if (g >= G) continue;
         const int i = c * G + g;
         const double r = __ldcg(d.rho + i);
@@ -1387,6 +1433,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       }
     }
     warp_sum2(e_rad1, b_in);
+    e_mat1 = warp_sum(e_mat1);
+    bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
     if (lane == 0 && acc_m >= 0) {
       Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
       atomicAdd(&cc->E_rad1, e_rad1);
@@ -1942,17 +1990,19 @@ static int g_si_blocks[2][2][3] = {};
 // One warp per cell.  On GB300 the FP64 pipe of an SM is the limit of this
 // kernel, so a small grid is spread one warp per block over all SMs; a large
 // grid uses 8-warp blocks (fewer arrivals at the grid barrier).
+// items: the kernel's work items (a warp's cells each; pair mode: one cell
+// per two-warp block)
 template <int NC, bool ENS, bool PAIR>
-static cudaError_t launch_si_t(const Dev& d, const Ens& e, long long ncell, cudaStream_t s) {
+static cudaError_t launch_si_t(const Dev& d, const Ens& e, long long items, cudaStream_t s) {
   const int sms = sm_count();
-  const int small = ncell <= 8 * sms;
+  const int small = items <= 8 * sms;
   const int threads = PAIR ? 64 : (small ? 32 : 256);
   int& per = g_si_blocks[NC - 1][ENS][PAIR ? 2 : small];
   if (!per) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_si<NC, ENS, PAIR>, threads, 0);
     if (per < 1) per = 1;
   }
-  const long long want = PAIR ? ncell : (ncell * 32 + threads - 1) / threads;
+  const long long want = PAIR ? items : (items * 32 + threads - 1) / threads;
   const long long maxb = (long long)sms * per;
   int blocks = (int)(want < maxb ? want : maxb);
   if (blocks < 1) blocks = 1;
@@ -1972,19 +2022,21 @@ static cudaError_t launch_si_t(const Dev& d, const Ens& e, long long ncell, cuda
 cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s) {
   if (e && e->M > 1) {
     if (e->M > kMaxEnsemble) return cudaErrorInvalidValue;
-    if (e->max_G > 32) return launch_si_t<2, true, false>(d, *e, e->total_cells, s);
-    return launch_si_t<1, true, false>(d, *e, e->total_cells, s);
+    if (e->max_G > 32) return launch_si_t<2, true, false>(d, *e, e->total_items, s);
+    return launch_si_t<1, true, false>(d, *e, e->total_items, s);
   }
   const Ens none{};
   // a 1D grid of at most two cells per SM, FP64 iterates only: two warps per
   // cell (one warp per cell would leave most SM sub-partitions idle)
   const bool pair = d.dim == 1 && !d.si_warm && d.ncell <= 2 * sm_count() && d.pair_si;
+  const int cpw = 32 / seg_width(d.G);
+  const long long items = ((long long)d.ncell + cpw - 1) / cpw;
   if (d.G > 32) {
     if (pair) return launch_si_t<2, false, true>(d, none, d.ncell, s);
-    return launch_si_t<2, false, false>(d, none, d.ncell, s);
+    return launch_si_t<2, false, false>(d, none, items, s);
   }
   if (pair) return launch_si_t<1, false, true>(d, none, d.ncell, s);
-  return launch_si_t<1, false, false>(d, none, d.ncell, s);
+  return launch_si_t<1, false, false>(d, none, items, s);
 }
 
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {

@@ -95,6 +95,49 @@ __device__ __forceinline__ void warp_sum2(double& a, double& b) {
   b = __shfl_sync(0xffffffffu, keep, 1);
 }
 
+// The lanes that serve one cell: a segment of `seg` lanes (8, 16 or 32, the
+// smallest that holds the problem's G groups; 32 above 16), so that a warp
+// carries 32/seg cells at once and an FP64 warp instruction, which costs the
+// same whatever the number of active lanes, does the work of several cells
+// where G is small.  Lane sl of a segment takes groups g = sl + seg j.  With
+// seg = 32 every reduction below runs in the order of the whole-warp one.
+struct Lanes {
+  int seg, sub, sl, base;   // width, segment index in the warp, lane in it, its first lane
+};
+
+
+__device__ __forceinline__ Lanes lanes_of(int seg) {
+  Lanes L;
+  const int lane = threadIdx.x & 31;
+  L.seg = seg;
+  L.sl = lane & (seg - 1);
+  L.base = lane - L.sl;
+  L.sub = L.base / seg;
+  return L;
+}
+
+// warp_sum2 within each segment (every lane of a segment gets its totals)
+__device__ __forceinline__ void seg_sum2(double& a, double& b, const Lanes& L) {
+  const bool odd = threadIdx.x & 1;
+  double keep = odd ? b : a;
+  const double send = odd ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, send, 1);
+  for (int o = 2; o < L.seg; o <<= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  a = __shfl_sync(0xffffffffu, keep, L.base);
+  b = __shfl_sync(0xffffffffu, keep, L.base + 1);
+}
+
+__device__ __forceinline__ float seg_sum_f(float v, const Lanes& L) {
+  for (int o = L.seg >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned seg_max_u(unsigned v, const Lanes& L) {
+  if (L.seg == 32) return __reduce_max_sync(0xffffffffu, v);
+  for (int o = 1; o < L.seg; o <<= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -144,20 +187,21 @@ __device__ __forceinline__ EdgeSI planck_edge_si(double x) {
 }
 
 // Planck quantities of one cell at temperature T (> 0 or not) for the lane's
-// groups g = lane + 32 j: sigma_g and Phi_g in FP64, dPhi_g/dT in FP32.
+// groups g = sl + seg j of the cell's segment L (G: the cell's group count,
+// 0 for a segment past the last cell): sigma_g and Phi_g in FP64, dPhi_g/dT
+// in FP32.
 // The same operations as cell_planck for sigma_g and Phi_g.  PART 1: Phi_g
 // and dPhi_g/dT only; 2: sigma_g only (two warps of a cell share the work).
 template <int NC, int PART = 0>
 __device__ __forceinline__ void si_planck(const Dev& d, double T, double invT, double sT, double* sig,
-                                          double* phi, float* dphi) {
-  const int lane = threadIdx.x & 31, G = d.G;
+                                          double* phi, float* dphi, const Lanes& L, int G) {
   const bool Tpos = __double_as_longlong(T) > 0;
   const double ac = d.a * d.c, T3 = T * T * T;
   const double acT3 = ac * T3, acT4 = acT3 * T;
   const float acT3f = d2f_trunc(acT3);
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
-    const int g = lane + 32 * j;
+    const int g = L.sl + L.seg * j;
     if (d.grey) {
       sig[j] = cap_sigma(d, sT);
       phi[j] = Tpos ? acT4 : 0.0;
@@ -172,10 +216,10 @@ __device__ __forceinline__ void si_planck(const Dev& d, double T, double invT, d
     if (g <= G && Tpos) lo = planck_edge_si(d.nu_edges[g] * invT);
     else { lo.V = 0.0; lo.g4 = 0.0f; lo.lower = true; }
     EdgeSI hi;
-    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
-    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
-    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
-    if (lane == 31 && g + 1 <= G && Tpos) hi = planck_edge_si(d.nu_edges[g + 1] * invT);
+    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1, L.seg);
+    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1, L.seg);
+    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1, L.seg) != 0;
+    if (L.sl == L.seg - 1 && g + 1 <= G && Tpos) hi = planck_edge_si(d.nu_edges[g + 1] * invT);
     if (g < G) {
       sig[j] = PART == 1 ? 1.0 : sigma_group_at(d, sT, T, invT, g);
       if (Tpos) {
@@ -285,14 +329,13 @@ __device__ __forceinline__ float sigma_group_f(const Dev& d, float sT, float T, 
 // sigma_g, Phi_g, dPhi_g/dT of one cell at T in FP32 (lanes as si_planck)
 template <int NC>
 __device__ __forceinline__ void si_planck_f(const Dev& d, float T, float invT, float sT, float* sig, float* phi,
-                                            float* dphi) {
-  const int lane = threadIdx.x & 31, G = d.G;
+                                            float* dphi, const Lanes& L, int G) {
   const bool Tpos = T > 0.0f;
   const float acT3 = d.acf * (T * T * T), acT4 = acT3 * T;
   const float k15 = (float)k15overPi4, kpi = (float)kPi4over15;
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
-    const int g = lane + 32 * j;
+    const int g = L.sl + L.seg * j;
     if (d.grey) {
       sig[j] = fminf(sT, d.capf);
       phi[j] = Tpos ? acT4 : 0.0f;
@@ -303,10 +346,10 @@ __device__ __forceinline__ void si_planck_f(const Dev& d, float T, float invT, f
     if (g <= G && Tpos) lo = planck_edge_f(__ldg(d.nu_edges_f + g) * invT);
     else { lo.V = 0.0f; lo.g4 = 0.0f; lo.lower = true; }
     EdgeF hi;
-    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1);
-    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1);
-    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1) != 0;
-    if (lane == 31 && g + 1 <= G && Tpos) hi = planck_edge_f(__ldg(d.nu_edges_f + g + 1) * invT);
+    hi.V = __shfl_down_sync(0xffffffffu, lo.V, 1, L.seg);
+    hi.g4 = __shfl_down_sync(0xffffffffu, lo.g4, 1, L.seg);
+    hi.lower = __shfl_down_sync(0xffffffffu, (int)lo.lower, 1, L.seg) != 0;
+    if (L.sl == L.seg - 1 && g + 1 <= G && Tpos) hi = planck_edge_f(__ldg(d.nu_edges_f + g + 1) * invT);
     if (g < G) {
       sig[j] = sigma_group_f(d, sT, T, invT, g);
       if (Tpos) {
