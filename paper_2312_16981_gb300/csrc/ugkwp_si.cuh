@@ -105,7 +105,6 @@ struct Lanes {
   int seg, sub, sl, base;   // width, segment index in the warp, lane in it, its first lane
 };
 
-
 __device__ __forceinline__ Lanes lanes_of(int seg) {
   Lanes L;
   const int lane = threadIdx.x & 31;
