@@ -38,16 +38,16 @@ N_PARTICLES = 1_000_000
 WORKLOAD = "multigroup_slab_200x30"
 METRIC = "particle segments/s"
 # kernels of one slab step: birth, one-block scan, wave flux, the particle
-# kernels (FP64: one; mixed: the survivor kernel, the newborns, the
-# face-crossing survivors), source iteration, the survivor sort (a one-block
-# scan and the scatter) and the end of step
-KERNELS_PER_STEP = {"fp64": 8, "mixed": 10}
+# kernel (FP64: k_stream64; mixed: the survivor kernel, which also streams
+# the newborns), source iteration, the survivor sort (a one-block scan and
+# the scatter) and the end of step
+KERNELS_PER_STEP = {"fp64": 8, "mixed": 8}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per processed
 # particle of the particle kernels, from one ncu capture of the current
 # kernels at 4e6 particles on the slab (the traffic grows with the particles
 # processed); the roofline's "traffic" is this times the particles a launch
 # processes.  None: no capture of the current kernels.
-TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": 51.7}
+TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": None}
 
 
 def combine_replicas(ms: float, segments: float, world: int, device):
@@ -295,7 +295,7 @@ def roofline(p, phase, launch_ms, n_proc, n_read, n_out, si_iters, mixed, pk, sr
     ach = abytes / (launch_ms * 1e-3) / 1e9 if abytes else 0.0
     tpp = TRAFFIC_PER_PROCESSED["mixed" if mixed else "fp64"]
     traffic = tpp * n_proc if (phase == "particles" and p.dim == 1 and tpp) else None
-    r = {"kernel": {"particles": ("k_stream32_fast + k_stream32_rest" if (mixed and p.dim == 1) else "k_stream32")
+    r = {"kernel": {"particles": ("k_stream32_fast" if (mixed and p.dim == 1) else "k_stream32")
                     if mixed else "k_stream64"}.get(phase, phase),
          "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
          "frac": ach / pk["hbm_gbs"], "traffic": traffic, "peak_source": src,

@@ -550,15 +550,12 @@ cudaError_t enqueue_step_dev(const Dev& d, const ugkwp::Ens* e, const ugkwp::Str
                              cudaStream_t s, const Branches& b = Branches()) {
   cudaError_t r = ugkwp::launch_birth_and_scan(d, e, s);
   if (b.side) {
-    // beside the particle kernels: the wave flux, and the newborns where
-    // the survivors have a kernel of their own
-    const bool apart = ugkwp::stream_newborns_apart(d, e);
+    // beside the particle kernel: the wave flux
     if (!r) r = cudaEventRecord(b.fork, s);
     if (!r) r = cudaStreamWaitEvent(b.side, b.fork, 0);
     if (!r) r = ugkwp::launch_wave(d, e, b.side);
-    if (!r && apart) r = ugkwp::launch_stream_newborns(d, b.side);
     if (!r) r = cudaEventRecord(b.join, b.side);
-    if (!r) r = ugkwp::launch_stream(d, e, sh, s, apart);
+    if (!r) r = ugkwp::launch_stream(d, e, sh, s);
     if (!r) r = cudaStreamWaitEvent(s, b.join, 0);
   } else {
     if (!r) r = ugkwp::launch_wave(d, e, s);

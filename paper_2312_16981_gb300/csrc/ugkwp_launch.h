@@ -20,15 +20,11 @@ int scan_parts(long long n);
 cudaError_t launch_scan(const uint32_t* N, long long n, uint32_t* part, uint32_t* off,
                         unsigned long long* total_a, unsigned long long* total_b, cudaStream_t s);
 cudaError_t launch_wave(const Dev& d, const Ens* e, cudaStream_t s);
-// The particle kernels of a step.  A mixed-precision 1D single problem with
-// few face crossings runs a survivor kernel and a general kernel for the
-// face-crossing survivors and the newborns; with newborns_elsewhere the
-// newborns are left to launch_stream_newborns (on another stream, after the
-// birth scan), which stream_newborns_apart says applies.
-cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s,
-                          bool newborns_elsewhere = false);
-bool stream_newborns_apart(const Dev& d, const Ens* e);
-cudaError_t launch_stream_newborns(const Dev& d, cudaStream_t s);
+// The particle kernels of a step: one launch.  A mixed-precision 1D single
+// problem with few face crossings takes the survivor kernel (which also
+// streams the newborns), every other problem the general kernel of its
+// precision.
+cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s);
 cudaError_t launch_si(const Dev& d, const Ens* e, cudaStream_t s);
 cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s);
 // survivor sort of every step: scan of the survivors per bin, scatter back

@@ -2044,7 +2044,11 @@ cudaError_t launch_end_step(const Dev& d, const Ens* e, cudaStream_t s) {
     k_end_step<true><<<dim3(1, e->M), 32, 0, s>>>(d, *e);
     k_scale_survivors<true><<<dim3(8, e->M), 256, 0, s>>>(d, *e);
   } else {
-    k_finish_step<<<sm_count() * 4, 256, 0, s>>>(d);
+    // a warp per 32 bins (a scaled bin's run is scaled by the warp that
+    // finds it), so the blocks' arrivals at the end stay few
+    const long long nb = (long long)d.ncell * d.G;
+    const long long blocks = (nb + 255) / 256;
+    k_finish_step<<<(int)(blocks < sm_count() * 4 ? (blocks > 0 ? blocks : 1) : sm_count() * 4), 256, 0, s>>>(d);
   }
   return cudaGetLastError();
 }

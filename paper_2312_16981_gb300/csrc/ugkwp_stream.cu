@@ -1089,27 +1089,33 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // remaining free time) in a per-warp buffer in shared memory.  The code of
 // that first flight has no crossing loop, no birth sampling and no
 // per-particle branching on the problem's options, so a warp's lanes stay
-// together; whenever 32 survivors are set aside, the warp streams them
-// through their faces, one per lane (and the rest after its last chunk).
-// P3: sigma ~ nu^-3.
-template <int NT, bool P3>
+// together; after each chunk, while 32 or more survivors are set aside, the
+// warp streams 32 of them through their faces, one per lane (and the rest
+// after its last chunk).  A chunk's R x 32 first flights are computed before
+// any of them is stored or tallied, so their dependent chains (Philox, the
+// logarithm) interleave.  The step's newborns (born in registers, the
+// general per-particle path) are streamed first, a chunk of 32 per warp,
+// while the warps' first survivor chunks are landing.
+// P3: sigma ~ nu^-3; R: 32-particle rounds per chunk.
+template <int NT, bool P3, int R>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
-    k_stream32_fast(const __grid_constant__ Dev d, int rounds) {
+    k_stream32_fast(const __grid_constant__ Dev d) {
+  constexpr int C = 32 * R;
+  constexpr int kBuf = 32 + C;   // set-aside entries: fewer than 32 left over, plus one chunk
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ uint64_t s_full[NT / 32][kStages];
-  __shared__ uint32_t s_li[NT / 32][64];
-  __shared__ float s_lt[NT / 32][64];
+  __shared__ uint32_t s_li[NT / 32][kBuf];
+  __shared__ float s_lt[NT / 32][kBuf];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const int ncell = d.ncell;
   float* s_sinv = reinterpret_cast<float*>(s_dyn);
   for (int c = threadIdx.x; c < ncell; c += NT) s_sinv[c] = __ldg(d.sTinv_f + c);
   Ring32<1, false> rg;
-  rg.C = 32 * rounds;
-  rg.stage_sz = (size_t)rg.C * StageF<1>::kBytesPer;
+  rg.C = C;
+  rg.stage_sz = (size_t)C * StageF<1>::kBytesPer;
   rg.ring = s_dyn + ((4 * (size_t)ncell + 127) & ~(size_t)127) + (size_t)warp * kStages * rg.stage_sz;
   rg.bar = s_full[warp];
-  const int C = rg.C;
   if (lane == 0) {
     for (int k = 0; k < kStages; ++k) mbar_init(&rg.bar[k], 1);
     mbar_init_fence();
@@ -1133,17 +1139,11 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
     if (lane == 0) rg.issue(&d, h0.cur, c0 + issued, h0.n_surv, issued);
   __syncwarp();
 
-  // this thread's run of E_surv (fixed point, at most 32 weights below
-  // 2^57 each) and survivor count in bin acc_key
   int acc_key = -1;
   long long acc_w = 0;
   unsigned acc_n = 0u;
   unsigned nl = 0;   // entries in the warp's buffer of set-aside survivors (same in every lane)
   Counters cnt;
-  // the first k set-aside survivors, one per lane: state from the input
-  // buffer, the free time from the buffer, the streaming loop from their
-  // first face (draw 0 of the step was the free time), stored, tallied and
-  // counted like every other particle; the rest of the buffer moves to the front
   auto run_set_aside = [&](unsigned k) {
     const bool act = (unsigned)lane < k;
     P32 q;
@@ -1182,16 +1182,59 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
       cnt.rem += q.fate == FATE_REMOVED;
       record32<1>(d, q, i, cell);
     }
+    // the rest of the buffer moves to the front, 32 entries a pass (each pass
+    // reads entries at least k beyond those it writes)
     __syncwarp();
-    uint32_t a = 0u;
-    float b = 0.0f;
-    const bool mv = (unsigned)lane < nl - k;
-    if (mv) { a = s_li[warp][k + lane]; b = s_lt[warp][k + lane]; }
-    __syncwarp();
-    if (mv) { s_li[warp][lane] = a; s_lt[warp][lane] = b; }
-    __syncwarp();
+    for (unsigned b = 0; b + k < nl; b += 32u) {
+      const bool mv = b + lane + k < nl;
+      uint32_t a = 0u;
+      float t = 0.0f;
+      if (mv) { a = s_li[warp][b + k + lane]; t = s_lt[warp][b + k + lane]; }
+      __syncwarp();
+      if (mv) { s_li[warp][b + lane] = a; s_lt[warp][b + lane] = t; }
+      __syncwarp();
+    }
     nl -= k;
   };
+
+  // ---- the newborns of the step (Eq. IhpFormula), while the first survivor
+  // chunks land: chunks of 32 consecutive birth ordinals, chunk k to block
+  // k mod (blocks), one warp of each block before the next
+  {
+    const long long n_new = h0.n_tot - h0.n_surv;
+    const long long nnc = (n_new + 31) / 32;
+    const int G = (int)d.G;
+    for (long long kc = blockIdx.x + (long long)gridDim.x * warp; kc < nnc; kc += (long long)gridDim.x * (NT / 32)) {
+      const long long jj = kc * 32 + lane;
+      const bool valid = jj < n_new;
+      const long long i = h0.n_surv + jj;
+      P32 q;
+      clear32(q);
+      DrawsF rng;
+      if (valid) birth32<1>(d, q, rng, (uint32_t)jj, h0.step, d.off);
+      else rng.init(0ull, h0.step, 0u);
+      q.cell0 = q.cx;
+      q.ghost = q.gside >= 0;
+      const float inup = (!valid || grey) ? 1.0f : pow_fast_f(q.nu, -spf);
+      bool more = false;
+      if (valid) more = first_flight32<1>(d, q, rng, inup, ncell, false, s_sinv, s_sinv + ncell);
+      if (more) stream_loop32<1>(d, q, rng, inup, ncell, false, s_sinv, s_sinv + ncell);
+      const int cell = q.cx;
+      bool stored = false;
+      if (valid) stored = store32<1>(d, nxb, q, i, cell);
+      const long long wq = valid ? to_fixed_f(q.w, tq_shift, &ctrl->status) : 0ll;
+      warp_run_add_fixed(d.Esq, stored ? cell * G + q.g : -1 - lane, wq, d.sort_cnt);
+      if (valid) {
+        cross_tallies32(d, q, cell, wq);
+        cnt.seg += (unsigned)q.nseg;
+        cnt.abs += q.fate == FATE_ABSORBED;
+        cnt.esc += q.fate == FATE_ESCAPED;
+        cnt.surv += q.fate == FATE_SURVIVED;
+        cnt.rem += q.fate == FATE_REMOVED;
+        record32<1>(d, q, i, cell);
+      }
+    }
+  }
 
   int k = 0, st = 0;
   unsigned par = 0u;   // stage st of chunk k, and the phase parity it waits for
@@ -1203,18 +1246,20 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
     const StageF<1> sg(rg.ring + st * rg.stage_sz, C);
     const long long base = c * C;
     const int nval = (int)(h0.n_surv - base < C ? h0.n_surv - base : C);
-    float* __restrict__ o_x = d.fx[nxb] + base;
-    float* __restrict__ o_ox = d.fox[nxb] + base;
-    float* __restrict__ o_nu = d.fnu[nxb] + base;
-    float* __restrict__ o_w = d.fw[nxb] + base;
-    unsigned long long* __restrict__ o_id = d.pid[nxb] + base;
-    uint32_t* __restrict__ o_key = d.pkey[nxb] + base;
-    for (int r = 0; r < rounds; ++r) {
+    // ---- the first flights of the chunk's R x 32 survivors, independent of
+    // one another (so their dependent chains interleave)
+    float a_x[R], a_ox[R], a_nu[R], a_w[R], a_tr[R];
+    unsigned long long a_id[R];
+    uint32_t a_key[R], a_cell[R];
+    bool a_col[R], a_later[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
       const int li = r * 32 + lane;
       const bool valid = li < nval;
-      const float xi = sg.x[li], ox = sg.ox[li], nu = sg.nu[li], w = sg.w[li];
+      const float xi = sg.x[li], ox = sg.ox[li], nu = sg.nu[li];
       const unsigned long long id = sg.id[li];
       const uint32_t key = valid ? sg.key[li] : 0u;
+      a_w[r] = sg.w[li];
       // cell = key / G through an FP32 reciprocal, corrected (key < 2^24)
       uint32_t cell = __float2uint_rz(__uint2float_rn(key) * invG);
       const int rem = (int)(key - cell * G);
@@ -1233,39 +1278,62 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
       // first flight: the face ahead comes first?
       const float dist = ox > 0.0f ? dxf - xi : xi;
       const float tf = fmaxf(dist, 0.0f) * rcp_approx(vf * fabsf(ox));
-      const bool later = valid && tf < t_rem;
+      a_later[r] = valid && tf < t_rem;
+      a_x[r] = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
+      a_ox[r] = ox;
+      a_nu[r] = nu;
+      a_tr[r] = t_rem;
+      a_id[r] = id;
+      a_key[r] = valid ? key : kDeadKey;
+      a_cell[r] = cell;
+      a_col[r] = collided;
+    }
+    // the stage is consumed: the chunk kStages further on goes into it
+    __syncwarp();
+    if (c + kStages < nchunks) {
+      if (lane == 0) rg.issue(&d, h0.cur, c + kStages, h0.n_surv, st);
+      ++issued;
+    }
+    float* __restrict__ o_x = d.fx[nxb] + base;
+    float* __restrict__ o_ox = d.fox[nxb] + base;
+    float* __restrict__ o_nu = d.fnu[nxb] + base;
+    float* __restrict__ o_w = d.fw[nxb] + base;
+    unsigned long long* __restrict__ o_id = d.pid[nxb] + base;
+    uint32_t* __restrict__ o_key = d.pkey[nxb] + base;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int li = r * 32 + lane;
+      const bool valid = a_key[r] != kDeadKey;
       // set aside: the slot and t_rem, negative when the flight ends in a collision
-      const unsigned lmask = __ballot_sync(full, later);
-      if (later) {
+      const unsigned lmask = __ballot_sync(full, a_later[r]);
+      if (a_later[r]) {
         const unsigned pos = nl + __popc(lmask & ((1u << lane) - 1u));
         s_li[warp][pos] = (uint32_t)(base + li);
-        s_lt[warp][pos] = collided ? -t_rem : t_rem;
+        s_lt[warp][pos] = a_col[r] ? -a_tr[r] : a_tr[r];
       }
-      __syncwarp();
       nl += __popc(lmask);
-      if (nl >= 32u) run_set_aside(32u);
-      const bool fin = valid && !later;
-      const float xn = fminf(fmaxf(fmaf(vf * ox, t_rem, xi), 0.0f), dxf);
+      const bool fin = valid && !a_later[r];
+      const bool collided = a_col[r];
       if (fin) {   // in place: slot i of the other buffer (i < n_surv <= capacity)
-        o_x[li] = xn;
-        o_ox[li] = ox;
-        o_nu[li] = nu;
-        o_w[li] = w;
-        o_id[li] = id;
-        o_key[li] = collided ? kDeadKey : key;
+        o_x[li] = a_x[r];
+        o_ox[li] = a_ox[r];
+        o_nu[li] = a_nu[r];
+        o_w[li] = a_w[r];
+        o_id[li] = a_id[r];
+        o_key[li] = collided ? kDeadKey : a_key[r];
       }
       // E_surv and the sort counts of the survivors (the particle stayed in
       // its cell, so W is unchanged), summed per thread while its bin stays
       // the same: a lane's successive particles are 32 slots apart in the
       // bin-sorted input, so nearly always in one bin
       if (fin && !collided) {
-        const long long wq = to_fixed_f(w, tq_shift, &ctrl->status);
-        if ((int)key != acc_key || acc_n == 32u) {
+        const long long wq = to_fixed_f(a_w[r], tq_shift, &ctrl->status);
+        if ((int)a_key[r] != acc_key || acc_n == 32u) {
           if (acc_n) {
             atomic_add_fixed(d.Esq + 2 * (long long)acc_key, acc_w);
             atomicAdd(d.sort_cnt + acc_key, acc_n);
           }
-          acc_key = (int)key;
+          acc_key = (int)a_key[r];
           acc_w = 0;
           acc_n = 0u;
         }
@@ -1278,87 +1346,22 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
       if (d.rec && fin && base + li < d.rec_cap) {
         P32 q;
         clear32(q);
-        q.xi = xn; q.ox = ox; q.nu = nu; q.w = w; q.id = id;
-        q.cx = (int)cell; q.g = (int)(key - cell * G);
-        q.fate = collided ? FATE_ABSORBED : FATE_SURVIVED; q.nseg = 1; q.t_tra = t_rem; q.cell0 = (int)cell;
+        const uint32_t cell = a_cell[r];
+        q.xi = a_x[r]; q.ox = a_ox[r]; q.nu = a_nu[r]; q.w = a_w[r]; q.id = a_id[r];
+        q.cx = (int)cell; q.g = (int)(a_key[r] - cell * G);
+        q.fate = collided ? FATE_ABSORBED : FATE_SURVIVED; q.nseg = 1; q.t_tra = a_tr[r]; q.cell0 = (int)cell;
         record32<1>(d, q, base + li, (int)cell);
       }
     }
     __syncwarp();
-    if (c + kStages < nchunks) {
-      if (lane == 0) rg.issue(&d, h0.cur, c + kStages, h0.n_surv, st);
-      ++issued;
-    }
-    __syncwarp();
+    while (nl >= 32u) run_set_aside(32u);
   }
+  while (nl >= 32u) run_set_aside(32u);   // (only after a failed wait)
   if (nl) run_set_aside(nl);
   // the last runs: the warp's lanes mostly end in the same bin
   warp_run_add_fixed_n(d.Esq, acc_n ? acc_key : -1 - lane, acc_w, acc_n, d.sort_cnt);
   if (lane == 0)
     for (int kk = k; kk < issued; ++kk) mbar_wait_bounded(&rg.bar[kk % kStages], (unsigned)(kk / kStages) & 1u);
-  flush_counters_block(ctrl, cnt);
-}
-
-// The newborns of a step whose survivors take k_stream32_fast, one per
-// thread (they need nothing from the survivor kernel, so a step graph runs
-// them beside it).  The birth offsets are searched in shared memory when
-// they fit.
-constexpr int kSmemBins = 8192;
-
-template <int DIM>
-__global__ void __launch_bounds__(256) k_stream32_rest(const __grid_constant__ Dev d) {
-  extern __shared__ __align__(128) unsigned char s_dyn[];
-  const int lane = threadIdx.x & 31;
-  const Tab32 tab = load_tab32<false>(d, s_dyn);
-  const bool off_sm = d.nbins + 1 <= kSmemBins;
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dyn + tab32_bytes(tab));
-  if (off_sm)
-    for (int b = threadIdx.x; b <= d.nbins; b += blockDim.x) s_off[b] = __ldg(d.off + b);
-  __syncthreads();
-  const uint32_t* off = off_sm ? s_off : d.off;
-  const StepHead h0 = step_head(d);
-  Ctrl* ctrl = d.ctrl;
-  const long long total = h0.n_tot - h0.n_surv;
-  const unsigned cur = h0.cur, nxb = cur ^ 1u;
-  const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
-  Counters cnt;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  // whole warps to the loop bound, so the warp intrinsics see every lane
-  const long long bound = (total + 31) & ~31ll;
-  (void)cur;
-  for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < bound; jj += stride) {
-    const bool valid = jj < total;
-    P32 q;
-    clear32(q);
-    DrawsF rng;
-    long long i = 0;
-    if (valid) {
-      i = h0.n_surv + jj;
-      birth32<DIM>(d, q, rng, (uint32_t)jj, h0.step, off);
-    } else {
-      rng.init(0ull, h0.step, 0u);
-    }
-    q.cell0 = q.gside >= 0 ? q.cx : (q.cz * ny + q.cy) * nx + q.cx;
-    q.ghost = q.gside >= 0;
-    const float inup = (!valid || d.grey) ? 1.0f : pow_fast_f(q.nu, -d.spf);
-    bool more = false;
-    if (valid) more = first_flight32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
-    if (more) stream_loop32<DIM>(d, q, rng, inup, tab.n, tab.invT, tab.sinv, tab.sinvT);
-    const int cell = (q.cz * ny + q.cy) * nx + q.cx;
-    bool stored = false;
-    if (valid) stored = store32<DIM>(d, nxb, q, i, cell);
-    const long long wq = valid ? to_fixed_f(q.w, d.tq_shift, &ctrl->status) : 0ll;
-    warp_run_add_fixed(d.Esq, stored ? cell * G + q.g : -1 - lane, wq, d.sort_cnt);
-    if (valid) {
-      cross_tallies32(d, q, cell, wq);
-      cnt.seg += (unsigned)q.nseg;
-      cnt.abs += q.fate == FATE_ABSORBED;
-      cnt.esc += q.fate == FATE_ESCAPED;
-      cnt.surv += q.fate == FATE_SURVIVED;
-      cnt.rem += q.fate == FATE_REMOVED;
-      record32<DIM>(d, q, i, cell);
-    }
-  }
   flush_counters_block(ctrl, cnt);
 }
 
@@ -1383,27 +1386,25 @@ static cudaError_t launch_stream64_t(const Dev& d, const Ens& e, const StreamSha
 
 static size_t table32_bytes(const Dev& d) { return (4 * (size_t)stream32_table_floats(d) + 127) & ~(size_t)127; }
 
-// the survivor kernel's companion: the newborns
-template <int DIM>
-static cudaError_t launch_rest32(const Dev& d, cudaStream_t s) {
-  const size_t tab = table32_bytes(d);
-  const size_t offb = d.nbins + 1 <= kSmemBins ? 4 * (size_t)(d.nbins + 1) : 0;
-  const size_t dyn = tab + offb;
-  if (dyn > 48 * 1024) cudaFuncSetAttribute(k_stream32_rest<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  // enough threads to hold every newborn of a typical step at once (their
-  // chains are latency-bound)
-  k_stream32_rest<DIM><<<sm_count() * 4, 256, dyn, s>>>(d);
-  return cudaGetLastError();
-}
-
 // 1D problems that take the survivor kernel (see launch_stream32_t)
 static bool split32(const Dev& d) {
   return d.dim == 1 && d.v * d.dt / d.dx < 0.25 && d.sig_law == 0 && d.ncell <= kSmemCells;
 }
 
+template <int NT>
+static const void* fast_fn(bool p3, int ppt) {
+  if (p3) {
+    if (ppt >= 4) return (const void*)k_stream32_fast<NT, true, 4>;
+    if (ppt == 2) return (const void*)k_stream32_fast<NT, true, 2>;
+    return (const void*)k_stream32_fast<NT, true, 1>;
+  }
+  if (ppt >= 4) return (const void*)k_stream32_fast<NT, false, 4>;
+  if (ppt == 2) return (const void*)k_stream32_fast<NT, false, 2>;
+  return (const void*)k_stream32_fast<NT, false, 1>;
+}
+
 template <int DIM, bool ENS, int NT>
-static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s,
-                                     bool newborns_elsewhere) {
+static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
   const int sms = sm_count();
   const int C = 32 * sh.ppt;
   const size_t tab = ENS ? 0 : table32_bytes(d);
@@ -1411,15 +1412,13 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
   const int bi = NT == 128 ? 0 : (NT == 512 ? 2 : 1);
   // a 1D problem whose particles seldom reach a face in a step (a particle
   // crosses at most v dt / dx cells) with the power-law opacity held in
-  // shared memory: the survivor kernel, and the newborns' kernel (on a side
-  // stream of the step graph, else after it)
+  // shared memory: the survivor kernel (newborns included)
   const bool split = !ENS && DIM == 1 && split32(d);
   const bool p3 = !d.grey && d.sig_p == -3.0;
-  const void* fn = !split ? (const void*)k_stream32<DIM, ENS, NT>
-                          : (p3 ? (const void*)k_stream32_fast<NT, true> : (const void*)k_stream32_fast<NT, false>);
+  const void* fn = !split ? (const void*)k_stream32<DIM, ENS, NT> : fast_fn<NT>(p3, sh.ppt);
   int& occ = g_stream32_occ[DIM][ENS][bi];
   int& occ_dyn = g_stream32_occ_dyn[DIM][ENS][bi];
-  const int key = (int)dyn * 4 + (split ? 1 : 0) + (p3 ? 2 : 0);
+  const int key = ((int)dyn * 4 + (split ? 1 : 0) + (p3 ? 2 : 0)) * 8 + sh.ppt;
   if (!occ || occ_dyn != key) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, dyn);
@@ -1431,49 +1430,40 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
     k_stream32<DIM, ENS, NT><<<sms * per, NT, dyn, s>>>(d, e, sh.ppt);
     return cudaGetLastError();
   }
-  if (p3) k_stream32_fast<NT, true><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
-  else k_stream32_fast<NT, false><<<sms * per, NT, dyn, s>>>(d, sh.ppt);
-  cudaError_t r = cudaGetLastError();
-  if (r || newborns_elsewhere) return r;
-  return launch_rest32<DIM>(d, s);
+  void* args[] = {(void*)&d};
+  cudaError_t r = cudaLaunchKernel(fn, dim3(sms * per), dim3(NT), args, dyn, s);
+  if (!r) r = cudaGetLastError();
+  return r;
 }
 
 template <int DIM, bool ENS>
-static cudaError_t launch_stream32_nt(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s,
-                                      bool newborns_elsewhere) {
-  if (sh.block == 128) return launch_stream32_t<DIM, ENS, 128>(d, e, sh, s, newborns_elsewhere);
-  if (sh.block == 512) return launch_stream32_t<DIM, ENS, 512>(d, e, sh, s, newborns_elsewhere);
-  return launch_stream32_t<DIM, ENS, 256>(d, e, sh, s, newborns_elsewhere);
+static cudaError_t launch_stream32_nt(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
+  if (sh.block == 128) return launch_stream32_t<DIM, ENS, 128>(d, e, sh, s);
+  if (sh.block == 512) return launch_stream32_t<DIM, ENS, 512>(d, e, sh, s);
+  return launch_stream32_t<DIM, ENS, 256>(d, e, sh, s);
 }
 
 template <bool ENS>
-static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s,
-                                     bool newborns_elsewhere) {
+static cudaError_t launch_stream_dim(const Dev& d, const Ens& e, int mixed, const StreamShape& sh, cudaStream_t s) {
   if (d.dim == 3) {   // single problems only (ensembles are 1D/2D)
     if (ENS) return cudaErrorNotSupported;
-    return mixed ? launch_stream32_nt<3, false>(d, e, sh, s, false) : launch_stream64_t<3, false, 1>(d, e, sh, s);
+    return mixed ? launch_stream32_nt<3, false>(d, e, sh, s) : launch_stream64_t<3, false, 1>(d, e, sh, s);
   }
   if (d.dim == 2) {
-    if (mixed) return launch_stream32_nt<2, ENS>(d, e, sh, s, false);
+    if (mixed) return launch_stream32_nt<2, ENS>(d, e, sh, s);
     if (sh.ppt >= 2) return launch_stream64_t<2, ENS, 2>(d, e, sh, s);
     return launch_stream64_t<2, ENS, 1>(d, e, sh, s);
   }
-  if (mixed) return launch_stream32_nt<1, ENS>(d, e, sh, s, newborns_elsewhere);
+  if (mixed) return launch_stream32_nt<1, ENS>(d, e, sh, s);
   if (sh.ppt >= 2) return launch_stream64_t<1, ENS, 2>(d, e, sh, s);
   return launch_stream64_t<1, ENS, 1>(d, e, sh, s);
 }
 
-bool stream_newborns_apart(const Dev& d, const Ens* e) {
-  return !(e && e->M > 1) && d.precision == 1 && split32(d);
-}
-
-cudaError_t launch_stream_newborns(const Dev& d, cudaStream_t s) { return launch_rest32<1>(d, s); }
-
-cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s, bool newborns_elsewhere) {
+cudaError_t launch_stream(const Dev& d, const Ens* e, const StreamShape& sh, cudaStream_t s) {
   const int mixed = d.precision == 1;
-  if (e && e->M > 1) return launch_stream_dim<true>(d, *e, mixed, sh, s, false);
+  if (e && e->M > 1) return launch_stream_dim<true>(d, *e, mixed, sh, s);
   const Ens none{};
-  return launch_stream_dim<false>(d, none, mixed, sh, s, newborns_elsewhere);
+  return launch_stream_dim<false>(d, none, mixed, sh, s);
 }
 
 }  // namespace ugkwp
