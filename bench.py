@@ -721,6 +721,9 @@ def main():
     ap.add_argument("--no-checkerboard", action="store_true", help="skip the 2D checkerboard leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the opacity-gradient leg")
     ap.add_argument("--checkerboard-particles", type=int, default=20_000_000)
+    ap.add_argument("--launch", default=None,
+                    help="particle-kernel launch shape BLOCK,PPT[,PER] of a --quick run (profiling the shape a "
+                         "full run's autotuner chose)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -749,16 +752,28 @@ def main():
     p_head = p.replace(precision=I.MIXED if head_mixed else I.FP64)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
-    def prepare(prob):
+    shapes = {}
+
+    def prepare(prob, tune):
+        # warm-up steps, the library's autotuner (the particle kernel's launch
+        # shape timed on identical steps from a saved state), more warm-up
         sim = B.Simulation(prob, device=dev)
         sim.set_state(s["T"], s["rho"], s["rho_h"], s["particles"], step=s["step"])
         for _ in range(max(args.warmup, 3)):
             sim.step(1)
+        if tune:
+            shapes[tune] = sim.autotune(steps=3)
+            for _ in range(3):
+                sim.step(1)
+        elif args.launch:
+            sim.set_launch(*[int(x) for x in args.launch.split(",")])
+            for _ in range(3):
+                sim.step(1)
         assert sim.tallies()["status_bits"] == 0
         return sim
 
-    sim = prepare(p_head)
-    sim64 = None if args.quick else prepare(p.replace(precision=I.FP64))
+    sim = prepare(p_head, None if args.quick else "mixed" if head_mixed else "fp64")
+    sim64 = None if args.quick else prepare(p.replace(precision=I.FP64), "fp64")
 
     # ---- timed region: whole steps as CUDA-graph replays (the headline build,
     # then the plain FP64 build it is compared with), device time from events
@@ -795,6 +810,10 @@ def main():
             "phase_timing": "the same step launched kernel by kernel, events between phases (%d more steps)" % K,
             "particles_per_step": n_in / K, "si_iters_per_step": si / K,
             "roofline": roof, "particle_kernel_roofline": roof_p, "clocks": clocks}
+    if shapes:
+        line["launch_shape"] = {k: {"block": v["block"], "particles_per_thread": v["particles_per_thread"],
+                                    "blocks_per_sm": v["blocks_per_sm"]} for k, v in shapes.items()}
+        line["launch_shape"]["how"] = "ugkwp_autotune: each candidate shape timed on 3 steps from the same saved state"
 
     if sim64 is not None:
         ph64, _, (qn_in, qn_rd), qn_out, qsi = timed_steps(sim64, K, flush)

@@ -512,7 +512,7 @@ struct Ctrl {
   unsigned int bar_timeout_spins; // bounded-wait limit (0: default)
   unsigned int bar_extra;         // arrivals a barrier also waits for (failure injection; 0)
   unsigned int scaled;            // some survivors' weights need scaling this step
-  unsigned int fin_count;         // blocks done in the end-of-step kernel (0 between steps)
+  unsigned int pad4_;
   unsigned long long tile_next;   // next particle tile to hand out (particle kernel; 0 at step start)
   unsigned long long pad3_;
   unsigned int n_scaled_bins;     // (cell, group) bins whose survivors were scaled this step
@@ -982,6 +982,39 @@ __device__ __forceinline__ unsigned long long load_acquire_u64(const unsigned lo
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Hint: bring the 128-byte line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The error slots (T and rho) of the iterate just finished and of its
+// predecessor, read after a grid barrier: relaxed GPU-scope loads (coherent
+// at L2), all four in flight at once.  The barrier's acquire and block
+// barrier already order them after every block's updates; acquire loads
+// here would make each wait for the one before it.
+struct ErrPair {
+  double eT, eR, pT, pR;
+};
+__device__ __forceinline__ ErrPair load_err_slots(const unsigned long long (*slot)[2], int it) {
+  unsigned long long a, b, c, e;
+  const unsigned long long* s0 = slot[it % 3];
+  const unsigned long long* s1 = slot[(it + 2) % 3];
+  asm volatile(
+      "ld.relaxed.gpu.global.u64 %0, [%4];\n\t"
+      "ld.relaxed.gpu.global.u64 %1, [%5];\n\t"
+      "ld.relaxed.gpu.global.u64 %2, [%6];\n\t"
+      "ld.relaxed.gpu.global.u64 %3, [%7];"
+      : "=l"(a), "=l"(b), "=l"(c), "=l"(e)
+      : "l"(s0), "l"(s0 + 1), "l"(s1), "l"(s1 + 1)
+      : "memory");
+  ErrPair r;
+  r.eT = __longlong_as_double((long long)a);
+  r.eR = __longlong_as_double((long long)b);
+  r.pT = __longlong_as_double((long long)c);
+  r.pR = __longlong_as_double((long long)e);
+  return r;
 }
 
 // --------------------------------------------------------------------------

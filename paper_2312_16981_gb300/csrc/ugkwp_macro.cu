@@ -636,7 +636,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, Ctrl* status_c
       const unsigned int c = load_acquire_u32(count);
       if (c >= target) break;
       if (++spins > limit) { to = 1; break; }
-      __nanosleep(64);
+      if (spins > 256) __nanosleep(64);   // back off only on a long wait
     }
     if (to) atomicOr(&status_ctrl->status, ST_TIMEOUT);
     __threadfence();
@@ -941,8 +941,9 @@ __device__ __forceinline__ float si_iterate_f(const Dev& d, int c, int cur, bool
 // the fluxes through shared memory; both form Q, the sums and T^{k+1} (the
 // same operations, so the same bits); then warp 0 evaluates the Planck
 // values while warp 1 updates rho and evaluates the opacities, tau and q.
-// Outside the iterates warp 0 does the cell's work.  The results are
-// bitwise those of one warp per cell.
+// The prologue and epilogue are split the same way (warp 0: R, T and the
+// rho^p/rho^h split; warp 1: the ledger sums and the kept state).  The
+// results are bitwise those of one warp per cell.
 // The cell a lane serves in work item q: an item is one warp's 32/seg
 // cells of one member (seg from the member's G, 32 in pair mode); a segment
 // past the member's last cell gets its last cell and G = 0 (no group work,
@@ -970,7 +971,6 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const long long gw = PAIR ? (long long)blockIdx.x : blockIdx.x * (long long)nwb + wib;
   const long long nw = PAIR ? (long long)gridDim.x : (long long)gridDim.x * nwb;
-  const bool lead = !PAIR || wib == 0;
   // work items: one warp's cells (several per warp where G <= 16)
   const int cpw0 = PAIR ? 1 : 32 / seg_width(d0.G);
   const long long nitems = ENS ? e.total_items : ((long long)d0.ncell + cpw0 - 1) / cpw0;
@@ -985,11 +985,37 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
   __shared__ double s_pair[PAIR ? 2 : 1][PAIR ? 32 * NC : 1];   // PAIR: the two faces' fluxes
   unsigned int bar = 0;
 
-  // ---- prologue
+  // The first iterate's inputs into L2 while the prologue runs: the Planck
+  // and C2 interpolant tables (a share per block) and, where the previous
+  // step left the iterate state, each cell's own rows of it (the neighbours'
+  // rows are their own cells')
+  {
+    constexpr int kLp = (int)((sizeof(kPlanckTab) + 127) / 128), kLc = (int)((sizeof(kC2Tab) + 127) / 128);
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < kLp + kLc;
+         l += (long long)gridDim.x * blockDim.x)
+      prefetch_l2(l < kLp ? (const void*)((const char*)kPlanckTab + 128 * l)
+                          : (const void*)((const char*)kC2Tab + 128 * (l - kLp)));
+    if (!ENS && !warm && d0.ctrl->si_state_ok) {
+      for (long long gq = gw; gq < nitems; gq += nw) {
+        const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
+        const long long i = (long long)sc.c * sc.G + sc.L.sl;
+        if (sc.L.sl < sc.G && (sc.L.sl & 15) == 0) {   // one lane per 128-byte line
+          prefetch_l2(d0.tauk[0] + i);
+          prefetch_l2(d0.phik[0] + i);
+          prefetch_l2(d0.qk + i);
+          prefetch_l2(d0.dphik + i);
+        }
+      }
+    }
+  }
+
+  // ---- prologue.  A pair splits it: warp 0 forms R (and the state on a
+  // first step), warp 1 the energy sums of the ledger.
+  const bool roleA = !PAIR || wib == 0, roleB = !PAIR || wib == 1;
   {
     double e_rad0 = 0.0, e_mat0 = 0.0, e_src = 0.0;
     int acc_m = -1;
-    for (long long gq = lead ? gw : nitems; gq < nitems; gq += nw) {
+    for (long long gq = gw; gq < nitems; gq += nw) {
       const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
       const int m = sc.m;
       if (ENS && m != acc_m && acc_m >= 0) {
@@ -1018,32 +1044,41 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (g < G) {
           const int i = c * G + g;
           const double r0 = d.rho[i];
-          double r = r0;
-          for (int axis = 0; axis < d.dim; ++axis) {
-            const int fl = face_index_xyz(d, ix, iy, iz, axis, -1), fr = face_index_xyz(d, ix, iy, iz, axis, +1);
-            r += (dt * inv_h_of(d, axis)) * (d.Fwave[fl * G + g] - d.Fwave[fr * G + g]);
+          if (roleA) {
+            double r = r0;
+            for (int axis = 0; axis < d.dim; ++axis) {
+              const int fl = face_index_xyz(d, ix, iy, iz, axis, -1), fr = face_index_xyz(d, ix, iy, iz, axis, +1);
+              r += (dt * inv_h_of(d, axis)) * (d.Fwave[fl * G + g] - d.Fwave[fr * G + g]);
+            }
+            const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
+            d.W[i] = Wd;
+            r += Wd * d.inv_vol;
+            if (src_on) r += d.src[i];
+            d.R[i] = r;
+            if (warm) d.R_f[i] = d2f_trunc(r);
           }
-          const double Wd = from_fixed(d.Wq + 2 * i, d.tq);
-          d.W[i] = Wd;
-          r += Wd * d.inv_vol;
-          if (src_on) { r += d.src[i]; e_src += V * d.src[i] * d.inv_c; }
-          d.R[i] = r;
-          if (warm) d.R_f[i] = d2f_trunc(r);
-          e_rad0 += V * r0 * d.inv_c;
+          if (roleB) {
+            if (src_on) e_src += V * d.src[i] * d.inv_c;
+            e_rad0 += V * r0 * d.inv_c;
+          }
         }
       }
       const double T = d.T[c];
-      if (L.sl == 0 && G > 0) e_mat0 += V * mat_energy(d, c, T);
-      if (warm) si_state_f<NC>(d, c, d2f_trunc(T), 0, L, G);
-      else if (!d.ctrl->si_state_ok) {
-        double invT, sT;
-        inv_and_sigma_T(d, c, T, &invT, &sT);
-        si_state<NC>(d, c, T, invT, sT, 0, L, G);
+      if (roleB && L.sl == 0 && G > 0) e_mat0 += V * mat_energy(d, c, T);
+      if (roleA) {
+        if (warm) si_state_f<NC>(d, c, d2f_trunc(T), 0, L, G);
+        else if (!d.ctrl->si_state_ok) {
+          double invT, sT;
+          inv_and_sigma_T(d, c, T, &invT, &sT);
+          si_state<NC>(d, c, T, invT, sT, 0, L, G);
+        }
       }
     }
-    warp_sum2(e_rad0, e_src);
-    e_mat0 = warp_sum(e_mat0);   // a warp carries several cells where G <= 16
-    if (lane == 0 && acc_m >= 0) {
+    if (roleB) {   // (warp-uniform)
+      warp_sum2(e_rad0, e_src);
+      e_mat0 = warp_sum(e_mat0);   // a warp carries several cells where G <= 16
+    }
+    if (roleB && lane == 0 && acc_m >= 0) {
       Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
       atomicAdd(&cc->E_rad0, e_rad0);
       atomicAdd(&cc->E_mat0, e_mat0);
@@ -1113,8 +1148,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
           cc->err_slot[(it + 1) % 3][1] = 0ull;
         }
       if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
-      const double eA = __longlong_as_double((long long)load_acquire_u64(&ctrlA->err_slot[it % 3][0]));
-      const double pA = __longlong_as_double((long long)load_acquire_u64(&ctrlA->err_slot[(it + 2) % 3][0]));
+      const ErrPair ep = load_err_slots(ctrlA->err_slot, it);
+      const double eA = ep.eT, pA = ep.pT;
       const bool stalled = itA > 0 && eA <= 1e-4 && eA > 0.5 * pA;
       if (!(eA <= 1e30) || eA <= kWarmTol || stalled || itA + 1 >= maxA) { ++itA; ++it; break; }
     }
@@ -1325,11 +1360,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     if (!grid_barrier(bar_count, st_ctrl, spin_limit, (++bar) * gridDim.x)) return;
     if (!ENS) {
       Ctrl* ctrl = d0.ctrl;
-      const double eT = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][0]));
-      const double eR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[it % 3][1]));
-      const double pT = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[(it + 2) % 3][0]));
-      const double pR = __longlong_as_double((long long)load_acquire_u64(&ctrl->err_slot[(it + 2) % 3][1]));
-      if (si_converged(eT, eR, pT, pR, d0.si_tol, itB > 0)) { s_conv[0] = itB + 1; all_done = 1; ++itB; ++it; break; }
+      const ErrPair ep = load_err_slots(ctrl->err_slot, it);
+      if (si_converged(ep.eT, ep.eR, ep.pT, ep.pR, d0.si_tol, itB > 0)) { s_conv[0] = itB + 1; all_done = 1; ++itB; ++it; break; }
     } else {
       if (threadIdx.x == 0) s_any = 0;
       __syncthreads();
@@ -1337,11 +1369,8 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       for (int k = threadIdx.x; k < M; k += blockDim.x) {
         if (s_conv[k]) continue;
         Ctrl* cc = e.devs[k].ctrl;
-        const double eT = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][0]));
-        const double eR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[it % 3][1]));
-        const double pT = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[(it + 2) % 3][0]));
-        const double pR = __longlong_as_double((long long)load_acquire_u64(&cc->err_slot[(it + 2) % 3][1]));
-        if (si_converged(eT, eR, pT, pR, e.devs[k].si_tol, itB > 0)) s_conv[k] = itB + 1; else running = 1;
+        const ErrPair ep = load_err_slots(cc->err_slot, it);
+        if (si_converged(ep.eT, ep.eR, ep.pT, ep.pR, e.devs[k].si_tol, itB > 0)) s_conv[k] = itB + 1; else running = 1;
       }
       if (running) s_any = 1;
       __syncthreads();
@@ -1349,11 +1378,14 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
     }
   }
 
-  // ---- epilogue: member m's last iterate wrote Tk[s_conv[m] & 1] (or Tk[itB & 1])
+  // ---- epilogue: member m's last iterate wrote Tk[s_conv[m] & 1] (or
+  // Tk[itB & 1]).  A pair splits it: warp 0 stores T and splits rho into
+  // rho^p and rho^h, warp 1 keeps the last iterate's state and sums the
+  // ledger.
   {
     double e_rad1 = 0.0, e_mat1 = 0.0, b_in = 0.0;
     int bad = 0, scaled = 0, acc_m = -1;
-    for (long long gq = lead ? gw : nitems; gq < nitems; gq += nw) {
+    for (long long gq = gw; gq < nitems; gq += nw) {
       const SiCell sc = si_cell<ENS, PAIR>(d0, e, gq);
       const int m = sc.m;
       if (ENS && m != acc_m && acc_m >= 0) {
@@ -1383,18 +1415,18 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
       const double T = __ldcg(d.Tk[fin] + c);
       // the last iterate's state (at T^{n+1}) into slot 0, where the next
       // step's iteration starts from it instead of re-evaluating it
-      if (fin == 1 && !warm) {
+      if (roleB && fin == 1 && !warm) {
         if (L.sl == 0 && G > 0) __stcg(d.Tk[0] + c, T);
         for (int g = L.sl; g < G; g += L.seg) {
           __stcg(d.tauk[0] + c * G + g, __ldcg(d.tauk[1] + c * G + g));
           __stcg(d.phik[0] + c * G + g, __ldcg(d.phik[1] + c * G + g));
         }
       }
-      if (G > 0 && (!(T == T) || T > 1e300)) bad = 1;
-      if (L.sl == 0 && G > 0) {
-        d.T[c] = T;
-        e_mat1 += V * mat_energy(d, c, T);
+      if (roleA) {
+        if (G > 0 && (!(T == T) || T > 1e300)) bad = 1;
+        if (L.sl == 0 && G > 0) d.T[c] = T;
       }
+      if (roleB && L.sl == 0 && G > 0) e_mat1 += V * mat_energy(d, c, T);
       int ixyz[3];
       cell_xyz(d, c, &ixyz[0], &ixyz[1], &ixyz[2]);
 #pragma unroll
@@ -1403,50 +1435,60 @@ __global__ void __launch_bounds__(256) k_si(const __grid_constant__ Dev d0, cons
         if (g >= G) continue;
         const int i = c * G + g;
         const double r = __ldcg(d.rho + i);
-        // survivors never hold more than rho^{n+1} leaves in their (cell,
-        // group): their weights are scaled to it (rho and the energy unchanged)
-        const double Es = from_fixed(d.Esq + 2 * i, d.tq);
-        d.E_surv[i] = Es;
-        double rp = Es * d.inv_vol, f = 1.0;
-        if (!d.split_literal && rp > 0.0 && r < rp) {
-          f = r > 0.0 ? r / rp : 0.0;
-          rp = r > 0.0 ? r : 0.0;
-          scaled += 1;
-        }
-        d.wscale[i] = f;
-        d.rho_p[i] = rp;
-        d.rho_h[i] = r - rp;
-        e_rad1 += V * r * d.inv_c;
-        // boundary faces: energy entering the domain
-        for (int axis = 0; axis < d.dim; ++axis) {
-          const double S = d.area[axis];
-          const int k = ixyz[axis], nk = axis == 0 ? d.nx : (axis == 1 ? d.ny : d.nz);
-          if (k == 0) {
-            const int f = face_index(d, c, axis, -1);
-            b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
+        if (roleA) {
+          // survivors never hold more than rho^{n+1} leaves in their (cell,
+          // group): their weights are scaled to it (rho and the energy unchanged)
+          const double Es = from_fixed(d.Esq + 2 * i, d.tq);
+          d.E_surv[i] = Es;
+          double rp = Es * d.inv_vol, f = 1.0;
+          if (!d.split_literal && rp > 0.0 && r < rp) {
+            f = r > 0.0 ? r / rp : 0.0;
+            rp = r > 0.0 ? r : 0.0;
+            scaled += 1;
           }
-          if (k == nk - 1) {
-            const int f = face_index(d, c, axis, +1);
-            b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
+          d.wscale[i] = f;
+          d.rho_p[i] = rp;
+          d.rho_h[i] = r - rp;
+        }
+        if (roleB) {
+          e_rad1 += V * r * d.inv_c;
+          // boundary faces: energy entering the domain
+          for (int axis = 0; axis < d.dim; ++axis) {
+            const double S = d.area[axis];
+            const int k = ixyz[axis], nk = axis == 0 ? d.nx : (axis == 1 ? d.ny : d.nz);
+            if (k == 0) {
+              const int f = face_index(d, c, axis, -1);
+              b_in += dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
+            }
+            if (k == nk - 1) {
+              const int f = face_index(d, c, axis, +1);
+              b_in -= dt * S * (d.Feq[f * G + g] + d.Fwave[f * G + g]) * d.inv_c;
+            }
           }
         }
       }
     }
-    warp_sum2(e_rad1, b_in);
-    e_mat1 = warp_sum(e_mat1);
-    bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
-    if (lane == 0 && acc_m >= 0) {
-      Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
-      atomicAdd(&cc->E_rad1, e_rad1);
-      atomicAdd(&cc->E_mat1, e_mat1);
-      if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
-      if (bad) atomicOr(&cc->status, ST_NONFINITE);
+    if (roleB) {   // (warp-uniform)
+      warp_sum2(e_rad1, b_in);
+      e_mat1 = warp_sum(e_mat1);
+      if (lane == 0 && acc_m >= 0) {
+        Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
+        atomicAdd(&cc->E_rad1, e_rad1);
+        atomicAdd(&cc->E_mat1, e_mat1);
+        if (b_in != 0.0) atomicAdd(&cc->bnd_in_macro, b_in);
+      }
     }
-    const unsigned sc_n = __reduce_add_sync(0xffffffffu, (unsigned)scaled);
-    if (sc_n && lane == 0 && acc_m >= 0) {
-      Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
-      atomicOr(&cc->scaled, 1u);
-      atomicAdd(&cc->n_scaled_bins, sc_n);
+    if (roleA) {
+      bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
+      const unsigned sc_n = __reduce_add_sync(0xffffffffu, (unsigned)scaled);
+      if (lane == 0 && acc_m >= 0) {
+        Ctrl* cc = ENS ? e.devs[acc_m].ctrl : d0.ctrl;
+        if (bad) atomicOr(&cc->status, ST_NONFINITE);
+        if (sc_n) {
+          atomicOr(&cc->scaled, 1u);
+          atomicAdd(&cc->n_scaled_bins, sc_n);
+        }
+      }
     }
   }
   if (blockIdx.x == 0) {
@@ -1543,9 +1585,24 @@ __device__ __forceinline__ void scale_weights(const Dev& d, unsigned b, long lon
       todo &= todo - 1;
       const double fk = __shfl_sync(full, f, l);
       const long long end = (long long)d.sort_off[k0 + l], begin = end - (long long)d.sort_cnt[k0 + l];
-      for (long long i = begin + lane; i < end; i += 32) {
-        if (mixed) d.fw[b][i] = (float)((double)d.fw[b][i] * fk);
-        else d.pw[b][i] *= fk;
+      // 256 weights a pass, their loads issued together (a run is a few
+      // hundred survivors; one load round trip per weight would serialise)
+      for (long long i0 = begin + lane; i0 < end; i0 += 256) {
+        if (mixed) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < end ? d.fw[b][i0 + 32 * u] : 0.0f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (i0 + 32 * u < end) d.fw[b][i0 + 32 * u] = (float)((double)v[u] * fk);
+        } else {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < end ? d.pw[b][i0 + 32 * u] : 0.0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (i0 + 32 * u < end) d.pw[b][i0 + 32 * u] = v[u] * fk;
+        }
       }
     }
   }
@@ -1560,41 +1617,33 @@ __global__ void __launch_bounds__(256) k_scale_survivors(const __grid_constant__
 }
 
 // End of step of a single problem in one launch: the sorted survivors'
-// weights are scaled in the input buffer, then the last block to finish
-// records their count, advances the step and sums the particle ledger (every
-// block has read the control block before it counts itself done).
+// weights are scaled in the input buffer (the bins the split capped), and
+// block 0 records their count, advances the step and sums the particle
+// ledger.  The other blocks read only the live-buffer index and the scaled
+// flag of the control block, which block 0 does not write, so no block
+// waits for another.
 __global__ void __launch_bounds__(256) k_finish_step(const __grid_constant__ Dev d) {
   Ctrl* ctrl = d.ctrl;
   const unsigned live = ctrl->cur;
-  const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
-  const long long n = (long long)(no < cap ? no : cap);
-  if (ctrl->scaled)
-    scale_weights(d, live, (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5,
-                  ((long long)gridDim.x * blockDim.x) >> 5);
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(&ctrl->fin_count, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  if (threadIdx.x == 0) {
-    ctrl->n_part[live] = (unsigned long long)n;
-    ctrl->n_part[live ^ 1u] = 0;
-    ctrl->step += 1;
-    ctrl->fin_count = 0;
-  }
-  if (threadIdx.x < 32) {
+  // block 0: the counts and the particle ledger (nothing else in this
+  // kernel reads the words it writes, so it needs no other block)
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
     double pin = 0.0, pout = 0.0;
     for (int i = threadIdx.x; i < 6 * d.G; i += 32) { pin += d.inflow[i]; pout += d.esc[i]; }
     pin = warp_sum(pin);
     pout = warp_sum(pout);
     if (threadIdx.x == 0) {
+      const unsigned long long no = ctrl->n_out, cap = (unsigned long long)d.capacity;
+      ctrl->n_part[live] = no < cap ? no : cap;
+      ctrl->n_part[live ^ 1u] = 0;
+      ctrl->step += 1;
       ctrl->bnd_in_part = pin / d.c;
       ctrl->bnd_out_part = pout / d.c;
     }
   }
+  if (ctrl->scaled)
+    scale_weights(d, live, (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5,
+                  ((long long)gridDim.x * blockDim.x) >> 5);
 }
 
 // --------------------------------------------------------------------------

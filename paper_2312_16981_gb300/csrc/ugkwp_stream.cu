@@ -205,6 +205,18 @@ static int stream32_table_floats(const Dev& d) {
   return d.ncell * (d.sig_law == 1 && !d.grey ? 2 : 1);
 }
 
+// The survivor kernel's table: 1/(sigma0 T^q) per cell, then every 32nd
+// birth offset (off[32 s], the segments the newborns' bin search starts
+// from) when there are at most kSegMax of them.
+constexpr int kSegMax = 1024;
+__host__ __device__ inline int fast_segments(int nbins) {
+  const int ns = (nbins + 31) / 32;
+  return ns <= kSegMax ? ns : 0;
+}
+__host__ __device__ inline size_t fast_table_bytes(int ncell, int nbins) {
+  return (4 * (size_t)ncell + 4 * (size_t)fast_segments(nbins) + 127) & ~(size_t)127;
+}
+
 struct Counters {   // per thread; a thread sees far fewer than 2^32 events
   unsigned seg = 0, abs = 0, esc = 0, surv = 0, rem = 0;
 };
@@ -739,17 +751,11 @@ __device__ __forceinline__ bool store32(const Dev& d, unsigned nxb, const P32& q
 // black-body ghost, the entering set), isotropic direction, frequency by
 // the linear sampler (App. A) and weight.
 template <int DIM>
-__device__ __forceinline__ void birth32(const Dev& d, P32& q, DrawsF& rng, uint32_t j, uint32_t step,
-                                       const uint32_t* off) {
+__device__ __forceinline__ void birth32_in(const Dev& d, P32& q, DrawsF& rng, uint32_t j, uint32_t step,
+                                          int bin, uint32_t off_bin) {
   const int G = d.G, nx = d.nx, ny = DIM >= 2 ? d.ny : 1;
   q.newborn = true;
-  int lo = 0, hi = d.nbins;   // largest bin with off[bin] <= j
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (off[mid] <= j) lo = mid; else hi = mid;
-  }
-  const int bin = lo;
-  const uint32_t kk = j - off[bin];
+  const uint32_t kk = j - off_bin;
   q.id = ((unsigned long long)step << kIdStepShift) | ((unsigned long long)bin << kIdBinShift) |
          (unsigned long long)kk;
   rng.init(q.id, step, 0u);
@@ -794,6 +800,59 @@ __device__ __forceinline__ void birth32(const Dev& d, P32& q, DrawsF& rng, uint3
     q.nu = sample_nu_f(__ldg(d.nu_edges_f + q.g), __ldg(d.nu_edges_f + q.g + 1), __ldg(d.khat_f + bin),
                        rng.next(d.pk));
   q.w = __ldg(d.omega_f + bin);
+}
+
+template <int DIM>
+__device__ __forceinline__ void birth32(const Dev& d, P32& q, DrawsF& rng, uint32_t j, uint32_t step,
+                                       const uint32_t* off) {
+  int lo = 0, hi = d.nbins;   // largest bin with off[bin] <= j
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= j) lo = mid; else hi = mid;
+  }
+  birth32_in<DIM>(d, q, rng, j, step, lo, off[lo]);
+}
+
+// Birth bins of a warp's 32 consecutive ordinals j (lanes with `need`): the
+// largest bin with off[bin] <= j.  The segment of 32 bins holding it comes
+// from a table of every 32nd offset (s_seg, ns entries, in shared memory);
+// then the warp loads one segment's 32 offsets at a time (a segment that
+// some unresolved lane needs) and each of its lanes finds its bin among them
+// by a five-step search over the warp's registers.  Consecutive ordinals
+// share segments, so a warp usually loads one or two.
+__device__ __forceinline__ int birth_bin32(const Dev& d, const uint32_t* s_seg, int ns, uint32_t j, bool need,
+                                          uint32_t* off_bin) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = ns;   // largest segment s with off[32 s] <= j
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_seg[mid] <= j) lo = mid; else hi = mid;
+  }
+  const int seg = lo;
+  int bin = 0;
+  uint32_t ob = 0u;
+  unsigned pend = __ballot_sync(full, need);
+  while (pend) {
+    const int s = __shfl_sync(full, seg, __ffs(pend) - 1);
+    const int b = 32 * s + lane;
+    const uint32_t o = b < d.nbins ? __ldg(d.off + b) : 0xffffffffu;
+    int t = 0;   // largest t with o_t <= j (o_0 <= j for the lanes of this segment)
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const uint32_t ov = __shfl_sync(full, o, t + step);
+      if (ov <= j) t += step;
+    }
+    const uint32_t ot = __shfl_sync(full, o, t);
+    if (need && seg == s) {
+      bin = 32 * s + t;
+      ob = ot;
+      need = false;
+    }
+    pend = __ballot_sync(full, need);
+  }
+  *off_bin = ob;
+  return bin;
 }
 
 // Cell coordinates of a survivor from its bin key (cell c * G + group g).
@@ -918,6 +977,10 @@ struct Ring32 {
     const long long first = lc * C;
     long long n = n_surv - first;
     n = n < 0 ? 0 : (n > C ? C : n);
+    issue_at(dm, cb, first, n, s);
+  }
+  // the same for the n (<= C) survivors from slot `first` (a multiple of 4)
+  __device__ __forceinline__ void issue_at(const Dev* dm, unsigned cb, long long first, long long n, int s) const {
     const unsigned c4 = (unsigned)((n + 3) & ~3ll), c2 = (unsigned)((n + 1) & ~1ll);
     const unsigned bytes = n ? c4 * 4u * StageF<DIM>::kArr4 + c2 * 8u : 0u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1110,11 +1173,14 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
   const unsigned full = 0xffffffffu;
   const int ncell = d.ncell;
   float* s_sinv = reinterpret_cast<float*>(s_dyn);
+  uint32_t* s_seg = reinterpret_cast<uint32_t*>(s_sinv + ncell);
+  const int ns = fast_segments(d.nbins);
   for (int c = threadIdx.x; c < ncell; c += NT) s_sinv[c] = __ldg(d.sTinv_f + c);
+  for (int s = threadIdx.x; s < ns; s += NT) s_seg[s] = __ldg(d.off + 32 * s);
   Ring32<1, false> rg;
   rg.C = C;
   rg.stage_sz = (size_t)C * StageF<1>::kBytesPer;
-  rg.ring = s_dyn + ((4 * (size_t)ncell + 127) & ~(size_t)127) + (size_t)warp * kStages * rg.stage_sz;
+  rg.ring = s_dyn + fast_table_bytes(ncell, d.nbins) + (size_t)warp * kStages * rg.stage_sz;
   rg.bar = s_full[warp];
   if (lane == 0) {
     for (int k = 0; k < kStages; ++k) mbar_init(&rg.bar[k], 1);
@@ -1123,11 +1189,15 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
   __syncthreads();
   const StepHead h0 = step_head(d);
   Ctrl* ctrl = d.ctrl;
-  // a contiguous range of chunks per warp (bins run on across its chunks)
+  // a contiguous range of survivors per warp, equal to within four (bins
+  // run on across its chunks), in chunks of C from its start (the last one
+  // partial)
   const long long gw = (long long)blockIdx.x * (NT / 32) + warp, tw = (long long)gridDim.x * (NT / 32);
   const long long nall = (h0.n_surv + C - 1) / C, per = (nall + tw - 1) / tw;
   const long long c0 = gw * per < nall ? gw * per : nall;
   const long long nchunks = c0 + per < nall ? c0 + per : nall;
+  const long long p0 = 0, p1 = h0.n_surv;
+  auto issue_chunk = [&](long long c, int s) { rg.issue(&d, h0.cur, c, h0.n_surv, s); };
   const unsigned nxb = h0.cur ^ 1u;
   const uint32_t G = (uint32_t)d.G;
   const float invG = d.invG_f;
@@ -1136,7 +1206,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
   const bool grey = d.grey;
   int issued = 0;
   for (; issued < kStages && c0 + issued < nchunks; ++issued)
-    if (lane == 0) rg.issue(&d, h0.cur, c0 + issued, h0.n_surv, issued);
+    if (lane == 0) issue_chunk(c0 + issued, issued);
   __syncwarp();
 
   int acc_key = -1;
@@ -1211,8 +1281,15 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
       P32 q;
       clear32(q);
       DrawsF rng;
-      if (valid) birth32<1>(d, q, rng, (uint32_t)jj, h0.step, d.off);
-      else rng.init(0ull, h0.step, 0u);
+      if (ns) {
+        uint32_t ob;
+        const int bin = birth_bin32(d, s_seg, ns, (uint32_t)jj, valid, &ob);
+        if (valid) birth32_in<1>(d, q, rng, (uint32_t)jj, h0.step, bin, ob);
+        else rng.init(0ull, h0.step, 0u);
+      } else {
+        if (valid) birth32<1>(d, q, rng, (uint32_t)jj, h0.step, d.off);
+        else rng.init(0ull, h0.step, 0u);
+      }
       q.cell0 = q.cx;
       q.ghost = q.gside >= 0;
       const float inup = (!valid || grey) ? 1.0f : pow_fast_f(q.nu, -spf);
@@ -1244,8 +1321,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
       break;
     }
     const StageF<1> sg(rg.ring + st * rg.stage_sz, C);
-    const long long base = c * C;
-    const int nval = (int)(h0.n_surv - base < C ? h0.n_surv - base : C);
+    const long long base = p0 + c * C;
+    const int nval = (int)(p1 - base < C ? p1 - base : C);
     // ---- the first flights of the chunk's R x 32 survivors, independent of
     // one another (so their dependent chains interleave)
     float a_x[R], a_ox[R], a_nu[R], a_w[R], a_tr[R];
@@ -1291,7 +1368,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
     // the stage is consumed: the chunk kStages further on goes into it
     __syncwarp();
     if (c + kStages < nchunks) {
-      if (lane == 0) rg.issue(&d, h0.cur, c + kStages, h0.n_surv, st);
+      if (lane == 0) issue_chunk(c + kStages, st);
       ++issued;
     }
     float* __restrict__ o_x = d.fx[nxb] + base;
@@ -1407,13 +1484,13 @@ template <int DIM, bool ENS, int NT>
 static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamShape& sh, cudaStream_t s) {
   const int sms = sm_count();
   const int C = 32 * sh.ppt;
-  const size_t tab = ENS ? 0 : table32_bytes(d);
-  const size_t dyn = tab + (size_t)(NT / 32) * kStages * stream32_stage_bytes(DIM, C);
-  const int bi = NT == 128 ? 0 : (NT == 512 ? 2 : 1);
   // a 1D problem whose particles seldom reach a face in a step (a particle
   // crosses at most v dt / dx cells) with the power-law opacity held in
   // shared memory: the survivor kernel (newborns included)
   const bool split = !ENS && DIM == 1 && split32(d);
+  const size_t tab = ENS ? 0 : (split ? fast_table_bytes(d.ncell, d.nbins) : table32_bytes(d));
+  const size_t dyn = tab + (size_t)(NT / 32) * kStages * stream32_stage_bytes(DIM, C);
+  const int bi = NT == 128 ? 0 : (NT == 512 ? 2 : 1);
   const bool p3 = !d.grey && d.sig_p == -3.0;
   const void* fn = !split ? (const void*)k_stream32<DIM, ENS, NT> : fast_fn<NT>(p3, sh.ppt);
   int& occ = g_stream32_occ[DIM][ENS][bi];
