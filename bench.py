@@ -43,11 +43,12 @@ METRIC = "particle segments/s"
 # the scatter) and the end of step
 KERNELS_PER_STEP = {"fp64": 8, "mixed": 8}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per processed
-# particle of the particle kernels, from one ncu capture of the current
-# kernels at 4e6 particles on the slab (the traffic grows with the particles
-# processed); the roofline's "traffic" is this times the particles a launch
-# processes.  None: no capture of the current kernels.
-TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": None}
+# particle of the particle kernel, from one ncu capture of the current kernel
+# on the slab's 1e6-particle state (the benchmark's workload; the survivors'
+# writes are still in L2 when the kernel ends); the roofline's "traffic" is
+# this times the particles a launch processes.  None: no capture of the
+# current kernel.
+TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": 27.0}
 
 
 def combine_replicas(ms: float, segments: float, world: int, device):
@@ -302,7 +303,7 @@ def roofline(p, phase, launch_ms, n_proc, n_read, n_out, si_iters, mixed, pk, sr
          "algorithmic_bytes_per_launch": abytes, "launch_ms": launch_ms,
          "bytes_per_particle": (2 * p.dim + 2) * (4 if mixed else 8) + 8}
     if traffic is not None:
-        r["traffic_source"] = "ncu capture at 4e6 particles, scaled by particles processed per launch"
+        r["traffic_source"] = "ncu capture of the same kernel on the 1e6-particle slab state, scaled by particles processed per launch"
     if phase == "particles" and not mixed:
         r["note"] = "FP64-pipe bound on GB300 (see profiles/): HBM is not the limit of this kernel"
     return r
