@@ -1980,6 +1980,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_small(const uint32_t* __r
                                                             uint32_t* __restrict__ off,
                                                             unsigned long long* total_a,
                                                             unsigned long long* total_b) {
+  // a kernel launched after this one as its programmatic dependent may set
+  // itself up now (it waits for this kernel's results before reading them)
+  asm volatile("griddepcontrol.launch_dependents;");
   uint32_t carry = 0;
   for (long long t = 0; t * kScanTile < n; ++t) {
     const long long base = t * kScanTile + (long long)threadIdx.x * kScanPer;

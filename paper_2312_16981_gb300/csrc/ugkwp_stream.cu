@@ -1175,39 +1175,46 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
   float* s_sinv = reinterpret_cast<float*>(s_dyn);
   uint32_t* s_seg = reinterpret_cast<uint32_t*>(s_sinv + ncell);
   const int ns = fast_segments(d.nbins);
-  for (int c = threadIdx.x; c < ncell; c += NT) s_sinv[c] = __ldg(d.sTinv_f + c);
-  for (int s = threadIdx.x; s < ns; s += NT) s_seg[s] = __ldg(d.off + 32 * s);
   Ring32<1, false> rg;
   rg.C = C;
   rg.stage_sz = (size_t)C * StageF<1>::kBytesPer;
   rg.ring = s_dyn + fast_table_bytes(ncell, d.nbins) + (size_t)warp * kStages * rg.stage_sz;
   rg.bar = s_full[warp];
+  Ctrl* ctrl = d.ctrl;
+  // Set-up that needs nothing from the kernels before this one in the
+  // stream (launched as a programmatic dependent of the birth scan, it may
+  // run while the scan finishes): the rings' barriers and the copies of the
+  // warps' first survivor chunks (the previous step's survivors; the live
+  // buffer and its count were set by the previous step's end).
+  const unsigned cur = ctrl->cur;
+  const long long n_surv = (long long)ctrl->n_part[cur];
+  // a contiguous range of chunks per warp (bins run on across its chunks)
+  const long long gw = (long long)blockIdx.x * (NT / 32) + warp, tw = (long long)gridDim.x * (NT / 32);
+  const long long nall = (n_surv + C - 1) / C, per = (nall + tw - 1) / tw;
+  const long long c0 = gw * per < nall ? gw * per : nall;
+  const long long nchunks = c0 + per < nall ? c0 + per : nall;
+  const long long p0 = 0, p1 = n_surv;
+  auto issue_chunk = [&](long long c, int s) { rg.issue(&d, cur, c, n_surv, s); };
+  int issued = 0;
   if (lane == 0) {
     for (int k = 0; k < kStages; ++k) mbar_init(&rg.bar[k], 1);
     mbar_init_fence();
+    for (; issued < kStages && c0 + issued < nchunks; ++issued) issue_chunk(c0 + issued, issued);
   }
+  issued = __shfl_sync(full, issued, 0);
+  __syncwarp();
+  // the birth kernel's tables and the scan's offsets and count
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  for (int c = threadIdx.x; c < ncell; c += NT) s_sinv[c] = __ldg(d.sTinv_f + c);
+  for (int s = threadIdx.x; s < ns; s += NT) s_seg[s] = __ldg(d.off + 32 * s);
   __syncthreads();
   const StepHead h0 = step_head(d);
-  Ctrl* ctrl = d.ctrl;
-  // a contiguous range of survivors per warp, equal to within four (bins
-  // run on across its chunks), in chunks of C from its start (the last one
-  // partial)
-  const long long gw = (long long)blockIdx.x * (NT / 32) + warp, tw = (long long)gridDim.x * (NT / 32);
-  const long long nall = (h0.n_surv + C - 1) / C, per = (nall + tw - 1) / tw;
-  const long long c0 = gw * per < nall ? gw * per : nall;
-  const long long nchunks = c0 + per < nall ? c0 + per : nall;
-  const long long p0 = 0, p1 = h0.n_surv;
-  auto issue_chunk = [&](long long c, int s) { rg.issue(&d, h0.cur, c, h0.n_surv, s); };
   const unsigned nxb = h0.cur ^ 1u;
   const uint32_t G = (uint32_t)d.G;
   const float invG = d.invG_f;
   const float dxf = d.dxf, vf = d.vf, dtf = d.dtf, inv_rate = d.inv_rate_f, inv_capf = d.inv_capf, spf = d.spf;
   const int tq_shift = d.tq_shift;
   const bool grey = d.grey;
-  int issued = 0;
-  for (; issued < kStages && c0 + issued < nchunks; ++issued)
-    if (lane == 0) issue_chunk(c0 + issued, issued);
-  __syncwarp();
 
   int acc_key = -1;
   long long acc_w = 0;
@@ -1507,8 +1514,21 @@ static cudaError_t launch_stream32_t(const Dev& d, const Ens& e, const StreamSha
     k_stream32<DIM, ENS, NT><<<sms * per, NT, dyn, s>>>(d, e, sh.ppt);
     return cudaGetLastError();
   }
+  // a programmatic dependent of the kernel before it in the stream (the
+  // birth scan): its set-up and first copies overlap that kernel's end, and
+  // it waits for the kernel's results before it reads them
   void* args[] = {(void*)&d};
-  cudaError_t r = cudaLaunchKernel(fn, dim3(sms * per), dim3(NT), args, dyn, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sms * per);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t r = cudaLaunchKernelExC(&cfg, fn, args);
   if (!r) r = cudaGetLastError();
   return r;
 }
