@@ -48,7 +48,7 @@ KERNELS_PER_STEP = {"fp64": 8, "mixed": 8}
 # writes are still in L2 when the kernel ends); the roofline's "traffic" is
 # this times the particles a launch processes.  None: no capture of the
 # current kernel.
-TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": 27.0}
+TRAFFIC_PER_PROCESSED = {"fp64": None, "mixed": 27.1}
 
 
 def combine_replicas(ms: float, segments: float, world: int, device):
