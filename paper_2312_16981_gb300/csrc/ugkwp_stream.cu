@@ -1188,11 +1188,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 4))
   // buffer and its count were set by the previous step's end).
   const unsigned cur = ctrl->cur;
   const long long n_surv = (long long)ctrl->n_part[cur];
-  // a contiguous range of chunks per warp (bins run on across its chunks)
+  // a contiguous range of chunks per warp (bins run on across its chunks),
+  // the counts differing by at most one between warps (with whole chunks
+  // rounded up per warp, a step of a few chunks per warp would leave the
+  // last warps, and the SMs holding them, without survivors)
   const long long gw = (long long)blockIdx.x * (NT / 32) + warp, tw = (long long)gridDim.x * (NT / 32);
-  const long long nall = (n_surv + C - 1) / C, per = (nall + tw - 1) / tw;
-  const long long c0 = gw * per < nall ? gw * per : nall;
-  const long long nchunks = c0 + per < nall ? c0 + per : nall;
+  const long long nall = (n_surv + C - 1) / C;
+  const long long c0 = gw * nall / tw, nchunks = (gw + 1) * nall / tw;
   const long long p0 = 0, p1 = n_surv;
   auto issue_chunk = [&](long long c, int s) { rg.issue(&d, cur, c, n_surv, s); };
   int issued = 0;
