@@ -29,9 +29,11 @@ def B():
     return binding
 
 
-def run_pair(B, p, st, op):
+def run_gpu(B, p, st, op, shape=None):
     pm = p.replace(precision=I.MIXED)
     sim = B.Simulation(pm)
+    if shape is not None:
+        sim.set_launch(*shape)
     sim.set_state(st.T, st.rho, st.rho_h, st.particles.view(), step=st.step)
     _, n_new, _ = O.birth_counts(op, st.T, st.rho_h)
     sim.attach_records(st.particles.n + n_new + 8)
@@ -39,8 +41,14 @@ def run_pair(B, p, st, op):
     t = sim.tallies()
     g = sim.get_state()
     rg = sim.records(t["n_in"] + t["n_born"])
+    assert t["status_bits"] == 0
+    return t, g, rg
+
+
+def run_pair(B, p, st, op, shape=None):
+    t, g, rg = run_gpu(B, p, st, op, shape)
     st2, tal, ro, status = O.step(op, st, records=True)
-    assert status == 0 and t["status_bits"] == 0
+    assert status == 0
     return t, g, rg, st2, tal, ro
 
 
@@ -99,12 +107,26 @@ def test_mixed_larsen_slab(B):
     check(p, *run_pair(B, p, st, op))
 
 
-def test_mixed_full_size_slab(B):
+@pytest.fixture(scope="module")
+def full_size_slab():
+    # the 200x30 slab from the benchmark's 1e6-particle synthetic state, and
+    # the oracle's step from it (computed once for every launch shape)
     p = I.multigroup_slab()
     s = I.synthetic_state(p, 1_000_000, seed=3)
     op = O.OracleProblem(p)
     st = O.State(p, s["T"], s["rho"], s["rho_h"], O.ParticleSet.from_arrays(s["particles"]), s["step"])
-    flips = check(p, *run_pair(B, p, st, op))
+    st2, tal, ro, status = O.step(op, st, records=True)
+    assert status == 0
+    return p, op, st, st2, tal, ro
+
+
+# the default shape and those the autotuner picks on this workload (the
+# benchmark times the one it picks)
+@pytest.mark.parametrize("shape", [None, (512, 4, 0), (256, 2, 0), (128, 1, 0)])
+def test_mixed_full_size_slab(B, full_size_slab, shape):
+    p, op, st, st2, tal, ro = full_size_slab
+    t, g, rg = run_gpu(B, p, st, op, shape)
+    flips = check(p, t, g, rg, st2, tal, ro)
     assert flips < 2000
 
 
